@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark: forward + gradient of the IQP Monte-Carlo estimator.
+
+Workload (default): m = 100000 random generators on k in {1,2,3} qubits,
+n = 1000 qubits, l = 10000 observables (Bernoulli(0.05) bits), s = 10000
+samples, theta ~ U(-0.05, 0.05). One step = iqp_expval (parities, phase
+contraction, cos / mean / standard error) followed by iqp_expval_grad for the
+linear loss sum_a w_a <Z_a> (parities, Phi recomputed tile by tile, gradient
+contraction), i.e. one autograd forward + backward.
+
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import ctypes
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2501_04776_gb300 import inputs as I  # noqa: E402
+
+METRIC = "fwd+grad ms, 10k observables x 10k samples x 1e5 gates"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32"])
+    ap.add_argument("--n", type=int, default=1000)
+    ap.add_argument("--m", type=int, default=100_000)
+    ap.add_argument("--l", type=int, default=10_000)
+    ap.add_argument("--s", type=int, default=10_000)
+    ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the plain FP32 form (0 = skip)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-l", type=int, default=16)
+    ap.add_argument("--cpu-sample-s", type=int, default=2000)
+    return ap.parse_args()
+
+
+def workload(args):
+    return I.random_gates(n=args.n, m=args.m, l=args.l, s=args.s)
+
+
+def workload_name(args):
+    return (f"random-gates n={args.n} m={args.m} (k in 1..3) l={args.l} (Bernoulli 0.05) s={args.s}, "
+            f"fwd+grad of sum_a w_a <Z_a>")
+
+
+# ------------------------------------------------------------- CPU baseline
+
+def cpu_baseline(p, args, gpu_ev=None, gpu_se=None, gpu_grad_fn=None):
+    """Time the FP64 oracle on a bounded sample and extrapolate to the full
+    step with its cost model T = 2 t_row (l + s) + c_phase l s: each oracle call
+    forms both parity matrices (linear in rows) and then loops over
+    (observable, sample) pairs. Also measures the GPU error on sampled
+    observables against the oracle on identical samples."""
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(cores)
+    th = p.theta.astype(np.float64)
+    ls, ss = min(args.cpu_sample_l, p.l), min(args.cpu_sample_s, p.s)
+    A1, Z1 = p.A[:ls], p.Z[:ss]
+    t0 = time.perf_counter()
+    oracle.parity(p.n, Z1, p.G)
+    t_par = time.perf_counter() - t0
+    t_row = t_par / ss
+    w = I.Rng(99).normal(p.l, 1)
+    t0 = time.perf_counter()
+    oracle.expval(p.n, p.G, A1, Z1, th)
+    oracle.expval_grad(p.n, p.G, A1, Z1, th, -w[:ls] / ss, None)
+    t_step = time.perf_counter() - t0
+    c_phase = max(t_step - 2 * t_row * (ls + ss), 0.0) / (ls * ss)
+    full_s = 2 * t_row * (p.l + p.s) + c_phase * p.l * p.s
+    out = {
+        "value": full_s * 1e3, "unit": "ms", "cores": cores, "kind": "oracle",
+        "sample": (f"oracle expval+expval_grad on {ls} observables x {ss} samples x all {p.m} gates "
+                   f"({t_step:.2f} s) plus parity of {ss} sample rows ({t_par:.2f} s); extrapolated to "
+                   f"{p.l} x {p.s} with T = 2*t_row*(l+s) + c*l*s"),
+        "measured_s": round(t_step + t_par, 3),
+    }
+    if gpu_ev is not None:
+        idx = np.unique(np.sort(I.Rng(77).integers(8, p.l, 1)))
+        ev, se, _, _ = oracle.expval(p.n, p.G, p.A[idx], p.Z, th)
+        err = {"observables_checked": int(idx.size),
+               "max_abs_err_expval": float(np.max(np.abs(gpu_ev[idx] - ev))),
+               "max_abs_err_std_err": float(np.max(np.abs(gpu_se[idx] - se)))}
+        if gpu_grad_fn is not None:
+            alpha = np.zeros(p.l)
+            alpha[idx] = -w[idx] / p.s
+            g = gpu_grad_fn(alpha)
+            want = oracle.expval_grad(p.n, p.G, p.A[idx], p.Z, th, alpha[idx], None)
+            err["grad_rel_l2"] = float(np.linalg.norm(g - want) / np.linalg.norm(want))
+        out["error_vs_fp64"] = err
+    return out
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p = workload(args)
+    steps = []
+    base = None
+    for _ in range(args.warmup + args.steps):
+        base = cpu_baseline(p, args)
+        steps.append(base["value"])
+    timed = steps[args.warmup:]
+    ms = statistics.mean(timed)
+    base["value"] = ms
+    line = {
+        "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded splitmix64)",
+        "config": {"workload": workload_name(args), "n": p.n, "m": p.m, "l": p.l, "s": p.s,
+                   "precision": "fp64 CPU oracle"},
+        "cpu_baseline": base,
+        "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_2501_04776_gb300 import _lib, api, build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    lib = _lib.load()
+    prec = _lib.SPLIT_BF16 if args.precision == "split_bf16" else _lib.FP32
+    if prec == _lib.SPLIT_BF16 and not lib.iqp_tensor_path_available():
+        raise SystemExit("the split-BF16 tensor path needs an sm_103 GPU")
+
+    p = workload(args)
+    n, m, l, s = p.n, p.m, p.l, p.s
+    w = I.Rng(99).normal(l, 1)
+    dev = torch.device("cuda", local)
+    G, A, Z = (api.to_device_bits(x, dev) for x in (p.G, p.A, p.Z))
+    theta = torch.from_numpy(p.theta).to(dev)
+    alpha = torch.from_numpy(-w / s).to(dev)
+    ev = torch.empty(l, dtype=torch.float64, device=dev)
+    se = torch.empty(l, dtype=torch.float64, device=dev)
+    grad = torch.empty(m, dtype=torch.float64, device=dev)
+    nbytes = max(lib.iqp_workspace_bytes(_lib.OP_EXPVAL, n, m, l, s, 0, prec),
+                 lib.iqp_workspace_bytes(_lib.OP_EXPVAL_GRAD, n, m, l, s, 0, prec))
+    ws = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    P = ctypes.c_void_p
+    st = P(stream.cuda_stream)
+
+    def step(precision, Gd=G, Ad=A, Zd=Z, th=theta, al=alpha, evd=ev, sed=se, gd=grad):
+        _lib.check(lib.iqp_expval(n, P(Gd.data_ptr()), m, Gd.shape[1], P(Ad.data_ptr()), l, Ad.shape[1],
+                                  P(Zd.data_ptr()), s, Zd.shape[1], P(th.data_ptr()), precision, P(evd.data_ptr()),
+                                  P(sed.data_ptr()), P(ws.data_ptr()), ws.numel(), st), "iqp_expval")
+        _lib.check(lib.iqp_expval_grad(n, P(Gd.data_ptr()), m, Gd.shape[1], P(Ad.data_ptr()), l, Ad.shape[1],
+                                       P(Zd.data_ptr()), s, Zd.shape[1], P(th.data_ptr()), P(al.data_ptr()), None,
+                                       precision, P(gd.data_ptr()), P(ws.data_ptr()), ws.numel(), st),
+                   "iqp_expval_grad")
+
+    def timed(precision, k, warm, profile=False):
+        for _ in range(warm):
+            step(precision)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        if profile:
+            lib.iqp_profile_reset()
+            lib.iqp_profile_enable(1)
+        launches0 = lib.iqp_launch_count()
+        evs = []
+        for _ in range(k):
+            flush.zero_()  # L2 flush between steps, outside the step's events
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(precision)
+            e1.record(stream)
+            evs.append((e0, e1))
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        launches = lib.iqp_launch_count() - launches0
+        if profile:
+            lib.iqp_profile_enable(0)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        return ms, launches
+
+    vis = [x for x in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if x.strip()]
+    sampler = ClockSampler(vis[local].strip() if local < len(vis) else str(local))
+    sampler.start()
+    ms_list, launches = timed(prec, args.steps, args.warmup, profile=True)
+    clocks = sampler.stop()
+    status = lib.iqp_read_status(P(ws.data_ptr()), ws.numel(), st)
+    if status != 0:
+        raise SystemExit(f"device status {status}: {_lib.status_string(status)}")
+    ms = statistics.mean(ms_list)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # Per-kernel live timings of the timed region (events on the launch stream).
+    kt = {}
+    for k, name in enumerate(_lib.KERNELS):
+        tot, cnt = ctypes.c_double(0), ctypes.c_uint64(0)
+        lib.iqp_profile_query(k, ctypes.byref(tot), ctypes.byref(cnt))
+        if cnt.value:
+            kt[name] = {"launches": int(cnt.value), "total_ms": round(tot.value, 4),
+                        "avg_ms": round(tot.value / cnt.value, 4)}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    if prec == _lib.SPLIT_BF16:
+        dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
+        executed = 4.0 * l * s * m  # two BF16 products (hi, lo) of 2*l*s*m flops per launch
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        achieved = executed / (kt[dom]["avg_ms"] * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "flops_per_launch": executed, "useful_tflops": round(achieved / 2, 1),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+                if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
+    else:
+        dom = max(("phase_fp32", "recompute_fp32", "grad_fp32"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
+        flops = 2.0 * l * s * m
+        achieved = flops / (kt[dom]["avg_ms"] * 1e-3) / 1e12
+        peak = 152 * 128 * 2 * (clocks or {}).get("sm_mhz", 1425.0) * 1e6 / 1e12
+        roof = {"bound": "alu", "kernel": dom, "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "flops_per_launch": flops, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock"}
+
+    # Plain FP32 form on the same GPU, same workload.
+    fp32 = None
+    if prec == _lib.SPLIT_BF16 and args.fp32_steps > 0:
+        ms32, _ = timed(_lib.FP32, args.fp32_steps, 1)
+        fp32 = {"ms_per_step": round(statistics.mean(ms32), 3), "steps": args.fp32_steps}
+
+    # End to end: host (pinned) inputs -> device, both calls, results -> host.
+    hG, hA, hZ = (x.cpu().pin_memory() for x in (G, A, Z))
+    hth, hal = theta.cpu().pin_memory(), alpha.cpu().pin_memory()
+    hev, hse, hgr = (torch.empty(x.shape, dtype=x.dtype).pin_memory() for x in (ev, se, grad))
+    dG, dA, dZ = (torch.empty_like(x) for x in (G, A, Z))
+    dth, dal = torch.empty_like(theta), torch.empty_like(alpha)
+    h2d = sum(x.numel() * x.element_size() for x in (hG, hA, hZ, hth, hal))
+    d2h = sum(x.numel() * x.element_size() for x in (hev, hse, hgr))
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for d, h in ((dG, hG), (dA, hA), (dZ, hZ), (dth, hth), (dal, hal)):
+            d.copy_(h, non_blocking=True)
+        step(prec, dG, dA, dZ, dth, dal)
+        for h, d in ((hev, ev), (hse, se), (hgr, grad)):
+            h.copy_(d, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append(e0.elapsed_time(e1))
+    e2e = {"value": round(statistics.mean(e2e_ms), 3), "unit": "ms", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(d2h)}
+
+    line = {
+        "metric": METRIC, "value": round(ms, 3), "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == _lib.SPLIT_BF16 else "f32",
+        "data": "synthetic (seeded splitmix64), shaped like the paper's op_expval benchmark",
+        "config": {"workload": workload_name(args), "n": n, "m": m, "l": l, "s": s,
+                   "precision": args.precision + (" (2 theta = hi + lo BF16, FP32 accumulate in TMEM, FP64 "
+                                                  "reductions)" if prec == _lib.SPLIT_BF16 else ""),
+                   "l2": "flushed between steps (256 MiB write, outside the step events)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roof, "kernels": kt, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
+        "ms_steps": [round(x, 3) for x in ms_list],
+    }
+    if fp32 is not None:
+        line["fp32_form"] = fp32
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        def gpu_grad_fn(alpha_np):
+            al = torch.from_numpy(alpha_np).to(dev)
+            g2 = torch.empty(m, dtype=torch.float64, device=dev)
+            _lib.check(lib.iqp_expval_grad(n, P(G.data_ptr()), m, G.shape[1], P(A.data_ptr()), l, A.shape[1],
+                                           P(Z.data_ptr()), s, Z.shape[1], P(theta.data_ptr()), P(al.data_ptr()),
+                                           None, prec, P(g2.data_ptr()), P(ws.data_ptr()), ws.numel(), st),
+                       "iqp_expval_grad")
+            return g2.cpu().numpy()
+        step(prec)
+        torch.cuda.synchronize()
+        line["cpu_baseline"] = cpu_baseline(p, args, ev.cpu().numpy(), se.cpu().numpy(), gpu_grad_fn)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * iqp.h - C ABI of the GB300 (sm_103a) IQP expectation-value library.
+ *
+ * The library computes, for a parameterised IQP circuit
+ *   U(theta) = prod_j exp(i theta_j X_{g_j})  acting on |0>   (Def. 1, Sec. 2),
+ * Monte-Carlo estimates of Pauli-Z expectation values
+ *   <Z_a> = E_{z ~ U{0,1}^n} [ cos Phi(a,z) ],
+ *   Phi(a,z) = sum_j 2 theta_j [g_j.a odd] (1 - 2 [g_j.z odd])
+ * (eqs. op_expval and expvalsample, Sec. 2.1; batch form E = C Theta B^T of
+ * eq. Emat, Sec. 2.2), their standard errors, the gradient in theta
+ * (Sec. 2.4), and the MMD^2 loss of eq. mmd_estimate (Sec. 3.3.1) between the
+ * circuit and a data set.
+ *
+ * Conventions for every call:
+ *  - Bit matrices (generators G, observables A, samples Z, data X, parities)
+ *    are uint64 words, row-major, `ld` words per row, LSB-first: bit b of word
+ *    w is column 64*w + b. `ld` is even and >= ceil(cols/64); base pointers
+ *    are 16-byte aligned; padding bits beyond the last column are zero.
+ *  - m = rows of G (gates), l = rows of A (observables), s = rows of Z
+ *    (samples), N = rows of X (data rows), n = qubits (columns).
+ *  - Every pointer except the host status strings is DEVICE memory owned by
+ *    the caller. The library allocates nothing: scratch comes from `ws`, sized
+ *    by iqp_workspace_bytes(), 256-byte aligned.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) and keep no state between calls, so distinct workspaces may be
+ *    used from several host threads at once.
+ *  - Errors: host-side argument checks run before any launch and return a
+ *    status; nothing is launched then. Device-side failures (a bounded wait
+ *    that ran out) set a status word inside `ws`, which iqp_read_status()
+ *    returns. Nothing aborts, exits or traps.
+ *  - Outputs are float64. theta is float32 on the device.
+ */
+#ifndef IQP_H
+#define IQP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IQP_OK = 0,
+    IQP_ERR_ARG = 1,         /* a size, pointer or flag is invalid            */
+    IQP_ERR_ALIGN = 2,       /* a pointer or leading dimension is misaligned  */
+    IQP_ERR_WORKSPACE = 3,   /* ws is NULL, misaligned or too small           */
+    IQP_ERR_CUDA = 4,        /* a CUDA runtime/driver call failed             */
+    IQP_ERR_TIMEOUT = 5,     /* a device-side bounded wait ran out            */
+    IQP_ERR_UNSUPPORTED = 6  /* the device or build lacks a required feature  */
+} iqp_status;
+
+/* Arithmetic of the phase contraction Phi = (2 theta . P_A) S_Z^T.
+ * IQP_FP32: FP32 FMA on the SIMT cores (the plain form).
+ * IQP_SPLIT_BF16: tcgen05 tensor cores; 2 theta is split into hi + lo BF16
+ * parts (hi = RN_bf16(2 theta), lo = RN_bf16(2 theta - hi)), the +-1 and 0/1
+ * operands are exact in BF16, and both products accumulate in FP32 in TMEM. */
+typedef enum { IQP_FP32 = 0, IQP_SPLIT_BF16 = 1 } iqp_precision;
+
+/* Operation whose scratch iqp_workspace_bytes() sizes. */
+typedef enum {
+    IQP_OP_EXPVAL = 1,
+    IQP_OP_EXPVAL_GRAD = 2,
+    IQP_OP_MMD_LOSS = 3,
+    IQP_OP_MMD_LOSS_GRAD = 4
+} iqp_op;
+
+/* Bytes of device scratch `ws` needed by `op` for these sizes (N is ignored
+ * except for the MMD ops). Returns 0 for invalid sizes. Host only. */
+size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N,
+                           iqp_precision prec);
+
+/* GF(2) products of Sec. 2.2 (A.G^T and Z.G^T mod 2):
+ *   P[r][j] = (R_r . g_j) mod 2,  r < rows, j < m,
+ * written bit-packed: row r of P is ldp words, bit j of the row is parity
+ * with gate j; bits j >= m of each written row are set to zero.
+ * R: rows x ldr words; G: m x ldg words; n <= 64*min(ldr, ldg).
+ * ldp >= ceil(m/64), even. Bit-exact. No scratch. */
+iqp_status iqp_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr,
+                      const uint64_t *G, int64_t m, int64_t ldg,
+                      uint64_t *P, int64_t ldp, void *stream);
+
+/* Data parity sums of Sec. 3.3.1: T[a] = sum_{x < N} (-1)^{a.x}, so that
+ * <Z_a>_p = T[a]/N for the empirical data distribution. A: l x lda words,
+ * X: N x ldx words. T: int64[l], overwritten. Exact. No scratch. */
+iqp_status iqp_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda,
+                          const uint64_t *X, int64_t N, int64_t ldx, int64_t *T, void *stream);
+
+/* Estimator of eq. expvalsample for every observable, on the sample batch Z
+ * shared by all observables (Sec. 2.2):
+ *   expval[a]  = (1/s) sum_i cos Phi(a, z_i),
+ *   std_err[a] = sqrt( (1/s) sum_i (cos Phi(a,z_i) - expval[a])^2 ) / sqrt(s)
+ * (population variance, ddof = 0). s >= 1. Either output may be NULL.
+ * ws: iqp_workspace_bytes(IQP_OP_EXPVAL, ...). */
+iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                      const uint64_t *A, int64_t l, int64_t lda,
+                      const uint64_t *Z, int64_t s, int64_t ldz,
+                      const float *theta, iqp_precision prec,
+                      double *expval, double *std_err,
+                      void *ws, size_t ws_bytes, void *stream);
+
+/* Gradient of the estimator in theta (Sec. 2.4; the estimator is a
+ * deterministic function of theta for fixed Z), for losses whose derivative
+ * in the samples has the form dL/dPhi(a,z_i) = -sin Phi (alpha[a] + beta[a] cos Phi):
+ *   grad[j] = sum_a sum_i sin Phi(a,z_i) (alpha[a] + beta[a] cos Phi(a,z_i))
+ *             * 2 [g_j.a odd] (1 - 2 [g_j.z_i odd]).
+ * For L = sum_a w_a expval[a] pass alpha[a] = -w_a/s and beta = NULL.
+ * Phi is recomputed tile by tile, never stored. alpha: float64[l] (device),
+ * beta: float64[l] or NULL. grad: float64[m], overwritten.
+ * ws: iqp_workspace_bytes(IQP_OP_EXPVAL_GRAD, ...). */
+iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                           const uint64_t *A, int64_t l, int64_t lda,
+                           const uint64_t *Z, int64_t s, int64_t ldz,
+                           const float *theta, const double *alpha, const double *beta,
+                           iqp_precision prec, double *grad,
+                           void *ws, size_t ws_bytes, void *stream);
+
+/* MMD^2 estimate of eq. mmd_estimate (Sec. 3.3.1) over the l observables in
+ * A (drawn by the caller, bits i.i.d. Bernoulli(p_sigma) for a Gaussian
+ * kernel of bandwidth sigma), with model terms from the estimator on Z and
+ * data terms from X:
+ *   unbiased != 0:  term_a = (T^2 - N)/(N(N-1)) - 2 (T/N)(S1/s) + (S1^2 - S2)/(s(s-1))
+ *   unbiased == 0:  term_a = (T/N - S1/s)^2
+ *   loss = (1/l) sum_a term_a,  S1 = sum_i cos Phi, S2 = sum_i cos^2 Phi, T as in
+ *   iqp_parity_sum. The unbiased form needs s >= 2 and N >= 2.
+ * loss: one float64 on the device. ws: iqp_workspace_bytes(IQP_OP_MMD_LOSS, ...). */
+iqp_status iqp_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                        const uint64_t *A, int64_t l, int64_t lda,
+                        const uint64_t *Z, int64_t s, int64_t ldz,
+                        const uint64_t *X, int64_t N, int64_t ldx,
+                        const float *theta, iqp_precision prec, int unbiased,
+                        double *loss, void *ws, size_t ws_bytes, void *stream);
+
+/* Loss as iqp_mmd_loss and its gradient grad[m] in theta, by the chain rule
+ * through S1 and S2 (alpha, beta of iqp_expval_grad formed on the device).
+ * ws: iqp_workspace_bytes(IQP_OP_MMD_LOSS_GRAD, ...). */
+iqp_status iqp_mmd_loss_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                             const uint64_t *A, int64_t l, int64_t lda,
+                             const uint64_t *Z, int64_t s, int64_t ldz,
+                             const uint64_t *X, int64_t N, int64_t ldx,
+                             const float *theta, iqp_precision prec, int unbiased,
+                             double *loss, double *grad, void *ws, size_t ws_bytes, void *stream);
+
+/* Device-side status of the last calls that used `ws`: synchronises
+ * `stream`, returns IQP_OK or the first error a kernel recorded (e.g.
+ * IQP_ERR_TIMEOUT), and clears it. */
+iqp_status iqp_read_status(void *ws, size_t ws_bytes, void *stream);
+
+/* Self-test of the bounded-wait machinery: one CTA waits on an mbarrier that
+ * nothing arrives on, gives up after `limit_seconds` (<= 10), records
+ * IQP_ERR_TIMEOUT in ws and returns. Read it with iqp_read_status(). */
+iqp_status iqp_selftest_timeout(void *ws, size_t ws_bytes, double limit_seconds, void *stream);
+
+/* Kernels of this library, for iqp_profile_query(). */
+typedef enum {
+    IQP_KERNEL_PARITY = 0,         /* GF(2) products (P_A, P_Z, P_Z^T)          */
+    IQP_KERNEL_PARITY_SUM = 1,     /* data parity sums T                        */
+    IQP_KERNEL_THETA_SPLIT = 2,    /* 2 theta, and its hi/lo BF16 split         */
+    IQP_KERNEL_PHASE_FP32 = 3,     /* SIMT phase contraction + statistics       */
+    IQP_KERNEL_RECOMPUTE_FP32 = 4, /* SIMT phase recompute -> W                 */
+    IQP_KERNEL_GRAD_FP32 = 5,      /* SIMT gradient contraction                 */
+    IQP_KERNEL_PHASE_TC = 6,       /* tcgen05 phase contraction + statistics    */
+    IQP_KERNEL_RECOMPUTE_TC = 7,   /* tcgen05 phase recompute -> W (hi/lo)      */
+    IQP_KERNEL_GRAD_TC = 8,        /* tcgen05 gradient contraction              */
+    IQP_KERNEL_FINALIZE = 9,       /* per-observable mean / standard error      */
+    IQP_KERNEL_GRAD_REDUCE = 10,   /* fixed-order reduction of gradient parts   */
+    IQP_KERNEL_MMD_COMBINE = 11,   /* MMD^2 terms and gradient coefficients     */
+    IQP_KERNEL_SELFTEST = 12,      /* iqp_selftest_timeout                      */
+    IQP_KERNEL_COUNT = 13
+} iqp_kernel;
+
+/* Per-kernel timing (off by default). When enabled, every launch is
+ * bracketed by two CUDA events recorded on the launch's stream; the events
+ * add a few microseconds per launch and no synchronisation. Host only;
+ * process-wide; thread-safe. */
+void iqp_profile_enable(int on);
+void iqp_profile_reset(void);
+/* Total elapsed milliseconds and launch count of `kernel` since the last
+ * reset. Synchronises on the pending events. */
+iqp_status iqp_profile_query(iqp_kernel kernel, double *total_ms, uint64_t *launches);
+
+/* Static text for a status. Host only. */
+const char *iqp_status_string(iqp_status st);
+
+/* Number of kernels this library has launched in this process (host counter). */
+uint64_t iqp_launch_count(void);
+
+/* 1 if the current device supports the IQP_SPLIT_BF16 path (sm_103 family). */
+int iqp_tensor_path_available(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IQP_H */

@@ -1,0 +1,413 @@
+// The C ABI of include/iqp.h: argument checks, workspace plan and the launch
+// sequence of each call. Every step of the computation runs in the kernels of
+// parity.cu, simt.cu and tc.cu; this file only validates and orders them.
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "common.cuh"
+
+namespace iqp {
+
+// ---- kernels (parity.cu, simt.cu, tc.cu)
+cudaError_t launch_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G, int64_t m,
+                          int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt, cudaStream_t st);
+cudaError_t launch_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,
+                              int64_t ldx, int64_t *T, cudaStream_t st);
+cudaError_t launch_theta_prep(const float *theta, int64_t m, int64_t mpad, float *c32, __nv_bfloat16 *hi,
+                              __nv_bfloat16 *lo, cudaStream_t st);
+cudaError_t launch_phase_simt(int mode, const uint64_t *PA, const uint64_t *PZ, int64_t ldp, const float *c,
+                              int64_t l, int64_t s, int64_t m, double2 *part, int64_t nparts, const double *alpha,
+                              const double *beta, float *W, int64_t ldw, cudaStream_t st);
+cudaError_t launch_grad_simt(const float *W, int64_t ldw, const uint64_t *PZ, const uint64_t *PA, int64_t ldp,
+                             int64_t l, int64_t s, int64_t m, double *gpart, cudaStream_t st);
+cudaError_t launch_finalize(const double2 *part, int64_t nparts, int64_t l, int64_t s, double *expval,
+                            double *std_err, double *S1, double *S2, cudaStream_t st);
+cudaError_t launch_grad_reduce(const double *gpart, int64_t ntiles, int64_t m, double *grad, cudaStream_t st);
+cudaError_t launch_mmd_combine(const int64_t *T, const double *S1, const double *S2, int64_t l, int64_t s, int64_t N,
+                               int unbiased, double *terms, double *alpha, double *beta, double *loss,
+                               cudaStream_t st);
+cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alpha, const double *beta,
+                            cudaStream_t st, iqp_status *why);
+cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why);
+cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st);
+
+// ---------------------------------------------------------------- plan
+
+Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec) {
+    Plan p;
+    std::memset(&p, 0, sizeof(p));
+    p.op = op;
+    p.prec = prec;
+    p.n = n;
+    p.m = m;
+    p.l = l;
+    p.s = s;
+    p.N = N;
+    p.ldp = round_up(cdiv(m, 64), 4);
+    p.ldzt = round_up(cdiv(s, 64), 4);
+    p.mpad = p.ldp * 64;
+    p.ldw = round_up(s, 64);
+    p.nparts = cdiv(s, kPartCols);
+    p.natile = cdiv(l, kATile);
+    const bool grad = op == IQP_OP_EXPVAL_GRAD || op == IQP_OP_MMD_LOSS_GRAD;
+    const bool mmd = op == IQP_OP_MMD_LOSS || op == IQP_OP_MMD_LOSS_GRAD;
+    const bool tc = prec == IQP_SPLIT_BF16;
+    size_t off = 0;
+    auto take = [&](int64_t bytes) {
+        const size_t o = off;
+        off += (size_t)round_up(bytes > 0 ? bytes : 0, 256);
+        return o;
+    };
+    p.off_status = take(256);
+    p.off_pa = take(l * p.ldp * 8);
+    p.off_pz = take(s * p.ldp * 8);
+    p.off_pzt = take(grad && tc ? m * p.ldzt * 8 : 0);
+    p.off_c = take(tc ? p.mpad * 4 : p.mpad * 4);
+    p.off_part = take(l * p.nparts * 16);
+    p.off_w = take(grad ? (tc ? l * p.ldw * 4 : l * p.ldw * 4) : 0);
+    p.off_gpart = take(grad ? p.natile * m * 8 : 0);
+    p.off_ab = take(mmd ? l * 16 : 0);
+    p.off_s12 = take(mmd ? l * 16 : 0);
+    p.off_T = take(mmd ? l * 8 : 0);
+    p.off_terms = take(mmd ? l * 8 : 0);
+    p.total = off;
+    return p;
+}
+
+// ---------------------------------------------------------------- misc
+
+static std::atomic<uint64_t> g_launches{0};
+static std::atomic<int> g_profiling{0};
+static std::mutex g_prof_mu;
+struct PendingEvent {
+    int kernel;
+    cudaEvent_t a, b;
+};
+static std::vector<PendingEvent> g_pending;
+static double g_prof_ms[IQP_KERNEL_COUNT];
+static uint64_t g_prof_n[IQP_KERNEL_COUNT];
+
+LaunchScope::LaunchScope(int k, cudaStream_t s) : kernel(k), st(s), ev0(nullptr), ev1(nullptr) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_profiling.load(std::memory_order_relaxed)) {
+        if (cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess) {
+            cudaEventRecord(ev0, st);
+        } else {
+            ev0 = ev1 = nullptr;
+        }
+    }
+}
+
+LaunchScope::~LaunchScope() {
+    if (ev0 != nullptr) {
+        cudaEventRecord(ev1, st);
+        std::lock_guard<std::mutex> g(g_prof_mu);
+        g_pending.push_back({kernel, ev0, ev1});
+    }
+}
+
+static void drain_pending() {
+    for (auto &p : g_pending) {
+        float ms = 0.f;
+        if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+            g_prof_ms[p.kernel] += ms;
+            g_prof_n[p.kernel] += 1;
+        }
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    g_pending.clear();
+}
+
+iqp_status cuda_status(cudaError_t e) { return e == cudaSuccess ? IQP_OK : IQP_ERR_CUDA; }
+
+int num_sms() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    return v;
+}
+
+int device_cc() {
+    int dev = 0, ma = 0, mi = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    cudaDeviceGetAttribute(&ma, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&mi, cudaDevAttrComputeCapabilityMinor, dev);
+    return ma * 10 + mi;
+}
+
+namespace {
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+iqp_status check_bits(const uint64_t *M, int64_t rows, int64_t ld, int64_t n) {
+    if (rows < 1) return IQP_ERR_ARG;
+    if (M == nullptr) return IQP_ERR_ARG;
+    if (ld < cdiv(n, 64) || (ld & 1)) return IQP_ERR_ARG;
+    if (!aligned(M, 16)) return IQP_ERR_ALIGN;
+    return IQP_OK;
+}
+
+iqp_status check_common(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                        int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                        iqp_precision prec) {
+    if (n < 1 || m < 1 || l < 1 || s < 1) return IQP_ERR_ARG;
+    if (m > (int64_t)1 << 40 || l > (int64_t)1 << 31 || s > (int64_t)1 << 31) return IQP_ERR_ARG;
+    iqp_status st;
+    if ((st = check_bits(G, m, ldg, n)) != IQP_OK) return st;
+    if ((st = check_bits(A, l, lda, n)) != IQP_OK) return st;
+    if ((st = check_bits(Z, s, ldz, n)) != IQP_OK) return st;
+    if (theta == nullptr) return IQP_ERR_ARG;
+    if (!aligned(theta, 4)) return IQP_ERR_ALIGN;
+    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16) return IQP_ERR_ARG;
+    if (prec == IQP_SPLIT_BF16 && !iqp_tensor_path_available()) return IQP_ERR_UNSUPPORTED;
+    return IQP_OK;
+}
+
+iqp_status check_ws(const Plan &p, void *ws, size_t ws_bytes) {
+    if (ws == nullptr || !aligned(ws, 256)) return IQP_ERR_WORKSPACE;
+    if (ws_bytes < p.total) return IQP_ERR_WORKSPACE;
+    return IQP_OK;
+}
+
+template <class T>
+T *at(void *ws, size_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
+}
+
+#define IQP_TRY(expr)                                   \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) return IQP_ERR_CUDA;     \
+    } while (0)
+
+// Parities of A and Z (and P_Z^T for the tensor-core gradient) + theta split.
+iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, const uint64_t *A, int64_t lda,
+                   const uint64_t *Z, int64_t ldz, const float *theta, bool need_pzt, cudaStream_t st) {
+    IQP_TRY(launch_parity(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp, nullptr, 0, st));
+    IQP_TRY(launch_parity(p.n, Z, p.s, ldz, G, p.m, ldg, at<uint64_t>(ws, p.off_pz), p.ldp,
+                          need_pzt ? at<uint64_t>(ws, p.off_pzt) : nullptr, p.ldzt, st));
+    if (p.prec == IQP_SPLIT_BF16) {
+        __nv_bfloat16 *hi = at<__nv_bfloat16>(ws, p.off_c);
+        IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, nullptr, hi, hi + p.mpad, st));
+    } else {
+        IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, at<float>(ws, p.off_c), nullptr, nullptr, st));
+    }
+    return IQP_OK;
+}
+
+// Phase contraction with the statistics epilogue -> (expval, std_err, S1, S2).
+iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_err, double *S1, double *S2,
+                         cudaStream_t st) {
+    double2 *part = at<double2>(ws, p.off_part);
+    if (p.prec == IQP_SPLIT_BF16) {
+        iqp_status why = IQP_OK;
+        if (launch_phase_tc(0, p, ws, nullptr, nullptr, st, &why) != cudaSuccess)
+            return why != IQP_OK ? why : IQP_ERR_CUDA;
+    } else {
+        IQP_TRY(launch_phase_simt(0, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pz), p.ldp,
+                                  at<float>(ws, p.off_c), p.l, p.s, p.m, part, p.nparts, nullptr, nullptr, nullptr, 0,
+                                  st));
+    }
+    IQP_TRY(launch_finalize(part, p.nparts, p.l, p.s, expval, std_err, S1, S2, st));
+    return IQP_OK;
+}
+
+// Recompute Phi tile by tile into W, contract against S_Z and mask by P_A.
+iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *beta, double *grad,
+                    cudaStream_t st) {
+    double *gpart = at<double>(ws, p.off_gpart);
+    if (p.prec == IQP_SPLIT_BF16) {
+        iqp_status why = IQP_OK;
+        if (launch_phase_tc(1, p, ws, alpha, beta, st, &why) != cudaSuccess) return why != IQP_OK ? why : IQP_ERR_CUDA;
+        if (launch_grad_tc(p, ws, st, &why) != cudaSuccess) return why != IQP_OK ? why : IQP_ERR_CUDA;
+    } else {
+        float *W = at<float>(ws, p.off_w);
+        IQP_TRY(launch_phase_simt(1, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pz), p.ldp,
+                                  at<float>(ws, p.off_c), p.l, p.s, p.m, nullptr, 0, alpha, beta, W, p.ldw, st));
+        IQP_TRY(launch_grad_simt(W, p.ldw, at<uint64_t>(ws, p.off_pz), at<uint64_t>(ws, p.off_pa), p.ldp, p.l, p.s,
+                                 p.m, gpart, st));
+    }
+    IQP_TRY(launch_grad_reduce(gpart, p.natile, p.m, grad, st));
+    return IQP_OK;
+}
+
+iqp_status mmd_core(int op, int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                    int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const uint64_t *X, int64_t N,
+                    int64_t ldx, const float *theta, iqp_precision prec, int unbiased, double *loss, double *grad,
+                    void *ws, size_t ws_bytes, void *stream) {
+    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    if (rc != IQP_OK) return rc;
+    if ((rc = check_bits(X, N, ldx, n)) != IQP_OK) return rc;
+    if (loss == nullptr || !aligned(loss, 8)) return IQP_ERR_ARG;
+    if (op == IQP_OP_MMD_LOSS_GRAD && (grad == nullptr || !aligned(grad, 8))) return IQP_ERR_ARG;
+    if (unbiased && (s < 2 || N < 2)) return IQP_ERR_ARG;
+    const Plan p = make_plan(op, n, m, l, s, N, prec);
+    if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const bool g = op == IQP_OP_MMD_LOSS_GRAD;
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, g && prec == IQP_SPLIT_BF16, st)) != IQP_OK) return rc;
+    double *S1 = at<double>(ws, p.off_s12), *S2 = S1 + l;
+    if ((rc = forward_stats(p, ws, nullptr, nullptr, S1, S2, st)) != IQP_OK) return rc;
+    int64_t *T = at<int64_t>(ws, p.off_T);
+    IQP_TRY(launch_parity_sum(n, A, l, lda, X, N, ldx, T, st));
+    double *alpha = at<double>(ws, p.off_ab), *beta = alpha + l;
+    IQP_TRY(launch_mmd_combine(T, S1, S2, l, s, N, unbiased, at<double>(ws, p.off_terms), alpha, beta, loss, st));
+    if (g) return backward(p, ws, alpha, beta, grad, st);
+    return IQP_OK;
+}
+
+uint64_t spin_limit_ns() {
+    const char *e = std::getenv("IQP_SPIN_LIMIT_MS");
+    double ms = e ? std::atof(e) : 4000.0;
+    if (!(ms > 0.0)) ms = 4000.0;
+    if (ms > 60000.0) ms = 60000.0;
+    return (uint64_t)(ms * 1e6);
+}
+
+}  // namespace
+
+uint64_t default_spin_limit_ns() { return spin_limit_ns(); }
+
+}  // namespace iqp
+
+using namespace iqp;
+
+extern "C" {
+
+size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, iqp_precision prec) {
+    if (n < 1 || m < 1 || l < 1 || s < 1) return 0;
+    if (op < IQP_OP_EXPVAL || op > IQP_OP_MMD_LOSS_GRAD) return 0;
+    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16) return 0;
+    return make_plan(op, n, m, l, s, N, prec).total;
+}
+
+iqp_status iqp_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G, int64_t m,
+                      int64_t ldg, uint64_t *P, int64_t ldp, void *stream) {
+    if (n < 1 || m < 1) return IQP_ERR_ARG;
+    iqp_status rc;
+    if ((rc = check_bits(R, rows, ldr, n)) != IQP_OK) return rc;
+    if ((rc = check_bits(G, m, ldg, n)) != IQP_OK) return rc;
+    if (P == nullptr) return IQP_ERR_ARG;
+    if (ldp < cdiv(m, 64) || (ldp & 1)) return IQP_ERR_ARG;
+    if (!aligned(P, 16)) return IQP_ERR_ALIGN;
+    return cuda_status(launch_parity(n, R, rows, ldr, G, m, ldg, P, ldp, nullptr, 0, static_cast<cudaStream_t>(stream)));
+}
+
+iqp_status iqp_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,
+                          int64_t ldx, int64_t *T, void *stream) {
+    if (n < 1) return IQP_ERR_ARG;
+    iqp_status rc;
+    if ((rc = check_bits(A, l, lda, n)) != IQP_OK) return rc;
+    if ((rc = check_bits(X, N, ldx, n)) != IQP_OK) return rc;
+    if (T == nullptr) return IQP_ERR_ARG;
+    if (!aligned(T, 8)) return IQP_ERR_ALIGN;
+    return cuda_status(launch_parity_sum(n, A, l, lda, X, N, ldx, T, static_cast<cudaStream_t>(stream)));
+}
+
+iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l, int64_t lda,
+                      const uint64_t *Z, int64_t s, int64_t ldz, const float *theta, iqp_precision prec,
+                      double *expval, double *std_err, void *ws, size_t ws_bytes, void *stream) {
+    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    if (rc != IQP_OK) return rc;
+    if ((expval && !aligned(expval, 8)) || (std_err && !aligned(std_err, 8))) return IQP_ERR_ALIGN;
+    const Plan p = make_plan(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
+    if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, false, st)) != IQP_OK) return rc;
+    return forward_stats(p, ws, expval, std_err, nullptr, nullptr, st);
+}
+
+iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                           int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                           const double *alpha, const double *beta, iqp_precision prec, double *grad, void *ws,
+                           size_t ws_bytes, void *stream) {
+    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    if (rc != IQP_OK) return rc;
+    if (alpha == nullptr || grad == nullptr) return IQP_ERR_ARG;
+    if (!aligned(alpha, 8) || !aligned(grad, 8) || (beta && !aligned(beta, 8))) return IQP_ERR_ALIGN;
+    const Plan p = make_plan(IQP_OP_EXPVAL_GRAD, n, m, l, s, 0, prec);
+    if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, prec == IQP_SPLIT_BF16, st)) != IQP_OK) return rc;
+    return backward(p, ws, alpha, beta, grad, st);
+}
+
+iqp_status iqp_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                        int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const uint64_t *X, int64_t N,
+                        int64_t ldx, const float *theta, iqp_precision prec, int unbiased, double *loss, void *ws,
+                        size_t ws_bytes, void *stream) {
+    return mmd_core(IQP_OP_MMD_LOSS, n, G, m, ldg, A, l, lda, Z, s, ldz, X, N, ldx, theta, prec, unbiased, loss,
+                    nullptr, ws, ws_bytes, stream);
+}
+
+iqp_status iqp_mmd_loss_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                             int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const uint64_t *X, int64_t N,
+                             int64_t ldx, const float *theta, iqp_precision prec, int unbiased, double *loss,
+                             double *grad, void *ws, size_t ws_bytes, void *stream) {
+    return mmd_core(IQP_OP_MMD_LOSS_GRAD, n, G, m, ldg, A, l, lda, Z, s, ldz, X, N, ldx, theta, prec, unbiased, loss,
+                    grad, ws, ws_bytes, stream);
+}
+
+iqp_status iqp_read_status(void *ws, size_t ws_bytes, void *stream) {
+    if (ws == nullptr || ws_bytes < 256 || !aligned(ws, 256)) return IQP_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    uint32_t word = 0;
+    if (cudaMemcpyAsync(&word, ws, sizeof(word), cudaMemcpyDeviceToHost, st) != cudaSuccess) return IQP_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return IQP_ERR_CUDA;
+    if (cudaMemsetAsync(ws, 0, sizeof(word), st) != cudaSuccess) return IQP_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return IQP_ERR_CUDA;
+    return static_cast<iqp_status>(word);
+}
+
+iqp_status iqp_selftest_timeout(void *ws, size_t ws_bytes, double limit_seconds, void *stream) {
+    if (ws == nullptr || ws_bytes < 256 || !aligned(ws, 256)) return IQP_ERR_WORKSPACE;
+    if (!(limit_seconds > 0.0) || limit_seconds > 10.0) return IQP_ERR_ARG;
+    return cuda_status(launch_timeout_selftest(static_cast<uint32_t *>(ws), (uint64_t)(limit_seconds * 1e9),
+                                               static_cast<cudaStream_t>(stream)));
+}
+
+const char *iqp_status_string(iqp_status st) {
+    switch (st) {
+        case IQP_OK: return "ok";
+        case IQP_ERR_ARG: return "invalid argument";
+        case IQP_ERR_ALIGN: return "misaligned pointer or leading dimension";
+        case IQP_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+        case IQP_ERR_CUDA: return "CUDA error";
+        case IQP_ERR_TIMEOUT: return "device-side wait timed out";
+        case IQP_ERR_UNSUPPORTED: return "unsupported on this device or build";
+    }
+    return "unknown status";
+}
+
+uint64_t iqp_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+void iqp_profile_enable(int on) { g_profiling.store(on ? 1 : 0); }
+
+void iqp_profile_reset(void) {
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    drain_pending();
+    for (int k = 0; k < IQP_KERNEL_COUNT; ++k) {
+        g_prof_ms[k] = 0.0;
+        g_prof_n[k] = 0;
+    }
+}
+
+iqp_status iqp_profile_query(iqp_kernel kernel, double *total_ms, uint64_t *launches) {
+    if (kernel < 0 || kernel >= IQP_KERNEL_COUNT) return IQP_ERR_ARG;
+    std::lock_guard<std::mutex> g(g_prof_mu);
+    drain_pending();
+    if (total_ms) *total_ms = g_prof_ms[kernel];
+    if (launches) *launches = g_prof_n[kernel];
+    return IQP_OK;
+}
+
+int iqp_tensor_path_available(void) {
+    const int cc = device_cc();
+    return cc == 103 ? 1 : 0;
+}
+
+}  // extern "C"

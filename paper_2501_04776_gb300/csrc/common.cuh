@@ -1,0 +1,272 @@
+// Shared internals of the IQP library: workspace plan, status word, launch
+// accounting and the PTX wrappers (mbarrier, TMA, tcgen05) used by the
+// kernels. Internal header; the public ABI is include/iqp.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <stddef.h>
+
+#include "iqp.h"
+
+namespace iqp {
+
+// ---------------------------------------------------------------- sizes
+
+constexpr int kPartCols = 128;   // samples per (S, M2) partial of the forward
+constexpr int kATile = 128;      // observables per gradient partial row
+
+__host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
+
+// Workspace layout. Every region is 256-byte aligned. Regions a given op does
+// not use have size 0.
+struct Plan {
+    int64_t n, m, l, s, N;
+    int op, prec;
+    int64_t ldp;    // words per row of P_A / P_Z (bits over m), multiple of 4
+    int64_t ldzt;   // words per row of P_Z^T (bits over s), multiple of 4
+    int64_t mpad;   // ldp * 64 (length of the split-theta arrays)
+    int64_t ldw;    // elements per row of W (multiple of 64)
+    int64_t nparts; // (S, M2) partials per observable: ceil(s / 128)
+    int64_t natile; // ceil(l / 128)
+    size_t off_status, off_pa, off_pz, off_pzt, off_c, off_part, off_w, off_gpart;
+    size_t off_ab, off_s12, off_T, off_terms, total;
+};
+
+Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec);
+
+// ---------------------------------------------------------------- status
+
+// Device status word at the start of the workspace (uint32): 0 = OK, else an
+// iqp_status recorded by the first kernel that failed.
+__device__ inline void record_status(uint32_t *status, uint32_t code) {
+    if (status) atomicCAS(status, 0u, code);
+}
+
+// Host-side launch accounting (iqp_launch_count) and optional per-kernel
+// event timing (iqp_profile_*). Construct one right before each launch.
+struct LaunchScope {
+    LaunchScope(int kernel, cudaStream_t st);
+    ~LaunchScope();
+    int kernel;
+    cudaStream_t st;
+    cudaEvent_t ev0, ev1;
+};
+iqp_status cuda_status(cudaError_t e);
+int num_sms();
+int device_cc();  // major*10+minor of the current device
+
+// ---------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of parity `parity` of `bar`. Gives up when the
+// CTA-wide abort flag is raised or after `limit_ns`; on its own timeout it
+// raises the abort flag and records IQP_ERR_TIMEOUT. Returns false on give-up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint32_t *status, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0u) {
+            if (*abort_flag) return false;
+            if (globaltimer_ns() - t0 > limit_ns) {
+                *abort_flag = 1;
+                record_status(status, IQP_ERR_TIMEOUT);
+                return false;
+            }
+        }
+    }
+}
+
+// Bounded wait that ignores the abort flag, for draining work that always
+// completes by itself (issued copies, issued MMAs) before a CTA exits.
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity, uint32_t *status, uint64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 0u && globaltimer_ns() - t0 > limit_ns) {
+            record_status(status, IQP_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// 2D tiled TMA load into shared memory, completing on `bar` (tx bytes).
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// 1D bulk copy global -> shared (16-byte aligned, size multiple of 16).
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tmap(const void *tmap) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(tmap) : "memory");
+}
+
+// ---- tcgen05 (5th-generation tensor cores, accumulators in tensor memory)
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot_smem)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::f16 (BF16 in, FP32 acc).
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive once on `bar` when all previously issued tcgen05.mma of this thread complete.
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 lanes x 32 columns of 32-bit words: thread t of the warp gets columns
+// [col, col+32) of TMEM lane (lane_base + t). The load and its wait are one
+// asm statement, so no use of r[] can be scheduled before the data lands.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major operand tile stored in the
+// 128-byte-swizzle canonical layout: rows of 128 B (64 BF16 along K), the
+// 16-byte chunks of row r permuted by chunk ^ (r & 7), 8-row groups 1024 B
+// apart (stride byte offset). Tile base must be 1024-byte aligned.
+__device__ __forceinline__ uint64_t sdesc_k128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);         // start address
+    d |= (uint64_t)1u << 16;                          // leading byte offset (unused here)
+    d |= (uint64_t)(1024u >> 4) << 32;                // stride byte offset
+    d |= (uint64_t)1u << 46;                          // descriptor version (tcgen05)
+    d |= (uint64_t)2u << 61;                          // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of 16-byte chunk `chunk` (0..7) of row `row` in a 128B-swizzled tile.
+__device__ __forceinline__ uint32_t swz128(uint32_t row, uint32_t chunk) {
+    return row * 128u + ((chunk ^ (row & 7u)) << 4);
+}
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Eight +-1 BF16 values from 8 parity bits: bit k set -> -1 (odd parity),
+// clear -> +1. S = 1 - 2P exactly. Word p holds elements 2p (low half) and
+// 2p+1 (high half).
+__device__ __forceinline__ uint4 expand_pm1(uint32_t b) {
+    // t * (2^15 + 2^30) puts bit 0 of t at 15 and bit 1 at 31 with no carries.
+    uint4 o;
+    o.x = ((b * 0x40008000u) & 0x80008000u) | 0x3F803F80u;
+    o.y = (((b >> 2) * 0x40008000u) & 0x80008000u) | 0x3F803F80u;
+    o.z = (((b >> 4) * 0x40008000u) & 0x80008000u) | 0x3F803F80u;
+    o.w = (((b >> 6) * 0x40008000u) & 0x80008000u) | 0x3F803F80u;
+    return o;
+}
+
+// Half-word masks (0x0000 / 0xFFFF) of 8 bits: word p masks elements 2p, 2p+1.
+__device__ __forceinline__ uint4 expand_mask(uint32_t b) {
+    // h * 0x10204080 places bit k of a nibble at the top of byte k (no carries);
+    // prmt with sign-replicating selectors broadcasts those bits over halves.
+    const uint32_t v0 = (b & 0xFu) * 0x10204080u;
+    const uint32_t v1 = ((b >> 4) & 0xFu) * 0x10204080u;
+    uint4 o;
+    o.x = prmt(v0, 0u, 0x9988u);
+    o.y = prmt(v0, 0u, 0xBBAAu);
+    o.z = prmt(v1, 0u, 0x9988u);
+    o.w = prmt(v1, 0u, 0xBBAAu);
+    return o;
+}
+
+}  // namespace iqp

@@ -1,0 +1,138 @@
+// GF(2) parity products of Sec. 2.2 (the exponents of B = (-1)^{Z G^T} and
+// C = 1 - (-1)^{A G^T}) and the data parity sums of Sec. 3.3.1, on bit-packed
+// rows. A lane owns one generator and folds (r AND g) over 32-bit words with
+// one LOP3 per word per row into a per-row XOR accumulator; popc(acc) & 1 is
+// the parity. Bit-exact.
+#include "common.cuh"
+
+namespace iqp {
+
+namespace {
+
+constexpr int kRows = 32;    // rows of R per block
+constexpr int kGens = 256;   // generators per block (8 warps x 32 lanes)
+constexpr int kKW = 32;      // 32-bit words per staged chunk
+constexpr int kPad = 36;     // smem row stride in words (16-byte aligned)
+
+// mode 0: P (and optional PT); mode 1: parity sums T.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__restrict__ R, int64_t ldr32, int64_t rows,
+                                                 const uint32_t *__restrict__ G, int64_t ldg32, int64_t m,
+                                                 uint32_t *__restrict__ P, int64_t ldp32, uint32_t *__restrict__ PT,
+                                                 int64_t ldpt32, long long *__restrict__ T) {
+    __shared__ __align__(16) uint32_t Rs[kRows][kPad];
+    __shared__ __align__(16) uint32_t Gs[kGens][kPad];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t g0 = (int64_t)blockIdx.x * kGens;
+    const int64_t r0 = (int64_t)blockIdx.y * kRows;
+    const int nw4 = (nw32 + 3) & ~3;  // words read per row (padding words are zero)
+
+    uint32_t acc[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) acc[r] = 0u;
+
+    for (int w0 = 0; w0 < nw4; w0 += kKW) {
+        // Stage R chunk: 32 rows x 8 uint4.
+        {
+            const int row = tid >> 3, q = tid & 7;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (r0 + row < rows && w0 + 4 * q < nw4)
+                v = *reinterpret_cast<const uint4 *>(R + (r0 + row) * ldr32 + w0 + 4 * q);
+            *reinterpret_cast<uint4 *>(&Rs[row][4 * q]) = v;
+        }
+        // Stage G chunk: 256 rows x 8 uint4.
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int idx = tid + 256 * k, row = idx >> 3, q = idx & 7;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (g0 + row < m && w0 + 4 * q < nw4)
+                v = *reinterpret_cast<const uint4 *>(G + (g0 + row) * ldg32 + w0 + 4 * q);
+            *reinterpret_cast<uint4 *>(&Gs[row][4 * q]) = v;
+        }
+        __syncthreads();
+        const int kw = min(kKW, nw4 - w0);
+        for (int w = 0; w < kw; w += 4) {
+            const uint4 g = *reinterpret_cast<const uint4 *>(&Gs[warp * 32 + lane][w]);
+#pragma unroll
+            for (int r = 0; r < kRows; ++r) {
+                const uint4 rv = *reinterpret_cast<const uint4 *>(&Rs[r][w]);
+                acc[r] ^= (rv.x & g.x) ^ (rv.y & g.y) ^ (rv.z & g.z) ^ (rv.w & g.w);
+            }
+        }
+        __syncthreads();
+    }
+
+    const int64_t gen = g0 + warp * 32 + lane;
+    if (MODE == 0) {
+        uint32_t mine = 0u, col = 0u;
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const uint32_t bit = __popc(acc[r]) & 1u;
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
+            if (lane == r) mine = bal;
+            col |= bit << r;
+        }
+        const int64_t row = r0 + lane;
+        if (row < rows && (g0 >> 5) + warp < ldp32) P[row * ldp32 + (g0 >> 5) + warp] = mine;
+        if (PT != nullptr && gen < m) PT[gen * ldpt32 + (r0 >> 5)] = col;
+    } else {
+        // Sum over the valid generators (data rows) of this warp: +1 even, -1 odd.
+        int64_t valid = m - (g0 + warp * 32);
+        valid = valid < 0 ? 0 : (valid > 32 ? 32 : valid);
+#pragma unroll
+        for (int r = 0; r < kRows; ++r) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, __popc(acc[r]) & 1u);
+            if (lane == r && r0 + r < rows && valid > 0) {
+                const long long v = (long long)valid - 2LL * (long long)__popc(bal);
+                atomicAdd(reinterpret_cast<unsigned long long *>(T + r0 + r), (unsigned long long)v);
+            }
+        }
+    }
+}
+
+}  // namespace
+
+// P (rows x ldp words) and, if PT != nullptr, P^T (m x ldpt words). Every
+// word of every P row is written (bits >= m are zero); PT rows get the bits
+// of rows [0, row_words*64) where row_words = ldpt if PT else ceil(rows/64).
+cudaError_t launch_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G, int64_t m,
+                          int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt, cudaStream_t st) {
+    const int nw32 = (int)(2 * cdiv(n, 64));
+    const int64_t gx = cdiv(ldp * 64, kGens);
+    const int64_t ry = PT ? ldpt * 2 : cdiv(rows, kRows);
+    for (int64_t y0 = 0; y0 < ry; y0 += 65535) {
+        const int64_t ny = ry - y0 < 65535 ? ry - y0 : 65535;
+        dim3 grid((unsigned)gx, (unsigned)ny);
+        const int64_t roff = y0 * kRows;
+        const int64_t rrows = rows - roff;
+        LaunchScope ls(IQP_KERNEL_PARITY, st);
+        k_parity<0><<<grid, 256, 0, st>>>(nw32, reinterpret_cast<const uint32_t *>(R + roff * ldr), 2 * ldr,
+                                          rrows, reinterpret_cast<const uint32_t *>(G), 2 * ldg, m,
+                                          reinterpret_cast<uint32_t *>(P + roff * ldp), 2 * ldp,
+                                          PT ? reinterpret_cast<uint32_t *>(PT) + (roff >> 5) : nullptr, 2 * ldpt,
+                                          nullptr);
+    }
+    return cudaGetLastError();
+}
+
+// T[a] = sum_x (-1)^{a.x}; T is zeroed here.
+cudaError_t launch_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,
+                              int64_t ldx, int64_t *T, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(T, 0, sizeof(int64_t) * (size_t)l, st);
+    if (e != cudaSuccess) return e;
+    const int nw32 = (int)(2 * cdiv(n, 64));
+    const int64_t gx = cdiv(N, kGens);
+    const int64_t ry = cdiv(l, kRows);
+    for (int64_t y0 = 0; y0 < ry; y0 += 65535) {
+        const int64_t ny = ry - y0 < 65535 ? ry - y0 : 65535;
+        const int64_t roff = y0 * kRows;
+        dim3 grid((unsigned)gx, (unsigned)ny);
+        LaunchScope ls(IQP_KERNEL_PARITY_SUM, st);
+        k_parity<1><<<grid, 256, 0, st>>>(nw32, reinterpret_cast<const uint32_t *>(A + roff * lda), 2 * lda,
+                                          l - roff, reinterpret_cast<const uint32_t *>(X), 2 * ldx, N, nullptr, 0,
+                                          nullptr, 0, reinterpret_cast<long long *>(T + roff));
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace iqp

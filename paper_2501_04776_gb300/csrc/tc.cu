@@ -1,0 +1,585 @@
+// Split-BF16 tensor-core (tcgen05 / TMEM) kernels for sm_103a.
+//
+// k_phase_tc: the phase contraction of eq. Emat, Phi = (2 theta . P_A) S_Z^T,
+// one 128 (observables) x 256 (samples) FP32 accumulator in TMEM per tile,
+// K = gates streamed in 64-wide stages. Operands never exist in HBM as
+// numbers: a TMA warp brings 256-gate slices of the parity bits (and of the
+// hi/lo BF16 split of 2 theta) into shared memory; eight producer warps
+// expand them into the 128-byte-swizzled K-major BF16 layout the MMA reads
+// (A_hi = hi_j [P_A], A_lo = lo_j [P_A], B = 1 - 2 P_Z, all exact in BF16);
+// one thread issues two tcgen05.mma per 16-gate step (hi and lo share B).
+// The epilogue runs in the producer warps straight from TMEM:
+//   mode 0: cos, per-observable (S, M2) partials over 128-sample halves;
+//   mode 1: W = sin Phi (alpha + beta cos Phi), split into hi + lo BF16 rows.
+// Phi itself is never written.
+//
+// k_grad_tc: the gradient contraction Q[a][j] = sum_i W[a][i] S_Z[i][j]
+// (Sec. 2.4, backward of eq. Emat), 128 observables x 256 gates per tile,
+// K = samples. W_hi / W_lo tiles arrive by TMA in the swizzled layout; the
+// +-1 operand is expanded from the transposed sample parities P_Z^T. The
+// epilogue masks by 2 P_A[a][j], reduces over the tile's observables with a
+// warp reduce-scatter and writes one FP64 partial per (observable tile, gate).
+//
+// Every wait is bounded (globaltimer); on expiry the CTA records
+// IQP_ERR_TIMEOUT, drains its in-flight copies and MMAs, frees TMEM and exits.
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace iqp {
+
+uint64_t default_spin_limit_ns();
+
+namespace {
+
+constexpr int TM = 128;      // UMMA M (observables)
+constexpr int TN = 256;      // UMMA N (samples or gates)
+constexpr int KS = 64;       // K per operand stage
+constexpr int KB = 256;      // K per bits stage
+constexpr int NOP = 2;       // operand stages
+constexpr int NBITS = 2;     // bits stages
+constexpr int NGEN = 8;      // producer / epilogue warps
+constexpr int kThreads = 64 + NGEN * 32;
+constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t IDESC = idesc_bf16(TM, TN);
+
+// Operand stage: A_hi (128 x 128 B), A_lo, B (256 x 128 B).
+constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = 32768, OP_BYTES = 65536;
+// Bits stage: A bits (128 rows x 32 B), B bits (256 rows x 32 B), c_hi, c_lo (256 BF16 each).
+constexpr uint32_t BT_A = 0, BT_B = 4096, BT_CHI = 12288, BT_CLO = 12800, BT_BYTES = 13312;
+constexpr uint32_t SM_OP = 0;
+constexpr uint32_t SM_BITS = SM_OP + NOP * OP_BYTES;
+constexpr uint32_t SM_BAR = SM_BITS + NBITS * BT_BYTES;
+constexpr uint32_t SM_RED = SM_BAR + 256;                 // 4 x 256 floats (grad epilogue)
+constexpr uint32_t SM_END = SM_RED + 4 * 256 * 4;
+constexpr uint32_t kSmemBytes = SM_END + 1024;            // + alignment slack
+
+struct TcArgs {
+    int64_t l, s, m;
+    int64_t nks;          // operand stages per tile
+    int64_t tiles_m, tiles_n;
+    const __nv_bfloat16 *chi, *clo;
+    double2 *part;
+    int64_t nparts;
+    const double *alpha, *beta;
+    __nv_bfloat16 *whi, *wlo;
+    int64_t ldw;
+    const uint32_t *pa32;  // P_A, for the gradient mask
+    int64_t ldp32;
+    double *gpart;
+    uint32_t *status;
+    uint64_t limit_ns;
+};
+
+struct Bars {
+    uint64_t bits_full[NBITS], bits_empty[NBITS], op_full[NOP], op_empty[NOP], w_full[NOP], acc_full, drain,
+        red_full;
+    uint32_t tmem_slot;
+    int abort_flag;
+};
+
+__device__ __forceinline__ uint8_t *aligned_smem(uint8_t *raw) {
+    const uint32_t a = smem_u32(raw);
+    return raw + ((1024u - (a & 1023u)) & 1023u);
+}
+
+// Expand one 64-gate sub-stage q of a bits stage into the B operand
+// (256 rows, +-1 BF16). Thread gt (0..255) handles chunk gt%8 of rows
+// gt/8 + 32k, k = 0..7.
+__device__ __forceinline__ void expand_b(const uint8_t *bits, uint8_t *opB, int q, int gt) {
+    const uint32_t c = gt & 7;
+    const uint32_t sub = (uint32_t)q * 8u + (c >> 2) * 4u;  // byte offset of the u32 holding chunk c
+    const uint32_t sh = (c & 3u) * 8u;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t row = (uint32_t)(gt >> 3) + 32u * k;
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(bits + row * 32u + sub);
+        const uint4 v = expand_pm1((w >> sh) & 0xFFu);
+        *reinterpret_cast<uint4 *>(opB + swz128(row, c)) = v;
+    }
+}
+
+// Expand sub-stage q into A_hi / A_lo (128 rows): hi_j / lo_j where the
+// parity bit is set, 0 elsewhere.
+__device__ __forceinline__ void expand_a(const uint8_t *bitsA, const uint8_t *chi, const uint8_t *clo, uint8_t *opHi,
+                                         uint8_t *opLo, int q, int gt) {
+    const uint32_t c = gt & 7;
+    const uint4 h = *reinterpret_cast<const uint4 *>(chi + (uint32_t)q * 128u + c * 16u);
+    const uint4 lo = *reinterpret_cast<const uint4 *>(clo + (uint32_t)q * 128u + c * 16u);
+    const uint32_t sub = (uint32_t)q * 8u + (c >> 2) * 4u;
+    const uint32_t sh = (c & 3u) * 8u;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint32_t row = (uint32_t)(gt >> 3) + 32u * k;
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(bitsA + row * 32u + sub);
+        const uint4 mk = expand_mask((w >> sh) & 0xFFu);
+        const uint32_t off = swz128(row, c);
+        *reinterpret_cast<uint4 *>(opHi + off) = make_uint4(h.x & mk.x, h.y & mk.y, h.z & mk.z, h.w & mk.w);
+        *reinterpret_cast<uint4 *>(opLo + off) = make_uint4(lo.x & mk.x, lo.y & mk.y, lo.z & mk.z, lo.w & mk.w);
+    }
+}
+
+// Sum over the 32 lanes of v[lane][k]: afterwards lane L returns the sum of column L.
+__device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const float send = upper ? v[k] : v[k + w];
+            const float keep = upper ? v[k + w] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xFFFFFFFFu, send, w);
+        }
+    }
+    return v[0];
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+    const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
+    return lo | (hi << 16);
+}
+
+// ------------------------------------------------------------------ kernel
+// GRAD = false: phase contraction (MODE 0 stats / MODE 1 W).
+// GRAD = true : gradient contraction.
+template <bool GRAD, int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
+         const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = aligned_smem(smem_raw);
+    Bars *bar = reinterpret_cast<Bars *>(smem + SM_BAR);
+    float *red = reinterpret_cast<float *>(smem + SM_RED);
+    volatile int *abort_flag = &bar->abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t lim = args.limit_ns;
+    uint32_t *status = args.status;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NBITS; ++i) {
+            mbar_init(&bar->bits_full[i], 1);
+            mbar_init(&bar->bits_empty[i], NGEN);
+        }
+        for (int i = 0; i < NOP; ++i) {
+            mbar_init(&bar->op_full[i], NGEN);
+            mbar_init(&bar->op_empty[i], 1);
+            mbar_init(&bar->w_full[i], 1);
+        }
+        mbar_init(&bar->acc_full, 1);
+        mbar_init(&bar->drain, 1);
+        mbar_init(&bar->red_full, NGEN);
+        bar->abort_flag = 0;
+        fence_barrier_init();
+        fence_proxy_async_smem();
+    }
+    if (warp == 1) {
+        tmem_alloc(&bar->tmem_slot, kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = bar->tmem_slot;
+
+    const int64_t ntiles = args.tiles_m * args.tiles_n;
+    const int64_t nks = args.nks;
+    const int64_t nkb = cdiv(nks, KB / KS);
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            prefetch_tmap(&tmA);
+            prefetch_tmap(&tmB);
+            if (GRAD) prefetch_tmap(&tmA2);
+            uint32_t itb = 0, ito = 0;
+            int last_b[NBITS] = {-1, -1};
+            int last_o[NOP] = {-1, -1};
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                const int tm = (int)(t / args.tiles_n), tn = (int)(t % args.tiles_n);
+                for (int64_t kb = 0; kb < nkb && ok; ++kb, ++itb) {
+                    const uint32_t bs = itb % NBITS;
+                    if (!mbar_wait(&bar->bits_empty[bs], ((itb / NBITS) & 1u) ^ 1u, abort_flag, status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *bits = smem + SM_BITS + bs * BT_BYTES;
+                    const int x = (int)(kb * 4);
+                    if (GRAD) {
+                        mbar_arrive_expect_tx(&bar->bits_full[bs], TN * 32);
+                        tma_load_2d(bits + BT_B, &tmB, &bar->bits_full[bs], x, tn * TN);
+                    } else {
+                        mbar_arrive_expect_tx(&bar->bits_full[bs], TM * 32 + TN * 32 + 1024);
+                        tma_load_2d(bits + BT_A, &tmA, &bar->bits_full[bs], x, tm * TM);
+                        tma_load_2d(bits + BT_B, &tmB, &bar->bits_full[bs], x, tn * TN);
+                        bulk_load(bits + BT_CHI, args.chi + kb * KB, 512, &bar->bits_full[bs]);
+                        bulk_load(bits + BT_CLO, args.clo + kb * KB, 512, &bar->bits_full[bs]);
+                    }
+                    last_b[bs] = (int)((itb / NBITS) & 1u);
+                    if (GRAD) {
+                        // W_hi / W_lo tiles of the operand stages of this bits stage.
+                        for (int q = 0; q < KB / KS; ++q) {
+                            const int64_t ks = kb * (KB / KS) + q;
+                            if (ks >= nks) break;
+                            const uint32_t os = ito % NOP;
+                            if (!mbar_wait(&bar->op_empty[os], ((ito / NOP) & 1u) ^ 1u, abort_flag, status, lim)) {
+                                ok = false;
+                                break;
+                            }
+                            uint8_t *op = smem + SM_OP + os * OP_BYTES;
+                            mbar_arrive_expect_tx(&bar->w_full[os], 2 * TM * KS * 2);
+                            tma_load_2d(op + OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), tm * TM);
+                            tma_load_2d(op + OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), tm * TM);
+                            last_o[os] = (int)((ito / NOP) & 1u);
+                            ++ito;
+                        }
+                    }
+                }
+            }
+            // Drain: every copy this thread issued has landed before exit.
+            for (int i = 0; i < NBITS; ++i)
+                if (last_b[i] >= 0) mbar_drain(&bar->bits_full[i], (uint32_t)last_b[i], status, lim);
+            for (int i = 0; i < NOP; ++i)
+                if (GRAD && last_o[i] >= 0) mbar_drain(&bar->w_full[i], (uint32_t)last_o[i], status, lim);
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            uint32_t ito = 0;
+            bool ok = true;
+            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                for (int64_t ks = 0; ks < nks; ++ks, ++ito) {
+                    const uint32_t os = ito % NOP;
+                    if (!mbar_wait(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim) ||
+                        (GRAD && !mbar_wait(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim))) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + SM_OP + os * OP_BYTES);
+#pragma unroll
+                    for (int k = 0; k < KS / 16; ++k) {
+                        const uint64_t bdesc = sdesc_k128(base + OP_B + k * 32);
+                        umma_f16(tmem, sdesc_k128(base + OP_A_HI + k * 32), bdesc, IDESC, (ks | k) != 0 ? 1u : 0u);
+                        umma_f16(tmem, sdesc_k128(base + OP_A_LO + k * 32), bdesc, IDESC, 1u);
+                    }
+                    umma_commit(&bar->op_empty[os]);
+                }
+                if (ok) umma_commit(&bar->acc_full);
+            }
+            // Drain: all issued MMAs complete before TMEM is freed.
+            umma_commit(&bar->drain);
+            mbar_drain(&bar->drain, 0u, status, lim);
+        }
+    } else {
+        // ------------------------------------------------ producers + epilogue
+        const int gt = threadIdx.x - 64;  // 0..255
+        const int quarter = warp & 3;     // TMEM lane quarter this warp may access
+        const int half = (warp - 2) >> 2; // column half of the epilogue
+        uint32_t itb = 0, ito = 0, tcount = 0;
+        bool ok = true;
+        // Every lane polls (each needs the acquire); the outcome is made
+        // warp-uniform so that a give-up never splits a warp.
+        auto wait_all = [&](uint64_t *b, uint32_t parity) {
+            const bool got = mbar_wait(b, parity, abort_flag, status, lim);
+            return __all_sync(0xFFFFFFFFu, got);
+        };
+        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+            const int64_t tm = t / args.tiles_n, tn = t % args.tiles_n;
+            for (int64_t ks = 0; ks < nks; ++ks) {
+                const int q = (int)(ks & 3);
+                const uint32_t bs = itb % NBITS;
+                if (q == 0 && !wait_all(&bar->bits_full[bs], (itb / NBITS) & 1u)) {
+                    ok = false;
+                    break;
+                }
+                const uint32_t os = ito % NOP;
+                if (!wait_all(&bar->op_empty[os], ((ito / NOP) & 1u) ^ 1u)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t *bits = smem + SM_BITS + bs * BT_BYTES;
+                uint8_t *op = smem + SM_OP + os * OP_BYTES;
+                expand_b(bits + BT_B, op + OP_B, q, gt);
+                if (!GRAD) expand_a(bits + BT_A, bits + BT_CHI, bits + BT_CLO, op + OP_A_HI, op + OP_A_LO, q, gt);
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar->op_full[os]);
+                ++ito;
+                if (q == 3 || ks == nks - 1) {
+                    if (lane == 0) mbar_arrive(&bar->bits_empty[bs]);
+                    ++itb;
+                }
+            }
+            if (!ok) break;
+            // ------------------------------------------------------ epilogue
+            if (!wait_all(&bar->acc_full, tcount & 1u)) {
+                ok = false;
+                break;
+            }
+            __syncwarp();  // lanes leave the wait loop independently; tcgen05.ld is warp-aligned
+            tc_fence_after();
+            const int64_t row = tm * TM + quarter * 32 + lane;  // observable a
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+            if (!GRAD && MODE == 0) {
+                const int64_t c0 = tn * TN + half * 128;  // first sample of this half
+                int64_t nvalid = args.s - c0;
+                nvalid = nvalid < 0 ? 0 : (nvalid > 128 ? 128 : nvalid);
+                float S = 0.f, M2 = 0.f;
+                uint32_t r[32];
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    tmem_ld32(tbase + c * 32, r);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
+                }
+                const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    tmem_ld32(tbase + c * 32, r);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if (c * 32 + e < nvalid) {
+                            const float d = cosf(__uint_as_float(r[e])) - mean;
+                            M2 = fmaf(d, d, M2);
+                        }
+                }
+                if (row < args.l && nvalid > 0)
+                    args.part[row * args.nparts + (c0 / 128)] = make_double2((double)S, (double)M2);
+            } else if (!GRAD) {
+                const int64_t c0 = tn * TN + half * 128;
+                const bool rv = row < args.l;
+                const float al = rv ? (float)args.alpha[row] : 0.f;
+                const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
+                uint32_t r[32];
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    tmem_ld32(tbase + c * 32, r);
+                    const int64_t i0 = c0 + c * 32;
+                    uint32_t ph[16], pl[16];
+#pragma unroll
+                    for (int e = 0; e < 32; e += 2) {
+                        float s0, k0, s1, k1;
+                        sincosf(__uint_as_float(r[e]), &s0, &k0);
+                        sincosf(__uint_as_float(r[e + 1]), &s1, &k1);
+                        const float w0 = s0 * (al + be * k0), w1 = s1 * (al + be * k1);
+                        const float h0 = __bfloat162float(__float2bfloat16_rn(w0));
+                        const float h1 = __bfloat162float(__float2bfloat16_rn(w1));
+                        ph[e / 2] = pack_bf16x2(h0, h1);
+                        pl[e / 2] = pack_bf16x2(w0 - h0, w1 - h1);
+                    }
+                    if (rv && i0 < args.s) {
+                        __nv_bfloat16 *dh = args.whi + row * args.ldw + i0;
+                        __nv_bfloat16 *dl = args.wlo + row * args.ldw + i0;
+                        if (i0 + 32 <= args.s) {
+#pragma unroll
+                            for (int v = 0; v < 4; ++v) {
+                                reinterpret_cast<uint4 *>(dh)[v] =
+                                    make_uint4(ph[4 * v], ph[4 * v + 1], ph[4 * v + 2], ph[4 * v + 3]);
+                                reinterpret_cast<uint4 *>(dl)[v] =
+                                    make_uint4(pl[4 * v], pl[4 * v + 1], pl[4 * v + 2], pl[4 * v + 3]);
+                            }
+                        } else {
+                            uint16_t *sh = reinterpret_cast<uint16_t *>(dh);
+                            uint16_t *sl = reinterpret_cast<uint16_t *>(dl);
+                            for (int e = 0; e < 32 && i0 + e < args.s; ++e) {
+                                sh[e] = (uint16_t)(ph[e / 2] >> ((e & 1) * 16));
+                                sl[e] = (uint16_t)(pl[e / 2] >> ((e & 1) * 16));
+                            }
+                        }
+                    }
+                }
+            } else {
+                // Gradient epilogue: mask by 2 P_A[a][j], reduce over observables.
+                const bool rv = row < args.l;
+                uint32_t r[32];
+#pragma unroll 1
+                for (int c = 0; c < 4; ++c) {
+                    tmem_ld32(tbase + c * 32, r);
+                    const int64_t j0 = tn * TN + half * 128 + c * 32;
+                    const uint32_t mask = (rv && j0 < args.m) ? args.pa32[row * args.ldp32 + (j0 >> 5)] : 0u;
+                    float v[32];
+#pragma unroll
+                    for (int e = 0; e < 32; ++e) v[e] = ((mask >> e) & 1u) ? 2.f * __uint_as_float(r[e]) : 0.f;
+                    red[quarter * 256 + half * 128 + c * 32 + lane] = reduce_scatter32(v, lane);
+                }
+                // All eight warps' column sums are in `red`; combine the four
+                // lane quarters in fixed order. (The next tile's writes to
+                // `red` follow a full K loop that needs every warp, so a
+                // second barrier is not needed.)
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar->red_full);
+                if (!wait_all(&bar->red_full, tcount & 1u)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                const int64_t j = tn * TN + gt;
+                if (j < args.m) {
+                    const double sum = (double)red[gt] + (double)red[256 + gt] + (double)red[512 + gt] +
+                                       (double)red[768 + gt];
+                    args.gpart[tm * args.m + j] = sum;
+                }
+            }
+            tc_fence_before();
+        }
+    }
+
+    __syncthreads();
+    if (warp == 1) {
+        __syncwarp();  // lane 0 ran the MMA loop alone; dealloc is warp-aligned
+        tc_fence_after();
+        tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// Bounded wait on an mbarrier nothing arrives on: exercises the timeout path.
+__global__ void k_timeout_selftest(uint32_t *status, uint64_t limit_ns) {
+    __shared__ __align__(8) uint64_t b;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&b, 1);
+        abort_flag = 0;
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&b, 0u, &abort_flag, status, limit_ns);
+    __syncthreads();
+}
+
+// ------------------------------------------------------------ tensor maps
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (fn == nullptr) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+// Row-major 2D tensor: `cols` elements per row (dim 0), `rows` rows, row
+// pitch `pitch_bytes`; box = box_cols x box_rows.
+bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_t cols, int64_t rows,
+              int64_t pitch_bytes, uint32_t box_cols, uint32_t box_rows, CUtensorMapSwizzle swz) {
+    EncodeTiledFn fn = encode_fn();
+    if (fn == nullptr) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch_bytes};
+    cuuint32_t box[2] = {box_cols, box_rows};
+    cuuint32_t es[2] = {1, 1};
+    return fn(map, dt, 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <bool GRAD, int MODE>
+cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
+                     cudaStream_t st) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kSmemBytes);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int64_t ntiles = args.tiles_m * args.tiles_n;
+    int sms = num_sms();
+    if (sms <= 0) sms = 1;
+    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    LaunchScope ls(GRAD ? IQP_KERNEL_GRAD_TC : (MODE == 0 ? IQP_KERNEL_PHASE_TC : IQP_KERNEL_RECOMPUTE_TC), st);
+    k_tc<GRAD, MODE><<<grid, kThreads, kSmemBytes, st>>>(a, a2, b, args);
+    return cudaGetLastError();
+}
+
+template <class T>
+T *at(void *ws, size_t off) {
+    return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
+}
+
+}  // namespace
+
+cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alpha, const double *beta,
+                            cudaStream_t st, iqp_status *why) {
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, at<uint64_t>(ws, p.off_pa), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldp, p.l, p.ldp * 8, 4, TM,
+                  CU_TENSOR_MAP_SWIZZLE_NONE) ||
+        !make_map(&mb, at<uint64_t>(ws, p.off_pz), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldp, p.s, p.ldp * 8, 4, TN,
+                  CU_TENSOR_MAP_SWIZZLE_NONE)) {
+        *why = IQP_ERR_UNSUPPORTED;
+        return cudaErrorNotSupported;
+    }
+    TcArgs a;
+    a.l = p.l;
+    a.s = p.s;
+    a.m = p.m;
+    a.nks = cdiv(p.m, KS);
+    a.tiles_m = cdiv(p.l, TM);
+    a.tiles_n = cdiv(p.s, TN);
+    a.chi = at<__nv_bfloat16>(ws, p.off_c);
+    a.clo = a.chi + p.mpad;
+    a.part = at<double2>(ws, p.off_part);
+    a.nparts = p.nparts;
+    a.alpha = alpha;
+    a.beta = beta;
+    a.whi = at<__nv_bfloat16>(ws, p.off_w);
+    a.wlo = a.whi + p.l * p.ldw;
+    a.ldw = p.ldw;
+    a.pa32 = nullptr;
+    a.ldp32 = 2 * p.ldp;
+    a.gpart = nullptr;
+    a.status = at<uint32_t>(ws, p.off_status);
+    a.limit_ns = default_spin_limit_ns();
+    return mode == 0 ? launch_k<false, 0>(ma, ma, mb, a, st) : launch_k<false, 1>(ma, ma, mb, a, st);
+}
+
+cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why) {
+    CUtensorMap mhi, mlo, mb;
+    const __nv_bfloat16 *whi = at<__nv_bfloat16>(ws, p.off_w);
+    const __nv_bfloat16 *wlo = whi + p.l * p.ldw;
+    if (!make_map(&mhi, whi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, TM,
+                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mlo, wlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, TM,
+                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mb, at<uint64_t>(ws, p.off_pzt), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldzt, p.m, p.ldzt * 8, 4, TN,
+                  CU_TENSOR_MAP_SWIZZLE_NONE)) {
+        *why = IQP_ERR_UNSUPPORTED;
+        return cudaErrorNotSupported;
+    }
+    TcArgs a;
+    a.l = p.l;
+    a.s = p.s;
+    a.m = p.m;
+    a.nks = cdiv(p.s, KS);
+    a.tiles_m = cdiv(p.l, TM);
+    a.tiles_n = cdiv(p.m, TN);
+    a.chi = a.clo = nullptr;
+    a.part = nullptr;
+    a.nparts = 0;
+    a.alpha = a.beta = nullptr;
+    a.whi = a.wlo = nullptr;
+    a.ldw = p.ldw;
+    a.pa32 = at<uint32_t>(ws, p.off_pa);
+    a.ldp32 = 2 * p.ldp;
+    a.gpart = at<double>(ws, p.off_gpart);
+    a.status = at<uint32_t>(ws, p.off_status);
+    a.limit_ns = default_spin_limit_ns();
+    return launch_k<true, 0>(mhi, mlo, mb, a, st);
+}
+
+cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st) {
+    LaunchScope ls(IQP_KERNEL_SELFTEST, st);
+    k_timeout_selftest<<<1, 32, 0, st>>>(status, limit_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace iqp

@@ -1,0 +1,97 @@
+"""C-ABI checks that need no GPU: the library loads, exports every symbol that
+include/iqp.h declares, sizes workspaces, and rejects bad arguments on the
+host before any launch."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "iqp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2501_04776_gb300 import build, _lib
+    build.build()
+    return _lib.load()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(iqp_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_documented_calls():
+    names = declared_functions()
+    for must in ("iqp_expval", "iqp_expval_grad", "iqp_mmd_loss", "iqp_mmd_loss_grad", "iqp_parity",
+                 "iqp_workspace_bytes"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2501_04776_gb300 import _lib
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in _lib.SIGNATURES, name
+
+
+def test_workspace_bytes(lib):
+    from paper_2501_04776_gb300 import _lib
+    n, m, l, s = 1000, 100_000, 10_000, 10_000
+    fwd = lib.iqp_workspace_bytes(_lib.OP_EXPVAL, n, m, l, s, 0, _lib.SPLIT_BF16)
+    grad = lib.iqp_workspace_bytes(_lib.OP_EXPVAL_GRAD, n, m, l, s, 0, _lib.SPLIT_BF16)
+    assert fwd > 0 and grad > fwd
+    # Bit-packed parities: (l + s) rows of ceil(m/64) words dominate the forward.
+    assert fwd >= (l + s) * ((m + 63) // 64) * 8
+    assert fwd < 2 * (l + s) * ((m + 255) // 256) * 32 + 64 * l * ((s + 127) // 128) + (1 << 22)
+    # W (hi + lo BF16, l x s) dominates the gradient's extra scratch.
+    assert grad - fwd >= 4 * l * s
+    assert lib.iqp_workspace_bytes(_lib.OP_EXPVAL, 0, m, l, s, 0, _lib.FP32) == 0
+    assert lib.iqp_workspace_bytes(99, n, m, l, s, 0, _lib.FP32) == 0
+    assert lib.iqp_workspace_bytes(_lib.OP_EXPVAL, n, m, l, s, 0, 7) == 0
+
+
+def _expval(lib, n=10, m=4, l=3, s=5, ldg=2, lda=2, ldz=2, G=0x10000, A=0x20000, Z=0x30000, th=0x40000,
+            prec=0, ws=0x100000, wsb=1 << 30):
+    return lib.iqp_expval(n, G, m, ldg, A, l, lda, Z, s, ldz, th, prec, 0x50000, 0x60000, ws, wsb, None)
+
+
+def test_host_side_argument_errors(lib):
+    from paper_2501_04776_gb300 import _lib
+    # Pointers below are never dereferenced: every case fails its host check.
+    assert _expval(lib, n=0) == _lib.ERR_ARG
+    assert _expval(lib, s=0) == _lib.ERR_ARG
+    assert _expval(lib, ldg=1) == _lib.ERR_ARG          # odd leading dimension
+    assert _expval(lib, n=200, ldz=2) == _lib.ERR_ARG   # ld < ceil(n/64)
+    assert _expval(lib, G=0) == _lib.ERR_ARG            # null pointer
+    assert _expval(lib, A=0x20008) == _lib.ERR_ALIGN    # not 16-byte aligned
+    assert _expval(lib, th=0x40002) == _lib.ERR_ALIGN
+    assert _expval(lib, prec=5) == _lib.ERR_ARG
+    assert _expval(lib, ws=0) == _lib.ERR_WORKSPACE
+    assert _expval(lib, ws=0x100010) == _lib.ERR_WORKSPACE  # not 256-byte aligned
+    assert _expval(lib, wsb=100) == _lib.ERR_WORKSPACE
+    # Unbiased MMD needs s >= 2 and N >= 2.
+    rc = lib.iqp_mmd_loss(10, 0x10000, 4, 2, 0x20000, 3, 2, 0x30000, 1, 2, 0x70000, 5, 2, 0x40000, 0, 1,
+                          0x50000, 0x100000, 1 << 30, None)
+    assert rc == _lib.ERR_ARG
+    rc = lib.iqp_parity(10, 0x10000, 3, 2, 0x20000, 4, 2, 0x30000, 1, None)
+    assert rc == _lib.ERR_ARG  # ldp odd
+    assert lib.iqp_selftest_timeout(None, 0, 1.0, None) == _lib.ERR_WORKSPACE
+    assert lib.iqp_selftest_timeout(0x100000, 1 << 20, 99.0, None) == _lib.ERR_ARG
+
+
+def test_status_strings(lib):
+    for st in range(7):
+        assert lib.iqp_status_string(st)
+    assert b"timed out" in lib.iqp_status_string(5)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    from paper_2501_04776_gb300 import _lib
+    monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(_lib, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        _lib.load()

@@ -1,0 +1,325 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on
+identical seeded inputs.
+
+Bars: parities bit-exact; expectation values, standard errors and losses
+within 1e-5 (FP32 form) / 1e-4 (split-BF16 form) absolute; gradients within
+1e-4 relative L2. Shapes span several tiles with ragged tails; the full-size
+cases run the exact launch configuration bench.py times and compare sampled
+observables, which the oracle computes one by one.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2501_04776_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 1e-5, "split_bf16": 1e-4}
+GRAD_RTOL = 1e-4
+PRECS = ["fp32", "split_bf16"]
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    from paper_2501_04776_gb300 import build
+    build.build()
+    from paper_2501_04776_gb300 import api as A
+    assert torch.cuda.is_available()
+    return A
+
+
+def dev(api, words):
+    return api.to_device_bits(words)
+
+
+def th_dev(theta):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(theta, dtype=np.float32)).cuda()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def gpu_expval(api, p, prec, Z=None):
+    Z = p.Z if Z is None else Z
+    ev, se = api.expval_raw(p.n, th_dev(p.theta), dev(api, p.G), dev(api, p.A), dev(api, Z), prec)
+    return ev.cpu().numpy(), se.cpu().numpy()
+
+
+def gpu_grad(api, p, alpha, beta, prec):
+    import torch
+    al = torch.from_numpy(np.asarray(alpha, dtype=np.float64)).cuda()
+    be = None if beta is None else torch.from_numpy(np.asarray(beta, dtype=np.float64)).cuda()
+    g = api.expval_grad(p.n, th_dev(p.theta), dev(api, p.G), dev(api, p.A), dev(api, p.Z), al, be, prec)
+    return g.cpu().numpy()
+
+
+def ragged_problem(seed=7, n=130, m=1000, l=300, s=600, ks=(1, 2, 3), pa=0.1, scale=0.3):
+    rng = I.Rng(seed)
+    G = I.random_k_body(rng, m, n, list(ks), 1)
+    theta = (scale * rng.normal(m, 2)).astype(np.float32)
+    A = I.bernoulli_bits(rng, l, n, pa, 3)
+    Z = I.uniform_bits(rng, s, n, 4)
+    return I.Problem(f"ragged-n{n}-m{m}-l{l}-s{s}", n, G, A, Z, theta)
+
+
+# ------------------------------------------------------------------ parity
+
+@pytest.mark.parametrize("n,m,rows", [(1, 1, 1), (63, 65, 33), (130, 300, 257), (300, 1000, 70), (5000, 513, 40)])
+def test_parity_bit_exact(api, n, m, rows):
+    rng = I.Rng(100 + n)
+    R = I.bernoulli_bits(rng, rows, n, 0.5, 1)
+    G = I.random_k_body(rng, m, n, [1, 2, 3], 2) if n >= 3 else I.bernoulli_bits(rng, m, n, 0.5, 2)
+    P = api.parity(n, dev(api, R), dev(api, G)).cpu().numpy().view(np.uint64)
+    want = oracle.parity(n, R, G)
+    got = I.unpack_bits(P, P.shape[1] * 64)
+    assert np.array_equal(got[:, :m], want)
+    assert not got[:, m:].any()  # padding bits are zero
+
+
+def test_parity_dense_generators_bit_exact(api):
+    rng = I.Rng(5)
+    n, m, rows = 777, 300, 129
+    R = I.bernoulli_bits(rng, rows, n, 0.5, 1)
+    G = I.bernoulli_bits(rng, m, n, 0.5, 2)
+    P = api.parity(n, dev(api, R), dev(api, G)).cpu().numpy().view(np.uint64)
+    assert np.array_equal(I.unpack_bits(P, m), oracle.parity(n, R, G))
+
+
+@pytest.mark.parametrize("n,l,N", [(8, 5, 3), (300, 70, 1000), (1000, 33, 2049)])
+def test_parity_sum_exact(api, n, l, N):
+    rng = I.Rng(200 + n)
+    A = I.bernoulli_bits(rng, l, n, 0.2, 1)
+    X = I.uniform_bits(rng, N, n, 2)
+    T = api.parity_sum(n, dev(api, A), dev(api, X)).cpu().numpy()
+    assert np.array_equal(T, oracle.data_parity_sum(n, A, X))
+
+
+# -------------------------------------------------------------- estimator
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_expval_local_n8(api, prec):
+    """n=8, all one- and two-body gates, 64 observables, 1024 samples."""
+    p = I.tiny_local(seed=1)
+    ev, se = gpu_expval(api, p, prec)
+    want_ev, want_se, _, _ = oracle.expval(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64))
+    assert np.max(np.abs(ev - want_ev)) <= TOL[prec]
+    assert np.max(np.abs(se - want_se)) <= TOL[prec]
+    # Over all 2^8 sample strings the estimate is the exact expectation value,
+    # which the oracle pins to a statevector.
+    allz = I.pack_bits(np.array([[(z >> q) & 1 for q in range(8)] for z in range(256)]))
+    ev_all, _ = gpu_expval(api, p, prec, Z=allz)
+    exact = oracle.statevector_expval(p.n, p.G, p.A, p.theta.astype(np.float64))
+    assert np.max(np.abs(ev_all - exact)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_expval_ragged_tiles(api, prec):
+    p = ragged_problem()
+    ev, se = gpu_expval(api, p, prec)
+    want_ev, want_se, _, _ = oracle.expval(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64))
+    assert np.max(np.abs(ev - want_ev)) <= TOL[prec]
+    assert np.max(np.abs(se - want_se)) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_expval_degenerate_cases(api, prec):
+    rng = I.Rng(9)
+    n = 70
+    G = I.random_k_body(rng, 50, n, [1, 2], 1)
+    theta = (0.4 * rng.normal(50, 2)).astype(np.float32)
+    A = I.bernoulli_bits(rng, 5, n, 0.3, 3)
+    A[0] = 0                      # a = 0: exactly 1
+    Z = I.uniform_bits(rng, 1, n, 4)  # one sample: SE = 0, expval = cos Phi
+    p = I.Problem("one-sample", n, G, A, Z, theta)
+    ev, se = gpu_expval(api, p, prec)
+    want, _, _, _ = oracle.expval(n, G, A, Z, theta.astype(np.float64))
+    assert ev[0] == 1.0 and np.all(se == 0.0)
+    assert np.max(np.abs(ev - want)) <= TOL[prec]
+    # theta = 0: every estimate is exactly 1 with zero error.
+    p0 = I.Problem("zero", n, G, A, I.uniform_bits(rng, 300, n, 5), np.zeros(50, np.float32))
+    ev0, se0 = gpu_expval(api, p0, prec)
+    assert np.all(ev0 == 1.0) and np.all(se0 == 0.0)
+    # One gate, one qubit, one observable.
+    p1 = I.Problem("single", 1, I.pack_index_lists([[0]], 1), I.pack_index_lists([[0]], 1),
+                   I.uniform_bits(rng, 7, 1, 6), np.array([0.3], np.float32))
+    ev1, se1 = gpu_expval(api, p1, prec)
+    assert abs(ev1[0] - math.cos(2 * float(np.float32(0.3)))) <= TOL[prec]
+
+
+# --------------------------------------------------------------- gradient
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_grad_vs_oracle(api, prec):
+    p = ragged_problem(seed=8, l=260, s=520)
+    rng = I.Rng(3)
+    alpha = rng.normal(p.l, 1) / p.s
+    beta = rng.normal(p.l, 2) / p.s
+    for b in (None, beta):
+        g = gpu_grad(api, p, alpha, b, prec)
+        want = oracle.expval_grad(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64), alpha, b)
+        assert rel_l2(g, want) <= GRAD_RTOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_autograd_linear_loss(api, prec):
+    import torch
+    p = ragged_problem(seed=10, l=140, s=300, m=700)
+    w = I.Rng(4).normal(p.l, 1)
+    theta = th_dev(p.theta).requires_grad_(True)
+    ev, se = api.expval(theta, dev(api, p.G), dev(api, p.A), dev(api, p.Z), p.n, prec)
+    loss = (ev * torch.from_numpy(w).cuda()).sum()
+    loss.backward()
+    want = oracle.expval_grad(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64), -w / p.s, None)
+    assert theta.grad.dtype == torch.float32
+    assert rel_l2(theta.grad.double().cpu().numpy(), want) <= GRAD_RTOL
+    assert not se.requires_grad
+
+
+def test_grad_central_differences_on_gpu(api):
+    """Directional derivative of the GPU estimator (split-BF16) by central
+    differences of the GPU forward, against the GPU gradient."""
+    p = ragged_problem(seed=12, n=40, m=200, l=64, s=512, scale=0.5)
+    w = I.Rng(5).normal(p.l, 1)
+    v = I.Rng(6).normal(p.m, 1)
+    g = gpu_grad(api, p, -w / p.s, None, "split_bf16")
+    h = 1e-2
+
+    def F(th):
+        q = I.Problem("fd", p.n, p.G, p.A, p.Z, th.astype(np.float32))
+        return float(np.dot(w, gpu_expval(api, q, "split_bf16")[0]))
+
+    th = p.theta.astype(np.float64)
+    fd = (F(th + h * v) - F(th - h * v)) / (2 * h)
+    assert abs(fd - float(np.dot(g, v))) <= 2e-2 * max(1.0, abs(fd))
+
+
+# -------------------------------------------------------------------- MMD
+
+def mmd_problem(seed=11, n=50, l=200, s=500, N=300):
+    p = I.mmd_training(seed=seed, n=n, l=l, s=s, N=N)
+    p.theta = (p.theta * 20).astype(np.float32)  # move away from theta ~ 0
+    return p
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("unbiased", [True, False])
+def test_mmd_loss_and_grad(api, prec, unbiased):
+    p = mmd_problem()
+    args = (p.n, th_dev(p.theta), dev(api, p.G), dev(api, p.A), dev(api, p.Z), dev(api, p.X), prec, unbiased)
+    loss_only, _ = api.mmd_loss_raw(*args, with_grad=False)
+    loss, grad = api.mmd_loss_raw(*args, with_grad=True)
+    want_loss, _, want_grad = oracle.mmd_loss(p.n, p.G, p.A, p.Z, p.X, p.theta.astype(np.float64), unbiased,
+                                              grad=True)
+    assert abs(float(loss_only) - want_loss) <= TOL[prec]
+    assert abs(float(loss) - want_loss) <= TOL[prec]
+    assert rel_l2(grad.cpu().numpy(), want_grad) <= GRAD_RTOL
+
+
+def test_mmd_autograd(api):
+    import torch
+    p = mmd_problem(seed=13, l=120, s=300, N=200)
+    theta = th_dev(p.theta).requires_grad_(True)
+    loss = api.mmd_loss(theta, dev(api, p.G), dev(api, p.A), dev(api, p.Z), dev(api, p.X), p.n, "split_bf16")
+    (3.0 * loss).backward()
+    _, _, want = oracle.mmd_loss(p.n, p.G, p.A, p.Z, p.X, p.theta.astype(np.float64), True, grad=True)
+    assert rel_l2(theta.grad.double().cpu().numpy(), 3.0 * want) <= GRAD_RTOL
+
+
+# ------------------------------------------------------- full-size sampled
+
+def _sampled_forward_check(api, p, prec, nsample, seed):
+    ev, se = gpu_expval(api, p, prec)
+    idx = np.sort(I.Rng(seed).integers(nsample, p.l, 1))
+    want_ev, want_se, _, _ = oracle.expval(p.n, p.G, p.A[idx], p.Z, p.theta.astype(np.float64))
+    assert np.max(np.abs(ev[idx] - want_ev)) <= TOL[prec]
+    assert np.max(np.abs(se[idx] - want_se)) <= TOL[prec]
+    assert np.all(np.isfinite(ev)) and np.all(np.abs(ev) <= 1.0 + 1e-6)
+
+
+def _sampled_grad_check(api, p, prec, nsample, seed):
+    """Gradient at full size with alpha nonzero on a sample of observables:
+    the others contribute exactly zero, so the oracle needs only the sample."""
+    idx = np.sort(I.Rng(seed).integers(nsample, p.l, 1))
+    idx = np.unique(idx)
+    alpha = np.zeros(p.l)
+    alpha[idx] = I.Rng(seed + 1).normal(idx.size, 1) / p.s
+    g = gpu_grad(api, p, alpha, None, prec)
+    want = oracle.expval_grad(p.n, p.G, p.A[idx], p.Z, p.theta.astype(np.float64), alpha[idx], None)
+    assert rel_l2(g, want) <= GRAD_RTOL
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_random_gates_n1000(api, prec):
+    """10000 observables x 10000 samples x 100000 gates, n = 1000 (the
+    benchmark workload), sampled observables."""
+    p = I.random_gates(n=1000)
+    _sampled_forward_check(api, p, prec, 16, 21)
+    _sampled_grad_check(api, p, prec, 8, 22)
+
+
+def test_full_size_local_n300(api):
+    """n=300, all 45150 one- and two-body gates, 1000 observables, 10000 samples."""
+    p = I.local300()
+    for prec in PRECS:
+        _sampled_forward_check(api, p, prec, 12, 23)
+    _sampled_grad_check(api, p, "split_bf16", 6, 24)
+
+
+# ------------------------------------------------------------ robustness
+
+def test_deterministic_repeat(api):
+    p = ragged_problem(seed=14)
+    for prec in PRECS:
+        a = gpu_expval(api, p, prec)
+        b = gpu_expval(api, p, prec)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+        alpha = np.full(p.l, 1.0 / p.s)
+        assert np.array_equal(gpu_grad(api, p, alpha, None, prec), gpu_grad(api, p, alpha, None, prec))
+
+
+def test_bounded_wait_times_out_and_context_survives(api):
+    import torch
+    from paper_2501_04776_gb300 import _lib
+    lib = _lib.load()
+    ws = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    st = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.iqp_read_status(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st) == _lib.OK
+    assert lib.iqp_selftest_timeout(ctypes.c_void_p(ws.data_ptr()), ws.numel(), 0.2, st) == _lib.OK
+    assert lib.iqp_read_status(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st) == _lib.ERR_TIMEOUT
+    assert lib.iqp_read_status(ctypes.c_void_p(ws.data_ptr()), ws.numel(), st) == _lib.OK  # cleared
+    p = I.tiny_local(seed=2, s=256)
+    ev, _ = gpu_expval(api, p, "split_bf16")
+    want, _, _, _ = oracle.expval(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64))
+    assert np.max(np.abs(ev - want)) <= TOL["split_bf16"]
+    assert api.read_status() == _lib.OK
+
+
+def test_workspace_too_small_is_rejected(api):
+    import torch
+    from paper_2501_04776_gb300 import _lib
+    lib = _lib.load()
+    p = I.tiny_local(seed=3, s=64)
+    G, A, Z = dev(api, p.G), dev(api, p.A), dev(api, p.Z)
+    th = th_dev(p.theta)
+    need = lib.iqp_workspace_bytes(_lib.OP_EXPVAL, p.n, p.m, p.l, p.s, 0, _lib.SPLIT_BF16)
+    ws = torch.zeros(need, dtype=torch.uint8, device="cuda")
+    out = torch.zeros(p.l, dtype=torch.float64, device="cuda")
+    P = ctypes.c_void_p
+    rc = lib.iqp_expval(p.n, P(G.data_ptr()), p.m, G.shape[1], P(A.data_ptr()), p.l, A.shape[1], P(Z.data_ptr()),
+                        p.s, Z.shape[1], P(th.data_ptr()), _lib.SPLIT_BF16, P(out.data_ptr()), None,
+                        P(ws.data_ptr()), need - 256, None)
+    assert rc == _lib.ERR_WORKSPACE
+
+
+def test_launch_counter_counts_kernels(api):
+    before = api.launch_count()
+    p = I.tiny_local(seed=4, s=128)
+    gpu_expval(api, p, "split_bf16")
+    assert api.launch_count() - before >= 4  # parity x2, theta split, phase, finalize
