@@ -95,3 +95,12 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         _lib.load()
+
+
+def test_binding_imports_without_gpu():
+    import paper_2501_04776_gb300 as pkg
+    from paper_2501_04776_gb300 import api
+    assert pkg.api is api
+    assert api.precision_code("split_bf16") == 1 and api.precision_code("fp32") == 0
+    with pytest.raises(ValueError):
+        api.precision_code("fp16")
