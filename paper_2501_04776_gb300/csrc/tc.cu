@@ -20,6 +20,13 @@
 // epilogue masks by 2 P_A[a][j], reduces over the tile's observables with a
 // warp reduce-scatter and writes one FP64 partial per (observable tile, gate).
 //
+// Accumulation: the tensor core's FP32 accumulation rounds toward zero, so a
+// single accumulator over ~10^4 K-steps shrinks |Phi| by ~1e-4 relative. Each
+// tile therefore accumulates in chunks of `chunk` K-stages: a chunk starts a
+// fresh accumulator (TMEM columns 0..255) and, when it completes, the
+// producer warps add it into an FP32 running sum (columns 256..511) with
+// round-to-nearest adds. The epilogue reads accumulator + running sum.
+//
 // Every wait is bounded (globaltimer); on expiry the CTA records
 // IQP_ERR_TIMEOUT, drains its in-flight copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
@@ -40,7 +47,8 @@ constexpr int NOP = 2;       // operand stages
 constexpr int NBITS = 2;     // bits stages
 constexpr int NGEN = 8;      // producer / epilogue warps
 constexpr int kThreads = 64 + NGEN * 32;
-constexpr uint32_t kTmemCols = 256;
+constexpr uint32_t kTmemCols = 512;   // accumulator (0..255) + running sum (256..511)
+constexpr uint32_t kSumCol = 256;
 constexpr uint32_t IDESC = idesc_bf16(TM, TN);
 
 // Operand stage: A_hi (128 x 128 B), A_lo, B (256 x 128 B).
@@ -57,6 +65,7 @@ constexpr uint32_t kSmemBytes = SM_END + 1024;            // + alignment slack
 struct TcArgs {
     int64_t l, s, m;
     int64_t nks;          // operand stages per tile
+    int64_t chunk;        // operand stages per accumulation chunk
     int64_t tiles_m, tiles_n;
     const __nv_bfloat16 *chi, *clo;
     double2 *part;
@@ -258,15 +267,17 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     const uint32_t base = smem_u32(smem + SM_OP + os * OP_BYTES);
+                    const bool fresh = (ks % args.chunk) == 0;  // first stage of a chunk
 #pragma unroll
                     for (int k = 0; k < KS / 16; ++k) {
                         const uint64_t bdesc = sdesc_k128(base + OP_B + k * 32);
-                        umma_f16(tmem, sdesc_k128(base + OP_A_HI + k * 32), bdesc, IDESC, (ks | k) != 0 ? 1u : 0u);
+                        umma_f16(tmem, sdesc_k128(base + OP_A_HI + k * 32), bdesc, IDESC,
+                                 (fresh && k == 0) ? 0u : 1u);
                         umma_f16(tmem, sdesc_k128(base + OP_A_LO + k * 32), bdesc, IDESC, 1u);
                     }
                     umma_commit(&bar->op_empty[os]);
+                    if ((ks % args.chunk) == args.chunk - 1 || ks == nks - 1) umma_commit(&bar->acc_full);
                 }
-                if (ok) umma_commit(&bar->acc_full);
             }
             // Drain: all issued MMAs complete before TMEM is freed.
             umma_commit(&bar->drain);
@@ -277,7 +288,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int gt = threadIdx.x - 64;  // 0..255
         const int quarter = warp & 3;     // TMEM lane quarter this warp may access
         const int half = (warp - 2) >> 2; // column half of the epilogue
-        uint32_t itb = 0, ito = 0, tcount = 0;
+        uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
         bool ok = true;
         // Every lane polls (each needs the acquire); the outcome is made
         // warp-uniform so that a give-up never splits a warp.
@@ -311,17 +322,57 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (lane == 0) mbar_arrive(&bar->bits_empty[bs]);
                     ++itb;
                 }
+                if ((ks % args.chunk) == args.chunk - 1 && ks != nks - 1) {
+                    // Chunk done: fold the accumulator into the running sum. The
+                    // next chunk's first MMA (which overwrites the accumulator)
+                    // waits for the next stage, produced only after this.
+                    if (!wait_all(&bar->acc_full, nacc & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    ++nacc;
+                    __syncwarp();
+                    tc_fence_after();
+                    const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+                    const bool first = ks < args.chunk;
+#pragma unroll 1
+                    for (int c = 0; c < 4; ++c) {
+                        uint32_t r[32], acc[32];
+                        tmem_ld32(tb + c * 32, r);
+                        if (!first) {
+                            tmem_ld32(tb + kSumCol + c * 32, acc);
+#pragma unroll
+                            for (int e = 0; e < 32; ++e)
+                                r[e] = __float_as_uint(__uint_as_float(r[e]) + __uint_as_float(acc[e]));
+                        }
+                        tmem_st32(tb + kSumCol + c * 32, r);
+                    }
+                    tc_fence_before();
+                }
             }
             if (!ok) break;
             // ------------------------------------------------------ epilogue
-            if (!wait_all(&bar->acc_full, tcount & 1u)) {
+            if (!wait_all(&bar->acc_full, nacc & 1u)) {
                 ok = false;
                 break;
             }
+            ++nacc;
             __syncwarp();  // lanes leave the wait loop independently; tcgen05.ld is warp-aligned
             tc_fence_after();
             const int64_t row = tm * TM + quarter * 32 + lane;  // observable a
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+            const bool chunked = nks > args.chunk;
+            // Phi (or Q) for 32 columns: last chunk's accumulator + running sum.
+            auto load_tile = [&](int c, uint32_t (&r)[32]) {
+                tmem_ld32(tbase + c * 32, r);
+                if (chunked) {
+                    uint32_t acc[32];
+                    tmem_ld32(tbase + kSumCol + c * 32, acc);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        r[e] = __float_as_uint(__uint_as_float(r[e]) + __uint_as_float(acc[e]));
+                }
+            };
             if (!GRAD && MODE == 0) {
                 const int64_t c0 = tn * TN + half * 128;  // first sample of this half
                 int64_t nvalid = args.s - c0;
@@ -330,7 +381,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    tmem_ld32(tbase + c * 32, r);
+                    load_tile(c, r);
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
@@ -338,7 +389,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    tmem_ld32(tbase + c * 32, r);
+                    load_tile(c, r);
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (c * 32 + e < nvalid) {
@@ -356,7 +407,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    tmem_ld32(tbase + c * 32, r);
+                    load_tile(c, r);
                     const int64_t i0 = c0 + c * 32;
                     uint32_t ph[16], pl[16];
 #pragma unroll
@@ -397,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    tmem_ld32(tbase + c * 32, r);
+                    load_tile(c, r);
                     const int64_t j0 = tn * TN + half * 128 + c * 32;
                     const uint32_t mask = (rv && j0 < args.m) ? args.pa32[row * args.ldp32 + (j0 >> 5)] : 0u;
                     float v[32];
@@ -523,6 +574,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.s = p.s;
     a.m = p.m;
     a.nks = cdiv(p.m, KS);
+    a.chunk = 64;  // 4096 gates per accumulation chunk
     a.tiles_m = cdiv(p.l, TM);
     a.tiles_n = cdiv(p.s, TN);
     a.chi = at<__nv_bfloat16>(ws, p.off_c);
@@ -560,6 +612,7 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.s = p.s;
     a.m = p.m;
     a.nks = cdiv(p.s, KS);
+    a.chunk = 32;  // 2048 samples per accumulation chunk
     a.tiles_m = cdiv(p.l, TM);
     a.tiles_n = cdiv(p.m, TN);
     a.chi = a.clo = nullptr;

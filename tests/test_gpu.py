@@ -182,22 +182,30 @@ def test_autograd_linear_loss(api, prec):
     assert not se.requires_grad
 
 
-def test_grad_central_differences_on_gpu(api):
-    """Directional derivative of the GPU estimator (split-BF16) by central
-    differences of the GPU forward, against the GPU gradient."""
+@pytest.mark.parametrize("prec", PRECS)
+def test_grad_central_differences_on_gpu(api, prec):
+    """Directional derivative of the GPU estimator by central differences of
+    the GPU forward (Richardson-extrapolated, so the O(h^2) term cancels),
+    against the GPU gradient."""
     p = ragged_problem(seed=12, n=40, m=200, l=64, s=512, scale=0.5)
     w = I.Rng(5).normal(p.l, 1)
-    v = I.Rng(6).normal(p.m, 1)
-    g = gpu_grad(api, p, -w / p.s, None, "split_bf16")
-    h = 1e-2
+    g = gpu_grad(api, p, -w / p.s, None, prec)
+    v = g / np.linalg.norm(g)  # steepest direction: g.v = |g|
 
     def F(th):
         q = I.Problem("fd", p.n, p.G, p.A, p.Z, th.astype(np.float32))
-        return float(np.dot(w, gpu_expval(api, q, "split_bf16")[0]))
+        return float(np.dot(w, gpu_expval(api, q, prec)[0]))
 
     th = p.theta.astype(np.float64)
-    fd = (F(th + h * v) - F(th - h * v)) / (2 * h)
-    assert abs(fd - float(np.dot(g, v))) <= 2e-2 * max(1.0, abs(fd))
+
+    def D(h):
+        return (F(th + h * v) - F(th - h * v)) / (2 * h)
+
+    h = 2e-2
+    fd = (4 * D(h / 2) - D(h)) / 3
+    gv = float(np.dot(g, v))
+    assert abs(gv) > 0.5
+    assert abs(fd - gv) <= 1e-2 * abs(gv)
 
 
 # -------------------------------------------------------------------- MMD
