@@ -99,6 +99,28 @@ iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                       double *expval, double *std_err,
                       void *ws, size_t ws_bytes, void *stream);
 
+/* iqp_expval for callers that cannot allocate device memory when they call
+ * in (for example a process whose device memory is all owned by another
+ * framework's caching pool, or latency-bound code that cannot afford
+ * cudaMalloc's device-wide synchronisation). The paper has no counterpart:
+ * it is a packaging of iqp_expval, with the same arguments and results
+ * minus `ws`. Scratch is one file-scope device array of 64 MiB inside this
+ * library, reserved on every GPU that loads the library and held until the
+ * process exits; this call allocates nothing. Sizes whose
+ * iqp_workspace_bytes(IQP_OP_EXPVAL, ...) exceeds 64 MiB are rejected with
+ * IQP_ERR_WORKSPACE before any launch. The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture. All calls share the one
+ * array: calls that overlap on the GPU (other streams, other host threads)
+ * race and corrupt each other's results, so serialise them. Device-side
+ * status (a bounded wait that ran out) is recorded in the array and cleared
+ * by the next call; it is not returned. */
+iqp_status iqp_expval_noalloc(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                              const uint64_t *A, int64_t l, int64_t lda,
+                              const uint64_t *Z, int64_t s, int64_t ldz,
+                              const float *theta, iqp_precision prec,
+                              double *expval, double *std_err, void *stream);
+
 /* Gradient of the estimator in theta (Sec. 2.4; the estimator is a
  * deterministic function of theta for fixed Z), for losses whose derivative
  * in the samples has the form dL/dPhi(a,z_i) = -sin Phi (alpha[a] + beta[a] cos Phi):
