@@ -155,7 +155,7 @@ iqp_status check_common(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, co
                         int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
                         iqp_precision prec) {
     if (n < 1 || m < 1 || l < 1 || s < 1) return IQP_ERR_ARG;
-    if (m > (int64_t)1 << 40 || l > (int64_t)1 << 31 || s > (int64_t)1 << 31) return IQP_ERR_ARG;
+    if (m > (int64_t)1 << 36 || l > (int64_t)1 << 31 || s > (int64_t)1 << 31) return IQP_ERR_ARG;
     iqp_status st;
     if ((st = check_bits(G, m, ldg, n)) != IQP_OK) return st;
     if ((st = check_bits(A, l, lda, n)) != IQP_OK) return st;

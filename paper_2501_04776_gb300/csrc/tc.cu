@@ -143,6 +143,26 @@ __device__ __forceinline__ float reduce_scatter32(float (&v)[32], int lane) {
     return v[0];
 }
 
+// Bounded wait polled by every lane (each needs the acquire), with the outcome
+// made warp-uniform so that a give-up never splits a warp.
+__device__ __forceinline__ bool wait_warp(uint64_t *b, uint32_t parity, volatile int *abort_flag, uint32_t *status,
+                                          uint64_t lim) {
+    const bool got = mbar_wait(b, parity, abort_flag, status, lim);
+    return __all_sync(0xFFFFFFFFu, got);
+}
+
+// 32 columns of the tile at TMEM address `t`: the current accumulator plus,
+// when the tile was accumulated in more than one chunk, the running sum.
+__device__ __forceinline__ void load_sum32(uint32_t t, bool chunked, uint32_t (&r)[32]) {
+    tmem_ld32(t, r);
+    if (chunked) {
+        uint32_t acc[32];
+        tmem_ld32(t + kSumCol, acc);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) r[e] = __float_as_uint(__uint_as_float(r[e]) + __uint_as_float(acc[e]));
+    }
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     const uint32_t lo = __bfloat16_as_ushort(__float2bfloat16_rn(a));
     const uint32_t hi = __bfloat16_as_ushort(__float2bfloat16_rn(b));
@@ -192,8 +212,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t tmem = bar->tmem_slot;
 
     const int64_t ntiles = args.tiles_m * args.tiles_n;
-    const int64_t nks = args.nks;
-    const int64_t nkb = cdiv(nks, KB / KS);
+    const int nks = (int)args.nks;     // host guarantees nks < 2^31
+    const int nkb = (nks + KB / KS - 1) / (KB / KS);
+    const int chunk = (int)args.chunk;
 
     if (warp == 0) {
         // ---------------------------------------------------------- TMA producer
@@ -202,12 +223,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             prefetch_tmap(&tmB);
             if (GRAD) prefetch_tmap(&tmA2);
             uint32_t itb = 0, ito = 0;
-            int last_b[NBITS] = {-1, -1};
-            int last_o[NOP] = {-1, -1};
+            uint32_t bmask = 0, bpar = 0, omask = 0, opar = 0;  // issued stages and their last parities
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 const int tm = (int)(t / args.tiles_n), tn = (int)(t % args.tiles_n);
-                for (int64_t kb = 0; kb < nkb && ok; ++kb, ++itb) {
+                for (int kb = 0; kb < nkb && ok; ++kb, ++itb) {
                     const uint32_t bs = itb % NBITS;
                     if (!mbar_wait(&bar->bits_empty[bs], ((itb / NBITS) & 1u) ^ 1u, abort_flag, status, lim)) {
                         ok = false;
@@ -225,11 +245,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                         bulk_load(bits + BT_CHI, args.chi + kb * KB, 512, &bar->bits_full[bs]);
                         bulk_load(bits + BT_CLO, args.clo + kb * KB, 512, &bar->bits_full[bs]);
                     }
-                    last_b[bs] = (int)((itb / NBITS) & 1u);
+                    bmask |= 1u << bs;
+                    bpar = (bpar & ~(1u << bs)) | (((itb / NBITS) & 1u) << bs);
                     if (GRAD) {
                         // W_hi / W_lo tiles of the operand stages of this bits stage.
                         for (int q = 0; q < KB / KS; ++q) {
-                            const int64_t ks = kb * (KB / KS) + q;
+                            const int ks = kb * (KB / KS) + q;
                             if (ks >= nks) break;
                             const uint32_t os = ito % NOP;
                             if (!mbar_wait(&bar->op_empty[os], ((ito / NOP) & 1u) ^ 1u, abort_flag, status, lim)) {
@@ -240,17 +261,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                             mbar_arrive_expect_tx(&bar->w_full[os], 2 * TM * KS * 2);
                             tma_load_2d(op + OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), tm * TM);
                             tma_load_2d(op + OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), tm * TM);
-                            last_o[os] = (int)((ito / NOP) & 1u);
+                            omask |= 1u << os;
+                            opar = (opar & ~(1u << os)) | (((ito / NOP) & 1u) << os);
                             ++ito;
                         }
                     }
                 }
             }
             // Drain: every copy this thread issued has landed before exit.
+#pragma unroll
             for (int i = 0; i < NBITS; ++i)
-                if (last_b[i] >= 0) mbar_drain(&bar->bits_full[i], (uint32_t)last_b[i], status, lim);
+                if ((bmask >> i) & 1u) mbar_drain(&bar->bits_full[i], (bpar >> i) & 1u, status, lim);
+#pragma unroll
             for (int i = 0; i < NOP; ++i)
-                if (GRAD && last_o[i] >= 0) mbar_drain(&bar->w_full[i], (uint32_t)last_o[i], status, lim);
+                if (GRAD && ((omask >> i) & 1u)) mbar_drain(&bar->w_full[i], (opar >> i) & 1u, status, lim);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
@@ -258,7 +282,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t ito = 0;
             bool ok = true;
             for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
-                for (int64_t ks = 0; ks < nks; ++ks, ++ito) {
+                int kc = 0;  // stage index within the current accumulation chunk
+                for (int ks = 0; ks < nks; ++ks, ++ito) {
                     const uint32_t os = ito % NOP;
                     if (!mbar_wait(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim) ||
                         (GRAD && !mbar_wait(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim))) {
@@ -267,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
                     const uint32_t base = smem_u32(smem + SM_OP + os * OP_BYTES);
-                    const bool fresh = (ks % args.chunk) == 0;  // first stage of a chunk
+                    const bool fresh = kc == 0;  // first stage of a chunk: overwrite the accumulator
 #pragma unroll
                     for (int k = 0; k < KS / 16; ++k) {
                         const uint64_t bdesc = sdesc_k128(base + OP_B + k * 32);
@@ -276,7 +301,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         umma_f16(tmem, sdesc_k128(base + OP_A_LO + k * 32), bdesc, IDESC, 1u);
                     }
                     umma_commit(&bar->op_empty[os]);
-                    if ((ks % args.chunk) == args.chunk - 1 || ks == nks - 1) umma_commit(&bar->acc_full);
+                    if (++kc == chunk || ks == nks - 1) {
+                        umma_commit(&bar->acc_full);
+                        kc = 0;
+                    }
                 }
             }
             // Drain: all issued MMAs complete before TMEM is freed.
@@ -290,23 +318,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int half = (warp - 2) >> 2; // column half of the epilogue
         uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
         bool ok = true;
-        // Every lane polls (each needs the acquire); the outcome is made
-        // warp-uniform so that a give-up never splits a warp.
-        auto wait_all = [&](uint64_t *b, uint32_t parity) {
-            const bool got = mbar_wait(b, parity, abort_flag, status, lim);
-            return __all_sync(0xFFFFFFFFu, got);
-        };
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
             const int64_t tm = t / args.tiles_n, tn = t % args.tiles_n;
-            for (int64_t ks = 0; ks < nks; ++ks) {
-                const int q = (int)(ks & 3);
+            int kc = 0;              // stage index within the current chunk
+            int nchunk = 0;          // chunks of this tile already folded into the running sum
+            bool fold_due = false;   // a finished chunk must be folded before the next release
+            for (int ks = 0; ks < nks; ++ks) {
+                const int q = ks & 3;
                 const uint32_t bs = itb % NBITS;
-                if (q == 0 && !wait_all(&bar->bits_full[bs], (itb / NBITS) & 1u)) {
+                if (q == 0 && !wait_warp(&bar->bits_full[bs], (itb / NBITS) & 1u, abort_flag, status, lim)) {
                     ok = false;
                     break;
                 }
                 const uint32_t os = ito % NOP;
-                if (!wait_all(&bar->op_empty[os], ((ito / NOP) & 1u) ^ 1u)) {
+                if (!wait_warp(&bar->op_empty[os], ((ito / NOP) & 1u) ^ 1u, abort_flag, status, lim)) {
                     ok = false;
                     break;
                 }
@@ -316,17 +341,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!GRAD) expand_a(bits + BT_A, bits + BT_CHI, bits + BT_CLO, op + OP_A_HI, op + OP_A_LO, q, gt);
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bar->op_full[os]);
-                ++ito;
-                if (q == 3 || ks == nks - 1) {
-                    if (lane == 0) mbar_arrive(&bar->bits_empty[bs]);
-                    ++itb;
-                }
-                if ((ks % args.chunk) == args.chunk - 1 && ks != nks - 1) {
-                    // Chunk done: fold the accumulator into the running sum. The
-                    // next chunk's first MMA (which overwrites the accumulator)
-                    // waits for the next stage, produced only after this.
-                    if (!wait_all(&bar->acc_full, nacc & 1u)) {
+                if (fold_due) {
+                    // This stage opens a new chunk and its first MMA overwrites
+                    // the accumulator: fold the finished chunk into the running
+                    // sum first, then release the stage (it was produced while
+                    // the previous chunk's last MMAs ran).
+                    if (!wait_warp(&bar->acc_full, nacc & 1u, abort_flag, status, lim)) {
                         ok = false;
                         break;
                     }
@@ -334,12 +354,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     __syncwarp();
                     tc_fence_after();
                     const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
-                    const bool first = ks < args.chunk;
 #pragma unroll 1
                     for (int c = 0; c < 4; ++c) {
                         uint32_t r[32], acc[32];
                         tmem_ld32(tb + c * 32, r);
-                        if (!first) {
+                        if (nchunk > 0) {
                             tmem_ld32(tb + kSumCol + c * 32, acc);
 #pragma unroll
                             for (int e = 0; e < 32; ++e)
@@ -348,11 +367,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_st32(tb + kSumCol + c * 32, r);
                     }
                     tc_fence_before();
+                    ++nchunk;
+                    fold_due = false;
+                }
+                if (lane == 0) mbar_arrive(&bar->op_full[os]);
+                ++ito;
+                if (q == 3 || ks == nks - 1) {
+                    if (lane == 0) mbar_arrive(&bar->bits_empty[bs]);
+                    ++itb;
+                }
+                if (++kc == chunk) {
+                    kc = 0;
+                    fold_due = ks != nks - 1;
                 }
             }
             if (!ok) break;
             // ------------------------------------------------------ epilogue
-            if (!wait_all(&bar->acc_full, nacc & 1u)) {
+            if (!wait_warp(&bar->acc_full, nacc & 1u, abort_flag, status, lim)) {
                 ok = false;
                 break;
             }
@@ -361,18 +392,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int64_t row = tm * TM + quarter * 32 + lane;  // observable a
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
-            const bool chunked = nks > args.chunk;
+            const bool chunked = nchunk > 0;
             // Phi (or Q) for 32 columns: last chunk's accumulator + running sum.
-            auto load_tile = [&](int c, uint32_t (&r)[32]) {
-                tmem_ld32(tbase + c * 32, r);
-                if (chunked) {
-                    uint32_t acc[32];
-                    tmem_ld32(tbase + kSumCol + c * 32, acc);
-#pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        r[e] = __float_as_uint(__uint_as_float(r[e]) + __uint_as_float(acc[e]));
-                }
-            };
             if (!GRAD && MODE == 0) {
                 const int64_t c0 = tn * TN + half * 128;  // first sample of this half
                 int64_t nvalid = args.s - c0;
@@ -381,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    load_tile(c, r);
+                    load_sum32(tbase + c * 32, chunked, r);
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
@@ -389,7 +410,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    load_tile(c, r);
+                    load_sum32(tbase + c * 32, chunked, r);
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (c * 32 + e < nvalid) {
@@ -407,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    load_tile(c, r);
+                    load_sum32(tbase + c * 32, chunked, r);
                     const int64_t i0 = c0 + c * 32;
                     uint32_t ph[16], pl[16];
 #pragma unroll
@@ -448,7 +469,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < 4; ++c) {
-                    load_tile(c, r);
+                    load_sum32(tbase + c * 32, chunked, r);
                     const int64_t j0 = tn * TN + half * 128 + c * 32;
                     const uint32_t mask = (rv && j0 < args.m) ? args.pa32[row * args.ldp32 + (j0 >> 5)] : 0u;
                     float v[32];
@@ -462,7 +483,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // second barrier is not needed.)
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar->red_full);
-                if (!wait_all(&bar->red_full, tcount & 1u)) {
+                if (!wait_warp(&bar->red_full, tcount & 1u, abort_flag, status, lim)) {
                     ok = false;
                     break;
                 }
