@@ -23,7 +23,7 @@ cudaError_t launch_phase_simt(int mode, const uint64_t *PA, const uint64_t *PZ, 
                               const double *beta, float *W, int64_t ldw, cudaStream_t st);
 cudaError_t launch_grad_simt(const float *W, int64_t ldw, const uint64_t *PZ, const uint64_t *PA, int64_t ldp,
                              int64_t l, int64_t s, int64_t m, double *gpart, cudaStream_t st);
-cudaError_t launch_finalize(const double2 *part, int64_t nparts, int64_t l, int64_t s, double *expval,
+cudaError_t launch_finalize(const double2 *part, int64_t nparts, int64_t pw, int64_t l, int64_t s, double *expval,
                             double *std_err, double *S1, double *S2, cudaStream_t st);
 cudaError_t launch_grad_reduce(const double *gpart, int64_t ntiles, int64_t m, double *grad, cudaStream_t st);
 cudaError_t launch_mmd_combine(const int64_t *T, const double *S1, const double *S2, int64_t l, int64_t s, int64_t N,
@@ -50,7 +50,8 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.ldzt = round_up(cdiv(s, 64), 4);
     p.mpad = p.ldp * 64;
     p.ldw = round_up(s, 64);
-    p.nparts = cdiv(s, kPartCols);
+    p.pw = prec == IQP_SPLIT_BF16 ? kPartColsTc : kPartColsSimt;
+    p.nparts = cdiv(s, p.pw);
     p.natile = cdiv(l, kATile);
     const bool grad = op == IQP_OP_EXPVAL_GRAD || op == IQP_OP_MMD_LOSS_GRAD;
     const bool mmd = op == IQP_OP_MMD_LOSS || op == IQP_OP_MMD_LOSS_GRAD;
@@ -212,7 +213,7 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
                                   at<float>(ws, p.off_c), p.l, p.s, p.m, part, p.nparts, nullptr, nullptr, nullptr, 0,
                                   st));
     }
-    IQP_TRY(launch_finalize(part, p.nparts, p.l, p.s, expval, std_err, S1, S2, st));
+    IQP_TRY(launch_finalize(part, p.nparts, p.pw, p.l, p.s, expval, std_err, S1, S2, st));
     return IQP_OK;
 }
 

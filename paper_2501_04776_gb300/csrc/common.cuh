@@ -14,7 +14,8 @@ namespace iqp {
 
 // ---------------------------------------------------------------- sizes
 
-constexpr int kPartCols = 128;   // samples per (S, M2) partial of the forward
+constexpr int kPartColsSimt = 128;  // samples per (S, M2) partial, FP32 form
+constexpr int kPartColsTc = 64;     // samples per (S, M2) partial, tensor-core form
 constexpr int kATile = 128;      // observables per gradient partial row
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
@@ -29,7 +30,8 @@ struct Plan {
     int64_t ldzt;   // words per row of P_Z^T (bits over s), multiple of 4
     int64_t mpad;   // ldp * 64 (length of the split-theta arrays)
     int64_t ldw;    // elements per row of W (multiple of 64)
-    int64_t nparts; // (S, M2) partials per observable: ceil(s / 128)
+    int64_t pw;     // samples per (S, M2) partial
+    int64_t nparts; // (S, M2) partials per observable: ceil(s / pw)
     int64_t natile; // ceil(l / 128)
     size_t off_status, off_pa, off_pz, off_pzt, off_c, off_part, off_w, off_gpart;
     size_t off_ab, off_s12, off_T, off_terms, total;

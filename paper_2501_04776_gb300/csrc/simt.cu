@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(256) k_grad_simt(const float *__restrict__ W, 
 
 // Merge the (S, M2) partials of each observable in fixed order (Chan et al.):
 // mean = S/s, M2 = sum_k [M2_k + n_k (S_k/n_k - mean)^2].
-__global__ void k_finalize(const double2 *__restrict__ part, int64_t nparts, int64_t l, int64_t s,
+__global__ void k_finalize(const double2 *__restrict__ part, int64_t nparts, int64_t pw, int64_t l, int64_t s,
                            double *__restrict__ expval, double *__restrict__ std_err, double *__restrict__ S1,
                            double *__restrict__ S2) {
     const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -263,7 +263,7 @@ __global__ void k_finalize(const double2 *__restrict__ part, int64_t nparts, int
     const double mean = S / (double)s;
     double M2 = 0.0;
     for (int64_t k = 0; k < nparts; ++k) {
-        const int64_t nk = (s - k * kPartCols) < kPartCols ? (s - k * kPartCols) : kPartCols;
+        const int64_t nk = (s - k * pw) < pw ? (s - k * pw) : pw;
         const double d = p[k].x / (double)nk - mean;
         M2 += p[k].y + (double)nk * d * d;
     }
@@ -375,10 +375,10 @@ cudaError_t launch_grad_simt(const float *W, int64_t ldw, const uint64_t *PZ, co
     return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const double2 *part, int64_t nparts, int64_t l, int64_t s, double *expval,
+cudaError_t launch_finalize(const double2 *part, int64_t nparts, int64_t pw, int64_t l, int64_t s, double *expval,
                             double *std_err, double *S1, double *S2, cudaStream_t st) {
     LaunchScope ls(IQP_KERNEL_FINALIZE, st);
-    k_finalize<<<(unsigned)cdiv(l, 256), 256, 0, st>>>(part, nparts, l, s, expval, std_err, S1, S2);
+    k_finalize<<<(unsigned)cdiv(l, 256), 256, 0, st>>>(part, nparts, pw, l, s, expval, std_err, S1, S2);
     return cudaGetLastError();
 }
 

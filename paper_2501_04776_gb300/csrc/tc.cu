@@ -4,12 +4,12 @@
 // one 128 (observables) x 256 (samples) FP32 accumulator in TMEM per tile,
 // K = gates streamed in 64-wide stages. Operands never exist in HBM as
 // numbers: a TMA warp brings 256-gate slices of the parity bits (and of the
-// hi/lo BF16 split of 2 theta) into shared memory; eight producer warps
+// hi/lo BF16 split of 2 theta) into shared memory; sixteen producer warps
 // expand them into the 128-byte-swizzled K-major BF16 layout the MMA reads
 // (A_hi = hi_j [P_A], A_lo = lo_j [P_A], B = 1 - 2 P_Z, all exact in BF16);
 // one thread issues two tcgen05.mma per 16-gate step (hi and lo share B).
 // The epilogue runs in the producer warps straight from TMEM:
-//   mode 0: cos, per-observable (S, M2) partials over 128-sample halves;
+//   mode 0: cos, per-observable (S, M2) partials over 64-sample groups;
 //   mode 1: W = sin Phi (alpha + beta cos Phi), split into hi + lo BF16 rows.
 // Phi itself is never written.
 //
@@ -45,8 +45,11 @@ constexpr int KS = 64;       // K per operand stage
 constexpr int KB = 256;      // K per bits stage
 constexpr int NOP = 2;       // operand stages
 constexpr int NBITS = 2;     // bits stages
-constexpr int NGEN = 8;      // producer / epilogue warps
+constexpr int NGEN = 16;     // producer / epilogue warps (4 per scheduler)
 constexpr int kThreads = 64 + NGEN * 32;
+constexpr int kRowsPerPass = NGEN * 32 / 8;   // operand rows expanded per pass (8 chunks per row)
+constexpr int kGroupCols = TN / (NGEN / 4);   // accumulator columns per epilogue warp
+constexpr int kGroupLoads = kGroupCols / 32;
 constexpr uint32_t kTmemCols = 512;   // accumulator (0..255) + running sum (256..511)
 constexpr uint32_t kSumCol = 256;
 constexpr uint32_t IDESC = idesc_bf16(TM, TN);
@@ -93,15 +96,15 @@ __device__ __forceinline__ uint8_t *aligned_smem(uint8_t *raw) {
 }
 
 // Expand one 64-gate sub-stage q of a bits stage into the B operand
-// (256 rows, +-1 BF16). Thread gt (0..255) handles chunk gt%8 of rows
-// gt/8 + 32k, k = 0..7.
+// (256 rows, +-1 BF16). Thread gt handles chunk gt%8 of rows
+// gt/8 + kRowsPerPass*k.
 __device__ __forceinline__ void expand_b(const uint8_t *bits, uint8_t *opB, int q, int gt) {
     const uint32_t c = gt & 7;
     const uint32_t sub = (uint32_t)q * 8u + (c >> 2) * 4u;  // byte offset of the u32 holding chunk c
     const uint32_t sh = (c & 3u) * 8u;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t row = (uint32_t)(gt >> 3) + 32u * k;
+    for (int k = 0; k < TN / kRowsPerPass; ++k) {
+        const uint32_t row = (uint32_t)(gt >> 3) + (uint32_t)kRowsPerPass * k;
         const uint32_t w = *reinterpret_cast<const uint32_t *>(bits + row * 32u + sub);
         const uint4 v = expand_pm1((w >> sh) & 0xFFu);
         *reinterpret_cast<uint4 *>(opB + swz128(row, c)) = v;
@@ -118,8 +121,8 @@ __device__ __forceinline__ void expand_a(const uint8_t *bitsA, const uint8_t *ch
     const uint32_t sub = (uint32_t)q * 8u + (c >> 2) * 4u;
     const uint32_t sh = (c & 3u) * 8u;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t row = (uint32_t)(gt >> 3) + 32u * k;
+    for (int k = 0; k < TM / kRowsPerPass; ++k) {
+        const uint32_t row = (uint32_t)(gt >> 3) + (uint32_t)kRowsPerPass * k;
         const uint32_t w = *reinterpret_cast<const uint32_t *>(bitsA + row * 32u + sub);
         const uint4 mk = expand_mask((w >> sh) & 0xFFu);
         const uint32_t off = swz128(row, c);
@@ -313,9 +316,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // ------------------------------------------------ producers + epilogue
-        const int gt = threadIdx.x - 64;  // 0..255
-        const int quarter = warp & 3;     // TMEM lane quarter this warp may access
-        const int half = (warp - 2) >> 2; // column half of the epilogue
+        const int gt = threadIdx.x - 64;   // 0 .. NGEN*32-1
+        const int quarter = warp & 3;      // TMEM lane quarter this warp may access
+        const int group = (warp - 2) >> 2; // accumulator column group of the epilogue
         uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
         bool ok = true;
         for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
@@ -353,9 +356,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ++nacc;
                     __syncwarp();
                     tc_fence_after();
-                    const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+                    const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(group * kGroupCols);
 #pragma unroll 1
-                    for (int c = 0; c < 4; ++c) {
+                    for (int c = 0; c < kGroupLoads; ++c) {
                         uint32_t r[32], acc[32];
                         tmem_ld32(tb + c * 32, r);
                         if (nchunk > 0) {
@@ -391,17 +394,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();  // lanes leave the wait loop independently; tcgen05.ld is warp-aligned
             tc_fence_after();
             const int64_t row = tm * TM + quarter * 32 + lane;  // observable a
-            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 128);
+            const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(group * kGroupCols);
             const bool chunked = nchunk > 0;
             // Phi (or Q) for 32 columns: last chunk's accumulator + running sum.
             if (!GRAD && MODE == 0) {
-                const int64_t c0 = tn * TN + half * 128;  // first sample of this half
+                const int64_t c0 = tn * TN + group * kGroupCols;  // first sample of this group
                 int64_t nvalid = args.s - c0;
-                nvalid = nvalid < 0 ? 0 : (nvalid > 128 ? 128 : nvalid);
+                nvalid = nvalid < 0 ? 0 : (nvalid > kGroupCols ? kGroupCols : nvalid);
                 float S = 0.f, M2 = 0.f;
                 uint32_t r[32];
 #pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < kGroupLoads; ++c) {
                     load_sum32(tbase + c * 32, chunked, r);
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
@@ -409,7 +412,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
 #pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < kGroupLoads; ++c) {
                     load_sum32(tbase + c * 32, chunked, r);
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
@@ -419,15 +422,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                 }
                 if (row < args.l && nvalid > 0)
-                    args.part[row * args.nparts + (c0 / 128)] = make_double2((double)S, (double)M2);
+                    args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
             } else if (!GRAD) {
-                const int64_t c0 = tn * TN + half * 128;
+                const int64_t c0 = tn * TN + group * kGroupCols;
                 const bool rv = row < args.l;
                 const float al = rv ? (float)args.alpha[row] : 0.f;
                 const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
                 uint32_t r[32];
 #pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < kGroupLoads; ++c) {
                     load_sum32(tbase + c * 32, chunked, r);
                     const int64_t i0 = c0 + c * 32;
                     uint32_t ph[16], pl[16];
@@ -468,16 +471,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const bool rv = row < args.l;
                 uint32_t r[32];
 #pragma unroll 1
-                for (int c = 0; c < 4; ++c) {
+                for (int c = 0; c < kGroupLoads; ++c) {
                     load_sum32(tbase + c * 32, chunked, r);
-                    const int64_t j0 = tn * TN + half * 128 + c * 32;
+                    const int64_t j0 = tn * TN + group * kGroupCols + c * 32;
                     const uint32_t mask = (rv && j0 < args.m) ? args.pa32[row * args.ldp32 + (j0 >> 5)] : 0u;
                     float v[32];
 #pragma unroll
                     for (int e = 0; e < 32; ++e) v[e] = ((mask >> e) & 1u) ? 2.f * __uint_as_float(r[e]) : 0.f;
-                    red[quarter * 256 + half * 128 + c * 32 + lane] = reduce_scatter32(v, lane);
+                    red[quarter * 256 + group * kGroupCols + c * 32 + lane] = reduce_scatter32(v, lane);
                 }
-                // All eight warps' column sums are in `red`; combine the four
+                // All producer warps' column sums are in `red`; combine the four
                 // lane quarters in fixed order. (The next tile's writes to
                 // `red` follow a full K loop that needs every warp, so a
                 // second barrier is not needed.)
@@ -489,7 +492,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 __syncwarp();
                 const int64_t j = tn * TN + gt;
-                if (j < args.m) {
+                if (gt < TN && j < args.m) {
                     const double sum = (double)red[gt] + (double)red[256 + gt] + (double)red[512 + gt] +
                                        (double)red[768 + gt];
                     args.gpart[tm * args.m + j] = sum;
