@@ -80,6 +80,19 @@ iqp_status iqp_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr,
                       const uint64_t *G, int64_t m, int64_t ldg,
                       uint64_t *P, int64_t ldp, void *stream);
 
+/* The same products by support gather, also returning the transpose: with
+ * R^T (n x ldpt words) formed in `scratch`, the parities of gate j with 64
+ * consecutive rows form one word, the XOR of the rows of R^T at the qubits
+ * of supp(g_j); a gate of weight k costs O(k) per 64 rows instead of a fold
+ * over all n qubits. Writes PT (m x ldpt words; bit r of row j is
+ * (R_r . g_j) mod 2, zero for r >= rows) and, if P != NULL, P exactly as
+ * iqp_parity does. ldpt >= ceil(rows/64), even. scratch: device memory of
+ * n*ldpt*8 bytes, 16-byte aligned, overwritten. Bit-exact. */
+iqp_status iqp_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr,
+                             const uint64_t *G, int64_t m, int64_t ldg,
+                             uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
+                             uint64_t *scratch, void *stream);
+
 /* Data parity sums of Sec. 3.3.1: T[a] = sum_{x < N} (-1)^{a.x}, so that
  * <Z_a>_p = T[a]/N for the empirical data distribution. A: l x lda words,
  * X: N x ldx words. T: int64[l], overwritten. Exact. No scratch. */

@@ -21,6 +21,7 @@ _MAT = [_p, _i64, _i64]
 SIGNATURES = {
     "iqp_workspace_bytes": (_sz, [_int, _i64, _i64, _i64, _i64, _i64, _int]),
     "iqp_parity": (_int, [_i64] + _MAT + _MAT + [_p, _i64, _p]),
+    "iqp_parity_gather": (_int, [_i64] + _MAT + _MAT + [_p, _i64, _p, _i64, _p, _p]),
     "iqp_parity_sum": (_int, [_i64] + _MAT + _MAT + [_p, _p]),
     "iqp_expval": (_int, [_i64] + _MAT * 3 + [_p, _int, _p, _p, _p, _sz, _p]),
     "iqp_expval_noalloc": (_int, [_i64] + _MAT * 3 + [_p, _int, _p, _p, _p]),

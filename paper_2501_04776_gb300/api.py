@@ -77,6 +77,23 @@ def parity(n: int, R: torch.Tensor, G: torch.Tensor, ldp: int | None = None) -> 
     return P
 
 
+def parity_gather(n: int, R: torch.Tensor, G: torch.Tensor):
+    """(P, P^T) by the support-gather method: P is rows x ldp words (bits over
+    gates), P^T is m x ldpt words (bits over rows)."""
+    _bits(R, "R"), _bits(G, "G")
+    rows, m = R.shape[0], G.shape[0]
+    ldp = (m + 63) // 64
+    ldp += ldp & 1
+    ldpt = (rows + 63) // 64
+    ldpt += ldpt & 1
+    P = torch.empty((rows, ldp), dtype=torch.int64, device=R.device)
+    PT = torch.empty((m, ldpt), dtype=torch.int64, device=R.device)
+    scratch = torch.empty((n, ldpt), dtype=torch.int64, device=R.device)
+    check(_lib.load().iqp_parity_gather(n, _ptr(R), rows, R.shape[1], _ptr(G), m, G.shape[1], _ptr(P), ldp, _ptr(PT),
+                                        ldpt, _ptr(scratch), ctypes.c_void_p(_stream(R.device))), "iqp_parity_gather")
+    return P, PT
+
+
 def parity_sum(n: int, A: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
     """T[a] = sum_x (-1)^{a.x} (int64)."""
     _bits(A, "A"), _bits(X, "X")

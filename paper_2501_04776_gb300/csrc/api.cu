@@ -14,6 +14,9 @@ namespace iqp {
 // ---- kernels (parity.cu, simt.cu, tc.cu)
 cudaError_t launch_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G, int64_t m,
                           int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt, cudaStream_t st);
+cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G,
+                                 int64_t m, int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
+                                 uint64_t *RT, cudaStream_t st);
 cudaError_t launch_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,
                               int64_t ldx, int64_t *T, cudaStream_t st);
 cudaError_t launch_theta_prep(const float *theta, int64_t m, int64_t mpad, float *c32, __nv_bfloat16 *hi,
@@ -48,6 +51,7 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.N = N;
     p.ldp = round_up(cdiv(m, 64), 4);
     p.ldzt = round_up(cdiv(s, 64), 4);
+    p.ldlt = round_up(cdiv(l, 64), 4);
     p.mpad = p.ldp * 64;
     p.ldw = round_up(s, 64);
     p.pw = prec == IQP_SPLIT_BF16 ? kPartColsTc : kPartColsSimt;
@@ -65,7 +69,9 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_status = take(256);
     p.off_pa = take(l * p.ldp * 8);
     p.off_pz = take(s * p.ldp * 8);
-    p.off_pzt = take(grad && tc ? m * p.ldzt * 8 : 0);
+    p.off_pzt = take(m * p.ldzt * 8);
+    p.off_pat = take(m * p.ldlt * 8);
+    p.off_rt = take(n * (p.ldzt > p.ldlt ? p.ldzt : p.ldlt) * 8);
     p.off_c = take(tc ? p.mpad * 4 : p.mpad * 4);
     p.off_part = take(l * p.nparts * 16);
     p.off_w = take(grad ? (tc ? l * p.ldw * 4 : l * p.ldw * 4) : 0);
@@ -185,12 +191,14 @@ T *at(void *ws, size_t off) {
         if (e_ != cudaSuccess) return IQP_ERR_CUDA;     \
     } while (0)
 
-// Parities of A and Z (and P_Z^T for the tensor-core gradient) + theta split.
+// Parities of A and Z by support gather (P_A, P_A^T, P_Z, P_Z^T) + theta split.
 iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, const uint64_t *A, int64_t lda,
-                   const uint64_t *Z, int64_t ldz, const float *theta, bool need_pzt, cudaStream_t st) {
-    IQP_TRY(launch_parity(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp, nullptr, 0, st));
-    IQP_TRY(launch_parity(p.n, Z, p.s, ldz, G, p.m, ldg, at<uint64_t>(ws, p.off_pz), p.ldp,
-                          need_pzt ? at<uint64_t>(ws, p.off_pzt) : nullptr, p.ldzt, st));
+                   const uint64_t *Z, int64_t ldz, const float *theta, cudaStream_t st) {
+    uint64_t *rt = at<uint64_t>(ws, p.off_rt);
+    IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
+                                 at<uint64_t>(ws, p.off_pat), p.ldlt, rt, st));
+    IQP_TRY(launch_parity_gather(p.n, Z, p.s, ldz, G, p.m, ldg, at<uint64_t>(ws, p.off_pz), p.ldp,
+                                 at<uint64_t>(ws, p.off_pzt), p.ldzt, rt, st));
     if (p.prec == IQP_SPLIT_BF16) {
         __nv_bfloat16 *hi = at<__nv_bfloat16>(ws, p.off_c);
         IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, nullptr, hi, hi + p.mpad, st));
@@ -250,7 +258,7 @@ iqp_status mmd_core(int op, int64_t n, const uint64_t *G, int64_t m, int64_t ldg
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const bool g = op == IQP_OP_MMD_LOSS_GRAD;
-    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, g && prec == IQP_SPLIT_BF16, st)) != IQP_OK) return rc;
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
     double *S1 = at<double>(ws, p.off_s12), *S2 = S1 + l;
     if ((rc = forward_stats(p, ws, nullptr, nullptr, S1, S2, st)) != IQP_OK) return rc;
     int64_t *T = at<int64_t>(ws, p.off_T);
@@ -298,6 +306,21 @@ iqp_status iqp_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, c
     return cuda_status(launch_parity(n, R, rows, ldr, G, m, ldg, P, ldp, nullptr, 0, static_cast<cudaStream_t>(stream)));
 }
 
+iqp_status iqp_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G, int64_t m,
+                             int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt, uint64_t *scratch,
+                             void *stream) {
+    if (n < 1 || m < 1) return IQP_ERR_ARG;
+    iqp_status rc;
+    if ((rc = check_bits(R, rows, ldr, n)) != IQP_OK) return rc;
+    if ((rc = check_bits(G, m, ldg, n)) != IQP_OK) return rc;
+    if (PT == nullptr || scratch == nullptr) return IQP_ERR_ARG;
+    if (ldpt < cdiv(rows, 64) || (ldpt & 1)) return IQP_ERR_ARG;
+    if (P != nullptr && (ldp < cdiv(m, 64) || (ldp & 1))) return IQP_ERR_ARG;
+    if (!aligned(PT, 16) || !aligned(scratch, 16) || (P && !aligned(P, 16))) return IQP_ERR_ALIGN;
+    return cuda_status(launch_parity_gather(n, R, rows, ldr, G, m, ldg, P, ldp, PT, ldpt, scratch,
+                                            static_cast<cudaStream_t>(stream)));
+}
+
 iqp_status iqp_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,
                           int64_t ldx, int64_t *T, void *stream) {
     if (n < 1) return IQP_ERR_ARG;
@@ -318,7 +341,7 @@ iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, cons
     const Plan p = make_plan(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, false, st)) != IQP_OK) return rc;
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
     return forward_stats(p, ws, expval, std_err, nullptr, nullptr, st);
 }
 
@@ -333,7 +356,7 @@ iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
     const Plan p = make_plan(IQP_OP_EXPVAL_GRAD, n, m, l, s, 0, prec);
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, prec == IQP_SPLIT_BF16, st)) != IQP_OK) return rc;
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
     return backward(p, ws, alpha, beta, grad, st);
 }
 

@@ -28,12 +28,13 @@ struct Plan {
     int op, prec;
     int64_t ldp;    // words per row of P_A / P_Z (bits over m), multiple of 4
     int64_t ldzt;   // words per row of P_Z^T (bits over s), multiple of 4
+    int64_t ldlt;   // words per row of P_A^T (bits over l), multiple of 4
     int64_t mpad;   // ldp * 64 (length of the split-theta arrays)
     int64_t ldw;    // elements per row of W (multiple of 64)
     int64_t pw;     // samples per (S, M2) partial
     int64_t nparts; // (S, M2) partials per observable: ceil(s / pw)
     int64_t natile; // ceil(l / 128)
-    size_t off_status, off_pa, off_pz, off_pzt, off_c, off_part, off_w, off_gpart;
+    size_t off_status, off_pa, off_pz, off_pzt, off_pat, off_rt, off_c, off_part, off_w, off_gpart;
     size_t off_ab, off_s12, off_T, off_terms, total;
 };
 

@@ -90,7 +90,128 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
     }
 }
 
+// ------------------------------------------------------------------
+// Support-gather path. With R^T (n x rows bits) in memory, the parities of
+// gate j with 64 consecutive rows are one word:
+//   P^T[j][w] = XOR over qubits q in supp(g_j) of R^T[q][w],
+// so a generator of weight k costs k coalesced row loads per 64 rows
+// (instead of a fold over all n qubits). The row-major P is a bit transpose
+// of P^T.
+
+// Bit transpose: out (in_cols x ld_out32*32 bits) = in^T, where in is
+// in_rows x in_cols bits with ld_in32 words per row. Output words beyond
+// in_rows bits are written as zero; output rows >= in_cols are not written.
+// Tile: 256 x 256 bits per block; each warp transposes 32 rows by ballots.
+__global__ void __launch_bounds__(256) k_bit_transpose(const uint32_t *__restrict__ in, int64_t in_rows,
+                                                        int64_t in_cols, int64_t ld_in32,
+                                                        uint32_t *__restrict__ out, int64_t ld_out32, int64_t gx) {
+    __shared__ uint32_t tin[256][9];
+    __shared__ uint32_t tout[256][9];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t bid = blockIdx.x;
+    const int64_t r0 = (bid % gx) * 256;   // input rows = output bit columns
+    const int64_t c0 = (bid / gx) * 256;   // input bit columns = output rows
+    const int64_t w0 = c0 >> 5;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int idx = tid + 256 * k, row = idx >> 3, q = idx & 7;
+        const int64_t r = r0 + row;
+        tin[row][q] = (r < in_rows && w0 + q < ld_in32) ? in[r * ld_in32 + w0 + q] : 0u;
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t word = tin[warp * 32 + lane][k];
+        uint32_t mine = 0u;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (word >> b) & 1u);
+            if (lane == b) mine = bal;
+        }
+        tout[k * 32 + lane][warp] = mine;  // output row c0 + 32k + lane, r-word r0/32 + warp
+    }
+    __syncthreads();
+    const int64_t orow = c0 + tid;
+    const int64_t ow0 = r0 >> 5;
+    if (orow < in_cols) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (ow0 + q < ld_out32) out[orow * ld_out32 + ow0 + q] = tout[tid][q];
+    }
+}
+
+// P^T[j][w] = XOR_{q in supp(g_j)} RT[q][w] for w < ldpt. One warp per
+// (gate, 256-word tile); the gate's support is scanned from its packed row.
+__global__ void __launch_bounds__(256) k_support_gather(const uint64_t *__restrict__ G, int64_t m, int64_t ldg,
+                                                         int64_t n, const uint64_t *__restrict__ RT, int64_t ldrt,
+                                                         uint64_t *__restrict__ PT, int64_t ldpt) {
+    const int nw = (int)((n + 63) >> 6);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 8 + warp;
+    if (j >= m) return;
+    const int64_t wt = (int64_t)blockIdx.y * 256;
+    uint64_t acc[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] = 0ull;
+    for (int wb = 0; wb < nw; wb += 32) {
+        const uint64_t word = (wb + lane < nw) ? G[j * ldg + wb + lane] : 0ull;
+        uint32_t nz = __ballot_sync(0xFFFFFFFFu, word != 0ull);
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            uint64_t wv = __shfl_sync(0xFFFFFFFFu, word, src);
+            while (wv) {
+                const int b = __ffsll((long long)wv) - 1;
+                wv &= wv - 1ull;
+                const int64_t q = (int64_t)64 * (wb + src) + b;
+                if (q >= n) break;  // padding bits must be zero; never read past R^T
+                const uint64_t *rt = RT + q * ldrt + wt;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int64_t w = lane + 32 * k;
+                    if (wt + w < ldpt) acc[k] ^= rt[w];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const int64_t w = wt + lane + 32 * k;
+        if (w < ldpt) PT[j * ldpt + w] = acc[k];
+    }
+}
+
+cudaError_t bit_transpose(const uint64_t *in, int64_t in_rows, int64_t in_cols, int64_t ld_in, uint64_t *out,
+                          int64_t ld_out, cudaStream_t st) {
+    const int64_t gx = cdiv(ld_out * 64, 256);
+    const int64_t gy = cdiv(in_cols, 256);
+    if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+    LaunchScope ls(IQP_KERNEL_PARITY, st);
+    k_bit_transpose<<<(unsigned)(gx * gy), 256, 0, st>>>(reinterpret_cast<const uint32_t *>(in), in_rows, in_cols,
+                                                          2 * ld_in, reinterpret_cast<uint32_t *>(out), 2 * ld_out, gx);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+// Support-gather parities: RT (n x ldpt words) is scratch; writes PT
+// (m x ldpt words: bits over rows, zero beyond `rows`) and, if P != nullptr,
+// P (rows x ldp words: bits over gates, zero beyond m).
+cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G,
+                                 int64_t m, int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
+                                 uint64_t *RT, cudaStream_t st) {
+    cudaError_t e = bit_transpose(R, rows, n, ldr, RT, ldpt, st);
+    if (e != cudaSuccess) return e;
+    {
+        dim3 grid((unsigned)cdiv(m, 8), (unsigned)cdiv(ldpt, 256));
+        LaunchScope ls(IQP_KERNEL_PARITY, st);
+        k_support_gather<<<grid, 256, 0, st>>>(G, m, ldg, n, RT, ldpt, PT, ldpt);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    if (P != nullptr) return bit_transpose(PT, m, rows, ldpt, P, ldp, st);
+    return cudaSuccess;
+}
 
 // P (rows x ldp words) and, if PT != nullptr, P^T (m x ldpt words). Every
 // word of every P row is written (bits >= m are zero); PT rows get the bits

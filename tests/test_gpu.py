@@ -83,6 +83,25 @@ def test_parity_bit_exact(api, n, m, rows):
     assert not got[:, m:].any()  # padding bits are zero
 
 
+@pytest.mark.parametrize("n,m,rows,dense", [(1, 1, 1, False), (63, 65, 33, False), (130, 300, 257, False),
+                                            (300, 1000, 700, False), (5000, 513, 40, False), (777, 300, 129, True)])
+def test_parity_gather_bit_exact(api, n, m, rows, dense):
+    rng = I.Rng(300 + n)
+    R = I.bernoulli_bits(rng, rows, n, 0.5, 1)
+    if dense or n < 3:
+        G = I.bernoulli_bits(rng, m, n, 0.5, 2)
+    else:
+        G = I.random_k_body(rng, m, n, [1, 2, 3], 2)
+    P, PT = api.parity_gather(n, dev(api, R), dev(api, G))
+    P = P.cpu().numpy().view(np.uint64)
+    PT = PT.cpu().numpy().view(np.uint64)
+    want = oracle.parity(n, R, G)
+    gotP = I.unpack_bits(P, P.shape[1] * 64)
+    gotT = I.unpack_bits(PT, PT.shape[1] * 64)
+    assert np.array_equal(gotP[:, :m], want) and not gotP[:, m:].any()
+    assert np.array_equal(gotT[:, :rows], want.T) and not gotT[:, rows:].any()
+
+
 def test_parity_dense_generators_bit_exact(api):
     rng = I.Rng(5)
     n, m, rows = 777, 300, 129
