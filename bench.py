@@ -135,6 +135,27 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ traffic
+
+def measured_traffic(kernel, sizes):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    (profiles/dram_traffic.json), or None if the capture was of another
+    workload or the kernel sources changed since."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
+        h = hashlib.sha256()
+        for f in ("tc.cu", "common.cuh"):
+            h.update(open(os.path.join(ROOT, "paper_2501_04776_gb300", "csrc", f), "rb").read())
+        if h.hexdigest()[:16] != rec["source_sha"]:
+            return None
+        if tuple(sizes) != (1000, 100_000, 10_000, 10_000):
+            return None
+        return rec["kernels"][kernel]["traffic_bytes"]
+    except Exception:
+        return None
+
+
 # ------------------------------------------------------------------- clocks
 
 class ClockSampler:
@@ -297,11 +318,12 @@ def main():
         pass
     if prec == _lib.SPLIT_BF16:
         dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
+        traffic = measured_traffic(dom, (n, m, l, s))
         executed = 4.0 * l * s * m  # two BF16 products (hi, lo) of 2*l*s*m flops per launch
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
         achieved = executed / (kt[dom]["avg_ms"] * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
                 "flops_per_launch": executed, "useful_tflops": round(achieved / 2, 1),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
