@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--s", type=int, default=10_000)
     ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the plain FP32 form (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-l", type=int, default=16)
-    ap.add_argument("--cpu-sample-s", type=int, default=2000)
+    ap.add_argument("--cpu-sample-l", type=int, default=128)
+    ap.add_argument("--cpu-sample-s", type=int, default=10_000)
     return ap.parse_args()
 
 

@@ -36,20 +36,28 @@ typedef struct {
     int32_t *idx;
 } support_t;
 
+/* Words that are zero hold no qubit of the support and are skipped. */
 static support_t support_of(const uint64_t *M, int64_t rows, int64_t ld, int64_t n) {
     support_t sp;
+    const int64_t nw = (n + 63) / 64;
     sp.start = (int64_t *)malloc(sizeof(int64_t) * (size_t)(rows + 1));
     int64_t total = 0;
     for (int64_t r = 0; r < rows; ++r) {
         sp.start[r] = total;
-        for (int64_t q = 0; q < n; ++q) total += bit_at(M + r * ld, q);
+        for (int64_t w = 0; w < nw; ++w) {
+            if (M[r * ld + w] == 0) continue;
+            for (int64_t q = 64 * w; q < 64 * w + 64 && q < n; ++q) total += bit_at(M + r * ld, q);
+        }
     }
     sp.start[rows] = total;
     sp.idx = (int32_t *)malloc(sizeof(int32_t) * (size_t)(total > 0 ? total : 1));
     int64_t k = 0;
     for (int64_t r = 0; r < rows; ++r)
-        for (int64_t q = 0; q < n; ++q)
-            if (bit_at(M + r * ld, q)) sp.idx[k++] = (int32_t)q;
+        for (int64_t w = 0; w < nw; ++w) {
+            if (M[r * ld + w] == 0) continue;
+            for (int64_t q = 64 * w; q < 64 * w + 64 && q < n; ++q)
+                if (bit_at(M + r * ld, q)) sp.idx[k++] = (int32_t)q;
+        }
     return sp;
 }
 

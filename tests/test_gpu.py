@@ -350,3 +350,99 @@ def test_launch_counter_counts_kernels(api):
     p = I.tiny_local(seed=4, s=128)
     gpu_expval(api, p, "split_bf16")
     assert api.launch_count() - before >= 4  # parity x2, theta split, phase, finalize
+
+
+# ------------------------------------------------ remaining workload shapes
+
+def _relevant_gates(n, G, A_sub):
+    """Gates that anticommute with at least one of the sampled observables.
+    Every other gate has P_A = 0 on all of them, so it adds exactly zero to
+    their phases and its gradient entry is exactly zero: the oracle can skip it."""
+    return np.nonzero(oracle.parity(n, A_sub, G).any(axis=0))[0]
+
+
+def _oracle_expval_chunked(n, G, A, Z, th, chunk=4096):
+    """Oracle estimate over all samples, computed on sample chunks (bounded
+    host memory); S1 and S2 are exact sums, so the mean and the population
+    variance follow directly."""
+    S1 = np.zeros(A.shape[0])
+    S2 = np.zeros(A.shape[0])
+    for i0 in range(0, Z.shape[0], chunk):
+        _, _, s1, s2 = oracle.expval(n, G, A, Z[i0:i0 + chunk], th)
+        S1 += s1
+        S2 += s2
+    s = Z.shape[0]
+    mean = S1 / s
+    var = np.maximum(S2 / s - mean ** 2, 0.0)
+    return mean, np.sqrt(var / s)
+
+
+def _oracle_grad_chunked(n, G, A, Z, th, alpha, chunk=4096):
+    g = np.zeros(G.shape[0])
+    for i0 in range(0, Z.shape[0], chunk):
+        g += oracle.expval_grad(n, G, A, Z[i0:i0 + chunk], th, alpha, None)
+    return g
+
+
+def _sampled_big_check(api, p, seed, nsample):
+    prec = "split_bf16"
+    ev, se = gpu_expval(api, p, prec)
+    idx = np.unique(np.sort(I.Rng(seed).integers(nsample, p.l, 1)))
+    A = p.A[idx]
+    J = _relevant_gates(p.n, p.G, A)
+    G, th = p.G[J], p.theta.astype(np.float64)[J]
+    want_ev, want_se = _oracle_expval_chunked(p.n, G, A, p.Z, th)
+    assert np.max(np.abs(ev[idx] - want_ev)) <= TOL[prec]
+    assert np.max(np.abs(se[idx] - want_se)) <= TOL[prec]
+    alpha = np.zeros(p.l)
+    alpha[idx] = I.Rng(seed + 1).normal(idx.size, 1) / p.s
+    g = gpu_grad(api, p, alpha, None, prec)
+    want = np.zeros(p.m)
+    want[J] = _oracle_grad_chunked(p.n, G, A, p.Z, th, alpha[idx])
+    assert rel_l2(g, want) <= GRAD_RTOL
+    outside = np.ones(p.m, bool)
+    outside[J] = False
+    assert np.all(g[outside] == 0.0)
+
+
+@pytest.mark.parametrize("n", [100, 5000])
+def test_full_size_random_gates_other_widths(api, n):
+    """10000 observables x 10000 samples x 100000 gates at n = 100 and 5000
+    (split-BF16), sampled observables."""
+    _sampled_big_check(api, I.random_gates(n=n), 31 + n, 8)
+
+
+def test_full_size_million_gates(api):
+    """n=5000, m=1e6 random one- and two-body gates, 4096 observables, 16384
+    samples (split-BF16, bit-packed operands only), sampled observables."""
+    _sampled_big_check(api, I.million_gates(), 41, 6)
+
+
+def test_full_size_mmd_training_shapes(api):
+    """MMD loss + gradient with the training workload's full m = 500500, n =
+    1000, s = 5000, N = 10000, on a 32-observable subsample (the loss is a
+    mean over observables, so a subsample is itself a valid MMD estimate)."""
+    p = I.mmd_training(n=1000, l=2000, s=5000, N=10_000)
+    p.theta = (p.theta * 10).astype(np.float32)
+    idx = np.unique(np.sort(I.Rng(51).integers(32, p.l, 1)))
+    A = p.A[idx]
+    J = _relevant_gates(p.n, p.G, A)
+    for unbiased in (True, False):
+        loss, grad = api.mmd_loss_raw(p.n, th_dev(p.theta), dev(api, p.G), dev(api, A), dev(api, p.Z),
+                                      dev(api, p.X), "split_bf16", unbiased, with_grad=True)
+        want_loss, _, wg = oracle.mmd_loss(p.n, p.G[J], A, p.Z, p.X, p.theta.astype(np.float64)[J], unbiased,
+                                           grad=True)
+        want_grad = np.zeros(p.m)
+        want_grad[J] = wg
+        assert abs(float(loss) - want_loss) <= TOL["split_bf16"]
+        assert rel_l2(grad.cpu().numpy(), want_grad) <= GRAD_RTOL
+
+
+def test_adam_on_mmd_loss_converges(api):
+    """The training loop (fresh samples and observables every step, Adam)
+    drives the MMD^2 loss of a small circuit towards the data."""
+    from paper_2501_04776_gb300 import train
+    p = I.mmd_training(seed=7, n=10, l=256, s=512, N=500)
+    _, losses = train.adam_mmd(p, steps=60, lr=0.05)
+    assert np.all(np.isfinite(losses))
+    assert np.mean(losses[-5:]) < 0.3 * np.mean(losses[:5])
