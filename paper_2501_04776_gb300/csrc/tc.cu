@@ -27,9 +27,20 @@
 // producer warps add it into an FP32 running sum (columns 256..511) with
 // round-to-nearest adds. The epilogue reads accumulator + running sum.
 //
+// CTA pairs: with CG = 2 the kernels run as clusters of two CTAs on two SMs.
+// A tile is 256 observables x 256 columns; each CTA holds 128 observables'
+// A rows and half (128 rows) of the B operand, and the even CTA issues
+// M256 x N256 pair MMAs (cta_group::2) that read both CTAs' shared memory and
+// write 128 accumulator rows into each CTA's TMEM. Per SM this halves the B
+// operand's expansion work and the tensor core's B reads from shared memory.
+// Both CTAs' producer warps arrive on the even CTA's stage barrier; stage and
+// chunk completions are multicast to both CTAs.
+//
 // Every wait is bounded (globaltimer); on expiry the CTA records
 // IQP_ERR_TIMEOUT, drains its in-flight copies and MMAs, frees TMEM and exits.
 #include <cuda.h>
+
+#include <cstdlib>
 
 #include "common.cuh"
 
@@ -39,11 +50,10 @@ uint64_t default_spin_limit_ns();
 
 namespace {
 
-constexpr int TM = 128;      // UMMA M (observables)
-constexpr int TN = 256;      // UMMA N (samples or gates)
+constexpr int TM = 128;      // accumulator rows (observables) per CTA
+constexpr int TN = 256;      // accumulator columns (samples or gates) per tile
 constexpr int KS = 64;       // K per operand stage
 constexpr int KB = 256;      // K per bits stage
-constexpr int NOP = 2;       // operand stages
 constexpr int NBITS = 2;     // bits stages
 constexpr int NGEN = 16;     // producer / epilogue warps (4 per scheduler)
 constexpr int kThreads = 64 + NGEN * 32;
@@ -52,18 +62,30 @@ constexpr int kGroupCols = TN / (NGEN / 4);   // accumulator columns per epilogu
 constexpr int kGroupLoads = kGroupCols / 32;
 constexpr uint32_t kTmemCols = 512;   // accumulator (0..255) + running sum (256..511)
 constexpr uint32_t kSumCol = 256;
-constexpr uint32_t IDESC = idesc_bf16(TM, TN);
+constexpr int kMaxOp = 4;
 
-// Operand stage: A_hi (128 x 128 B), A_lo, B (256 x 128 B).
-constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = 32768, OP_BYTES = 65536;
-// Bits stage: A bits (128 rows x 32 B), B bits (256 rows x 32 B), c_hi, c_lo (256 BF16 each).
-constexpr uint32_t BT_A = 0, BT_B = 4096, BT_CHI = 12288, BT_CLO = 12800, BT_BYTES = 13312;
-constexpr uint32_t SM_OP = 0;
-constexpr uint32_t SM_BITS = SM_OP + NOP * OP_BYTES;
-constexpr uint32_t SM_BAR = SM_BITS + NBITS * BT_BYTES;
-constexpr uint32_t SM_RED = SM_BAR + 256;                 // 4 x 256 floats (grad epilogue)
-constexpr uint32_t SM_END = SM_RED + 4 * 256 * 4;
-constexpr uint32_t kSmemBytes = SM_END + 1024;            // + alignment slack
+// Shared-memory layout for a CTA group of CG CTAs (CG = 1 or 2).
+template <int CG>
+struct Cfg {
+    static constexpr int TNB = TN / CG;      // B rows this CTA holds
+    static constexpr int NOP = CG == 2 ? 4 : 2;
+    // Operand stage: A_hi (128 x 128 B), A_lo, B (TNB x 128 B).
+    static constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = 32768;
+    static constexpr uint32_t OP_BYTES = 32768 + TNB * 128;
+    // Bits stage: A bits (128 rows x 32 B), B bits (TNB rows x 32 B), c_hi, c_lo.
+    static constexpr uint32_t BT_A = 0, BT_B = 4096;
+    static constexpr uint32_t BT_CHI = BT_B + TNB * 32, BT_CLO = BT_CHI + 512;
+    static constexpr uint32_t BT_BYTES = BT_CLO + 512;
+    static constexpr uint32_t SM_OP = 0;
+    static constexpr uint32_t SM_BITS = SM_OP + NOP * OP_BYTES;
+    static constexpr uint32_t SM_BAR = SM_BITS + NBITS * BT_BYTES;
+    static constexpr uint32_t SM_RED = SM_BAR + 256;   // 4 x 256 floats (grad epilogue)
+    static constexpr uint32_t SM_END = SM_RED + 4 * 256 * 4;
+    static constexpr uint32_t SMEM = SM_END + 1024;     // + alignment slack
+    static constexpr uint32_t IDESC = idesc_bf16(TM * CG, TN);
+    static_assert(OP_BYTES % 1024 == 0 && BT_BYTES % 1024 == 0, "stage alignment");
+    static_assert(SMEM <= 232448, "shared memory");
+};
 
 struct TcArgs {
     int64_t l, s, m;
@@ -84,8 +106,8 @@ struct TcArgs {
 };
 
 struct Bars {
-    uint64_t bits_full[NBITS], bits_empty[NBITS], op_full[NOP], op_empty[NOP], w_full[NOP], acc_full, drain,
-        red_full;
+    uint64_t bits_full[NBITS], bits_empty[NBITS], op_full[kMaxOp], op_empty[kMaxOp], w_full[kMaxOp],
+        peer_full[kMaxOp], acc_full, drain, red_full;
     uint32_t tmem_slot;
     int abort_flag;
 };
@@ -96,14 +118,15 @@ __device__ __forceinline__ uint8_t *aligned_smem(uint8_t *raw) {
 }
 
 // Expand one 64-gate sub-stage q of a bits stage into the B operand
-// (256 rows, +-1 BF16). Thread gt handles chunk gt%8 of rows
+// (ROWS rows, +-1 BF16). Thread gt handles chunk gt%8 of rows
 // gt/8 + kRowsPerPass*k.
+template <int ROWS>
 __device__ __forceinline__ void expand_b(const uint8_t *bits, uint8_t *opB, int q, int gt) {
     const uint32_t c = gt & 7;
     const uint32_t sub = (uint32_t)q * 8u + (c >> 2) * 4u;  // byte offset of the u32 holding chunk c
     const uint32_t sh = (c & 3u) * 8u;
 #pragma unroll
-    for (int k = 0; k < TN / kRowsPerPass; ++k) {
+    for (int k = 0; k < ROWS / kRowsPerPass; ++k) {
         const uint32_t row = (uint32_t)(gt >> 3) + (uint32_t)kRowsPerPass * k;
         const uint32_t w = *reinterpret_cast<const uint32_t *>(bits + row * 32u + sub);
         const uint4 v = expand_pm1((w >> sh) & 0xFFu);
@@ -175,18 +198,24 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // ------------------------------------------------------------------ kernel
 // GRAD = false: phase contraction (MODE 0 stats / MODE 1 W).
 // GRAD = true : gradient contraction.
-template <bool GRAD, int MODE>
+// CG = 1: one CTA per tile of 128 rows; CG = 2: a CTA pair per tile of 256 rows.
+template <bool GRAD, int MODE, int CG>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
          const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
+    using C = Cfg<CG>;
+    constexpr int NOP = C::NOP;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = aligned_smem(smem_raw);
-    Bars *bar = reinterpret_cast<Bars *>(smem + SM_BAR);
-    float *red = reinterpret_cast<float *>(smem + SM_RED);
+    Bars *bar = reinterpret_cast<Bars *>(smem + C::SM_BAR);
+    float *red = reinterpret_cast<float *>(smem + C::SM_RED);
     volatile int *abort_flag = &bar->abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t lim = args.limit_ns;
     uint32_t *status = args.status;
+    const uint32_t crank = CG == 2 ? cluster_ctarank() : 0u;  // CTA rank in the pair
+    const bool leader = crank == 0;
+    const int64_t group0 = blockIdx.x / CG, ngroups = gridDim.x / CG;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NBITS; ++i) {
@@ -194,9 +223,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&bar->bits_empty[i], NGEN);
         }
         for (int i = 0; i < NOP; ++i) {
-            mbar_init(&bar->op_full[i], NGEN);
+            // Even CTA: its own producer warps, plus one forwarded arrival from
+            // the odd CTA of a pair.
+            mbar_init(&bar->op_full[i], CG == 2 ? NGEN + 1 : NGEN);
             mbar_init(&bar->op_empty[i], 1);
             mbar_init(&bar->w_full[i], 1);
+            mbar_init(&bar->peer_full[i], NGEN);  // odd CTA: its producer warps
         }
         mbar_init(&bar->acc_full, 1);
         mbar_init(&bar->drain, 1);
@@ -206,11 +238,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_proxy_async_smem();
     }
     if (warp == 1) {
-        tmem_alloc(&bar->tmem_slot, kTmemCols);
-        tmem_relinquish();
+        if (CG == 2) {
+            tmem_alloc_pair(&bar->tmem_slot, kTmemCols);
+            tmem_relinquish_pair();
+        } else {
+            tmem_alloc(&bar->tmem_slot, kTmemCols);
+            tmem_relinquish();
+        }
     }
     tc_fence_before();
     __syncthreads();
+    if (CG == 2) cluster_sync_all();  // the peer's barriers exist before anyone arrives on them
     tc_fence_after();
     const uint32_t tmem = bar->tmem_slot;
 
@@ -228,25 +266,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t itb = 0, ito = 0;
             uint32_t bmask = 0, bpar = 0, omask = 0, opar = 0;  // issued stages and their last parities
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
                 const int tm = (int)(t / args.tiles_n), tn = (int)(t % args.tiles_n);
+                const int a0 = tm * TM * CG + (int)crank * TM;     // this CTA's first A row
+                const int b0 = tn * TN + (int)crank * C::TNB;      // this CTA's first B row
                 for (int kb = 0; kb < nkb && ok; ++kb, ++itb) {
                     const uint32_t bs = itb % NBITS;
                     if (!mbar_wait(&bar->bits_empty[bs], ((itb / NBITS) & 1u) ^ 1u, abort_flag, status, lim)) {
                         ok = false;
                         break;
                     }
-                    uint8_t *bits = smem + SM_BITS + bs * BT_BYTES;
+                    uint8_t *bits = smem + C::SM_BITS + bs * C::BT_BYTES;
                     const int x = (int)(kb * 4);
                     if (GRAD) {
-                        mbar_arrive_expect_tx(&bar->bits_full[bs], TN * 32);
-                        tma_load_2d(bits + BT_B, &tmB, &bar->bits_full[bs], x, tn * TN);
+                        mbar_arrive_expect_tx(&bar->bits_full[bs], C::TNB * 32);
+                        tma_load_2d(bits + C::BT_B, &tmB, &bar->bits_full[bs], x, b0);
                     } else {
-                        mbar_arrive_expect_tx(&bar->bits_full[bs], TM * 32 + TN * 32 + 1024);
-                        tma_load_2d(bits + BT_A, &tmA, &bar->bits_full[bs], x, tm * TM);
-                        tma_load_2d(bits + BT_B, &tmB, &bar->bits_full[bs], x, tn * TN);
-                        bulk_load(bits + BT_CHI, args.chi + kb * KB, 512, &bar->bits_full[bs]);
-                        bulk_load(bits + BT_CLO, args.clo + kb * KB, 512, &bar->bits_full[bs]);
+                        mbar_arrive_expect_tx(&bar->bits_full[bs], TM * 32 + C::TNB * 32 + 1024);
+                        tma_load_2d(bits + C::BT_A, &tmA, &bar->bits_full[bs], x, a0);
+                        tma_load_2d(bits + C::BT_B, &tmB, &bar->bits_full[bs], x, b0);
+                        bulk_load(bits + C::BT_CHI, args.chi + kb * KB, 512, &bar->bits_full[bs]);
+                        bulk_load(bits + C::BT_CLO, args.clo + kb * KB, 512, &bar->bits_full[bs]);
                     }
                     bmask |= 1u << bs;
                     bpar = (bpar & ~(1u << bs)) | (((itb / NBITS) & 1u) << bs);
@@ -260,10 +300,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                                 ok = false;
                                 break;
                             }
-                            uint8_t *op = smem + SM_OP + os * OP_BYTES;
+                            uint8_t *op = smem + C::SM_OP + os * C::OP_BYTES;
                             mbar_arrive_expect_tx(&bar->w_full[os], 2 * TM * KS * 2);
-                            tma_load_2d(op + OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), tm * TM);
-                            tma_load_2d(op + OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), tm * TM);
+                            tma_load_2d(op + C::OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), a0);
+                            tma_load_2d(op + C::OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), a0);
                             omask |= 1u << os;
                             opar = (opar & ~(1u << os)) | (((ito / NOP) & 1u) << os);
                             ++ito;
@@ -281,38 +321,67 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             uint32_t ito = 0;
             bool ok = true;
-            for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
                 int kc = 0;  // stage index within the current accumulation chunk
                 for (int ks = 0; ks < nks; ++ks, ++ito) {
                     const uint32_t os = ito % NOP;
-                    if (!mbar_wait(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim) ||
-                        (GRAD && !mbar_wait(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim))) {
+                    const bool got = CG == 2
+                                         ? mbar_wait_cluster(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim)
+                                         : mbar_wait(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim);
+                    if (!got) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t base = smem_u32(smem + SM_OP + os * OP_BYTES);
+                    const uint32_t base = smem_u32(smem + C::SM_OP + os * C::OP_BYTES);
                     const bool fresh = kc == 0;  // first stage of a chunk: overwrite the accumulator
 #pragma unroll
                     for (int k = 0; k < KS / 16; ++k) {
-                        const uint64_t bdesc = sdesc_k128(base + OP_B + k * 32);
-                        umma_f16(tmem, sdesc_k128(base + OP_A_HI + k * 32), bdesc, IDESC,
-                                 (fresh && k == 0) ? 0u : 1u);
-                        umma_f16(tmem, sdesc_k128(base + OP_A_LO + k * 32), bdesc, IDESC, 1u);
+                        const uint64_t bdesc = sdesc_k128(base + C::OP_B + k * 32);
+                        const uint64_t ahi = sdesc_k128(base + C::OP_A_HI + k * 32);
+                        const uint64_t alo = sdesc_k128(base + C::OP_A_LO + k * 32);
+                        if (CG == 2) {
+                            umma_f16_pair(tmem, ahi, bdesc, C::IDESC, (fresh && k == 0) ? 0u : 1u);
+                            umma_f16_pair(tmem, alo, bdesc, C::IDESC, 1u);
+                        } else {
+                            umma_f16(tmem, ahi, bdesc, C::IDESC, (fresh && k == 0) ? 0u : 1u);
+                            umma_f16(tmem, alo, bdesc, C::IDESC, 1u);
+                        }
                     }
-                    umma_commit(&bar->op_empty[os]);
+                    if (CG == 2) umma_commit_pair(&bar->op_empty[os]);
+                    else umma_commit(&bar->op_empty[os]);
                     if (++kc == chunk || ks == nks - 1) {
-                        umma_commit(&bar->acc_full);
+                        if (CG == 2) umma_commit_pair(&bar->acc_full);
+                        else umma_commit(&bar->acc_full);
                         kc = 0;
                     }
                 }
             }
-            // Drain: all issued MMAs complete before TMEM is freed.
-            umma_commit(&bar->drain);
+            // Drain: all issued MMAs complete before TMEM is freed (and, for a
+            // pair, before the peer may leave: the cluster barrier below).
+            if (CG == 2) umma_commit_pair(&bar->drain);
+            else umma_commit(&bar->drain);
             mbar_drain(&bar->drain, 0u, status, lim);
+        } else if (CG == 2 && lane == 0) {
+            // Odd CTA of a pair: forward "my half of stage ks is ready" to the
+            // even CTA's stage barrier, one cluster-scope release per stage,
+            // so the producer warps themselves only use CTA-scope arrivals.
+            const uint32_t op_full_remote = mapa_shared(smem_u32(&bar->op_full[0]), 0u);
+            uint32_t ito = 0;
+            bool ok = true;
+            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+                for (int ks = 0; ks < nks; ++ks, ++ito) {
+                    const uint32_t os = ito % NOP;
+                    if (!mbar_wait(&bar->peer_full[os], (ito / NOP) & 1u, abort_flag, status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_remote(op_full_remote + os * 8u);
+                }
+            }
         }
     } else {
         // ------------------------------------------------ producers + epilogue
@@ -321,8 +390,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int group = (warp - 2) >> 2; // accumulator column group of the epilogue
         uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
         bool ok = true;
-        for (int64_t t = blockIdx.x; t < ntiles && ok; t += gridDim.x, ++tcount) {
+        for (int64_t t = group0; t < ntiles && ok; t += ngroups, ++tcount) {
             const int64_t tm = t / args.tiles_n, tn = t % args.tiles_n;
+            const int64_t arow0 = tm * TM * CG + (int64_t)crank * TM;  // this CTA's first observable
             int kc = 0;              // stage index within the current chunk
             int nchunk = 0;          // chunks of this tile already folded into the running sum
             bool fold_due = false;   // a finished chunk must be folded before the next release
@@ -338,12 +408,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = false;
                     break;
                 }
-                const uint8_t *bits = smem + SM_BITS + bs * BT_BYTES;
-                uint8_t *op = smem + SM_OP + os * OP_BYTES;
-                expand_b(bits + BT_B, op + OP_B, q, gt);
-                if (!GRAD) expand_a(bits + BT_A, bits + BT_CHI, bits + BT_CLO, op + OP_A_HI, op + OP_A_LO, q, gt);
+                const uint8_t *bits = smem + C::SM_BITS + bs * C::BT_BYTES;
+                uint8_t *op = smem + C::SM_OP + os * C::OP_BYTES;
+                expand_b<C::TNB>(bits + C::BT_B, op + C::OP_B, q, gt);
+                if (!GRAD)
+                    expand_a(bits + C::BT_A, bits + C::BT_CHI, bits + C::BT_CLO, op + C::OP_A_HI, op + C::OP_A_LO, q,
+                             gt);
                 fence_proxy_async_smem();
                 __syncwarp();
+                if (GRAD && !wait_warp(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim)) {
+                    // This CTA's W tiles must have landed before the stage is released.
+                    ok = false;
+                    break;
+                }
                 if (fold_due) {
                     // This stage opens a new chunk and its first MMA overwrites
                     // the accumulator: fold the finished chunk into the running
@@ -373,7 +450,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ++nchunk;
                     fold_due = false;
                 }
-                if (lane == 0) mbar_arrive(&bar->op_full[os]);
+                if (lane == 0) {
+                    // Even CTA: straight to the stage barrier; odd CTA: to the
+                    // local barrier its forwarder watches.
+                    if (CG == 2 && !leader) mbar_arrive(&bar->peer_full[os]);
+                    else mbar_arrive(&bar->op_full[os]);
+                }
                 ++ito;
                 if (q == 3 || ks == nks - 1) {
                     if (lane == 0) mbar_arrive(&bar->bits_empty[bs]);
@@ -393,7 +475,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ++nacc;
             __syncwarp();  // lanes leave the wait loop independently; tcgen05.ld is warp-aligned
             tc_fence_after();
-            const int64_t row = tm * TM + quarter * 32 + lane;  // observable a
+            const int64_t row = arow0 + quarter * 32 + lane;  // observable a
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(group * kGroupCols);
             const bool chunked = nchunk > 0;
             // Phi (or Q) for 32 columns: last chunk's accumulator + running sum.
@@ -492,10 +574,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 __syncwarp();
                 const int64_t j = tn * TN + gt;
-                if (gt < TN && j < args.m) {
+                if (gt < TN && j < args.m && arow0 < args.l) {
                     const double sum = (double)red[gt] + (double)red[256 + gt] + (double)red[512 + gt] +
                                        (double)red[768 + gt];
-                    args.gpart[tm * args.m + j] = sum;
+                    args.gpart[(arow0 / TM) * args.m + j] = sum;
                 }
             }
             tc_fence_before();
@@ -503,10 +585,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     __syncthreads();
+    if (CG == 2) cluster_sync_all();  // the even CTA's MMAs (which read this CTA) have drained
     if (warp == 1) {
         __syncwarp();  // lane 0 ran the MMA loop alone; dealloc is warp-aligned
         tc_fence_after();
-        tmem_dealloc(tmem, kTmemCols);
+        if (CG == 2) tmem_dealloc_pair(tmem, kTmemCols);
+        else tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -557,23 +641,49 @@ bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool GRAD, int MODE>
+template <bool GRAD, int MODE, int CG>
 cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
                      cudaStream_t st) {
+    using C = Cfg<CG>;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)kSmemBytes);
+        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     const int64_t ntiles = args.tiles_m * args.tiles_n;
     int sms = num_sms();
-    if (sms <= 0) sms = 1;
-    const int grid = (int)(ntiles < sms ? ntiles : sms);
+    if (sms < CG) sms = CG;
+    const int64_t groups = ntiles < sms / CG ? ntiles : sms / CG;
     LaunchScope ls(GRAD ? IQP_KERNEL_GRAD_TC : (MODE == 0 ? IQP_KERNEL_PHASE_TC : IQP_KERNEL_RECOMPUTE_TC), st);
-    k_tc<GRAD, MODE><<<grid, kThreads, kSmemBytes, st>>>(a, a2, b, args);
-    return cudaGetLastError();
+    if (CG == 1) {
+        k_tc<GRAD, MODE, 1><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(groups * CG), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CG;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG>, a, a2, b, args);
+}
+
+// Tensor-core group size: CTA pairs unless IQP_CTA_PAIRS=0.
+int cta_group() {
+    static int cg = -1;
+    if (cg < 0) {
+        const char *e = std::getenv("IQP_CTA_PAIRS");
+        cg = (e != nullptr && e[0] == '0') ? 1 : 2;
+    }
+    return cg;
 }
 
 template <class T>
@@ -585,11 +695,12 @@ T *at(void *ws, size_t off) {
 
 cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alpha, const double *beta,
                             cudaStream_t st, iqp_status *why) {
+    const int cg = cta_group();
     CUtensorMap ma, mb;
     if (!make_map(&ma, at<uint64_t>(ws, p.off_pa), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldp, p.l, p.ldp * 8, 4, TM,
                   CU_TENSOR_MAP_SWIZZLE_NONE) ||
-        !make_map(&mb, at<uint64_t>(ws, p.off_pz), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldp, p.s, p.ldp * 8, 4, TN,
-                  CU_TENSOR_MAP_SWIZZLE_NONE)) {
+        !make_map(&mb, at<uint64_t>(ws, p.off_pz), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldp, p.s, p.ldp * 8, 4,
+                  (uint32_t)(TN / cg), CU_TENSOR_MAP_SWIZZLE_NONE)) {
         *why = IQP_ERR_UNSUPPORTED;
         return cudaErrorNotSupported;
     }
@@ -599,7 +710,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.m = p.m;
     a.nks = cdiv(p.m, KS);
     a.chunk = 64;  // 4096 gates per accumulation chunk
-    a.tiles_m = cdiv(p.l, TM);
+    a.tiles_m = cdiv(p.l, TM * cg);
     a.tiles_n = cdiv(p.s, TN);
     a.chi = at<__nv_bfloat16>(ws, p.off_c);
     a.clo = a.chi + p.mpad;
@@ -615,10 +726,13 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.gpart = nullptr;
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
-    return mode == 0 ? launch_k<false, 0>(ma, ma, mb, a, st) : launch_k<false, 1>(ma, ma, mb, a, st);
+    if (cg == 2)
+        return mode == 0 ? launch_k<false, 0, 2>(ma, ma, mb, a, st) : launch_k<false, 1, 2>(ma, ma, mb, a, st);
+    return mode == 0 ? launch_k<false, 0, 1>(ma, ma, mb, a, st) : launch_k<false, 1, 1>(ma, ma, mb, a, st);
 }
 
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why) {
+    const int cg = cta_group();
     CUtensorMap mhi, mlo, mb;
     const __nv_bfloat16 *whi = at<__nv_bfloat16>(ws, p.off_w);
     const __nv_bfloat16 *wlo = whi + p.l * p.ldw;
@@ -626,8 +740,8 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
                   CU_TENSOR_MAP_SWIZZLE_128B) ||
         !make_map(&mlo, wlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, TM,
                   CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_map(&mb, at<uint64_t>(ws, p.off_pzt), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldzt, p.m, p.ldzt * 8, 4, TN,
-                  CU_TENSOR_MAP_SWIZZLE_NONE)) {
+        !make_map(&mb, at<uint64_t>(ws, p.off_pzt), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldzt, p.m, p.ldzt * 8, 4,
+                  (uint32_t)(TN / cg), CU_TENSOR_MAP_SWIZZLE_NONE)) {
         *why = IQP_ERR_UNSUPPORTED;
         return cudaErrorNotSupported;
     }
@@ -637,7 +751,7 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.m = p.m;
     a.nks = cdiv(p.s, KS);
     a.chunk = 32;  // 2048 samples per accumulation chunk
-    a.tiles_m = cdiv(p.l, TM);
+    a.tiles_m = cdiv(p.l, TM * cg);
     a.tiles_n = cdiv(p.m, TN);
     a.chi = a.clo = nullptr;
     a.part = nullptr;
@@ -650,7 +764,7 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.gpart = at<double>(ws, p.off_gpart);
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
-    return launch_k<true, 0>(mhi, mlo, mb, a, st);
+    return cg == 2 ? launch_k<true, 0, 2>(mhi, mlo, mb, a, st) : launch_k<true, 0, 1>(mhi, mlo, mb, a, st);
 }
 
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st) {
