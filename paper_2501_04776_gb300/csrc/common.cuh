@@ -280,6 +280,27 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
         : "memory");
 }
 
+// 2D TMA load multicast to the CTAs in `mask` (same shared offset in each),
+// completing on the barrier at `bar`'s offset in each of them.
+__device__ __forceinline__ void tma_load_2d_multicast(void *dst, const void *tmap, uint64_t *bar, int x, int y,
+                                                      uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
+        : "memory");
+}
+
+// Single-CTA MMA completion signalled to the barrier at `bar`'s offset in
+// every CTA of `mask`.
+__device__ __forceinline__ void umma_commit_multicast(uint64_t *bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+
 // Arrive once on `bar` when all previously issued tcgen05.mma of this thread complete.
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(

@@ -65,10 +65,10 @@ constexpr uint32_t kSumCol = 256;
 constexpr int kMaxOp = 4;
 
 // Shared-memory layout for a CTA group of CG CTAs (CG = 1 or 2).
-template <int CG>
+template <int CG, bool GRAD>
 struct Cfg {
     static constexpr int TNB = TN / CG;      // B rows this CTA holds
-    static constexpr int NOP = CG == 2 ? 4 : 2;
+    static constexpr int NOP = CG == 2 ? 4 : 2;  // operand stages
     // Operand stage: A_hi (128 x 128 B), A_lo, B (TNB x 128 B).
     static constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = 32768;
     static constexpr uint32_t OP_BYTES = 32768 + TNB * 128;
@@ -199,11 +199,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // GRAD = false: phase contraction (MODE 0 stats / MODE 1 W).
 // GRAD = true : gradient contraction.
 // CG = 1: one CTA per tile of 128 rows; CG = 2: a CTA pair per tile of 256 rows.
-template <bool GRAD, int MODE, int CG>
+// MC = 2 (gradient with CG = 1): clusters of two CTAs on the same 128
+// observables and adjacent 256-gate columns; each loads half of every W tile
+// and multicasts it to both, halving W's L2-to-SM traffic.
+template <bool GRAD, int MODE, int CG, int MC>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
          const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
-    using C = Cfg<CG>;
+    using C = Cfg<CG, GRAD>;
     constexpr int NOP = C::NOP;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = aligned_smem(smem_raw);
@@ -213,9 +216,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t lim = args.limit_ns;
     uint32_t *status = args.status;
-    const uint32_t crank = CG == 2 ? cluster_ctarank() : 0u;  // CTA rank in the pair
-    const bool leader = crank == 0;
-    const int64_t group0 = blockIdx.x / CG, ngroups = gridDim.x / CG;
+    constexpr int CL = CG * MC;  // CTAs per cluster
+    const uint32_t crank = CL == 2 ? cluster_ctarank() : 0u;  // CTA rank in the cluster
+    const bool leader = CG == 1 || crank == 0;                 // issues this CTA's MMAs
+    const int64_t group0 = blockIdx.x / CL, ngroups = gridDim.x / CL;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NBITS; ++i) {
@@ -226,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // Even CTA: its own producer warps, plus one forwarded arrival from
             // the odd CTA of a pair.
             mbar_init(&bar->op_full[i], CG == 2 ? NGEN + 1 : NGEN);
-            mbar_init(&bar->op_empty[i], 1);
+            mbar_init(&bar->op_empty[i], MC);  // every MMA that reads the stage
             mbar_init(&bar->w_full[i], 1);
             mbar_init(&bar->peer_full[i], NGEN);  // odd CTA: its producer warps
         }
@@ -248,11 +252,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     tc_fence_before();
     __syncthreads();
-    if (CG == 2) cluster_sync_all();  // the peer's barriers exist before anyone arrives on them
+    if (CL == 2) cluster_sync_all();  // the peer's barriers exist before anyone arrives on them
     tc_fence_after();
     const uint32_t tmem = bar->tmem_slot;
 
-    const int64_t ntiles = args.tiles_m * args.tiles_n;
+    // Tiles per cluster iteration: with MC = 2 a cluster takes two adjacent
+    // column tiles of one row block.
+    const int64_t tiles_nc = MC == 2 ? (args.tiles_n + 1) / 2 : args.tiles_n;
+    const int64_t ntiles = args.tiles_m * tiles_nc;
     const int nks = (int)args.nks;     // host guarantees nks < 2^31
     const int nkb = (nks + KB / KS - 1) / (KB / KS);
     const int chunk = (int)args.chunk;
@@ -267,9 +274,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t bmask = 0, bpar = 0, omask = 0, opar = 0;  // issued stages and their last parities
             bool ok = true;
             for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
-                const int tm = (int)(t / args.tiles_n), tn = (int)(t % args.tiles_n);
-                const int a0 = tm * TM * CG + (int)crank * TM;     // this CTA's first A row
-                const int b0 = tn * TN + (int)crank * C::TNB;      // this CTA's first B row
+                const int tm = (int)(t / tiles_nc);
+                const int tn = (int)(MC == 2 ? 2 * (t % tiles_nc) + crank : t % tiles_nc);
+                const int prank = CG == 2 ? (int)crank : 0;        // rank within an MMA pair
+                const int a0 = tm * TM * CG + prank * TM;          // this CTA's first A row
+                const int b0 = tn * TN + prank * C::TNB;           // this CTA's first B row
                 for (int kb = 0; kb < nkb && ok; ++kb, ++itb) {
                     const uint32_t bs = itb % NBITS;
                     if (!mbar_wait(&bar->bits_empty[bs], ((itb / NBITS) & 1u) ^ 1u, abort_flag, status, lim)) {
@@ -302,8 +311,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                             uint8_t *op = smem + C::SM_OP + os * C::OP_BYTES;
                             mbar_arrive_expect_tx(&bar->w_full[os], 2 * TM * KS * 2);
-                            tma_load_2d(op + C::OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), a0);
-                            tma_load_2d(op + C::OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), a0);
+                            if (MC == 2) {
+                                // This CTA's half of the rows, written into both CTAs.
+                                const uint32_t h = crank * (TM / 2) * 128u;
+                                const int y = a0 + (int)crank * (TM / 2);
+                                tma_load_2d_multicast(op + C::OP_A_HI + h, &tmA, &bar->w_full[os], (int)(ks * KS), y,
+                                                      (uint16_t)3);
+                                tma_load_2d_multicast(op + C::OP_A_LO + h, &tmA2, &bar->w_full[os], (int)(ks * KS), y,
+                                                      (uint16_t)3);
+                            } else {
+                                tma_load_2d(op + C::OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), a0);
+                                tma_load_2d(op + C::OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), a0);
+                            }
                             omask |= 1u << os;
                             opar = (opar & ~(1u << os)) | (((ito / NOP) & 1u) << os);
                             ++ito;
@@ -328,9 +347,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int kc = 0;  // stage index within the current accumulation chunk
                 for (int ks = 0; ks < nks; ++ks, ++ito) {
                     const uint32_t os = ito % NOP;
-                    const bool got = CG == 2
-                                         ? mbar_wait_cluster(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim)
-                                         : mbar_wait(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim);
+                    // One-CTA gradient: this thread also waits for the stage's W
+                    // tiles (a pair's W halves are vouched for by its producers).
+                    const bool got =
+                        CG == 2 ? mbar_wait_cluster(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim)
+                                : (mbar_wait(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim) &&
+                                   (!GRAD ||
+                                    mbar_wait(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim)));
                     if (!got) {
                         ok = false;
                         break;
@@ -352,6 +375,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     if (CG == 2) umma_commit_pair(&bar->op_empty[os]);
+                    else if (MC == 2) umma_commit_multicast(&bar->op_empty[os], (uint16_t)3);
                     else umma_commit(&bar->op_empty[os]);
                     if (++kc == chunk || ks == nks - 1) {
                         if (CG == 2) umma_commit_pair(&bar->acc_full);
@@ -391,8 +415,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
         bool ok = true;
         for (int64_t t = group0; t < ntiles && ok; t += ngroups, ++tcount) {
-            const int64_t tm = t / args.tiles_n, tn = t % args.tiles_n;
-            const int64_t arow0 = tm * TM * CG + (int64_t)crank * TM;  // this CTA's first observable
+            const int64_t tm = t / tiles_nc;
+            const int64_t tn = MC == 2 ? 2 * (t % tiles_nc) + crank : t % tiles_nc;
+            const int64_t arow0 = tm * TM * CG + (CG == 2 ? (int64_t)crank * TM : 0);  // first observable here
             int kc = 0;              // stage index within the current chunk
             int nchunk = 0;          // chunks of this tile already folded into the running sum
             bool fold_due = false;   // a finished chunk must be folded before the next release
@@ -416,8 +441,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                              gt);
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (GRAD && !wait_warp(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim)) {
-                    // This CTA's W tiles must have landed before the stage is released.
+                if (GRAD && CG == 2 && !wait_warp(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim)) {
+                    // A pair's W tiles must have landed before the stage is released.
                     ok = false;
                     break;
                 }
@@ -585,7 +610,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     __syncthreads();
-    if (CG == 2) cluster_sync_all();  // the even CTA's MMAs (which read this CTA) have drained
+    if (CL == 2) cluster_sync_all();  // no MMA or multicast copy still touches the peer
     if (warp == 1) {
         __syncwarp();  // lane 0 ran the MMA loop alone; dealloc is warp-aligned
         tc_fence_after();
@@ -641,39 +666,52 @@ bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool GRAD, int MODE, int CG>
+template <bool GRAD, int MODE, int CG, int MC = 1>
 cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
                      cudaStream_t st) {
-    using C = Cfg<CG>;
+    using C = Cfg<CG, GRAD>;
+    constexpr int CL = CG * MC;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int64_t ntiles = args.tiles_m * args.tiles_n;
+    const int64_t ntiles = args.tiles_m * (MC == 2 ? (args.tiles_n + 1) / 2 : args.tiles_n);
     int sms = num_sms();
-    if (sms < CG) sms = CG;
-    const int64_t groups = ntiles < sms / CG ? ntiles : sms / CG;
+    if (sms < CL) sms = CL;
+    const int64_t groups = ntiles < sms / CL ? ntiles : sms / CL;
     LaunchScope ls(GRAD ? IQP_KERNEL_GRAD_TC : (MODE == 0 ? IQP_KERNEL_PHASE_TC : IQP_KERNEL_RECOMPUTE_TC), st);
-    if (CG == 1) {
-        k_tc<GRAD, MODE, 1><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
+    if (CL == 1) {
+        k_tc<GRAD, MODE, 1, 1><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(groups * CG), 1, 1);
+    cfg.gridDim = dim3((unsigned)(groups * CL), 1, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = C::SMEM;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = CG;
+    attr[0].val.clusterDim.x = CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG>, a, a2, b, args);
+    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, MC>, a, a2, b, args);
+}
+
+// Gradient kernel form: single-CTA MMAs; with IQP_GRAD_MULTICAST=1, clusters
+// of two that share each W tile by TMA multicast (halves W's L2-to-SM
+// traffic; measured no faster on the benchmark workload, so off by default).
+bool grad_multicast() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("IQP_GRAD_MULTICAST");
+        v = (e != nullptr && e[0] == '1') ? 1 : 0;
+    }
+    return v == 1;
 }
 
 // Tensor-core group size: CTA pairs unless IQP_CTA_PAIRS=0.
@@ -732,13 +770,15 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
 }
 
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why) {
-    const int cg = cta_group();
+    const bool mc = grad_multicast();
+    const int cg = 1;
     CUtensorMap mhi, mlo, mb;
     const __nv_bfloat16 *whi = at<__nv_bfloat16>(ws, p.off_w);
     const __nv_bfloat16 *wlo = whi + p.l * p.ldw;
-    if (!make_map(&mhi, whi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, TM,
+    const uint32_t wrows = mc ? TM / 2 : TM;  // each CTA of a multicast pair loads half the rows
+    if (!make_map(&mhi, whi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, wrows,
                   CU_TENSOR_MAP_SWIZZLE_128B) ||
-        !make_map(&mlo, wlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, TM,
+        !make_map(&mlo, wlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, wrows,
                   CU_TENSOR_MAP_SWIZZLE_128B) ||
         !make_map(&mb, at<uint64_t>(ws, p.off_pzt), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldzt, p.m, p.ldzt * 8, 4,
                   (uint32_t)(TN / cg), CU_TENSOR_MAP_SWIZZLE_NONE)) {
@@ -764,7 +804,8 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.gpart = at<double>(ws, p.off_gpart);
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
-    return cg == 2 ? launch_k<true, 0, 2>(mhi, mlo, mb, a, st) : launch_k<true, 0, 1>(mhi, mlo, mb, a, st);
+    if (mc) return launch_k<true, 0, 1, 2>(mhi, mlo, mb, a, st);
+    return launch_k<true, 0, 1>(mhi, mlo, mb, a, st);
 }
 
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st) {

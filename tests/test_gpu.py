@@ -446,3 +446,37 @@ def test_adam_on_mmd_loss_converges(api):
     _, losses = train.adam_mmd(p, steps=60, lr=0.05)
     assert np.all(np.isfinite(losses))
     assert np.mean(losses[-5:]) < 0.3 * np.mean(losses[:5])
+
+
+@pytest.mark.parametrize("pairs,multicast", [("0", "0"), ("2", "1")])
+def test_other_tensor_kernel_forms_match_oracle(pairs, multicast):
+    """The tensor-core kernel forms the defaults do not use: one-CTA phase
+    kernels (IQP_CTA_PAIRS=0) and the W-multicast gradient
+    (IQP_GRAD_MULTICAST=1), on the ragged problem, in a fresh process."""
+    import json
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import json, numpy as np, torch, oracle
+from paper_2501_04776_gb300 import api, inputs as I
+rng = I.Rng(8)
+n, m, l, s = 130, 1000, 260, 520
+G = I.random_k_body(rng, m, n, [1, 2, 3], 1); th = (0.3 * rng.normal(m, 2)).astype(np.float32)
+A = I.bernoulli_bits(rng, l, n, 0.1, 3); Z = I.uniform_bits(rng, s, n, 4)
+d = api.to_device_bits
+ev, se = api.expval_raw(n, torch.from_numpy(th).cuda(), d(G), d(A), d(Z), "split_bf16")
+wev, wse, _, _ = oracle.expval(n, G, A, Z, th.astype(np.float64))
+al = rng.normal(l, 9) / s
+g = api.expval_grad(n, torch.from_numpy(th).cuda(), d(G), d(A), d(Z), torch.from_numpy(al).cuda(), None, "split_bf16")
+wg = oracle.expval_grad(n, G, A, Z, th.astype(np.float64), al, None)
+print(json.dumps({"ev": float(np.max(np.abs(ev.cpu().numpy() - wev))), "se": float(np.max(np.abs(se.cpu().numpy() - wse))),
+                  "g": float(np.linalg.norm(g.cpu().numpy() - wg) / np.linalg.norm(wg)), "status": api.read_status()}))
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, IQP_CTA_PAIRS=pairs, IQP_GRAD_MULTICAST=multicast, PYTHONPATH=root)
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    assert r["status"] == 0
+    assert r["ev"] <= TOL["split_bf16"] and r["se"] <= TOL["split_bf16"] and r["g"] <= GRAD_RTOL
