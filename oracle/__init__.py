@@ -49,6 +49,7 @@ def _load():
             "oracle_statevector_expval": [i64] + mat * 2 + [p, p],
             "oracle_subset_expansion": [i64] + mat * 2 + [p, p],
             "oracle_bitflip_expval": [i64] + mat * 2 + [p, p],
+            "oracle_bitflip_grad": [i64] + mat * 2 + [p, p, p],
             "oracle_set_threads": [ctypes.c_int],
             "oracle_max_threads": [],
         }
@@ -195,6 +196,16 @@ def bitflip_expval(n, G, A, theta):
     out = np.empty(l)
     lib.oracle_bitflip_expval(n, pg, m, ldg, pa, l, lda, _d(theta).ctypes.data, out.ctypes.data)
     return out
+
+
+def bitflip_grad(n, G, A, theta, w):
+    """d/dtheta of sum_a w_a prod_{j in J_a} cos(2 theta_j) (product rule)."""
+    lib = _load()
+    G, pg, m, ldg = _w(G)
+    A, pa, l, lda = _w(A)
+    g = np.empty(m)
+    lib.oracle_bitflip_grad(n, pg, m, ldg, pa, l, lda, _d(theta).ctypes.data, _d(w).ctypes.data, g.ctypes.data)
+    return g
 
 
 if __name__ == "__main__":  # pragma: no cover

@@ -441,6 +441,28 @@ void oracle_bitflip_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
     free(PA);
 }
 
+/* Gradient of L = sum_a w_a <Z_a> for the bitflip model, by the product
+ * rule on eq. expval_bitflip: d/dtheta_j prod_{k in J_a} cos(2 theta_k) =
+ * -2 sin(2 theta_j) prod_{k in J_a, k != j} cos(2 theta_k) for j in J_a. */
+void oracle_bitflip_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                         const uint64_t *A, int64_t l, int64_t lda, const double *theta,
+                         const double *w, double *grad) {
+    uint8_t *PA = parity_matrix(n, A, l, lda, G, m, ldg);
+    int64_t *J = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < m; ++j) grad[j] = 0.0;
+    for (int64_t a = 0; a < l; ++a) {
+        int64_t k = gates_of(PA + a * m, m, J);
+        for (int64_t t = 0; t < k; ++t) {
+            double rest = 1.0;
+            for (int64_t u = 0; u < k; ++u)
+                if (u != t) rest *= cos(2.0 * theta[J[u]]);
+            grad[J[t]] += w[a] * (-2.0 * sin(2.0 * theta[J[t]])) * rest;
+        }
+    }
+    free(J);
+    free(PA);
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -269,6 +269,38 @@ def test_grad_zero_at_theta_zero():
     assert np.all(g == 0.0)
 
 
+def test_bitflip_grad_matches_central_differences():
+    """Stochastic bitflip circuit (eq. expval_bitflip): the product-rule
+    gradient against central differences of the product form."""
+    rng = I.Rng(45)
+    n = 9
+    G = I.local_gates_packed(n)
+    th = rng.normal(G.shape[0], 1) * 0.5
+    A = I.bernoulli_bits(rng, 12, n, 0.5, 2, nonzero=True)
+    w = rng.normal(12, 3)
+    g = oracle.bitflip_grad(n, G, A, th, w)
+    fd = _fd(lambda t: float(np.dot(w, oracle.bitflip_expval(n, G, A, t))), th)
+    assert np.linalg.norm(g - fd) / np.linalg.norm(fd) < 1e-8
+
+
+def test_bitflip_model_is_the_ancilla_iqp_circuit():
+    """Sec. 2.5: the bitflip circuit equals the IQP circuit on n + m qubits
+    whose gate j also acts on its own ancilla n + j, observed on the first n
+    qubits; its exact expectation (enumeration over all 2^(n+m) samples) is
+    the product form."""
+    rng = I.Rng(46)
+    n, m = 4, 6
+    gates = [list(np.nonzero(b)[0]) for b in (rng.uniform(m * n, 1).reshape(m, n) < 0.5)]
+    gates = [g if g else [0] for g in gates]
+    th = rng.normal(m, 2) * 0.7
+    A = I.bernoulli_bits(rng, 10, n, 0.5, 3)
+    G = I.pack_index_lists(gates, n)
+    G_anc = I.pack_index_lists([g + [n + j] for j, g in enumerate(gates)], n + m)
+    A_anc = I.pack_bits(np.concatenate([I.unpack_bits(A, n), np.zeros((10, m), np.uint8)], axis=1))
+    exact = oracle.exact_expval(n + m, G_anc, A_anc, th)
+    assert np.max(np.abs(exact - oracle.bitflip_expval(n, G, A, th))) < 1e-12
+
+
 # ---------------------------------------------------------------------- MMD
 
 def test_mmd_kernel_identity():
