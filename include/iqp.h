@@ -62,7 +62,8 @@ typedef enum {
     IQP_OP_EXPVAL = 1,
     IQP_OP_EXPVAL_GRAD = 2,
     IQP_OP_MMD_LOSS = 3,
-    IQP_OP_MMD_LOSS_GRAD = 4
+    IQP_OP_MMD_LOSS_GRAD = 4,
+    IQP_OP_BITFLIP = 5   /* iqp_bitflip_expval and iqp_bitflip_grad */
 } iqp_op;
 
 /* Bytes of device scratch `ws` needed by `op` for these sizes (N is ignored
@@ -176,6 +177,23 @@ iqp_status iqp_mmd_loss_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ld
                              const float *theta, iqp_precision prec, int unbiased,
                              double *loss, double *grad, void *ws, size_t ws_bytes, void *stream);
 
+/* Stochastic bitflip circuit (Sec. 2.5): every gate, instead of acting
+ * coherently, flips the bits of g_j with probability sin^2(theta_j). Its
+ * expectation values are exact products (eq. expval_bitflip), no sampling:
+ *   expval[a] = prod_{j : g_j.a odd} cos(2 theta_j).
+ * FP64. ws: iqp_workspace_bytes(IQP_OP_BITFLIP, n, m, l, 1, 0, prec). */
+iqp_status iqp_bitflip_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                              const uint64_t *A, int64_t l, int64_t lda, const float *theta,
+                              double *expval, void *ws, size_t ws_bytes, void *stream);
+
+/* Gradient of L = sum_a w[a] expval[a] for the bitflip circuit:
+ *   grad[j] = -2 tan(2 theta_j) sum_{a : g_j.a odd} w[a] expval[a].
+ * w: float64[l] on the device (e.g. dL/d expval). grad: float64[m]. FP64.
+ * Same workspace as iqp_bitflip_expval. */
+iqp_status iqp_bitflip_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                            const uint64_t *A, int64_t l, int64_t lda, const float *theta,
+                            const double *w, double *grad, void *ws, size_t ws_bytes, void *stream);
+
 /* Device-side status of the last calls that used `ws`: synchronises
  * `stream`, returns IQP_OK or the first error a kernel recorded (e.g.
  * IQP_ERR_TIMEOUT), and clears it. */
@@ -201,7 +219,8 @@ typedef enum {
     IQP_KERNEL_GRAD_REDUCE = 10,   /* fixed-order reduction of gradient parts   */
     IQP_KERNEL_MMD_COMBINE = 11,   /* MMD^2 terms and gradient coefficients     */
     IQP_KERNEL_SELFTEST = 12,      /* iqp_selftest_timeout                      */
-    IQP_KERNEL_COUNT = 13
+    IQP_KERNEL_BITFLIP = 13,       /* bitflip products and gradient sums        */
+    IQP_KERNEL_COUNT = 14
 } iqp_kernel;
 
 /* Per-kernel timing (off by default). When enabled, every launch is

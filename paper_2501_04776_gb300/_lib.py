@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libiqp_gb300.so")
 
 OK, ERR_ARG, ERR_ALIGN, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 FP32, SPLIT_BF16 = 0, 1
-OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD = 1, 2, 3, 4
+OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP = 1, 2, 3, 4, 5
 
 # Every symbol include/iqp.h declares, with (restype, argtypes).
 _i64, _p, _int, _sz, _dbl = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
@@ -28,6 +28,8 @@ SIGNATURES = {
     "iqp_expval_grad": (_int, [_i64] + _MAT * 3 + [_p, _p, _p, _int, _p, _p, _sz, _p]),
     "iqp_mmd_loss": (_int, [_i64] + _MAT * 4 + [_p, _int, _int, _p, _p, _sz, _p]),
     "iqp_mmd_loss_grad": (_int, [_i64] + _MAT * 4 + [_p, _int, _int, _p, _p, _p, _sz, _p]),
+    "iqp_bitflip_expval": (_int, [_i64] + _MAT * 2 + [_p, _p, _p, _sz, _p]),
+    "iqp_bitflip_grad": (_int, [_i64] + _MAT * 2 + [_p, _p, _p, _p, _sz, _p]),
     "iqp_read_status": (_int, [_p, _sz, _p]),
     "iqp_selftest_timeout": (_int, [_p, _sz, _dbl, _p]),
     "iqp_status_string": (ctypes.c_char_p, [_int]),
@@ -39,7 +41,7 @@ SIGNATURES = {
 }
 
 KERNELS = ["parity", "parity_sum", "theta_split", "phase_fp32", "recompute_fp32", "grad_fp32", "phase_tc",
-           "recompute_tc", "grad_tc", "finalize", "grad_reduce", "mmd_combine", "selftest"]
+           "recompute_tc", "grad_tc", "finalize", "grad_reduce", "mmd_combine", "selftest", "bitflip"]
 
 _lib = None
 

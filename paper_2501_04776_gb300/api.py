@@ -14,7 +14,7 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import FP32, SPLIT_BF16, OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, check
+from ._lib import FP32, SPLIT_BF16, OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP, check
 
 _PRECISIONS = {"fp32": FP32, "split_bf16": SPLIT_BF16, FP32: FP32, SPLIT_BF16: SPLIT_BF16}
 
@@ -211,6 +211,53 @@ def mmd_loss(theta, G, A, Z, X, n: int, precision="split_bf16", unbiased=True):
     and its gradient come from one library call (the backward recomputes Phi
     tile by tile inside it)."""
     return _MmdFn.apply(theta, G, A, Z, X, n, precision, unbiased)
+
+
+def bitflip_expval_raw(n, theta, G, A):
+    """Exact <Z_a> of the stochastic bitflip circuit (float64), no autograd."""
+    _bits(G, "G"), _bits(A, "A")
+    th = _theta32(theta)
+    m, l = G.shape[0], A.shape[0]
+    lib = _lib.load()
+    ws = _WS.get(lib.iqp_workspace_bytes(OP_BITFLIP, n, m, l, 1, 0, FP32), G.device)
+    ev = torch.empty(l, dtype=torch.float64, device=G.device)
+    check(lib.iqp_bitflip_expval(n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(th), _ptr(ev), _ptr(ws),
+                                 ws.numel(), ctypes.c_void_p(_stream(G.device))), "iqp_bitflip_expval")
+    return ev
+
+
+def bitflip_grad(n, theta, G, A, w) -> torch.Tensor:
+    """d/dtheta of sum_a w_a <Z_a> for the bitflip circuit (float64)."""
+    _bits(G, "G"), _bits(A, "A")
+    th = _theta32(theta)
+    m, l = G.shape[0], A.shape[0]
+    wd = w.detach().to(device=G.device, dtype=torch.float64).contiguous()
+    lib = _lib.load()
+    ws = _WS.get(lib.iqp_workspace_bytes(OP_BITFLIP, n, m, l, 1, 0, FP32), G.device)
+    grad = torch.empty(m, dtype=torch.float64, device=G.device)
+    check(lib.iqp_bitflip_grad(n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(th), _ptr(wd), _ptr(grad),
+                               _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(G.device))), "iqp_bitflip_grad")
+    return grad
+
+
+class _BitflipFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, G, A, n):
+        ev = bitflip_expval_raw(n, theta, G, A)
+        ctx.save_for_backward(theta, G, A)
+        ctx.n = n
+        return ev
+
+    @staticmethod
+    def backward(ctx, g):
+        theta, G, A = ctx.saved_tensors
+        return bitflip_grad(ctx.n, theta, G, A, g).to(theta.dtype), None, None, None
+
+
+def bitflip_expval(theta, G, A, n: int):
+    """Exact expectation values of the stochastic bitflip circuit (Sec. 2.5),
+    differentiable in theta."""
+    return _BitflipFn.apply(theta, G, A, n)
 
 
 def read_status(device=None) -> int:

@@ -36,6 +36,11 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
                             cudaStream_t st, iqp_status *why);
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why);
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st);
+cudaError_t launch_bitflip_gates(const float *theta, int64_t m, int64_t mpad, double *c, double *t, cudaStream_t st);
+cudaError_t launch_bitflip_rows(const uint64_t *PA, int64_t ldp, int64_t l, const double *c, double *expval,
+                                cudaStream_t st);
+cudaError_t launch_bitflip_grad(const uint64_t *PAT, int64_t ldlt, int64_t m, int64_t l, const double *w,
+                                const double *ev, double *v, const double *t, double *grad, cudaStream_t st);
 
 // ---------------------------------------------------------------- plan
 
@@ -60,6 +65,7 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     const bool grad = op == IQP_OP_EXPVAL_GRAD || op == IQP_OP_MMD_LOSS_GRAD;
     const bool mmd = op == IQP_OP_MMD_LOSS || op == IQP_OP_MMD_LOSS_GRAD;
     const bool tc = prec == IQP_SPLIT_BF16;
+    const bool bitflip = op == IQP_OP_BITFLIP;
     size_t off = 0;
     auto take = [&](int64_t bytes) {
         const size_t o = off;
@@ -68,12 +74,12 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     };
     p.off_status = take(256);
     p.off_pa = take(l * p.ldp * 8);
-    p.off_pz = take(s * p.ldp * 8);
-    p.off_pzt = take(m * p.ldzt * 8);
+    p.off_pz = take(bitflip ? 0 : s * p.ldp * 8);
+    p.off_pzt = take(bitflip ? 0 : m * p.ldzt * 8);
     p.off_pat = take(m * p.ldlt * 8);
     p.off_rt = take(n * (p.ldzt > p.ldlt ? p.ldzt : p.ldlt) * 8);
-    p.off_c = take(tc ? p.mpad * 4 : p.mpad * 4);
-    p.off_part = take(l * p.nparts * 16);
+    p.off_c = take(bitflip ? p.mpad * 16 : p.mpad * 4);  // bitflip: cos(2 theta), -2 tan(2 theta) in FP64
+    p.off_part = take(bitflip ? l * 16 : l * p.nparts * 16);  // bitflip: expval, w * expval
     p.off_w = take(grad ? (tc ? l * p.ldw * 4 : l * p.ldw * 4) : 0);
     p.off_gpart = take(grad ? p.natile * m * 8 : 0);
     p.off_ab = take(mmd ? l * 16 : 0);
@@ -289,7 +295,7 @@ extern "C" {
 
 size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, iqp_precision prec) {
     if (n < 1 || m < 1 || l < 1 || s < 1) return 0;
-    if (op < IQP_OP_EXPVAL || op > IQP_OP_MMD_LOSS_GRAD) return 0;
+    if (op < IQP_OP_EXPVAL || op > IQP_OP_BITFLIP) return 0;
     if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16) return 0;
     return make_plan(op, n, m, l, s, N, prec).total;
 }
@@ -374,6 +380,51 @@ iqp_status iqp_mmd_loss_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ld
                              double *grad, void *ws, size_t ws_bytes, void *stream) {
     return mmd_core(IQP_OP_MMD_LOSS_GRAD, n, G, m, ldg, A, l, lda, Z, s, ldz, X, N, ldx, theta, prec, unbiased, loss,
                     grad, ws, ws_bytes, stream);
+}
+
+namespace {
+
+iqp_status bitflip_core(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                        int64_t lda, const float *theta, double *expval, const double *w, double *grad, void *ws,
+                        size_t ws_bytes, void *stream) {
+    if (n < 1 || m < 1 || l < 1) return IQP_ERR_ARG;
+    if (m > (int64_t)1 << 36 || l > (int64_t)1 << 31) return IQP_ERR_ARG;
+    iqp_status rc;
+    if ((rc = check_bits(G, m, ldg, n)) != IQP_OK) return rc;
+    if ((rc = check_bits(A, l, lda, n)) != IQP_OK) return rc;
+    if (theta == nullptr) return IQP_ERR_ARG;
+    if (!aligned(theta, 4)) return IQP_ERR_ALIGN;
+    if ((expval && !aligned(expval, 8)) || (w && !aligned(w, 8)) || (grad && !aligned(grad, 8))) return IQP_ERR_ALIGN;
+    const Plan p = make_plan(IQP_OP_BITFLIP, n, m, l, 1, 0, IQP_FP32);
+    if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    IQP_TRY(launch_parity_gather(n, A, l, lda, G, m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
+                                 at<uint64_t>(ws, p.off_pat), p.ldlt, at<uint64_t>(ws, p.off_rt), st));
+    double *c = at<double>(ws, p.off_c), *t = c + p.mpad;
+    IQP_TRY(launch_bitflip_gates(theta, m, p.mpad, c, t, st));
+    double *ev = expval ? expval : at<double>(ws, p.off_part);
+    IQP_TRY(launch_bitflip_rows(at<uint64_t>(ws, p.off_pa), p.ldp, l, c, ev, st));
+    if (grad != nullptr) {
+        double *v = at<double>(ws, p.off_part) + l;
+        IQP_TRY(launch_bitflip_grad(at<uint64_t>(ws, p.off_pat), p.ldlt, m, l, w, ev, v, t, grad, st));
+    }
+    return IQP_OK;
+}
+
+}  // namespace
+
+iqp_status iqp_bitflip_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                              int64_t lda, const float *theta, double *expval, void *ws, size_t ws_bytes,
+                              void *stream) {
+    if (expval == nullptr) return IQP_ERR_ARG;
+    return bitflip_core(n, G, m, ldg, A, l, lda, theta, expval, nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+iqp_status iqp_bitflip_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                            int64_t lda, const float *theta, const double *w, double *grad, void *ws,
+                            size_t ws_bytes, void *stream) {
+    if (w == nullptr || grad == nullptr) return IQP_ERR_ARG;
+    return bitflip_core(n, G, m, ldg, A, l, lda, theta, nullptr, w, grad, ws, ws_bytes, stream);
 }
 
 iqp_status iqp_read_status(void *ws, size_t ws_bytes, void *stream) {

@@ -480,3 +480,36 @@ print(json.dumps({"ev": float(np.max(np.abs(ev.cpu().numpy() - wev))), "se": flo
     r = json.loads(out.stdout.strip().splitlines()[-1])
     assert r["status"] == 0
     assert r["ev"] <= TOL["split_bf16"] and r["se"] <= TOL["split_bf16"] and r["g"] <= GRAD_RTOL
+
+
+# --------------------------------------------------------- bitflip circuits
+
+@pytest.mark.parametrize("n,m,l", [(8, 36, 64), (130, 1000, 300), (1000, 100_000, 257)])
+def test_bitflip_expval_and_grad(api, n, m, l):
+    """Stochastic bitflip circuit (Sec. 2.5): exact products and their
+    gradient in FP64 against the oracle's product form / product rule."""
+    import torch
+    rng = I.Rng(60 + n)
+    G = I.local_gates_packed(n) if n == 8 else I.random_k_body(rng, m, n, [1, 2, 3], 1)
+    # angles small enough that the products over |J_a| ~ 0.1 m factors stay O(1)
+    scale = {8: 0.15, 130: 0.1, 1000: 0.01}[n]
+    th = (scale * rng.normal(G.shape[0], 2)).astype(np.float32)
+    A = I.bernoulli_bits(rng, l, n, 0.5 if n == 8 else 0.05, 3)
+    if n >= 1000:  # oracle on a subsample of observables: the gradient is linear in w
+        idx = np.arange(0, l, 37)
+    else:
+        idx = np.arange(l)
+    w = np.zeros(l)
+    w[idx] = rng.normal(idx.size, 4)
+    theta = th_dev(th).requires_grad_(True)
+    ev = api.bitflip_expval(theta, dev(api, G), dev(api, A), n)
+    (ev * torch.from_numpy(w).cuda()).sum().backward()
+    want = oracle.bitflip_expval(n, G, A[idx], th.astype(np.float64))
+    assert np.min(np.abs(want)) > 1e-3  # the check is not vacuous
+    assert np.max(np.abs(ev.detach().cpu().numpy()[idx] - want)) <= 1e-12
+    wg = oracle.bitflip_grad(n, G, A[idx], th.astype(np.float64), w[idx])
+    g = theta.grad.double().cpu().numpy()
+    # theta.grad is cast to theta's float32; compare the float64 result too.
+    g64 = api.bitflip_grad(n, th_dev(th), dev(api, G), dev(api, A), torch.from_numpy(w).cuda()).cpu().numpy()
+    assert rel_l2(g64, wg) <= 1e-10
+    assert rel_l2(g, wg) <= 1e-6
