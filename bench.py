@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--s", type=int, default=10_000)
     ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the plain FP32 form (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-rows", action="store_true", help="skip the bitflip and MMD per-call timings")
     ap.add_argument("--cpu-sample-l", type=int, default=128)
     ap.add_argument("--cpu-sample-s", type=int, default=10_000)
     return ap.parse_args()
@@ -209,6 +210,95 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------- the other hot-path rows
+
+def _kernel_times(lib):
+    from paper_2501_04776_gb300 import _lib
+    kt = {}
+    for k, name in enumerate(_lib.KERNELS):
+        tot, cnt = ctypes.c_double(0), ctypes.c_uint64(0)
+        lib.iqp_profile_query(k, ctypes.byref(tot), ctypes.byref(cnt))
+        if cnt.value:
+            kt[name] = {"launches": int(cnt.value), "total_ms": round(tot.value, 4),
+                        "avg_ms": round(tot.value / cnt.value, 4)}
+    return kt
+
+
+def other_rows(args, lib, dev, st, timed, peaks, G, A, theta, w, n, m, l):
+    """Per-call timings of the paths beside the headline step, each on its
+    own workload: the bitflip circuit on the headline's G, A, theta, and one
+    MMD^2 loss + gradient call of the MMD training workload."""
+    import torch
+    from paper_2501_04776_gb300 import _lib
+    P = ctypes.c_void_p
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    out = {}
+
+    # Stochastic bitflip circuit: exact products and their gradient (FP64).
+    ws = torch.empty(lib.iqp_workspace_bytes(_lib.OP_BITFLIP, n, m, l, 1, 0, _lib.FP32), dtype=torch.uint8,
+                     device=dev)
+    ev = torch.empty(l, dtype=torch.float64, device=dev)
+    gr = torch.empty(m, dtype=torch.float64, device=dev)
+    wd = torch.from_numpy(np.ascontiguousarray(w, dtype=np.float64)).to(dev)
+
+    def bitflip():
+        _lib.check(lib.iqp_bitflip_expval(n, P(G.data_ptr()), m, G.shape[1], P(A.data_ptr()), l, A.shape[1],
+                                          P(theta.data_ptr()), P(ev.data_ptr()), P(ws.data_ptr()), ws.numel(), st),
+                   "iqp_bitflip_expval")
+        _lib.check(lib.iqp_bitflip_grad(n, P(G.data_ptr()), m, G.shape[1], P(A.data_ptr()), l, A.shape[1],
+                                        P(theta.data_ptr()), P(wd.data_ptr()), P(gr.data_ptr()), P(ws.data_ptr()),
+                                        ws.numel(), st), "iqp_bitflip_grad")
+
+    lib.iqp_profile_reset()
+    ms, _ = timed(None, args.steps, args.warmup, profile=True, fn=bitflip)
+    kt = _kernel_times(lib)
+    ldp, ldlt = -(-m // 256) * 4, -(-l // 256) * 4
+    # Algorithmic bytes of the product / gradient-sum kernels: one read of
+    # P_A (l x ldp words) and one of P_A^T (m x ldlt words).
+    nbytes = 8.0 * (l * ldp + m * ldlt)
+    bf_ms = kt.get("bitflip", {}).get("total_ms", 0.0) / max(1, args.steps)
+    out["bitflip_fwd_grad"] = {
+        "workload": f"bitflip circuit, n={n} m={m} l={l} (the headline's G, A, theta), FP64",
+        "ms_per_call_pair": round(statistics.mean(ms), 3), "kernels": kt,
+        "roofline": {"bound": "hbm", "kernel": "bitflip", "achieved": round(nbytes / (bf_ms * 1e-3) / 1e9, 1)
+                     if bf_ms else None, "peak": hbm, "unit": "GB/s",
+                     "frac": round(nbytes / (bf_ms * 1e-3) / 1e9 / hbm, 4) if bf_ms else None,
+                     "bytes_per_step": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
+    del ws
+
+    # MMD^2 loss and gradient, one training step's call (unbiased form).
+    p = I.mmd_training()
+    Gm, Am, Zm, Xm = (torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).to(dev)
+                      for x in (p.G, p.A, p.Z, p.X))
+    thm = torch.from_numpy(p.theta).to(dev)
+    mm, lm, sm, Nm = p.G.shape[0], p.A.shape[0], p.Z.shape[0], p.X.shape[0]
+    ws = torch.empty(lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD, p.n, mm, lm, sm, Nm, _lib.SPLIT_BF16),
+                     dtype=torch.uint8, device=dev)
+    loss = torch.empty(1, dtype=torch.float64, device=dev)
+    gm = torch.empty(mm, dtype=torch.float64, device=dev)
+
+    def mmd():
+        _lib.check(lib.iqp_mmd_loss_grad(p.n, P(Gm.data_ptr()), mm, Gm.shape[1], P(Am.data_ptr()), lm, Am.shape[1],
+                                         P(Zm.data_ptr()), sm, Zm.shape[1], P(Xm.data_ptr()), Nm, Xm.shape[1],
+                                         P(thm.data_ptr()), _lib.SPLIT_BF16, 1, P(loss.data_ptr()),
+                                         P(gm.data_ptr()), P(ws.data_ptr()), ws.numel(), st), "iqp_mmd_loss_grad")
+
+    lib.iqp_profile_reset()
+    ms, _ = timed(None, args.steps, args.warmup, profile=True, fn=mmd)
+    kt = _kernel_times(lib)
+    dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
+    executed = 4.0 * lm * sm * mm
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    ach = executed / (kt[dom]["avg_ms"] * 1e-3) / 1e12
+    out["mmd_loss_grad"] = {
+        "workload": f"MMD^2 loss + grad, n={p.n} m={mm} (all 1- and 2-body) l={lm} s={sm} N={Nm}, split-BF16",
+        "ms_per_call": round(statistics.mean(ms), 3), "kernels": kt,
+        "roofline": {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": peak,
+                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "flops_per_launch": executed,
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}}
+    return out
+
+
 # ---------------------------------------------------------------- GPU arm
 
 def main():
@@ -260,9 +350,10 @@ def main():
                                        precision, P(gd.data_ptr()), P(ws.data_ptr()), ws.numel(), st),
                    "iqp_expval_grad")
 
-    def timed(precision, k, warm, profile=False):
+    def timed(precision, k, warm, profile=False, fn=None):
+        fn = fn or (lambda: step(precision))
         for _ in range(warm):
-            step(precision)
+            fn()
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -276,7 +367,7 @@ def main():
             flush.zero_()  # L2 flush between steps, outside the step's events
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(precision)
+            fn()
             e1.record(stream)
             evs.append((e0, e1))
         torch.cuda.synchronize()
@@ -382,6 +473,8 @@ def main():
     }
     if fp32 is not None:
         line["fp32_form"] = fp32
+    if not args.no_rows and prec == _lib.SPLIT_BF16:
+        line["rows"] = other_rows(args, lib, dev, st, timed, peaks, G, A, theta, w, n, m, l)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def gpu_grad_fn(alpha_np):
             al = torch.from_numpy(alpha_np).to(dev)
