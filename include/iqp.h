@@ -54,8 +54,13 @@ typedef enum {
  * IQP_FP32: FP32 FMA on the SIMT cores (the plain form).
  * IQP_SPLIT_BF16: tcgen05 tensor cores; 2 theta is split into hi + lo BF16
  * parts (hi = RN_bf16(2 theta), lo = RN_bf16(2 theta - hi)), the +-1 and 0/1
- * operands are exact in BF16, and both products accumulate in FP32 in TMEM. */
-typedef enum { IQP_FP32 = 0, IQP_SPLIT_BF16 = 1 } iqp_precision;
+ * operands are exact in BF16, and both products accumulate in FP32 in TMEM.
+ * IQP_SPARSE_FP32: row-sparse FP32 form on the SIMT cores: for each
+ * observable only the gates with [g_j.a odd] are visited, so the work is
+ * nnz(P_A) * s instead of l * m * s; the choice when P_A is sparse (density
+ * below a few percent, e.g. low-weight observables drawn with small p_sigma).
+ * Same tolerances as IQP_FP32; its gradient is bitwise reproducible. */
+typedef enum { IQP_FP32 = 0, IQP_SPLIT_BF16 = 1, IQP_SPARSE_FP32 = 2 } iqp_precision;
 
 /* Operation whose scratch iqp_workspace_bytes() sizes. */
 typedef enum {
@@ -220,7 +225,9 @@ typedef enum {
     IQP_KERNEL_MMD_COMBINE = 11,   /* MMD^2 terms and gradient coefficients     */
     IQP_KERNEL_SELFTEST = 12,      /* iqp_selftest_timeout                      */
     IQP_KERNEL_BITFLIP = 13,       /* bitflip products and gradient sums        */
-    IQP_KERNEL_COUNT = 14
+    IQP_KERNEL_PHASE_SPARSE = 14,  /* row-sparse phase + statistics             */
+    IQP_KERNEL_GRAD_SPARSE = 15,   /* row-sparse recompute + gradient           */
+    IQP_KERNEL_COUNT = 16
 } iqp_kernel;
 
 /* Per-kernel timing (off by default). When enabled, every launch is

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libiqp_gb300.so")
 
 OK, ERR_ARG, ERR_ALIGN, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
-FP32, SPLIT_BF16 = 0, 1
+FP32, SPLIT_BF16, SPARSE_FP32 = 0, 1, 2
 OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP = 1, 2, 3, 4, 5
 
 # Every symbol include/iqp.h declares, with (restype, argtypes).
@@ -41,7 +41,8 @@ SIGNATURES = {
 }
 
 KERNELS = ["parity", "parity_sum", "theta_split", "phase_fp32", "recompute_fp32", "grad_fp32", "phase_tc",
-           "recompute_tc", "grad_tc", "finalize", "grad_reduce", "mmd_combine", "selftest", "bitflip"]
+           "recompute_tc", "grad_tc", "finalize", "grad_reduce", "mmd_combine", "selftest", "bitflip",
+           "phase_sparse", "grad_sparse"]
 
 _lib = None
 

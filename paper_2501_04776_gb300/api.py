@@ -14,16 +14,17 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import FP32, SPLIT_BF16, OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP, check
+from ._lib import FP32, SPLIT_BF16, SPARSE_FP32, OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP, check
 
-_PRECISIONS = {"fp32": FP32, "split_bf16": SPLIT_BF16, FP32: FP32, SPLIT_BF16: SPLIT_BF16}
+_PRECISIONS = {"fp32": FP32, "split_bf16": SPLIT_BF16, "sparse_fp32": SPARSE_FP32, FP32: FP32,
+               SPLIT_BF16: SPLIT_BF16, SPARSE_FP32: SPARSE_FP32}
 
 
 def precision_code(precision) -> int:
     try:
         return _PRECISIONS[precision]
     except KeyError:
-        raise ValueError(f"precision must be 'fp32' or 'split_bf16', got {precision!r}") from None
+        raise ValueError(f"precision must be 'fp32', 'split_bf16' or 'sparse_fp32', got {precision!r}") from None
 
 
 def _stream(device) -> int:

@@ -36,6 +36,13 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
                             cudaStream_t st, iqp_status *why);
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why);
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st);
+int64_t sparse_part_samples();
+cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
+                                int64_t l, int64_t s, double2 *part, int64_t nparts, cudaStream_t st);
+cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
+                               int64_t l, int64_t s, int64_t m, int64_t nparts, const double *alpha,
+                               const double *beta, double *scale, unsigned long long *gfx, double *grad,
+                               cudaStream_t st);
 cudaError_t launch_bitflip_gates(const float *theta, int64_t m, int64_t mpad, double *c, double *t, cudaStream_t st);
 cudaError_t launch_bitflip_rows(const uint64_t *PA, int64_t ldp, int64_t l, const double *c, double *expval,
                                 cudaStream_t st);
@@ -59,13 +66,14 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.ldlt = round_up(cdiv(l, 64), 4);
     p.mpad = p.ldp * 64;
     p.ldw = round_up(s, 64);
-    p.pw = prec == IQP_SPLIT_BF16 ? kPartColsTc : kPartColsSimt;
+    p.pw = prec == IQP_SPLIT_BF16 ? kPartColsTc : (prec == IQP_SPARSE_FP32 ? sparse_part_samples() : kPartColsSimt);
     p.nparts = cdiv(s, p.pw);
     p.natile = cdiv(l, kATile);
     const bool grad = op == IQP_OP_EXPVAL_GRAD || op == IQP_OP_MMD_LOSS_GRAD;
     const bool mmd = op == IQP_OP_MMD_LOSS || op == IQP_OP_MMD_LOSS_GRAD;
     const bool tc = prec == IQP_SPLIT_BF16;
     const bool bitflip = op == IQP_OP_BITFLIP;
+    const bool sparse = prec == IQP_SPARSE_FP32 && !bitflip;
     size_t off = 0;
     auto take = [&](int64_t bytes) {
         const size_t o = off;
@@ -74,14 +82,15 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     };
     p.off_status = take(256);
     p.off_pa = take(l * p.ldp * 8);
-    p.off_pz = take(bitflip ? 0 : s * p.ldp * 8);
+    p.off_pz = take(bitflip || sparse ? 0 : s * p.ldp * 8);
     p.off_pzt = take(bitflip ? 0 : m * p.ldzt * 8);
     p.off_pat = take(m * p.ldlt * 8);
     p.off_rt = take(n * (p.ldzt > p.ldlt ? p.ldzt : p.ldlt) * 8);
     p.off_c = take(bitflip ? p.mpad * 16 : p.mpad * 4);  // bitflip: cos(2 theta), -2 tan(2 theta) in FP64
     p.off_part = take(bitflip ? l * 16 : l * p.nparts * 16);  // bitflip: expval, w * expval
-    p.off_w = take(grad ? (tc ? l * p.ldw * 4 : l * p.ldw * 4) : 0);
-    p.off_gpart = take(grad ? p.natile * m * 8 : 0);
+    p.off_w = take(grad && !sparse ? l * p.ldw * 4 : 0);
+    // sparse: 64-bit fixed-point gradient accumulators and their scale
+    p.off_gpart = take(grad ? (sparse ? m * 8 + 8 : p.natile * m * 8) : 0);
     p.off_ab = take(mmd ? l * 16 : 0);
     p.off_s12 = take(mmd ? l * 16 : 0);
     p.off_T = take(mmd ? l * 8 : 0);
@@ -175,8 +184,10 @@ iqp_status check_common(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, co
     if ((st = check_bits(Z, s, ldz, n)) != IQP_OK) return st;
     if (theta == nullptr) return IQP_ERR_ARG;
     if (!aligned(theta, 4)) return IQP_ERR_ALIGN;
-    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16) return IQP_ERR_ARG;
+    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32) return IQP_ERR_ARG;
     if (prec == IQP_SPLIT_BF16 && !iqp_tensor_path_available()) return IQP_ERR_UNSUPPORTED;
+    // sparse grid: observables on x (< 2^31), blocks of 8 x 2048 samples on y (< 65536)
+    if (prec == IQP_SPARSE_FP32 && (l > INT32_MAX || cdiv(s, (int64_t)8 * 2048) > 65535)) return IQP_ERR_ARG;
     return IQP_OK;
 }
 
@@ -203,7 +214,9 @@ iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, cons
     uint64_t *rt = at<uint64_t>(ws, p.off_rt);
     IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
                                  at<uint64_t>(ws, p.off_pat), p.ldlt, rt, st));
-    IQP_TRY(launch_parity_gather(p.n, Z, p.s, ldz, G, p.m, ldg, at<uint64_t>(ws, p.off_pz), p.ldp,
+    // The sparse form reads only P_Z^T (bits over samples).
+    IQP_TRY(launch_parity_gather(p.n, Z, p.s, ldz, G, p.m, ldg,
+                                 p.prec == IQP_SPARSE_FP32 ? nullptr : at<uint64_t>(ws, p.off_pz), p.ldp,
                                  at<uint64_t>(ws, p.off_pzt), p.ldzt, rt, st));
     if (p.prec == IQP_SPLIT_BF16) {
         __nv_bfloat16 *hi = at<__nv_bfloat16>(ws, p.off_c);
@@ -222,6 +235,9 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
         iqp_status why = IQP_OK;
         if (launch_phase_tc(0, p, ws, nullptr, nullptr, st, &why) != cudaSuccess)
             return why != IQP_OK ? why : IQP_ERR_CUDA;
+    } else if (p.prec == IQP_SPARSE_FP32) {
+        IQP_TRY(launch_sparse_stats(at<uint64_t>(ws, p.off_pa), p.ldp, at<uint64_t>(ws, p.off_pzt), p.ldzt,
+                                    at<float>(ws, p.off_c), p.l, p.s, part, p.nparts, st));
     } else {
         IQP_TRY(launch_phase_simt(0, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pz), p.ldp,
                                   at<float>(ws, p.off_c), p.l, p.s, p.m, part, p.nparts, nullptr, nullptr, nullptr, 0,
@@ -235,6 +251,13 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
 iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *beta, double *grad,
                     cudaStream_t st) {
     double *gpart = at<double>(ws, p.off_gpart);
+    if (p.prec == IQP_SPARSE_FP32) {
+        unsigned long long *gfx = at<unsigned long long>(ws, p.off_gpart);
+        IQP_TRY(launch_sparse_grad(at<uint64_t>(ws, p.off_pa), p.ldp, at<uint64_t>(ws, p.off_pzt), p.ldzt,
+                                   at<float>(ws, p.off_c), p.l, p.s, p.m, p.nparts, alpha, beta,
+                                   reinterpret_cast<double *>(gfx + p.m), gfx, grad, st));
+        return IQP_OK;
+    }
     if (p.prec == IQP_SPLIT_BF16) {
         iqp_status why = IQP_OK;
         if (launch_phase_tc(1, p, ws, alpha, beta, st, &why) != cudaSuccess) return why != IQP_OK ? why : IQP_ERR_CUDA;
@@ -296,7 +319,7 @@ extern "C" {
 size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, iqp_precision prec) {
     if (n < 1 || m < 1 || l < 1 || s < 1) return 0;
     if (op < IQP_OP_EXPVAL || op > IQP_OP_BITFLIP) return 0;
-    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16) return 0;
+    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32) return 0;
     return make_plan(op, n, m, l, s, N, prec).total;
 }
 

@@ -1,0 +1,260 @@
+// Row-sparse form of the phase contraction and of its gradient, for parity
+// matrices P_A of low density (Sec. 2.2 notes that C = 1 - (-1)^{A G^T} is
+// sparse when observables and generators have small support).
+//
+// For one observable a, with J_a = { j : P_A[a][j] = 1 } and c_j = 2 theta_j,
+//   Phi[a][i] = sum_{j in J_a} c_j (1 - 2 P_Z[i][j])          (eq. Emat)
+// and, for W[a][i] = sin Phi (alpha_a + beta_a cos Phi),
+//   grad_j    = sum_{a : j in J_a} 2 sum_i W[a][i] (1 - 2 P_Z[i][j]).
+// The work is |J_a| * s per observable instead of m * s: the dense forms
+// multiply every zero of P_A too.
+//
+// Layout: one CTA per (observable, block of up to 8 x 2048 samples). Lane q of
+// warp r owns the 64 samples of word (32 r + q) of every P_Z^T row, so the
+// P_Z^T word of a gate is one coalesced 256-byte load per warp and each term
+// is a sign flip and an add in FP32 (no multiply: the operand is +-c_j). The
+// set bits of the P_A row are visited in increasing gate order by every warp
+// of the CTA (32 words per coalesced load), with the next gate's P_Z^T word
+// loaded before the current one is consumed.
+//
+// Statistics: per-warp (sum cos, sum (cos - mean)^2) partials of 2048 samples
+// (FP32 within a lane, FP64 across lanes), merged by the shared finaliser.
+// Gradient: the per-warp dot products are added into a 64-bit fixed-point
+// accumulator per gate with integer atomics. Integer addition is associative,
+// so the result does not depend on the order of the atomics: the gradient is
+// bitwise reproducible. The fixed-point scale 2^k is chosen per call from the
+// bound B = sum_a 2 s (|alpha_a| + |beta_a|) >= |every partial sum| so that
+// B 2^k < 2^62: nothing can overflow, and the rounding error per gate is at
+// most (number of contributions) * 2^-k / 2.
+#include "common.cuh"
+
+namespace iqp {
+
+namespace {
+
+constexpr int kWarpSamples = 32 * 64;
+constexpr int kMaxWarps = 8;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// acc[k] += (bit k of z ? -c : c), bit k = sample 64 w + k of the lane's word.
+__device__ __forceinline__ void add_signed(float (&acc)[64], uint64_t z, uint32_t cb) {
+    const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[k] += __uint_as_float(cb ^ ((lo << (31 - k)) & 0x80000000u));
+#pragma unroll
+    for (int k = 0; k < 32; ++k) acc[32 + k] += __uint_as_float(cb ^ ((hi << (31 - k)) & 0x80000000u));
+}
+
+// sum_k (bit k of z ? -w_k : w_k), in 8 interleaved partial sums.
+__device__ __forceinline__ float signed_dot(const float (&w)[64], uint64_t z) {
+    const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
+    float p[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) p[t] = 0.f;
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+        p[k & 7] += __uint_as_float(__float_as_uint(w[k]) ^ ((lo << (31 - k)) & 0x80000000u));
+#pragma unroll
+    for (int k = 0; k < 32; ++k)
+        p[k & 7] += __uint_as_float(__float_as_uint(w[32 + k]) ^ ((hi << (31 - k)) & 0x80000000u));
+    return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+}
+
+// Calls fn(j) for every set bit j of the P_A row, in increasing j, with the
+// same j on all lanes of the warp.
+template <class F>
+__device__ __forceinline__ void for_each_gate(const uint64_t *__restrict__ row, int64_t ldp, int lane, F &fn) {
+    uint64_t next = lane < ldp ? __ldg(row + lane) : 0ull;
+    for (int64_t w0 = 0; w0 < ldp; w0 += 32) {
+        const uint64_t bits = next;
+        next = (w0 + 32 + lane < ldp) ? __ldg(row + w0 + 32 + lane) : 0ull;
+        uint32_t live = __ballot_sync(kFull, bits != 0ull);
+        while (live) {
+            const int src = __ffs(live) - 1;
+            live &= live - 1u;
+            uint64_t wb = __shfl_sync(kFull, bits, src);
+            const int64_t jb = (w0 + src) * 64;
+            while (wb) {
+                const int b = __ffsll((long long)wb) - 1;
+                wb &= wb - 1ull;
+                fn(jb + b);
+            }
+        }
+    }
+}
+
+// Phi for the lane's 64 samples (sum over J_a, increasing j).
+__device__ __forceinline__ void phase_row(float (&acc)[64], const uint64_t *__restrict__ parow, int64_t ldp,
+                                          const uint64_t *__restrict__ PZT, int64_t ldzt, int64_t word,
+                                          const float *__restrict__ c, int lane) {
+#pragma unroll
+    for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+    uint64_t zp = 0ull;
+    uint32_t cp = 0u;
+    bool have = false;
+    auto visit = [&](int64_t j) {
+        const uint64_t zn = __ldg(PZT + j * ldzt + word);
+        const uint32_t cn = __float_as_uint(__ldg(c + j));
+        if (have) add_signed(acc, zp, cp);
+        zp = zn;
+        cp = cn;
+        have = true;
+    };
+    for_each_gate(parow, ldp, lane, visit);
+    if (have) add_signed(acc, zp, cp);
+}
+
+// MODE 0: statistics partials. MODE 1: W from the recomputed Phi, then the
+// gradient contributions of every gate of J_a.
+template <int MODE>
+__global__ void __launch_bounds__(256, 2)
+    k_sparse(const uint64_t *__restrict__ PA, int64_t ldp, const uint64_t *__restrict__ PZT, int64_t ldzt,
+             const float *__restrict__ c, int64_t s, int64_t nparts, double2 *__restrict__ part,
+             const double *__restrict__ alpha, const double *__restrict__ beta, const double *__restrict__ scale,
+             unsigned long long *__restrict__ gfx) {
+    const int lane = threadIdx.x & 31;
+    const int64_t a = blockIdx.x;
+    const int64_t r = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);  // 2048-sample range
+    if (r >= nparts) return;  // warp-uniform; no block-level barriers below
+    const int64_t vwords = cdiv(s, 64);
+    const int64_t word_raw = r * 32 + lane;
+    const bool wvalid = word_raw < vwords;
+    const int64_t word = wvalid ? word_raw : vwords - 1;  // in-bounds load, result masked
+    const int64_t i0 = word_raw * 64;
+    const int nvalid = !wvalid ? 0 : (s - i0 >= 64 ? 64 : (int)(s - i0));
+    const uint64_t *parow = PA + a * ldp;
+
+    float acc[64];
+    phase_row(acc, parow, ldp, PZT, ldzt, word, c, lane);
+
+    if (MODE == 0) {
+        float sum = 0.f;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            const float cv = k < nvalid ? cosf(acc[k]) : 0.f;
+            acc[k] = cv;
+            sum += cv;
+        }
+        double ds = (double)sum;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) ds += __shfl_xor_sync(kFull, ds, off);
+        const int64_t nr = (s - r * kWarpSamples) < kWarpSamples ? (s - r * kWarpSamples) : kWarpSamples;
+        const float mean = (float)(ds / (double)nr);
+        float m2 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            const float d = acc[k] - mean;
+            m2 += k < nvalid ? d * d : 0.f;
+        }
+        double dm = (double)m2;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) dm += __shfl_xor_sync(kFull, dm, off);
+        if (lane == 0) part[a * nparts + r] = make_double2(ds, dm);
+    } else {
+        const float al = (float)alpha[a];
+        const float be = beta ? (float)beta[a] : 0.f;
+#pragma unroll
+        for (int k = 0; k < 64; ++k) {
+            float sn, cn;
+            sincosf(acc[k], &sn, &cn);
+            acc[k] = k < nvalid ? sn * (al + be * cn) : 0.f;
+        }
+        const double sc = 2.0 * *scale;
+        uint64_t zp = 0ull;
+        int64_t jp = -1;
+        auto visit = [&](int64_t j) {
+            const uint64_t zn = __ldg(PZT + j * ldzt + word);
+            if (jp >= 0) {
+                float d = signed_dot(acc, zp);
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
+                if (lane == 0) atomicAdd(gfx + jp, (unsigned long long)__double2ll_rn(sc * (double)d));
+            }
+            zp = zn;
+            jp = j;
+        };
+        for_each_gate(parow, ldp, lane, visit);
+        if (jp >= 0) {
+            float d = signed_dot(acc, zp);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
+            if (lane == 0) atomicAdd(gfx + jp, (unsigned long long)__double2ll_rn(sc * (double)d));
+        }
+    }
+}
+
+// scale = 2^k with B 2^k < 2^62, B = sum_a 2 s (|alpha_a| + |beta_a|)
+// (fixed-order FP64 sum).
+__global__ void __launch_bounds__(256) k_sparse_scale(const double *__restrict__ alpha,
+                                                      const double *__restrict__ beta, int64_t l, int64_t s,
+                                                      double *__restrict__ scale) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t a = threadIdx.x; a < l; a += 256) acc += fabs(alpha[a]) + (beta ? fabs(beta[a]) : 0.0);
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = 128; w >= 1; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double B = 2.0 * (double)s * red[0];
+        int e = (B > 0.0 && B < 1e300) ? ilogb(B) : 0;
+        if (e < -900) e = -900;
+        *scale = ldexp(1.0, 61 - e);
+    }
+}
+
+// grad[j] = fixed-point accumulator / scale.
+__global__ void k_sparse_grad_out(const unsigned long long *__restrict__ gfx, int64_t m,
+                                  const double *__restrict__ scale, double *__restrict__ grad) {
+    const double inv = 1.0 / *scale;  // a power of two: exact
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        grad[j] = (double)(long long)gfx[j] * inv;
+}
+
+dim3 sparse_grid(int64_t l, int64_t nparts, int *threads) {
+    const int nw = nparts < kMaxWarps ? (int)nparts : kMaxWarps;
+    *threads = 32 * nw;
+    return dim3((unsigned)l, (unsigned)cdiv(nparts, nw));
+}
+
+}  // namespace
+
+int64_t sparse_part_samples() { return kWarpSamples; }
+
+cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
+                                int64_t l, int64_t s, double2 *part, int64_t nparts, cudaStream_t st) {
+    int threads = 0;
+    const dim3 grid = sparse_grid(l, nparts, &threads);
+    LaunchScope ls(IQP_KERNEL_PHASE_SPARSE, st);
+    k_sparse<0><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, nullptr, nullptr, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
+                               int64_t l, int64_t s, int64_t m, int64_t nparts, const double *alpha,
+                               const double *beta, double *scale, unsigned long long *gfx, double *grad,
+                               cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(gfx, 0, (size_t)m * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
+        k_sparse_scale<<<1, 256, 0, st>>>(alpha, beta, l, s, scale);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        int threads = 0;
+        const dim3 grid = sparse_grid(l, nparts, &threads);
+        LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
+        k_sparse<1><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, nullptr, alpha, beta, scale, gfx);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    int blocks = (int)cdiv(m, 256);
+    if (blocks > 8192) blocks = 8192;
+    LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
+    k_sparse_grad_out<<<blocks, 256, 0, st>>>(gfx, m, scale, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace iqp

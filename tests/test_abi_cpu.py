@@ -52,6 +52,14 @@ def test_workspace_bytes(lib):
     assert lib.iqp_workspace_bytes(_lib.OP_EXPVAL, 0, m, l, s, 0, _lib.FP32) == 0
     assert lib.iqp_workspace_bytes(99, n, m, l, s, 0, _lib.FP32) == 0
     assert lib.iqp_workspace_bytes(_lib.OP_EXPVAL, n, m, l, s, 0, 7) == 0
+    # Row-sparse form: no P_Z rows and no W; 8 bytes per gate of fixed-point gradient.
+    sp_f = lib.iqp_workspace_bytes(_lib.OP_EXPVAL, n, m, l, s, 0, _lib.SPARSE_FP32)
+    sp_g = lib.iqp_workspace_bytes(_lib.OP_EXPVAL_GRAD, n, m, l, s, 0, _lib.SPARSE_FP32)
+    assert 0 < sp_f < fwd and sp_f >= (l + s) * ((m + 63) // 64) * 8
+    assert sp_g - sp_f >= 8 * m and sp_g - sp_f < 8 * m + 1024
+    # Bitflip: parities of A only.
+    bf = lib.iqp_workspace_bytes(_lib.OP_BITFLIP, n, m, l, 1, 0, _lib.FP32)
+    assert 2 * l * ((m + 63) // 64) * 8 <= bf < fwd
 
 
 def _expval(lib, n=10, m=4, l=3, s=5, ldg=2, lda=2, ldz=2, G=0x10000, A=0x20000, Z=0x30000, th=0x40000,

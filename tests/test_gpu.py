@@ -18,9 +18,9 @@ from paper_2501_04776_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-5, "split_bf16": 1e-4}
+TOL = {"fp32": 1e-5, "split_bf16": 1e-4, "sparse_fp32": 1e-5}
 GRAD_RTOL = 1e-4
-PRECS = ["fp32", "split_bf16"]
+PRECS = ["fp32", "split_bf16", "sparse_fp32"]
 
 
 @pytest.fixture(scope="module")
@@ -384,8 +384,7 @@ def _oracle_grad_chunked(n, G, A, Z, th, alpha, chunk=4096):
     return g
 
 
-def _sampled_big_check(api, p, seed, nsample):
-    prec = "split_bf16"
+def _sampled_big_check(api, p, seed, nsample, prec="split_bf16"):
     ev, se = gpu_expval(api, p, prec)
     idx = np.unique(np.sort(I.Rng(seed).integers(nsample, p.l, 1)))
     A = p.A[idx]
@@ -412,13 +411,15 @@ def test_full_size_random_gates_other_widths(api, n):
     _sampled_big_check(api, I.random_gates(n=n), 31 + n, 8)
 
 
-def test_full_size_million_gates(api):
+@pytest.mark.parametrize("prec", ["split_bf16", "sparse_fp32"])
+def test_full_size_million_gates(api, prec):
     """n=5000, m=1e6 random one- and two-body gates, 4096 observables, 16384
-    samples (split-BF16, bit-packed operands only), sampled observables."""
-    _sampled_big_check(api, I.million_gates(), 41, 6)
+    samples (bit-packed operands only), sampled observables."""
+    _sampled_big_check(api, I.million_gates(), 41, 6, prec)
 
 
-def test_full_size_mmd_training_shapes(api):
+@pytest.mark.parametrize("prec", ["split_bf16", "sparse_fp32"])
+def test_full_size_mmd_training_shapes(api, prec):
     """MMD loss + gradient with the training workload's full m = 500500, n =
     1000, s = 5000, N = 10000, on a 32-observable subsample (the loss is a
     mean over observables, so a subsample is itself a valid MMD estimate)."""
@@ -429,12 +430,12 @@ def test_full_size_mmd_training_shapes(api):
     J = _relevant_gates(p.n, p.G, A)
     for unbiased in (True, False):
         loss, grad = api.mmd_loss_raw(p.n, th_dev(p.theta), dev(api, p.G), dev(api, A), dev(api, p.Z),
-                                      dev(api, p.X), "split_bf16", unbiased, with_grad=True)
+                                      dev(api, p.X), prec, unbiased, with_grad=True)
         want_loss, _, wg = oracle.mmd_loss(p.n, p.G[J], A, p.Z, p.X, p.theta.astype(np.float64)[J], unbiased,
                                            grad=True)
         want_grad = np.zeros(p.m)
         want_grad[J] = wg
-        assert abs(float(loss) - want_loss) <= TOL["split_bf16"]
+        assert abs(float(loss) - want_loss) <= TOL[prec]
         assert rel_l2(grad.cpu().numpy(), want_grad) <= GRAD_RTOL
 
 
@@ -513,3 +514,38 @@ def test_bitflip_expval_and_grad(api, n, m, l):
     g64 = api.bitflip_grad(n, th_dev(th), dev(api, G), dev(api, A), torch.from_numpy(w).cuda()).cpu().numpy()
     assert rel_l2(g64, wg) <= 1e-10
     assert rel_l2(g, wg) <= 1e-6
+
+
+# ------------------------------------------------------- row-sparse form
+
+def test_sparse_matches_dense_fp32_on_sparse_parities(api):
+    """Low-density P_A (observables of weight ~4, one- and two-body gates):
+    the row-sparse form agrees with the oracle and with the plain FP32 form,
+    including observables whose P_A row is empty (<Z_a> = 1 exactly)."""
+    p = I.mmd_training(seed=3, n=200, l=300, s=4100, N=10)
+    p.theta = (p.theta * 20).astype(np.float32)
+    p.A[:3] = 0  # a = 0: every phase is 0
+    ev, se = gpu_expval(api, p, "sparse_fp32")
+    want_ev, want_se, _, _ = oracle.expval(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64))
+    assert np.max(np.abs(ev - want_ev)) <= TOL["sparse_fp32"]
+    assert np.max(np.abs(se - want_se)) <= TOL["sparse_fp32"]
+    assert np.all(ev[:3] == 1.0) and np.all(se[:3] == 0.0)
+    ev32, _ = gpu_expval(api, p, "fp32")
+    assert np.max(np.abs(ev - ev32)) <= 2 * TOL["fp32"]
+    w = I.Rng(8).normal(p.l, 1)
+    g = gpu_grad(api, p, -w / p.s, None, "sparse_fp32")
+    want = oracle.expval_grad(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64), -w / p.s, None)
+    assert rel_l2(g, want) <= GRAD_RTOL
+
+
+def test_sparse_gradient_zero_weights_and_scale_extremes(api):
+    """alpha = beta = 0 gives an exactly zero gradient; a tiny and a large
+    weight scale give the same relative accuracy (the fixed-point scale is
+    chosen per call)."""
+    p = ragged_problem(seed=21, pa=0.02)
+    assert np.array_equal(gpu_grad(api, p, np.zeros(p.l), None, "sparse_fp32"), np.zeros(p.m))
+    w = I.Rng(9).normal(p.l, 1) / p.s
+    want = oracle.expval_grad(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64), w, None)
+    for f in (1e-30, 1.0, 1e30):
+        g = gpu_grad(api, p, w * f, None, "sparse_fp32")
+        assert rel_l2(g / f, want) <= GRAD_RTOL
