@@ -41,11 +41,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32"])
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "sparse_fp32"])
+    ap.add_argument("--workload", default="random", choices=["random", "mmd", "million"],
+                    help="random: k in 1..3 random gates (sizes from --n --m --l --s); mmd: all 1- and 2-body "
+                         "gates, p_sigma observables (--n --l --s); million: n=5000, 1e6 random 1-2-body gates")
     ap.add_argument("--n", type=int, default=1000)
     ap.add_argument("--m", type=int, default=100_000)
-    ap.add_argument("--l", type=int, default=10_000)
-    ap.add_argument("--s", type=int, default=10_000)
+    ap.add_argument("--l", type=int, default=None)
+    ap.add_argument("--s", type=int, default=None)
     ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the plain FP32 form (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the bitflip and MMD per-call timings")
@@ -55,12 +58,21 @@ def parse():
 
 
 def workload(args):
-    return I.random_gates(n=args.n, m=args.m, l=args.l, s=args.s)
+    if args.workload == "mmd":
+        return I.mmd_training(n=args.n, l=args.l or 2000, s=args.s or 5000)
+    if args.workload == "million":
+        return I.million_gates(l=args.l or 4096, s=args.s or 16384)
+    return I.random_gates(n=args.n, m=args.m, l=args.l or 10_000, s=args.s or 10_000)
 
 
-def workload_name(args):
-    return (f"random-gates n={args.n} m={args.m} (k in 1..3) l={args.l} (Bernoulli 0.05) s={args.s}, "
-            f"fwd+grad of sum_a w_a <Z_a>")
+def workload_name(args, p):
+    if args.workload == "mmd":
+        desc = f"all 1- and 2-body gates n={p.n} m={p.m}, l={p.l} observables ~ Bernoulli(p_sigma), s={p.s}"
+    elif args.workload == "million":
+        desc = f"random 1-2-body gates n={p.n} m={p.m}, l={p.l} (Bernoulli 0.01), s={p.s}"
+    else:
+        desc = f"random-gates n={p.n} m={p.m} (k in 1..3) l={p.l} (Bernoulli 0.05) s={p.s}"
+    return desc + ", fwd+grad of sum_a w_a <Z_a>"
 
 
 # ------------------------------------------------------------- CPU baseline
@@ -128,7 +140,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded splitmix64)",
-        "config": {"workload": workload_name(args), "n": p.n, "m": p.m, "l": p.l, "s": p.s,
+        "config": {"workload": workload_name(args, p), "n": p.n, "m": p.m, "l": p.l, "s": p.s,
                    "precision": "fp64 CPU oracle"},
         "cpu_baseline": base,
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -212,6 +224,16 @@ class ClockSampler:
 
 # ---------------------------------------------------- the other hot-path rows
 
+def nnz_parities(api, n, A, G):
+    """nnz(P_A) (computed on the GPU): the row-sparse form does nnz * s signed
+    additions per pass."""
+    x = api.parity(n, A, G).view(-1)
+    x = x - ((x >> 1) & 0x5555555555555555)
+    x = (x & 0x3333333333333333) + ((x >> 2) & 0x3333333333333333)
+    x = (x + (x >> 4)) & 0x0F0F0F0F0F0F0F0F
+    return int(((x * 0x0101010101010101) >> 56).sum().item())
+
+
 def _kernel_times(lib):
     from paper_2501_04776_gb300 import _lib
     kt = {}
@@ -224,12 +246,12 @@ def _kernel_times(lib):
     return kt
 
 
-def other_rows(args, lib, dev, st, timed, peaks, G, A, theta, w, n, m, l):
+def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l):
     """Per-call timings of the paths beside the headline step, each on its
     own workload: the bitflip circuit on the headline's G, A, theta, and one
     MMD^2 loss + gradient call of the MMD training workload."""
     import torch
-    from paper_2501_04776_gb300 import _lib
+    from paper_2501_04776_gb300 import _lib, api
     P = ctypes.c_void_p
     hbm = peaks.get("hbm_gbs") or 6800.0
     out = {}
@@ -266,36 +288,52 @@ def other_rows(args, lib, dev, st, timed, peaks, G, A, theta, w, n, m, l):
                      "bytes_per_step": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}}
     del ws
 
-    # MMD^2 loss and gradient, one training step's call (unbiased form).
+    # MMD^2 loss and gradient, one training step's call (unbiased form), in
+    # the tensor-core form and in the row-sparse form.
     p = I.mmd_training()
     Gm, Am, Zm, Xm = (torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).to(dev)
                       for x in (p.G, p.A, p.Z, p.X))
     thm = torch.from_numpy(p.theta).to(dev)
     mm, lm, sm, Nm = p.G.shape[0], p.A.shape[0], p.Z.shape[0], p.X.shape[0]
-    ws = torch.empty(lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD, p.n, mm, lm, sm, Nm, _lib.SPLIT_BF16),
-                     dtype=torch.uint8, device=dev)
     loss = torch.empty(1, dtype=torch.float64, device=dev)
     gm = torch.empty(mm, dtype=torch.float64, device=dev)
+    nnz = nnz_parities(api, p.n, Am, Gm)
+    for prec, tag in ((_lib.SPLIT_BF16, "split_bf16"), (_lib.SPARSE_FP32, "sparse_fp32")):
+        ws = torch.empty(lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD, p.n, mm, lm, sm, Nm, prec),
+                         dtype=torch.uint8, device=dev)
 
-    def mmd():
-        _lib.check(lib.iqp_mmd_loss_grad(p.n, P(Gm.data_ptr()), mm, Gm.shape[1], P(Am.data_ptr()), lm, Am.shape[1],
-                                         P(Zm.data_ptr()), sm, Zm.shape[1], P(Xm.data_ptr()), Nm, Xm.shape[1],
-                                         P(thm.data_ptr()), _lib.SPLIT_BF16, 1, P(loss.data_ptr()),
-                                         P(gm.data_ptr()), P(ws.data_ptr()), ws.numel(), st), "iqp_mmd_loss_grad")
+        def mmd():
+            _lib.check(lib.iqp_mmd_loss_grad(p.n, P(Gm.data_ptr()), mm, Gm.shape[1], P(Am.data_ptr()), lm,
+                                             Am.shape[1], P(Zm.data_ptr()), sm, Zm.shape[1], P(Xm.data_ptr()), Nm,
+                                             Xm.shape[1], P(thm.data_ptr()), prec, 1, P(loss.data_ptr()),
+                                             P(gm.data_ptr()), P(ws.data_ptr()), ws.numel(), st),
+                       "iqp_mmd_loss_grad")
 
-    lib.iqp_profile_reset()
-    ms, _ = timed(None, args.steps, args.warmup, profile=True, fn=mmd)
-    kt = _kernel_times(lib)
-    dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
-    executed = 4.0 * lm * sm * mm
-    peak = peaks.get("bf16_tflops_sustained") or 1700.0
-    ach = executed / (kt[dom]["avg_ms"] * 1e-3) / 1e12
-    out["mmd_loss_grad"] = {
-        "workload": f"MMD^2 loss + grad, n={p.n} m={mm} (all 1- and 2-body) l={lm} s={sm} N={Nm}, split-BF16",
-        "ms_per_call": round(statistics.mean(ms), 3), "kernels": kt,
-        "roofline": {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": peak,
-                     "unit": "TFLOP/s", "frac": round(ach / peak, 4), "flops_per_launch": executed,
-                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}}
+        lib.iqp_profile_reset()
+        ms, _ = timed(None, args.steps, args.warmup, profile=True, fn=mmd)
+        kt = _kernel_times(lib)
+        if prec == _lib.SPLIT_BF16:
+            dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
+            executed = 4.0 * lm * sm * mm
+            peak = peaks.get("bf16_tflops_sustained") or 1700.0
+            ach = executed / (kt[dom]["avg_ms"] * 1e-3) / 1e12
+            roof = {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
+                    "frac": round(ach / peak, 4), "flops_per_launch": executed,
+                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+        else:
+            # Forward kernel: nnz * s FP32 signed additions; peak = one FP32
+            # add per lane per clock: 152 SMs x 128 lanes x max SM clock.
+            mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+            peak = 152 * 128 * mhz * 1e6 / 1e12
+            ach = nnz * sm / (kt["phase_sparse"]["avg_ms"] * 1e-3) / 1e12
+            roof = {"bound": "alu", "kernel": "phase_sparse", "achieved": round(ach, 2), "peak": round(peak, 1),
+                    "unit": "Tadd/s", "frac": round(ach / peak, 4), "adds_per_launch": nnz * sm,
+                    "nnz_PA": nnz, "density_PA": round(nnz / (lm * mm), 5),
+                    "peak_source": "FP32 add: 152 SMs x 128 lanes x max SM clock"}
+        out["mmd_loss_grad_" + tag] = {
+            "workload": f"MMD^2 loss + grad, n={p.n} m={mm} (all 1- and 2-body) l={lm} s={sm} N={Nm}, {tag}",
+            "ms_per_call": round(statistics.mean(ms), 3), "kernels": kt, "roofline": roof}
+        del ws
     return out
 
 
@@ -319,7 +357,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     lib = _lib.load()
-    prec = _lib.SPLIT_BF16 if args.precision == "split_bf16" else _lib.FP32
+    prec = {"split_bf16": _lib.SPLIT_BF16, "fp32": _lib.FP32, "sparse_fp32": _lib.SPARSE_FP32}[args.precision]
     if prec == _lib.SPLIT_BF16 and not lib.iqp_tensor_path_available():
         raise SystemExit("the split-BF16 tensor path needs an sm_103 GPU")
 
@@ -418,6 +456,15 @@ def main():
                 "flops_per_launch": executed, "useful_tflops": round(achieved / 2, 1),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
+    elif prec == _lib.SPARSE_FP32:
+        nnz = nnz_parities(api, p.n, A, G)
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = 152 * 128 * mhz * 1e6 / 1e12
+        achieved = nnz * s / (kt["phase_sparse"]["avg_ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "phase_sparse", "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "Tadd/s", "frac": round(achieved / peak, 4), "traffic": None, "adds_per_launch": nnz * s,
+                "nnz_PA": nnz, "density_PA": round(nnz / (l * m), 5),
+                "peak_source": "FP32 add: 152 SMs x 128 lanes x max SM clock"}
     else:
         dom = max(("phase_fp32", "recompute_fp32", "grad_fp32"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
         flops = 2.0 * l * s * m
@@ -463,7 +510,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec == _lib.SPLIT_BF16 else "f32",
         "data": "synthetic (seeded splitmix64), shaped like the paper's op_expval benchmark",
-        "config": {"workload": workload_name(args), "n": n, "m": m, "l": l, "s": s,
+        "config": {"workload": workload_name(args, p), "n": n, "m": m, "l": l, "s": s,
                    "precision": args.precision + (" (2 theta = hi + lo BF16, FP32 accumulate in TMEM, FP64 "
                                                   "reductions)" if prec == _lib.SPLIT_BF16 else ""),
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
@@ -474,7 +521,7 @@ def main():
     if fp32 is not None:
         line["fp32_form"] = fp32
     if not args.no_rows and prec == _lib.SPLIT_BF16:
-        line["rows"] = other_rows(args, lib, dev, st, timed, peaks, G, A, theta, w, n, m, l)
+        line["rows"] = other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def gpu_grad_fn(alpha_np):
             al = torch.from_numpy(alpha_np).to(dev)
