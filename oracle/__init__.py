@@ -50,6 +50,12 @@ def _load():
             "oracle_subset_expansion": [i64] + mat * 2 + [p, p],
             "oracle_bitflip_expval": [i64] + mat * 2 + [p, p],
             "oracle_bitflip_grad": [i64] + mat * 2 + [p, p, p],
+            "oracle_mmd_loss_sqrt": [i64] + mat * 4 + [p, ctypes.c_int, p, p],
+            "oracle_expand_params": [p, p, i64, p],
+            "oracle_reduce_params": [p, p, i64, p],
+            "oracle_embed_bits": [p, i64, i64, p, i64, p, i64],
+            "oracle_expval_indep": [i64] + mat * 3 + [p, p, p, p, p],
+            "oracle_expval_indep_grad": [i64] + mat * 3 + [p, p, p, p],
             "oracle_set_threads": [ctypes.c_int],
             "oracle_max_threads": [],
         }
@@ -205,6 +211,84 @@ def bitflip_grad(n, G, A, theta, w):
     A, pa, l, lda = _w(A)
     g = np.empty(m)
     lib.oracle_bitflip_grad(n, pg, m, ldg, pa, l, lda, _d(theta).ctypes.data, _d(w).ctypes.data, g.ctypes.data)
+    return g
+
+
+def mmd_loss_sqrt(n, G, A, Z, X, theta, unbiased=True, grad=False):
+    """sqrt_loss form of the MMD loss: (sqrt(MMD^2 estimate), grad or None)."""
+    lib = _load()
+    G, pg, m, ldg = _w(G)
+    A, pa, l, lda = _w(A)
+    Z, pz, s, ldz = _w(Z)
+    X, px, N, ldx = _w(X)
+    loss = ctypes.c_double(0.0)
+    g = np.empty(m) if grad else None
+    lib.oracle_mmd_loss_sqrt(n, pg, m, ldg, pa, l, lda, pz, s, ldz, px, N, ldx, _d(theta).ctypes.data,
+                             1 if unbiased else 0, ctypes.addressof(loss), g.ctypes.data if g is not None else None)
+    return loss.value, g
+
+
+def expand_params(theta_p, start):
+    """Per-generator parameters of shared-parameter gates (gate p owns
+    generators start[p]..start[p+1]-1)."""
+    lib = _load()
+    th = _d(theta_p)
+    st = np.ascontiguousarray(start, dtype=np.int64)
+    out = np.empty(int(st[-1]))
+    lib.oracle_expand_params(th.ctypes.data, st.ctypes.data, th.shape[0], out.ctypes.data)
+    return out
+
+
+def reduce_params(grad_gen, start):
+    """Gradient per shared parameter: sum over the gate's generators."""
+    lib = _load()
+    g = _d(grad_gen)
+    st = np.ascontiguousarray(start, dtype=np.int64)
+    out = np.empty(st.shape[0] - 1)
+    lib.oracle_reduce_params(g.ctypes.data, st.ctypes.data, out.shape[0], out.ctypes.data)
+    return out
+
+
+def embed_bits(src, nw, wires, n):
+    """Rows on `nw` wire qubits -> rows on n qubits (bit k -> qubit wires[k])."""
+    lib = _load()
+    S, ps, rows, lds = _w(src)
+    wi = np.ascontiguousarray(wires, dtype=np.int64)
+    assert wi.shape[0] == nw
+    ld = max(1, (n + 63) // 64)
+    ld += ld & 1
+    out = np.empty((rows, ld), dtype=np.uint64)
+    lib.oracle_embed_bits(ps, rows, lds, wi.ctypes.data, nw, out.ctypes.data, ld)
+    return out
+
+
+def expval_indep(n, G, A, Z, theta):
+    """Independent-batch estimator: observable a uses Z rows a*s..a*s+s-1.
+    Returns (expval, std_err, S1, S2)."""
+    lib = _load()
+    G, pg, m, ldg = _w(G)
+    A, pa, l, lda = _w(A)
+    Z, pz, ls, ldz = _w(Z)
+    assert ls % l == 0
+    s = ls // l
+    ev, se, s1, s2 = (np.empty(l) for _ in range(4))
+    lib.oracle_expval_indep(n, pg, m, ldg, pa, l, lda, pz, s, ldz, _d(theta).ctypes.data,
+                            ev.ctypes.data, se.ctypes.data, s1.ctypes.data, s2.ctypes.data)
+    return ev, se, s1, s2
+
+
+def expval_indep_grad(n, G, A, Z, theta, alpha, beta=None):
+    """Gradient of the independent-batch estimator (alpha/beta as in expval_grad)."""
+    lib = _load()
+    G, pg, m, ldg = _w(G)
+    A, pa, l, lda = _w(A)
+    Z, pz, ls, ldz = _w(Z)
+    s = ls // l
+    al = _d(alpha)
+    be = _d(beta) if beta is not None else None
+    g = np.empty(m)
+    lib.oracle_expval_indep_grad(n, pg, m, ldg, pa, l, lda, pz, s, ldz, _d(theta).ctypes.data, al.ctypes.data,
+                                 be.ctypes.data if be is not None else None, g.ctypes.data)
     return g
 
 

@@ -463,6 +463,88 @@ void oracle_bitflip_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
     free(PA);
 }
 
+/* ------------------------------------------------------- API variants */
+
+/* sqrt_loss option of the MMD loss (Sec. 3.3.1): the square root of the
+ * MMD^2 estimate, L' = sqrt(L), with dL'/dtheta = (dL/dtheta) / (2 L') by the
+ * chain rule. An estimate L <= 0 (the unbiased form can be negative) gives
+ * L' = 0 and a zero gradient. */
+void oracle_mmd_loss_sqrt(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                          const uint64_t *A, int64_t l, int64_t lda,
+                          const uint64_t *Z, int64_t s, int64_t ldz,
+                          const uint64_t *X, int64_t N, int64_t ldx, const double *theta,
+                          int unbiased, double *loss, double *grad) {
+    oracle_mmd_loss(n, G, m, ldg, A, l, lda, Z, s, ldz, X, N, ldx, theta, unbiased, loss, NULL, grad);
+    double L = *loss;
+    double r = L > 0.0 ? sqrt(L) : 0.0;
+    if (grad)
+        for (int64_t j = 0; j < m; ++j) grad[j] = L > 0.0 ? grad[j] / (2.0 * r) : 0.0;
+    *loss = r;
+}
+
+/* Shared-parameter gates (Sec. 3.1.1): gate p is the product of the
+ * commuting exponentials of its generators, all with parameter theta_p.
+ * Generators are stored gate by gate: gate p owns rows [start[p], start[p+1])
+ * of G. The per-generator parameter vector is theta_gen[j] = theta_p for j in
+ * gate p, and the gradient of a gate is the sum of its generators'
+ * gradients (chain rule through the shared parameter). */
+void oracle_expand_params(const double *theta_p, const int64_t *start, int64_t np, double *theta_gen) {
+    for (int64_t p = 0; p < np; ++p)
+        for (int64_t j = start[p]; j < start[p + 1]; ++j) theta_gen[j] = theta_p[p];
+}
+
+void oracle_reduce_params(const double *grad_gen, const int64_t *start, int64_t np, double *grad_p) {
+    for (int64_t p = 0; p < np; ++p) {
+        double acc = 0.0;
+        for (int64_t j = start[p]; j < start[p + 1]; ++j) acc += grad_gen[j];
+        grad_p[p] = acc;
+    }
+}
+
+/* `wires` option of the MMD loss (Sec. 3.3.1): observables and data live on
+ * the listed qubits only, the others are ancillas. Bit k of each source row
+ * (k < nw) becomes bit wires[k] of the n-qubit destination row; every other
+ * destination bit is zero. */
+void oracle_embed_bits(const uint64_t *src, int64_t rows, int64_t ld_src, const int64_t *wires, int64_t nw,
+                       uint64_t *dst, int64_t ld_dst) {
+    for (int64_t r = 0; r < rows; ++r) {
+        uint64_t *d = dst + r * ld_dst;
+        for (int64_t w = 0; w < ld_dst; ++w) d[w] = 0;
+        for (int64_t k = 0; k < nw; ++k)
+            if (bit_at(src + r * ld_src, k)) d[wires[k] >> 6] |= (uint64_t)1 << (wires[k] & 63);
+    }
+}
+
+/* indep_estimates option (Sec. 2.2, Sec. 3.1.2): observable a uses its own
+ * sample batch, rows [a s, (a+1) s) of Z, so the estimates of different
+ * observables are independent. Each observable is the estimator of
+ * eq. expvalsample on its own batch. */
+void oracle_expval_indep(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                         const uint64_t *A, int64_t l, int64_t lda,
+                         const uint64_t *Z, int64_t s, int64_t ldz, const double *theta,
+                         double *expval, double *std_err, double *S1, double *S2) {
+    for (int64_t a = 0; a < l; ++a)
+        oracle_expval(n, G, m, ldg, A + a * lda, 1, lda, Z + a * s * ldz, s, ldz, theta,
+                      expval ? expval + a : NULL, std_err ? std_err + a : NULL, S1 ? S1 + a : NULL,
+                      S2 ? S2 + a : NULL);
+}
+
+/* Gradient of the independent-batch estimator: the sum over observables of
+ * oracle_expval_grad on each observable's own batch. */
+void oracle_expval_indep_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                              const uint64_t *A, int64_t l, int64_t lda,
+                              const uint64_t *Z, int64_t s, int64_t ldz, const double *theta,
+                              const double *alpha, const double *beta, double *grad) {
+    double *g = (double *)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < m; ++j) grad[j] = 0.0;
+    for (int64_t a = 0; a < l; ++a) {
+        oracle_expval_grad(n, G, m, ldg, A + a * lda, 1, lda, Z + a * s * ldz, s, ldz, theta,
+                           alpha ? alpha + a : NULL, beta ? beta + a : NULL, g);
+        for (int64_t j = 0; j < m; ++j) grad[j] += g[j];
+    }
+    free(g);
+}
+
 int oracle_max_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

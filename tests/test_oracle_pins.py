@@ -416,3 +416,165 @@ def test_random_k_body_distinct_qubits():
     k = bits_of(G, 17).sum(axis=1)
     assert set(np.unique(k)) == {1, 2, 3}
     assert abs(np.mean(k) - 2.0) < 0.05
+
+
+# ------------------------------------------------------------ API variants
+
+def test_mmd_sqrt_loss_grad_matches_central_differences():
+    """sqrt_loss (Sec. 3.3.1): the gradient of sqrt(MMD^2) by central
+    differences of the square-rooted loss itself."""
+    rng = I.Rng(55)
+    n = 6
+    G = I.local_gates_packed(n)
+    th = rng.normal(G.shape[0], 1) * 0.3
+    A = I.bernoulli_bits(rng, 8, n, 0.4, 2, nonzero=True)
+    Z = I.uniform_bits(rng, 40, n, 3)
+    X = I.prototype_data(rng, 30, n, 2, 0.1, 4)
+    for unbiased in (True, False):
+        L, g = oracle.mmd_loss_sqrt(n, G, A, Z, X, th, unbiased, grad=True)
+        assert L > 0.05
+        fd = _fd(lambda t: oracle.mmd_loss_sqrt(n, G, A, Z, X, t, unbiased)[0], th)
+        assert np.linalg.norm(g - fd) / np.linalg.norm(fd) < 1e-6
+
+
+def _pauli_x_string(n, qubits):
+    """Dense 2^n x 2^n matrix of prod_{q in qubits} X_q (basis index bit q =
+    qubit q): it maps |x> to |x xor mask>."""
+    mask = sum(1 << q for q in qubits)
+    M = np.zeros((1 << n, 1 << n))
+    for x in range(1 << n):
+        M[x ^ mask, x] = 1.0
+    return M
+
+
+def test_shared_parameter_gates_match_matrix_exponential():
+    """The paper's shared-parameter example on three qubits: gate 1 =
+    exp(i theta_1 (X I X + X X X)), gate 2 = exp(i theta_2 X I I). The
+    expanded generator list with per-generator parameters must reproduce the
+    state exp(i H)|0> built by a dense matrix exponential of the summed
+    generators, for every observable."""
+    scipy_linalg = pytest.importorskip("scipy.linalg")
+    gold = json.load(open(GOLDEN))["shared_parameter_example_n3"]["value"]
+    n = 3
+    gens, start = [], [0]
+    for gate in gold:
+        gens.extend(gate)
+        start.append(len(gens))
+    G = I.pack_index_lists(gens, n)
+    th_p = np.array([0.37, -0.81])
+    H = sum(th_p[p] * _pauli_x_string(n, g) for p, gate in enumerate(gold) for g in gate)
+    psi = scipy_linalg.expm(1j * H)[:, 0]
+    probs = np.abs(psi) ** 2
+    A = all_strings(n)
+    signs = (-1.0) ** (bits_of(A, n) @ bits_of(all_strings(n), n).T)
+    want = signs @ probs
+    got = oracle.exact_expval(n, G, A, oracle.expand_params(th_p, start))
+    assert np.max(np.abs(got - want)) < 1e-12
+    assert np.max(np.abs(want - 1.0)) > 0.1  # not trivial
+
+
+def test_shared_parameter_grad_matches_central_differences():
+    """Chain rule through shared parameters: the gate gradient is the sum of
+    its generators' gradients; checked by central differences in theta_p of
+    the estimator evaluated with the expanded parameters."""
+    rng = I.Rng(56)
+    n = 7
+    gens = [[0, 2], [0, 1, 2], [0], [3, 4], [5], [1, 6], [2, 3, 5]]
+    start = [0, 2, 3, 5, 7]
+    G = I.pack_index_lists(gens, n)
+    th_p = rng.normal(4, 1) * 0.4
+    A = I.bernoulli_bits(rng, 6, n, 0.4, 2, nonzero=True)
+    Z = I.uniform_bits(rng, 64, n, 3)
+    w = rng.normal(A.shape[0], 4)
+    alpha = -w / Z.shape[0]
+    g_gen = oracle.expval_grad(n, G, A, Z, oracle.expand_params(th_p, start), alpha)
+    g_p = oracle.reduce_params(g_gen, start)
+    fd = _fd(lambda t: float(np.dot(w, oracle.expval(n, G, A, Z, oracle.expand_params(t, start))[0])), th_p)
+    assert np.linalg.norm(g_p - fd) / np.linalg.norm(fd) < 1e-7
+
+
+def test_mmd_with_wires_is_kernel_mmd_of_the_marginal():
+    """wires (Sec. 3.3.1): with observables and data on the wire qubits only,
+    sum_a P_sigma(a) term_a over all a on the wires equals the Gaussian-kernel
+    MMD^2 between the data and the circuit's marginal distribution on the
+    wires (ancillas summed out of the statevector probabilities)."""
+    rng = I.Rng(57)
+    n, wires = 5, [0, 2, 3]
+    nw = len(wires)
+    G = I.local_gates_packed(n)
+    th = rng.normal(G.shape[0], 1) * 0.5
+    Xw = I.prototype_data(rng, 40, nw, 2, 0.15, 2)
+    sigma2 = 0.9
+    ps = I.p_sigma(sigma2)
+    Aw = all_strings(nw)
+    A = oracle.embed_bits(Aw, nw, wires, n)
+    X = oracle.embed_bits(Xw, nw, wires, n)
+    _, terms, _ = oracle.mmd_loss(n, G, A, all_strings(n), X, th, unbiased=False)
+    abits = bits_of(Aw, nw)
+    wgt = np.prod(np.where(abits == 1, ps, 1 - ps), axis=1)
+    observable_form = float(np.dot(wgt, terms))
+
+    probs = oracle.statevector_probs(n, G, th)
+    xs = np.arange(1 << n)
+    wire_index = sum(((xs >> q) & 1) << k for k, q in enumerate(wires))
+    q_marg = np.bincount(wire_index, weights=probs, minlength=1 << nw)
+    idx = bits_of(Xw, nw) @ (1 << np.arange(nw))
+    p_data = np.bincount(idx, minlength=1 << nw) / Xw.shape[0]
+    d = p_data - q_marg
+    ys = np.arange(1 << nw)
+    ham = np.array([[bin(x ^ y).count("1") for y in ys] for x in ys])
+    kernel_form = float(d @ np.exp(-ham / (2 * sigma2)) @ d)
+    assert abs(observable_form - kernel_form) < 1e-12
+    assert kernel_form > 1e-4
+
+
+def test_embed_bits_places_each_wire():
+    rng = I.Rng(58)
+    n, wires = 130, [129, 0, 64, 63, 7]
+    src = I.uniform_bits(rng, 9, len(wires), 1)
+    out = oracle.embed_bits(src, len(wires), wires, n)
+    want = np.zeros((9, n), np.uint8)
+    want[:, wires] = I.unpack_bits(src, len(wires))
+    assert np.array_equal(I.unpack_bits(out, n), want)
+    assert np.array_equal(out, I.pack_bits(want))  # padding bits zero
+
+
+def test_indep_estimates_are_independent_and_unbiased():
+    """indep_estimates (Sec. 2.2): with one batch per observable, copies of the
+    same observable get independent estimates whose spread matches the
+    single-estimate variance Var(cos Phi)/s, each within 3 SE of the exact
+    value; with a shared batch the copies would be identical."""
+    rng = I.Rng(59)
+    n = 6
+    G = I.local_gates_packed(n)
+    th = rng.normal(G.shape[0], 1) * 0.35
+    a = I.bernoulli_bits(rng, 1, n, 0.5, 2, nonzero=True)
+    copies, s = 400, 64
+    A = np.repeat(a, copies, axis=0)
+    Z = I.uniform_bits(rng, copies * s, n, 3)
+    ev, se, _, _ = oracle.expval_indep(n, G, A, Z, th)
+    exact = float(oracle.exact_expval(n, G, a, th)[0])
+    # Var(cos Phi) over z ~ U{0,1}^n, exactly: E[cos^2] - E[cos]^2.
+    allz = all_strings(n)
+    _, _, s1, s2 = oracle.expval(n, G, a, allz, th)
+    var = s2[0] / allz.shape[0] - (s1[0] / allz.shape[0]) ** 2
+    spread = float(np.var(ev))
+    assert abs(spread / (var / s) - 1.0) < 0.25  # chi-square with 399 dof: sd ~ 0.07
+    assert abs(float(np.mean(ev)) - exact) < 4 * math.sqrt(var / s / copies)
+    assert np.mean(np.abs(ev - exact) <= 3 * se) > 0.97
+    ev_shared, _, _, _ = oracle.expval(n, G, A, Z[:s], th)
+    assert np.all(ev_shared == ev_shared[0])
+
+
+def test_indep_grad_matches_central_differences():
+    rng = I.Rng(60)
+    n = 6
+    G = I.local_gates_packed(n)
+    th = rng.normal(G.shape[0], 1) * 0.3
+    A = I.bernoulli_bits(rng, 5, n, 0.4, 2, nonzero=True)
+    s = 30
+    Z = I.uniform_bits(rng, A.shape[0] * s, n, 3)
+    w = rng.normal(A.shape[0], 4)
+    g = oracle.expval_indep_grad(n, G, A, Z, th, -w / s)
+    fd = _fd(lambda t: float(np.dot(w, oracle.expval_indep(n, G, A, Z, t)[0])), th)
+    assert np.linalg.norm(g - fd) / np.linalg.norm(fd) < 1e-7
