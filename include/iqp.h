@@ -68,8 +68,17 @@ typedef enum {
     IQP_OP_EXPVAL_GRAD = 2,
     IQP_OP_MMD_LOSS = 3,
     IQP_OP_MMD_LOSS_GRAD = 4,
-    IQP_OP_BITFLIP = 5   /* iqp_bitflip_expval and iqp_bitflip_grad */
+    IQP_OP_BITFLIP = 5,  /* iqp_bitflip_expval and iqp_bitflip_grad */
+    IQP_OP_EXPVAL_INDEP = 6,          /* iqp_expval_indep                       */
+    IQP_OP_EXPVAL_INDEP_GRAD = 7,     /* iqp_expval_indep_grad                  */
+    IQP_OP_MMD_LOSS_INDEP = 8,        /* iqp_mmd_loss with IQP_MMD_INDEP        */
+    IQP_OP_MMD_LOSS_GRAD_INDEP = 9    /* iqp_mmd_loss_grad with IQP_MMD_INDEP   */
 } iqp_op;
+
+/* Flags of the MMD loss calls (the `unbiased` argument is a bit set). */
+#define IQP_MMD_UNBIASED 1 /* U-statistics (else the plug-in form)                     */
+#define IQP_MMD_SQRT 2     /* sqrt_loss: return sqrt(max(MMD^2, 0)) and its gradient   */
+#define IQP_MMD_INDEP 4    /* one batch per observable: Z has l * s rows (indep_estimates) */
 
 /* Bytes of device scratch `ws` needed by `op` for these sizes (N is ignored
  * except for the MMD ops). Returns 0 for invalid sizes. Host only. */
@@ -164,6 +173,15 @@ iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
  *   unbiased == 0:  term_a = (T/N - S1/s)^2
  *   loss = (1/l) sum_a term_a,  S1 = sum_i cos Phi, S2 = sum_i cos^2 Phi, T as in
  *   iqp_parity_sum. The unbiased form needs s >= 2 and N >= 2.
+ * `unbiased` is a set of IQP_MMD_* flags (1 = unbiased keeps its meaning):
+ *   IQP_MMD_SQRT   sqrt_loss (Sec. 3.3.1): loss = sqrt(max(MMD^2, 0)); the
+ *                  gradient is (d MMD^2) / (2 loss), zero where loss = 0.
+ *   IQP_MMD_INDEP  indep_estimates: observable a uses its own samples, rows
+ *                  [a s, (a+1) s) of Z (Z has l * s rows); the estimator runs
+ *                  in the row-sparse FP32 arithmetic and `prec` is ignored.
+ *                  Workspace op IQP_OP_MMD_LOSS_INDEP.
+ * Observables and data on a subset of the qubits (`wires`): embed both with
+ * iqp_embed_bits first.
  * loss: one float64 on the device. ws: iqp_workspace_bytes(IQP_OP_MMD_LOSS, ...). */
 iqp_status iqp_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                         const uint64_t *A, int64_t l, int64_t lda,
@@ -199,6 +217,66 @@ iqp_status iqp_bitflip_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg
                             const uint64_t *A, int64_t l, int64_t lda, const float *theta,
                             const double *w, double *grad, void *ws, size_t ws_bytes, void *stream);
 
+/* Independent estimates (indep_estimates, Sec. 2.2 and 3.1.2): observable a
+ * is estimated on its own sample batch, rows [a s, (a+1) s) of Z (Z has
+ * l * s rows of ldz words), so estimates of different observables are
+ * uncorrelated, at the cost of l * s * (n-bit) samples and per-observable
+ * parities. Outputs as iqp_expval. Arithmetic: the row-sparse FP32 form
+ * (work nnz(P_A) * s), with the parity of each (gate, sample) formed from the
+ * observable's own samples as the XOR over the gate's support.
+ * ws: iqp_workspace_bytes(IQP_OP_EXPVAL_INDEP, n, m, l, s, 0, prec) (prec
+ * ignored); it holds every batch transposed (l * n * ceil(s/64) words). */
+iqp_status iqp_expval_indep(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                            const uint64_t *A, int64_t l, int64_t lda,
+                            const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                            double *expval, double *std_err, void *ws, size_t ws_bytes, void *stream);
+
+/* Gradient of the independent-batch estimator, alpha/beta as in
+ * iqp_expval_grad. ws: iqp_workspace_bytes(IQP_OP_EXPVAL_INDEP_GRAD, ...). */
+iqp_status iqp_expval_indep_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                                 const uint64_t *A, int64_t l, int64_t lda,
+                                 const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                                 const double *alpha, const double *beta, double *grad,
+                                 void *ws, size_t ws_bytes, void *stream);
+
+/* Shared-parameter gates (Sec. 3.1.1): a gate is a tuple of generators with
+ * one parameter, exp(i theta_p sum_{g in gate p} X_g). Store G gate by gate:
+ * gate p owns generator rows [start[p], start[p+1]), start[0] = 0,
+ * start[np] = m, non-decreasing (int64, device). Fixed gates (init_gates with
+ * init_coefs) are gates whose parameter the caller does not train.
+ * iqp_expand_params: theta_gen[j] = theta_p[p] for j in gate p (float32[m]).
+ * iqp_reduce_params: grad_p[p] = sum_{j in gate p} grad_gen[j] (float64, in
+ * index order): the gradient in the shared parameters.
+ * Ranges outside [0, m) are clamped; rows not covered by a gate are left
+ * unwritten. No scratch. */
+iqp_status iqp_expand_params(const float *theta_p, int64_t np, const int64_t *start, float *theta_gen, int64_t m,
+                             void *stream);
+iqp_status iqp_reduce_params(const double *grad_gen, int64_t m, const int64_t *start, int64_t np, double *grad_p,
+                             void *stream);
+
+/* `wires` (Sec. 3.3.1): rows on nw wire qubits -> rows on n qubits. Bit k of
+ * src row r becomes bit wires[k] of dst row r; every other bit of dst is zero.
+ * wires: int32[nw] on the device, distinct, in [0, n) (others are skipped).
+ * src: rows x ld_src words (ld_src >= ceil(nw/64)); dst: rows x ld_dst words
+ * (ld_dst >= ceil(n/64), even). No scratch. */
+iqp_status iqp_embed_bits(const uint64_t *src, int64_t rows, int64_t ld_src, const int32_t *wires, int64_t nw,
+                          uint64_t *dst, int64_t ld_dst, int64_t n, void *stream);
+
+/* Random bits on the device for a training loop (fresh samples each step,
+ * Sec. 2.4; observables a ~ P_sigma, Sec. 3.3.1), from a counter-based
+ * splitmix64 (Steele, Lea and Flood 2014): value k >= 1 of stream t under
+ * seed S is mix(S * 0xD1B54A32D192ED03 + t * 0xAEF17502108EF2D9 + k *
+ * 0x9E3779B97F4A7C15) with the splitmix64 finaliser.
+ * iqp_uniform_bits: word w < ceil(n/64) of row r is value r * L + w + 1, L =
+ * ceil(n/64) rounded up to even; bits >= n and words >= ceil(n/64) are zero.
+ * iqp_bernoulli_bits: bit q of row r is set iff (value r * n + q + 1 >> 11)
+ * * 2^-53 < p (exact in FP64).
+ * out: rows x ld words on the device, ld >= ceil(n/64) and even. */
+iqp_status iqp_uniform_bits(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t n, uint64_t *out, int64_t ld,
+                            void *stream);
+iqp_status iqp_bernoulli_bits(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t n, double p, uint64_t *out,
+                              int64_t ld, void *stream);
+
 /* Device-side status of the last calls that used `ws`: synchronises
  * `stream`, returns IQP_OK or the first error a kernel recorded (e.g.
  * IQP_ERR_TIMEOUT), and clears it. */
@@ -227,7 +305,9 @@ typedef enum {
     IQP_KERNEL_BITFLIP = 13,       /* bitflip products and gradient sums        */
     IQP_KERNEL_PHASE_SPARSE = 14,  /* row-sparse phase + statistics             */
     IQP_KERNEL_GRAD_SPARSE = 15,   /* row-sparse recompute + gradient           */
-    IQP_KERNEL_COUNT = 16
+    IQP_KERNEL_VARIANTS = 16,      /* shared-parameter expand/reduce, embedding */
+    IQP_KERNEL_RNG = 17,           /* on-device random bits                     */
+    IQP_KERNEL_COUNT = 18
 } iqp_kernel;
 
 /* Per-kernel timing (off by default). When enabled, every launch is

@@ -51,6 +51,7 @@ def _load():
             "oracle_bitflip_expval": [i64] + mat * 2 + [p, p],
             "oracle_bitflip_grad": [i64] + mat * 2 + [p, p, p],
             "oracle_mmd_loss_sqrt": [i64] + mat * 4 + [p, ctypes.c_int, p, p],
+            "oracle_mmd_loss_ex": [i64] + mat * 4 + [p, ctypes.c_int, p, p, p],
             "oracle_expand_params": [p, p, i64, p],
             "oracle_reduce_params": [p, p, i64, p],
             "oracle_embed_bits": [p, i64, i64, p, i64, p, i64],
@@ -226,6 +227,24 @@ def mmd_loss_sqrt(n, G, A, Z, X, theta, unbiased=True, grad=False):
     lib.oracle_mmd_loss_sqrt(n, pg, m, ldg, pa, l, lda, pz, s, ldz, px, N, ldx, _d(theta).ctypes.data,
                              1 if unbiased else 0, ctypes.addressof(loss), g.ctypes.data if g is not None else None)
     return loss.value, g
+
+
+def mmd_loss_ex(n, G, A, Z, X, theta, unbiased=True, sqrt_loss=False, indep=False, grad=False):
+    """MMD loss with the API options: sqrt_loss, indep (Z has l * s rows, one
+    batch per observable). Returns (loss, terms[l], grad[m] or None)."""
+    lib = _load()
+    G, pg, m, ldg = _w(G)
+    A, pa, l, lda = _w(A)
+    Z, pz, zr, ldz = _w(Z)
+    X, px, N, ldx = _w(X)
+    s = zr // l if indep else zr
+    flags = (1 if unbiased else 0) | (2 if sqrt_loss else 0) | (4 if indep else 0)
+    loss = ctypes.c_double(0.0)
+    terms = np.empty(l)
+    g = np.empty(m) if grad else None
+    lib.oracle_mmd_loss_ex(n, pg, m, ldg, pa, l, lda, pz, s, ldz, px, N, ldx, _d(theta).ctypes.data, flags,
+                           ctypes.addressof(loss), terms.ctypes.data, g.ctypes.data if g is not None else None)
+    return loss.value, terms, g
 
 
 def expand_params(theta_p, start):

@@ -248,20 +248,21 @@ void oracle_data_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda
  * loss = (1/l) sum_a term_a. terms (l) and grad (m) may be NULL. The
  * gradient uses alpha/beta of oracle_expval_grad, from differentiating the
  * chosen form in S1 and S2. */
-void oracle_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
-                     const uint64_t *A, int64_t l, int64_t lda,
-                     const uint64_t *Z, int64_t s, int64_t ldz,
-                     const uint64_t *X, int64_t N, int64_t ldx, const double *theta,
-                     int unbiased, double *loss, double *terms, double *grad) {
-    double *S1 = (double *)malloc(sizeof(double) * (size_t)(l > 0 ? l : 1));
-    double *S2 = (double *)malloc(sizeof(double) * (size_t)(l > 0 ? l : 1));
-    int64_t *T = (int64_t *)malloc(sizeof(int64_t) * (size_t)(l > 0 ? l : 1));
-    oracle_expval(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, NULL, NULL, S1, S2);
-    oracle_data_parity_sum(n, A, l, lda, X, N, ldx, T);
+void oracle_expval_indep(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                         const uint64_t *A, int64_t l, int64_t lda,
+                         const uint64_t *Z, int64_t s, int64_t ldz, const double *theta,
+                         double *expval, double *std_err, double *S1, double *S2);
+void oracle_expval_indep_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                              const uint64_t *A, int64_t l, int64_t lda,
+                              const uint64_t *Z, int64_t s, int64_t ldz, const double *theta,
+                              const double *alpha, const double *beta, double *grad);
+
+/* Terms, loss and gradient coefficients from the per-observable sums S1, S2
+ * (model) and T (data), in the form chosen by `unbiased`. */
+static void mmd_terms(int64_t l, int64_t s, int64_t N, const double *S1, const double *S2, const int64_t *T,
+                      int unbiased, double *loss, double *terms, double *alpha, double *beta) {
     double ds = (double)s, dN = (double)N, dl = (double)l;
     double acc = 0.0;
-    double *alpha = (double *)malloc(sizeof(double) * (size_t)(l > 0 ? l : 1));
-    double *beta = (double *)malloc(sizeof(double) * (size_t)(l > 0 ? l : 1));
     for (int64_t a = 0; a < l; ++a) {
         double Td = (double)T[a];
         double p = Td / dN, q = S1[a] / ds, term;
@@ -283,12 +284,57 @@ void oracle_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
         acc += term;
     }
     *loss = acc / dl;
-    if (grad) oracle_expval_grad(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, alpha, beta, grad);
+}
+
+/* flags: 1 = unbiased form, 2 = sqrt_loss, 4 = independent batches (Z has
+ * l * s rows, observable a uses rows [a s, (a+1) s)). */
+void oracle_mmd_loss_ex(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                        const uint64_t *A, int64_t l, int64_t lda,
+                        const uint64_t *Z, int64_t s, int64_t ldz,
+                        const uint64_t *X, int64_t N, int64_t ldx, const double *theta,
+                        int flags, double *loss, double *terms, double *grad) {
+    const size_t L = (size_t)(l > 0 ? l : 1);
+    double *S1 = (double *)malloc(sizeof(double) * L);
+    double *S2 = (double *)malloc(sizeof(double) * L);
+    int64_t *T = (int64_t *)malloc(sizeof(int64_t) * L);
+    double *alpha = (double *)malloc(sizeof(double) * L);
+    double *beta = (double *)malloc(sizeof(double) * L);
+    const int indep = (flags & 4) != 0;
+    if (indep)
+        oracle_expval_indep(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, NULL, NULL, S1, S2);
+    else
+        oracle_expval(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, NULL, NULL, S1, S2);
+    oracle_data_parity_sum(n, A, l, lda, X, N, ldx, T);
+    mmd_terms(l, s, N, S1, S2, T, flags & 1, loss, terms, alpha, beta);
+    if (grad) {
+        if (indep)
+            oracle_expval_indep_grad(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, alpha, beta, grad);
+        else
+            oracle_expval_grad(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, alpha, beta, grad);
+    }
+    if (flags & 2) {
+        /* sqrt_loss (Sec. 3.3.1): L' = sqrt(L), dL' = dL / (2 L'); an estimate
+         * L <= 0 (the unbiased form can be negative) gives L' = 0 and a zero
+         * gradient. */
+        double Lv = *loss;
+        double r = Lv > 0.0 ? sqrt(Lv) : 0.0;
+        if (grad)
+            for (int64_t j = 0; j < m; ++j) grad[j] = Lv > 0.0 ? grad[j] / (2.0 * r) : 0.0;
+        *loss = r;
+    }
     free(beta);
     free(alpha);
     free(T);
     free(S2);
     free(S1);
+}
+
+void oracle_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                     const uint64_t *A, int64_t l, int64_t lda,
+                     const uint64_t *Z, int64_t s, int64_t ldz,
+                     const uint64_t *X, int64_t N, int64_t ldx, const double *theta,
+                     int unbiased, double *loss, double *terms, double *grad) {
+    oracle_mmd_loss_ex(n, G, m, ldg, A, l, lda, Z, s, ldz, X, N, ldx, theta, unbiased ? 1 : 0, loss, terms, grad);
 }
 
 /* ---------------------------------------------------------------- exact forms */
@@ -465,21 +511,14 @@ void oracle_bitflip_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
 
 /* ------------------------------------------------------- API variants */
 
-/* sqrt_loss option of the MMD loss (Sec. 3.3.1): the square root of the
- * MMD^2 estimate, L' = sqrt(L), with dL'/dtheta = (dL/dtheta) / (2 L') by the
- * chain rule. An estimate L <= 0 (the unbiased form can be negative) gives
- * L' = 0 and a zero gradient. */
+/* sqrt_loss option of the MMD loss (Sec. 3.3.1); see oracle_mmd_loss_ex. */
 void oracle_mmd_loss_sqrt(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                           const uint64_t *A, int64_t l, int64_t lda,
                           const uint64_t *Z, int64_t s, int64_t ldz,
                           const uint64_t *X, int64_t N, int64_t ldx, const double *theta,
                           int unbiased, double *loss, double *grad) {
-    oracle_mmd_loss(n, G, m, ldg, A, l, lda, Z, s, ldz, X, N, ldx, theta, unbiased, loss, NULL, grad);
-    double L = *loss;
-    double r = L > 0.0 ? sqrt(L) : 0.0;
-    if (grad)
-        for (int64_t j = 0; j < m; ++j) grad[j] = L > 0.0 ? grad[j] / (2.0 * r) : 0.0;
-    *loss = r;
+    oracle_mmd_loss_ex(n, G, m, ldg, A, l, lda, Z, s, ldz, X, N, ldx, theta, (unbiased ? 1 : 0) | 2, loss, NULL,
+                       grad);
 }
 
 /* Shared-parameter gates (Sec. 3.1.1): gate p is the product of the

@@ -14,6 +14,8 @@ LIB_PATH = os.path.join(HERE, "libiqp_gb300.so")
 OK, ERR_ARG, ERR_ALIGN, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 FP32, SPLIT_BF16, SPARSE_FP32 = 0, 1, 2
 OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP = 1, 2, 3, 4, 5
+OP_EXPVAL_INDEP, OP_EXPVAL_INDEP_GRAD, OP_MMD_LOSS_INDEP, OP_MMD_LOSS_GRAD_INDEP = 6, 7, 8, 9
+MMD_UNBIASED, MMD_SQRT, MMD_INDEP = 1, 2, 4
 
 # Every symbol include/iqp.h declares, with (restype, argtypes).
 _i64, _p, _int, _sz, _dbl = ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_double
@@ -30,6 +32,13 @@ SIGNATURES = {
     "iqp_mmd_loss_grad": (_int, [_i64] + _MAT * 4 + [_p, _int, _int, _p, _p, _p, _sz, _p]),
     "iqp_bitflip_expval": (_int, [_i64] + _MAT * 2 + [_p, _p, _p, _sz, _p]),
     "iqp_bitflip_grad": (_int, [_i64] + _MAT * 2 + [_p, _p, _p, _p, _sz, _p]),
+    "iqp_expval_indep": (_int, [_i64] + _MAT * 3 + [_p, _p, _p, _p, _sz, _p]),
+    "iqp_expval_indep_grad": (_int, [_i64] + _MAT * 3 + [_p, _p, _p, _p, _p, _sz, _p]),
+    "iqp_expand_params": (_int, [_p, _i64, _p, _p, _i64, _p]),
+    "iqp_reduce_params": (_int, [_p, _i64, _p, _i64, _p, _p]),
+    "iqp_embed_bits": (_int, [_p, _i64, _i64, _p, _i64, _p, _i64, _i64, _p]),
+    "iqp_uniform_bits": (_int, [ctypes.c_uint64, ctypes.c_uint64, _i64, _i64, _p, _i64, _p]),
+    "iqp_bernoulli_bits": (_int, [ctypes.c_uint64, ctypes.c_uint64, _i64, _i64, _dbl, _p, _i64, _p]),
     "iqp_read_status": (_int, [_p, _sz, _p]),
     "iqp_selftest_timeout": (_int, [_p, _sz, _dbl, _p]),
     "iqp_status_string": (ctypes.c_char_p, [_int]),
@@ -42,7 +51,7 @@ SIGNATURES = {
 
 KERNELS = ["parity", "parity_sum", "theta_split", "phase_fp32", "recompute_fp32", "grad_fp32", "phase_tc",
            "recompute_tc", "grad_tc", "finalize", "grad_reduce", "mmd_combine", "selftest", "bitflip",
-           "phase_sparse", "grad_sparse"]
+           "phase_sparse", "grad_sparse", "variants", "rng"]
 
 _lib = None
 

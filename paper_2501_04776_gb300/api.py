@@ -15,6 +15,8 @@ import torch
 
 from . import _lib
 from ._lib import FP32, SPLIT_BF16, SPARSE_FP32, OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP, check
+from ._lib import OP_EXPVAL_INDEP, OP_EXPVAL_INDEP_GRAD, OP_MMD_LOSS_INDEP, OP_MMD_LOSS_GRAD_INDEP
+from ._lib import MMD_UNBIASED, MMD_SQRT, MMD_INDEP
 
 _PRECISIONS = {"fp32": FP32, "split_bf16": SPLIT_BF16, "sparse_fp32": SPARSE_FP32, FP32: FP32,
                SPLIT_BF16: SPLIT_BF16, SPARSE_FP32: SPARSE_FP32}
@@ -172,19 +174,29 @@ def expval(theta, G, A, Z, n: int, precision="split_bf16"):
     return _ExpvalFn.apply(theta, G, A, Z, n, precision)
 
 
-def mmd_loss_raw(n, theta, G, A, Z, X, precision="split_bf16", unbiased=True, with_grad=False):
+def mmd_loss_raw(n, theta, G, A, Z, X, precision="split_bf16", unbiased=True, with_grad=False, sqrt_loss=False,
+                 indep=False):
+    """MMD^2 (or its square root with sqrt_loss) and optionally its gradient.
+    indep: observable a uses its own samples, rows a*s..a*s+s-1 of Z."""
     for t, nm in ((G, "G"), (A, "A"), (Z, "Z"), (X, "X")):
         _bits(t, nm)
     th = _theta32(theta)
-    m, l, s, N = G.shape[0], A.shape[0], Z.shape[0], X.shape[0]
+    m, l, N = G.shape[0], A.shape[0], X.shape[0]
+    if indep and Z.shape[0] % l:
+        raise ValueError("indep: Z must have l * s rows")
+    s = Z.shape[0] // l if indep else Z.shape[0]
     prec = precision_code(precision)
     lib = _lib.load()
-    op = OP_MMD_LOSS_GRAD if with_grad else OP_MMD_LOSS
+    if indep:
+        op = OP_MMD_LOSS_GRAD_INDEP if with_grad else OP_MMD_LOSS_INDEP
+    else:
+        op = OP_MMD_LOSS_GRAD if with_grad else OP_MMD_LOSS
+    flags = (MMD_UNBIASED if unbiased else 0) | (MMD_SQRT if sqrt_loss else 0) | (MMD_INDEP if indep else 0)
     ws = _WS.get(lib.iqp_workspace_bytes(op, n, m, l, s, N, prec), G.device)
     loss = torch.empty(1, dtype=torch.float64, device=G.device)
     st = ctypes.c_void_p(_stream(G.device))
     args = (n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(Z), s, Z.shape[1], _ptr(X), N, X.shape[1],
-            _ptr(th), prec, 1 if unbiased else 0)
+            _ptr(th), prec, flags)
     if with_grad:
         grad = torch.empty(m, dtype=torch.float64, device=G.device)
         check(lib.iqp_mmd_loss_grad(*args, _ptr(loss), _ptr(grad), _ptr(ws), ws.numel(), st), "iqp_mmd_loss_grad")
@@ -195,8 +207,9 @@ def mmd_loss_raw(n, theta, G, A, Z, X, precision="split_bf16", unbiased=True, wi
 
 class _MmdFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, theta, G, A, Z, X, n, precision, unbiased):
-        loss, grad = mmd_loss_raw(n, theta, G, A, Z, X, precision, unbiased, with_grad=theta.requires_grad)
+    def forward(ctx, theta, G, A, Z, X, n, precision, unbiased, sqrt_loss, indep):
+        loss, grad = mmd_loss_raw(n, theta, G, A, Z, X, precision, unbiased, with_grad=theta.requires_grad,
+                                  sqrt_loss=sqrt_loss, indep=indep)
         ctx.save_for_backward(grad if grad is not None else torch.empty(0, device=theta.device))
         ctx.theta_dtype = theta.dtype
         return loss
@@ -204,14 +217,153 @@ class _MmdFn(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         (grad,) = ctx.saved_tensors
-        return (g.to(torch.float64) * grad).to(ctx.theta_dtype), None, None, None, None, None, None, None
+        return (g.to(torch.float64) * grad).to(ctx.theta_dtype), None, None, None, None, None, None, None, None, None
 
 
-def mmd_loss(theta, G, A, Z, X, n: int, precision="split_bf16", unbiased=True):
+def mmd_loss(theta, G, A, Z, X, n: int, precision="split_bf16", unbiased=True, sqrt_loss=False, indep=False):
     """MMD^2 estimate (float64 scalar tensor), differentiable in theta: the loss
     and its gradient come from one library call (the backward recomputes Phi
-    tile by tile inside it)."""
-    return _MmdFn.apply(theta, G, A, Z, X, n, precision, unbiased)
+    tile by tile inside it). sqrt_loss returns sqrt(max(MMD^2, 0)); indep uses
+    one sample batch per observable (Z with l * s rows)."""
+    return _MmdFn.apply(theta, G, A, Z, X, n, precision, unbiased, sqrt_loss, indep)
+
+
+# ------------------------------------------------------ independent batches
+
+def expval_indep_raw(n, theta, G, A, Z):
+    """(expval, std_err) with one sample batch per observable: observable a
+    uses rows a*s..a*s+s-1 of Z (Z has l * s rows). No autograd."""
+    for t, nm in ((G, "G"), (A, "A"), (Z, "Z")):
+        _bits(t, nm)
+    th = _theta32(theta)
+    m, l = G.shape[0], A.shape[0]
+    if Z.shape[0] % l:
+        raise ValueError("Z must have l * s rows")
+    s = Z.shape[0] // l
+    lib = _lib.load()
+    ws = _WS.get(lib.iqp_workspace_bytes(OP_EXPVAL_INDEP, n, m, l, s, 0, SPARSE_FP32), G.device)
+    ev = torch.empty(l, dtype=torch.float64, device=G.device)
+    se = torch.empty(l, dtype=torch.float64, device=G.device)
+    check(lib.iqp_expval_indep(n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(Z), s, Z.shape[1], _ptr(th),
+                               _ptr(ev), _ptr(se), _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(G.device))),
+          "iqp_expval_indep")
+    return ev, se
+
+
+def expval_indep_grad(n, theta, G, A, Z, alpha, beta=None) -> torch.Tensor:
+    """Gradient of the independent-batch estimator (alpha/beta as in expval_grad)."""
+    for t, nm in ((G, "G"), (A, "A"), (Z, "Z")):
+        _bits(t, nm)
+    th = _theta32(theta)
+    m, l = G.shape[0], A.shape[0]
+    s = Z.shape[0] // l
+    al = alpha.detach().to(device=G.device, dtype=torch.float64).contiguous()
+    be = None if beta is None else beta.detach().to(device=G.device, dtype=torch.float64).contiguous()
+    lib = _lib.load()
+    ws = _WS.get(lib.iqp_workspace_bytes(OP_EXPVAL_INDEP_GRAD, n, m, l, s, 0, SPARSE_FP32), G.device)
+    grad = torch.empty(m, dtype=torch.float64, device=G.device)
+    check(lib.iqp_expval_indep_grad(n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(Z), s, Z.shape[1],
+                                    _ptr(th), _ptr(al), _ptr(be), _ptr(grad), _ptr(ws), ws.numel(),
+                                    ctypes.c_void_p(_stream(G.device))), "iqp_expval_indep_grad")
+    return grad
+
+
+class _ExpvalIndepFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta, G, A, Z, n):
+        ev, se = expval_indep_raw(n, theta, G, A, Z)
+        ctx.save_for_backward(theta, G, A, Z)
+        ctx.n = n
+        ctx.mark_non_differentiable(se)
+        return ev, se
+
+    @staticmethod
+    def backward(ctx, g_ev, g_se):
+        theta, G, A, Z = ctx.saved_tensors
+        if g_ev is None:
+            return (None,) * 5
+        s = Z.shape[0] // A.shape[0]
+        grad = expval_indep_grad(ctx.n, theta, G, A, Z, -g_ev.to(torch.float64) / s, None)
+        return grad.to(theta.dtype), None, None, None, None
+
+
+def expval_indep(theta, G, A, Z, n: int):
+    """indep_estimates: <Z_a> and standard errors with one sample batch per
+    observable (uncorrelated estimates), differentiable in theta."""
+    return _ExpvalIndepFn.apply(theta, G, A, Z, n)
+
+
+# ----------------------------------------------- shared-parameter gates
+
+def _start_dev(start, device) -> torch.Tensor:
+    st = torch.as_tensor(start, dtype=torch.int64)
+    return st.to(device).contiguous()
+
+
+class _ExpandFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, theta_p, start, m):
+        th = _theta32(theta_p)
+        out = torch.empty(m, dtype=torch.float32, device=th.device)
+        check(_lib.load().iqp_expand_params(_ptr(th), th.shape[0], _ptr(start), _ptr(out), m,
+                                            ctypes.c_void_p(_stream(th.device))), "iqp_expand_params")
+        ctx.save_for_backward(start)
+        ctx.np, ctx.m, ctx.dtype = th.shape[0], m, theta_p.dtype
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        (start,) = ctx.saved_tensors
+        gg = g.detach().to(torch.float64).contiguous()
+        out = torch.empty(ctx.np, dtype=torch.float64, device=gg.device)
+        check(_lib.load().iqp_reduce_params(_ptr(gg), ctx.m, _ptr(start), ctx.np, _ptr(out),
+                                            ctypes.c_void_p(_stream(gg.device))), "iqp_reduce_params")
+        return out.to(ctx.dtype), None, None
+
+
+def expand_params(theta_p, start, m: int):
+    """Shared-parameter gates (Sec. 3.1.1): per-generator parameters from one
+    parameter per gate; gate p owns generator rows start[p]..start[p+1]-1.
+    Differentiable: the gradient of a gate is the sum over its generators."""
+    return _ExpandFn.apply(theta_p, _start_dev(start, theta_p.device), m)
+
+
+# ---------------------------------------------------------- wires, RNG
+
+def embed_bits(src: torch.Tensor, nw: int, wires, n: int) -> torch.Tensor:
+    """Rows on nw wire qubits -> rows on n qubits (bit k -> qubit wires[k])."""
+    _bits(src, "src")
+    w = torch.as_tensor(wires, dtype=torch.int32).to(src.device).contiguous()
+    ld = words_per_row(n)
+    out = torch.empty(src.shape[0], ld, dtype=torch.int64, device=src.device)
+    check(_lib.load().iqp_embed_bits(_ptr(src), src.shape[0], src.shape[1], _ptr(w), nw, _ptr(out), ld, n,
+                                     ctypes.c_void_p(_stream(src.device))), "iqp_embed_bits")
+    return out
+
+
+def words_per_row(n: int) -> int:
+    w = max(1, (n + 63) // 64)
+    return w + (w & 1)
+
+
+def uniform_bits(seed: int, stream: int, rows: int, n: int, device="cuda") -> torch.Tensor:
+    """Uniform bitstrings drawn on the device (same bits as
+    inputs.uniform_bits(Rng(seed), rows, n, stream))."""
+    ld = words_per_row(n)
+    out = torch.empty(rows, ld, dtype=torch.int64, device=device)
+    check(_lib.load().iqp_uniform_bits(seed & (2 ** 64 - 1), stream & (2 ** 64 - 1), rows, n, _ptr(out), ld,
+                                       ctypes.c_void_p(_stream(device))), "iqp_uniform_bits")
+    return out
+
+
+def bernoulli_bits(seed: int, stream: int, rows: int, n: int, p: float, device="cuda") -> torch.Tensor:
+    """Bernoulli(p) bits drawn on the device (same bits as
+    inputs.bernoulli_bits(Rng(seed), rows, n, p, stream))."""
+    ld = words_per_row(n)
+    out = torch.empty(rows, ld, dtype=torch.int64, device=device)
+    check(_lib.load().iqp_bernoulli_bits(seed & (2 ** 64 - 1), stream & (2 ** 64 - 1), rows, n, float(p),
+                                         _ptr(out), ld, ctypes.c_void_p(_stream(device))), "iqp_bernoulli_bits")
+    return out
 
 
 def bitflip_expval_raw(n, theta, G, A):

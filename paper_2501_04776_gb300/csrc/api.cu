@@ -30,7 +30,7 @@ cudaError_t launch_finalize(const double2 *part, int64_t nparts, int64_t pw, int
                             double *std_err, double *S1, double *S2, cudaStream_t st);
 cudaError_t launch_grad_reduce(const double *gpart, int64_t ntiles, int64_t m, double *grad, cudaStream_t st);
 cudaError_t launch_mmd_combine(const int64_t *T, const double *S1, const double *S2, int64_t l, int64_t s, int64_t N,
-                               int unbiased, double *terms, double *alpha, double *beta, double *loss,
+                               int unbiased, bool sqrt_loss, double *terms, double *alpha, double *beta, double *loss,
                                cudaStream_t st);
 cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alpha, const double *beta,
                             cudaStream_t st, iqp_status *why);
@@ -38,11 +38,25 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st);
 int64_t sparse_part_samples();
 cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
-                                int64_t l, int64_t s, double2 *part, int64_t nparts, cudaStream_t st);
+                                int64_t l, int64_t s, double2 *part, int64_t nparts, const SparseIndep *indep,
+                                cudaStream_t st);
 cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
                                int64_t l, int64_t s, int64_t m, int64_t nparts, const double *alpha,
                                const double *beta, double *scale, unsigned long long *gfx, double *grad,
-                               cudaStream_t st);
+                               const SparseIndep *indep, cudaStream_t st);
+cudaError_t launch_bit_transpose_batched(const uint64_t *in, int64_t batch, int64_t in_rows, int64_t in_cols,
+                                         int64_t ld_in, uint64_t *out, int64_t ld_out, cudaStream_t st);
+cudaError_t launch_support_list(const uint64_t *G, int64_t m, int64_t ldg, int64_t n, int4 *sup, cudaStream_t st);
+cudaError_t launch_expand_params(const float *theta_p, int64_t np, const int64_t *start, int64_t m, float *theta_gen,
+                                 cudaStream_t st);
+cudaError_t launch_reduce_params(const double *grad_gen, int64_t m, const int64_t *start, int64_t np,
+                                 double *grad_p, cudaStream_t st);
+cudaError_t launch_embed_bits(const uint64_t *src, int64_t rows, int64_t ld_src, const int32_t *wires, int64_t nw,
+                              uint64_t *dst, int64_t ld_dst, int64_t n, cudaStream_t st);
+cudaError_t launch_uniform_bits(uint64_t seed, uint64_t stream, int64_t rows, int64_t n, int64_t ld, uint64_t *out,
+                                cudaStream_t st);
+cudaError_t launch_bernoulli_bits(uint64_t seed, uint64_t stream, int64_t rows, int64_t n, double p, int64_t ld,
+                                  uint64_t *out, cudaStream_t st);
 cudaError_t launch_bitflip_gates(const float *theta, int64_t m, int64_t mpad, double *c, double *t, cudaStream_t st);
 cudaError_t launch_bitflip_rows(const uint64_t *PA, int64_t ldp, int64_t l, const double *c, double *expval,
                                 cudaStream_t st);
@@ -54,6 +68,8 @@ cudaError_t launch_bitflip_grad(const uint64_t *PAT, int64_t ldlt, int64_t m, in
 Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec) {
     Plan p;
     std::memset(&p, 0, sizeof(p));
+    p.indep = op >= IQP_OP_EXPVAL_INDEP && op <= IQP_OP_MMD_LOSS_GRAD_INDEP;
+    if (p.indep) prec = IQP_SPARSE_FP32;  // the independent-batch estimator is row-sparse FP32
     p.op = op;
     p.prec = prec;
     p.n = n;
@@ -69,9 +85,11 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.pw = prec == IQP_SPLIT_BF16 ? kPartColsTc : (prec == IQP_SPARSE_FP32 ? sparse_part_samples() : kPartColsSimt);
     p.nparts = cdiv(s, p.pw);
     p.natile = cdiv(l, kATile);
-    const bool grad = op == IQP_OP_EXPVAL_GRAD || op == IQP_OP_MMD_LOSS_GRAD;
-    const bool mmd = op == IQP_OP_MMD_LOSS || op == IQP_OP_MMD_LOSS_GRAD;
-    const bool tc = prec == IQP_SPLIT_BF16;
+    const bool grad = op == IQP_OP_EXPVAL_GRAD || op == IQP_OP_MMD_LOSS_GRAD || op == IQP_OP_EXPVAL_INDEP_GRAD ||
+                      op == IQP_OP_MMD_LOSS_GRAD_INDEP;
+    const bool mmd = op == IQP_OP_MMD_LOSS || op == IQP_OP_MMD_LOSS_GRAD || op == IQP_OP_MMD_LOSS_INDEP ||
+                     op == IQP_OP_MMD_LOSS_GRAD_INDEP;
+    const bool indep = p.indep;
     const bool bitflip = op == IQP_OP_BITFLIP;
     const bool sparse = prec == IQP_SPARSE_FP32 && !bitflip;
     size_t off = 0;
@@ -83,7 +101,7 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_status = take(256);
     p.off_pa = take(l * p.ldp * 8);
     p.off_pz = take(bitflip || sparse ? 0 : s * p.ldp * 8);
-    p.off_pzt = take(bitflip ? 0 : m * p.ldzt * 8);
+    p.off_pzt = take(bitflip || indep ? 0 : m * p.ldzt * 8);
     p.off_pat = take(m * p.ldlt * 8);
     p.off_rt = take(n * (p.ldzt > p.ldlt ? p.ldzt : p.ldlt) * 8);
     p.off_c = take(bitflip ? p.mpad * 16 : p.mpad * 4);  // bitflip: cos(2 theta), -2 tan(2 theta) in FP64
@@ -95,6 +113,8 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_s12 = take(mmd ? l * 16 : 0);
     p.off_T = take(mmd ? l * 8 : 0);
     p.off_terms = take(mmd ? l * 8 : 0);
+    p.off_zt = take(indep ? l * n * p.ldzt * 8 : 0);  // every batch transposed: n rows of bits over samples
+    p.off_sup = take(indep ? m * 16 : 0);             // int4 support list per gate
     p.total = off;
     return p;
 }
@@ -209,11 +229,19 @@ T *at(void *ws, size_t off) {
     } while (0)
 
 // Parities of A and Z by support gather (P_A, P_A^T, P_Z, P_Z^T) + theta split.
+// Independent batches: P_A, every batch of Z transposed, and the gate
+// supports (the sample parities are formed inside the row-sparse kernels).
 iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, const uint64_t *A, int64_t lda,
                    const uint64_t *Z, int64_t ldz, const float *theta, cudaStream_t st) {
     uint64_t *rt = at<uint64_t>(ws, p.off_rt);
     IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
                                  at<uint64_t>(ws, p.off_pat), p.ldlt, rt, st));
+    if (p.indep) {
+        IQP_TRY(launch_bit_transpose_batched(Z, p.l, p.s, p.n, ldz, at<uint64_t>(ws, p.off_zt), p.ldzt, st));
+        IQP_TRY(launch_support_list(G, p.m, ldg, p.n, at<int4>(ws, p.off_sup), st));
+        IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, at<float>(ws, p.off_c), nullptr, nullptr, st));
+        return IQP_OK;
+    }
     // The sparse form reads only P_Z^T (bits over samples).
     IQP_TRY(launch_parity_gather(p.n, Z, p.s, ldz, G, p.m, ldg,
                                  p.prec == IQP_SPARSE_FP32 ? nullptr : at<uint64_t>(ws, p.off_pz), p.ldp,
@@ -236,8 +264,10 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
         if (launch_phase_tc(0, p, ws, nullptr, nullptr, st, &why) != cudaSuccess)
             return why != IQP_OK ? why : IQP_ERR_CUDA;
     } else if (p.prec == IQP_SPARSE_FP32) {
-        IQP_TRY(launch_sparse_stats(at<uint64_t>(ws, p.off_pa), p.ldp, at<uint64_t>(ws, p.off_pzt), p.ldzt,
-                                    at<float>(ws, p.off_c), p.l, p.s, part, p.nparts, st));
+        const SparseIndep ind{at<int4>(ws, p.off_sup), p.G, p.ldg, p.n};
+        IQP_TRY(launch_sparse_stats(at<uint64_t>(ws, p.off_pa), p.ldp,
+                                    at<uint64_t>(ws, p.indep ? p.off_zt : p.off_pzt), p.ldzt, at<float>(ws, p.off_c),
+                                    p.l, p.s, part, p.nparts, p.indep ? &ind : nullptr, st));
     } else {
         IQP_TRY(launch_phase_simt(0, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pz), p.ldp,
                                   at<float>(ws, p.off_c), p.l, p.s, p.m, part, p.nparts, nullptr, nullptr, nullptr, 0,
@@ -253,9 +283,11 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
     double *gpart = at<double>(ws, p.off_gpart);
     if (p.prec == IQP_SPARSE_FP32) {
         unsigned long long *gfx = at<unsigned long long>(ws, p.off_gpart);
-        IQP_TRY(launch_sparse_grad(at<uint64_t>(ws, p.off_pa), p.ldp, at<uint64_t>(ws, p.off_pzt), p.ldzt,
-                                   at<float>(ws, p.off_c), p.l, p.s, p.m, p.nparts, alpha, beta,
-                                   reinterpret_cast<double *>(gfx + p.m), gfx, grad, st));
+        const SparseIndep ind{at<int4>(ws, p.off_sup), p.G, p.ldg, p.n};
+        IQP_TRY(launch_sparse_grad(at<uint64_t>(ws, p.off_pa), p.ldp,
+                                   at<uint64_t>(ws, p.indep ? p.off_zt : p.off_pzt), p.ldzt, at<float>(ws, p.off_c),
+                                   p.l, p.s, p.m, p.nparts, alpha, beta, reinterpret_cast<double *>(gfx + p.m), gfx,
+                                   grad, p.indep ? &ind : nullptr, st));
         return IQP_OK;
     }
     if (p.prec == IQP_SPLIT_BF16) {
@@ -275,25 +307,34 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
 
 iqp_status mmd_core(int op, int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
                     int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const uint64_t *X, int64_t N,
-                    int64_t ldx, const float *theta, iqp_precision prec, int unbiased, double *loss, double *grad,
+                    int64_t ldx, const float *theta, iqp_precision prec, int flags, double *loss, double *grad,
                     void *ws, size_t ws_bytes, void *stream) {
-    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta,
+                                 (flags & IQP_MMD_INDEP) ? IQP_SPARSE_FP32 : prec);
     if (rc != IQP_OK) return rc;
     if ((rc = check_bits(X, N, ldx, n)) != IQP_OK) return rc;
     if (loss == nullptr || !aligned(loss, 8)) return IQP_ERR_ARG;
     if (op == IQP_OP_MMD_LOSS_GRAD && (grad == nullptr || !aligned(grad, 8))) return IQP_ERR_ARG;
+    if (flags & ~(IQP_MMD_UNBIASED | IQP_MMD_SQRT | IQP_MMD_INDEP)) return IQP_ERR_ARG;
+    const int unbiased = flags & IQP_MMD_UNBIASED;
     if (unbiased && (s < 2 || N < 2)) return IQP_ERR_ARG;
-    const Plan p = make_plan(op, n, m, l, s, N, prec);
+    const bool indep = (flags & IQP_MMD_INDEP) != 0;
+    if (indep && l > INT32_MAX / 2) return IQP_ERR_ARG;
+    const bool g = op == IQP_OP_MMD_LOSS_GRAD;
+    const int pop = indep ? (g ? IQP_OP_MMD_LOSS_GRAD_INDEP : IQP_OP_MMD_LOSS_INDEP) : op;
+    Plan p = make_plan(pop, n, m, l, s, N, prec);
+    p.G = G;
+    p.ldg = ldg;
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const bool g = op == IQP_OP_MMD_LOSS_GRAD;
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
     double *S1 = at<double>(ws, p.off_s12), *S2 = S1 + l;
     if ((rc = forward_stats(p, ws, nullptr, nullptr, S1, S2, st)) != IQP_OK) return rc;
     int64_t *T = at<int64_t>(ws, p.off_T);
     IQP_TRY(launch_parity_sum(n, A, l, lda, X, N, ldx, T, st));
     double *alpha = at<double>(ws, p.off_ab), *beta = alpha + l;
-    IQP_TRY(launch_mmd_combine(T, S1, S2, l, s, N, unbiased, at<double>(ws, p.off_terms), alpha, beta, loss, st));
+    IQP_TRY(launch_mmd_combine(T, S1, S2, l, s, N, unbiased, (flags & IQP_MMD_SQRT) != 0,
+                               at<double>(ws, p.off_terms), alpha, beta, loss, st));
     if (g) return backward(p, ws, alpha, beta, grad, st);
     return IQP_OK;
 }
@@ -318,7 +359,7 @@ extern "C" {
 
 size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, iqp_precision prec) {
     if (n < 1 || m < 1 || l < 1 || s < 1) return 0;
-    if (op < IQP_OP_EXPVAL || op > IQP_OP_BITFLIP) return 0;
+    if (op < IQP_OP_EXPVAL || op > IQP_OP_MMD_LOSS_GRAD_INDEP) return 0;
     if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32) return 0;
     return make_plan(op, n, m, l, s, N, prec).total;
 }
@@ -403,6 +444,86 @@ iqp_status iqp_mmd_loss_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ld
                              double *grad, void *ws, size_t ws_bytes, void *stream) {
     return mmd_core(IQP_OP_MMD_LOSS_GRAD, n, G, m, ldg, A, l, lda, Z, s, ldz, X, N, ldx, theta, prec, unbiased, loss,
                     grad, ws, ws_bytes, stream);
+}
+
+namespace {
+
+iqp_status indep_core(int op, int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                      int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta, double *expval,
+                      double *std_err, const double *alpha, const double *beta, double *grad, void *ws,
+                      size_t ws_bytes, void *stream) {
+    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, IQP_SPARSE_FP32);
+    if (rc != IQP_OK) return rc;
+    if (l > INT32_MAX / 2) return IQP_ERR_ARG;
+    Plan p = make_plan(op, n, m, l, s, 0, IQP_SPARSE_FP32);
+    p.G = G;
+    p.ldg = ldg;
+    if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
+    if (op == IQP_OP_EXPVAL_INDEP) return forward_stats(p, ws, expval, std_err, nullptr, nullptr, st);
+    return backward(p, ws, alpha, beta, grad, st);
+}
+
+}  // namespace
+
+iqp_status iqp_expval_indep(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                            int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                            double *expval, double *std_err, void *ws, size_t ws_bytes, void *stream) {
+    if ((expval && !aligned(expval, 8)) || (std_err && !aligned(std_err, 8))) return IQP_ERR_ALIGN;
+    return indep_core(IQP_OP_EXPVAL_INDEP, n, G, m, ldg, A, l, lda, Z, s, ldz, theta, expval, std_err, nullptr,
+                      nullptr, nullptr, ws, ws_bytes, stream);
+}
+
+iqp_status iqp_expval_indep_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                                 int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                                 const double *alpha, const double *beta, double *grad, void *ws, size_t ws_bytes,
+                                 void *stream) {
+    if (alpha == nullptr || grad == nullptr) return IQP_ERR_ARG;
+    if (!aligned(alpha, 8) || !aligned(grad, 8) || (beta && !aligned(beta, 8))) return IQP_ERR_ALIGN;
+    return indep_core(IQP_OP_EXPVAL_INDEP_GRAD, n, G, m, ldg, A, l, lda, Z, s, ldz, theta, nullptr, nullptr, alpha,
+                      beta, grad, ws, ws_bytes, stream);
+}
+
+iqp_status iqp_expand_params(const float *theta_p, int64_t np, const int64_t *start, float *theta_gen, int64_t m,
+                             void *stream) {
+    if (np < 1 || m < 1 || theta_p == nullptr || start == nullptr || theta_gen == nullptr) return IQP_ERR_ARG;
+    if (!aligned(theta_p, 4) || !aligned(theta_gen, 4) || !aligned(start, 8)) return IQP_ERR_ALIGN;
+    return cuda_status(launch_expand_params(theta_p, np, start, m, theta_gen, static_cast<cudaStream_t>(stream)));
+}
+
+iqp_status iqp_reduce_params(const double *grad_gen, int64_t m, const int64_t *start, int64_t np, double *grad_p,
+                             void *stream) {
+    if (np < 1 || m < 1 || grad_gen == nullptr || start == nullptr || grad_p == nullptr) return IQP_ERR_ARG;
+    if (!aligned(grad_gen, 8) || !aligned(grad_p, 8) || !aligned(start, 8)) return IQP_ERR_ALIGN;
+    return cuda_status(launch_reduce_params(grad_gen, m, start, np, grad_p, static_cast<cudaStream_t>(stream)));
+}
+
+iqp_status iqp_embed_bits(const uint64_t *src, int64_t rows, int64_t ld_src, const int32_t *wires, int64_t nw,
+                          uint64_t *dst, int64_t ld_dst, int64_t n, void *stream) {
+    if (nw < 1 || n < 1 || wires == nullptr) return IQP_ERR_ARG;
+    iqp_status rc;
+    if ((rc = check_bits(src, rows, ld_src, nw)) != IQP_OK) return rc;
+    if ((rc = check_bits(dst, rows, ld_dst, n)) != IQP_OK) return rc;
+    if (!aligned(wires, 4)) return IQP_ERR_ALIGN;
+    return cuda_status(
+        launch_embed_bits(src, rows, ld_src, wires, nw, dst, ld_dst, n, static_cast<cudaStream_t>(stream)));
+}
+
+iqp_status iqp_uniform_bits(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t n, uint64_t *out, int64_t ld,
+                            void *stream) {
+    if (n < 1) return IQP_ERR_ARG;
+    iqp_status rc;
+    if ((rc = check_bits(out, rows, ld, n)) != IQP_OK) return rc;
+    return cuda_status(launch_uniform_bits(seed, stream_id, rows, n, ld, out, static_cast<cudaStream_t>(stream)));
+}
+
+iqp_status iqp_bernoulli_bits(uint64_t seed, uint64_t stream_id, int64_t rows, int64_t n, double p, uint64_t *out,
+                              int64_t ld, void *stream) {
+    if (n < 1 || !(p >= 0.0 && p <= 1.0)) return IQP_ERR_ARG;
+    iqp_status rc;
+    if ((rc = check_bits(out, rows, ld, n)) != IQP_OK) return rc;
+    return cuda_status(launch_bernoulli_bits(seed, stream_id, rows, n, p, ld, out, static_cast<cudaStream_t>(stream)));
 }
 
 namespace {

@@ -35,7 +35,18 @@ struct Plan {
     int64_t nparts; // (S, M2) partials per observable: ceil(s / pw)
     int64_t natile; // ceil(l / 128)
     size_t off_status, off_pa, off_pz, off_pzt, off_pat, off_rt, off_c, off_part, off_w, off_gpart;
-    size_t off_ab, off_s12, off_T, off_terms, total;
+    size_t off_ab, off_s12, off_T, off_terms, off_zt, off_sup, total;
+    bool indep;     // one sample batch per observable (Z has l * s rows)
+    const uint64_t *G;  // generators (read by the independent-batch kernels)
+    int64_t ldg;
+};
+
+// Independent-batch arguments of the row-sparse kernels.
+struct SparseIndep {
+    const int4 *sup;    // per gate: first three support qubits and |supp|
+    const uint64_t *G;  // generators, for |supp| > 3
+    int64_t ldg;
+    int64_t n;
 };
 
 Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec);

@@ -102,9 +102,13 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
 // in_rows x in_cols bits with ld_in32 words per row. Output words beyond
 // in_rows bits are written as zero; output rows >= in_cols are not written.
 // Tile: 256 x 256 bits per block; each warp transposes 32 rows by ballots.
+// Batched over blockIdx.y: matrix b starts at in + b in_bs32 / out + b out_bs32.
 __global__ void __launch_bounds__(256) k_bit_transpose(const uint32_t *__restrict__ in, int64_t in_rows,
                                                         int64_t in_cols, int64_t ld_in32,
-                                                        uint32_t *__restrict__ out, int64_t ld_out32, int64_t gx) {
+                                                        uint32_t *__restrict__ out, int64_t ld_out32, int64_t gx,
+                                                        int64_t in_bs32, int64_t out_bs32) {
+    in += (int64_t)blockIdx.y * in_bs32;
+    out += (int64_t)blockIdx.y * out_bs32;
     __shared__ uint32_t tin[256][9];
     __shared__ uint32_t tout[256][9];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -188,11 +192,70 @@ cudaError_t bit_transpose(const uint64_t *in, int64_t in_rows, int64_t in_cols, 
     if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
     LaunchScope ls(IQP_KERNEL_PARITY, st);
     k_bit_transpose<<<(unsigned)(gx * gy), 256, 0, st>>>(reinterpret_cast<const uint32_t *>(in), in_rows, in_cols,
-                                                          2 * ld_in, reinterpret_cast<uint32_t *>(out), 2 * ld_out, gx);
+                                                          2 * ld_in, reinterpret_cast<uint32_t *>(out), 2 * ld_out, gx,
+                                                          0, 0);
     return cudaGetLastError();
 }
 
+// Support list of every generator: (q0, q1, q2, |supp g_j|), the first three
+// qubits of its support in increasing order. One warp per generator.
+__global__ void __launch_bounds__(256) k_support_list(const uint64_t *__restrict__ G, int64_t m, int64_t ldg,
+                                                       int64_t n, int4 *__restrict__ sup) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= m) return;
+    const int64_t nw = (n + 63) >> 6;
+    int cnt = 0, q0 = 0, q1 = 0, q2 = 0;
+    for (int64_t wb = 0; wb < nw; wb += 32) {
+        const uint64_t word = (wb + lane < nw) ? G[j * ldg + wb + lane] : 0ull;
+        uint32_t nz = __ballot_sync(0xFFFFFFFFu, word != 0ull);
+        while (nz) {
+            const int src = __ffs(nz) - 1;
+            nz &= nz - 1u;
+            uint64_t wv = __shfl_sync(0xFFFFFFFFu, word, src);
+            while (wv) {
+                const int b = __ffsll((long long)wv) - 1;
+                wv &= wv - 1ull;
+                const int64_t q = 64 * (wb + src) + b;
+                if (q >= n) break;
+                if (cnt == 0) q0 = (int)q;
+                else if (cnt == 1) q1 = (int)q;
+                else if (cnt == 2) q2 = (int)q;
+                ++cnt;
+            }
+        }
+    }
+    if (lane == 0) sup[j] = make_int4(q0, q1, q2, cnt);
+}
+
 }  // namespace
+
+// Transposes `batch` bit matrices of in_rows x in_cols bits (ld_in words per
+// row, consecutive in memory) into in_cols x (64 ld_out) bits each, also
+// consecutive: matrix b of the output starts at out + b in_cols ld_out.
+cudaError_t launch_bit_transpose_batched(const uint64_t *in, int64_t batch, int64_t in_rows, int64_t in_cols,
+                                         int64_t ld_in, uint64_t *out, int64_t ld_out, cudaStream_t st) {
+    const int64_t gx = cdiv(ld_out * 64, 256);
+    const int64_t gy = cdiv(in_cols, 256);
+    if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+    for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
+        const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
+        LaunchScope ls(IQP_KERNEL_PARITY, st);
+        k_bit_transpose<<<dim3((unsigned)(gx * gy), (unsigned)nb), 256, 0, st>>>(
+            reinterpret_cast<const uint32_t *>(in + b0 * in_rows * ld_in), in_rows, in_cols, 2 * ld_in,
+            reinterpret_cast<uint32_t *>(out + b0 * in_cols * ld_out), 2 * ld_out, gx, 2 * in_rows * ld_in,
+            2 * in_cols * ld_out);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_support_list(const uint64_t *G, int64_t m, int64_t ldg, int64_t n, int4 *sup, cudaStream_t st) {
+    LaunchScope ls(IQP_KERNEL_PARITY, st);
+    k_support_list<<<(unsigned)cdiv(m, 8), 256, 0, st>>>(G, m, ldg, n, sup);
+    return cudaGetLastError();
+}
 
 // Support-gather parities: RT (n x ldpt words) is scratch; writes PT
 // (m x ldpt words: bits over rows, zero beyond `rows`) and, if P != nullptr,

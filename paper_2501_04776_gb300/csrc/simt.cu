@@ -283,9 +283,11 @@ __global__ void k_grad_reduce(const double *__restrict__ gpart, int64_t ntiles, 
 }
 
 // MMD^2 of eq. mmd_estimate and the gradient coefficients alpha, beta.
+// sqrt_loss: loss' = sqrt(max(loss, 0)) and alpha, beta scaled by 1/(2 loss')
+// (chain rule; zero where loss' = 0).
 __global__ void __launch_bounds__(1024) k_mmd_combine(const long long *__restrict__ T, const double *__restrict__ S1,
                                                       const double *__restrict__ S2, int64_t l, int64_t s, int64_t N,
-                                                      int unbiased, double *__restrict__ terms,
+                                                      int unbiased, int sqrt_loss, double *__restrict__ terms,
                                                       double *__restrict__ alpha, double *__restrict__ beta,
                                                       double *__restrict__ loss) {
     __shared__ double red[1024];
@@ -317,7 +319,18 @@ __global__ void __launch_bounds__(1024) k_mmd_combine(const long long *__restric
         if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *loss = red[0] / dl;
+    const double L = red[0] / dl;
+    if (!sqrt_loss) {
+        if (threadIdx.x == 0) *loss = L;
+        return;
+    }
+    const double r = L > 0.0 ? sqrt(L) : 0.0;
+    const double f = L > 0.0 ? 0.5 / r : 0.0;
+    for (int64_t a = threadIdx.x; a < l; a += blockDim.x) {
+        if (alpha) alpha[a] *= f;
+        if (beta) beta[a] *= f;
+    }
+    if (threadIdx.x == 0) *loss = r;
 }
 
 // alpha_a = -w_a / s for a linear loss given weights (device helper).
@@ -391,11 +404,11 @@ cudaError_t launch_grad_reduce(const double *gpart, int64_t ntiles, int64_t m, d
 }
 
 cudaError_t launch_mmd_combine(const int64_t *T, const double *S1, const double *S2, int64_t l, int64_t s, int64_t N,
-                               int unbiased, double *terms, double *alpha, double *beta, double *loss,
+                               int unbiased, bool sqrt_loss, double *terms, double *alpha, double *beta, double *loss,
                                cudaStream_t st) {
     LaunchScope ls(IQP_KERNEL_MMD_COMBINE, st);
-    k_mmd_combine<<<1, 1024, 0, st>>>(reinterpret_cast<const long long *>(T), S1, S2, l, s, N, unbiased, terms, alpha,
-                                      beta, loss);
+    k_mmd_combine<<<1, 1024, 0, st>>>(reinterpret_cast<const long long *>(T), S1, S2, l, s, N, unbiased,
+                                      sqrt_loss ? 1 : 0, terms, alpha, beta, loss);
     return cudaGetLastError();
 }
 

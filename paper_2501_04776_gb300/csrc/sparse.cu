@@ -83,17 +83,58 @@ __device__ __forceinline__ void for_each_gate(const uint64_t *__restrict__ row, 
     }
 }
 
+// The lane's P_Z^T word of gate j. Shared batch: a load from P_Z^T.
+// Independent batches: the parity is formed here from the observable's own
+// transposed samples ZT (n rows of bits over samples) as the XOR of the rows
+// of the gate's support (listed for |supp| <= 3, else read from G).
+struct ZSource {
+    const uint64_t *PZT;  // shared: P_Z^T; independent: this observable's ZT
+    int64_t ldzt;
+    int64_t word;
+    const int4 *sup;      // independent batches only
+    const uint64_t *G;
+    int64_t ldg;
+    int64_t n;
+
+    template <bool INDEP>
+    __device__ __forceinline__ uint64_t get(int64_t j) const {
+        if (!INDEP) return __ldg(PZT + j * ldzt + word);
+        const int4 sp = __ldg(sup + j);
+        if (sp.w <= 3) {
+            uint64_t z = 0ull;
+            if (sp.w > 0) z = __ldg(PZT + (int64_t)sp.x * ldzt + word);
+            if (sp.w > 1) z ^= __ldg(PZT + (int64_t)sp.y * ldzt + word);
+            if (sp.w > 2) z ^= __ldg(PZT + (int64_t)sp.z * ldzt + word);
+            return z;
+        }
+        uint64_t z = 0ull;
+        const uint64_t *g = G + j * ldg;
+        const int64_t nw = (n + 63) >> 6;
+        for (int64_t w = 0; w < nw; ++w) {
+            uint64_t gv = __ldg(g + w);
+            while (gv) {
+                const int b = __ffsll((long long)gv) - 1;
+                gv &= gv - 1ull;
+                const int64_t q = 64 * w + b;
+                if (q >= n) break;
+                z ^= __ldg(PZT + q * ldzt + word);
+            }
+        }
+        return z;
+    }
+};
+
 // Phi for the lane's 64 samples (sum over J_a, increasing j).
+template <bool INDEP>
 __device__ __forceinline__ void phase_row(float (&acc)[64], const uint64_t *__restrict__ parow, int64_t ldp,
-                                          const uint64_t *__restrict__ PZT, int64_t ldzt, int64_t word,
-                                          const float *__restrict__ c, int lane) {
+                                          const ZSource &zs, const float *__restrict__ c, int lane) {
 #pragma unroll
     for (int k = 0; k < 64; ++k) acc[k] = 0.f;
     uint64_t zp = 0ull;
     uint32_t cp = 0u;
     bool have = false;
     auto visit = [&](int64_t j) {
-        const uint64_t zn = __ldg(PZT + j * ldzt + word);
+        const uint64_t zn = zs.get<INDEP>(j);
         const uint32_t cn = __float_as_uint(__ldg(c + j));
         if (have) add_signed(acc, zp, cp);
         zp = zn;
@@ -106,12 +147,15 @@ __device__ __forceinline__ void phase_row(float (&acc)[64], const uint64_t *__re
 
 // MODE 0: statistics partials. MODE 1: W from the recomputed Phi, then the
 // gradient contributions of every gate of J_a.
-template <int MODE>
+// INDEP: PZT holds every observable's transposed samples (n x ldzt words
+// each, observable a at PZT + a n ldzt) and the parities are formed on the fly.
+template <int MODE, bool INDEP>
 __global__ void __launch_bounds__(256, 2)
     k_sparse(const uint64_t *__restrict__ PA, int64_t ldp, const uint64_t *__restrict__ PZT, int64_t ldzt,
              const float *__restrict__ c, int64_t s, int64_t nparts, double2 *__restrict__ part,
              const double *__restrict__ alpha, const double *__restrict__ beta, const double *__restrict__ scale,
-             unsigned long long *__restrict__ gfx) {
+             unsigned long long *__restrict__ gfx, const int4 *__restrict__ sup, const uint64_t *__restrict__ G,
+             int64_t ldg, int64_t n) {
     const int lane = threadIdx.x & 31;
     const int64_t a = blockIdx.x;
     const int64_t r = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);  // 2048-sample range
@@ -123,9 +167,10 @@ __global__ void __launch_bounds__(256, 2)
     const int64_t i0 = word_raw * 64;
     const int nvalid = !wvalid ? 0 : (s - i0 >= 64 ? 64 : (int)(s - i0));
     const uint64_t *parow = PA + a * ldp;
+    const ZSource zs{INDEP ? PZT + a * n * ldzt : PZT, ldzt, word, sup, G, ldg, n};
 
     float acc[64];
-    phase_row(acc, parow, ldp, PZT, ldzt, word, c, lane);
+    phase_row<INDEP>(acc, parow, ldp, zs, c, lane);
 
     if (MODE == 0) {
         float sum = 0.f;
@@ -163,7 +208,7 @@ __global__ void __launch_bounds__(256, 2)
         uint64_t zp = 0ull;
         int64_t jp = -1;
         auto visit = [&](int64_t j) {
-            const uint64_t zn = __ldg(PZT + j * ldzt + word);
+            const uint64_t zn = zs.get<INDEP>(j);
             if (jp >= 0) {
                 float d = signed_dot(acc, zp);
 #pragma unroll
@@ -223,19 +268,26 @@ dim3 sparse_grid(int64_t l, int64_t nparts, int *threads) {
 
 int64_t sparse_part_samples() { return kWarpSamples; }
 
+// indep != nullptr: independent batches (PZT = every observable's ZT).
 cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
-                                int64_t l, int64_t s, double2 *part, int64_t nparts, cudaStream_t st) {
+                                int64_t l, int64_t s, double2 *part, int64_t nparts, const SparseIndep *indep,
+                                cudaStream_t st) {
     int threads = 0;
     const dim3 grid = sparse_grid(l, nparts, &threads);
     LaunchScope ls(IQP_KERNEL_PHASE_SPARSE, st);
-    k_sparse<0><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, nullptr, nullptr, nullptr, nullptr);
+    if (indep)
+        k_sparse<0, true><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, nullptr, nullptr,
+                                                    nullptr, nullptr, indep->sup, indep->G, indep->ldg, indep->n);
+    else
+        k_sparse<0, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, nullptr, nullptr,
+                                                     nullptr, nullptr, nullptr, nullptr, 0, 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
                                int64_t l, int64_t s, int64_t m, int64_t nparts, const double *alpha,
                                const double *beta, double *scale, unsigned long long *gfx, double *grad,
-                               cudaStream_t st) {
+                               const SparseIndep *indep, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(gfx, 0, (size_t)m * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     {
@@ -247,7 +299,12 @@ cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *
         int threads = 0;
         const dim3 grid = sparse_grid(l, nparts, &threads);
         LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
-        k_sparse<1><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, nullptr, alpha, beta, scale, gfx);
+        if (indep)
+            k_sparse<1, true><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, nullptr, alpha, beta, scale,
+                                                        gfx, indep->sup, indep->G, indep->ldg, indep->n);
+        else
+            k_sparse<1, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, nullptr, alpha, beta,
+                                                         scale, gfx, nullptr, nullptr, 0, 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     int blocks = (int)cdiv(m, 256);

@@ -22,9 +22,13 @@ from . import api, inputs as I
 
 
 def adam_mmd(problem: I.Problem, steps: int, lr: float = 1e-3, precision: str = "split_bf16",
-             unbiased: bool = True, seed: int = 0, device: str = "cuda", log=None):
+             unbiased: bool = True, seed: int = 0, device: str = "cuda", log=None, device_rng: bool = False,
+             sqrt_loss: bool = False, indep: bool = False):
     """Returns (theta, losses). problem.A / problem.Z give the observable and
-    sample counts; fresh ones are drawn every step from seed."""
+    sample counts; fresh ones are drawn every step from seed: on the host
+    (inputs.fresh_*) or, with device_rng, by the library's on-device generator
+    (bit-identical draws). indep draws l * s samples per step, one batch per
+    observable; sqrt_loss trains on sqrt(MMD^2)."""
     n = problem.n
     l, s = problem.A.shape[0], problem.Z.shape[0]
     ps = problem.extra.get("p_sigma", 0.5)
@@ -35,10 +39,15 @@ def adam_mmd(problem: I.Problem, steps: int, lr: float = 1e-3, precision: str = 
     losses = []
     for step in range(steps):
         t0 = time.perf_counter()
-        A = api.to_device_bits(I.fresh_observables(seed, step, l, n, ps), device)
-        Z = api.to_device_bits(I.fresh_samples(seed, step, s, n), device)
+        zrows = l * s if indep else s
+        if device_rng:
+            A = api.bernoulli_bits(seed, 1001 + 2 * step, l, n, ps, device)
+            Z = api.uniform_bits(seed, 1000 + 2 * step, zrows, n, device)
+        else:
+            A = api.to_device_bits(I.fresh_observables(seed, step, l, n, ps), device)
+            Z = api.to_device_bits(I.fresh_samples(seed, step, zrows, n), device)
         opt.zero_grad(set_to_none=True)
-        loss = api.mmd_loss(theta, G, A, Z, X, n, precision, unbiased)
+        loss = api.mmd_loss(theta, G, A, Z, X, n, precision, unbiased, sqrt_loss, indep)
         loss.backward()
         opt.step()
         lv = float(loss.detach())
@@ -57,11 +66,15 @@ def main():
     ap.add_argument("--N", type=int, default=10_000)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--precision", default="split_bf16")
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "sparse_fp32"])
+    ap.add_argument("--device-rng", action="store_true", help="draw samples and observables on the GPU")
+    ap.add_argument("--sqrt-loss", action="store_true")
+    ap.add_argument("--indep", action="store_true", help="one sample batch per observable")
     args = ap.parse_args()
     p = I.mmd_training(n=args.n, l=args.l, s=args.s, N=args.N)
     print(json.dumps({"workload": p.name, "p_sigma": p.extra["p_sigma"], "m": p.m}), flush=True)
-    _, losses = adam_mmd(p, args.steps, args.lr, args.precision, log=lambda r: print(json.dumps(r), flush=True))
+    _, losses = adam_mmd(p, args.steps, args.lr, args.precision, log=lambda r: print(json.dumps(r), flush=True),
+                         device_rng=args.device_rng, sqrt_loss=args.sqrt_loss, indep=args.indep)
     print(json.dumps({"first_loss": losses[0], "last_loss": losses[-1],
                       "mean_first5": float(np.mean(losses[:5])), "mean_last5": float(np.mean(losses[-5:]))}))
 

@@ -578,3 +578,21 @@ def test_indep_grad_matches_central_differences():
     g = oracle.expval_indep_grad(n, G, A, Z, th, -w / s)
     fd = _fd(lambda t: float(np.dot(w, oracle.expval_indep(n, G, A, Z, t)[0])), th)
     assert np.linalg.norm(g - fd) / np.linalg.norm(fd) < 1e-7
+
+
+def test_mmd_indep_with_repeated_batch_equals_shared_batch():
+    """indep_estimates with every observable given the same batch is the
+    shared-batch estimator (loss, terms and gradient)."""
+    rng = I.Rng(61)
+    n = 6
+    G = I.local_gates_packed(n)
+    th = rng.normal(G.shape[0], 1) * 0.3
+    A = I.bernoulli_bits(rng, 5, n, 0.4, 2, nonzero=True)
+    Z = I.uniform_bits(rng, 33, n, 3)
+    X = I.prototype_data(rng, 20, n, 2, 0.1, 4)
+    for unbiased in (True, False):
+        L0, t0, g0 = oracle.mmd_loss(n, G, A, Z, X, th, unbiased, grad=True)
+        L1, t1, g1 = oracle.mmd_loss_ex(n, G, A, np.tile(Z, (A.shape[0], 1)), X, th, unbiased, indep=True,
+                                        grad=True)
+        assert abs(L0 - L1) < 1e-14 and np.max(np.abs(t0 - t1)) < 1e-14
+        assert np.max(np.abs(g0 - g1)) < 1e-12
