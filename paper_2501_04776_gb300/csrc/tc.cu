@@ -87,11 +87,27 @@ struct Cfg {
     static_assert(SMEM <= 232448, "shared memory");
 };
 
+// Tile t -> (row block tm, column block tc), walking `gm` row blocks of one
+// column block before the next column block (the last group may be
+// shorter). The CTAs running at once then share gm row panels and about
+// (CTAs / gm) column panels, which stay in L2: each column panel is read
+// from DRAM once per group instead of once per row block.
+__device__ __forceinline__ void tile_coords(int64_t t, int64_t tiles_m, int64_t tiles_nc, int64_t gm, int64_t &tm,
+                                            int64_t &tc) {
+    const int64_t per = gm * tiles_nc;
+    const int64_t g = t / per;
+    const int64_t r = t - g * per;
+    const int64_t rows = tiles_m - g * gm < gm ? tiles_m - g * gm : gm;
+    tm = g * gm + r % rows;
+    tc = r / rows;
+}
+
 struct TcArgs {
     int64_t l, s, m;
     int64_t nks;          // operand stages per tile
     int64_t chunk;        // operand stages per accumulation chunk
     int64_t tiles_m, tiles_n;
+    int64_t group_m;      // row blocks per tile group (L2 rasterisation)
     const __nv_bfloat16 *chi, *clo;
     double2 *part;
     int64_t nparts;
@@ -274,8 +290,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t bmask = 0, bpar = 0, omask = 0, opar = 0;  // issued stages and their last parities
             bool ok = true;
             for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
-                const int tm = (int)(t / tiles_nc);
-                const int tn = (int)(MC == 2 ? 2 * (t % tiles_nc) + crank : t % tiles_nc);
+                int64_t tm64, tc64;
+                tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm64, tc64);
+                const int tm = (int)tm64;
+                const int tn = (int)(MC == 2 ? 2 * tc64 + crank : tc64);
                 const int prank = CG == 2 ? (int)crank : 0;        // rank within an MMA pair
                 const int a0 = tm * TM * CG + prank * TM;          // this CTA's first A row
                 const int b0 = tn * TN + prank * C::TNB;           // this CTA's first B row
@@ -415,8 +433,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
         bool ok = true;
         for (int64_t t = group0; t < ntiles && ok; t += ngroups, ++tcount) {
-            const int64_t tm = t / tiles_nc;
-            const int64_t tn = MC == 2 ? 2 * (t % tiles_nc) + crank : t % tiles_nc;
+            int64_t tm, tc;
+            tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm, tc);
+            const int64_t tn = MC == 2 ? 2 * tc + crank : tc;
             const int64_t arow0 = tm * TM * CG + (CG == 2 ? (int64_t)crank * TM : 0);  // first observable here
             int kc = 0;              // stage index within the current chunk
             int nchunk = 0;          // chunks of this tile already folded into the running sum
@@ -715,6 +734,18 @@ bool grad_multicast() {
 }
 
 // Tensor-core group size: CTA pairs unless IQP_CTA_PAIRS=0.
+// Row blocks per tile group (IQP_TILE_GROUP, 1..64; default 8; 1 = plain
+// row-major order).
+int64_t tile_group() {
+    static int64_t g = -1;
+    if (g < 0) {
+        const char *e = std::getenv("IQP_TILE_GROUP");
+        const long v = e ? std::atol(e) : 8;
+        g = (v >= 1 && v <= 64) ? v : 8;
+    }
+    return g;
+}
+
 int cta_group() {
     static int cg = -1;
     if (cg < 0) {
@@ -750,6 +781,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.chunk = 64;  // 4096 gates per accumulation chunk
     a.tiles_m = cdiv(p.l, TM * cg);
     a.tiles_n = cdiv(p.s, TN);
+    a.group_m = tile_group();
     a.chi = at<__nv_bfloat16>(ws, p.off_c);
     a.clo = a.chi + p.mpad;
     a.part = at<double2>(ws, p.off_part);
@@ -793,6 +825,7 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.chunk = 32;  // 2048 samples per accumulation chunk
     a.tiles_m = cdiv(p.l, TM * cg);
     a.tiles_n = cdiv(p.m, TN);
+    a.group_m = tile_group();
     a.chi = a.clo = nullptr;
     a.part = nullptr;
     a.nparts = 0;
