@@ -24,7 +24,7 @@
 // so the result does not depend on the order of the atomics: the gradient is
 // bitwise reproducible. The fixed-point scale 2^k is chosen per call from the
 // bound B = sum_a 2 s (|alpha_a| + |beta_a|) >= |every partial sum| so that
-// B 2^k < 2^62: nothing can overflow, and the rounding error per gate is at
+// B 2^k < 2^61: nothing can overflow, and the rounding error per gate is at
 // most (number of contributions) * 2^-k / 2.
 #include "common.cuh"
 
@@ -36,28 +36,46 @@ constexpr int kWarpSamples = 32 * 64;
 constexpr int kMaxWarps = 8;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// acc[k] += (bit k of z ? -c : c), bit k = sample 64 w + k of the lane's word.
-__device__ __forceinline__ void add_signed(float (&acc)[64], uint64_t z, uint32_t cb) {
-    const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc[k] += __uint_as_float(cb ^ ((lo << (31 - k)) & 0x80000000u));
-#pragma unroll
-    for (int k = 0; k < 32; ++k) acc[32 + k] += __uint_as_float(cb ^ ((hi << (31 - k)) & 0x80000000u));
+// Two FP32 adds in one instruction (sm_100+ packed FP32): (a.x + b.x, a.y + b.y),
+// each rounded to nearest like a scalar add.
+__device__ __forceinline__ uint64_t add_f32x2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
 }
 
-// sum_k (bit k of z ? -w_k : w_k), in 8 interleaved partial sums.
-__device__ __forceinline__ float signed_dot(const float (&w)[64], uint64_t z) {
+__device__ __forceinline__ uint64_t pack2(uint32_t lo, uint32_t hi) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+    return d;
+}
+
+// The lane's 64 accumulators as 32 pairs: pair t holds samples t (low half)
+// and 32 + t (high half) of the lane's word.
+// acc[t] += (bit t of z ? -c : c, bit 32+t of z ? -c : c).
+__device__ __forceinline__ void add_signed(uint64_t (&acc)[32], uint64_t z, uint32_t cb) {
     const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
-    float p[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) p[t] = 0.f;
+    for (int t = 0; t < 32; ++t) {
+        const uint32_t a = cb ^ ((lo << (31 - t)) & 0x80000000u);
+        const uint32_t b = cb ^ ((hi << (31 - t)) & 0x80000000u);
+        acc[t] = add_f32x2(acc[t], pack2(a, b));
+    }
+}
+
+// sum_k (bit k of z ? -w_k : w_k) over the lane's 64 samples, w paired like
+// the accumulators, in 4 interleaved pair sums.
+__device__ __forceinline__ float signed_dot(const uint64_t (&w)[32], uint64_t z) {
+    const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
+    uint64_t p[4] = {0ull, 0ull, 0ull, 0ull};
 #pragma unroll
-    for (int k = 0; k < 32; ++k)
-        p[k & 7] += __uint_as_float(__float_as_uint(w[k]) ^ ((lo << (31 - k)) & 0x80000000u));
-#pragma unroll
-    for (int k = 0; k < 32; ++k)
-        p[k & 7] += __uint_as_float(__float_as_uint(w[32 + k]) ^ ((hi << (31 - k)) & 0x80000000u));
-    return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+    for (int t = 0; t < 32; ++t) {
+        const uint32_t a = (uint32_t)w[t] ^ ((lo << (31 - t)) & 0x80000000u);
+        const uint32_t b = (uint32_t)(w[t] >> 32) ^ ((hi << (31 - t)) & 0x80000000u);
+        p[t & 3] = add_f32x2(p[t & 3], pack2(a, b));
+    }
+    const uint64_t q = add_f32x2(add_f32x2(p[0], p[1]), add_f32x2(p[2], p[3]));
+    return __uint_as_float((uint32_t)q) + __uint_as_float((uint32_t)(q >> 32));
 }
 
 // Calls fn(j) for every set bit j of the P_A row, in increasing j, with the
@@ -124,12 +142,13 @@ struct ZSource {
     }
 };
 
-// Phi for the lane's 64 samples (sum over J_a, increasing j).
+// Phi for the lane's 64 samples (sum over J_a, increasing j), paired as in
+// add_signed.
 template <bool INDEP>
-__device__ __forceinline__ void phase_row(float (&acc)[64], const uint64_t *__restrict__ parow, int64_t ldp,
+__device__ __forceinline__ void phase_row(uint64_t (&acc)[32], const uint64_t *__restrict__ parow, int64_t ldp,
                                           const ZSource &zs, const float *__restrict__ c, int lane) {
 #pragma unroll
-    for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+    for (int t = 0; t < 32; ++t) acc[t] = 0ull;
     uint64_t zp = 0ull;
     uint32_t cp = 0u;
     bool have = false;
@@ -169,8 +188,14 @@ __global__ void __launch_bounds__(256, 2)
     const uint64_t *parow = PA + a * ldp;
     const ZSource zs{INDEP ? PZT + a * n * ldzt : PZT, ldzt, word, sup, G, ldg, n};
 
+    uint64_t acc2[32];
+    phase_row<INDEP>(acc2, parow, ldp, zs, c, lane);
     float acc[64];
-    phase_row<INDEP>(acc, parow, ldp, zs, c, lane);
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+        acc[t] = __uint_as_float((uint32_t)acc2[t]);
+        acc[32 + t] = __uint_as_float((uint32_t)(acc2[t] >> 32));
+    }
 
     if (MODE == 0) {
         float sum = 0.f;
@@ -204,27 +229,34 @@ __global__ void __launch_bounds__(256, 2)
             sincosf(acc[k], &sn, &cn);
             acc[k] = k < nvalid ? sn * (al + be * cn) : 0.f;
         }
-        const double sc = 2.0 * *scale;
+#pragma unroll
+        for (int t = 0; t < 32; ++t) acc2[t] = pack2(__float_as_uint(acc[t]), __float_as_uint(acc[32 + t]));
+        // 2 * scale is a power of two in [2^-119, 2^119]: exact scaling in FP32.
+        const float sc = (float)(2.0 * *scale);
+        // Fixed-point value of one contribution without FP64 (slow on this
+        // GPU): x = sc d, |x| < 2^61, split exactly into hi 2^31 + lo.
+        auto emit = [&](uint64_t z, int64_t j) {
+            float d = signed_dot(acc2, z);
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
+            if (lane == 0) {
+                const float x = sc * d;
+                const float hi = truncf(x * 0x1.0p-31f);
+                const float lo = fmaf(-hi, 0x1.0p31f, x);
+                const long long q = ((long long)__float2int_rz(hi) << 31) + (long long)__float2int_rn(lo);
+                atomicAdd(gfx + j, (unsigned long long)q);
+            }
+        };
         uint64_t zp = 0ull;
         int64_t jp = -1;
         auto visit = [&](int64_t j) {
             const uint64_t zn = zs.get<INDEP>(j);
-            if (jp >= 0) {
-                float d = signed_dot(acc, zp);
-#pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
-                if (lane == 0) atomicAdd(gfx + jp, (unsigned long long)__double2ll_rn(sc * (double)d));
-            }
+            if (jp >= 0) emit(zp, jp);
             zp = zn;
             jp = j;
         };
         for_each_gate(parow, ldp, lane, visit);
-        if (jp >= 0) {
-            float d = signed_dot(acc, zp);
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
-            if (lane == 0) atomicAdd(gfx + jp, (unsigned long long)__double2ll_rn(sc * (double)d));
-        }
+        if (jp >= 0) emit(zp, jp);
     }
 }
 
@@ -243,10 +275,13 @@ __global__ void __launch_bounds__(256) k_sparse_scale(const double *__restrict__
         __syncthreads();
     }
     if (threadIdx.x == 0) {
+        // B in [2^e, 2^(e+1)); scale = 2^(60-e) gives B scale < 2^61. e is
+        // clamped to [-58, 180] so that 2 scale is a normal FP32 number.
         const double B = 2.0 * (double)s * red[0];
         int e = (B > 0.0 && B < 1e300) ? ilogb(B) : 0;
-        if (e < -900) e = -900;
-        *scale = ldexp(1.0, 61 - e);
+        if (e < -58) e = -58;
+        if (e > 180) e = 180;
+        *scale = ldexp(1.0, 60 - e);
     }
 }
 
