@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the plain FP32 form (0 = skip)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the bitflip and MMD per-call timings")
-    ap.add_argument("--cpu-sample-l", type=int, default=128)
+    ap.add_argument("--cpu-sample-l", type=int, default=512)
     ap.add_argument("--cpu-sample-s", type=int, default=10_000)
     return ap.parse_args()
 
@@ -167,6 +167,20 @@ def measured_traffic(kernel, sizes):
         return rec["kernels"][kernel]["traffic_bytes"]
     except Exception:
         return None
+
+
+# --------------------------------------------------------------- replicas
+
+def max_over_ranks(x: float, device=None) -> float:
+    """The slowest replica's value (all ranks get it); x itself when no
+    process group is running or it has one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ------------------------------------------------------------------- clocks
@@ -426,11 +440,7 @@ def main():
     status = lib.iqp_read_status(P(ws.data_ptr()), ws.numel(), st)
     if status != 0:
         raise SystemExit(f"device status {status}: {_lib.status_string(status)}")
-    ms = statistics.mean(ms_list)
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(ms_list), dev)
 
     # Per-kernel live timings of the timed region (events on the launch stream).
     kt = {}

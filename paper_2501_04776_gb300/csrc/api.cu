@@ -206,8 +206,8 @@ iqp_status check_common(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, co
     if (!aligned(theta, 4)) return IQP_ERR_ALIGN;
     if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32) return IQP_ERR_ARG;
     if (prec == IQP_SPLIT_BF16 && !iqp_tensor_path_available()) return IQP_ERR_UNSUPPORTED;
-    // sparse grid: observables on x (< 2^31), blocks of 8 x 2048 samples on y (< 65536)
-    if (prec == IQP_SPARSE_FP32 && (l > INT32_MAX || cdiv(s, (int64_t)8 * 2048) > 65535)) return IQP_ERR_ARG;
+    // sparse grid: observables on x (< 2^31), 2048-sample blocks on y (< 65536)
+    if (prec == IQP_SPARSE_FP32 && (l > INT32_MAX || cdiv(s, (int64_t)2048) > 65535)) return IQP_ERR_ARG;
     return IQP_OK;
 }
 

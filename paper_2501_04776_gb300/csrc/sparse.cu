@@ -26,6 +26,8 @@
 // bound B = sum_a 2 s (|alpha_a| + |beta_a|) >= |every partial sum| so that
 // B 2^k < 2^61: nothing can overflow, and the rounding error per gate is at
 // most (number of contributions) * 2^-k / 2.
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace iqp {
@@ -142,6 +144,62 @@ struct ZSource {
     }
 };
 
+// Gates are consumed in batches of kBatch: the batch's P_Z^T words and
+// c_j are all loaded before the first is used, so their latencies overlap
+// (the batch holds only gate indices while it fills; a register holding an
+// in-flight load is never copied, which would wait for it). The gradient
+// pass, which also holds W in registers, uses half as many.
+constexpr int kPhaseBatch = 8, kGradBatch = 4;
+
+template <class R, int kBatch>
+struct GateBatcher {
+    int64_t jb[kBatch];
+    int nb;
+    R &run;
+    __device__ __forceinline__ explicit GateBatcher(R &r) : nb(0), run(r) {
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) jb[t] = 0;
+    }
+    __device__ __forceinline__ void operator()(int64_t j) {
+#pragma unroll
+        for (int t = 0; t + 1 < kBatch; ++t) jb[t] = jb[t + 1];
+        jb[kBatch - 1] = j;
+        if (++nb == kBatch) {
+            run.go(jb);
+            nb = 0;
+        }
+    }
+    __device__ __forceinline__ void finish() {
+        // warp-uniform: the same gates on every lane
+#pragma unroll
+        for (int cnt = 1; cnt < kBatch; ++cnt)
+            if (nb == cnt) run.go_tail(jb, cnt);
+    }
+};
+
+template <bool INDEP, int kBatch>
+struct PhaseRun {
+    uint64_t (&acc)[32];
+    const ZSource &zs;
+    const float *__restrict__ c;
+    __device__ __forceinline__ void go(const int64_t (&jb)[kBatch]) {
+        uint64_t z[kBatch];
+        uint32_t cv[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) {
+            z[t] = zs.get<INDEP>(jb[t]);
+            cv[t] = __float_as_uint(__ldg(c + jb[t]));
+        }
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) add_signed(acc, z[t], cv[t]);
+    }
+    __device__ __forceinline__ void go_tail(const int64_t (&jb)[kBatch], int cnt) {
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t)
+            if (t >= kBatch - cnt) add_signed(acc, zs.get<INDEP>(jb[t]), __float_as_uint(__ldg(c + jb[t])));
+    }
+};
+
 // Phi for the lane's 64 samples (sum over J_a, increasing j), paired as in
 // add_signed.
 template <bool INDEP>
@@ -149,20 +207,49 @@ __device__ __forceinline__ void phase_row(uint64_t (&acc)[32], const uint64_t *_
                                           const ZSource &zs, const float *__restrict__ c, int lane) {
 #pragma unroll
     for (int t = 0; t < 32; ++t) acc[t] = 0ull;
-    uint64_t zp = 0ull;
-    uint32_t cp = 0u;
-    bool have = false;
-    auto visit = [&](int64_t j) {
-        const uint64_t zn = zs.get<INDEP>(j);
-        const uint32_t cn = __float_as_uint(__ldg(c + j));
-        if (have) add_signed(acc, zp, cp);
-        zp = zn;
-        cp = cn;
-        have = true;
-    };
-    for_each_gate(parow, ldp, lane, visit);
-    if (have) add_signed(acc, zp, cp);
+    PhaseRun<INDEP, kPhaseBatch> run{acc, zs, c};
+    GateBatcher<PhaseRun<INDEP, kPhaseBatch>, kPhaseBatch> batch(run);
+    for_each_gate(parow, ldp, lane, batch);
+    batch.finish();
 }
+
+// Gradient contributions of a batch of gates: per gate the lane's signed
+// dot product of W with the gate's P_Z^T word, reduced over the warp, added
+// in fixed point to the gate's accumulator.
+template <bool INDEP, int kBatch>
+struct GradRun {
+    const uint64_t (&w)[32];
+    const ZSource &zs;
+    unsigned long long *__restrict__ gfx;
+    float sc;  // 2 * scale, a power of two in [2^-119, 2^119]: exact scaling in FP32
+    int lane;
+    // Fixed-point value of one contribution without FP64 (slow on this GPU):
+    // x = sc d, |x| < 2^61, split exactly into hi 2^31 + lo.
+    __device__ __forceinline__ void emit(uint64_t z, int64_t j) {
+        float d = signed_dot(w, z);
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
+        if (lane == 0) {
+            const float x = sc * d;
+            const float hi = truncf(x * 0x1.0p-31f);
+            const float lo = fmaf(-hi, 0x1.0p31f, x);
+            const long long q = ((long long)__float2int_rz(hi) << 31) + (long long)__float2int_rn(lo);
+            atomicAdd(gfx + j, (unsigned long long)q);
+        }
+    }
+    __device__ __forceinline__ void go(const int64_t (&jb)[kBatch]) {
+        uint64_t z[kBatch];
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) z[t] = zs.get<INDEP>(jb[t]);
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t) emit(z[t], jb[t]);
+    }
+    __device__ __forceinline__ void go_tail(const int64_t (&jb)[kBatch], int cnt) {
+#pragma unroll
+        for (int t = 0; t < kBatch; ++t)
+            if (t >= kBatch - cnt) emit(zs.get<INDEP>(jb[t]), jb[t]);
+    }
+};
 
 // MODE 0: statistics partials. MODE 1: W from the recomputed Phi, then the
 // gradient contributions of every gate of J_a.
@@ -231,36 +318,15 @@ __global__ void __launch_bounds__(256, 2)
         }
 #pragma unroll
         for (int t = 0; t < 32; ++t) acc2[t] = pack2(__float_as_uint(acc[t]), __float_as_uint(acc[32 + t]));
-        // 2 * scale is a power of two in [2^-119, 2^119]: exact scaling in FP32.
         const float sc = (float)(2.0 * *scale);
-        // Fixed-point value of one contribution without FP64 (slow on this
-        // GPU): x = sc d, |x| < 2^61, split exactly into hi 2^31 + lo.
-        auto emit = [&](uint64_t z, int64_t j) {
-            float d = signed_dot(acc2, z);
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
-            if (lane == 0) {
-                const float x = sc * d;
-                const float hi = truncf(x * 0x1.0p-31f);
-                const float lo = fmaf(-hi, 0x1.0p31f, x);
-                const long long q = ((long long)__float2int_rz(hi) << 31) + (long long)__float2int_rn(lo);
-                atomicAdd(gfx + j, (unsigned long long)q);
-            }
-        };
-        uint64_t zp = 0ull;
-        int64_t jp = -1;
-        auto visit = [&](int64_t j) {
-            const uint64_t zn = zs.get<INDEP>(j);
-            if (jp >= 0) emit(zp, jp);
-            zp = zn;
-            jp = j;
-        };
-        for_each_gate(parow, ldp, lane, visit);
-        if (jp >= 0) emit(zp, jp);
+        GradRun<INDEP, kGradBatch> run{acc2, zs, gfx, sc, lane};
+        GateBatcher<GradRun<INDEP, kGradBatch>, kGradBatch> batch(run);
+        for_each_gate(parow, ldp, lane, batch);
+        batch.finish();
     }
 }
 
-// scale = 2^k with B 2^k < 2^62, B = sum_a 2 s (|alpha_a| + |beta_a|)
+// scale = 2^k with B 2^k < 2^61, B = sum_a 2 s (|alpha_a| + |beta_a|)
 // (fixed-order FP64 sum).
 __global__ void __launch_bounds__(256) k_sparse_scale(const double *__restrict__ alpha,
                                                       const double *__restrict__ beta, int64_t l, int64_t s,
@@ -293,8 +359,24 @@ __global__ void k_sparse_grad_out(const unsigned long long *__restrict__ gfx, in
         grad[j] = (double)(long long)gfx[j] * inv;
 }
 
+// Warps per CTA (IQP_SPARSE_WARPS, 1..8, default 1): every warp scans its
+// observable's P_A row on its own, so larger CTAs share nothing and only
+// coarsen the scheduling; single-warp CTAs balance observables of unequal
+// |J_a| best and, ordered observable-fastest, keep the P_Z^T segments of one
+// 2048-sample range hot in L2 across observables.
+int sparse_warps() {
+    static int w = -1;
+    if (w < 0) {
+        const char *e = std::getenv("IQP_SPARSE_WARPS");
+        const int v = e ? std::atoi(e) : 1;
+        w = (v >= 1 && v <= kMaxWarps) ? v : 1;
+    }
+    return w;
+}
+
 dim3 sparse_grid(int64_t l, int64_t nparts, int *threads) {
-    const int nw = nparts < kMaxWarps ? (int)nparts : kMaxWarps;
+    const int cap = sparse_warps();
+    const int nw = nparts < cap ? (int)nparts : cap;
     *threads = 32 * nw;
     return dim3((unsigned)l, (unsigned)cdiv(nparts, nw));
 }
