@@ -112,3 +112,45 @@ def test_binding_imports_without_gpu():
     assert api.precision_code("split_bf16") == 1 and api.precision_code("fp32") == 0
     with pytest.raises(ValueError):
         api.precision_code("fp16")
+
+
+def test_host_side_argument_errors_of_the_options(lib):
+    """The option entry points check their arguments on the host before any
+    launch (no pointer below is dereferenced)."""
+    from paper_2501_04776_gb300 import _lib
+    G, A, Z, X, th, out, ws = 0x10000, 0x20000, 0x30000, 0x70000, 0x40000, 0x50000, 0x100000
+    # MMD flags outside IQP_MMD_UNBIASED | IQP_MMD_SQRT | IQP_MMD_INDEP
+    rc = lib.iqp_mmd_loss(10, G, 4, 2, A, 3, 2, Z, 5, 2, X, 5, 2, th, 0, 8, out, ws, 1 << 30, None)
+    assert rc == _lib.ERR_ARG
+    # indep: workspace sized for the shared-batch op is too small
+    need = lib.iqp_workspace_bytes(_lib.OP_EXPVAL_INDEP, 10, 4, 3, 5, 0, 0)
+    assert need > lib.iqp_workspace_bytes(_lib.OP_EXPVAL, 10, 4, 3, 5, 0, 2) > 0
+    assert lib.iqp_expval_indep(10, G, 4, 2, A, 3, 2, Z, 5, 2, th, out, out, ws, need - 256, None) == \
+        _lib.ERR_WORKSPACE
+    assert lib.iqp_expval_indep_grad(10, G, 4, 2, A, 3, 2, Z, 5, 2, th, None, None, out, ws, need, None) == \
+        _lib.ERR_ARG  # alpha is required
+    # sparse form: more than 65535 blocks of 2048 samples
+    assert lib.iqp_expval(10, G, 4, 2, A, 3, 2, Z, 2048 * 65536, 2, th, 2, out, out, ws, 1 << 40, None) == \
+        _lib.ERR_ARG
+    # shared parameters, wires, random bits
+    assert lib.iqp_expand_params(th, 0, 0x60000, out, 4, None) == _lib.ERR_ARG
+    assert lib.iqp_reduce_params(out, 4, 0x60004, 2, out, None) == _lib.ERR_ALIGN
+    assert lib.iqp_embed_bits(A, 3, 2, None, 2, X, 2, 10, None) == _lib.ERR_ARG
+    assert lib.iqp_embed_bits(A, 3, 2, 0x60000, 2, X, 1, 10, None) == _lib.ERR_ARG   # odd ld_dst
+    assert lib.iqp_uniform_bits(1, 2, 3, 130, X, 2, None) == _lib.ERR_ARG            # ld < ceil(n/64)
+    assert lib.iqp_bernoulli_bits(1, 2, 3, 10, 1.5, X, 2, None) == _lib.ERR_ARG      # p outside [0, 1]
+    assert lib.iqp_bernoulli_bits(1, 2, 3, 10, float("nan"), X, 2, None) == _lib.ERR_ARG
+    # bitflip
+    assert lib.iqp_bitflip_grad(10, G, 4, 2, A, 3, 2, th, None, out, ws, 1 << 30, None) == _lib.ERR_ARG
+
+
+def test_workspace_sizes_of_the_options(lib):
+    from paper_2501_04776_gb300 import _lib
+    n, m, l, s = 1000, 100_000, 100, 1000
+    ind = lib.iqp_workspace_bytes(_lib.OP_EXPVAL_INDEP, n, m, l, s, 0, 0)
+    # every batch transposed: l * n * ceil(s/64 -> 4) words
+    assert ind >= l * n * 16 * 8
+    assert lib.iqp_workspace_bytes(_lib.OP_EXPVAL_INDEP_GRAD, n, m, l, s, 0, 0) >= ind + 8 * m
+    mmd = lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD_INDEP, n, m, l, s, 50, 0)
+    assert mmd > lib.iqp_workspace_bytes(_lib.OP_EXPVAL_INDEP_GRAD, n, m, l, s, 0, 0)
+    assert lib.iqp_workspace_bytes(10, n, m, l, s, 0, 0) == 0
