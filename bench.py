@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "sparse_fp32"])
+    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "sparse_fp32", "loworder_fp32"])
     ap.add_argument("--workload", default="random", choices=["random", "mmd", "million"],
                     help="random: k in 1..3 random gates (sizes from --n --m --l --s); mmd: all 1- and 2-body "
                          "gates, p_sigma observables (--n --l --s); million: n=5000, 1e6 random 1-2-body gates")
@@ -312,7 +312,8 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
     loss = torch.empty(1, dtype=torch.float64, device=dev)
     gm = torch.empty(mm, dtype=torch.float64, device=dev)
     nnz = nnz_parities(api, p.n, Am, Gm)
-    for prec, tag in ((_lib.SPLIT_BF16, "split_bf16"), (_lib.SPARSE_FP32, "sparse_fp32")):
+    for prec, tag in ((_lib.SPLIT_BF16, "split_bf16"), (_lib.SPARSE_FP32, "sparse_fp32"),
+                      (_lib.LOWORDER_FP32, "loworder_fp32")):
         ws = torch.empty(lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD, p.n, mm, lm, sm, Nm, prec),
                          dtype=torch.uint8, device=dev)
 
@@ -334,6 +335,17 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
             roof = {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
                     "frac": round(ach / peak, 4), "flops_per_launch": executed,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+        elif prec == _lib.LOWORDER_FP32:
+            # Dominant part: the n x n x s contractions M = C S (twice, in the
+            # forward and again in the gradient call) and H = (s V) S^T, each
+            # 2 n^2 s flops, on the FP32 FMA pipe.
+            mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+            flops = 2.0 * p.n * p.n * sm
+            ach = flops / (kt["loworder_gemm"]["avg_ms"] * 1e-3) / 1e12
+            roof = {"bound": "alu", "kernel": "loworder_gemm", "achieved": round(ach, 2), "peak": round(peak, 1),
+                    "unit": "TFLOP/s", "frac": round(ach / peak, 4), "flops_per_launch": flops,
+                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
         else:
             # Forward kernel: nnz * s FP32 signed additions; peak = one FP32
             # add per lane per clock: 152 SMs x 128 lanes x max SM clock.
@@ -371,7 +383,8 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     lib = _lib.load()
-    prec = {"split_bf16": _lib.SPLIT_BF16, "fp32": _lib.FP32, "sparse_fp32": _lib.SPARSE_FP32}[args.precision]
+    prec = {"split_bf16": _lib.SPLIT_BF16, "fp32": _lib.FP32, "sparse_fp32": _lib.SPARSE_FP32,
+            "loworder_fp32": _lib.LOWORDER_FP32}[args.precision]
     if prec == _lib.SPLIT_BF16 and not lib.iqp_tensor_path_available():
         raise SystemExit("the split-BF16 tensor path needs an sm_103 GPU")
 
@@ -466,6 +479,14 @@ def main():
                 "flops_per_launch": executed, "useful_tflops": round(achieved / 2, 1),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
+    elif prec == _lib.LOWORDER_FP32:
+        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
+        flops = 2.0 * n * n * s
+        achieved = flops / (kt["loworder_gemm"]["avg_ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "kernel": "loworder_gemm", "achieved": round(achieved, 2), "peak": round(peak, 1),
+                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None, "flops_per_launch": flops,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
     elif prec == _lib.SPARSE_FP32:
         nnz = nnz_parities(api, p.n, A, G)
         mhz = (clocks or {}).get("sm_max_mhz") or 2070.0

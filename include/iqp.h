@@ -59,8 +59,17 @@ typedef enum {
  * observable only the gates with [g_j.a odd] are visited, so the work is
  * nnz(P_A) * s instead of l * m * s; the choice when P_A is sparse (density
  * below a few percent, e.g. low-weight observables drawn with small p_sigma).
- * Same tolerances as IQP_FP32; its gradient is bitwise reproducible. */
-typedef enum { IQP_FP32 = 0, IQP_SPLIT_BF16 = 1, IQP_SPARSE_FP32 = 2 } iqp_precision;
+ * Same tolerances as IQP_FP32; its gradient is bitwise reproducible.
+ * IQP_LOWORDER_FP32: for generators of weight <= 2 only (one- and two-body
+ * gates, e.g. local_gates of Sec. 3.1.1). With s_q(i) = (-1)^{z_iq} the
+ * phase regroups exactly into
+ *   Phi[a,i] = sum_{q in a} s_q(i) (d_q + (C S)[q,i]) - 2 sum_{q<r in a} C_qr s_q(i) s_r(i),
+ * d_q / C_qr = sums of 2 theta_j over the gates on {q} / {q, r}, so the work
+ * is two n x n x s contractions plus O(l |a|^2 s) instead of O(l m s). FP32
+ * (tolerances of IQP_FP32). A generator of weight > 2 records IQP_ERR_ARG
+ * and an observable of weight > 1024 records IQP_ERR_UNSUPPORTED in the
+ * device status (iqp_read_status); the outputs are then not meaningful. */
+typedef enum { IQP_FP32 = 0, IQP_SPLIT_BF16 = 1, IQP_SPARSE_FP32 = 2, IQP_LOWORDER_FP32 = 3 } iqp_precision;
 
 /* Operation whose scratch iqp_workspace_bytes() sizes. */
 typedef enum {
@@ -307,7 +316,9 @@ typedef enum {
     IQP_KERNEL_GRAD_SPARSE = 15,   /* row-sparse recompute + gradient           */
     IQP_KERNEL_VARIANTS = 16,      /* shared-parameter expand/reduce, embedding */
     IQP_KERNEL_RNG = 17,           /* on-device random bits                     */
-    IQP_KERNEL_COUNT = 18
+    IQP_KERNEL_LOWORDER = 18,      /* weight <= 2 generators: the low-order form */
+    IQP_KERNEL_LOWORDER_GEMM = 19, /* its n x n x s contractions                */
+    IQP_KERNEL_COUNT = 20
 } iqp_kernel;
 
 /* Per-kernel timing (off by default). When enabled, every launch is

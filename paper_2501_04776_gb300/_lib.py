@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libiqp_gb300.so")
 
 OK, ERR_ARG, ERR_ALIGN, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
-FP32, SPLIT_BF16, SPARSE_FP32 = 0, 1, 2
+FP32, SPLIT_BF16, SPARSE_FP32, LOWORDER_FP32 = 0, 1, 2, 3
 OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP = 1, 2, 3, 4, 5
 OP_EXPVAL_INDEP, OP_EXPVAL_INDEP_GRAD, OP_MMD_LOSS_INDEP, OP_MMD_LOSS_GRAD_INDEP = 6, 7, 8, 9
 MMD_UNBIASED, MMD_SQRT, MMD_INDEP = 1, 2, 4
@@ -51,7 +51,8 @@ SIGNATURES = {
 
 KERNELS = ["parity", "parity_sum", "theta_split", "phase_fp32", "recompute_fp32", "grad_fp32", "phase_tc",
            "recompute_tc", "grad_tc", "finalize", "grad_reduce", "mmd_combine", "selftest", "bitflip",
-           "phase_sparse", "grad_sparse", "variants", "rng"]
+           "phase_sparse", "grad_sparse", "variants", "rng", "loworder",
+           "loworder_gemm"]
 
 _lib = None
 

@@ -14,19 +14,20 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import FP32, SPLIT_BF16, SPARSE_FP32, OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP, check
+from ._lib import FP32, SPLIT_BF16, SPARSE_FP32, LOWORDER_FP32, OP_EXPVAL, OP_EXPVAL_GRAD, OP_MMD_LOSS, OP_MMD_LOSS_GRAD, OP_BITFLIP, check
 from ._lib import OP_EXPVAL_INDEP, OP_EXPVAL_INDEP_GRAD, OP_MMD_LOSS_INDEP, OP_MMD_LOSS_GRAD_INDEP
 from ._lib import MMD_UNBIASED, MMD_SQRT, MMD_INDEP
 
-_PRECISIONS = {"fp32": FP32, "split_bf16": SPLIT_BF16, "sparse_fp32": SPARSE_FP32, FP32: FP32,
-               SPLIT_BF16: SPLIT_BF16, SPARSE_FP32: SPARSE_FP32}
+_PRECISIONS = {"fp32": FP32, "split_bf16": SPLIT_BF16, "sparse_fp32": SPARSE_FP32, "loworder_fp32": LOWORDER_FP32,
+               FP32: FP32, SPLIT_BF16: SPLIT_BF16, SPARSE_FP32: SPARSE_FP32, LOWORDER_FP32: LOWORDER_FP32}
 
 
 def precision_code(precision) -> int:
     try:
         return _PRECISIONS[precision]
     except KeyError:
-        raise ValueError(f"precision must be 'fp32', 'split_bf16' or 'sparse_fp32', got {precision!r}") from None
+        raise ValueError("precision must be 'fp32', 'split_bf16', 'sparse_fp32' or 'loworder_fp32', "
+                         f"got {precision!r}") from None
 
 
 def _stream(device) -> int:
@@ -41,6 +42,14 @@ def _bits(t: torch.Tensor, name: str) -> torch.Tensor:
     return t
 
 
+def _resolve(device) -> torch.device:
+    """torch.device with an explicit index ("cuda" -> the current device)."""
+    d = torch.device(device)
+    if d.type == "cuda" and d.index is None:
+        d = torch.device("cuda", torch.cuda.current_device())
+    return d
+
+
 def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
@@ -52,7 +61,8 @@ class _Workspace:
         self._bufs = {}
 
     def get(self, nbytes: int, device) -> torch.Tensor:
-        key = (torch.device(device).index, _stream(device))
+        device = _resolve(device)
+        key = (device.index, _stream(device))
         buf = self._bufs.get(key)
         if buf is None or buf.numel() < nbytes:
             buf = torch.zeros(max(nbytes, 256), dtype=torch.uint8, device=device)
@@ -415,7 +425,7 @@ def bitflip_expval(theta, G, A, n: int):
 
 def read_status(device=None) -> int:
     """Device-side status recorded in the current stream's workspace (clears it)."""
-    device = torch.device("cuda") if device is None else torch.device(device)
+    device = _resolve("cuda" if device is None else device)
     ws = _WS.get(256, device)
     return int(_lib.load().iqp_read_status(_ptr(ws), ws.numel(), ctypes.c_void_p(_stream(device))))
 

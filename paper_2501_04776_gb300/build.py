@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "iqp")
 LIB = os.path.join(HERE, "libiqp_gb300.so")
-SOURCES = ["parity.cu", "simt.cu", "tc.cu", "bitflip.cu", "sparse.cu", "variants.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["parity.cu", "simt.cu", "tc.cu", "bitflip.cu", "sparse.cu", "variants.cu", "loworder.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I" + INCLUDE, "-I" + CSRC]
 

@@ -57,6 +57,18 @@ cudaError_t launch_uniform_bits(uint64_t seed, uint64_t stream, int64_t rows, in
                                 cudaStream_t st);
 cudaError_t launch_bernoulli_bits(uint64_t seed, uint64_t stream, int64_t rows, int64_t n, double p, int64_t ld,
                                   uint64_t *out, cudaStream_t st);
+int64_t lo_part_samples();
+cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *Z, int64_t s,
+                              int64_t ldz, const float *c, int4 *sup, uint64_t *ZT, int64_t ldzt, float *C,
+                              int64_t ldc, float *M, int64_t lds, uint32_t *status, cudaStream_t st);
+cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
+                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, double2 *part,
+                            int64_t nparts, uint32_t *status, cudaStream_t st);
+cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
+                           const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
+                           const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
+                           float *W, float *V, float *H, double *gsp, unsigned long long *Kfx, double *grad,
+                           uint32_t *status, cudaStream_t st);
 cudaError_t launch_bitflip_gates(const float *theta, int64_t m, int64_t mpad, double *c, double *t, cudaStream_t st);
 cudaError_t launch_bitflip_rows(const uint64_t *PA, int64_t ldp, int64_t l, const double *c, double *expval,
                                 cudaStream_t st);
@@ -82,7 +94,11 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.ldlt = round_up(cdiv(l, 64), 4);
     p.mpad = p.ldp * 64;
     p.ldw = round_up(s, 64);
-    p.pw = prec == IQP_SPLIT_BF16 ? kPartColsTc : (prec == IQP_SPARSE_FP32 ? sparse_part_samples() : kPartColsSimt);
+    p.pw = prec == IQP_SPLIT_BF16    ? kPartColsTc
+           : prec == IQP_SPARSE_FP32 ? sparse_part_samples()
+           : prec == IQP_LOWORDER_FP32 ? lo_part_samples()
+                                       : kPartColsSimt;
+    p.ldc = round_up(n, 4);
     p.nparts = cdiv(s, p.pw);
     p.natile = cdiv(l, kATile);
     const bool grad = op == IQP_OP_EXPVAL_GRAD || op == IQP_OP_MMD_LOSS_GRAD || op == IQP_OP_EXPVAL_INDEP_GRAD ||
@@ -92,6 +108,7 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     const bool indep = p.indep;
     const bool bitflip = op == IQP_OP_BITFLIP;
     const bool sparse = prec == IQP_SPARSE_FP32 && !bitflip;
+    const bool lo = prec == IQP_LOWORDER_FP32 && !bitflip && !indep;
     size_t off = 0;
     auto take = [&](int64_t bytes) {
         const size_t o = off;
@@ -99,22 +116,27 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
         return o;
     };
     p.off_status = take(256);
-    p.off_pa = take(l * p.ldp * 8);
-    p.off_pz = take(bitflip || sparse ? 0 : s * p.ldp * 8);
-    p.off_pzt = take(bitflip || indep ? 0 : m * p.ldzt * 8);
-    p.off_pat = take(m * p.ldlt * 8);
+    p.off_pa = take(lo ? 0 : l * p.ldp * 8);
+    p.off_pz = take(bitflip || sparse || lo ? 0 : s * p.ldp * 8);
+    p.off_pzt = take(bitflip || indep ? 0 : (lo ? n : m) * p.ldzt * 8);  // low-order: the samples transposed
+    p.off_pat = take(lo ? 0 : m * p.ldlt * 8);
     p.off_rt = take(n * (p.ldzt > p.ldlt ? p.ldzt : p.ldlt) * 8);
     p.off_c = take(bitflip ? p.mpad * 16 : p.mpad * 4);  // bitflip: cos(2 theta), -2 tan(2 theta) in FP64
     p.off_part = take(bitflip ? l * 16 : l * p.nparts * 16);  // bitflip: expval, w * expval
     p.off_w = take(grad && !sparse ? l * p.ldw * 4 : 0);
+    p.off_lo_c = take(lo ? (n + 1) * p.ldc * 4 : 0);
+    p.off_lo_m = take(lo ? n * p.ldw * 4 : 0);
+    p.off_lo_v = take(lo && grad ? n * p.ldw * 4 : 0);
+    p.off_lo_h = take(lo && grad ? n * p.ldc * 4 : 0);
+    p.off_lo_gs = take(lo && grad ? n * cdiv(s, lo_part_samples()) * 8 : 0);
     // sparse: 64-bit fixed-point gradient accumulators and their scale
-    p.off_gpart = take(grad ? (sparse ? m * 8 + 8 : p.natile * m * 8) : 0);
+    p.off_gpart = take(grad ? (sparse ? m * 8 + 8 : (lo ? n * n * 8 + 8 : p.natile * m * 8)) : 0);
     p.off_ab = take(mmd ? l * 16 : 0);
     p.off_s12 = take(mmd ? l * 16 : 0);
     p.off_T = take(mmd ? l * 8 : 0);
     p.off_terms = take(mmd ? l * 8 : 0);
     p.off_zt = take(indep ? l * n * p.ldzt * 8 : 0);  // every batch transposed: n rows of bits over samples
-    p.off_sup = take(indep ? m * 16 : 0);             // int4 support list per gate
+    p.off_sup = take(indep || lo ? m * 16 : 0);       // int4 support list per gate
     p.total = off;
     return p;
 }
@@ -204,8 +226,13 @@ iqp_status check_common(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, co
     if ((st = check_bits(Z, s, ldz, n)) != IQP_OK) return st;
     if (theta == nullptr) return IQP_ERR_ARG;
     if (!aligned(theta, 4)) return IQP_ERR_ALIGN;
-    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32) return IQP_ERR_ARG;
+    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32 && prec != IQP_LOWORDER_FP32)
+        return IQP_ERR_ARG;
     if (prec == IQP_SPLIT_BF16 && !iqp_tensor_path_available()) return IQP_ERR_UNSUPPORTED;
+    // low-order grids: observables on x, 256-sample blocks and 128-row GEMM tiles on y
+    if (prec == IQP_LOWORDER_FP32 && (l > INT32_MAX || n > INT32_MAX || cdiv(s, (int64_t)256) > 65535 ||
+                                      cdiv(n, (int64_t)128) > 65535))
+        return IQP_ERR_ARG;
     // sparse grid: observables on x (< 2^31), 2048-sample blocks on y (< 65536)
     if (prec == IQP_SPARSE_FP32 && (l > INT32_MAX || cdiv(s, (int64_t)2048) > 65535)) return IQP_ERR_ARG;
     return IQP_OK;
@@ -234,6 +261,14 @@ T *at(void *ws, size_t off) {
 iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, const uint64_t *A, int64_t lda,
                    const uint64_t *Z, int64_t ldz, const float *theta, cudaStream_t st) {
     uint64_t *rt = at<uint64_t>(ws, p.off_rt);
+    if (p.prec == IQP_LOWORDER_FP32 && !p.indep) {
+        // no parity matrices: C, d, the samples transposed and M = C S
+        IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, at<float>(ws, p.off_c), nullptr, nullptr, st));
+        IQP_TRY(launch_lo_prepare(p.n, G, p.m, ldg, Z, p.s, ldz, at<float>(ws, p.off_c), at<int4>(ws, p.off_sup),
+                                  at<uint64_t>(ws, p.off_pzt), p.ldzt, at<float>(ws, p.off_lo_c), p.ldc,
+                                  at<float>(ws, p.off_lo_m), p.ldw, at<uint32_t>(ws, p.off_status), st));
+        return IQP_OK;
+    }
     IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
                                  at<uint64_t>(ws, p.off_pat), p.ldlt, rt, st));
     if (p.indep) {
@@ -263,6 +298,10 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
         iqp_status why = IQP_OK;
         if (launch_phase_tc(0, p, ws, nullptr, nullptr, st, &why) != cudaSuccess)
             return why != IQP_OK ? why : IQP_ERR_CUDA;
+    } else if (p.prec == IQP_LOWORDER_FP32) {
+        IQP_TRY(launch_lo_stats(p.A, p.lda, p.n, p.l, at<uint64_t>(ws, p.off_pzt), p.ldzt, at<float>(ws, p.off_lo_m),
+                                p.ldw, at<float>(ws, p.off_lo_c), p.ldc, p.s, part, p.nparts,
+                                at<uint32_t>(ws, p.off_status), st));
     } else if (p.prec == IQP_SPARSE_FP32) {
         const SparseIndep ind{at<int4>(ws, p.off_sup), p.G, p.ldg, p.n};
         IQP_TRY(launch_sparse_stats(at<uint64_t>(ws, p.off_pa), p.ldp,
@@ -281,6 +320,14 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
 iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *beta, double *grad,
                     cudaStream_t st) {
     double *gpart = at<double>(ws, p.off_gpart);
+    if (p.prec == IQP_LOWORDER_FP32) {
+        IQP_TRY(launch_lo_grad(p.A, p.lda, p.n, p.l, at<uint64_t>(ws, p.off_pzt), p.ldzt, at<float>(ws, p.off_lo_m),
+                               p.ldw, at<float>(ws, p.off_lo_c), p.ldc, p.s, p.m, at<int4>(ws, p.off_sup), alpha, beta,
+                               at<uint64_t>(ws, p.off_rt), p.ldlt, at<float>(ws, p.off_w), at<float>(ws, p.off_lo_v),
+                               at<float>(ws, p.off_lo_h), at<double>(ws, p.off_lo_gs),
+                               at<unsigned long long>(ws, p.off_gpart), grad, at<uint32_t>(ws, p.off_status), st));
+        return IQP_OK;
+    }
     if (p.prec == IQP_SPARSE_FP32) {
         unsigned long long *gfx = at<unsigned long long>(ws, p.off_gpart);
         const SparseIndep ind{at<int4>(ws, p.off_sup), p.G, p.ldg, p.n};
@@ -325,6 +372,8 @@ iqp_status mmd_core(int op, int64_t n, const uint64_t *G, int64_t m, int64_t ldg
     Plan p = make_plan(pop, n, m, l, s, N, prec);
     p.G = G;
     p.ldg = ldg;
+    p.A = A;
+    p.lda = lda;
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
@@ -360,7 +409,7 @@ extern "C" {
 size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, iqp_precision prec) {
     if (n < 1 || m < 1 || l < 1 || s < 1) return 0;
     if (op < IQP_OP_EXPVAL || op > IQP_OP_MMD_LOSS_GRAD_INDEP) return 0;
-    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32) return 0;
+    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32 && prec != IQP_LOWORDER_FP32) return 0;
     return make_plan(op, n, m, l, s, N, prec).total;
 }
 
@@ -408,7 +457,11 @@ iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, cons
     iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
     if (rc != IQP_OK) return rc;
     if ((expval && !aligned(expval, 8)) || (std_err && !aligned(std_err, 8))) return IQP_ERR_ALIGN;
-    const Plan p = make_plan(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
+    Plan p = make_plan(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
+    p.G = G;
+    p.ldg = ldg;
+    p.A = A;
+    p.lda = lda;
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
@@ -423,7 +476,11 @@ iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
     if (rc != IQP_OK) return rc;
     if (alpha == nullptr || grad == nullptr) return IQP_ERR_ARG;
     if (!aligned(alpha, 8) || !aligned(grad, 8) || (beta && !aligned(beta, 8))) return IQP_ERR_ALIGN;
-    const Plan p = make_plan(IQP_OP_EXPVAL_GRAD, n, m, l, s, 0, prec);
+    Plan p = make_plan(IQP_OP_EXPVAL_GRAD, n, m, l, s, 0, prec);
+    p.G = G;
+    p.ldg = ldg;
+    p.A = A;
+    p.lda = lda;
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;

@@ -36,9 +36,14 @@ struct Plan {
     int64_t natile; // ceil(l / 128)
     size_t off_status, off_pa, off_pz, off_pzt, off_pat, off_rt, off_c, off_part, off_w, off_gpart;
     size_t off_ab, off_s12, off_T, off_terms, off_zt, off_sup, total;
+    // low-order form: C (+ d), M = C S, V, H, single-gate partials; ldc floats per row of C and H
+    size_t off_lo_c, off_lo_m, off_lo_v, off_lo_h, off_lo_gs;
+    int64_t ldc;
     bool indep;     // one sample batch per observable (Z has l * s rows)
     const uint64_t *G;  // generators (read by the independent-batch kernels)
     int64_t ldg;
+    const uint64_t *A;  // observables (read by the low-order kernels)
+    int64_t lda;
 };
 
 // Independent-batch arguments of the row-sparse kernels.

@@ -385,6 +385,15 @@ dim3 sparse_grid(int64_t l, int64_t nparts, int *threads) {
 
 int64_t sparse_part_samples() { return kWarpSamples; }
 
+// scale (one double) = 2^k with sum_a 2 s (|alpha_a| + |beta_a|) 2^k < 2^61;
+// used by every fixed-point gradient accumulation.
+cudaError_t launch_fixed_scale(const double *alpha, const double *beta, int64_t l, int64_t s, double *scale,
+                               cudaStream_t st) {
+    LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
+    k_sparse_scale<<<1, 256, 0, st>>>(alpha, beta, l, s, scale);
+    return cudaGetLastError();
+}
+
 // indep != nullptr: independent batches (PZT = every observable's ZT).
 cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
                                 int64_t l, int64_t s, double2 *part, int64_t nparts, const SparseIndep *indep,
