@@ -238,6 +238,27 @@ class ClockSampler:
 
 # ---------------------------------------------------- the other hot-path rows
 
+def generator_pairs(n, G):
+    """Number of distinct qubit pairs that carry a weight-2 generator
+    (host-side count from the packed rows)."""
+    G = np.ascontiguousarray(G, dtype=np.uint64)
+    wt = np.bitwise_count(G).sum(axis=1)
+    rows = G[wt == 2]
+    if rows.shape[0] == 0:
+        return 0
+    lo = np.full(rows.shape[0], -1, dtype=np.int64)
+    hi = np.full(rows.shape[0], -1, dtype=np.int64)
+    for w in range(rows.shape[1]):
+        x = rows[:, w]
+        nz = x != 0
+        low = (x & (~x + np.uint64(1)))
+        lbit = np.where(nz, np.log2(np.where(nz, low, 1).astype(np.float64)).astype(np.int64), -1) + 64 * w
+        hbit = np.where(nz, np.floor(np.log2(np.where(nz, x, 1).astype(np.float64))).astype(np.int64), -1) + 64 * w
+        lo = np.where((lo < 0) & nz, lbit, lo)
+        hi = np.where(nz, hbit, hi)
+    return int(np.unique(lo * n + hi).size)
+
+
 def nnz_parities(api, n, A, G):
     """nnz(P_A) (computed on the GPU): the row-sparse form does nnz * s signed
     additions per pass."""
@@ -246,6 +267,19 @@ def nnz_parities(api, n, A, G):
     x = (x & 0x3333333333333333) + ((x >> 2) & 0x3333333333333333)
     x = (x + (x >> 4)) & 0x0F0F0F0F0F0F0F0F
     return int(((x * 0x0101010101010101) >> 56).sum().item())
+
+
+def loworder_roofline(kt, clocks, n, G, s):
+    """The low-order form's pair contractions (M = C S and H = (s V) S^T):
+    2 p s signed FP32 additions per launch, p = qubit pairs with a generator,
+    against one add per lane per clock."""
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    adds = 2.0 * generator_pairs(n, G) * s
+    ach = adds / (kt["loworder_gemm"]["avg_ms"] * 1e-3) / 1e12
+    return {"bound": "alu", "kernel": "loworder_gemm (pair contractions)", "achieved": round(ach, 2),
+            "peak": round(peak, 1), "unit": "Tadd/s", "frac": round(ach / peak, 4), "adds_per_launch": adds,
+            "peak_source": "FP32 add: 152 SMs x 128 lanes x max SM clock"}
 
 
 def _kernel_times(lib):
@@ -336,16 +370,7 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
                     "frac": round(ach / peak, 4), "flops_per_launch": executed,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
         elif prec == _lib.LOWORDER_FP32:
-            # Dominant part: the n x n x s contractions M = C S (twice, in the
-            # forward and again in the gradient call) and H = (s V) S^T, each
-            # 2 n^2 s flops, on the FP32 FMA pipe.
-            mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-            peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-            flops = 2.0 * p.n * p.n * sm
-            ach = flops / (kt["loworder_gemm"]["avg_ms"] * 1e-3) / 1e12
-            roof = {"bound": "alu", "kernel": "loworder_gemm", "achieved": round(ach, 2), "peak": round(peak, 1),
-                    "unit": "TFLOP/s", "frac": round(ach / peak, 4), "flops_per_launch": flops,
-                    "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
+            roof = loworder_roofline(kt, clocks, p.n, p.G, sm)
         else:
             # Forward kernel: nnz * s FP32 signed additions; peak = one FP32
             # add per lane per clock: 152 SMs x 128 lanes x max SM clock.
@@ -480,13 +505,8 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
     elif prec == _lib.LOWORDER_FP32:
-        mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-        peak = 152 * 128 * 2 * mhz * 1e6 / 1e12
-        flops = 2.0 * n * n * s
-        achieved = flops / (kt["loworder_gemm"]["avg_ms"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": "loworder_gemm", "achieved": round(achieved, 2), "peak": round(peak, 1),
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None, "flops_per_launch": flops,
-                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
+        roof = loworder_roofline(kt, clocks, n, p.G, s)
+        roof["traffic"] = None
     elif prec == _lib.SPARSE_FP32:
         nnz = nnz_parities(api, p.n, A, G)
         mhz = (clocks or {}).get("sm_max_mhz") or 2070.0

@@ -67,7 +67,7 @@ cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l
 cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
                            const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
-                           float *W, float *V, float *H, double *gsp, unsigned long long *Kfx, double *grad,
+                           float *W, float *V, double *H, double *gsp, unsigned long long *Kfx, double *grad,
                            uint32_t *status, cudaStream_t st);
 cudaError_t launch_bitflip_gates(const float *theta, int64_t m, int64_t mpad, double *c, double *t, cudaStream_t st);
 cudaError_t launch_bitflip_rows(const uint64_t *PA, int64_t ldp, int64_t l, const double *c, double *expval,
@@ -124,10 +124,10 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_c = take(bitflip ? p.mpad * 16 : p.mpad * 4);  // bitflip: cos(2 theta), -2 tan(2 theta) in FP64
     p.off_part = take(bitflip ? l * 16 : l * p.nparts * 16);  // bitflip: expval, w * expval
     p.off_w = take(grad && !sparse ? l * p.ldw * 4 : 0);
-    p.off_lo_c = take(lo ? (n + 1) * p.ldc * 4 : 0);
+    p.off_lo_c = take(lo ? (n + 1) * p.ldc * 4 + n * cdiv(n, 64) * 8 : 0);  // C, d, pair-existence bits E
     p.off_lo_m = take(lo ? n * p.ldw * 4 : 0);
     p.off_lo_v = take(lo && grad ? n * p.ldw * 4 : 0);
-    p.off_lo_h = take(lo && grad ? n * p.ldc * 4 : 0);
+    p.off_lo_h = take(lo && grad ? n * p.ldc * 8 : 0);
     p.off_lo_gs = take(lo && grad ? n * cdiv(s, lo_part_samples()) * 8 : 0);
     // sparse: 64-bit fixed-point gradient accumulators and their scale
     p.off_gpart = take(grad ? (sparse ? m * 8 + 8 : (lo ? n * n * 8 + 8 : p.natile * m * 8)) : 0);
@@ -324,7 +324,7 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
         IQP_TRY(launch_lo_grad(p.A, p.lda, p.n, p.l, at<uint64_t>(ws, p.off_pzt), p.ldzt, at<float>(ws, p.off_lo_m),
                                p.ldw, at<float>(ws, p.off_lo_c), p.ldc, p.s, p.m, at<int4>(ws, p.off_sup), alpha, beta,
                                at<uint64_t>(ws, p.off_rt), p.ldlt, at<float>(ws, p.off_w), at<float>(ws, p.off_lo_v),
-                               at<float>(ws, p.off_lo_h), at<double>(ws, p.off_lo_gs),
+                               at<double>(ws, p.off_lo_h), at<double>(ws, p.off_lo_gs),
                                at<unsigned long long>(ws, p.off_gpart), grad, at<uint32_t>(ws, p.off_status), st));
         return IQP_OK;
     }

@@ -7,14 +7,15 @@
 //   1 - 2[g_j.z odd] = s_q(z), or s_q(z) s_r(z),
 // so the phase of eq. expvalsample regroups exactly into
 //   Phi[a,i] = sum_{q in Q_a} s_q(i) (d_q + M[q,i]) - 2 sum_{q<r in Q_a} C_qr s_q(i) s_r(i),
-//   M = C S,  S[r][i] = s_r(i)                              (an n x n x s contraction),
+//   M = C S,  S[r][i] = s_r(i)        (an n x n x s contraction over the pairs with a generator),
 // and with W[a,i] = sin Phi (alpha_a + beta_a cos Phi), V[q,i] = sum_{a : q in Q_a} W[a,i]:
 //   grad(gate e_q)       = 2 sum_i s_q(i) V[q,i],
 //   grad(gate e_q + e_r) = 2 (H[q,r] + H[r,q]) - 4 K[q,r],
-//   H[q,r] = sum_i s_q(i) V[q,i] s_r(i)                     (a second n x n x s contraction),
+//   H[q,r] = sum_i s_q(i) V[q,i] s_r(i)   (needed only for the pairs with a generator),
 //   K[q,r] = sum_{a : q, r in Q_a} sum_i W[a,i] s_q(i) s_r(i).
-// The work is O(n^2 s + l |Q_a|^2 s) instead of nnz(P_A) s, and nnz(P_A) is
-// about l |Q_a| n for all one- and two-body gates. FP32 arithmetic, FP64
+// The work is O(p s + l |Q_a|^2 s), p = number of qubit pairs carrying a
+// generator, instead of nnz(P_A) s, and nnz(P_A) is about l |Q_a| n for all
+// one- and two-body gates. FP32 arithmetic, FP64
 // reductions over samples, K accumulated in 64-bit fixed point (integer
 // atomics, so the gradient is bitwise reproducible).
 //
@@ -28,91 +29,171 @@ namespace iqp {
 namespace {
 
 constexpr int kQMax = 1024;  // observable weight limit (support list in shared memory)
-constexpr int kCQ = 64;      // C restricted to Q_a is staged in shared memory for |Q_a| <= 64
+constexpr int kPairMax = 1024;  // pairs of Q_a held in shared memory per round
 constexpr int kBlk = 256;    // samples per CTA in the per-observable kernels
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// d_q and C_qr from the support list (q0 < q1 < ... , count).
-__global__ void k_lo_build(const int4 *__restrict__ sup, const float *__restrict__ c, int64_t m, float *__restrict__ C,
-                           int64_t ldc, float *__restrict__ d, uint32_t *__restrict__ status) {
+// Optional self-checks (-DIQP_LO_CHECKS): an index out of its buffer records
+// status 100 + site and the access is skipped.
+#ifdef IQP_LO_CHECKS
+#define LO_OK(cond, site) ((cond) ? true : (record_status(status_dbg, 100u + (site)), false))
+#else
+#define LO_OK(cond, site) true
+#endif
+
+// d_q, C_qr and E (bits r of row q and q of row r set iff some generator
+// acts on {q, r}),
+// from the support list (q0 < q1 < ..., count).
+__global__ void k_lo_build(const int4 *__restrict__ sup, const float *__restrict__ c, int64_t m, int64_t n,
+                           float *__restrict__ C, int64_t ldc, float *__restrict__ d,
+                           unsigned long long *__restrict__ E, int64_t lde, uint32_t *__restrict__ status) {
+    [[maybe_unused]] uint32_t *status_dbg = status;
+    (void)n;
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const int4 sp = sup[j];
+        if (!LO_OK(sp.w <= 0 || (sp.x >= 0 && sp.x < n && (sp.w < 2 || (sp.y > sp.x && sp.y < n))), 8)) continue;
         if (sp.w == 1) {
             atomicAdd(d + sp.x, c[j]);
         } else if (sp.w == 2) {
             atomicAdd(C + (int64_t)sp.x * ldc + sp.y, c[j]);
             atomicAdd(C + (int64_t)sp.y * ldc + sp.x, c[j]);
+            atomicOr(E + (int64_t)sp.x * lde + (sp.y >> 6), 1ull << (sp.y & 63));
+            atomicOr(E + (int64_t)sp.y * lde + (sp.x >> 6), 1ull << (sp.x & 63));
         } else if (sp.w > 2) {
             record_status(status, IQP_ERR_ARG);
         }
     }
 }
 
-// out[p][i] = sum_{k < K} A[p][k] sa(p,k) sb(i,k), sb(i,k) = 1 - 2 bit k of
-// row i of Bb, sa likewise from Ab (or 1 when Ab is null). A: P x lda fp32,
-// Bb: I x ldb words, Ab: P x ldab words, out: P x ldo fp32. 128 x 128 tiles,
-// 8 x 8 per thread, 32-wide K steps; FP32 FMA in k order.
-constexpr int GM = 128, GN = 128, GK = 32, GPAD = 4;
+// ------------------------------------------------ pair contractions
+// Both n x n x s contractions visit only the pairs that carry a generator
+// (the set bits of E): one warp per (qubit q, range of 2048 samples), lane
+// l owning the 64 samples of word 32 range + l of every ZT row, each term a
+// sign flip and an FP32 add (as in the row-sparse form).
 
-__global__ void __launch_bounds__(256) k_lo_gemm(const float *__restrict__ A, int64_t lda,
-                                                 const uint32_t *__restrict__ Ab, int64_t ldab32,
-                                                 const uint32_t *__restrict__ Bb, int64_t ldb32, int64_t P, int64_t I,
-                                                 int64_t K, float *__restrict__ out, int64_t ldo) {
-    __shared__ __align__(16) float As[GK][GM + GPAD];
-    __shared__ __align__(16) float Bs[GK][GN + GPAD];
-    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t i0 = (int64_t)blockIdx.x * GN, p0 = (int64_t)blockIdx.y * GM;
-    float acc[8][8];
-#pragma unroll
-    for (int r = 0; r < 8; ++r)
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
-    const int ar = tid & 127, ac = (tid >> 7) * 16;  // A loader: row, first of 16 k's
-    const int64_t prow = p0 + ar;
-    for (int64_t k0 = 0; k0 < K; k0 += GK) {
-        // A tile, transposed to k-major, with the optional sign from Ab.
-        uint32_t fl = 0u;
-        if (Ab != nullptr && prow < P) fl = Ab[prow * ldab32 + (k0 >> 5)] >> ac;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int64_t k = k0 + ac + q;
-            float v = (prow < P && k < K) ? A[prow * lda + k] : 0.f;
-            if ((fl >> q) & 1u) v = -v;
-            As[ac + q][ar] = v;
-        }
-        // B tile: +-1 from 32 bits of row i.
-        if (tid < GN) {
-            const int64_t i = i0 + tid;
-            const uint32_t b = i < I ? Bb[i * ldb32 + (k0 >> 5)] : 0u;
-#pragma unroll
-            for (int q = 0; q < GK; ++q) Bs[q][tid] = ((b >> q) & 1u) ? -1.f : 1.f;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int k = 0; k < GK; ++k) {
-            const float4 a_lo = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
-            const float4 a_hi = *reinterpret_cast<const float4 *>(&As[k][64 + ty * 4]);
-            const float4 b_lo = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
-            const float4 b_hi = *reinterpret_cast<const float4 *>(&Bs[k][64 + tx * 4]);
-            const float av[8] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
-            const float bv[8] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
-#pragma unroll
-            for (int r = 0; r < 8; ++r)
-#pragma unroll
-                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(av[r], bv[q], acc[r][q]);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-        const int64_t p = p0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
-        if (p >= P) continue;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int64_t i = i0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + (q - 4));
-            if (i < I) out[p * ldo + i] = acc[r][q];
+// fn(r) for every set bit r of E row q, in increasing r, warp-uniformly.
+template <class F>
+__device__ __forceinline__ void for_each_bit(const unsigned long long *__restrict__ row, int64_t nw, int lane, F &fn) {
+    for (int64_t w0 = 0; w0 < nw; w0 += 32) {
+        const uint64_t bits = w0 + lane < nw ? row[w0 + lane] : 0ull;
+        uint32_t live = __ballot_sync(kFull, bits != 0ull);
+        while (live) {
+            const int src = __ffs(live) - 1;
+            live &= live - 1u;
+            uint64_t wb = __shfl_sync(kFull, bits, src);
+            const int64_t rb = (w0 + src) * 64;
+            while (wb) {
+                const int b = __ffsll((long long)wb) - 1;
+                wb &= wb - 1ull;
+                fn(rb + b);
+            }
         }
     }
+}
+
+// M[q][i] = sum_{r in E_q} C_qr s_r(i) (M = C S restricted to the pairs with
+// a generator, which is all of C's nonzeros). Grid (n, ranges) x 32 threads.
+__global__ void __launch_bounds__(32) k_lo_cs(const unsigned long long *__restrict__ E, int64_t lde,
+                                              const float *__restrict__ C, int64_t ldc,
+                                              const uint64_t *__restrict__ ZT, int64_t ldzt, int64_t s,
+                                              float *__restrict__ M, int64_t lds) {
+    const int lane = threadIdx.x;
+    const int64_t q = blockIdx.x, r0 = blockIdx.y;
+    const int64_t vwords = cdiv(s, 64);
+    const int64_t wraw = r0 * 32 + lane;
+    const int64_t word = wraw < vwords ? wraw : vwords - 1;  // in-bounds load, result unused
+    float acc[64];
+#pragma unroll
+    for (int k = 0; k < 64; ++k) acc[k] = 0.f;
+    const float *crow = C + q * ldc;
+    auto visit = [&](int64_t r) {
+        const uint64_t z = __ldg(ZT + r * ldzt + word);
+        const uint32_t cb = __float_as_uint(__ldg(crow + r));
+        const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[k] += __uint_as_float(cb ^ ((lo << (31 - k)) & 0x80000000u));
+#pragma unroll
+        for (int k = 0; k < 32; ++k) acc[32 + k] += __uint_as_float(cb ^ ((hi << (31 - k)) & 0x80000000u));
+    };
+    for_each_bit(E + q * lde, lde, lane, visit);
+    if (wraw < vwords) {
+        float *mrow = M + q * lds + wraw * 64;  // lds is a multiple of 64
+#pragma unroll
+        for (int k = 0; k < 64; k += 4) *reinterpret_cast<float4 *>(mrow + k) = make_float4(acc[k], acc[k + 1], acc[k + 2], acc[k + 3]);
+    }
+}
+
+// H[q][r] = sum_i s_q(i) V[q][i] s_r(i) for r in E_q. Warp (q, k) takes
+// every kHSplit-th set bit of E_q starting at the k-th and walks the sample
+// ranges in order, so each H[q][r] is accumulated by one warp alone (fixed
+// order, FP32 per range, FP64 across ranges).
+constexpr int kHSplit = 8;
+
+__global__ void __launch_bounds__(32) k_lo_h(const unsigned long long *__restrict__ E, int64_t lde,
+                                             const uint64_t *__restrict__ ZT, int64_t ldzt,
+                                             const float *__restrict__ V, int64_t lds, int64_t s,
+                                             double *__restrict__ Hd, int64_t ldh) {
+    const int lane = threadIdx.x;
+    const int64_t q = blockIdx.x;
+    const int split = blockIdx.y;
+    const int64_t vwords = cdiv(s, 64);
+    const int64_t nranges = cdiv(vwords, 32);
+    double *hrow = Hd + q * ldh;
+    for (int64_t r0 = 0; r0 < nranges; ++r0) {
+        const int64_t wraw = r0 * 32 + lane;
+        const bool wvalid = wraw < vwords;
+        const int64_t word = wvalid ? wraw : vwords - 1;
+        // U = s_q V_q for the lane's 64 samples (V is zero beyond s).
+        float u[64];
+        const uint64_t zq = __ldg(ZT + q * ldzt + word);
+        const float *vrow = V + q * lds + word * 64;
+#pragma unroll
+        for (int k = 0; k < 64; k += 4) {
+            const float4 v4 = wvalid ? *reinterpret_cast<const float4 *>(vrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+            u[k] = v4.x;
+            u[k + 1] = v4.y;
+            u[k + 2] = v4.z;
+            u[k + 3] = v4.w;
+        }
+#pragma unroll
+        for (int k = 0; k < 64; ++k) u[k] = ((zq >> k) & 1ull) ? -u[k] : u[k];
+        int idx = 0;
+        auto visit = [&](int64_t r) {
+            if ((idx++ % kHSplit) != split) return;  // warp-uniform
+            const uint64_t z = __ldg(ZT + r * ldzt + word);
+            const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
+            float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                p[k & 7] += __uint_as_float(__float_as_uint(u[k]) ^ ((lo << (31 - k)) & 0x80000000u));
+#pragma unroll
+            for (int k = 0; k < 32; ++k)
+                p[k & 7] += __uint_as_float(__float_as_uint(u[32 + k]) ^ ((hi << (31 - k)) & 0x80000000u));
+            float dsum = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) dsum += __shfl_xor_sync(kFull, dsum, off);
+            if (lane == 0) hrow[r] = r0 == 0 ? (double)dsum : hrow[r] + (double)dsum;
+        };
+        for_each_bit(E + q * lde, lde, lane, visit);
+    }
+}
+
+// Exclusive prefix sum of v over the CTA (every thread calls it); *total
+// receives the sum.
+__device__ int block_scan(int v, int *scan, int *total) {
+    const int tid = threadIdx.x;
+    scan[tid] = v;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // inclusive (Hillis-Steele)
+        const int u = tid >= off ? scan[tid - off] : 0;
+        __syncthreads();
+        scan[tid] += u;
+        __syncthreads();
+    }
+    const int incl = scan[tid];
+    *total = scan[blockDim.x - 1];
+    __syncthreads();
+    return incl - v;
 }
 
 // The support of observable a in increasing qubit order into Q (shared);
@@ -120,32 +201,24 @@ __global__ void __launch_bounds__(256) k_lo_gemm(const float *__restrict__ A, in
 // Every thread of the CTA calls it.
 __device__ int support_of_row(const uint64_t *__restrict__ arow, int64_t n, int *Q, int *scan,
                               uint32_t *__restrict__ status) {
+    [[maybe_unused]] uint32_t *status_dbg = status;
     const int tid = threadIdx.x;
     const int64_t nw = (n + 63) >> 6;
     int total = 0;
     for (int64_t base = 0; base < nw; base += blockDim.x) {
         uint64_t w = base + tid < nw ? arow[base + tid] : 0ull;
         if (base + tid == nw - 1 && (n & 63)) w &= (1ull << (n & 63)) - 1ull;  // never a qubit >= n
-        const int cnt = __popcll(w);
-        scan[tid] = cnt;
-        __syncthreads();
-        // inclusive scan over the CTA (Hillis-Steele)
-        for (int off = 1; off < (int)blockDim.x; off <<= 1) {
-            const int v = tid >= off ? scan[tid - off] : 0;
-            __syncthreads();
-            scan[tid] += v;
-            __syncthreads();
-        }
-        int pos = total + scan[tid] - cnt;
+        int sum = 0;
+        int pos = total + block_scan(__popcll(w), scan, &sum);
         while (w) {
             const int b = __ffsll((long long)w) - 1;
             w &= w - 1ull;
-            if (pos < kQMax) Q[pos] = (int)(64 * (base + tid) + b);
+            if (pos < kQMax && LO_OK(64 * (base + tid) + b < n, 1)) Q[pos] = (int)(64 * (base + tid) + b);
             ++pos;
         }
-        total += scan[blockDim.x - 1];
-        __syncthreads();
+        total += sum;
     }
+    __syncthreads();  // Q is complete before anyone reads it
     if (total > kQMax) {
         if (tid == 0) record_status(status, IQP_ERR_UNSUPPORTED);
         total = kQMax;
@@ -153,49 +226,67 @@ __device__ int support_of_row(const uint64_t *__restrict__ arow, int64_t n, int 
     return total;
 }
 
-// Bits of the lane's sample for qubits Q[t0 .. t0+cnt) (bit t - t0).
-__device__ __forceinline__ uint32_t sample_bits(const int *Q, int t0, int cnt, const uint64_t *__restrict__ ZT,
-                                                int64_t ldzt, int64_t wi, int bi) {
-    uint32_t m = 0u;
-    for (int t = 0; t < cnt; ++t) m |= (uint32_t)((ZT[(int64_t)Q[t0 + t] * ldzt + wi] >> bi) & 1ull) << t;
-    return m;
+// Shared state of the per-(observable, 256-sample block) kernels.
+struct LoShared {
+    int Q[kQMax];              // support of the observable
+    uint32_t bits[kQMax][8];   // bit (i - i0) of word i/32: sample bit of qubit Q[t]
+    int pr[kPairMax];          // pairs t | u << 16 (t < u) with a generator on {Q[t], Q[u]}
+    float pc[kPairMax];        // C restricted to those pairs
+    int scan[kBlk];
+    int npairs;
+    double red[kBlk / 32];
+};
+
+// Support and the block's sample bits for every support qubit.
+__device__ int lo_setup(LoShared &sh, const uint64_t *__restrict__ arow, int64_t n, const uint64_t *__restrict__ ZT,
+                        int64_t ldzt, int64_t blk, uint32_t *__restrict__ status) {
+    [[maybe_unused]] uint32_t *status_dbg = status;
+    const int nq = support_of_row(arow, n, sh.Q, sh.scan, status);
+    for (int e = threadIdx.x; e < nq * 4; e += kBlk) {
+        const int t = e >> 2, k = e & 3;
+        const int64_t w = blk * 4 + k;
+        const bool okq = LO_OK(t < kQMax && sh.Q[t] >= 0 && sh.Q[t] < n, 2);
+        const uint64_t z = (w < ldzt && okq) ? ZT[(int64_t)sh.Q[t] * ldzt + w] : 0ull;
+        sh.bits[t][2 * k] = (uint32_t)z;
+        sh.bits[t][2 * k + 1] = (uint32_t)(z >> 32);
+    }
+    __syncthreads();
+    return nq;
 }
 
-// Phi for one sample (see the header), the pair term over chunks of 32
-// support qubits whose sample bits are gathered once per chunk.
-__device__ float lo_phase(const int *Q, int nq, const float *CQ, const float *__restrict__ C, int64_t ldc,
-                          const float *__restrict__ d, const float *__restrict__ M, int64_t lds,
-                          const uint64_t *__restrict__ ZT, int64_t ldzt, int64_t ic) {
-    const int64_t wi = ic >> 6;
-    const int bi = (int)(ic & 63);
-    float phi = 0.f;
-    for (int t = 0; t < nq; ++t) {
-        const int q = Q[t];
-        const float v = d[q] + M[(int64_t)q * lds + ic];
-        phi += ((ZT[(int64_t)q * ldzt + wi] >> bi) & 1ull) ? -v : v;
-    }
-    float pairs = 0.f;
-    const int nch = (nq + 31) >> 5;
-    for (int T = 0; T < nch; ++T) {
-        const int tn = nq - 32 * T < 32 ? nq - 32 * T : 32;
-        const uint32_t mT = sample_bits(Q, 32 * T, tn, ZT, ldzt, wi, bi);
-        for (int U = T; U < nch; ++U) {
-            const int un = nq - 32 * U < 32 ? nq - 32 * U : 32;
-            const uint32_t mU = U == T ? mT : sample_bits(Q, 32 * U, un, ZT, ldzt, wi, bi);
-            for (int t = 0; t < tn; ++t) {
-                const int tt = 32 * T + t;
-                const uint32_t st = (mT >> t) & 1u;
-                float acc = 0.f;
-                for (int u = (U == T ? t + 1 : 0); u < un; ++u) {
-                    const int uu = 32 * U + u;
-                    const float cv = nq <= kCQ ? CQ[tt * nq + uu] : C[(int64_t)Q[tt] * ldc + Q[uu]];
-                    acc += ((st ^ (mU >> u)) & 1u) ? -cv : cv;
-                }
-                pairs += acc;
+// Appends, in (t, u) order, the next pairs with a generator, scanning the
+// candidates c = t nq + u from *c0 until the list holds kPairMax - kBlk or
+// more entries or the candidates run out. Every thread calls it.
+__device__ void lo_fill_pairs(LoShared &sh, int nq, int64_t *c0, const unsigned long long *__restrict__ E,
+                              int64_t lde, const float *__restrict__ C, int64_t ldc, int64_t n,
+                              [[maybe_unused]] uint32_t *__restrict__ status_dbg) {
+    (void)n;
+    const int64_t ncand = (int64_t)nq * nq;
+    if (threadIdx.x == 0) sh.npairs = 0;
+    __syncthreads();
+    while (*c0 < ncand && sh.npairs <= kPairMax - kBlk) {
+        const int64_t c = *c0 + threadIdx.x;
+        int t = 0, u = 0;
+        bool ok = false;
+        if (c < ncand) {
+            t = (int)(c / nq);
+            u = (int)(c - (int64_t)t * nq);
+            if (u > t && LO_OK(t < nq && u < nq, 3)) {
+                const int q = sh.Q[t], r = sh.Q[u];
+                if (LO_OK(q >= 0 && q < n && r >= 0 && r < n, 4)) ok = (E[(int64_t)q * lde + (r >> 6)] >> (r & 63)) & 1ull;
             }
         }
+        int added = 0;
+        const int pos = sh.npairs + block_scan(ok ? 1 : 0, sh.scan, &added);
+        if (ok && LO_OK(pos >= 0 && pos < kPairMax, 5)) {
+            sh.pr[pos] = t | (u << 16);
+            sh.pc[pos] = C[(int64_t)sh.Q[t] * ldc + sh.Q[u]];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) sh.npairs += added;
+        *c0 += kBlk;
+        __syncthreads();
     }
-    return phi - 2.f * pairs;
 }
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -212,36 +303,56 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 
 // MODE 0: (sum cos, sum (cos - mean)^2) per (observable, 256 samples) into
 // part. MODE 1: W[a][i] = sin Phi (alpha_a + beta_a cos Phi), zero for i >= s.
+// One thread per sample; the pair term visits only the pairs of Q_a that
+// carry a generator (C_qr is zero on the others).
 template <int MODE>
 __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
                                                    const uint64_t *__restrict__ ZT, int64_t ldzt,
                                                    const float *__restrict__ M, int64_t lds,
                                                    const float *__restrict__ C, int64_t ldc,
-                                                   const float *__restrict__ d, int64_t s, int64_t nparts,
-                                                   double2 *__restrict__ part, const double *__restrict__ alpha,
-                                                   const double *__restrict__ beta, float *__restrict__ W,
-                                                   uint32_t *__restrict__ status) {
-    __shared__ int Q[kQMax];
-    __shared__ float CQ[kCQ * kCQ];
-    __shared__ int scan[kBlk];
-    __shared__ double red[kBlk / 32];
+                                                   const float *__restrict__ d, const unsigned long long *__restrict__ E,
+                                                   int64_t lde, int64_t s, int64_t nparts, double2 *__restrict__ part,
+                                                   const double *__restrict__ alpha, const double *__restrict__ beta,
+                                                   float *__restrict__ W, uint32_t *__restrict__ status) {
+    __shared__ LoShared sh;
     const int64_t a = blockIdx.x, blk = blockIdx.y;
-    const int nq = support_of_row(A + a * lda, n, Q, scan, status);
-    if (nq <= kCQ)
-        for (int e = threadIdx.x; e < nq * nq; e += kBlk) CQ[e] = C[(int64_t)Q[e / nq] * ldc + Q[e % nq]];
-    __syncthreads();
-    const int64_t i = blk * kBlk + threadIdx.x;
+    [[maybe_unused]] uint32_t *status_dbg = status;
+    const int nq = lo_setup(sh, A + a * lda, n, ZT, ldzt, blk, status);
+    const int tid = threadIdx.x, w = tid >> 5, bit = tid & 31;
+    const int64_t i = blk * kBlk + tid;
     const bool valid = i < s;
     const int64_t ic = valid ? i : s - 1;
-    const float phi = lo_phase(Q, nq, CQ, C, ldc, d, M, lds, ZT, ldzt, ic);
+    float phi = 0.f;
+    for (int t = 0; t < nq; ++t) {
+        const int q = sh.Q[t];
+        if (!LO_OK(q >= 0 && q < n && ic >= 0 && ic < lds, 7)) continue;
+        const float v = d[q] + M[(int64_t)q * lds + ic];
+        phi += ((sh.bits[t][w] >> bit) & 1u) ? -v : v;
+    }
+    float pairs = 0.f;
+    int64_t c0 = 0;
+    const int64_t ncand = (int64_t)nq * nq;
+    while (c0 < ncand) {
+        lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
+        const int np = sh.npairs;
+        for (int p = 0; p < np; ++p) {
+            const int pr = sh.pr[p];
+            if (!LO_OK((pr & 0xFFFF) < nq && (pr >> 16) < nq && p < kPairMax, 6)) continue;
+            const uint32_t x = sh.bits[pr & 0xFFFF][w] ^ sh.bits[pr >> 16][w];
+            const float cv = sh.pc[p];
+            pairs += ((x >> bit) & 1u) ? -cv : cv;
+        }
+        __syncthreads();
+    }
+    phi -= 2.f * pairs;
     if (MODE == 0) {
         const float cv = valid ? cosf(phi) : 0.f;
-        const double S = block_sum((double)cv, red);
+        const double S = block_sum((double)cv, sh.red);
         const int64_t nb = s - blk * kBlk < kBlk ? s - blk * kBlk : kBlk;
         const float mean = (float)(S / (double)nb);
         const float dv = cv - mean;
-        const double M2 = block_sum(valid ? (double)(dv * dv) : 0.0, red);
-        if (threadIdx.x == 0) part[a * nparts + blk] = make_double2(S, M2);
+        const double M2 = block_sum(valid ? (double)(dv * dv) : 0.0, sh.red);
+        if (tid == 0) part[a * nparts + blk] = make_double2(S, M2);
     } else {
         float sn, cn;
         sincosf(phi, &sn, &cn);
@@ -286,47 +397,54 @@ __device__ __forceinline__ long long to_fixed(float x, float sc) {
     return ((long long)__float2int_rz(hi) << 31) + (long long)__float2int_rn(lo);
 }
 
-// K[q][r] (q < r in Q_a) += sum_i W[a][i] s_q(i) s_r(i), one warp per pair,
-// in 64-bit fixed point with scale `scale`.
+// K[q][r] += sum over the block's samples of W[a][i] s_q(i) s_r(i) for the
+// pairs q < r of Q_a that carry a generator (the only K entries the
+// gradient reads); one warp per pair, 8 samples per lane, one fixed-point
+// atomic per (pair, block).
 __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
                                                    const uint64_t *__restrict__ ZT, int64_t ldzt,
+                                                   const float *__restrict__ C, int64_t ldc,
+                                                   const unsigned long long *__restrict__ E, int64_t lde,
                                                    const float *__restrict__ W, int64_t lds, int64_t s,
                                                    const double *__restrict__ scale,
                                                    unsigned long long *__restrict__ Kfx,
                                                    uint32_t *__restrict__ status) {
-    __shared__ int Q[kQMax];
-    __shared__ int scan[kBlk];
-    const int64_t a = blockIdx.x;
-    const int nq = support_of_row(A + a * lda, n, Q, scan, status);
+    __shared__ LoShared sh;
+    __shared__ float wb[kBlk];
+    const int64_t a = blockIdx.x, blk = blockIdx.y;
+    const int nq = lo_setup(sh, A + a * lda, n, ZT, ldzt, blk, status);
+    const int64_t i = blk * kBlk + threadIdx.x;
+    wb[threadIdx.x] = i < s ? W[a * lds + i] : 0.f;
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float sc = (float)*scale;
-    const int64_t npairs = (int64_t)nq * (nq - 1) / 2;
-    const float *wrow = W + a * lds;
-    for (int64_t p = warp; p < npairs; p += kBlk / 32) {
-        int t = 0;
-        int64_t rem = p;
-        while (rem >= nq - 1 - t) {
-            rem -= nq - 1 - t;
-            ++t;
-        }
-        const int u = t + 1 + (int)rem;
-        const uint64_t *zt = ZT + (int64_t)Q[t] * ldzt;
-        const uint64_t *zu = ZT + (int64_t)Q[u] * ldzt;
-        float acc = 0.f;
-        for (int64_t i = lane; i < s; i += 32) {
-            const uint64_t x = (zt[i >> 6] ^ zu[i >> 6]) >> (i & 63);
-            const float w = wrow[i];
-            acc += (x & 1ull) ? -w : w;
-        }
+    int64_t c0 = 0;
+    const int64_t ncand = (int64_t)nq * nq;
+    while (c0 < ncand) {
+        lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
+        const int np = sh.npairs;
+        for (int p = warp; p < np; p += kBlk / 32) {
+            const int pr = sh.pr[p];
+            const int t = pr & 0xFFFF, u = pr >> 16;
+            float acc = 0.f;
 #pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-        if (lane == 0) atomicAdd(Kfx + (int64_t)Q[t] * n + Q[u], (unsigned long long)to_fixed(acc, sc));
+            for (int k = 0; k < 8; ++k) {
+                const uint32_t x = sh.bits[t][k] ^ sh.bits[u][k];
+                const float v = wb[32 * k + lane];
+                acc += ((x >> lane) & 1u) ? -v : v;
+            }
+#pragma unroll
+            for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
+            if (lane == 0)
+                atomicAdd(Kfx + (int64_t)sh.Q[t] * n + sh.Q[u], (unsigned long long)to_fixed(acc, sc));
+        }
+        __syncthreads();
     }
 }
 
 // grad_j from the parts above (see the header).
 __global__ void k_lo_grad_out(const int4 *__restrict__ sup, int64_t m, int64_t n, const double *__restrict__ gsp,
-                              int64_t nblk, const float *__restrict__ H, int64_t ldh,
+                              int64_t nblk, const double *__restrict__ H, int64_t ldh,
                               const unsigned long long *__restrict__ Kfx, const double *__restrict__ scale,
                               double *__restrict__ grad) {
     const double inv = 1.0 / *scale;
@@ -339,7 +457,7 @@ __global__ void k_lo_grad_out(const int4 *__restrict__ sup, int64_t m, int64_t n
             g = 2.0 * t;
         } else if (sp.w == 2) {
             const int64_t q = sp.x, r = sp.y;
-            const double h = (double)H[q * ldh + r] + (double)H[r * ldh + q];
+            const double h = H[q * ldh + r] + H[r * ldh + q];
             const double k = (double)(long long)Kfx[q * n + r] * inv;
             g = 2.0 * h - 4.0 * k;
         }
@@ -366,6 +484,11 @@ int64_t lo_part_samples() { return kBlk; }
 
 // C, d and M = C S. C: n x ldc fp32 (+ d: ldc fp32 after it), M: n x lds,
 // ZT: n x ldzt words (the samples transposed), sup: m int4.
+int64_t lo_lde(int64_t n) { return cdiv(n, 64); }
+
+// C, d, E and M = C S. C: n x ldc fp32 (+ d: ldc fp32 after it), E: n x
+// lo_lde(n) words right after d, M: n x lds, ZT: n x ldzt words (the samples
+// transposed), sup: m int4.
 cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *Z, int64_t s,
                               int64_t ldz, const float *c, int4 *sup, uint64_t *ZT, int64_t ldzt, float *C,
                               int64_t ldc, float *M, int64_t lds, uint32_t *status, cudaStream_t st) {
@@ -373,16 +496,17 @@ cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t l
     if (e != cudaSuccess) return e;
     if ((e = launch_bit_transpose_batched(Z, 1, s, n, ldz, ZT, ldzt, st)) != cudaSuccess) return e;
     float *d = C + n * ldc;
-    if ((e = cudaMemsetAsync(C, 0, (size_t)(n + 1) * ldc * sizeof(float), st)) != cudaSuccess) return e;
+    unsigned long long *E = reinterpret_cast<unsigned long long *>(d + ldc);
+    const int64_t lde = lo_lde(n);
+    if ((e = cudaMemsetAsync(C, 0, (size_t)(n + 1) * ldc * sizeof(float) + (size_t)n * lde * 8, st)) != cudaSuccess)
+        return e;
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_build<<<grid_1d(m), 256, 0, st>>>(sup, c, m, C, ldc, d, status);
+        k_lo_build<<<grid_1d(m), 256, 0, st>>>(sup, c, m, n, C, ldc, d, E, lde, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     LaunchScope ls(IQP_KERNEL_LOWORDER_GEMM, st);
-    // M[q][i] = sum_r C[q][r] s_r(i): A = C, B bits = Z rows (bits over qubits).
-    k_lo_gemm<<<dim3((unsigned)cdiv(s, GN), (unsigned)cdiv(n, GM)), 256, 0, st>>>(
-        C, ldc, nullptr, 0, reinterpret_cast<const uint32_t *>(Z), 2 * ldz, n, s, n, M, lds);
+    k_lo_cs<<<dim3((unsigned)n, (unsigned)cdiv(s, 2048)), 32, 0, st>>>(E, lde, C, ldc, ZT, ldzt, s, M, lds);
     return cudaGetLastError();
 }
 
@@ -390,9 +514,11 @@ cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l
                             const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, double2 *part,
                             int64_t nparts, uint32_t *status, cudaStream_t st) {
     LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-    k_lo_phase<0><<<dim3((unsigned)l, (unsigned)nparts), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc,
-                                                                       C + n * ldc, s, nparts, part, nullptr,
-                                                                       nullptr, nullptr, status);
+    const float *d = C + n * ldc;
+    const unsigned long long *E = reinterpret_cast<const unsigned long long *>(d + ldc);
+    k_lo_phase<0><<<dim3((unsigned)l, (unsigned)nparts), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d, E,
+                                                                       lo_lde(n), s, nparts, part, nullptr, nullptr,
+                                                                       nullptr, status);
     return cudaGetLastError();
 }
 
@@ -401,19 +527,22 @@ cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l
 cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
                            const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
-                           float *W, float *V, float *H, double *gsp, unsigned long long *Kfx, double *grad,
+                           float *W, float *V, double *H, double *gsp, unsigned long long *Kfx, double *grad,
                            uint32_t *status, cudaStream_t st) {
     const int64_t nblk = cdiv(s, kBlk);
     double *scale = reinterpret_cast<double *>(Kfx + n * n);
+    const float *d = C + n * ldc;
+    const unsigned long long *E = reinterpret_cast<const unsigned long long *>(d + ldc);
+    const int64_t lde = lo_lde(n);
     cudaError_t e = launch_bit_transpose_batched(A, 1, l, n, lda, AT, ldlt, st);
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(Kfx, 0, (size_t)n * n * sizeof(unsigned long long), st)) != cudaSuccess) return e;
     if ((e = launch_fixed_scale(alpha, beta, l, s, scale, st)) != cudaSuccess) return e;
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_phase<1><<<dim3((unsigned)l, (unsigned)nblk), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc,
-                                                                         C + n * ldc, s, nblk, nullptr, alpha, beta,
-                                                                         W, status);
+        k_lo_phase<1><<<dim3((unsigned)l, (unsigned)nblk), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d,
+                                                                         E, lde, s, nblk, nullptr, alpha, beta, W,
+                                                                         status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
@@ -422,16 +551,14 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
-        // H[q][r] = sum_i (s_q(i) V[q][i]) s_r(i): A = V with signs from ZT, B bits = ZT rows.
         LaunchScope ls(IQP_KERNEL_LOWORDER_GEMM, st);
-        const uint32_t *zt32 = reinterpret_cast<const uint32_t *>(ZT);
-        k_lo_gemm<<<dim3((unsigned)cdiv(n, GN), (unsigned)cdiv(n, GM)), 256, 0, st>>>(V, lds, zt32, 2 * ldzt, zt32,
-                                                                                       2 * ldzt, n, n, s, H, ldc);
+        k_lo_h<<<dim3((unsigned)n, (unsigned)kHSplit), 32, 0, st>>>(E, lde, ZT, ldzt, V, lds, s, H, ldc);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_pairs<<<(unsigned)l, kBlk, 0, st>>>(A, lda, n, ZT, ldzt, W, lds, s, scale, Kfx, status);
+        k_lo_pairs<<<dim3((unsigned)l, (unsigned)nblk), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, C, ldc, E, lde, W, lds,
+                                                                       s, scale, Kfx, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     LaunchScope ls(IQP_KERNEL_LOWORDER, st);
