@@ -29,7 +29,7 @@ namespace iqp {
 namespace {
 
 constexpr int kQMax = 1024;  // observable weight limit (support list in shared memory)
-constexpr int kPairMax = 1024;  // pairs of Q_a held in shared memory per round
+constexpr int kPairMax = 512;  // pairs of Q_a held in shared memory per round
 constexpr int kBlk = 256;    // samples per CTA in the per-observable kernels
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
@@ -124,57 +124,85 @@ __global__ void __launch_bounds__(32) k_lo_cs(const unsigned long long *__restri
 }
 
 // H[q][r] = sum_i s_q(i) V[q][i] s_r(i) for r in E_q. Warp (q, k) takes
-// every kHSplit-th set bit of E_q starting at the k-th and walks the sample
-// ranges in order, so each H[q][r] is accumulated by one warp alone (fixed
-// order, FP32 per range, FP64 across ranges).
+// every kHSplit-th set bit of E_q starting at the k-th (listed in shared
+// memory, kRMax at a time) and walks the sample ranges in order, so each
+// H[q][r] is accumulated by one warp alone (fixed order, FP32 per range,
+// FP64 across ranges).
 constexpr int kHSplit = 8;
+constexpr int kRMax = 1024;
 
 __global__ void __launch_bounds__(32) k_lo_h(const unsigned long long *__restrict__ E, int64_t lde,
                                              const uint64_t *__restrict__ ZT, int64_t ldzt,
                                              const float *__restrict__ V, int64_t lds, int64_t s,
                                              double *__restrict__ Hd, int64_t ldh) {
+    __shared__ int rl[kRMax];
     const int lane = threadIdx.x;
     const int64_t q = blockIdx.x;
     const int split = blockIdx.y;
     const int64_t vwords = cdiv(s, 64);
     const int64_t nranges = cdiv(vwords, 32);
     double *hrow = Hd + q * ldh;
-    for (int64_t r0 = 0; r0 < nranges; ++r0) {
-        const int64_t wraw = r0 * 32 + lane;
-        const bool wvalid = wraw < vwords;
-        const int64_t word = wvalid ? wraw : vwords - 1;
-        // U = s_q V_q for the lane's 64 samples (V is zero beyond s).
-        float u[64];
-        const uint64_t zq = __ldg(ZT + q * ldzt + word);
-        const float *vrow = V + q * lds + word * 64;
-#pragma unroll
-        for (int k = 0; k < 64; k += 4) {
-            const float4 v4 = wvalid ? *reinterpret_cast<const float4 *>(vrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
-            u[k] = v4.x;
-            u[k + 1] = v4.y;
-            u[k + 2] = v4.z;
-            u[k + 3] = v4.w;
+    const unsigned long long *erow = E + q * lde;
+    int seen = 0;        // set bits of E_q visited so far
+    int64_t w0 = 0;      // next E word to scan
+    while (w0 < lde) {
+        // list this warp's next pairs
+        int nr = 0;
+        while (w0 < lde && nr <= kRMax - 64) {
+            const uint64_t bits0 = erow[w0];
+            uint64_t bits = bits0;
+            // bit b of the word is this warp's when (seen + rank of b) % kHSplit == split
+            const int rank_start = seen;
+            const int cnt = __popcll(bits0);
+            if (lane == 0) {
+                int rk = rank_start;
+                while (bits) {
+                    const int b = __ffsll((long long)bits) - 1;
+                    bits &= bits - 1ull;
+                    if (rk % kHSplit == split) rl[nr++] = (int)(64 * w0 + b);
+                    ++rk;
+                }
+            }
+            nr = __shfl_sync(kFull, nr, 0);
+            seen += cnt;
+            ++w0;
         }
+        __syncwarp();
+        for (int64_t r0 = 0; r0 < nranges; ++r0) {
+            const int64_t wraw = r0 * 32 + lane;
+            const bool wvalid = wraw < vwords;
+            const int64_t word = wvalid ? wraw : vwords - 1;
+            float u[64];
+            const uint64_t zq = __ldg(ZT + q * ldzt + word);
+            const float *vrow = V + q * lds + word * 64;
 #pragma unroll
-        for (int k = 0; k < 64; ++k) u[k] = ((zq >> k) & 1ull) ? -u[k] : u[k];
-        int idx = 0;
-        auto visit = [&](int64_t r) {
-            if ((idx++ % kHSplit) != split) return;  // warp-uniform
-            const uint64_t z = __ldg(ZT + r * ldzt + word);
-            const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
-            float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            for (int k = 0; k < 64; k += 4) {
+                const float4 v4 = wvalid ? *reinterpret_cast<const float4 *>(vrow + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+                u[k] = v4.x;
+                u[k + 1] = v4.y;
+                u[k + 2] = v4.z;
+                u[k + 3] = v4.w;
+            }
 #pragma unroll
-            for (int k = 0; k < 32; ++k)
-                p[k & 7] += __uint_as_float(__float_as_uint(u[k]) ^ ((lo << (31 - k)) & 0x80000000u));
+            for (int k = 0; k < 64; ++k) u[k] = ((zq >> k) & 1ull) ? -u[k] : u[k];
+            for (int e = 0; e < nr; ++e) {
+                const int64_t r = rl[e];
+                const uint64_t z = __ldg(ZT + r * ldzt + word);
+                const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
+                float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int k = 0; k < 32; ++k)
-                p[k & 7] += __uint_as_float(__float_as_uint(u[32 + k]) ^ ((hi << (31 - k)) & 0x80000000u));
-            float dsum = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+                for (int k = 0; k < 32; ++k)
+                    p[k & 7] += __uint_as_float(__float_as_uint(u[k]) ^ ((lo << (31 - k)) & 0x80000000u));
 #pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) dsum += __shfl_xor_sync(kFull, dsum, off);
-            if (lane == 0) hrow[r] = r0 == 0 ? (double)dsum : hrow[r] + (double)dsum;
-        };
-        for_each_bit(E + q * lde, lde, lane, visit);
+                for (int k = 0; k < 32; ++k)
+                    p[k & 7] += __uint_as_float(__float_as_uint(u[32 + k]) ^ ((hi << (31 - k)) & 0x80000000u));
+                float dsum = ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) dsum += __shfl_xor_sync(kFull, dsum, off);
+                if (lane == 0) hrow[r] = r0 == 0 ? (double)dsum : hrow[r] + (double)dsum;
+            }
+        }
+        __syncwarp();
     }
 }
 
@@ -233,15 +261,19 @@ struct LoShared {
     int pr[kPairMax];          // pairs t | u << 16 (t < u) with a generator on {Q[t], Q[u]}
     float pc[kPairMax];        // C restricted to those pairs
     int scan[kBlk];
-    int npairs;
+    int wsum[kBlk / 32];
     double red[kBlk / 32];
 };
 
-// Support and the block's sample bits for every support qubit.
-__device__ int lo_setup(LoShared &sh, const uint64_t *__restrict__ arow, int64_t n, const uint64_t *__restrict__ ZT,
-                        int64_t ldzt, int64_t blk, uint32_t *__restrict__ status) {
-    [[maybe_unused]] uint32_t *status_dbg = status;
-    const int nq = support_of_row(arow, n, sh.Q, sh.scan, status);
+// Sample blocks handled by one CTA: the support and, when it fits, the
+// pair list are built once and reused for every block.
+constexpr int kGroup = 8;
+constexpr int kObsMax = 4096;  // observables of one qubit listed per pass in k_lo_v
+
+// The sample bits of block blk for every support qubit.
+__device__ void lo_load_bits(LoShared &sh, int nq, int64_t n, const uint64_t *__restrict__ ZT, int64_t ldzt,
+                             int64_t blk, [[maybe_unused]] uint32_t *__restrict__ status_dbg) {
+    __syncthreads();  // previous readers of bits are done
     for (int e = threadIdx.x; e < nq * 4; e += kBlk) {
         const int t = e >> 2, k = e & 3;
         const int64_t w = blk * 4 + k;
@@ -251,20 +283,21 @@ __device__ int lo_setup(LoShared &sh, const uint64_t *__restrict__ arow, int64_t
         sh.bits[t][2 * k + 1] = (uint32_t)(z >> 32);
     }
     __syncthreads();
-    return nq;
 }
 
-// Appends, in (t, u) order, the next pairs with a generator, scanning the
-// candidates c = t nq + u from *c0 until the list holds kPairMax - kBlk or
-// more entries or the candidates run out. Every thread calls it.
-__device__ void lo_fill_pairs(LoShared &sh, int nq, int64_t *c0, const unsigned long long *__restrict__ E,
-                              int64_t lde, const float *__restrict__ C, int64_t ldc, int64_t n,
-                              [[maybe_unused]] uint32_t *__restrict__ status_dbg) {
+// Appends to the pair list, in (t, u) order, the pairs with a generator
+// among the candidates c = t nq + u from *c0 on, 256 per round (compacted
+// with warp ballots), until the list holds more than kPairMax - kBlk
+// entries or the candidates run out. Returns the list length; every thread
+// calls it and gets the same value.
+__device__ int lo_fill_pairs(LoShared &sh, int nq, int64_t *c0, const unsigned long long *__restrict__ E,
+                             int64_t lde, const float *__restrict__ C, int64_t ldc, int64_t n,
+                             [[maybe_unused]] uint32_t *__restrict__ status_dbg) {
     (void)n;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t ncand = (int64_t)nq * nq;
-    if (threadIdx.x == 0) sh.npairs = 0;
-    __syncthreads();
-    while (*c0 < ncand && sh.npairs <= kPairMax - kBlk) {
+    int np = 0;
+    while (*c0 < ncand && np <= kPairMax - kBlk) {
         const int64_t c = *c0 + threadIdx.x;
         int t = 0, u = 0;
         bool ok = false;
@@ -276,17 +309,26 @@ __device__ void lo_fill_pairs(LoShared &sh, int nq, int64_t *c0, const unsigned 
                 if (LO_OK(q >= 0 && q < n && r >= 0 && r < n, 4)) ok = (E[(int64_t)q * lde + (r >> 6)] >> (r & 63)) & 1ull;
             }
         }
-        int added = 0;
-        const int pos = sh.npairs + block_scan(ok ? 1 : 0, sh.scan, &added);
+        const uint32_t bal = __ballot_sync(kFull, ok);
+        if (lane == 0) sh.wsum[warp] = __popc(bal);
+        __syncthreads();
+        int off = np, tot = 0;
+#pragma unroll
+        for (int w = 0; w < kBlk / 32; ++w) {
+            const int v = sh.wsum[w];
+            off += w < warp ? v : 0;
+            tot += v;
+        }
+        const int pos = off + __popc(bal & ((1u << lane) - 1u));
         if (ok && LO_OK(pos >= 0 && pos < kPairMax, 5)) {
             sh.pr[pos] = t | (u << 16);
             sh.pc[pos] = C[(int64_t)sh.Q[t] * ldc + sh.Q[u]];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) sh.npairs += added;
+        np += tot;
         *c0 += kBlk;
         __syncthreads();
     }
+    return np;
 }
 
 __device__ __forceinline__ double block_sum(double v, double *red) {
@@ -304,7 +346,8 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
 // MODE 0: (sum cos, sum (cos - mean)^2) per (observable, 256 samples) into
 // part. MODE 1: W[a][i] = sin Phi (alpha_a + beta_a cos Phi), zero for i >= s.
 // One thread per sample; the pair term visits only the pairs of Q_a that
-// carry a generator (C_qr is zero on the others).
+// carry a generator (C_qr is zero on the others). CTA (a, g) takes sample
+// blocks kGroup g .. kGroup g + kGroup - 1.
 template <int MODE>
 __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
                                                    const uint64_t *__restrict__ ZT, int64_t ldzt,
@@ -314,50 +357,61 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
                                                    int64_t lde, int64_t s, int64_t nparts, double2 *__restrict__ part,
                                                    const double *__restrict__ alpha, const double *__restrict__ beta,
                                                    float *__restrict__ W, uint32_t *__restrict__ status) {
-    __shared__ LoShared sh;
-    const int64_t a = blockIdx.x, blk = blockIdx.y;
     [[maybe_unused]] uint32_t *status_dbg = status;
-    const int nq = lo_setup(sh, A + a * lda, n, ZT, ldzt, blk, status);
+    __shared__ LoShared sh;
+    const int64_t a = blockIdx.x;
+    const int nq = support_of_row(A + a * lda, n, sh.Q, sh.scan, status);
     const int tid = threadIdx.x, w = tid >> 5, bit = tid & 31;
-    const int64_t i = blk * kBlk + tid;
-    const bool valid = i < s;
-    const int64_t ic = valid ? i : s - 1;
-    float phi = 0.f;
-    for (int t = 0; t < nq; ++t) {
-        const int q = sh.Q[t];
-        if (!LO_OK(q >= 0 && q < n && ic >= 0 && ic < lds, 7)) continue;
-        const float v = d[q] + M[(int64_t)q * lds + ic];
-        phi += ((sh.bits[t][w] >> bit) & 1u) ? -v : v;
-    }
-    float pairs = 0.f;
-    int64_t c0 = 0;
     const int64_t ncand = (int64_t)nq * nq;
-    while (c0 < ncand) {
-        lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
-        const int np = sh.npairs;
-        for (int p = 0; p < np; ++p) {
-            const int pr = sh.pr[p];
-            if (!LO_OK((pr & 0xFFFF) < nq && (pr >> 16) < nq && p < kPairMax, 6)) continue;
-            const uint32_t x = sh.bits[pr & 0xFFFF][w] ^ sh.bits[pr >> 16][w];
-            const float cv = sh.pc[p];
-            pairs += ((x >> bit) & 1u) ? -cv : cv;
+    int64_t c0 = 0;
+    int np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
+    const bool complete = c0 >= ncand;  // the whole list fits: reuse it for every block
+    const float al = MODE == 1 ? (float)alpha[a] : 0.f;
+    const float be = (MODE == 1 && beta) ? (float)beta[a] : 0.f;
+    const int64_t b1 = (blockIdx.y + 1) * (int64_t)kGroup < nparts ? (blockIdx.y + 1) * (int64_t)kGroup : nparts;
+    for (int64_t blk = blockIdx.y * (int64_t)kGroup; blk < b1; ++blk) {
+        lo_load_bits(sh, nq, n, ZT, ldzt, blk, status);
+        const int64_t i = blk * kBlk + tid;
+        const bool valid = i < s;
+        const int64_t ic = valid ? i : s - 1;
+        float phi = 0.f;
+        for (int t = 0; t < nq; ++t) {
+            const int q = sh.Q[t];
+            if (!LO_OK(q >= 0 && q < n && ic >= 0 && ic < lds, 7)) continue;
+            const float v = d[q] + M[(int64_t)q * lds + ic];
+            phi += ((sh.bits[t][w] >> bit) & 1u) ? -v : v;
         }
-        __syncthreads();
-    }
-    phi -= 2.f * pairs;
-    if (MODE == 0) {
-        const float cv = valid ? cosf(phi) : 0.f;
-        const double S = block_sum((double)cv, sh.red);
-        const int64_t nb = s - blk * kBlk < kBlk ? s - blk * kBlk : kBlk;
-        const float mean = (float)(S / (double)nb);
-        const float dv = cv - mean;
-        const double M2 = block_sum(valid ? (double)(dv * dv) : 0.0, sh.red);
-        if (tid == 0) part[a * nparts + blk] = make_double2(S, M2);
-    } else {
-        float sn, cn;
-        sincosf(phi, &sn, &cn);
-        const float al = (float)alpha[a], be = beta ? (float)beta[a] : 0.f;
-        if (i < lds) W[a * lds + i] = valid ? sn * (al + be * cn) : 0.f;
+        float pairs = 0.f;
+        if (!complete && blk != blockIdx.y * (int64_t)kGroup) {
+            c0 = 0;  // the list is rebuilt round by round for every block
+            np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
+        }
+        while (true) {
+            for (int p = 0; p < np; ++p) {
+                const int pr = sh.pr[p];
+                if (!LO_OK((pr & 0xFFFF) < nq && (pr >> 16) < nq && p < kPairMax, 6)) continue;
+                const uint32_t x = sh.bits[pr & 0xFFFF][w] ^ sh.bits[pr >> 16][w];
+                const float cv = sh.pc[p];
+                pairs += ((x >> bit) & 1u) ? -cv : cv;
+            }
+            if (complete || c0 >= ncand) break;
+            __syncthreads();
+            np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
+        }
+        phi -= 2.f * pairs;
+        if (MODE == 0) {
+            const float cv = valid ? cosf(phi) : 0.f;
+            const double S = block_sum((double)cv, sh.red);
+            const int64_t nb = s - blk * kBlk < kBlk ? s - blk * kBlk : kBlk;
+            const float mean = (float)(S / (double)nb);
+            const float dv = cv - mean;
+            const double M2 = block_sum(valid ? (double)(dv * dv) : 0.0, sh.red);
+            if (tid == 0) part[a * nparts + blk] = make_double2(S, M2);
+        } else {
+            float sn, cn;
+            sincosf(phi, &sn, &cn);
+            if (i < lds) W[a * lds + i] = valid ? sn * (al + be * cn) : 0.f;
+        }
     }
 }
 
@@ -369,25 +423,73 @@ __global__ void __launch_bounds__(kBlk) k_lo_v(const uint64_t *__restrict__ AT, 
                                                const float *__restrict__ W, int64_t lds, int64_t s, int64_t nblk,
                                                float *__restrict__ V, double *__restrict__ gsp) {
     __shared__ double red[kBlk / 32];
-    const int64_t q = blockIdx.x, blk = blockIdx.y;
-    const int64_t i = blk * kBlk + threadIdx.x;
-    const bool valid = i < s;
-    const int64_t ic = valid ? i : s - 1;
+    __shared__ int obs[kObsMax];
+    __shared__ int wsum[kBlk / 32];
+    const int64_t q = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t *row = AT + q * ldlt;
-    float v = 0.f;
-    for (int64_t w = 0; w < ldlt; ++w) {
-        uint64_t bits = row[w];
-        while (bits) {
-            const int b = __ffsll((long long)bits) - 1;
-            bits &= bits - 1ull;
-            v += W[(64 * w + b) * lds + ic];
+    const int64_t b0 = blockIdx.y * (int64_t)kGroup;
+    const int64_t b1 = b0 + kGroup < nblk ? b0 + kGroup : nblk;
+    float v[kGroup];
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) v[g] = 0.f;
+    // The observables containing q, kObsMax at a time, in increasing order
+    // (each thread compacts one 64-observable word; warps in order).
+    for (int64_t w0 = 0; w0 < ldlt; w0 += kObsMax / 64) {
+        int no = 0;
+        for (int64_t wb = w0; wb < w0 + kObsMax / 64 && wb < ldlt; wb += kBlk) {
+            const int64_t wi = wb + threadIdx.x;
+            uint64_t bits = (wi < w0 + kObsMax / 64 && wi < ldlt) ? row[wi] : 0ull;
+            const int cnt = __popcll(bits);
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int u = __shfl_up_sync(kFull, incl, off);
+                if (lane >= off) incl += u;
+            }
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            int off = no, tot = 0;
+#pragma unroll
+            for (int k = 0; k < kBlk / 32; ++k) {
+                off += k < warp ? wsum[k] : 0;
+                tot += wsum[k];
+            }
+            int pos = off + incl - cnt;
+            while (bits) {
+                const int b = __ffsll((long long)bits) - 1;
+                bits &= bits - 1ull;
+                obs[pos++] = (int)(64 * wi + b);
+            }
+            no += tot;
+            __syncthreads();
         }
+#pragma unroll
+        for (int g = 0; g < kGroup; ++g) {
+            const int64_t blk = b0 + g;
+            if (blk < b1) {
+                const int64_t i = blk * kBlk + threadIdx.x;
+                const int64_t ic = i < s ? i : s - 1;
+                float acc = v[g];
+                for (int k = 0; k < no; ++k) acc += W[(int64_t)obs[k] * lds + ic];
+                v[g] = acc;
+            }
+        }
+        __syncthreads();
     }
-    if (!valid) v = 0.f;
-    if (i < lds) V[q * lds + i] = v;
-    const float u = ((ZT[q * ldzt + (ic >> 6)] >> (ic & 63)) & 1ull) ? -v : v;
-    const double t = block_sum((double)u, red);
-    if (threadIdx.x == 0) gsp[q * nblk + blk] = t;
+#pragma unroll
+    for (int g = 0; g < kGroup; ++g) {
+        const int64_t blk = b0 + g < b1 ? b0 + g : b1 - 1;  // uniform; repeats of the last block are not stored
+        const bool store = b0 + g < b1;
+        const int64_t i = blk * kBlk + threadIdx.x;
+        const bool valid = i < s;
+        const int64_t ic = valid ? i : s - 1;
+        const float vv = valid ? v[g] : 0.f;
+        if (store && i < lds) V[q * lds + i] = vv;
+        const float u = ((ZT[q * ldzt + (ic >> 6)] >> (ic & 63)) & 1ull) ? -vv : vv;
+        const double t = block_sum((double)u, red);
+        if (store && threadIdx.x == 0) gsp[q * nblk + blk] = t;
+    }
 }
 
 __device__ __forceinline__ long long to_fixed(float x, float sc) {
@@ -397,46 +499,57 @@ __device__ __forceinline__ long long to_fixed(float x, float sc) {
     return ((long long)__float2int_rz(hi) << 31) + (long long)__float2int_rn(lo);
 }
 
-// K[q][r] += sum over the block's samples of W[a][i] s_q(i) s_r(i) for the
-// pairs q < r of Q_a that carry a generator (the only K entries the
-// gradient reads); one warp per pair, 8 samples per lane, one fixed-point
-// atomic per (pair, block).
+// K[q][r] += sum over the samples of W[a][i] s_q(i) s_r(i) for the pairs
+// q < r of Q_a that carry a generator (the only K entries the gradient
+// reads); one warp per pair, 8 samples per lane and block, summed over the
+// CTA's blocks in shared memory, one fixed-point atomic per (pair, CTA).
+// CTA (a, g) takes blocks kGroup g ...
 __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
                                                    const uint64_t *__restrict__ ZT, int64_t ldzt,
                                                    const float *__restrict__ C, int64_t ldc,
                                                    const unsigned long long *__restrict__ E, int64_t lde,
                                                    const float *__restrict__ W, int64_t lds, int64_t s,
-                                                   const double *__restrict__ scale,
+                                                   int64_t nblk, const double *__restrict__ scale,
                                                    unsigned long long *__restrict__ Kfx,
                                                    uint32_t *__restrict__ status) {
     __shared__ LoShared sh;
     __shared__ float wb[kBlk];
-    const int64_t a = blockIdx.x, blk = blockIdx.y;
-    const int nq = lo_setup(sh, A + a * lda, n, ZT, ldzt, blk, status);
-    const int64_t i = blk * kBlk + threadIdx.x;
-    wb[threadIdx.x] = i < s ? W[a * lds + i] : 0.f;
-    __syncthreads();
+    __shared__ float pacc[kPairMax];
+    const int64_t a = blockIdx.x;
+    const int nq = support_of_row(A + a * lda, n, sh.Q, sh.scan, status);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float sc = (float)*scale;
-    int64_t c0 = 0;
     const int64_t ncand = (int64_t)nq * nq;
+    const int64_t b0 = blockIdx.y * (int64_t)kGroup;
+    const int64_t b1 = b0 + kGroup < nblk ? b0 + kGroup : nblk;
+    int64_t c0 = 0;
     while (c0 < ncand) {
-        lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
-        const int np = sh.npairs;
-        for (int p = warp; p < np; p += kBlk / 32) {
-            const int pr = sh.pr[p];
-            const int t = pr & 0xFFFF, u = pr >> 16;
-            float acc = 0.f;
+        const int np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
+        for (int p = threadIdx.x; p < np; p += kBlk) pacc[p] = 0.f;  // the sum over the CTA's blocks, per pair
+        for (int64_t blk = b0; blk < b1; ++blk) {
+            lo_load_bits(sh, nq, n, ZT, ldzt, blk, status);
+            const int64_t i = blk * kBlk + threadIdx.x;
+            wb[threadIdx.x] = i < s ? W[a * lds + i] : 0.f;
+            __syncthreads();
+            for (int p = warp; p < np; p += kBlk / 32) {
+                const int pr = sh.pr[p];
+                const int t = pr & 0xFFFF, u = pr >> 16;
+                float v = 0.f;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const uint32_t x = sh.bits[t][k] ^ sh.bits[u][k];
-                const float v = wb[32 * k + lane];
-                acc += ((x >> lane) & 1u) ? -v : v;
+                for (int kk = 0; kk < 8; ++kk) {
+                    const uint32_t x = sh.bits[t][kk] ^ sh.bits[u][kk];
+                    const float wv = wb[32 * kk + lane];
+                    v += ((x >> lane) & 1u) ? -wv : wv;
+                }
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+                if (lane == 0) pacc[p] += v;  // pair p belongs to this warp alone
             }
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(kFull, acc, off);
-            if (lane == 0)
-                atomicAdd(Kfx + (int64_t)sh.Q[t] * n + sh.Q[u], (unsigned long long)to_fixed(acc, sc));
+        }
+        __syncthreads();
+        for (int p = threadIdx.x; p < np; p += kBlk) {
+            const int pr = sh.pr[p];
+            atomicAdd(Kfx + (int64_t)sh.Q[pr & 0xFFFF] * n + sh.Q[pr >> 16], (unsigned long long)to_fixed(pacc[p], sc));
         }
         __syncthreads();
     }
@@ -516,7 +629,7 @@ cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l
     LaunchScope ls(IQP_KERNEL_LOWORDER, st);
     const float *d = C + n * ldc;
     const unsigned long long *E = reinterpret_cast<const unsigned long long *>(d + ldc);
-    k_lo_phase<0><<<dim3((unsigned)l, (unsigned)nparts), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d, E,
+    k_lo_phase<0><<<dim3((unsigned)l, (unsigned)cdiv(nparts, kGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d, E,
                                                                        lo_lde(n), s, nparts, part, nullptr, nullptr,
                                                                        nullptr, status);
     return cudaGetLastError();
@@ -540,14 +653,15 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
     if ((e = launch_fixed_scale(alpha, beta, l, s, scale, st)) != cudaSuccess) return e;
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_phase<1><<<dim3((unsigned)l, (unsigned)nblk), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d,
+        k_lo_phase<1><<<dim3((unsigned)l, (unsigned)cdiv(nblk, kGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d,
                                                                          E, lde, s, nblk, nullptr, alpha, beta, W,
                                                                          status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_v<<<dim3((unsigned)n, (unsigned)nblk), kBlk, 0, st>>>(AT, ldlt, ZT, ldzt, W, lds, s, nblk, V, gsp);
+        k_lo_v<<<dim3((unsigned)n, (unsigned)cdiv(nblk, kGroup)), kBlk, 0, st>>>(AT, ldlt, ZT, ldzt, W, lds, s, nblk,
+                                                                                  V, gsp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     {
@@ -557,8 +671,9 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
     }
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_pairs<<<dim3((unsigned)l, (unsigned)nblk), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, C, ldc, E, lde, W, lds,
-                                                                       s, scale, Kfx, status);
+        k_lo_pairs<<<dim3((unsigned)l, (unsigned)cdiv(nblk, kGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, C, ldc, E,
+                                                                                     lde, W, lds, s, nblk, scale, Kfx,
+                                                                                     status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     LaunchScope ls(IQP_KERNEL_LOWORDER, st);
