@@ -71,6 +71,8 @@ __global__ void k_lo_build(const int4 *__restrict__ sup, const float *__restrict
 // l owning the 64 samples of word 32 range + l of every ZT row, each term a
 // sign flip and an FP32 add (as in the row-sparse form).
 
+constexpr int kCsBatch = 8;
+
 // fn(r) for every set bit r of E row q, in increasing r, warp-uniformly.
 template <class F>
 __device__ __forceinline__ void for_each_bit(const unsigned long long *__restrict__ row, int64_t nw, int lane, F &fn) {
@@ -106,16 +108,41 @@ __global__ void __launch_bounds__(32) k_lo_cs(const unsigned long long *__restri
 #pragma unroll
     for (int k = 0; k < 64; ++k) acc[k] = 0.f;
     const float *crow = C + q * ldc;
-    auto visit = [&](int64_t r) {
-        const uint64_t z = __ldg(ZT + r * ldzt + word);
-        const uint32_t cb = __float_as_uint(__ldg(crow + r));
+    auto add = [&](uint64_t z, uint32_t cb) {
         const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
 #pragma unroll
         for (int k = 0; k < 32; ++k) acc[k] += __uint_as_float(cb ^ ((lo << (31 - k)) & 0x80000000u));
 #pragma unroll
         for (int k = 0; k < 32; ++k) acc[32 + k] += __uint_as_float(cb ^ ((hi << (31 - k)) & 0x80000000u));
     };
+    // Pairs are consumed in batches of kCsBatch: the batch's loads are all
+    // issued before the first is used (only indices are held while a batch
+    // fills), so their latencies overlap.
+    int64_t rb[kCsBatch];
+    int nb = 0;
+#pragma unroll
+    for (int t = 0; t < kCsBatch; ++t) rb[t] = 0;
+    auto visit = [&](int64_t r) {
+#pragma unroll
+        for (int t = 0; t + 1 < kCsBatch; ++t) rb[t] = rb[t + 1];
+        rb[kCsBatch - 1] = r;
+        if (++nb == kCsBatch) {
+            uint64_t z[kCsBatch];
+            uint32_t cb[kCsBatch];
+#pragma unroll
+            for (int t = 0; t < kCsBatch; ++t) {
+                z[t] = __ldg(ZT + rb[t] * ldzt + word);
+                cb[t] = __float_as_uint(__ldg(crow + rb[t]));
+            }
+#pragma unroll
+            for (int t = 0; t < kCsBatch; ++t) add(z[t], cb[t]);
+            nb = 0;
+        }
+    };
     for_each_bit(E + q * lde, lde, lane, visit);
+#pragma unroll
+    for (int t = 0; t < kCsBatch; ++t)
+        if (t >= kCsBatch - nb) add(__ldg(ZT + rb[t] * ldzt + word), __float_as_uint(__ldg(crow + rb[t])));
     if (wraw < vwords) {
         float *mrow = M + q * lds + wraw * 64;  // lds is a multiple of 64
 #pragma unroll
@@ -130,6 +157,7 @@ __global__ void __launch_bounds__(32) k_lo_cs(const unsigned long long *__restri
 // FP64 across ranges).
 constexpr int kHSplit = 8;
 constexpr int kRMax = 1024;
+constexpr int kHPre = 4;
 
 __global__ void __launch_bounds__(32) k_lo_h(const unsigned long long *__restrict__ E, int64_t lde,
                                              const uint64_t *__restrict__ ZT, int64_t ldzt,
@@ -185,9 +213,24 @@ __global__ void __launch_bounds__(32) k_lo_h(const unsigned long long *__restric
             }
 #pragma unroll
             for (int k = 0; k < 64; ++k) u[k] = ((zq >> k) & 1ull) ? -u[k] : u[k];
-            for (int e = 0; e < nr; ++e) {
+            // loads of the next kHPre pairs are issued ahead of their use
+            uint64_t zn[kHPre];
+#pragma unroll
+            for (int t = 0; t < kHPre; ++t) zn[t] = t < nr ? __ldg(ZT + (int64_t)rl[t] * ldzt + word) : 0ull;
+            for (int e0 = 0; e0 < nr; e0 += kHPre) {
+                uint64_t zc[kHPre];
+#pragma unroll
+                for (int t = 0; t < kHPre; ++t) {
+                    zc[t] = zn[t];
+                    const int en = e0 + kHPre + t;
+                    zn[t] = en < nr ? __ldg(ZT + (int64_t)rl[en] * ldzt + word) : 0ull;
+                }
+#pragma unroll
+                for (int t = 0; t < kHPre; ++t) {
+                const int e = e0 + t;
+                if (e >= nr) break;
                 const int64_t r = rl[e];
-                const uint64_t z = __ldg(ZT + r * ldzt + word);
+                const uint64_t z = zc[t];
                 const uint32_t lo = (uint32_t)z, hi = (uint32_t)(z >> 32);
                 float p[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
@@ -200,6 +243,7 @@ __global__ void __launch_bounds__(32) k_lo_h(const unsigned long long *__restric
 #pragma unroll
                 for (int off = 16; off >= 1; off >>= 1) dsum += __shfl_xor_sync(kFull, dsum, off);
                 if (lane == 0) hrow[r] = r0 == 0 ? (double)dsum : hrow[r] + (double)dsum;
+                }
             }
         }
         __syncwarp();
