@@ -21,7 +21,14 @@ import torch
 from . import api, inputs as I
 
 
-def adam_mmd(problem: I.Problem, steps: int, lr: float = 1e-3, precision: str = "split_bf16",
+def choose_precision(G: np.ndarray) -> str:
+    """The low-order form when every generator acts on at most two qubits
+    (checked on the host from the packed rows), else split BF16."""
+    wt = np.bitwise_count(np.ascontiguousarray(G, dtype=np.uint64)).sum(axis=1)
+    return "loworder_fp32" if wt.size and int(wt.max()) <= 2 else "split_bf16"
+
+
+def adam_mmd(problem: I.Problem, steps: int, lr: float = 1e-3, precision: str = "auto",
              unbiased: bool = True, seed: int = 0, device: str = "cuda", log=None, device_rng: bool = False,
              sqrt_loss: bool = False, indep: bool = False):
     """Returns (theta, losses). problem.A / problem.Z give the observable and
@@ -31,6 +38,8 @@ def adam_mmd(problem: I.Problem, steps: int, lr: float = 1e-3, precision: str = 
     observable; sqrt_loss trains on sqrt(MMD^2)."""
     n = problem.n
     l, s = problem.A.shape[0], problem.Z.shape[0]
+    if precision == "auto":
+        precision = choose_precision(problem.G)
     ps = problem.extra.get("p_sigma", 0.5)
     G = api.to_device_bits(problem.G, device)
     X = api.to_device_bits(problem.X, device)
@@ -66,7 +75,7 @@ def main():
     ap.add_argument("--N", type=int, default=10_000)
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--lr", type=float, default=1e-3)
-    ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "sparse_fp32"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "split_bf16", "fp32", "sparse_fp32", "loworder_fp32"])
     ap.add_argument("--device-rng", action="store_true", help="draw samples and observables on the GPU")
     ap.add_argument("--sqrt-loss", action="store_true")
     ap.add_argument("--indep", action="store_true", help="one sample batch per observable")
