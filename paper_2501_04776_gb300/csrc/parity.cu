@@ -101,46 +101,67 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
 // Bit transpose: out (in_cols x ld_out32*32 bits) = in^T, where in is
 // in_rows x in_cols bits with ld_in32 words per row. Output words beyond
 // in_rows bits are written as zero; output rows >= in_cols are not written.
-// Tile: 256 x 256 bits per block; each warp transposes 32 rows by ballots.
+// Tile: 512 x 512 bits per block of 512 threads, read and written as
+// 64-byte row segments; each warp transposes 32 x 32 blocks in registers
+// (five shuffle stages swapping off-diagonal sub-blocks of 16, 8, 4, 2, 1).
 // Batched over blockIdx.y: matrix b starts at in + b in_bs32 / out + b out_bs32.
-__global__ void __launch_bounds__(256) k_bit_transpose(const uint32_t *__restrict__ in, int64_t in_rows,
+constexpr int kTT = 512;            // tile edge in bits
+constexpr int kTW = kTT / 32;       // 32-bit words per tile row
+
+__global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restrict__ in, int64_t in_rows,
                                                         int64_t in_cols, int64_t ld_in32,
                                                         uint32_t *__restrict__ out, int64_t ld_out32, int64_t gx,
                                                         int64_t in_bs32, int64_t out_bs32) {
     in += (int64_t)blockIdx.y * in_bs32;
     out += (int64_t)blockIdx.y * out_bs32;
-    __shared__ uint32_t tin[256][9];
-    __shared__ uint32_t tout[256][9];
+    __shared__ uint32_t tin[kTT][kTW + 1];  // transposed in place
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t bid = blockIdx.x;
-    const int64_t r0 = (bid % gx) * 256;   // input rows = output bit columns
-    const int64_t c0 = (bid / gx) * 256;   // input bit columns = output rows
+    const int64_t r0 = (bid % gx) * kTT;   // input rows = output bit columns
+    const int64_t c0 = (bid / gx) * kTT;   // input bit columns = output rows
     const int64_t w0 = c0 >> 5;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int idx = tid + 256 * k, row = idx >> 3, q = idx & 7;
+    for (int k = 0; k < kTW; ++k) {
+        const int idx = tid + kTT * k, row = idx / kTW, q = idx % kTW;
         const int64_t r = r0 + row;
         tin[row][q] = (r < in_rows && w0 + q < ld_in32) ? in[r * ld_in32 + w0 + q] : 0u;
     }
     __syncthreads();
-#pragma unroll 1
-    for (int k = 0; k < 8; ++k) {
-        const uint32_t word = tin[warp * 32 + lane][k];
-        uint32_t mine = 0u;
-#pragma unroll
-        for (int b = 0; b < 32; ++b) {
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, (word >> b) & 1u);
-            if (lane == b) mine = bal;
+    // 32 x 32 blocks (row block rb, word column cb): each warp takes a pair
+    // (rb, cb), (cb, rb) with rb <= cb, transposes both and swaps them, so
+    // afterwards tin[32 cb + lane][rb] is output row c0 + 32 cb + lane, word
+    // r0/32 + rb. A lane stores only to the two words it loaded.
+    for (int item = warp; item < kTW * (kTW + 1) / 2; item += kTT / 32) {
+        int rb = 0, rem = item;
+        while (rem >= kTW - rb) {
+            rem -= kTW - rb;
+            ++rb;
         }
-        tout[k * 32 + lane][warp] = mine;  // output row c0 + 32k + lane, r-word r0/32 + warp
+        const int cb = rb + rem;
+        uint32_t x1 = tin[rb * 32 + lane][cb];
+        uint32_t x2 = tin[cb * 32 + lane][rb];
+#pragma unroll
+        for (int j = 16; j >= 1; j >>= 1) {
+            const uint32_t lowm = j == 16 ? 0x0000FFFFu
+                                  : j == 8 ? 0x00FF00FFu
+                                  : j == 4 ? 0x0F0F0F0Fu
+                                  : j == 2 ? 0x33333333u
+                                           : 0x55555555u;
+            const uint32_t y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, j);
+            const uint32_t y2 = __shfl_xor_sync(0xFFFFFFFFu, x2, j);
+            x1 = (lane & j) ? ((x1 & ~lowm) | ((y1 >> j) & lowm)) : ((x1 & lowm) | ((y1 & lowm) << j));
+            x2 = (lane & j) ? ((x2 & ~lowm) | ((y2 >> j) & lowm)) : ((x2 & lowm) | ((y2 & lowm) << j));
+        }
+        tin[cb * 32 + lane][rb] = x1;
+        if (rb != cb) tin[rb * 32 + lane][cb] = x2;
     }
     __syncthreads();
-    const int64_t orow = c0 + tid;
     const int64_t ow0 = r0 >> 5;
-    if (orow < in_cols) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q)
-            if (ow0 + q < ld_out32) out[orow * ld_out32 + ow0 + q] = tout[tid][q];
+    for (int k = 0; k < kTW; ++k) {
+        const int idx = tid + kTT * k, row = idx / kTW, q = idx % kTW;
+        const int64_t orow = c0 + row;
+        if (orow < in_cols && ow0 + q < ld_out32) out[orow * ld_out32 + ow0 + q] = tin[row][q];
     }
 }
 
@@ -187,11 +208,11 @@ __global__ void __launch_bounds__(256) k_support_gather(const uint64_t *__restri
 
 cudaError_t bit_transpose(const uint64_t *in, int64_t in_rows, int64_t in_cols, int64_t ld_in, uint64_t *out,
                           int64_t ld_out, cudaStream_t st) {
-    const int64_t gx = cdiv(ld_out * 64, 256);
-    const int64_t gy = cdiv(in_cols, 256);
+    const int64_t gx = cdiv(ld_out * 64, kTT);
+    const int64_t gy = cdiv(in_cols, kTT);
     if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
     LaunchScope ls(IQP_KERNEL_PARITY, st);
-    k_bit_transpose<<<(unsigned)(gx * gy), 256, 0, st>>>(reinterpret_cast<const uint32_t *>(in), in_rows, in_cols,
+    k_bit_transpose<<<(unsigned)(gx * gy), kTT, 0, st>>>(reinterpret_cast<const uint32_t *>(in), in_rows, in_cols,
                                                           2 * ld_in, reinterpret_cast<uint32_t *>(out), 2 * ld_out, gx,
                                                           0, 0);
     return cudaGetLastError();
@@ -235,13 +256,13 @@ __global__ void __launch_bounds__(256) k_support_list(const uint64_t *__restrict
 // consecutive: matrix b of the output starts at out + b in_cols ld_out.
 cudaError_t launch_bit_transpose_batched(const uint64_t *in, int64_t batch, int64_t in_rows, int64_t in_cols,
                                          int64_t ld_in, uint64_t *out, int64_t ld_out, cudaStream_t st) {
-    const int64_t gx = cdiv(ld_out * 64, 256);
-    const int64_t gy = cdiv(in_cols, 256);
+    const int64_t gx = cdiv(ld_out * 64, kTT);
+    const int64_t gy = cdiv(in_cols, kTT);
     if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
     for (int64_t b0 = 0; b0 < batch; b0 += 65535) {
         const int64_t nb = batch - b0 < 65535 ? batch - b0 : 65535;
         LaunchScope ls(IQP_KERNEL_PARITY, st);
-        k_bit_transpose<<<dim3((unsigned)(gx * gy), (unsigned)nb), 256, 0, st>>>(
+        k_bit_transpose<<<dim3((unsigned)(gx * gy), (unsigned)nb), kTT, 0, st>>>(
             reinterpret_cast<const uint32_t *>(in + b0 * in_rows * ld_in), in_rows, in_cols, 2 * ld_in,
             reinterpret_cast<uint32_t *>(out + b0 * in_cols * ld_out), 2 * ld_out, gx, 2 * in_rows * ld_in,
             2 * in_cols * ld_out);
