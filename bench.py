@@ -269,6 +269,24 @@ def nnz_parities(api, n, A, G):
     return int(((x * 0x0101010101010101) >> 56).sum().item())
 
 
+def parity_roofline(kt, peaks, n, m, l, s, steps):
+    """The parity gathers of one step (two calls, each forming P_A, P_A^T and
+    P_Z, P_Z^T from A and Z): algorithmic bytes = the bit matrices written
+    (each l m / 8 or s m / 8 bytes, twice) plus the rows of A and Z read,
+    against the measured HBM copy bandwidth."""
+    if "parity" not in kt:
+        return None
+    words = lambda bits: -(-bits // 64)
+    per_call = 8 * (2 * l * words(m) + 2 * s * words(m) + (l + s) * words(n))
+    nbytes = 2 * per_call
+    ms = kt["parity"]["total_ms"] / max(1, steps)
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "kernels": "k_bit_transpose + k_support_gather", "bytes_per_step": nbytes,
+            "ms_per_step": round(ms, 4), "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+            "frac": round(gbs / hbm, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+
+
 def loworder_roofline(kt, clocks, n, G, s):
     """The low-order form's pair contractions (M = C S and H = (s V) S^T):
     2 p s signed FP32 additions per launch, p = qubit pairs with a generator,
@@ -566,7 +584,8 @@ def main():
                                                   "reductions)" if prec == _lib.SPLIT_BF16 else ""),
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": roof, "kernels": kt, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
+        "roofline": roof, "parity_roofline": parity_roofline(kt, peaks, n, m, l, s, args.steps),
+        "kernels": kt, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
         "ms_steps": [round(x, 3) for x in ms_list],
     }
     if fp32 is not None:
