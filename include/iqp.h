@@ -65,8 +65,9 @@ typedef enum {
  * phase regroups exactly into
  *   Phi[a,i] = sum_{q in a} s_q(i) (d_q + (C S)[q,i]) - 2 sum_{q<r in a} C_qr s_q(i) s_r(i),
  * d_q / C_qr = sums of 2 theta_j over the gates on {q} / {q, r}, so the work
- * is two n x n x s contractions plus O(l |a|^2 s) instead of O(l m s). FP32
- * (tolerances of IQP_FP32). A generator of weight > 2 records IQP_ERR_ARG
+ * is two contractions over the qubit pairs that carry a generator plus
+ * O(l |a|^2 s) instead of O(l m s). n <= 65536 (its n x n pair matrices take
+ * about 20 n^2 bytes of workspace). FP32 (tolerances of IQP_FP32). A generator of weight > 2 records IQP_ERR_ARG
  * and an observable of weight > 1024 records IQP_ERR_UNSUPPORTED in the
  * device status (iqp_read_status); the outputs are then not meaningful. */
 typedef enum { IQP_FP32 = 0, IQP_SPLIT_BF16 = 1, IQP_SPARSE_FP32 = 2, IQP_LOWORDER_FP32 = 3 } iqp_precision;

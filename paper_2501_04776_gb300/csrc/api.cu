@@ -229,9 +229,9 @@ iqp_status check_common(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, co
     if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32 && prec != IQP_LOWORDER_FP32)
         return IQP_ERR_ARG;
     if (prec == IQP_SPLIT_BF16 && !iqp_tensor_path_available()) return IQP_ERR_UNSUPPORTED;
-    // low-order grids: observables on x, 256-sample blocks and 128-row GEMM tiles on y
-    if (prec == IQP_LOWORDER_FP32 && (l > INT32_MAX || n > INT32_MAX || cdiv(s, (int64_t)256) > 65535 ||
-                                      cdiv(n, (int64_t)128) > 65535))
+    // low-order form: observables on grid x, 256-sample blocks on y; its n x n
+    // pair matrices (C, H, K: 20 n^2 bytes) bound n
+    if (prec == IQP_LOWORDER_FP32 && (l > INT32_MAX || n > 65536 || cdiv(s, (int64_t)256) > 65535))
         return IQP_ERR_ARG;
     // sparse grid: observables on x (< 2^31), 2048-sample blocks on y (< 65536)
     if (prec == IQP_SPARSE_FP32 && (l > INT32_MAX || cdiv(s, (int64_t)2048) > 65535)) return IQP_ERR_ARG;

@@ -154,3 +154,14 @@ def test_workspace_sizes_of_the_options(lib):
     mmd = lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD_INDEP, n, m, l, s, 50, 0)
     assert mmd > lib.iqp_workspace_bytes(_lib.OP_EXPVAL_INDEP_GRAD, n, m, l, s, 0, 0)
     assert lib.iqp_workspace_bytes(10, n, m, l, s, 0, 0) == 0
+
+
+def test_loworder_size_limit(lib):
+    from paper_2501_04776_gb300 import _lib
+    G, A, Z, th, out, ws = 0x10000, 0x20000, 0x30000, 0x40000, 0x50000, 0x100000
+    n = 65537
+    ld = 2 * ((n + 127) // 128)
+    assert lib.iqp_expval(n, G, 4, ld, A, 3, ld, Z, 5, ld, th, _lib.LOWORDER_FP32, out, out, ws, 1 << 40, None) == \
+        _lib.ERR_ARG
+    assert lib.iqp_workspace_bytes(_lib.OP_EXPVAL, 1000, 500500, 2000, 5000, 0, _lib.LOWORDER_FP32) < \
+        lib.iqp_workspace_bytes(_lib.OP_EXPVAL, 1000, 500500, 2000, 5000, 0, _lib.SPLIT_BF16)
