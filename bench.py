@@ -38,7 +38,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="split_bf16", choices=["split_bf16", "fp32", "sparse_fp32", "loworder_fp32"])
@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--l", type=int, default=None)
     ap.add_argument("--s", type=int, default=None)
     ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the plain FP32 form (0 = skip)")
+    ap.add_argument("--step", default="fused", choices=["fused", "two-call"],
+                    help="fused: iqp_expval_value_and_grad (one phase pass); two-call: iqp_expval + iqp_expval_grad, "
+                         "as autograd runs them (Phi recomputed); the other form is timed too")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the bitflip and MMD per-call timings")
     ap.add_argument("--cpu-sample-l", type=int, default=512)
@@ -269,16 +272,16 @@ def nnz_parities(api, n, A, G):
     return int(((x * 0x0101010101010101) >> 56).sum().item())
 
 
-def parity_roofline(kt, peaks, n, m, l, s, steps):
-    """The parity gathers of one step (two calls, each forming P_A, P_A^T and
-    P_Z, P_Z^T from A and Z): algorithmic bytes = the bit matrices written
-    (each l m / 8 or s m / 8 bytes, twice) plus the rows of A and Z read,
-    against the measured HBM copy bandwidth."""
+def parity_roofline(kt, peaks, n, m, l, s, steps, calls=2):
+    """The parity gathers of one step (`calls` library calls, each forming
+    P_A, P_A^T and P_Z, P_Z^T from A and Z): algorithmic bytes = the bit
+    matrices written (each l m / 8 or s m / 8 bytes, twice) plus the rows of
+    A and Z read, against the measured HBM copy bandwidth."""
     if "parity" not in kt:
         return None
     words = lambda bits: -(-bits // 64)
     per_call = 8 * (2 * l * words(m) + 2 * s * words(m) + (l + s) * words(n))
-    nbytes = 2 * per_call
+    nbytes = calls * per_call
     ms = kt["parity"]["total_ms"] / max(1, steps)
     hbm = peaks.get("hbm_gbs") or 6800.0
     gbs = nbytes / (ms * 1e-3) / 1e9
@@ -449,7 +452,8 @@ def main():
     P = ctypes.c_void_p
     st = P(stream.cuda_stream)
 
-    def step(precision, Gd=G, Ad=A, Zd=Z, th=theta, al=alpha, evd=ev, sed=se, gd=grad):
+    def two_call_step(precision, Gd=G, Ad=A, Zd=Z, th=theta, al=alpha, evd=ev, sed=se, gd=grad):
+        # what autograd runs: iqp_expval, then iqp_expval_grad (Phi recomputed)
         _lib.check(lib.iqp_expval(n, P(Gd.data_ptr()), m, Gd.shape[1], P(Ad.data_ptr()), l, Ad.shape[1],
                                   P(Zd.data_ptr()), s, Zd.shape[1], P(th.data_ptr()), precision, P(evd.data_ptr()),
                                   P(sed.data_ptr()), P(ws.data_ptr()), ws.numel(), st), "iqp_expval")
@@ -457,6 +461,16 @@ def main():
                                        P(Zd.data_ptr()), s, Zd.shape[1], P(th.data_ptr()), P(al.data_ptr()), None,
                                        precision, P(gd.data_ptr()), P(ws.data_ptr()), ws.numel(), st),
                    "iqp_expval_grad")
+
+    def fused_step(precision, Gd=G, Ad=A, Zd=Z, th=theta, al=alpha, evd=ev, sed=se, gd=grad):
+        # one call: parities once, one phase pass for the statistics and W, the gradient contraction
+        _lib.check(lib.iqp_expval_value_and_grad(n, P(Gd.data_ptr()), m, Gd.shape[1], P(Ad.data_ptr()), l,
+                                                 Ad.shape[1], P(Zd.data_ptr()), s, Zd.shape[1], P(th.data_ptr()),
+                                                 P(al.data_ptr()), None, precision, P(evd.data_ptr()),
+                                                 P(sed.data_ptr()), P(gd.data_ptr()), P(ws.data_ptr()), ws.numel(),
+                                                 st), "iqp_expval_value_and_grad")
+
+    step = fused_step if args.step == "fused" else two_call_step
 
     def timed(precision, k, warm, profile=False, fn=None):
         fn = fn or (lambda: step(precision))
@@ -543,10 +557,18 @@ def main():
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": None,
                 "flops_per_launch": flops, "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x median SM clock"}
 
+    # The other step form on the same workload (same timing rules).
+    other_fn = (lambda: two_call_step(prec)) if args.step == "fused" else (lambda: fused_step(prec))
+    lib.iqp_profile_reset()
+    ms_other, _ = timed(prec, max(2, args.steps // 2), 2, profile=True, fn=other_fn)
+    other = {"step": "two-call" if args.step == "fused" else "fused",
+             "ms_per_step": round(max_over_ranks(statistics.mean(ms_other), dev), 3),
+             "kernels": {k: v["avg_ms"] for k, v in _kernel_times(lib).items()}}
+
     # Plain FP32 form on the same GPU, same workload.
     fp32 = None
     if prec == _lib.SPLIT_BF16 and args.fp32_steps > 0:
-        ms32, _ = timed(_lib.FP32, args.fp32_steps, 1)
+        ms32, _ = timed(_lib.FP32, args.fp32_steps, 1, fn=lambda: step(_lib.FP32))
         fp32 = {"ms_per_step": round(statistics.mean(ms32), 3), "steps": args.fp32_steps}
 
     # End to end: host (pinned) inputs -> device, both calls, results -> host.
@@ -564,7 +586,7 @@ def main():
         e0.record(stream)
         for d, h in ((dG, hG), (dA, hA), (dZ, hZ), (dth, hth), (dal, hal)):
             d.copy_(h, non_blocking=True)
-        step(prec, dG, dA, dZ, dth, dal)
+        step(prec, dG, dA, dZ, dth, dal)  # through the same public call as the timed step
         for h, d in ((hev, ev), (hse, se), (hgr, grad)):
             h.copy_(d, non_blocking=True)
         e1.record(stream)
@@ -584,7 +606,12 @@ def main():
                                                   "reductions)" if prec == _lib.SPLIT_BF16 else ""),
                    "l2": "flushed between steps (256 MiB write, outside the step events)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": roof, "parity_roofline": parity_roofline(kt, peaks, n, m, l, s, args.steps),
+        "step": ("one iqp_expval_value_and_grad call (parities once, one phase pass for the statistics and W, the "
+                 "gradient contraction)" if args.step == "fused" else
+                 "iqp_expval then iqp_expval_grad (as autograd runs them; Phi recomputed in the second)"),
+        "other_step": other,
+        "roofline": roof, "parity_roofline": parity_roofline(kt, peaks, n, m, l, s, args.steps,
+                                                              1 if args.step == "fused" else 2),
         "kernels": kt, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
         "ms_steps": [round(x, 3) for x in ms_list],
     }

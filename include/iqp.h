@@ -175,6 +175,20 @@ iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                            iqp_precision prec, double *grad,
                            void *ws, size_t ws_bytes, void *stream);
 
+/* Estimates and gradient in one call, for a loss whose gradient coefficients
+ * alpha, beta (as in iqp_expval_grad) are known before the estimates, e.g.
+ * L = sum_a w_a <Z_a> with alpha_a = -w_a / s, beta = NULL. Outputs as
+ * iqp_expval plus grad[m]. In IQP_SPLIT_BF16 the parities are formed once and
+ * a single pass of the phase contraction yields both the statistics and W
+ * (no recompute); the other forms run their forward and gradient passes on
+ * parities formed once. ws: iqp_workspace_bytes(IQP_OP_EXPVAL_GRAD, ...). */
+iqp_status iqp_expval_value_and_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                                     const uint64_t *A, int64_t l, int64_t lda,
+                                     const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                                     const double *alpha, const double *beta, iqp_precision prec,
+                                     double *expval, double *std_err, double *grad,
+                                     void *ws, size_t ws_bytes, void *stream);
+
 /* MMD^2 estimate of eq. mmd_estimate (Sec. 3.3.1) over the l observables in
  * A (drawn by the caller, bits i.i.d. Bernoulli(p_sigma) for a Gaussian
  * kernel of bandwidth sigma), with model terms from the estimator on Z and

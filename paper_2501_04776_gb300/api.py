@@ -158,6 +158,29 @@ def expval_grad(n, theta, G, A, Z, alpha, beta=None, precision="split_bf16") -> 
     return grad
 
 
+def expval_value_and_grad(n, theta, G, A, Z, alpha, beta=None, precision="split_bf16"):
+    """(expval, std_err, grad) from one call, for gradient coefficients known
+    before the estimates (for L = sum_a w_a <Z_a>: alpha = -w / s). In
+    split BF16 one pass of the phase contraction yields both the statistics
+    and the gradient's W (no recompute)."""
+    for t, nm in ((G, "G"), (A, "A"), (Z, "Z")):
+        _bits(t, nm)
+    th = _theta32(theta)
+    m, l, s = G.shape[0], A.shape[0], Z.shape[0]
+    prec = precision_code(precision)
+    al = alpha.detach().to(device=G.device, dtype=torch.float64).contiguous()
+    be = None if beta is None else beta.detach().to(device=G.device, dtype=torch.float64).contiguous()
+    lib = _lib.load()
+    ws = _WS.get(lib.iqp_workspace_bytes(OP_EXPVAL_GRAD, n, m, l, s, 0, prec), G.device)
+    ev = torch.empty(l, dtype=torch.float64, device=G.device)
+    se = torch.empty(l, dtype=torch.float64, device=G.device)
+    grad = torch.empty(m, dtype=torch.float64, device=G.device)
+    check(lib.iqp_expval_value_and_grad(n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(Z), s, Z.shape[1],
+                                        _ptr(th), _ptr(al), _ptr(be), prec, _ptr(ev), _ptr(se), _ptr(grad), _ptr(ws),
+                                        ws.numel(), ctypes.c_void_p(_stream(G.device))), "iqp_expval_value_and_grad")
+    return ev, se, grad
+
+
 class _ExpvalFn(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, G, A, Z, n, precision):

@@ -487,6 +487,38 @@ iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
     return backward(p, ws, alpha, beta, grad, st);
 }
 
+iqp_status iqp_expval_value_and_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A,
+                                     int64_t l, int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz,
+                                     const float *theta, const double *alpha, const double *beta, iqp_precision prec,
+                                     double *expval, double *std_err, double *grad, void *ws, size_t ws_bytes,
+                                     void *stream) {
+    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    if (rc != IQP_OK) return rc;
+    if (alpha == nullptr || grad == nullptr) return IQP_ERR_ARG;
+    if (!aligned(alpha, 8) || !aligned(grad, 8) || (beta && !aligned(beta, 8)) || (expval && !aligned(expval, 8)) ||
+        (std_err && !aligned(std_err, 8)))
+        return IQP_ERR_ALIGN;
+    Plan p = make_plan(IQP_OP_EXPVAL_GRAD, n, m, l, s, 0, prec);
+    p.G = G;
+    p.ldg = ldg;
+    p.A = A;
+    p.lda = lda;
+    if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
+    if (prec != IQP_SPLIT_BF16) {
+        if ((rc = forward_stats(p, ws, expval, std_err, nullptr, nullptr, st)) != IQP_OK) return rc;
+        return backward(p, ws, alpha, beta, grad, st);
+    }
+    iqp_status why = IQP_OK;
+    if (launch_phase_tc(2, p, ws, alpha, beta, st, &why) != cudaSuccess) return why != IQP_OK ? why : IQP_ERR_CUDA;
+    IQP_TRY(launch_finalize(at<double2>(ws, p.off_part), p.nparts, p.pw, p.l, p.s, expval, std_err, nullptr, nullptr,
+                            st));
+    if (launch_grad_tc(p, ws, st, &why) != cudaSuccess) return why != IQP_OK ? why : IQP_ERR_CUDA;
+    IQP_TRY(launch_grad_reduce(at<double>(ws, p.off_gpart), p.natile, p.m, grad, st));
+    return IQP_OK;
+}
+
 iqp_status iqp_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
                         int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const uint64_t *X, int64_t N,
                         int64_t ldx, const float *theta, iqp_precision prec, int unbiased, double *loss, void *ws,

@@ -212,7 +212,28 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 }
 
 // ------------------------------------------------------------------ kernel
-// GRAD = false: phase contraction (MODE 0 stats / MODE 1 W).
+// W hi/lo (BF16 pairs) of 32 consecutive samples i0.. of observable row.
+__device__ __forceinline__ void store_w32(const TcArgs &args, int64_t row, int64_t i0, const uint32_t (&ph)[16],
+                                          const uint32_t (&pl)[16]) {
+    __nv_bfloat16 *dh = args.whi + row * args.ldw + i0;
+    __nv_bfloat16 *dl = args.wlo + row * args.ldw + i0;
+    if (i0 + 32 <= args.s) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            reinterpret_cast<uint4 *>(dh)[v] = make_uint4(ph[4 * v], ph[4 * v + 1], ph[4 * v + 2], ph[4 * v + 3]);
+            reinterpret_cast<uint4 *>(dl)[v] = make_uint4(pl[4 * v], pl[4 * v + 1], pl[4 * v + 2], pl[4 * v + 3]);
+        }
+    } else {
+        uint16_t *sh = reinterpret_cast<uint16_t *>(dh);
+        uint16_t *sl = reinterpret_cast<uint16_t *>(dl);
+        for (int e = 0; e < 32 && i0 + e < args.s; ++e) {
+            sh[e] = (uint16_t)(ph[e / 2] >> ((e & 1) * 16));
+            sl[e] = (uint16_t)(pl[e / 2] >> ((e & 1) * 16));
+        }
+    }
+}
+
+// GRAD = false: phase contraction (MODE 0 stats / MODE 1 W / MODE 2 both).
 // GRAD = true : gradient contraction.
 // CG = 1: one CTA per tile of 128 rows; CG = 2: a CTA pair per tile of 256 rows.
 // MC = 2 (gradient with CG = 1): clusters of two CTAs on the same 128
@@ -549,6 +570,48 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (row < args.l && nvalid > 0)
                     args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
+            } else if (!GRAD && MODE == 2) {
+                // Both: the statistics of MODE 0 and W of MODE 1 from one
+                // pass over Phi (the loss's alpha, beta known in advance).
+                const int64_t c0 = tn * TN + group * kGroupCols;
+                int64_t nvalid = args.s - c0;
+                nvalid = nvalid < 0 ? 0 : (nvalid > kGroupCols ? kGroupCols : nvalid);
+                const bool rv = row < args.l;
+                const float al = rv ? (float)args.alpha[row] : 0.f;
+                const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
+                float S = 0.f, M2 = 0.f;
+                uint32_t r[32];
+#pragma unroll 1
+                for (int c = 0; c < kGroupLoads; ++c) {
+                    load_sum32(tbase + c * 32, chunked, r);
+#pragma unroll
+                    for (int e = 0; e < 32; ++e)
+                        if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
+                }
+                const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
+#pragma unroll 1
+                for (int c = 0; c < kGroupLoads; ++c) {
+                    load_sum32(tbase + c * 32, chunked, r);
+                    const int64_t i0 = c0 + c * 32;
+                    uint32_t ph[16], pl[16];
+#pragma unroll
+                    for (int e = 0; e < 32; e += 2) {
+                        float s0, k0, s1, k1;
+                        sincosf(__uint_as_float(r[e]), &s0, &k0);
+                        sincosf(__uint_as_float(r[e + 1]), &s1, &k1);
+                        const float d0 = k0 - mean, d1 = k1 - mean;
+                        if (c * 32 + e < nvalid) M2 = fmaf(d0, d0, M2);
+                        if (c * 32 + e + 1 < nvalid) M2 = fmaf(d1, d1, M2);
+                        const float w0 = s0 * (al + be * k0), w1 = s1 * (al + be * k1);
+                        const float h0 = __bfloat162float(__float2bfloat16_rn(w0));
+                        const float h1 = __bfloat162float(__float2bfloat16_rn(w1));
+                        ph[e / 2] = pack_bf16x2(h0, h1);
+                        pl[e / 2] = pack_bf16x2(w0 - h0, w1 - h1);
+                    }
+                    if (rv && i0 < args.s) store_w32(args, row, i0, ph, pl);
+                }
+                if (rv && nvalid > 0)
+                    args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
             } else if (!GRAD) {
                 const int64_t c0 = tn * TN + group * kGroupCols;
                 const bool rv = row < args.l;
@@ -571,26 +634,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ph[e / 2] = pack_bf16x2(h0, h1);
                         pl[e / 2] = pack_bf16x2(w0 - h0, w1 - h1);
                     }
-                    if (rv && i0 < args.s) {
-                        __nv_bfloat16 *dh = args.whi + row * args.ldw + i0;
-                        __nv_bfloat16 *dl = args.wlo + row * args.ldw + i0;
-                        if (i0 + 32 <= args.s) {
-#pragma unroll
-                            for (int v = 0; v < 4; ++v) {
-                                reinterpret_cast<uint4 *>(dh)[v] =
-                                    make_uint4(ph[4 * v], ph[4 * v + 1], ph[4 * v + 2], ph[4 * v + 3]);
-                                reinterpret_cast<uint4 *>(dl)[v] =
-                                    make_uint4(pl[4 * v], pl[4 * v + 1], pl[4 * v + 2], pl[4 * v + 3]);
-                            }
-                        } else {
-                            uint16_t *sh = reinterpret_cast<uint16_t *>(dh);
-                            uint16_t *sl = reinterpret_cast<uint16_t *>(dl);
-                            for (int e = 0; e < 32 && i0 + e < args.s; ++e) {
-                                sh[e] = (uint16_t)(ph[e / 2] >> ((e & 1) * 16));
-                                sl[e] = (uint16_t)(pl[e / 2] >> ((e & 1) * 16));
-                            }
-                        }
-                    }
+                    if (rv && i0 < args.s) store_w32(args, row, i0, ph, pl);
                 }
             } else {
                 // Gradient epilogue: mask by 2 P_A[a][j], reduce over observables.
@@ -701,7 +745,7 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
     int sms = num_sms();
     if (sms < CL) sms = CL;
     const int64_t groups = ntiles < sms / CL ? ntiles : sms / CL;
-    LaunchScope ls(GRAD ? IQP_KERNEL_GRAD_TC : (MODE == 0 ? IQP_KERNEL_PHASE_TC : IQP_KERNEL_RECOMPUTE_TC), st);
+    LaunchScope ls(GRAD ? IQP_KERNEL_GRAD_TC : (MODE == 1 ? IQP_KERNEL_RECOMPUTE_TC : IQP_KERNEL_PHASE_TC), st);
     if (CL == 1) {
         k_tc<GRAD, MODE, 1, 1><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
         return cudaGetLastError();
@@ -796,9 +840,14 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.gpart = nullptr;
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
-    if (cg == 2)
-        return mode == 0 ? launch_k<false, 0, 2>(ma, ma, mb, a, st) : launch_k<false, 1, 2>(ma, ma, mb, a, st);
-    return mode == 0 ? launch_k<false, 0, 1>(ma, ma, mb, a, st) : launch_k<false, 1, 1>(ma, ma, mb, a, st);
+    if (cg == 2) {
+        if (mode == 0) return launch_k<false, 0, 2>(ma, ma, mb, a, st);
+        if (mode == 1) return launch_k<false, 1, 2>(ma, ma, mb, a, st);
+        return launch_k<false, 2, 2>(ma, ma, mb, a, st);
+    }
+    if (mode == 0) return launch_k<false, 0, 1>(ma, ma, mb, a, st);
+    if (mode == 1) return launch_k<false, 1, 1>(ma, ma, mb, a, st);
+    return launch_k<false, 2, 1>(ma, ma, mb, a, st);
 }
 
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why) {

@@ -549,3 +549,45 @@ def test_sparse_gradient_zero_weights_and_scale_extremes(api):
     for f in (1e-30, 1.0, 1e30):
         g = gpu_grad(api, p, w * f, None, "sparse_fp32")
         assert rel_l2(g / f, want) <= GRAD_RTOL
+
+
+# ------------------------------------------------------ value and gradient
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_value_and_grad_matches_oracle(api, prec):
+    """One call: estimates, standard errors and the gradient of a loss whose
+    coefficients are known in advance (in split BF16 from a single pass of the
+    phase contraction)."""
+    import torch
+    p = ragged_problem(seed=31)
+    w = I.Rng(32).normal(p.l, 1)
+    alpha = torch.from_numpy(-w / p.s).cuda()
+    beta = torch.from_numpy(I.Rng(33).normal(p.l, 1) * 0.1 / p.s).cuda()
+    ev, se, g = api.expval_value_and_grad(p.n, th_dev(p.theta), dev(api, p.G), dev(api, p.A), dev(api, p.Z), alpha,
+                                          beta, prec)
+    want_ev, want_se, _, _ = oracle.expval(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64))
+    assert np.max(np.abs(ev.cpu().numpy() - want_ev)) <= TOL[prec]
+    assert np.max(np.abs(se.cpu().numpy() - want_se)) <= TOL[prec]
+    want = oracle.expval_grad(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64), -w / p.s,
+                              beta.cpu().numpy())
+    assert rel_l2(g.cpu().numpy(), want) <= GRAD_RTOL
+    # the same numbers as the two separate calls
+    ev2, se2 = gpu_expval(api, p, prec)
+    assert np.array_equal(ev.cpu().numpy(), ev2) and np.array_equal(se.cpu().numpy(), se2)
+
+
+def test_value_and_grad_full_size(api):
+    """The benchmark workload (n=1000, m=1e5, l=s=1e4) in one call, sampled
+    observables against the oracle on identical samples."""
+    import torch
+    p = I.random_gates(n=1000)
+    idx = np.unique(np.sort(I.Rng(61).integers(8, p.l, 1)))
+    alpha = np.zeros(p.l)
+    alpha[idx] = I.Rng(62).normal(idx.size, 1) / p.s
+    ev, se, g = api.expval_value_and_grad(p.n, th_dev(p.theta), dev(api, p.G), dev(api, p.A), dev(api, p.Z),
+                                          torch.from_numpy(alpha).cuda(), None, "split_bf16")
+    want_ev, want_se, _, _ = oracle.expval(p.n, p.G, p.A[idx], p.Z, p.theta.astype(np.float64))
+    assert np.max(np.abs(ev.cpu().numpy()[idx] - want_ev)) <= TOL["split_bf16"]
+    assert np.max(np.abs(se.cpu().numpy()[idx] - want_se)) <= TOL["split_bf16"]
+    want = oracle.expval_grad(p.n, p.G, p.A[idx], p.Z, p.theta.astype(np.float64), alpha[idx], None)
+    assert rel_l2(g.cpu().numpy(), want) <= GRAD_RTOL
