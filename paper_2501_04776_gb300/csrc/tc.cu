@@ -63,12 +63,13 @@ constexpr int kGroupLoads = kGroupCols / 32;
 constexpr uint32_t kTmemCols = 512;   // accumulator (0..255) + running sum (256..511)
 constexpr uint32_t kSumCol = 256;
 constexpr int kMaxOp = 4;
+constexpr int kWPrefetch = 8;  // gradient: W tiles prefetched into L2 this many stages ahead
 
 // Shared-memory layout for a CTA group of CG CTAs (CG = 1 or 2).
 template <int CG, bool GRAD>
 struct Cfg {
     static constexpr int TNB = TN / CG;      // B rows this CTA holds
-    static constexpr int NOP = CG == 2 ? 4 : 2;  // operand stages
+    static constexpr int NOP = CG == 2 ? 4 : (GRAD ? 3 : 2);  // operand stages
     // Operand stage: A_hi (128 x 128 B), A_lo, B (TNB x 128 B).
     static constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = 32768;
     static constexpr uint32_t OP_BYTES = 32768 + TNB * 128;
@@ -361,6 +362,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                             } else {
                                 tma_load_2d(op + C::OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), a0);
                                 tma_load_2d(op + C::OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), a0);
+                                // Warm L2 with the W tiles kWPrefetch stages ahead.
+                                if (ks + kWPrefetch < nks) {
+                                    tma_prefetch_2d(&tmA, (int)((ks + kWPrefetch) * KS), a0);
+                                    tma_prefetch_2d(&tmA2, (int)((ks + kWPrefetch) * KS), a0);
+                                }
                             }
                             omask |= 1u << os;
                             opar = (opar & ~(1u << os)) | (((ito / NOP) & 1u) << os);
