@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
 // in_rows x in_cols bits with ld_in32 words per row. Output words beyond
 // in_rows bits are written as zero; output rows >= in_cols are not written.
 // Tile: 512 x 512 bits per block of 512 threads, read and written as
-// 64-byte row segments; each warp transposes 32 x 32 blocks in registers
+// 64-byte row segments (16-byte accesses where the rows are aligned); each warp transposes 32 x 32 blocks in registers
 // (five shuffle stages swapping off-diagonal sub-blocks of 16, 8, 4, 2, 1).
 // Batched over blockIdx.y: matrix b starts at in + b in_bs32 / out + b out_bs32.
 constexpr int kTT = 512;            // tile edge in bits
@@ -120,11 +120,32 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
     const int64_t r0 = (bid % gx) * kTT;   // input rows = output bit columns
     const int64_t c0 = (bid / gx) * kTT;   // input bit columns = output rows
     const int64_t w0 = c0 >> 5;
+    // Row segments move as 16-byte words (4 threads per 64-byte segment)
+    // when the rows are 16-byte aligned, else word by word.
+    const bool vin = ((ld_in32 & 3) == 0) && ((reinterpret_cast<uintptr_t>(in) & 15) == 0);
+    {
+        uint4 v[kTW / 4];
 #pragma unroll
-    for (int k = 0; k < kTW; ++k) {
-        const int idx = tid + kTT * k, row = idx / kTW, q = idx % kTW;
-        const int64_t r = r0 + row;
-        tin[row][q] = (r < in_rows && w0 + q < ld_in32) ? in[r * ld_in32 + w0 + q] : 0u;
+        for (int k = 0; k < kTW / 4; ++k) {
+            const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
+            const int64_t r = r0 + row;
+            if (vin && r < in_rows && w0 + q + 3 < ld_in32) {
+                v[k] = *reinterpret_cast<const uint4 *>(in + r * ld_in32 + w0 + q);
+            } else {
+                v[k].x = (r < in_rows && w0 + q < ld_in32) ? in[r * ld_in32 + w0 + q] : 0u;
+                v[k].y = (r < in_rows && w0 + q + 1 < ld_in32) ? in[r * ld_in32 + w0 + q + 1] : 0u;
+                v[k].z = (r < in_rows && w0 + q + 2 < ld_in32) ? in[r * ld_in32 + w0 + q + 2] : 0u;
+                v[k].w = (r < in_rows && w0 + q + 3 < ld_in32) ? in[r * ld_in32 + w0 + q + 3] : 0u;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kTW / 4; ++k) {
+            const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
+            tin[row][q] = v[k].x;
+            tin[row][q + 1] = v[k].y;
+            tin[row][q + 2] = v[k].z;
+            tin[row][q + 3] = v[k].w;
+        }
     }
     __syncthreads();
     // 32 x 32 blocks (row block rb, word column cb): each warp takes a pair
@@ -157,11 +178,19 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
     }
     __syncthreads();
     const int64_t ow0 = r0 >> 5;
+    const bool vout = ((ld_out32 & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
 #pragma unroll
-    for (int k = 0; k < kTW; ++k) {
-        const int idx = tid + kTT * k, row = idx / kTW, q = idx % kTW;
+    for (int k = 0; k < kTW / 4; ++k) {
+        const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
         const int64_t orow = c0 + row;
-        if (orow < in_cols && ow0 + q < ld_out32) out[orow * ld_out32 + ow0 + q] = tin[row][q];
+        if (orow >= in_cols) continue;
+        if (vout && ow0 + q + 3 < ld_out32) {
+            *reinterpret_cast<uint4 *>(out + orow * ld_out32 + ow0 + q) =
+                make_uint4(tin[row][q], tin[row][q + 1], tin[row][q + 2], tin[row][q + 3]);
+        } else {
+            for (int e = 0; e < 4; ++e)
+                if (ow0 + q + e < ld_out32) out[orow * ld_out32 + ow0 + q + e] = tin[row][q + e];
+        }
     }
 }
 
