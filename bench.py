@@ -272,34 +272,55 @@ def nnz_parities(api, n, A, G):
     return int(((x * 0x0101010101010101) >> 56).sum().item())
 
 
-def parity_roofline(kt, peaks, n, m, l, s, steps, calls=2):
+def parity_roofline(kt, peaks, n, m, l, s, steps, calls=2, loworder=False):
     """The parity gathers of one step (`calls` library calls, each forming
     P_A, P_A^T and P_Z, P_Z^T from A and Z): algorithmic bytes = the bit
     matrices written (each l m / 8 or s m / 8 bytes, twice) plus the rows of
-    A and Z read, against the measured HBM copy bandwidth."""
+    A and Z read, against the measured HBM copy bandwidth. The low-order form
+    forms no parity matrices: per call it lists the generators' supports (G
+    read, 16 bytes per gate written) and transposes Z (bits read and
+    written); the gradient transposes A once per step."""
     if "parity" not in kt:
         return None
     words = lambda bits: -(-bits // 64)
-    per_call = 8 * (2 * l * words(m) + 2 * s * words(m) + (l + s) * words(n))
-    nbytes = calls * per_call
+    if loworder:
+        wn = words(n) + (words(n) & 1)
+        nbytes = calls * (m * wn * 8 + m * 16 + 2 * s * wn * 8) + 2 * l * wn * 8
+    else:
+        nbytes = calls * 8 * (2 * l * words(m) + 2 * s * words(m) + (l + s) * words(n))
     ms = kt["parity"]["total_ms"] / max(1, steps)
     hbm = peaks.get("hbm_gbs") or 6800.0
     gbs = nbytes / (ms * 1e-3) / 1e9
-    return {"bound": "hbm", "kernels": "k_bit_transpose + k_support_gather", "bytes_per_step": nbytes,
+    names = "k_support_list + k_bit_transpose" if loworder else "k_bit_transpose + k_support_gather"
+    return {"bound": "hbm", "kernels": names, "bytes_per_step": nbytes,
             "ms_per_step": round(ms, 4), "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(gbs / hbm, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
 
-def loworder_roofline(kt, clocks, n, G, s):
-    """The low-order form's pair contractions (M = C S and H = (s V) S^T):
-    2 p s signed FP32 additions per launch, p = qubit pairs with a generator,
-    against one add per lane per clock."""
+def loworder_roofline(kt, clocks, n, G, s, peaks=None):
+    """The low-order form's pair contractions (M = C S and H = (s V) S^T),
+    one launch each. On the tensor cores (the default): dense n x n x s
+    contractions in split BF16, 2 * 2 n^2 s executed flops per launch, against
+    the measured sustained BF16 peak. As sign-flip additions (IQP_LO_TC=0):
+    2 p s FP32 additions per launch, p = qubit pairs with a generator, against
+    one add per lane per clock. Either way the useful work is 2 p s."""
+    useful = 2.0 * generator_pairs(n, G) * s
+    avg_ms = kt["loworder_gemm"]["avg_ms"]
+    if os.environ.get("IQP_LO_TC", "1") != "0" and n >= 256:
+        peaks = peaks or {}
+        executed = 4.0 * n * n * s
+        peak = peaks.get("bf16_tflops_sustained") or 1700.0
+        ach = executed / (avg_ms * 1e-3) / 1e12
+        return {"bound": "tensor", "kernel": "loworder_gemm (pair contractions, tcgen05 split BF16)",
+                "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                "flops_per_launch": executed, "useful_adds_per_launch": useful,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+                if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
     peak = 152 * 128 * mhz * 1e6 / 1e12
-    adds = 2.0 * generator_pairs(n, G) * s
-    ach = adds / (kt["loworder_gemm"]["avg_ms"] * 1e-3) / 1e12
+    ach = useful / (avg_ms * 1e-3) / 1e12
     return {"bound": "alu", "kernel": "loworder_gemm (pair contractions)", "achieved": round(ach, 2),
-            "peak": round(peak, 1), "unit": "Tadd/s", "frac": round(ach / peak, 4), "adds_per_launch": adds,
+            "peak": round(peak, 1), "unit": "Tadd/s", "frac": round(ach / peak, 4), "adds_per_launch": useful,
             "peak_source": "FP32 add: 152 SMs x 128 lanes x max SM clock"}
 
 
@@ -391,7 +412,7 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
                     "frac": round(ach / peak, 4), "flops_per_launch": executed,
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
         elif prec == _lib.LOWORDER_FP32:
-            roof = loworder_roofline(kt, clocks, p.n, p.G, sm)
+            roof = loworder_roofline(kt, clocks, p.n, p.G, sm, peaks)
         else:
             # Forward kernel: nnz * s FP32 signed additions; peak = one FP32
             # add per lane per clock: 152 SMs x 128 lanes x max SM clock.
@@ -537,7 +558,7 @@ def main():
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
     elif prec == _lib.LOWORDER_FP32:
-        roof = loworder_roofline(kt, clocks, n, p.G, s)
+        roof = loworder_roofline(kt, clocks, n, p.G, s, peaks)
         roof["traffic"] = None
     elif prec == _lib.SPARSE_FP32:
         nnz = nnz_parities(api, p.n, A, G)
@@ -611,7 +632,8 @@ def main():
                  "iqp_expval then iqp_expval_grad (as autograd runs them; Phi recomputed in the second)"),
         "other_step": other,
         "roofline": roof, "parity_roofline": parity_roofline(kt, peaks, n, m, l, s, args.steps,
-                                                              1 if args.step == "fused" else 2),
+                                                              1 if args.step == "fused" else 2,
+                                                              loworder=prec == _lib.LOWORDER_FP32),
         "kernels": kt, "gpu_launches": int(launches), "clocks": clocks, "e2e": e2e,
         "ms_steps": [round(x, 3) for x in ms_list],
     }

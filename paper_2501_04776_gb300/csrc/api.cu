@@ -58,9 +58,11 @@ cudaError_t launch_uniform_bits(uint64_t seed, uint64_t stream, int64_t rows, in
 cudaError_t launch_bernoulli_bits(uint64_t seed, uint64_t stream, int64_t rows, int64_t n, double p, int64_t ld,
                                   uint64_t *out, cudaStream_t st);
 int64_t lo_part_samples();
+int64_t lo_split_elems(int64_t n, int64_t lds);
 cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *Z, int64_t s,
                               int64_t ldz, const float *c, int4 *sup, uint64_t *ZT, int64_t ldzt, float *C,
-                              int64_t ldc, float *M, int64_t lds, uint32_t *status, cudaStream_t st);
+                              int64_t ldc, float *M, int64_t lds, __nv_bfloat16 *split, uint32_t *status,
+                              cudaStream_t st);
 cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                             const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, double2 *part,
                             int64_t nparts, uint32_t *status, cudaStream_t st);
@@ -68,7 +70,7 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
                            const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
                            float *W, float *V, double *H, double *gsp, unsigned long long *Kfx, double *grad,
-                           uint32_t *status, cudaStream_t st);
+                           __nv_bfloat16 *split, uint32_t *status, cudaStream_t st);
 cudaError_t launch_bitflip_gates(const float *theta, int64_t m, int64_t mpad, double *c, double *t, cudaStream_t st);
 cudaError_t launch_bitflip_rows(const uint64_t *PA, int64_t ldp, int64_t l, const double *c, double *expval,
                                 cudaStream_t st);
@@ -129,6 +131,7 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_lo_v = take(lo && grad ? n * p.ldw * 4 : 0);
     p.off_lo_h = take(lo && grad ? n * p.ldc * 8 : 0);
     p.off_lo_gs = take(lo && grad ? n * cdiv(s, lo_part_samples()) * 8 : 0);
+    p.off_lo_a = take(lo ? lo_split_elems(n, p.ldw) * 2 : 0);  // split-BF16 operand of the pair contractions
     // sparse: 64-bit fixed-point gradient accumulators and their scale
     p.off_gpart = take(grad ? (sparse ? m * 8 + 8 : (lo ? n * n * 8 + 8 : p.natile * m * 8)) : 0);
     p.off_ab = take(mmd ? l * 16 : 0);
@@ -266,7 +269,8 @@ iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, cons
         IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, at<float>(ws, p.off_c), nullptr, nullptr, st));
         IQP_TRY(launch_lo_prepare(p.n, G, p.m, ldg, Z, p.s, ldz, at<float>(ws, p.off_c), at<int4>(ws, p.off_sup),
                                   at<uint64_t>(ws, p.off_pzt), p.ldzt, at<float>(ws, p.off_lo_c), p.ldc,
-                                  at<float>(ws, p.off_lo_m), p.ldw, at<uint32_t>(ws, p.off_status), st));
+                                  at<float>(ws, p.off_lo_m), p.ldw, at<__nv_bfloat16>(ws, p.off_lo_a),
+                                  at<uint32_t>(ws, p.off_status), st));
         return IQP_OK;
     }
     IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
@@ -325,7 +329,8 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
                                p.ldw, at<float>(ws, p.off_lo_c), p.ldc, p.s, p.m, at<int4>(ws, p.off_sup), alpha, beta,
                                at<uint64_t>(ws, p.off_rt), p.ldlt, at<float>(ws, p.off_w), at<float>(ws, p.off_lo_v),
                                at<double>(ws, p.off_lo_h), at<double>(ws, p.off_lo_gs),
-                               at<unsigned long long>(ws, p.off_gpart), grad, at<uint32_t>(ws, p.off_status), st));
+                               at<unsigned long long>(ws, p.off_gpart), grad, at<__nv_bfloat16>(ws, p.off_lo_a),
+                               at<uint32_t>(ws, p.off_status), st));
         return IQP_OK;
     }
     if (p.prec == IQP_SPARSE_FP32) {

@@ -37,7 +37,7 @@ struct Plan {
     size_t off_status, off_pa, off_pz, off_pzt, off_pat, off_rt, off_c, off_part, off_w, off_gpart;
     size_t off_ab, off_s12, off_T, off_terms, off_zt, off_sup, total;
     // low-order form: C (+ d), M = C S, V, H, single-gate partials; ldc floats per row of C and H
-    size_t off_lo_c, off_lo_m, off_lo_v, off_lo_h, off_lo_gs;
+    size_t off_lo_c, off_lo_m, off_lo_v, off_lo_h, off_lo_gs, off_lo_a;
     int64_t ldc;
     bool indep;     // one sample batch per observable (Z has l * s rows)
     const uint64_t *G;  // generators (read by the independent-batch kernels)
@@ -55,6 +55,17 @@ struct SparseIndep {
 };
 
 Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec);
+
+// Dense contraction on the tensor cores (split BF16, FP32 accumulation):
+//   out[r][c] = sum_{k < K} (a_hi[r][k] + a_lo[r][k]) (1 - 2 bit k of b row c)
+// for r < rows, c < nb. a_hi / a_lo: rows x kpad BF16 (row-major, kpad a
+// multiple of 64, zero for k >= K); b_bits: nb rows of ldb words (even,
+// >= 4, bits >= K zero or multiplied by zero); out: row-major, ldo elements
+// per row (a multiple of 4), FP32 or FP64. cudaErrorNotSupported when a
+// shape or layout rule does not hold (nothing is launched then).
+cudaError_t launch_tc_dense(const __nv_bfloat16 *a_hi, const __nv_bfloat16 *a_lo, int64_t rows, int64_t kpad,
+                            int64_t k, const uint64_t *b_bits, int64_t nb, int64_t ldb, void *out, int64_t ldo,
+                            bool out_f64, uint32_t *status, cudaStream_t st);
 
 // ---------------------------------------------------------------- status
 

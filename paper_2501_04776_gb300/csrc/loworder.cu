@@ -22,6 +22,8 @@
 // Device-side errors: a generator of weight > 2 records IQP_ERR_ARG, an
 // observable of weight > 1024 records IQP_ERR_UNSUPPORTED (in the workspace
 // status word); the outputs are then not meaningful.
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace iqp {
@@ -247,6 +249,39 @@ __global__ void __launch_bounds__(32) k_lo_h(const unsigned long long *__restric
             }
         }
         __syncwarp();
+    }
+}
+
+// ------------------------------------- the contractions on the tensor cores
+// With the tensor cores both contractions are dense GEMMs with one +-1
+// operand from bits, M = C S (K = the n qubits r) and H = (s o V) S^T
+// (K = the s samples), like the phase contraction; the FP32 operand goes in
+// as a hi + lo BF16 split. k_lo_split writes that split: element (q, k) of
+// a rows x cols FP32 matrix, multiplied by s_q(k) = (-1)^(bit k of zt row q)
+// when zt is given, into rows x kpad BF16 matrices (zero for k >= cols).
+// One thread per 8 consecutive elements.
+__global__ void k_lo_split(const float *__restrict__ in, int64_t ld_in, int64_t rows, int64_t cols,
+                           const uint64_t *__restrict__ zt, int64_t ldzt, int64_t kpad, __nv_bfloat16 *__restrict__ hi,
+                           __nv_bfloat16 *__restrict__ lo) {
+    const int64_t per_row = kpad / 8, total = rows * per_row;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = e / per_row, k0 = (e - q * per_row) * 8;
+        const uint32_t sb = zt ? (uint32_t)(zt[q * ldzt + (k0 >> 6)] >> (k0 & 63)) & 0xFFu : 0u;
+        uint32_t ph[4], pl[4];
+#pragma unroll
+        for (int t = 0; t < 8; t += 2) {
+            float x0 = k0 + t < cols ? in[q * ld_in + k0 + t] : 0.f;
+            float x1 = k0 + t + 1 < cols ? in[q * ld_in + k0 + t + 1] : 0.f;
+            if ((sb >> t) & 1u) x0 = -x0;
+            if ((sb >> (t + 1)) & 1u) x1 = -x1;
+            const __nv_bfloat16 h0 = __float2bfloat16_rn(x0), h1 = __float2bfloat16_rn(x1);
+            const __nv_bfloat16 l0 = __float2bfloat16_rn(x0 - __bfloat162float(h0));
+            const __nv_bfloat16 l1 = __float2bfloat16_rn(x1 - __bfloat162float(h1));
+            ph[t / 2] = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+            pl[t / 2] = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+        }
+        *reinterpret_cast<uint4 *>(hi + q * kpad + k0) = make_uint4(ph[0], ph[1], ph[2], ph[3]);
+        *reinterpret_cast<uint4 *>(lo + q * kpad + k0) = make_uint4(pl[0], pl[1], pl[2], pl[3]);
     }
 }
 
@@ -639,6 +674,33 @@ cudaError_t launch_fixed_scale(const double *alpha, const double *beta, int64_t 
 
 int64_t lo_part_samples() { return kBlk; }
 
+// The pair contractions on the tensor cores (split BF16) unless IQP_LO_TC=0.
+bool lo_tensor() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("IQP_LO_TC");
+        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+// Elements of the split-BF16 operand buffer (hi and lo) the tensor-core
+// contractions need: the larger of C's (n x round_up(n, 64)) and s o V's
+// (n x lds), twice.
+int64_t lo_split_elems(int64_t n, int64_t lds) {
+    const int64_t kc = round_up(n, 64);
+    return 2 * n * (kc > lds ? kc : lds);
+}
+
+namespace {
+cudaError_t launch_split(const float *in, int64_t ld_in, int64_t rows, int64_t cols, const uint64_t *zt,
+                         int64_t ldzt, int64_t kpad, __nv_bfloat16 *hi, __nv_bfloat16 *lo, cudaStream_t st) {
+    LaunchScope ls(IQP_KERNEL_LOWORDER, st);
+    k_lo_split<<<grid_1d(rows * (kpad / 8)), 256, 0, st>>>(in, ld_in, rows, cols, zt, ldzt, kpad, hi, lo);
+    return cudaGetLastError();
+}
+}  // namespace
+
 // C, d and M = C S. C: n x ldc fp32 (+ d: ldc fp32 after it), M: n x lds,
 // ZT: n x ldzt words (the samples transposed), sup: m int4.
 int64_t lo_lde(int64_t n) { return cdiv(n, 64); }
@@ -648,7 +710,8 @@ int64_t lo_lde(int64_t n) { return cdiv(n, 64); }
 // transposed), sup: m int4.
 cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *Z, int64_t s,
                               int64_t ldz, const float *c, int4 *sup, uint64_t *ZT, int64_t ldzt, float *C,
-                              int64_t ldc, float *M, int64_t lds, uint32_t *status, cudaStream_t st) {
+                              int64_t ldc, float *M, int64_t lds, __nv_bfloat16 *split, uint32_t *status,
+                              cudaStream_t st) {
     cudaError_t e = launch_support_list(G, m, ldg, n, sup, st);
     if (e != cudaSuccess) return e;
     if ((e = launch_bit_transpose_batched(Z, 1, s, n, ldz, ZT, ldzt, st)) != cudaSuccess) return e;
@@ -661,6 +724,14 @@ cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t l
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
         k_lo_build<<<grid_1d(m), 256, 0, st>>>(sup, c, m, n, C, ldc, d, E, lde, status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    // M = C S: rows q, columns the samples (Z's rows), K the qubits r.
+    const int64_t kc = round_up(n, 64);
+    if (lo_tensor() && split != nullptr && ldz >= 4 && ldz % 2 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15) == 0) {
+        __nv_bfloat16 *hi = split, *lo = split + n * kc;
+        if ((e = launch_split(C, ldc, n, n, nullptr, 0, kc, hi, lo, st)) != cudaSuccess) return e;
+        e = launch_tc_dense(hi, lo, n, kc, n, Z, s, ldz, M, lds, false, status, st);
+        if (e != cudaErrorNotSupported) return e;
     }
     LaunchScope ls(IQP_KERNEL_LOWORDER_GEMM, st);
     k_lo_cs<<<dim3((unsigned)n, (unsigned)cdiv(s, 2048)), 32, 0, st>>>(E, lde, C, ldc, ZT, ldzt, s, M, lds);
@@ -685,7 +756,7 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
                            const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
                            float *W, float *V, double *H, double *gsp, unsigned long long *Kfx, double *grad,
-                           uint32_t *status, cudaStream_t st) {
+                           __nv_bfloat16 *split, uint32_t *status, cudaStream_t st) {
     const int64_t nblk = cdiv(s, kBlk);
     double *scale = reinterpret_cast<double *>(Kfx + n * n);
     const float *d = C + n * ldc;
@@ -708,7 +779,16 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
                                                                                   V, gsp);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    {
+    // H = (s o V) S^T: rows q, columns r (ZT's rows), K the samples.
+    bool h_done = false;
+    if (lo_tensor() && split != nullptr) {
+        __nv_bfloat16 *hi = split, *lo = split + n * lds;
+        if ((e = launch_split(V, lds, n, s, ZT, ldzt, lds, hi, lo, st)) != cudaSuccess) return e;
+        e = launch_tc_dense(hi, lo, n, lds, s, ZT, n, ldzt, H, ldc, true, status, st);
+        if (e != cudaSuccess && e != cudaErrorNotSupported) return e;
+        h_done = e == cudaSuccess;
+    }
+    if (!h_done) {
         LaunchScope ls(IQP_KERNEL_LOWORDER_GEMM, st);
         k_lo_h<<<dim3((unsigned)n, (unsigned)kHSplit), 32, 0, st>>>(E, lde, ZT, ldzt, V, lds, s, H, ldc);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -66,10 +66,10 @@ constexpr int kMaxOp = 4;
 constexpr int kWPrefetch = 8;  // gradient: W tiles prefetched into L2 this many stages ahead
 
 // Shared-memory layout for a CTA group of CG CTAs (CG = 1 or 2).
-template <int CG, bool GRAD>
+template <int CG, bool ATMA>
 struct Cfg {
     static constexpr int TNB = TN / CG;      // B rows this CTA holds
-    static constexpr int NOP = CG == 2 ? 4 : (GRAD ? 3 : 2);  // operand stages
+    static constexpr int NOP = CG == 2 ? 4 : (ATMA ? 3 : 2);  // operand stages
     // Operand stage: A_hi (128 x 128 B), A_lo, B (TNB x 128 B).
     static constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = 32768;
     static constexpr uint32_t OP_BYTES = 32768 + TNB * 128;
@@ -118,6 +118,9 @@ struct TcArgs {
     const uint32_t *pa32;  // P_A, for the gradient mask
     int64_t ldp32;
     double *gpart;
+    void *out;             // mode 3: the accumulator stored as is (FP32, or FP64 if out_f64)
+    int64_t ldo;
+    int out_f64;
     uint32_t *status;
     uint64_t limit_ns;
 };
@@ -234,17 +237,49 @@ __device__ __forceinline__ void store_w32(const TcArgs &args, int64_t row, int64
     }
 }
 
-// GRAD = false: phase contraction (MODE 0 stats / MODE 1 W / MODE 2 both).
+// Accumulator values of 32 consecutive columns col0.. of `row`, stored into
+// args.out (row-major, args.ldo elements per row, columns < args.s): FP32, or
+// FP64 when args.out_f64. Rows start 16-byte aligned (ldo a multiple of 4).
+__device__ __forceinline__ void store_out32(const TcArgs &args, int64_t row, int64_t col0, const uint32_t (&r)[32]) {
+    if (args.out_f64) {
+        double *d = static_cast<double *>(args.out) + row * args.ldo + col0;
+        if (col0 + 32 <= args.s) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 2)
+                *reinterpret_cast<double2 *>(d + e) =
+                    make_double2((double)__uint_as_float(r[e]), (double)__uint_as_float(r[e + 1]));
+        } else {
+            for (int e = 0; e < 32 && col0 + e < args.s; ++e) d[e] = (double)__uint_as_float(r[e]);
+        }
+    } else {
+        float *f = static_cast<float *>(args.out) + row * args.ldo + col0;
+        if (col0 + 32 <= args.s) {
+#pragma unroll
+            for (int e = 0; e < 32; e += 4)
+                *reinterpret_cast<float4 *>(f + e) = make_float4(__uint_as_float(r[e]), __uint_as_float(r[e + 1]),
+                                                                 __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
+        } else {
+            for (int e = 0; e < 32 && col0 + e < args.s; ++e) f[e] = __uint_as_float(r[e]);
+        }
+    }
+}
+
+// GRAD = false: phase contraction (MODE 0 stats / MODE 1 W / MODE 2 both),
+//              or (MODE 3) a dense contraction whose accumulator is stored.
 // GRAD = true : gradient contraction.
+// AT = true: the A operand arrives by TMA in the swizzled layout (always for
+// the gradient's W; for MODE 3, a dense split-BF16 matrix); AT = false: the
+// producer warps expand it from P_A bits and the hi/lo split of 2 theta.
 // CG = 1: one CTA per tile of 128 rows; CG = 2: a CTA pair per tile of 256 rows.
 // MC = 2 (gradient with CG = 1): clusters of two CTAs on the same 128
 // observables and adjacent 256-gate columns; each loads half of every W tile
 // and multicasts it to both, halving W's L2-to-SM traffic.
-template <bool GRAD, int MODE, int CG, int MC>
+template <bool GRAD, int MODE, int CG, int MC, bool AT>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
          const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
-    using C = Cfg<CG, GRAD>;
+    constexpr bool ATMA = GRAD || AT;  // A operand by TMA
+    using C = Cfg<CG, ATMA>;
     constexpr int NOP = C::NOP;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = aligned_smem(smem_raw);
@@ -307,7 +342,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             prefetch_tmap(&tmA);
             prefetch_tmap(&tmB);
-            if (GRAD) prefetch_tmap(&tmA2);
+            if (ATMA) prefetch_tmap(&tmA2);
             uint32_t itb = 0, ito = 0;
             uint32_t bmask = 0, bpar = 0, omask = 0, opar = 0;  // issued stages and their last parities
             bool ok = true;
@@ -327,7 +362,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     uint8_t *bits = smem + C::SM_BITS + bs * C::BT_BYTES;
                     const int x = (int)(kb * 4);
-                    if (GRAD) {
+                    if (ATMA) {
                         mbar_arrive_expect_tx(&bar->bits_full[bs], C::TNB * 32);
                         tma_load_2d(bits + C::BT_B, &tmB, &bar->bits_full[bs], x, b0);
                     } else {
@@ -339,8 +374,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     bmask |= 1u << bs;
                     bpar = (bpar & ~(1u << bs)) | (((itb / NBITS) & 1u) << bs);
-                    if (GRAD) {
-                        // W_hi / W_lo tiles of the operand stages of this bits stage.
+                    if (ATMA) {
+                        // A_hi / A_lo tiles (W, or a dense operand) of the operand stages of this bits stage.
                         for (int q = 0; q < KB / KS; ++q) {
                             const int ks = kb * (KB / KS) + q;
                             if (ks >= nks) break;
@@ -381,7 +416,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if ((bmask >> i) & 1u) mbar_drain(&bar->bits_full[i], (bpar >> i) & 1u, status, lim);
 #pragma unroll
             for (int i = 0; i < NOP; ++i)
-                if (GRAD && ((omask >> i) & 1u)) mbar_drain(&bar->w_full[i], (opar >> i) & 1u, status, lim);
+                if (ATMA && ((omask >> i) & 1u)) mbar_drain(&bar->w_full[i], (opar >> i) & 1u, status, lim);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
@@ -397,7 +432,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const bool got =
                         CG == 2 ? mbar_wait_cluster(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim)
                                 : (mbar_wait(&bar->op_full[os], (ito / NOP) & 1u, abort_flag, status, lim) &&
-                                   (!GRAD ||
+                                   (!ATMA ||
                                     mbar_wait(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim)));
                     if (!got) {
                         ok = false;
@@ -482,12 +517,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint8_t *bits = smem + C::SM_BITS + bs * C::BT_BYTES;
                 uint8_t *op = smem + C::SM_OP + os * C::OP_BYTES;
                 expand_b<C::TNB>(bits + C::BT_B, op + C::OP_B, q, gt);
-                if (!GRAD)
+                if (!ATMA)
                     expand_a(bits + C::BT_A, bits + C::BT_CHI, bits + C::BT_CLO, op + C::OP_A_HI, op + C::OP_A_LO, q,
                              gt);
                 fence_proxy_async_smem();
                 __syncwarp();
-                if (GRAD && CG == 2 && !wait_warp(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim)) {
+                if (ATMA && CG == 2 && !wait_warp(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim)) {
                     // A pair's W tiles must have landed before the stage is released.
                     ok = false;
                     break;
@@ -618,6 +653,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 if (rv && nvalid > 0)
                     args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
+            } else if (!GRAD && MODE == 3) {
+                const int64_t c0 = tn * TN + group * kGroupCols;
+                uint32_t r[32];
+#pragma unroll 1
+                for (int c = 0; c < kGroupLoads; ++c) {
+                    load_sum32(tbase + c * 32, chunked, r);
+                    if (row < args.l && c0 + c * 32 < args.s) store_out32(args, row, c0 + c * 32, r);
+                }
             } else if (!GRAD) {
                 const int64_t c0 = tn * TN + group * kGroupCols;
                 const bool rv = row < args.l;
@@ -735,14 +778,14 @@ bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool GRAD, int MODE, int CG, int MC = 1>
+template <bool GRAD, int MODE, int CG, int MC = 1, bool AT = GRAD>
 cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
                      cudaStream_t st) {
-    using C = Cfg<CG, GRAD>;
+    using C = Cfg<CG, GRAD || AT>;
     constexpr int CL = CG * MC;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, MC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, MC, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -751,9 +794,13 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
     int sms = num_sms();
     if (sms < CL) sms = CL;
     const int64_t groups = ntiles < sms / CL ? ntiles : sms / CL;
-    LaunchScope ls(GRAD ? IQP_KERNEL_GRAD_TC : (MODE == 1 ? IQP_KERNEL_RECOMPUTE_TC : IQP_KERNEL_PHASE_TC), st);
+    LaunchScope ls(GRAD          ? IQP_KERNEL_GRAD_TC
+                   : MODE == 1 ? IQP_KERNEL_RECOMPUTE_TC
+                   : MODE == 3 ? IQP_KERNEL_LOWORDER_GEMM
+                               : IQP_KERNEL_PHASE_TC,
+                   st);
     if (CL == 1) {
-        k_tc<GRAD, MODE, 1, 1><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
+        k_tc<GRAD, MODE, 1, 1, AT><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -768,7 +815,7 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, MC>, a, a2, b, args);
+    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, MC, AT>, a, a2, b, args);
 }
 
 // Gradient kernel form: single-CTA MMAs; with IQP_GRAD_MULTICAST=1, clusters
@@ -844,6 +891,9 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.pa32 = nullptr;
     a.ldp32 = 2 * p.ldp;
     a.gpart = nullptr;
+    a.out = nullptr;
+    a.ldo = 0;
+    a.out_f64 = 0;
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
     if (cg == 2) {
@@ -890,10 +940,53 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.pa32 = at<uint32_t>(ws, p.off_pa);
     a.ldp32 = 2 * p.ldp;
     a.gpart = at<double>(ws, p.off_gpart);
+    a.out = nullptr;
+    a.ldo = 0;
+    a.out_f64 = 0;
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
     if (mc) return launch_k<true, 0, 1, 2>(mhi, mlo, mb, a, st);
     return launch_k<true, 0, 1>(mhi, mlo, mb, a, st);
+}
+
+cudaError_t launch_tc_dense(const __nv_bfloat16 *a_hi, const __nv_bfloat16 *a_lo, int64_t rows, int64_t kpad,
+                            int64_t k, const uint64_t *b_bits, int64_t nb, int64_t ldb, void *out, int64_t ldo,
+                            bool out_f64, uint32_t *status, cudaStream_t st) {
+    const int cg = cta_group();
+    CUtensorMap mhi, mlo, mb;
+    if (kpad % KS != 0 || k > kpad || k > 64 * ldb || ldb % 2 != 0 || ldb < 4 || ldo % 4 != 0 ||
+        !make_map(&mhi, a_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, kpad, rows, kpad * 2, KS, TM,
+                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mlo, a_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, kpad, rows, kpad * 2, KS, TM,
+                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mb, b_bits, CU_TENSOR_MAP_DATA_TYPE_UINT64, ldb, nb, ldb * 8, 4, (uint32_t)(TN / cg),
+                  CU_TENSOR_MAP_SWIZZLE_NONE))
+        return cudaErrorNotSupported;
+    TcArgs a;
+    a.l = rows;
+    a.s = nb;
+    a.m = k;
+    a.nks = cdiv(k, KS);
+    a.chunk = 64;
+    a.tiles_m = cdiv(rows, TM * cg);
+    a.tiles_n = cdiv(nb, TN);
+    a.group_m = tile_group();
+    a.chi = a.clo = nullptr;
+    a.part = nullptr;
+    a.nparts = 0;
+    a.alpha = a.beta = nullptr;
+    a.whi = a.wlo = nullptr;
+    a.ldw = 0;
+    a.pa32 = nullptr;
+    a.ldp32 = 0;
+    a.gpart = nullptr;
+    a.out = out;
+    a.ldo = ldo;
+    a.out_f64 = out_f64 ? 1 : 0;
+    a.status = status;
+    a.limit_ns = default_spin_limit_ns();
+    if (cg == 2) return launch_k<false, 3, 2, 1, true>(mhi, mlo, mb, a, st);
+    return launch_k<false, 3, 1, 1, true>(mhi, mlo, mb, a, st);
 }
 
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st) {

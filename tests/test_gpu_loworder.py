@@ -183,3 +183,40 @@ def test_device_errors_for_heavy_generators_and_observables(api):
     api.expval_raw(n, th_dev(np.zeros(G.shape[0])), dev(api, G), dev(api, A), dev(api, Z), LO)
     assert api.read_status() == _lib.ERR_UNSUPPORTED
     assert api.read_status() == _lib.OK  # cleared
+
+
+@pytest.mark.parametrize("lo_tc", ["0", "1"])
+def test_pair_contraction_forms_match_oracle(lo_tc):
+    """Both forms of the pair contractions M = C S and H = (s o V) S^T: on the
+    tensor cores (split BF16, the default) and as sign-flip FP32 additions
+    over the pairs that carry a generator (IQP_LO_TC=0), on a ragged shape
+    (n = 300: 300 rows in 256-row tiles, s = 1500), in a fresh process."""
+    import json
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import json, numpy as np, torch, oracle
+from paper_2501_04776_gb300 import api, inputs as I
+rng = I.Rng(17)
+n, l, s = 300, 120, 1500
+G = I.local_gates_packed(n)
+th = (0.02 * rng.normal(G.shape[0], 1)).astype(np.float32)
+A = I.bernoulli_bits(rng, l, n, 0.03, 2); Z = I.uniform_bits(rng, s, n, 3)
+w = rng.normal(l, 4)
+d = api.to_device_bits
+t = torch.from_numpy(th).cuda()
+ev, se = api.expval_raw(n, t, d(G), d(A), d(Z), "loworder_fp32")
+g = api.expval_grad(n, t, d(G), d(A), d(Z), torch.from_numpy(-w / s).cuda(), None, "loworder_fp32")
+wev, wse, _, _ = oracle.expval(n, G, A, Z, th.astype(np.float64))
+wg = oracle.expval_grad(n, G, A, Z, th.astype(np.float64), -w / s, None)
+print(json.dumps({"ev": float(np.max(np.abs(ev.cpu().numpy() - wev))), "se": float(np.max(np.abs(se.cpu().numpy() - wse))),
+                  "g": float(np.linalg.norm(g.cpu().numpy() - wg) / np.linalg.norm(wg)), "status": api.read_status()}))
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, IQP_LO_TC=lo_tc, PYTHONPATH=root)
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=900)
+    assert out.returncode == 0, out.stderr[-2000:]
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    assert r["status"] == 0
+    assert r["ev"] <= TOL and r["se"] <= TOL and r["g"] <= GRAD_RTOL
