@@ -341,7 +341,7 @@ struct LoShared {
     float pc[kPairMax];        // C restricted to those pairs
     int scan[kBlk];
     int wsum[kBlk / 32];
-    double red[kBlk / 32];
+    float redf[kBlk / 32];
 };
 
 // Sample blocks handled by one CTA: the support and, when it fits, the
@@ -410,15 +410,20 @@ __device__ int lo_fill_pairs(LoShared &sh, int nq, int64_t *c0, const unsigned l
     return np;
 }
 
-__device__ __forceinline__ double block_sum(double v, double *red) {
+// Sum of v over the CTA in FP32 (warp shuffles, then the warps' sums in
+// fixed order); every thread gets it. The partial sums of one 256-sample
+// block are kept in FP32 and combined across blocks in FP64, as in the
+// tensor-core epilogue (FP64 arithmetic runs at 1/64 of the FP32 rate here).
+__device__ __forceinline__ float block_sum_f(float v, float *red) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double t = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kBlk / 32; ++w) t += red[w];
     return t;
 }
 
@@ -480,12 +485,12 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
         phi -= 2.f * pairs;
         if (MODE == 0) {
             const float cv = valid ? cosf(phi) : 0.f;
-            const double S = block_sum((double)cv, sh.red);
+            const float S = block_sum_f(cv, sh.redf);
             const int64_t nb = s - blk * kBlk < kBlk ? s - blk * kBlk : kBlk;
-            const float mean = (float)(S / (double)nb);
+            const float mean = S / (float)nb;
             const float dv = cv - mean;
-            const double M2 = block_sum(valid ? (double)(dv * dv) : 0.0, sh.red);
-            if (tid == 0) part[a * nparts + blk] = make_double2(S, M2);
+            const float M2 = block_sum_f(valid ? dv * dv : 0.f, sh.redf);
+            if (tid == 0) part[a * nparts + blk] = make_double2((double)S, (double)M2);
         } else {
             float sn, cn;
             sincosf(phi, &sn, &cn);
@@ -501,7 +506,7 @@ __global__ void __launch_bounds__(kBlk) k_lo_v(const uint64_t *__restrict__ AT, 
                                                const uint64_t *__restrict__ ZT, int64_t ldzt,
                                                const float *__restrict__ W, int64_t lds, int64_t s, int64_t nblk,
                                                float *__restrict__ V, double *__restrict__ gsp) {
-    __shared__ double red[kBlk / 32];
+    __shared__ float red[kBlk / 32];
     __shared__ int obs[kObsMax];
     __shared__ int wsum[kBlk / 32];
     const int64_t q = blockIdx.x;
@@ -566,8 +571,8 @@ __global__ void __launch_bounds__(kBlk) k_lo_v(const uint64_t *__restrict__ AT, 
         const float vv = valid ? v[g] : 0.f;
         if (store && i < lds) V[q * lds + i] = vv;
         const float u = ((ZT[q * ldzt + (ic >> 6)] >> (ic & 63)) & 1ull) ? -vv : vv;
-        const double t = block_sum((double)u, red);
-        if (store && threadIdx.x == 0) gsp[q * nblk + blk] = t;
+        const float t = block_sum_f(u, red);
+        if (store && threadIdx.x == 0) gsp[q * nblk + blk] = (double)t;
     }
 }
 
