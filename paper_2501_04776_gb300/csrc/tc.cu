@@ -10,12 +10,19 @@
 // one thread issues two tcgen05.mma per 16-gate step (hi and lo share B).
 // The epilogue runs in the producer warps straight from TMEM:
 //   mode 0: cos, per-observable (S, M2) partials over 64-sample groups;
-//   mode 1: W = sin Phi (alpha + beta cos Phi), split into hi + lo BF16 rows.
+//   mode 1: W = sin Phi (alpha + beta cos Phi), split into hi + lo BF16 rows;
+//   mode 2: both from one pass (the loss coefficients known in advance).
 // Phi itself is never written.
+//
+// Dense form (mode 3, A by TMA): out = (A_hi + A_lo) (1 - 2 B_bits)^T for a
+// dense split-BF16 matrix A brought in by TMA and a +-1 operand expanded from
+// bits as above, the FP32 accumulator stored as is (FP32 or FP64). The
+// low-order form's pair contractions M = C S and H = (s o V) S^T use it.
 //
 // k_grad_tc: the gradient contraction Q[a][j] = sum_i W[a][i] S_Z[i][j]
 // (Sec. 2.4, backward of eq. Emat), 128 observables x 256 gates per tile,
-// K = samples. W_hi / W_lo tiles arrive by TMA in the swizzled layout; the
+// K = samples. W_hi / W_lo tiles arrive by TMA in the swizzled layout (three
+// operand stages, each W tile also prefetched into L2 eight stages ahead); the
 // +-1 operand is expanded from the transposed sample parities P_Z^T. The
 // epilogue masks by 2 P_A[a][j], reduces over the tile's observables with a
 // warp reduce-scatter and writes one FP64 partial per (observable tile, gate).
