@@ -278,6 +278,30 @@ __global__ void __launch_bounds__(256) k_support_list(const uint64_t *__restrict
     if (lane == 0) sup[j] = make_int4(q0, q1, q2, cnt);
 }
 
+// The same list with one thread per generator, for rows of at most 16 words
+// (n <= 1024): a warp per generator would leave most lanes idle there.
+__global__ void __launch_bounds__(256) k_support_list_short(const uint64_t *__restrict__ G, int64_t m, int64_t ldg,
+                                                             int64_t n, int4 *__restrict__ sup) {
+    const int64_t nw = (n + 63) >> 6;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t *row = G + j * ldg;
+        int cnt = 0, q0 = 0, q1 = 0, q2 = 0;
+        for (int64_t w = 0; w < nw; ++w) {
+            uint64_t word = row[w];
+            if (w == nw - 1 && (n & 63)) word &= (1ull << (n & 63)) - 1ull;  // never a qubit >= n
+            while (word) {
+                const int q = (int)(64 * w) + __ffsll((long long)word) - 1;
+                word &= word - 1ull;
+                if (cnt == 0) q0 = q;
+                else if (cnt == 1) q1 = q;
+                else if (cnt == 2) q2 = q;
+                ++cnt;
+            }
+        }
+        sup[j] = make_int4(q0, q1, q2, cnt);
+    }
+}
+
 }  // namespace
 
 // Transposes `batch` bit matrices of in_rows x in_cols bits (ld_in words per
@@ -303,7 +327,13 @@ cudaError_t launch_bit_transpose_batched(const uint64_t *in, int64_t batch, int6
 
 cudaError_t launch_support_list(const uint64_t *G, int64_t m, int64_t ldg, int64_t n, int4 *sup, cudaStream_t st) {
     LaunchScope ls(IQP_KERNEL_PARITY, st);
-    k_support_list<<<(unsigned)cdiv(m, 8), 256, 0, st>>>(G, m, ldg, n, sup);
+    if (cdiv(n, 64) <= 16) {
+        int64_t blocks = cdiv(m, 256);
+        if (blocks > 16384) blocks = 16384;
+        k_support_list_short<<<(unsigned)(blocks < 1 ? 1 : blocks), 256, 0, st>>>(G, m, ldg, n, sup);
+    } else {
+        k_support_list<<<(unsigned)cdiv(m, 8), 256, 0, st>>>(G, m, ldg, n, sup);
+    }
     return cudaGetLastError();
 }
 
