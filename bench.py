@@ -154,7 +154,7 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------ traffic
 
 def measured_traffic(kernel, sizes):
-    """DRAM bytes per launch of `kernel` from the committed ncu capture
+    """DRAM bytes per contraction of `kernel` (summed over its launches) from the committed ncu capture
     (profiles/dram_traffic.json), or None if the capture was of another
     workload or the kernel sources changed since."""
     import hashlib
@@ -405,11 +405,14 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
         kt = _kernel_times(lib)
         if prec == _lib.SPLIT_BF16:
             dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
-            executed = 4.0 * lm * sm * mm
+            executed = 4.0 * lm * sm * mm  # one contraction per call (a split last round is a second launch)
             peak = peaks.get("bf16_tflops_sustained") or 1700.0
-            ach = executed / (kt[dom]["avg_ms"] * 1e-3) / 1e12
+            per_call = kt[dom]["total_ms"] / max(1, args.steps)
+            ach = executed / (per_call * 1e-3) / 1e12
             roof = {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
-                    "frac": round(ach / peak, 4), "flops_per_launch": executed,
+                    "frac": round(ach / peak, 4), "flops_per_contraction": executed,
+                    "ms_per_contraction": round(per_call, 4),
+                    "launches_per_contraction": round(kt[dom]["launches"] / max(1, args.steps), 2),
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
         elif prec == _lib.LOWORDER_FP32:
             roof = loworder_roofline(kt, clocks, p.n, p.G, sm, peaks)
@@ -549,12 +552,18 @@ def main():
     if prec == _lib.SPLIT_BF16:
         dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
         traffic = measured_traffic(dom, (n, m, l, s))
-        executed = 4.0 * l * s * m  # two BF16 products (hi, lo) of 2*l*s*m flops per launch
+        # two BF16 products (hi, lo) of 2*l*s*m flops per contraction; one
+        # contraction per step, in one launch or (a split last round of
+        # tiles) two, timed together
+        executed = 4.0 * l * s * m
         peak = peaks.get("bf16_tflops_sustained") or 1700.0
-        achieved = executed / (kt[dom]["avg_ms"] * 1e-3) / 1e12
+        per_step = kt[dom]["total_ms"] / max(1, args.steps)
+        achieved = executed / (per_step * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
                 "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "flops_per_launch": executed, "useful_tflops": round(achieved / 2, 1),
+                "flops_per_contraction": executed, "ms_per_contraction": round(per_step, 4),
+                "launches_per_contraction": round(kt[dom]["launches"] / max(1, args.steps), 2),
+                "useful_tflops": round(achieved / 2, 1),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
                 if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
     elif prec == _lib.LOWORDER_FP32:

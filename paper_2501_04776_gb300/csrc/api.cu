@@ -132,6 +132,11 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_lo_h = take(lo && grad ? n * p.ldc * 8 : 0);
     p.off_lo_gs = take(lo && grad ? n * cdiv(s, lo_part_samples()) * 8 : 0);
     p.off_lo_a = take(lo ? lo_split_elems(n, p.ldw) * 2 : 0);  // split-BF16 operand of the pair contractions
+    p.off_skp = 0;
+    const size_t skp = take(prec == IQP_SPLIT_BF16 && !bitflip && !indep
+                                ? (int64_t)kMaxSplitCtas * kSplitSlotFloats * 4 + (int64_t)kMaxSplitCtas * 4
+                                : 0);
+    if (prec == IQP_SPLIT_BF16 && !bitflip && !indep) p.off_skp = skp;
     // sparse: 64-bit fixed-point gradient accumulators and their scale
     p.off_gpart = take(grad ? (sparse ? m * 8 + 8 : (lo ? n * n * 8 + 8 : p.natile * m * 8)) : 0);
     p.off_ab = take(mmd ? l * 16 : 0);

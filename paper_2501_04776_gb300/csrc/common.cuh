@@ -17,6 +17,10 @@ namespace iqp {
 constexpr int kPartColsSimt = 128;  // samples per (S, M2) partial, FP32 form
 constexpr int kPartColsTc = 64;     // samples per (S, M2) partial, tensor-core form
 constexpr int kATile = 128;      // observables per gradient partial row
+// Split phase tiles: one 128 x 256 FP32 partial accumulator per (part, CTA),
+// for at most kMaxSplitCtas CTAs, then one int counter per (tile, CTA).
+constexpr int64_t kSplitSlotFloats = 128 * 256;
+constexpr int kMaxSplitCtas = 160;
 
 __host__ __device__ inline int64_t cdiv(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ inline int64_t round_up(int64_t a, int64_t b) { return cdiv(a, b) * b; }
@@ -38,6 +42,7 @@ struct Plan {
     size_t off_ab, off_s12, off_T, off_terms, off_zt, off_sup, total;
     // low-order form: C (+ d), M = C S, V, H, single-gate partials; ldc floats per row of C and H
     size_t off_lo_c, off_lo_m, off_lo_v, off_lo_h, off_lo_gs, off_lo_a;
+    size_t off_skp;  // split BF16: partial accumulators and counters of split phase tiles (0 if none)
     int64_t ldc;
     bool indep;     // one sample batch per observable (Z has l * s rows)
     const uint64_t *G;  // generators (read by the independent-batch kernels)

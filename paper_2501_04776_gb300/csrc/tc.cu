@@ -128,16 +128,48 @@ struct TcArgs {
     void *out;             // mode 3: the accumulator stored as is (FP32, or FP64 if out_f64)
     int64_t ldo;
     int out_f64;
+    // Work units of this launch: the tiles, whole (nunits tiles); or, for a
+    // split launch, nunits parts of the tiles from `whole` on, nsplit parts
+    // per tile (phase modes only).
+    int64_t nunits, whole;
+    int nsplit;
+    float *skp;            // split parts' partial accumulators, TM x TN FP32 per (part, CTA of the pair)
+    int *skc;              // per (split tile, CTA of the pair): parts finished so far
     uint32_t *status;
     uint64_t limit_ns;
 };
 
 struct Bars {
     uint64_t bits_full[NBITS], bits_empty[NBITS], op_full[kMaxOp], op_empty[kMaxOp], w_full[kMaxOp],
-        peer_full[kMaxOp], acc_full, drain, red_full;
+        peer_full[kMaxOp], acc_full, drain, red_full, part_done, part_flag;
     uint32_t tmem_slot;
     int abort_flag;
+    int last_flag;  // this CTA finished the last part of a split tile
 };
+
+// Work unit u -> its tile, its operand-stage range [ks0, ks1) and, for a
+// part of a split tile, its slot v (-1 for a whole tile). SPL = false: the
+// units are the tiles, whole. SPL = true: unit u is part u % nsplit of tile
+// whole + u / nsplit; the parts cover the tile's stages in ranges of whole
+// bits stages (KB / KS operand stages), in order.
+template <bool SPL>
+__device__ __forceinline__ void unit_of(int64_t u, const TcArgs &a, int nks, int64_t &tile, int &ks0, int &ks1,
+                                        int64_t &v) {
+    if (!SPL) {
+        tile = u;
+        ks0 = 0;
+        ks1 = nks;
+        v = -1;
+        return;
+    }
+    v = u;
+    tile = a.whole + v / a.nsplit;
+    const int64_t part = v % a.nsplit;
+    const int64_t nkb = (nks + KB / KS - 1) / (KB / KS);
+    ks0 = (KB / KS) * (int)(part * nkb / a.nsplit);
+    const int e = (KB / KS) * (int)((part + 1) * nkb / a.nsplit);
+    ks1 = e < nks ? e : nks;
+}
 
 __device__ __forceinline__ uint8_t *aligned_smem(uint8_t *raw) {
     const uint32_t a = smem_u32(raw);
@@ -271,6 +303,43 @@ __device__ __forceinline__ void store_out32(const TcArgs &args, int64_t row, int
     }
 }
 
+// Split phase tiles (kept out of line, so that their registers do not weigh
+// on the stage loop). split_store: this warp's 32 rows x 64 columns of the
+// accumulator (+ running sum) into its part's slot. split_sum: the sum of
+// the tile's nsplit parts, in part order, into the accumulator columns.
+__device__ __noinline__ void split_store(float *dst, uint32_t tbase, bool chunked) {
+    uint32_t r[32];
+#pragma unroll 1
+    for (int c = 0; c < kGroupLoads; ++c) {
+        load_sum32(tbase + c * 32, chunked, r);
+#pragma unroll
+        for (int e = 0; e < 32; e += 4)
+            *reinterpret_cast<float4 *>(dst + c * 32 + e) = make_float4(
+                __uint_as_float(r[e]), __uint_as_float(r[e + 1]), __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3]));
+    }
+}
+
+__device__ __noinline__ void split_sum(const float *src0, int64_t part_stride, int nsplit, uint32_t tbase) {
+#pragma unroll 1
+    for (int c = 0; c < kGroupLoads; ++c) {
+        uint32_t r[32];
+#pragma unroll
+        for (int e = 0; e < 32; ++e) r[e] = 0u;  // +0.0f
+        for (int pp = 0; pp < nsplit; ++pp) {
+            const float *src = src0 + pp * part_stride + c * 32;
+#pragma unroll
+            for (int e = 0; e < 32; e += 4) {
+                const float4 x = __ldcg(reinterpret_cast<const float4 *>(src + e));
+                r[e] = __float_as_uint(__uint_as_float(r[e]) + x.x);
+                r[e + 1] = __float_as_uint(__uint_as_float(r[e + 1]) + x.y);
+                r[e + 2] = __float_as_uint(__uint_as_float(r[e + 2]) + x.z);
+                r[e + 3] = __float_as_uint(__uint_as_float(r[e + 3]) + x.w);
+            }
+        }
+        tmem_st32(tbase + c * 32, r);
+    }
+}
+
 // GRAD = false: phase contraction (MODE 0 stats / MODE 1 W / MODE 2 both),
 //              or (MODE 3) a dense contraction whose accumulator is stored.
 // GRAD = true : gradient contraction.
@@ -281,7 +350,7 @@ __device__ __forceinline__ void store_out32(const TcArgs &args, int64_t row, int
 // MC = 2 (gradient with CG = 1): clusters of two CTAs on the same 128
 // observables and adjacent 256-gate columns; each loads half of every W tile
 // and multicasts it to both, halving W's L2-to-SM traffic.
-template <bool GRAD, int MODE, int CG, int MC, bool AT>
+template <bool GRAD, int MODE, int CG, int MC, bool AT, bool SPL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
          const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
@@ -317,6 +386,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         mbar_init(&bar->acc_full, 1);
         mbar_init(&bar->drain, 1);
         mbar_init(&bar->red_full, NGEN);
+        mbar_init(&bar->part_done, NGEN);
+        mbar_init(&bar->part_flag, 1);
+        bar->last_flag = 0;
         bar->abort_flag = 0;
         fence_barrier_init();
         fence_proxy_async_smem();
@@ -339,9 +411,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     // Tiles per cluster iteration: with MC = 2 a cluster takes two adjacent
     // column tiles of one row block.
     const int64_t tiles_nc = MC == 2 ? (args.tiles_n + 1) / 2 : args.tiles_n;
-    const int64_t ntiles = args.tiles_m * tiles_nc;
+    const int64_t nunits = args.nunits;
     const int nks = (int)args.nks;     // host guarantees nks < 2^31
-    const int nkb = (nks + KB / KS - 1) / (KB / KS);
     const int chunk = (int)args.chunk;
 
     if (warp == 0) {
@@ -353,7 +424,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t itb = 0, ito = 0;
             uint32_t bmask = 0, bpar = 0, omask = 0, opar = 0;  // issued stages and their last parities
             bool ok = true;
-            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+            for (int64_t u = group0; u < nunits && ok; u += ngroups) {
+                int64_t t, uv;
+                int ks0, ks1;
+                unit_of<SPL>(u, args, nks, t, ks0, ks1, uv);
                 int64_t tm64, tc64;
                 tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm64, tc64);
                 const int tm = (int)tm64;
@@ -361,7 +435,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int prank = CG == 2 ? (int)crank : 0;        // rank within an MMA pair
                 const int a0 = tm * TM * CG + prank * TM;          // this CTA's first A row
                 const int b0 = tn * TN + prank * C::TNB;           // this CTA's first B row
-                for (int kb = 0; kb < nkb && ok; ++kb, ++itb) {
+                for (int kb = ks0 / (KB / KS); kb < (ks1 + KB / KS - 1) / (KB / KS) && ok; ++kb, ++itb) {
                     const uint32_t bs = itb % NBITS;
                     if (!mbar_wait(&bar->bits_empty[bs], ((itb / NBITS) & 1u) ^ 1u, abort_flag, status, lim)) {
                         ok = false;
@@ -385,7 +459,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         // A_hi / A_lo tiles (W, or a dense operand) of the operand stages of this bits stage.
                         for (int q = 0; q < KB / KS; ++q) {
                             const int ks = kb * (KB / KS) + q;
-                            if (ks >= nks) break;
+                            if (ks >= ks1) break;
                             const uint32_t os = ito % NOP;
                             if (!mbar_wait(&bar->op_empty[os], ((ito / NOP) & 1u) ^ 1u, abort_flag, status, lim)) {
                                 ok = false;
@@ -430,9 +504,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0 && leader) {
             uint32_t ito = 0;
             bool ok = true;
-            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+            for (int64_t u = group0; u < nunits && ok; u += ngroups) {
+                int64_t t, uv;
+                int ks0, ks1;
+                unit_of<SPL>(u, args, nks, t, ks0, ks1, uv);
                 int kc = 0;  // stage index within the current accumulation chunk
-                for (int ks = 0; ks < nks; ++ks, ++ito) {
+                for (int ks = ks0; ks < ks1; ++ks, ++ito) {
                     const uint32_t os = ito % NOP;
                     // One-CTA gradient: this thread also waits for the stage's W
                     // tiles (a pair's W halves are vouched for by its producers).
@@ -464,7 +541,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (CG == 2) umma_commit_pair(&bar->op_empty[os]);
                     else if (MC == 2) umma_commit_multicast(&bar->op_empty[os], (uint16_t)3);
                     else umma_commit(&bar->op_empty[os]);
-                    if (++kc == chunk || ks == nks - 1) {
+                    if (++kc == chunk || ks == ks1 - 1) {
                         if (CG == 2) umma_commit_pair(&bar->acc_full);
                         else umma_commit(&bar->acc_full);
                         kc = 0;
@@ -483,8 +560,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t op_full_remote = mapa_shared(smem_u32(&bar->op_full[0]), 0u);
             uint32_t ito = 0;
             bool ok = true;
-            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
-                for (int ks = 0; ks < nks; ++ks, ++ito) {
+            for (int64_t u = group0; u < nunits && ok; u += ngroups) {
+                int64_t t, uv;
+                int ks0, ks1;
+                unit_of<SPL>(u, args, nks, t, ks0, ks1, uv);
+                for (int ks = ks0; ks < ks1; ++ks, ++ito) {
                     const uint32_t os = ito % NOP;
                     if (!mbar_wait(&bar->peer_full[os], (ito / NOP) & 1u, abort_flag, status, lim)) {
                         ok = false;
@@ -501,15 +581,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int group = (warp - 2) >> 2; // accumulator column group of the epilogue
         uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
         bool ok = true;
-        for (int64_t t = group0; t < ntiles && ok; t += ngroups, ++tcount) {
+        for (int64_t u = group0; u < nunits && ok; u += ngroups, ++tcount) {
+            int ks0, ks1;
             int64_t tm, tc;
-            tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm, tc);
+            {
+                int64_t t, uv0;
+                unit_of<SPL>(u, args, nks, t, ks0, ks1, uv0);
+                tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm, tc);
+            }
             const int64_t tn = MC == 2 ? 2 * tc + crank : tc;
             const int64_t arow0 = tm * TM * CG + (CG == 2 ? (int64_t)crank * TM : 0);  // first observable here
             int kc = 0;              // stage index within the current chunk
             int nchunk = 0;          // chunks of this tile already folded into the running sum
             bool fold_due = false;   // a finished chunk must be folded before the next release
-            for (int ks = 0; ks < nks; ++ks) {
+            for (int ks = ks0; ks < ks1; ++ks) {
                 const int q = ks & 3;
                 const uint32_t bs = itb % NBITS;
                 if (q == 0 && !wait_warp(&bar->bits_full[bs], (itb / NBITS) & 1u, abort_flag, status, lim)) {
@@ -570,13 +655,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     else mbar_arrive(&bar->op_full[os]);
                 }
                 ++ito;
-                if (q == 3 || ks == nks - 1) {
+                if (q == 3 || ks == ks1 - 1) {
                     if (lane == 0) mbar_arrive(&bar->bits_empty[bs]);
                     ++itb;
                 }
                 if (++kc == chunk) {
                     kc = 0;
-                    fold_due = ks != nks - 1;
+                    fold_due = ks != ks1 - 1;
                 }
             }
             if (!ok) break;
@@ -590,7 +675,45 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int64_t row = arow0 + quarter * 32 + lane;  // observable a
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(group * kGroupCols);
-            const bool chunked = nchunk > 0;
+            bool chunked = nchunk > 0;
+            if (!GRAD && MODE != 3 && SPL) {
+                const int64_t uv = u;  // this part's slot
+                // A part of a split tile: store this part's accumulator; the
+                // CTA that finishes the tile's last part sums every part's,
+                // in part order, back into TMEM and runs the epilogue.
+                const int64_t half = CG == 2 ? (int64_t)crank : 0;
+                const int rl = quarter * 32 + lane;  // accumulator row in this CTA
+                split_store(args.skp + ((uv * CG + half) * TM + rl) * TN + group * kGroupCols, tbase, chunked);
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bar->part_done);
+                const int64_t tt = uv / args.nsplit;  // index among the split tiles
+                const uint32_t nsu = tcount;          // split parts this CTA finished before
+                if (warp == 2 && lane == 0) {
+                    if (mbar_wait(&bar->part_done, nsu & 1u, abort_flag, status, lim)) {
+                        int *cnt = args.skc + tt * CG + half;
+                        const int last = atomicAdd(cnt, 1) == args.nsplit - 1;
+                        if (last) {
+                            atomicExch(cnt, 0);  // ready for the next launch
+                            __threadfence();
+                        }
+                        bar->last_flag = last;
+                    }
+                    mbar_arrive(&bar->part_flag);
+                }
+                if (!wait_warp(&bar->part_flag, nsu & 1u, abort_flag, status, lim) || *abort_flag) {
+                    ok = false;
+                    break;
+                }
+                if (*reinterpret_cast<volatile int *>(&bar->last_flag) == 0) {
+                    tc_fence_before();
+                    continue;  // another CTA finishes this tile
+                }
+                __threadfence();
+                split_sum(args.skp + ((tt * args.nsplit * CG + half) * TM + rl) * TN + group * kGroupCols,
+                          (int64_t)CG * TM * TN, args.nsplit, tbase);
+                chunked = false;  // the sum of the parts is in the accumulator columns
+            }
             // Phi (or Q) for 32 columns: last chunk's accumulator + running sum.
             if (!GRAD && MODE == 0) {
                 const int64_t c0 = tn * TN + group * kGroupCols;  // first sample of this group
@@ -785,29 +908,28 @@ bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool GRAD, int MODE, int CG, int MC = 1, bool AT = GRAD>
+template <bool GRAD, int MODE, int CG, int MC = 1, bool AT = GRAD, bool SPL = false>
 cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
                      cudaStream_t st) {
     using C = Cfg<CG, GRAD || AT>;
     constexpr int CL = CG * MC;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, MC, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, MC, AT, SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int64_t ntiles = args.tiles_m * (MC == 2 ? (args.tiles_n + 1) / 2 : args.tiles_n);
     int sms = num_sms();
     if (sms < CL) sms = CL;
-    const int64_t groups = ntiles < sms / CL ? ntiles : sms / CL;
+    const int64_t groups = args.nunits < sms / CL ? args.nunits : sms / CL;
     LaunchScope ls(GRAD          ? IQP_KERNEL_GRAD_TC
                    : MODE == 1 ? IQP_KERNEL_RECOMPUTE_TC
                    : MODE == 3 ? IQP_KERNEL_LOWORDER_GEMM
                                : IQP_KERNEL_PHASE_TC,
                    st);
     if (CL == 1) {
-        k_tc<GRAD, MODE, 1, 1, AT><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
+        k_tc<GRAD, MODE, 1, 1, AT, SPL><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -822,7 +944,7 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, MC, AT>, a, a2, b, args);
+    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, MC, AT, SPL>, a, a2, b, args);
 }
 
 // Gradient kernel form: single-CTA MMAs; with IQP_GRAD_MULTICAST=1, clusters
@@ -850,6 +972,17 @@ int64_t tile_group() {
     return g;
 }
 
+// Split the last round of phase tiles across idle CTA groups unless
+// IQP_SPLIT_TAIL=0.
+bool split_tail() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("IQP_SPLIT_TAIL");
+        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 int cta_group() {
     static int cg = -1;
     if (cg < 0) {
@@ -859,11 +992,34 @@ int cta_group() {
     return cg;
 }
 
+// Every tile whole (no split parts).
+void whole_tiles(TcArgs &a, int64_t ntiles) {
+    a.nunits = a.whole = ntiles;
+    a.nsplit = 1;
+    a.skp = nullptr;
+    a.skc = nullptr;
+}
+
 template <class T>
 T *at(void *ws, size_t off) {
     return reinterpret_cast<T *>(static_cast<char *>(ws) + off);
 }
 
+}  // namespace
+
+namespace {
+template <bool SPL>
+cudaError_t launch_phase_k(int mode, int cg, const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a,
+                           cudaStream_t st) {
+    if (cg == 2) {
+        if (mode == 0) return launch_k<false, 0, 2, 1, false, SPL>(ma, ma, mb, a, st);
+        if (mode == 1) return launch_k<false, 1, 2, 1, false, SPL>(ma, ma, mb, a, st);
+        return launch_k<false, 2, 2, 1, false, SPL>(ma, ma, mb, a, st);
+    }
+    if (mode == 0) return launch_k<false, 0, 1, 1, false, SPL>(ma, ma, mb, a, st);
+    if (mode == 1) return launch_k<false, 1, 1, 1, false, SPL>(ma, ma, mb, a, st);
+    return launch_k<false, 2, 1, 1, false, SPL>(ma, ma, mb, a, st);
+}
 }  // namespace
 
 cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alpha, const double *beta,
@@ -903,14 +1059,39 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.out_f64 = 0;
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
-    if (cg == 2) {
-        if (mode == 0) return launch_k<false, 0, 2>(ma, ma, mb, a, st);
-        if (mode == 1) return launch_k<false, 1, 2>(ma, ma, mb, a, st);
-        return launch_k<false, 2, 2>(ma, ma, mb, a, st);
+    // A last round of tiles that would leave CTA groups idle is split along
+    // the gates across them: the whole tiles run first (full rounds), then a
+    // second launch runs the remaining tiles' parts, each a range of whole
+    // bits stages, and the last part of a tile to finish sums the parts (in
+    // part order) and runs the epilogue.
+    const int64_t T = a.tiles_m * a.tiles_n;
+    whole_tiles(a, T);
+    int64_t R = 0, ns = 1;
+    if (split_tail() && p.off_skp != 0) {
+        int sms = num_sms();
+        if (sms > kMaxSplitCtas) sms = kMaxSplitCtas;
+        const int64_t P = sms / cg;  // CTA groups
+        R = T >= P ? T % P : T;
+        ns = (P >= 2 && R > 0) ? P / R : 1;
+        const int64_t nkb = cdiv(a.nks, KB / KS);
+        if (ns > nkb) ns = nkb;
+        if (ns < 2) R = 0;
     }
-    if (mode == 0) return launch_k<false, 0, 1>(ma, ma, mb, a, st);
-    if (mode == 1) return launch_k<false, 1, 1>(ma, ma, mb, a, st);
-    return launch_k<false, 2, 1>(ma, ma, mb, a, st);
+    if (R == 0) return launch_phase_k<false>(mode, cg, ma, mb, a, st);
+    if (T - R > 0) {
+        TcArgs w = a;
+        whole_tiles(w, T - R);
+        const cudaError_t e = launch_phase_k<false>(mode, cg, ma, mb, w, st);
+        if (e != cudaSuccess) return e;
+    }
+    a.whole = T - R;
+    a.nsplit = (int)ns;
+    a.nunits = R * ns;
+    a.skp = at<float>(ws, p.off_skp);
+    a.skc = reinterpret_cast<int *>(a.skp + (int64_t)kMaxSplitCtas * kSplitSlotFloats);
+    const cudaError_t e = cudaMemsetAsync(a.skc, 0, (size_t)(R * cg) * sizeof(int), st);
+    if (e != cudaSuccess) return e;
+    return launch_phase_k<true>(mode, cg, ma, mb, a, st);
 }
 
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why) {
@@ -950,6 +1131,7 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.out = nullptr;
     a.ldo = 0;
     a.out_f64 = 0;
+    whole_tiles(a, a.tiles_m * (mc ? (a.tiles_n + 1) / 2 : a.tiles_n));
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
     if (mc) return launch_k<true, 0, 1, 2>(mhi, mlo, mb, a, st);
@@ -990,6 +1172,7 @@ cudaError_t launch_tc_dense(const __nv_bfloat16 *a_hi, const __nv_bfloat16 *a_lo
     a.out = out;
     a.ldo = ldo;
     a.out_f64 = out_f64 ? 1 : 0;
+    whole_tiles(a, a.tiles_m * a.tiles_n);
     a.status = status;
     a.limit_ns = default_spin_limit_ns();
     if (cg == 2) return launch_k<false, 3, 2, 1, true>(mhi, mlo, mb, a, st);
