@@ -91,7 +91,11 @@ typedef enum {
 #define IQP_MMD_INDEP 4    /* one batch per observable: Z has l * s rows (indep_estimates) */
 
 /* Bytes of device scratch `ws` needed by `op` for these sizes (N is ignored
- * except for the MMD ops). Returns 0 for invalid sizes. Host only. */
+ * except for the MMD ops). Returns 0 for invalid sizes. Host only.
+ * With IQP_SPLIT_BF16 the last 20.5 MB of it (160 x 128 KiB plus 640 bytes)
+ * are optional: they let a last round of phase tiles that would leave SMs
+ * idle be split along the gates across them. A `ws_bytes` short of the full
+ * size by at most that much runs every phase tile whole instead. */
 size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N,
                            iqp_precision prec);
 
@@ -145,8 +149,9 @@ iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
  * minus `ws`. Scratch is one file-scope device array of 64 MiB inside this
  * library, reserved on every GPU that loads the library and held until the
  * process exits; this call allocates nothing. Sizes whose
- * iqp_workspace_bytes(IQP_OP_EXPVAL, ...) exceeds 64 MiB are rejected with
- * IQP_ERR_WORKSPACE before any launch. The first call on a device looks up
+ * iqp_workspace_bytes(IQP_OP_EXPVAL, ...), less its optional part (see
+ * there), exceeds 64 MiB are rejected with IQP_ERR_WORKSPACE before any
+ * launch. The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture. All calls share the one
  * array: calls that overlap on the GPU (other streams, other host threads)

@@ -132,11 +132,6 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_lo_h = take(lo && grad ? n * p.ldc * 8 : 0);
     p.off_lo_gs = take(lo && grad ? n * cdiv(s, lo_part_samples()) * 8 : 0);
     p.off_lo_a = take(lo ? lo_split_elems(n, p.ldw) * 2 : 0);  // split-BF16 operand of the pair contractions
-    p.off_skp = 0;
-    const size_t skp = take(prec == IQP_SPLIT_BF16 && !bitflip && !indep
-                                ? (int64_t)kMaxSplitCtas * kSplitSlotFloats * 4 + (int64_t)kMaxSplitCtas * 4
-                                : 0);
-    if (prec == IQP_SPLIT_BF16 && !bitflip && !indep) p.off_skp = skp;
     // sparse: 64-bit fixed-point gradient accumulators and their scale
     p.off_gpart = take(grad ? (sparse ? m * 8 + 8 : (lo ? n * n * 8 + 8 : p.natile * m * 8)) : 0);
     p.off_ab = take(mmd ? l * 16 : 0);
@@ -145,8 +140,27 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_terms = take(mmd ? l * 8 : 0);
     p.off_zt = take(indep ? l * n * p.ldzt * 8 : 0);  // every batch transposed: n rows of bits over samples
     p.off_sup = take(indep || lo ? m * 16 : 0);       // int4 support list per gate
+    // Last, and optional: the split-tile scratch of the tensor-core phase (a
+    // workspace that ends before it runs every phase tile whole).
+    p.off_skp = 0;
+    if (prec == IQP_SPLIT_BF16 && !bitflip && !indep)
+        p.off_skp = take((int64_t)kMaxSplitCtas * kSplitSlotFloats * 4 + (int64_t)kMaxSplitCtas * 4);
     p.total = off;
     return p;
+}
+
+// Bytes of the workspace below which `p` cannot run (the optional split-tile
+// scratch at its end left out).
+size_t plan_min_bytes(const Plan &p) { return p.off_skp != 0 ? p.off_skp : p.total; }
+
+// The smallest workspace `op` runs with (iqp_workspace_bytes less the
+// optional split-tile scratch at its end); 0 for invalid arguments (the
+// checks of iqp_workspace_bytes).
+size_t workspace_min_bytes(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec) {
+    if (n < 1 || m < 1 || l < 1 || s < 1) return 0;
+    if (op < IQP_OP_EXPVAL || op > IQP_OP_MMD_LOSS_GRAD_INDEP) return 0;
+    if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32 && prec != IQP_LOWORDER_FP32) return 0;
+    return plan_min_bytes(make_plan(op, n, m, l, s, N, prec));
 }
 
 // ---------------------------------------------------------------- misc
@@ -246,9 +260,12 @@ iqp_status check_common(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, co
     return IQP_OK;
 }
 
-iqp_status check_ws(const Plan &p, void *ws, size_t ws_bytes) {
+iqp_status check_ws(Plan &p, void *ws, size_t ws_bytes) {
     if (ws == nullptr || !aligned(ws, 256)) return IQP_ERR_WORKSPACE;
-    if (ws_bytes < p.total) return IQP_ERR_WORKSPACE;
+    if (ws_bytes < p.total) {
+        if (ws_bytes < plan_min_bytes(p)) return IQP_ERR_WORKSPACE;
+        p.off_skp = 0;  // no room for the split-tile scratch: phase tiles run whole
+    }
     return IQP_OK;
 }
 
@@ -422,6 +439,7 @@ size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s
     if (prec != IQP_FP32 && prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32 && prec != IQP_LOWORDER_FP32) return 0;
     return make_plan(op, n, m, l, s, N, prec).total;
 }
+
 
 iqp_status iqp_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G, int64_t m,
                       int64_t ldg, uint64_t *P, int64_t ldp, void *stream) {
@@ -638,7 +656,7 @@ iqp_status bitflip_core(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, co
     if (theta == nullptr) return IQP_ERR_ARG;
     if (!aligned(theta, 4)) return IQP_ERR_ALIGN;
     if ((expval && !aligned(expval, 8)) || (w && !aligned(w, 8)) || (grad && !aligned(grad, 8))) return IQP_ERR_ALIGN;
-    const Plan p = make_plan(IQP_OP_BITFLIP, n, m, l, 1, 0, IQP_FP32);
+    Plan p = make_plan(IQP_OP_BITFLIP, n, m, l, 1, 0, IQP_FP32);
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     IQP_TRY(launch_parity_gather(n, A, l, lda, G, m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,

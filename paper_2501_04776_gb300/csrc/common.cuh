@@ -60,6 +60,9 @@ struct SparseIndep {
 };
 
 Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec);
+// The smallest workspace an op runs with (without the optional split-tile
+// scratch at the end of its plan); 0 for invalid arguments.
+size_t workspace_min_bytes(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec);
 
 // Dense contraction on the tensor cores (split BF16, FP32 accumulation):
 //   out[r][c] = sum_{k < K} (a_hi[r][k] + a_lo[r][k]) (1 - 2 bit k of b row c)

@@ -49,8 +49,10 @@ extern "C" iqp_status iqp_expval_noalloc(int64_t n, const uint64_t *G, int64_t m
                                          int64_t l, int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz,
                                          const float *theta, iqp_precision prec, double *expval, double *std_err,
                                          void *stream) {
-    const size_t need = iqp_workspace_bytes(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
-    if (need > iqp::kNoAllocBytes) return IQP_ERR_WORKSPACE;
+    // The array must hold the op's workspace; the optional split-tile scratch
+    // at its end is used only when it fits as well.
+    const size_t need = iqp::workspace_min_bytes(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
+    if (need == 0 || need > iqp::kNoAllocBytes) return IQP_ERR_WORKSPACE;
     void *ws = nullptr;
     const iqp_status rc = iqp::noalloc_scratch(&ws);
     if (rc != IQP_OK) return rc;

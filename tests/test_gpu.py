@@ -328,21 +328,45 @@ def test_bounded_wait_times_out_and_context_survives(api):
     assert api.read_status() == _lib.OK
 
 
-def test_workspace_too_small_is_rejected(api):
+def test_workspace_too_small_is_rejected_and_the_split_scratch_is_optional(api):
     import torch
     from paper_2501_04776_gb300 import _lib
     lib = _lib.load()
-    p = I.tiny_local(seed=3, s=64)
+    # 1000 gates (16 operand stages: a tile can split into 4 gate ranges),
+    # 2 x 3 pair tiles, all of them in the last round
+    rng = I.Rng(13)
+    n_, m_, l_, s_ = 130, 1000, 260, 520
+    Gb = I.random_k_body(rng, m_, n_, [1, 2, 3], 1)
+    p = I.Problem("ragged-n130-m1000-l260-s520", n_, Gb, I.bernoulli_bits(rng, l_, n_, 0.1, 3),
+                  I.uniform_bits(rng, s_, n_, 4), (0.3 * rng.normal(m_, 2)).astype(np.float32))
     G, A, Z = dev(api, p.G), dev(api, p.A), dev(api, p.Z)
     th = th_dev(p.theta)
     need = lib.iqp_workspace_bytes(_lib.OP_EXPVAL, p.n, p.m, p.l, p.s, 0, _lib.SPLIT_BF16)
     ws = torch.zeros(need, dtype=torch.uint8, device="cuda")
     out = torch.zeros(p.l, dtype=torch.float64, device="cuda")
     P = ctypes.c_void_p
-    rc = lib.iqp_expval(p.n, P(G.data_ptr()), p.m, G.shape[1], P(A.data_ptr()), p.l, A.shape[1], P(Z.data_ptr()),
-                        p.s, Z.shape[1], P(th.data_ptr()), _lib.SPLIT_BF16, P(out.data_ptr()), None,
-                        P(ws.data_ptr()), need - 256, None)
-    assert rc == _lib.ERR_WORKSPACE
+    # The split-tile scratch at the end of the split-BF16 workspace (160
+    # partial accumulators of 128 x 256 FP32 and 160 counters, rounded to
+    # 256 bytes) is optional; anything shorter than the rest is rejected.
+    optional = -(-(160 * 128 * 256 * 4 + 160 * 4) // 256) * 256
+
+    def call(nbytes, res):
+        return lib.iqp_expval(p.n, P(G.data_ptr()), p.m, G.shape[1], P(A.data_ptr()), p.l, A.shape[1],
+                              P(Z.data_ptr()), p.s, Z.shape[1], P(th.data_ptr()), _lib.SPLIT_BF16,
+                              P(res.data_ptr()), None, P(ws.data_ptr()), nbytes, None)
+
+    assert call(need - optional - 256, out) == _lib.ERR_WORKSPACE
+    # Without the optional part every phase tile runs whole (with it, this
+    # problem runs as split parts only): the same estimates within the
+    # split-BF16 tolerance.
+    full = torch.zeros(p.l, dtype=torch.float64, device="cuda")
+    assert call(need, full) == _lib.OK
+    assert call(need - optional, out) == _lib.OK
+    torch.cuda.synchronize()
+    assert api.read_status() == _lib.OK
+    want, _, _, _ = oracle.expval(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64))
+    assert np.max(np.abs(out.cpu().numpy() - want)) <= TOL["split_bf16"]
+    assert np.max(np.abs(full.cpu().numpy() - want)) <= TOL["split_bf16"]
 
 
 def test_launch_counter_counts_kernels(api):
