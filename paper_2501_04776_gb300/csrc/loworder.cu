@@ -346,7 +346,8 @@ struct LoShared {
 
 // Sample blocks handled by one CTA: the support and, when it fits, the
 // pair list are built once and reused for every block.
-constexpr int kGroup = 8;
+constexpr int kGroup = 8;    // sample blocks per CTA of k_lo_v (its per-block sums live in registers)
+constexpr int kPGroup = 16;  // sample blocks per CTA of k_lo_phase and k_lo_pairs (support and pair list built once)
 constexpr int kObsMax = 4096;  // observables of one qubit listed per pass in k_lo_v
 
 // The sample bits of block blk for every support qubit.
@@ -431,7 +432,7 @@ __device__ __forceinline__ float block_sum_f(float v, float *red) {
 // part. MODE 1: W[a][i] = sin Phi (alpha_a + beta_a cos Phi), zero for i >= s.
 // One thread per sample; the pair term visits only the pairs of Q_a that
 // carry a generator (C_qr is zero on the others). CTA (a, g) takes sample
-// blocks kGroup g .. kGroup g + kGroup - 1.
+// blocks kPGroup g .. kPGroup g + kPGroup - 1.
 template <int MODE>
 __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
                                                    const uint64_t *__restrict__ ZT, int64_t ldzt,
@@ -452,8 +453,8 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
     const bool complete = c0 >= ncand;  // the whole list fits: reuse it for every block
     const float al = MODE == 1 ? (float)alpha[a] : 0.f;
     const float be = (MODE == 1 && beta) ? (float)beta[a] : 0.f;
-    const int64_t b1 = (blockIdx.y + 1) * (int64_t)kGroup < nparts ? (blockIdx.y + 1) * (int64_t)kGroup : nparts;
-    for (int64_t blk = blockIdx.y * (int64_t)kGroup; blk < b1; ++blk) {
+    const int64_t b1 = (blockIdx.y + 1) * (int64_t)kPGroup < nparts ? (blockIdx.y + 1) * (int64_t)kPGroup : nparts;
+    for (int64_t blk = blockIdx.y * (int64_t)kPGroup; blk < b1; ++blk) {
         lo_load_bits(sh, nq, n, ZT, ldzt, blk, status);
         const int64_t i = blk * kBlk + tid;
         const bool valid = i < s;
@@ -466,7 +467,7 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
             phi += ((sh.bits[t][w] >> bit) & 1u) ? -v : v;
         }
         float pairs = 0.f;
-        if (!complete && blk != blockIdx.y * (int64_t)kGroup) {
+        if (!complete && blk != blockIdx.y * (int64_t)kPGroup) {
             c0 = 0;  // the list is rebuilt round by round for every block
             np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
         }
@@ -587,7 +588,7 @@ __device__ __forceinline__ long long to_fixed(float x, float sc) {
 // q < r of Q_a that carry a generator (the only K entries the gradient
 // reads); one warp per pair, 8 samples per lane and block, summed over the
 // CTA's blocks in shared memory, one fixed-point atomic per (pair, CTA).
-// CTA (a, g) takes blocks kGroup g ...
+// CTA (a, g) takes blocks kPGroup g ...
 __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
                                                    const uint64_t *__restrict__ ZT, int64_t ldzt,
                                                    const float *__restrict__ C, int64_t ldc,
@@ -604,8 +605,8 @@ __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float sc = (float)*scale;
     const int64_t ncand = (int64_t)nq * nq;
-    const int64_t b0 = blockIdx.y * (int64_t)kGroup;
-    const int64_t b1 = b0 + kGroup < nblk ? b0 + kGroup : nblk;
+    const int64_t b0 = blockIdx.y * (int64_t)kPGroup;
+    const int64_t b1 = b0 + kPGroup < nblk ? b0 + kPGroup : nblk;
     int64_t c0 = 0;
     while (c0 < ncand) {
         const int np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
@@ -749,7 +750,7 @@ cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l
     LaunchScope ls(IQP_KERNEL_LOWORDER, st);
     const float *d = C + n * ldc;
     const unsigned long long *E = reinterpret_cast<const unsigned long long *>(d + ldc);
-    k_lo_phase<0><<<dim3((unsigned)l, (unsigned)cdiv(nparts, kGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d, E,
+    k_lo_phase<0><<<dim3((unsigned)l, (unsigned)cdiv(nparts, kPGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d, E,
                                                                        lo_lde(n), s, nparts, part, nullptr, nullptr,
                                                                        nullptr, status);
     return cudaGetLastError();
@@ -773,7 +774,7 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
     if ((e = launch_fixed_scale(alpha, beta, l, s, scale, st)) != cudaSuccess) return e;
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_phase<1><<<dim3((unsigned)l, (unsigned)cdiv(nblk, kGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d,
+        k_lo_phase<1><<<dim3((unsigned)l, (unsigned)cdiv(nblk, kPGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d,
                                                                          E, lde, s, nblk, nullptr, alpha, beta, W,
                                                                          status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -800,7 +801,7 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
     }
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_pairs<<<dim3((unsigned)l, (unsigned)cdiv(nblk, kGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, C, ldc, E,
+        k_lo_pairs<<<dim3((unsigned)l, (unsigned)cdiv(nblk, kPGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, C, ldc, E,
                                                                                      lde, W, lds, s, nblk, scale, Kfx,
                                                                                      status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
