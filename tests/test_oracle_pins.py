@@ -4,8 +4,10 @@ expval_bitflip when no subset of J_a XORs to zero), three independent exact
 evaluations (enumeration of eq. op_expval, a statevector built from the gate
 action of Sec. 2.5, the subset expansion of eq. expval_intefere), the MC error
 bound, a hand-derived standard error, central finite differences, numpy
-brute force for GF(2) products, pair-mean U-statistics and the kernel form of
-MMD^2 (eq. mmd_loss) against its observable form (eq. mmd_estimate).
+brute force for GF(2) products, pair-mean U-statistics, the kernel form of
+MMD^2 (eq. mmd_loss) against its observable form (eq. mmd_estimate), and the
+per-qubit/per-pair regrouping of the phase and its gradient for generators of
+weight <= 2.
 
 All CPU; no GPU, no CUDA extension.
 """
@@ -596,3 +598,86 @@ def test_mmd_indep_with_repeated_batch_equals_shared_batch():
                                         grad=True)
         assert abs(L0 - L1) < 1e-14 and np.max(np.abs(t0 - t1)) < 1e-14
         assert np.max(np.abs(g0 - g1)) < 1e-12
+
+
+# ------------------------------------------------------------ low-order regrouping
+
+def _low_order_problem(seed, n=11, m=70, l=23, s=97):
+    """Random one- and two-body generators in random order, with repeated
+    supports, plus observables and samples."""
+    rng = np.random.default_rng(seed)
+    gates = []
+    for _ in range(m):
+        if rng.random() < 0.3:
+            gates.append([int(rng.integers(n))])
+        else:
+            q, r = sorted(int(x) for x in rng.choice(n, 2, replace=False))
+            gates.append([q, r])
+    gates += gates[:5]  # repeated supports add their angles
+    theta = rng.normal(0.0, 0.4, len(gates))
+    a = (rng.random((l, n)) < 0.4).astype(np.int64)
+    z = rng.integers(0, 2, (s, n))
+    return gates, theta, a, z
+
+
+def _pair_coefficients(gates, theta, n):
+    """d_q = sum of 2 theta over gates on {q}; C_qr = C_rq = sum of 2 theta
+    over gates on {q, r}."""
+    d, C = np.zeros(n), np.zeros((n, n))
+    for g, t in zip(gates, theta):
+        if len(g) == 1:
+            d[g[0]] += 2 * t
+        else:
+            C[g[0], g[1]] += 2 * t
+            C[g[1], g[0]] += 2 * t
+    return d, C
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_low_order_regrouping_of_the_phase(seed):
+    """For generators of weight <= 2 the phase of eq. expvalsample factors per
+    qubit: [g.a odd] s_g = (a_q + a_r - 2 a_q a_r) s_q s_r for g = {q, r}, so
+    Phi(a, z) = sum_{q in a} s_q (d_q + (C s)_q) - 2 sum_{q<r in a} C_qr s_q s_r
+    with s = 1 - 2z. The oracle evaluates the phase gate by gate; the
+    regrouped form here never forms a gate parity."""
+    n = 11
+    gates, theta, a, z = _low_order_problem(seed, n)
+    d, C = _pair_coefficients(gates, theta, n)
+    S = 1 - 2 * z
+    lin = a @ (S * (d + S @ C)).T                        # [l, s]
+    U = a[:, None, :] * S[None, :, :]                    # a_q s_q
+    quad = 0.5 * np.einsum("lsq,qr,lsr->ls", U, C, U)    # sum_{q<r}
+    phi = lin - 2 * quad
+    ev, se, _, _ = oracle.expval(n, I.pack_index_lists(gates, n), I.pack_bits(a),
+                                 I.pack_bits(z), theta)
+    want = np.cos(phi).mean(axis=1)
+    assert np.abs(ev - want).max() < 1e-12
+    sd = np.cos(phi).std(axis=1, ddof=0) / math.sqrt(z.shape[0])
+    assert np.abs(se - sd).max() < 1e-12
+
+
+@pytest.mark.parametrize("seed", [4, 5])
+def test_low_order_regrouping_of_the_gradient(seed):
+    """The gradient of the regrouped phase: with V = sin(Phi)(alpha + beta cos Phi),
+    a one-body gate on q gets 2 sum V a_q s_q and a pair gate on {q, r} gets
+    2 sum V (a_q + a_r - 2 a_q a_r) s_q s_r; gates sharing a support share
+    the value."""
+    n = 11
+    gates, theta, a, z = _low_order_problem(seed, n)
+    rng = np.random.default_rng(seed + 100)
+    alpha, beta = rng.normal(size=a.shape[0]), rng.normal(size=a.shape[0])
+    d, C = _pair_coefficients(gates, theta, n)
+    S = 1 - 2 * z
+    U = a[:, None, :] * S[None, :, :]
+    phi = a @ (S * (d + S @ C)).T - np.einsum("lsq,qr,lsr->ls", U, C, U)
+    V = np.sin(phi) * (alpha[:, None] + beta[:, None] * np.cos(phi))
+    K = a.T @ V                                          # [n, s]: sum_a V a_q
+    M1 = (K * S.T) @ S                                   # sum V a_q s_q s_r
+    Q = np.einsum("ls,lq,lr,sq,sr->qr", V, a, a, S, S)   # sum V a_q a_r s_q s_r
+    M0 = (K * S.T).sum(axis=1)                           # sum V a_q s_q
+    want = np.array([2 * M0[g[0]] if len(g) == 1 else
+                     2 * (M1[g[0], g[1]] + M1[g[1], g[0]] - 2 * Q[g[0], g[1]])
+                     for g in gates])
+    got = oracle.expval_grad(n, I.pack_index_lists(gates, n), I.pack_bits(a),
+                             I.pack_bits(z), theta, alpha, beta)
+    assert np.abs(got - want).max() < 1e-10 * max(1.0, np.abs(want).max())
