@@ -33,6 +33,7 @@ namespace {
 constexpr int kQMax = 1024;  // observable weight limit (support list in shared memory)
 constexpr int kPairMax = 512;  // pairs of Q_a held in shared memory per round
 constexpr int kBlk = 256;    // samples per CTA in the per-observable kernels
+constexpr int kQ4 = 256;     // supports up to this size take four sample blocks per pass in k_lo_phase
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // Optional self-checks (-DIQP_LO_CHECKS): an index out of its buffer records
@@ -336,7 +337,10 @@ __device__ int support_of_row(const uint64_t *__restrict__ arow, int64_t n, int 
 // Shared state of the per-(observable, 256-sample block) kernels.
 struct LoShared {
     int Q[kQMax];              // support of the observable
-    uint32_t bits[kQMax][8];   // bit (i - i0) of word i/32: sample bit of qubit Q[t]
+    union alignas(16) {
+        uint32_t bits[kQMax][8];    // one 256-sample block: bit (i - i0) of word i/32 for qubit Q[t]
+        uint32_t bits4[kQ4][32];    // four blocks at once, for supports of at most kQ4 qubits
+    };
     int pr[kPairMax];          // pairs t | u << 16 (t < u) with a generator on {Q[t], Q[u]}
     float pc[kPairMax];        // C restricted to those pairs
     int scan[kBlk];
@@ -428,11 +432,36 @@ __device__ __forceinline__ float block_sum_f(float v, float *red) {
     return t;
 }
 
+// The sample bits of blocks blk0 .. blk0 + 3 for every support qubit:
+// bits4[t][w] holds samples 32 w .. 32 w + 31 of the 1024.
+__device__ void lo_load_bits4(LoShared &sh, int nq, int64_t n, const uint64_t *__restrict__ ZT, int64_t ldzt,
+                              int64_t blk0, [[maybe_unused]] uint32_t *__restrict__ status_dbg) {
+    __syncthreads();  // previous readers of bits4 are done
+    for (int e = threadIdx.x; e < nq * 16; e += kBlk) {
+        const int t = e >> 4, k = e & 15;
+        const int64_t w = blk0 * 4 + k;
+        const bool okq = LO_OK(t < kQ4 && sh.Q[t] >= 0 && sh.Q[t] < n, 2);
+        const uint64_t z = (w < ldzt && okq) ? ZT[(int64_t)sh.Q[t] * ldzt + w] : 0ull;
+        sh.bits4[t][2 * k] = (uint32_t)z;
+        sh.bits4[t][2 * k + 1] = (uint32_t)(z >> 32);
+    }
+    __syncthreads();
+}
+
+// v with its sign flipped when bit 31 of y is set.
+__device__ __forceinline__ float flip_if(float v, uint32_t y) {
+    return __int_as_float(__float_as_int(v) ^ (int)(y & 0x80000000u));
+}
+
 // MODE 0: (sum cos, sum (cos - mean)^2) per (observable, 256 samples) into
 // part. MODE 1: W[a][i] = sin Phi (alpha_a + beta_a cos Phi), zero for i >= s.
-// One thread per sample; the pair term visits only the pairs of Q_a that
-// carry a generator (C_qr is zero on the others). CTA (a, g) takes sample
-// blocks kPGroup g .. kPGroup g + kPGroup - 1.
+// The pair term visits only the pairs of Q_a that carry a generator (C_qr is
+// zero on the others). CTA (a, g) takes sample blocks kPGroup g ..
+// kPGroup g + kPGroup - 1. For |Q_a| <= kQ4 a thread owns four consecutive
+// samples of a 1024-sample pass (four blocks; block b is warps 2b, 2b + 1),
+// so every support qubit costs one 16-byte load of M and every pair one
+// word pair of sample bits for four samples; larger supports take one block
+// per pass, one sample per thread.
 template <int MODE>
 __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
                                                    const uint64_t *__restrict__ ZT, int64_t ldzt,
@@ -444,6 +473,8 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
                                                    float *__restrict__ W, uint32_t *__restrict__ status) {
     [[maybe_unused]] uint32_t *status_dbg = status;
     __shared__ LoShared sh;
+    __shared__ const float *mrow[kQ4];  // M + Q[t] lds (four-block form)
+    __shared__ float dq[kQ4];           // d[Q[t]] (four-block form)
     const int64_t a = blockIdx.x;
     const int nq = support_of_row(A + a * lda, n, sh.Q, sh.scan, status);
     const int tid = threadIdx.x, w = tid >> 5, bit = tid & 31;
@@ -453,8 +484,100 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
     const bool complete = c0 >= ncand;  // the whole list fits: reuse it for every block
     const float al = MODE == 1 ? (float)alpha[a] : 0.f;
     const float be = (MODE == 1 && beta) ? (float)beta[a] : 0.f;
-    const int64_t b1 = (blockIdx.y + 1) * (int64_t)kPGroup < nparts ? (blockIdx.y + 1) * (int64_t)kPGroup : nparts;
-    for (int64_t blk = blockIdx.y * (int64_t)kPGroup; blk < b1; ++blk) {
+    const int64_t bstart = blockIdx.y * (int64_t)kPGroup;
+    const int64_t b1 = bstart + kPGroup < nparts ? bstart + kPGroup : nparts;
+    if (nq <= kQ4) {
+        for (int t = tid; t < nq; t += kBlk) {
+            const int q = sh.Q[t];
+            const bool ok = LO_OK(q >= 0 && q < n, 7);
+            mrow[t] = M + (ok ? (int64_t)q * lds : 0);
+            dq[t] = ok ? d[q] : 0.f;
+        }
+        const int word = tid >> 3;              // bits4 word of this thread's samples
+        const int sh4 = 28 - 4 * (tid & 7);     // moves their four bits to bits 28 .. 31
+        for (int64_t blk0 = bstart; blk0 < b1; blk0 += 4) {
+            lo_load_bits4(sh, nq, n, ZT, ldzt, blk0, status);  // also orders the mrow/dq stores
+            const int64_t i0 = blk0 * kBlk + 4 * (int64_t)tid;
+            const int64_t blk = blk0 + (tid >> 6);  // this thread's block
+            const int64_t i0c = i0 < lds ? i0 : lds - 4;  // lds is a multiple of 64
+            float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+            for (int t = 0; t < nq; ++t) {
+                if (!LO_OK(i0c >= 0 && i0c + 3 < lds, 8)) break;
+                const float4 mv = *reinterpret_cast<const float4 *>(mrow[t] + i0c);
+                const float dv = dq[t];
+                const uint32_t y = sh.bits4[t][word] << sh4;
+                p0 = p0 + flip_if(dv + mv.x, y << 3);
+                p1 = p1 + flip_if(dv + mv.y, y << 2);
+                p2 = p2 + flip_if(dv + mv.z, y << 1);
+                p3 = p3 + flip_if(dv + mv.w, y);
+            }
+            float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+            if (!complete && blk0 != bstart) {
+                c0 = 0;  // the list is rebuilt round by round for every pass
+                np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
+            }
+            while (true) {
+                for (int p = 0; p < np; ++p) {
+                    const int pr = sh.pr[p];
+                    if (!LO_OK((pr & 0xFFFF) < nq && (pr >> 16) < nq && p < kPairMax, 6)) continue;
+                    const uint32_t y = (sh.bits4[pr & 0xFFFF][word] ^ sh.bits4[pr >> 16][word]) << sh4;
+                    const float cv = sh.pc[p];
+                    q0 = q0 + flip_if(cv, y << 3);
+                    q1 = q1 + flip_if(cv, y << 2);
+                    q2 = q2 + flip_if(cv, y << 1);
+                    q3 = q3 + flip_if(cv, y);
+                }
+                if (complete || c0 >= ncand) break;
+                __syncthreads();
+                np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
+            }
+            const float phi[4] = {p0 - 2.f * q0, p1 - 2.f * q1, p2 - 2.f * q2, p3 - 2.f * q3};
+            bool valid[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) valid[k] = i0 + k < s && blk < b1;
+            if (MODE == 0) {
+                float cv[4], S1 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    cv[k] = valid[k] ? cosf(phi[k]) : 0.f;
+                    S1 += cv[k];
+                }
+                // Block b's sums: its two warps' shuffle sums, in warp order.
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) S1 += __shfl_xor_sync(kFull, S1, off);
+                __syncthreads();
+                if (bit == 0) sh.redf[w] = S1;
+                __syncthreads();
+                const float S = sh.redf[w & ~1] + sh.redf[w | 1];
+                const int64_t nb = s - blk * kBlk < kBlk ? s - blk * kBlk : kBlk;
+                const float mean = nb > 0 ? S / (float)nb : 0.f;
+                float M2 = 0.f;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float dv = cv[k] - mean;
+                    M2 += valid[k] ? dv * dv : 0.f;
+                }
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) M2 += __shfl_xor_sync(kFull, M2, off);
+                __syncthreads();
+                if (bit == 0) sh.redf[w] = M2;
+                __syncthreads();
+                if ((tid & 63) == 0 && blk < b1)
+                    part[a * nparts + blk] = make_double2((double)S, (double)(sh.redf[w] + sh.redf[w + 1]));
+            } else if (i0 < lds && blk < b1) {
+                float o[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float sn, cn;
+                    sincosf(phi[k], &sn, &cn);
+                    o[k] = valid[k] ? sn * (al + be * cn) : 0.f;
+                }
+                *reinterpret_cast<float4 *>(W + a * lds + i0) = make_float4(o[0], o[1], o[2], o[3]);
+            }
+        }
+        return;
+    }
+    for (int64_t blk = bstart; blk < b1; ++blk) {
         lo_load_bits(sh, nq, n, ZT, ldzt, blk, status);
         const int64_t i = blk * kBlk + tid;
         const bool valid = i < s;
@@ -467,7 +590,7 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
             phi += ((sh.bits[t][w] >> bit) & 1u) ? -v : v;
         }
         float pairs = 0.f;
-        if (!complete && blk != blockIdx.y * (int64_t)kPGroup) {
+        if (!complete && blk != bstart) {
             c0 = 0;  // the list is rebuilt round by round for every block
             np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
         }
@@ -502,7 +625,9 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
 
 // V[q][i] = sum over the observables a containing q of W[a][i] (in a order),
 // zero for i >= s; gsp[q * nblk + blk] = sum_i s_q(i) V[q][i] over the
-// CTA's 256 samples (FP64).
+// CTA's 256 samples (FP64). A thread owns four consecutive samples of each
+// 1024-sample pass (block b of the pass is warps 2b, 2b + 1), so every
+// observable costs one 16-byte load of W per thread and pass.
 __global__ void __launch_bounds__(kBlk) k_lo_v(const uint64_t *__restrict__ AT, int64_t ldlt,
                                                const uint64_t *__restrict__ ZT, int64_t ldzt,
                                                const float *__restrict__ W, int64_t lds, int64_t s, int64_t nblk,
@@ -510,14 +635,15 @@ __global__ void __launch_bounds__(kBlk) k_lo_v(const uint64_t *__restrict__ AT, 
     __shared__ float red[kBlk / 32];
     __shared__ int obs[kObsMax];
     __shared__ int wsum[kBlk / 32];
+    constexpr int kPass = kGroup / 4;  // 1024-sample passes per CTA
     const int64_t q = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t *row = AT + q * ldlt;
     const int64_t b0 = blockIdx.y * (int64_t)kGroup;
     const int64_t b1 = b0 + kGroup < nblk ? b0 + kGroup : nblk;
-    float v[kGroup];
+    float4 v[kPass];
 #pragma unroll
-    for (int g = 0; g < kGroup; ++g) v[g] = 0.f;
+    for (int g = 0; g < kPass; ++g) v[g] = make_float4(0.f, 0.f, 0.f, 0.f);
     // The observables containing q, kObsMax at a time, in increasing order
     // (each thread compacts one 64-observable word; warps in order).
     for (int64_t w0 = 0; w0 < ldlt; w0 += kObsMax / 64) {
@@ -550,30 +676,43 @@ __global__ void __launch_bounds__(kBlk) k_lo_v(const uint64_t *__restrict__ AT, 
             __syncthreads();
         }
 #pragma unroll
-        for (int g = 0; g < kGroup; ++g) {
-            const int64_t blk = b0 + g;
-            if (blk < b1) {
-                const int64_t i = blk * kBlk + threadIdx.x;
-                const int64_t ic = i < s ? i : s - 1;
-                float acc = v[g];
-                for (int k = 0; k < no; ++k) acc += W[(int64_t)obs[k] * lds + ic];
+        for (int g = 0; g < kPass; ++g) {
+            if (b0 + 4 * g < b1) {  // uniform
+                const int64_t i0 = (b0 + 4 * g) * kBlk + 4 * (int64_t)threadIdx.x;
+                const int64_t i0c = i0 < lds ? i0 : lds - 4;  // lds is a multiple of 64
+                float4 acc = v[g];
+                for (int k = 0; k < no; ++k) {
+                    const float4 x = *reinterpret_cast<const float4 *>(W + (int64_t)obs[k] * lds + i0c);
+                    acc.x += x.x;
+                    acc.y += x.y;
+                    acc.z += x.z;
+                    acc.w += x.w;
+                }
                 v[g] = acc;
             }
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int g = 0; g < kGroup; ++g) {
-        const int64_t blk = b0 + g < b1 ? b0 + g : b1 - 1;  // uniform; repeats of the last block are not stored
-        const bool store = b0 + g < b1;
-        const int64_t i = blk * kBlk + threadIdx.x;
-        const bool valid = i < s;
-        const int64_t ic = valid ? i : s - 1;
-        const float vv = valid ? v[g] : 0.f;
-        if (store && i < lds) V[q * lds + i] = vv;
-        const float u = ((ZT[q * ldzt + (ic >> 6)] >> (ic & 63)) & 1ull) ? -vv : vv;
-        const float t = block_sum_f(u, red);
-        if (store && threadIdx.x == 0) gsp[q * nblk + blk] = (double)t;
+    for (int g = 0; g < kPass; ++g) {
+        if (b0 + 4 * g >= b1) continue;  // uniform
+        const int64_t i0 = (b0 + 4 * g) * kBlk + 4 * (int64_t)threadIdx.x;
+        const int64_t blk = b0 + 4 * g + (threadIdx.x >> 6);
+        const bool in = blk < b1 && i0 < lds;
+        const float vv[4] = {in && i0 < s ? v[g].x : 0.f, in && i0 + 1 < s ? v[g].y : 0.f,
+                             in && i0 + 2 < s ? v[g].z : 0.f, in && i0 + 3 < s ? v[g].w : 0.f};
+        if (in) *reinterpret_cast<float4 *>(V + q * lds + i0) = make_float4(vv[0], vv[1], vv[2], vv[3]);
+        // lds <= 64 ldzt, so the word of i0 is inside row q of ZT when i0 < lds.
+        const uint32_t nib = in ? (uint32_t)(ZT[q * ldzt + (i0 >> 6)] >> (i0 & 63)) : 0u;
+        float u = 0.f;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) u += ((nib >> k) & 1u) ? -vv[k] : vv[k];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) u += __shfl_xor_sync(kFull, u, off);
+        __syncthreads();
+        if (lane == 0) red[warp] = u;
+        __syncthreads();
+        if ((threadIdx.x & 63) == 0 && blk < b1) gsp[q * nblk + blk] = (double)(red[warp] + red[warp + 1]);
     }
 }
 
@@ -586,9 +725,12 @@ __device__ __forceinline__ long long to_fixed(float x, float sc) {
 
 // K[q][r] += sum over the samples of W[a][i] s_q(i) s_r(i) for the pairs
 // q < r of Q_a that carry a generator (the only K entries the gradient
-// reads); one warp per pair, 8 samples per lane and block, summed over the
-// CTA's blocks in shared memory, one fixed-point atomic per (pair, CTA).
+// reads). The pair list is taken kPairPass pairs at a time; warp w owns
+// pairs w, w + 8, ... of the pass, each lane eight samples of every block,
+// with a running sum per (pair, lane) in registers over the CTA's blocks,
+// then one shuffle reduction and one fixed-point atomic per (pair, CTA).
 // CTA (a, g) takes blocks kPGroup g ...
+constexpr int kPairPass = 128;
 __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
                                                    const uint64_t *__restrict__ ZT, int64_t ldzt,
                                                    const float *__restrict__ C, int64_t ldc,
@@ -597,12 +739,14 @@ __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ 
                                                    int64_t nblk, const double *__restrict__ scale,
                                                    unsigned long long *__restrict__ Kfx,
                                                    uint32_t *__restrict__ status) {
+    [[maybe_unused]] uint32_t *status_dbg = status;
     __shared__ LoShared sh;
     __shared__ float wb[kBlk];
-    __shared__ float pacc[kPairMax];
+    constexpr int kPerWarp = kPairPass / (kBlk / 32);
     const int64_t a = blockIdx.x;
     const int nq = support_of_row(A + a * lda, n, sh.Q, sh.scan, status);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int sa = 31 - lane;  // moves this lane's sample bit to bit 31
     const float sc = (float)*scale;
     const int64_t ncand = (int64_t)nq * nq;
     const int64_t b0 = blockIdx.y * (int64_t)kPGroup;
@@ -610,33 +754,57 @@ __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ 
     int64_t c0 = 0;
     while (c0 < ncand) {
         const int np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
-        for (int p = threadIdx.x; p < np; p += kBlk) pacc[p] = 0.f;  // the sum over the CTA's blocks, per pair
-        for (int64_t blk = b0; blk < b1; ++blk) {
-            lo_load_bits(sh, nq, n, ZT, ldzt, blk, status);
-            const int64_t i = blk * kBlk + threadIdx.x;
-            wb[threadIdx.x] = i < s ? W[a * lds + i] : 0.f;
-            __syncthreads();
-            for (int p = warp; p < np; p += kBlk / 32) {
-                const int pr = sh.pr[p];
-                const int t = pr & 0xFFFF, u = pr >> 16;
-                float v = 0.f;
+        for (int p0 = 0; p0 < np; p0 += kPairPass) {
+            float acc[kPerWarp];
 #pragma unroll
-                for (int kk = 0; kk < 8; ++kk) {
-                    const uint32_t x = sh.bits[t][kk] ^ sh.bits[u][kk];
-                    const float wv = wb[32 * kk + lane];
-                    v += ((x >> lane) & 1u) ? -wv : wv;
+            for (int j = 0; j < kPerWarp; ++j) acc[j] = 0.f;
+            for (int64_t blk = b0; blk < b1; ++blk) {
+                lo_load_bits(sh, nq, n, ZT, ldzt, blk, status);
+                const int64_t i = blk * kBlk + threadIdx.x;
+                wb[threadIdx.x] = i < s ? W[a * lds + i] : 0.f;
+                __syncthreads();
+                float wv[8];
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) wv[kk] = wb[32 * kk + lane];
+#pragma unroll
+                for (int j = 0; j < kPerWarp; ++j) {
+                    const int p = p0 + warp + (kBlk / 32) * j;
+                    if (p < np) {  // uniform in the warp
+                        const int pr = sh.pr[p];
+                        const int t = pr & 0xFFFF, u = pr >> 16;
+                        if (!LO_OK(t < nq && u < nq && t < kQMax && u < kQMax && p < kPairMax, 9)) continue;
+                        const uint4 t0 = *reinterpret_cast<const uint4 *>(&sh.bits[t][0]);
+                        const uint4 t1 = *reinterpret_cast<const uint4 *>(&sh.bits[t][4]);
+                        const uint4 u0 = *reinterpret_cast<const uint4 *>(&sh.bits[u][0]);
+                        const uint4 u1 = *reinterpret_cast<const uint4 *>(&sh.bits[u][4]);
+                        float v = acc[j];
+                        v += flip_if(wv[0], (t0.x ^ u0.x) << sa);
+                        v += flip_if(wv[1], (t0.y ^ u0.y) << sa);
+                        v += flip_if(wv[2], (t0.z ^ u0.z) << sa);
+                        v += flip_if(wv[3], (t0.w ^ u0.w) << sa);
+                        v += flip_if(wv[4], (t1.x ^ u1.x) << sa);
+                        v += flip_if(wv[5], (t1.y ^ u1.y) << sa);
+                        v += flip_if(wv[6], (t1.z ^ u1.z) << sa);
+                        v += flip_if(wv[7], (t1.w ^ u1.w) << sa);
+                        acc[j] = v;
+                    }
                 }
+            }
 #pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
-                if (lane == 0) pacc[p] += v;  // pair p belongs to this warp alone
+            for (int j = 0; j < kPerWarp; ++j) {
+                const int p = p0 + warp + (kBlk / 32) * j;
+                if (p < np) {  // uniform in the warp
+                    float v = acc[j];
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(kFull, v, off);
+                    const int pr = sh.pr[p];
+                    if (lane == 0)
+                        atomicAdd(Kfx + (int64_t)sh.Q[pr & 0xFFFF] * n + sh.Q[pr >> 16],
+                                  (unsigned long long)to_fixed(v, sc));
+                }
             }
         }
-        __syncthreads();
-        for (int p = threadIdx.x; p < np; p += kBlk) {
-            const int pr = sh.pr[p];
-            atomicAdd(Kfx + (int64_t)sh.Q[pr & 0xFFFF] * n + sh.Q[pr >> 16], (unsigned long long)to_fixed(pacc[p], sc));
-        }
-        __syncthreads();
+        __syncthreads();  // the list is read before the next round rebuilds it
     }
 }
 
