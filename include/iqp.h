@@ -221,6 +221,10 @@ iqp_status iqp_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
 
 /* Loss as iqp_mmd_loss and its gradient grad[m] in theta, by the chain rule
  * through S1 and S2 (alpha, beta of iqp_expval_grad formed on the device).
+ * With IQP_SPLIT_BF16 and IQP_LOWORDER_FP32 the call runs one phase
+ * contraction: the statistics pass keeps Phi (l x s FP32, in the workspace)
+ * and W is formed from it once alpha, beta are known; the other precisions
+ * recompute Phi for W.
  * ws: iqp_workspace_bytes(IQP_OP_MMD_LOSS_GRAD, ...). */
 iqp_status iqp_mmd_loss_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                              const uint64_t *A, int64_t l, int64_t lda,
@@ -325,7 +329,8 @@ typedef enum {
     IQP_KERNEL_RECOMPUTE_FP32 = 4, /* SIMT phase recompute -> W                 */
     IQP_KERNEL_GRAD_FP32 = 5,      /* SIMT gradient contraction                 */
     IQP_KERNEL_PHASE_TC = 6,       /* tcgen05 phase contraction + statistics    */
-    IQP_KERNEL_RECOMPUTE_TC = 7,   /* tcgen05 phase recompute -> W (hi/lo)      */
+    IQP_KERNEL_RECOMPUTE_TC = 7,   /* W (hi/lo): tcgen05 phase recompute, or
+                                      from the Phi an MMD statistics pass kept */
     IQP_KERNEL_GRAD_TC = 8,        /* tcgen05 gradient contraction              */
     IQP_KERNEL_FINALIZE = 9,       /* per-observable mean / standard error      */
     IQP_KERNEL_GRAD_REDUCE = 10,   /* fixed-order reduction of gradient parts   */

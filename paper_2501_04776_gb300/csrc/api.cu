@@ -34,6 +34,7 @@ cudaError_t launch_mmd_combine(const int64_t *T, const double *S1, const double 
                                cudaStream_t st);
 cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alpha, const double *beta,
                             cudaStream_t st, iqp_status *why);
+cudaError_t launch_w_from_phi(const Plan &p, void *ws, const double *alpha, const double *beta, cudaStream_t st);
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why);
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st);
 int64_t sparse_part_samples();
@@ -65,12 +66,12 @@ cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t l
                               cudaStream_t st);
 cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                             const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, double2 *part,
-                            int64_t nparts, uint32_t *status, cudaStream_t st);
+                            int64_t nparts, float *phi_out, uint32_t *status, cudaStream_t st);
 cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
                            const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
                            float *W, float *V, double *H, double *gsp, unsigned long long *Kfx, double *grad,
-                           __nv_bfloat16 *split, uint32_t *status, cudaStream_t st);
+                           __nv_bfloat16 *split, bool phi_ready, uint32_t *status, cudaStream_t st);
 cudaError_t launch_bitflip_gates(const float *theta, int64_t m, int64_t mpad, double *c, double *t, cudaStream_t st);
 cudaError_t launch_bitflip_rows(const uint64_t *PA, int64_t ldp, int64_t l, const double *c, double *expval,
                                 cudaStream_t st);
@@ -140,6 +141,10 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_terms = take(mmd ? l * 8 : 0);
     p.off_zt = take(indep ? l * n * p.ldzt * 8 : 0);  // every batch transposed: n rows of bits over samples
     p.off_sup = take(indep || lo ? m * 16 : 0);       // int4 support list per gate
+    // Split BF16 MMD gradient: Phi kept from the statistics pass, so W needs
+    // no second phase contraction (the loss's alpha, beta come between).
+    p.off_phi = (prec == IQP_SPLIT_BF16 && op == IQP_OP_MMD_LOSS_GRAD) ? take(l * p.ldw * 4) : 0;
+    p.store_phi = false;
     // Last, and optional: the split-tile scratch of the tensor-core phase (a
     // workspace that ends before it runs every phase tile whole).
     p.off_skp = 0;
@@ -327,7 +332,7 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
     } else if (p.prec == IQP_LOWORDER_FP32) {
         IQP_TRY(launch_lo_stats(p.A, p.lda, p.n, p.l, at<uint64_t>(ws, p.off_pzt), p.ldzt, at<float>(ws, p.off_lo_m),
                                 p.ldw, at<float>(ws, p.off_lo_c), p.ldc, p.s, part, p.nparts,
-                                at<uint32_t>(ws, p.off_status), st));
+                                p.store_phi ? at<float>(ws, p.off_w) : nullptr, at<uint32_t>(ws, p.off_status), st));
     } else if (p.prec == IQP_SPARSE_FP32) {
         const SparseIndep ind{at<int4>(ws, p.off_sup), p.G, p.ldg, p.n};
         IQP_TRY(launch_sparse_stats(at<uint64_t>(ws, p.off_pa), p.ldp,
@@ -352,7 +357,7 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
                                at<uint64_t>(ws, p.off_rt), p.ldlt, at<float>(ws, p.off_w), at<float>(ws, p.off_lo_v),
                                at<double>(ws, p.off_lo_h), at<double>(ws, p.off_lo_gs),
                                at<unsigned long long>(ws, p.off_gpart), grad, at<__nv_bfloat16>(ws, p.off_lo_a),
-                               at<uint32_t>(ws, p.off_status), st));
+                               p.store_phi, at<uint32_t>(ws, p.off_status), st));
         return IQP_OK;
     }
     if (p.prec == IQP_SPARSE_FP32) {
@@ -366,7 +371,11 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
     }
     if (p.prec == IQP_SPLIT_BF16) {
         iqp_status why = IQP_OK;
-        if (launch_phase_tc(1, p, ws, alpha, beta, st, &why) != cudaSuccess) return why != IQP_OK ? why : IQP_ERR_CUDA;
+        if (p.store_phi) {
+            IQP_TRY(launch_w_from_phi(p, ws, alpha, beta, st));
+        } else if (launch_phase_tc(1, p, ws, alpha, beta, st, &why) != cudaSuccess) {
+            return why != IQP_OK ? why : IQP_ERR_CUDA;
+        }
         if (launch_grad_tc(p, ws, st, &why) != cudaSuccess) return why != IQP_OK ? why : IQP_ERR_CUDA;
     } else {
         float *W = at<float>(ws, p.off_w);
@@ -405,6 +414,7 @@ iqp_status mmd_core(int op, int64_t n, const uint64_t *G, int64_t m, int64_t ldg
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
     double *S1 = at<double>(ws, p.off_s12), *S2 = S1 + l;
+    p.store_phi = g && (p.prec == IQP_LOWORDER_FP32 || p.off_phi != 0);
     if ((rc = forward_stats(p, ws, nullptr, nullptr, S1, S2, st)) != IQP_OK) return rc;
     int64_t *T = at<int64_t>(ws, p.off_T);
     IQP_TRY(launch_parity_sum(n, A, l, lda, X, N, ldx, T, st));
@@ -535,6 +545,7 @@ iqp_status iqp_expval_value_and_grad(int64_t n, const uint64_t *G, int64_t m, in
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
     if (prec != IQP_SPLIT_BF16) {
+        p.store_phi = prec == IQP_LOWORDER_FP32;  // W from the kept Phi, no second phase pass
         if ((rc = forward_stats(p, ws, expval, std_err, nullptr, nullptr, st)) != IQP_OK) return rc;
         return backward(p, ws, alpha, beta, grad, st);
     }

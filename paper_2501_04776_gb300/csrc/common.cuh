@@ -43,6 +43,8 @@ struct Plan {
     // low-order form: C (+ d), M = C S, V, H, single-gate partials; ldc floats per row of C and H
     size_t off_lo_c, off_lo_m, off_lo_v, off_lo_h, off_lo_gs, off_lo_a;
     size_t off_skp;  // split BF16: partial accumulators and counters of split phase tiles (0 if none)
+    size_t off_phi;  // split BF16 MMD gradient: Phi (l x ldw fp32) from the statistics pass (0 if none)
+    bool store_phi;  // the statistics pass keeps Phi for the gradient pass that follows in the same call
     int64_t ldc;
     bool indep;     // one sample batch per observable (Z has l * s rows)
     const uint64_t *G;  // generators (read by the independent-batch kernels)

@@ -454,7 +454,9 @@ __device__ __forceinline__ float flip_if(float v, uint32_t y) {
 }
 
 // MODE 0: (sum cos, sum (cos - mean)^2) per (observable, 256 samples) into
-// part. MODE 1: W[a][i] = sin Phi (alpha_a + beta_a cos Phi), zero for i >= s.
+// part, and Phi itself into W (columns < lds) when W is not null (a gradient
+// pass follows). MODE 1: W[a][i] = sin Phi (alpha_a + beta_a cos Phi), zero
+// for i >= s.
 // The pair term visits only the pairs of Q_a that carry a generator (C_qr is
 // zero on the others). CTA (a, g) takes sample blocks kPGroup g ..
 // kPGroup g + kPGroup - 1. For |Q_a| <= kQ4 a thread owns four consecutive
@@ -564,6 +566,8 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
                 __syncthreads();
                 if ((tid & 63) == 0 && blk < b1)
                     part[a * nparts + blk] = make_double2((double)S, (double)(sh.redf[w] + sh.redf[w + 1]));
+                if (W != nullptr && i0 < lds && blk < b1)
+                    *reinterpret_cast<float4 *>(W + a * lds + i0) = make_float4(phi[0], phi[1], phi[2], phi[3]);
             } else if (i0 < lds && blk < b1) {
                 float o[4];
 #pragma unroll
@@ -615,6 +619,7 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
             const float dv = cv - mean;
             const float M2 = block_sum_f(valid ? dv * dv : 0.f, sh.redf);
             if (tid == 0) part[a * nparts + blk] = make_double2((double)S, (double)M2);
+            if (W != nullptr && i < lds) W[a * lds + i] = phi;
         } else {
             float sn, cn;
             sincosf(phi, &sn, &cn);
@@ -713,6 +718,31 @@ __global__ void __launch_bounds__(kBlk) k_lo_v(const uint64_t *__restrict__ AT, 
         if (lane == 0) red[warp] = u;
         __syncthreads();
         if ((threadIdx.x & 63) == 0 && blk < b1) gsp[q * nblk + blk] = (double)(red[warp] + red[warp + 1]);
+    }
+}
+
+// W[a][i] = sin Phi (alpha_a + beta_a cos Phi) in place over the Phi the
+// statistics pass kept in W (zero for i >= s), four samples per thread: the
+// arithmetic of k_lo_phase<1>, without recomputing Phi.
+__global__ void __launch_bounds__(256) k_lo_w(float *__restrict__ W, int64_t lds, int64_t l, int64_t s,
+                                             const double *__restrict__ alpha, const double *__restrict__ beta) {
+    const int64_t per_row = lds / 4;
+    const int64_t total = l * per_row;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = g / per_row, i0 = (g - a * per_row) * 4;
+        const float al = (float)alpha[a];
+        const float be = beta ? (float)beta[a] : 0.f;
+        float4 *p = reinterpret_cast<float4 *>(W + a * lds + i0);
+        const float4 f = *p;
+        const float v[4] = {f.x, f.y, f.z, f.w};
+        float o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float sn, cn;
+            sincosf(v[k], &sn, &cn);
+            o[k] = i0 + k < s ? sn * (al + be * cn) : 0.f;
+        }
+        *p = make_float4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -914,13 +944,13 @@ cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t l
 
 cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                             const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, double2 *part,
-                            int64_t nparts, uint32_t *status, cudaStream_t st) {
+                            int64_t nparts, float *phi_out, uint32_t *status, cudaStream_t st) {
     LaunchScope ls(IQP_KERNEL_LOWORDER, st);
     const float *d = C + n * ldc;
     const unsigned long long *E = reinterpret_cast<const unsigned long long *>(d + ldc);
     k_lo_phase<0><<<dim3((unsigned)l, (unsigned)cdiv(nparts, kPGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d, E,
                                                                        lo_lde(n), s, nparts, part, nullptr, nullptr,
-                                                                       nullptr, status);
+                                                                       phi_out, status);
     return cudaGetLastError();
 }
 
@@ -930,7 +960,7 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
                            const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
                            float *W, float *V, double *H, double *gsp, unsigned long long *Kfx, double *grad,
-                           __nv_bfloat16 *split, uint32_t *status, cudaStream_t st) {
+                           __nv_bfloat16 *split, bool phi_ready, uint32_t *status, cudaStream_t st) {
     const int64_t nblk = cdiv(s, kBlk);
     double *scale = reinterpret_cast<double *>(Kfx + n * n);
     const float *d = C + n * ldc;
@@ -940,7 +970,11 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(Kfx, 0, (size_t)n * n * sizeof(unsigned long long), st)) != cudaSuccess) return e;
     if ((e = launch_fixed_scale(alpha, beta, l, s, scale, st)) != cudaSuccess) return e;
-    {
+    if (phi_ready) {  // W holds Phi from the statistics pass
+        LaunchScope ls(IQP_KERNEL_LOWORDER, st);
+        k_lo_w<<<grid_1d(l * (lds / 4)), 256, 0, st>>>(W, lds, l, s, alpha, beta);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
         k_lo_phase<1><<<dim3((unsigned)l, (unsigned)cdiv(nblk, kPGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d,
                                                                          E, lde, s, nblk, nullptr, alpha, beta, W,

@@ -254,6 +254,41 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return lo | (hi << 16);
 }
 
+// W = sin Phi (alpha_a + beta_a cos Phi) as BF16 hi/lo from a Phi the
+// statistics pass kept (l x ldw FP32, columns < s), with the arithmetic of
+// the recompute epilogue, so W is the same bit for bit. Four samples per
+// thread; columns >= s get zeros (the gradient's tensor map ends at s).
+__global__ void __launch_bounds__(256) k_w_from_phi(const float *__restrict__ phi, int64_t ldw, int64_t l, int64_t s,
+                                                    const double *__restrict__ alpha,
+                                                    const double *__restrict__ beta, __nv_bfloat16 *__restrict__ whi,
+                                                    __nv_bfloat16 *__restrict__ wlo) {
+    const int64_t per_row = ldw / 4;
+    const int64_t total = l * per_row;
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t row = g / per_row, i0 = (g - row * per_row) * 4;
+        if (i0 >= s) continue;
+        const float al = (float)alpha[row];
+        const float be = beta ? (float)beta[row] : 0.f;
+        const float4 f = *reinterpret_cast<const float4 *>(phi + row * ldw + i0);
+        const float v[4] = {f.x, f.y, f.z, f.w};
+        uint32_t ph[2], pl[2];
+#pragma unroll
+        for (int e = 0; e < 4; e += 2) {
+            float s0, k0, s1, k1;
+            sincosf(v[e], &s0, &k0);
+            sincosf(v[e + 1], &s1, &k1);
+            const float w0 = i0 + e < s ? s0 * (al + be * k0) : 0.f;
+            const float w1 = i0 + e + 1 < s ? s1 * (al + be * k1) : 0.f;
+            const float h0 = __bfloat162float(__float2bfloat16_rn(w0));
+            const float h1 = __bfloat162float(__float2bfloat16_rn(w1));
+            ph[e / 2] = pack_bf16x2(h0, h1);
+            pl[e / 2] = pack_bf16x2(w0 - h0, w1 - h1);
+        }
+        *reinterpret_cast<uint2 *>(whi + row * ldw + i0) = make_uint2(ph[0], ph[1]);
+        *reinterpret_cast<uint2 *>(wlo + row * ldw + i0) = make_uint2(pl[0], pl[1]);
+    }
+}
+
 // ------------------------------------------------------------------ kernel
 // W hi/lo (BF16 pairs) of 32 consecutive samples i0.. of observable row.
 __device__ __forceinline__ void store_w32(const TcArgs &args, int64_t row, int64_t i0, const uint32_t (&ph)[16],
@@ -739,6 +774,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                             M2 = fmaf(d, d, M2);
                         }
                 }
+                // Phi itself, when a gradient pass follows (W from it instead
+                // of a second contraction).
+                if (args.out != nullptr) {  // uniform: every lane takes the TMEM loads
+#pragma unroll 1
+                    for (int c = 0; c * 32 < nvalid; ++c) {
+                        load_sum32(tbase + c * 32, chunked, r);
+                        if (row < args.l) store_out32(args, row, c0 + c * 32, r);
+                    }
+                }
                 if (row < args.l && nvalid > 0)
                     args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
             } else if (!GRAD && MODE == 2) {
@@ -1054,8 +1098,9 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.pa32 = nullptr;
     a.ldp32 = 2 * p.ldp;
     a.gpart = nullptr;
-    a.out = nullptr;
-    a.ldo = 0;
+    // MODE 0 keeps Phi (FP32, l x ldw) when a gradient pass follows.
+    a.out = (mode == 0 && p.store_phi && p.off_phi != 0) ? static_cast<void *>(at<float>(ws, p.off_phi)) : nullptr;
+    a.ldo = p.ldw;
     a.out_f64 = 0;
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
@@ -1136,6 +1181,20 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.limit_ns = default_spin_limit_ns();
     if (mc) return launch_k<true, 0, 1, 2>(mhi, mlo, mb, a, st);
     return launch_k<true, 0, 1>(mhi, mlo, mb, a, st);
+}
+
+cudaError_t launch_w_from_phi(const Plan &p, void *ws, const double *alpha, const double *beta, cudaStream_t st) {
+    if (p.off_phi == 0 || p.ldw % 4 != 0) return cudaErrorInvalidValue;
+    __nv_bfloat16 *whi = at<__nv_bfloat16>(ws, p.off_w);
+    __nv_bfloat16 *wlo = whi + p.l * p.ldw;
+    const int64_t total = p.l * (p.ldw / 4);
+    int64_t grid = cdiv(total, 256);
+    const int64_t cap = (int64_t)num_sms() * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    LaunchScope ls(IQP_KERNEL_RECOMPUTE_TC, st);
+    k_w_from_phi<<<(unsigned)grid, 256, 0, st>>>(at<float>(ws, p.off_phi), p.ldw, p.l, p.s, alpha, beta, whi, wlo);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tc_dense(const __nv_bfloat16 *a_hi, const __nv_bfloat16 *a_lo, int64_t rows, int64_t kpad,
