@@ -433,10 +433,10 @@ __device__ __forceinline__ float block_sum_f(float v, float *red) {
 }
 
 // The sample bits of blocks blk0 .. blk0 + 3 for every support qubit:
-// bits4[t][w] holds samples 32 w .. 32 w + 31 of the 1024.
-__device__ void lo_load_bits4(LoShared &sh, int nq, int64_t n, const uint64_t *__restrict__ ZT, int64_t ldzt,
-                              int64_t blk0, [[maybe_unused]] uint32_t *__restrict__ status_dbg) {
-    __syncthreads();  // previous readers of bits4 are done
+// bits4[t][w] holds samples 32 w .. 32 w + 31 of the 1024. No barriers.
+__device__ __forceinline__ void lo_fill_bits4(LoShared &sh, int nq, int64_t n, const uint64_t *__restrict__ ZT,
+                                              int64_t ldzt, int64_t blk0,
+                                              [[maybe_unused]] uint32_t *__restrict__ status_dbg) {
     for (int e = threadIdx.x; e < nq * 16; e += kBlk) {
         const int t = e >> 4, k = e & 15;
         const int64_t w = blk0 * 4 + k;
@@ -445,6 +445,14 @@ __device__ void lo_load_bits4(LoShared &sh, int nq, int64_t n, const uint64_t *_
         sh.bits4[t][2 * k] = (uint32_t)z;
         sh.bits4[t][2 * k + 1] = (uint32_t)(z >> 32);
     }
+}
+
+// lo_fill_bits4 between barriers: previous readers of bits4 are done before
+// it, every word is in place after it.
+__device__ void lo_load_bits4(LoShared &sh, int nq, int64_t n, const uint64_t *__restrict__ ZT, int64_t ldzt,
+                              int64_t blk0, uint32_t *__restrict__ status_dbg) {
+    __syncthreads();
+    lo_fill_bits4(sh, nq, n, ZT, ldzt, blk0, status_dbg);
     __syncthreads();
 }
 
@@ -759,6 +767,8 @@ __device__ __forceinline__ long long to_fixed(float x, float sc) {
 // pairs w, w + 8, ... of the pass, each lane eight samples of every block,
 // with a running sum per (pair, lane) in registers over the CTA's blocks,
 // then one shuffle reduction and one fixed-point atomic per (pair, CTA).
+// For supports of at most kQ4 qubits the sample bits and W of four blocks
+// are staged per pair of barriers (one block at a time otherwise).
 // CTA (a, g) takes blocks kPGroup g ...
 constexpr int kPairPass = 128;
 __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ A, int64_t lda, int64_t n,
@@ -771,7 +781,7 @@ __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ 
                                                    uint32_t *__restrict__ status) {
     [[maybe_unused]] uint32_t *status_dbg = status;
     __shared__ LoShared sh;
-    __shared__ float wb[kBlk];
+    __shared__ __align__(16) float wb[4 * kBlk];
     constexpr int kPerWarp = kPairPass / (kBlk / 32);
     const int64_t a = blockIdx.x;
     const int nq = support_of_row(A + a * lda, n, sh.Q, sh.scan, status);
@@ -788,14 +798,9 @@ __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ 
             float acc[kPerWarp];
 #pragma unroll
             for (int j = 0; j < kPerWarp; ++j) acc[j] = 0.f;
-            for (int64_t blk = b0; blk < b1; ++blk) {
-                lo_load_bits(sh, nq, n, ZT, ldzt, blk, status);
-                const int64_t i = blk * kBlk + threadIdx.x;
-                wb[threadIdx.x] = i < s ? W[a * lds + i] : 0.f;
-                __syncthreads();
-                float wv[8];
-#pragma unroll
-                for (int kk = 0; kk < 8; ++kk) wv[kk] = wb[32 * kk + lane];
+            // One block's sample-bit rows (8 words per support qubit, at
+            // word stride ws of the shared rows) against the lane's 8 W values.
+            auto block_pairs = [&](const uint32_t *rows, int ws, const float (&wv)[8]) {
 #pragma unroll
                 for (int j = 0; j < kPerWarp; ++j) {
                     const int p = p0 + warp + (kBlk / 32) * j;
@@ -803,10 +808,10 @@ __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ 
                         const int pr = sh.pr[p];
                         const int t = pr & 0xFFFF, u = pr >> 16;
                         if (!LO_OK(t < nq && u < nq && t < kQMax && u < kQMax && p < kPairMax, 9)) continue;
-                        const uint4 t0 = *reinterpret_cast<const uint4 *>(&sh.bits[t][0]);
-                        const uint4 t1 = *reinterpret_cast<const uint4 *>(&sh.bits[t][4]);
-                        const uint4 u0 = *reinterpret_cast<const uint4 *>(&sh.bits[u][0]);
-                        const uint4 u1 = *reinterpret_cast<const uint4 *>(&sh.bits[u][4]);
+                        const uint4 t0 = *reinterpret_cast<const uint4 *>(rows + t * ws);
+                        const uint4 t1 = *reinterpret_cast<const uint4 *>(rows + t * ws + 4);
+                        const uint4 u0 = *reinterpret_cast<const uint4 *>(rows + u * ws);
+                        const uint4 u1 = *reinterpret_cast<const uint4 *>(rows + u * ws + 4);
                         float v = acc[j];
                         v += flip_if(wv[0], (t0.x ^ u0.x) << sa);
                         v += flip_if(wv[1], (t0.y ^ u0.y) << sa);
@@ -818,6 +823,41 @@ __global__ void __launch_bounds__(kBlk) k_lo_pairs(const uint64_t *__restrict__ 
                         v += flip_if(wv[7], (t1.w ^ u1.w) << sa);
                         acc[j] = v;
                     }
+                }
+            };
+            if (nq <= kQ4) {
+                for (int64_t blk0 = b0; blk0 < b1; blk0 += 4) {
+                    __syncthreads();  // previous readers of bits4 and wb are done
+                    lo_fill_bits4(sh, nq, n, ZT, ldzt, blk0, status);
+                    {
+                        const int64_t i0 = blk0 * kBlk + 4 * (int64_t)threadIdx.x;
+                        const bool in = blk0 + (threadIdx.x >> 6) < b1 && i0 < lds;  // lds: a multiple of 64
+                        float4 w4 = in ? *reinterpret_cast<const float4 *>(W + a * lds + i0)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (i0 >= s) w4.x = 0.f;
+                        if (i0 + 1 >= s) w4.y = 0.f;
+                        if (i0 + 2 >= s) w4.z = 0.f;
+                        if (i0 + 3 >= s) w4.w = 0.f;
+                        *reinterpret_cast<float4 *>(&wb[4 * threadIdx.x]) = w4;
+                    }
+                    __syncthreads();
+                    for (int b = 0; b < 4 && blk0 + b < b1; ++b) {  // uniform
+                        float wv[8];
+#pragma unroll
+                        for (int kk = 0; kk < 8; ++kk) wv[kk] = wb[kBlk * b + 32 * kk + lane];
+                        block_pairs(&sh.bits4[0][8 * b], 32, wv);
+                    }
+                }
+            } else {
+                for (int64_t blk = b0; blk < b1; ++blk) {
+                    lo_load_bits(sh, nq, n, ZT, ldzt, blk, status);
+                    const int64_t i = blk * kBlk + threadIdx.x;
+                    wb[threadIdx.x] = i < s ? W[a * lds + i] : 0.f;
+                    __syncthreads();
+                    float wv[8];
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) wv[kk] = wb[32 * kk + lane];
+                    block_pairs(&sh.bits[0][0], 8, wv);
                 }
             }
 #pragma unroll
