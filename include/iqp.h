@@ -221,10 +221,10 @@ iqp_status iqp_mmd_loss(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
 
 /* Loss as iqp_mmd_loss and its gradient grad[m] in theta, by the chain rule
  * through S1 and S2 (alpha, beta of iqp_expval_grad formed on the device).
- * With IQP_SPLIT_BF16 and IQP_LOWORDER_FP32 the call runs one phase
- * contraction: the statistics pass keeps Phi (l x s FP32, in the workspace)
- * and W is formed from it once alpha, beta are known; the other precisions
- * recompute Phi for W.
+ * With IQP_SPLIT_BF16, IQP_SPARSE_FP32 and IQP_LOWORDER_FP32 (shared
+ * batches) the call runs one phase contraction: the statistics pass keeps Phi
+ * (l x s FP32, in the workspace) and W is formed from it once alpha, beta are
+ * known; IQP_FP32 and independent batches recompute Phi for W.
  * ws: iqp_workspace_bytes(IQP_OP_MMD_LOSS_GRAD, ...). */
 iqp_status iqp_mmd_loss_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                              const uint64_t *A, int64_t l, int64_t lda,

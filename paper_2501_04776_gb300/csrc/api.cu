@@ -40,11 +40,11 @@ cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStr
 int64_t sparse_part_samples();
 cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
                                 int64_t l, int64_t s, double2 *part, int64_t nparts, const SparseIndep *indep,
-                                cudaStream_t st);
+                                float *phi, int64_t ldphi, cudaStream_t st);
 cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
                                int64_t l, int64_t s, int64_t m, int64_t nparts, const double *alpha,
                                const double *beta, double *scale, unsigned long long *gfx, double *grad,
-                               const SparseIndep *indep, cudaStream_t st);
+                               const SparseIndep *indep, const float *phi, int64_t ldphi, cudaStream_t st);
 cudaError_t launch_bit_transpose_batched(const uint64_t *in, int64_t batch, int64_t in_rows, int64_t in_cols,
                                          int64_t ld_in, uint64_t *out, int64_t ld_out, cudaStream_t st);
 cudaError_t launch_support_list(const uint64_t *G, int64_t m, int64_t ldg, int64_t n, int4 *sup, cudaStream_t st);
@@ -141,9 +141,11 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_terms = take(mmd ? l * 8 : 0);
     p.off_zt = take(indep ? l * n * p.ldzt * 8 : 0);  // every batch transposed: n rows of bits over samples
     p.off_sup = take(indep || lo ? m * 16 : 0);       // int4 support list per gate
-    // Split BF16 MMD gradient: Phi kept from the statistics pass, so W needs
-    // no second phase contraction (the loss's alpha, beta come between).
-    p.off_phi = (prec == IQP_SPLIT_BF16 && op == IQP_OP_MMD_LOSS_GRAD) ? take(l * p.ldw * 4) : 0;
+    // MMD gradient (split BF16, row-sparse; shared batches): Phi kept from
+    // the statistics pass, so W needs no second phase pass (the loss's alpha,
+    // beta come between). The low-order form keeps it in its W buffer.
+    p.off_phi = (op == IQP_OP_MMD_LOSS_GRAD && (prec == IQP_SPLIT_BF16 || prec == IQP_SPARSE_FP32)) ? take(l * p.ldw * 4)
+                                                                                                : 0;
     p.store_phi = false;
     // Last, and optional: the split-tile scratch of the tensor-core phase (a
     // workspace that ends before it runs every phase tile whole).
@@ -337,7 +339,8 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
         const SparseIndep ind{at<int4>(ws, p.off_sup), p.G, p.ldg, p.n};
         IQP_TRY(launch_sparse_stats(at<uint64_t>(ws, p.off_pa), p.ldp,
                                     at<uint64_t>(ws, p.indep ? p.off_zt : p.off_pzt), p.ldzt, at<float>(ws, p.off_c),
-                                    p.l, p.s, part, p.nparts, p.indep ? &ind : nullptr, st));
+                                    p.l, p.s, part, p.nparts, p.indep ? &ind : nullptr,
+                                    p.store_phi ? at<float>(ws, p.off_phi) : nullptr, p.ldw, st));
     } else {
         IQP_TRY(launch_phase_simt(0, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pz), p.ldp,
                                   at<float>(ws, p.off_c), p.l, p.s, p.m, part, p.nparts, nullptr, nullptr, nullptr, 0,
@@ -366,7 +369,8 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
         IQP_TRY(launch_sparse_grad(at<uint64_t>(ws, p.off_pa), p.ldp,
                                    at<uint64_t>(ws, p.indep ? p.off_zt : p.off_pzt), p.ldzt, at<float>(ws, p.off_c),
                                    p.l, p.s, p.m, p.nparts, alpha, beta, reinterpret_cast<double *>(gfx + p.m), gfx,
-                                   grad, p.indep ? &ind : nullptr, st));
+                                   grad, p.indep ? &ind : nullptr, p.store_phi ? at<float>(ws, p.off_phi) : nullptr,
+                                   p.ldw, st));
         return IQP_OK;
     }
     if (p.prec == IQP_SPLIT_BF16) {

@@ -251,8 +251,11 @@ struct GradRun {
     }
 };
 
-// MODE 0: statistics partials. MODE 1: W from the recomputed Phi, then the
-// gradient contributions of every gate of J_a.
+// MODE 0: statistics partials, and Phi itself into phi (l x ldphi FP32) when
+// phi is not null (a gradient pass follows). MODE 1: W from Phi (read from
+// phi when not null, else recomputed), then the gradient contributions of
+// every gate of J_a. Independent batches always recompute (keeping Phi there
+// would push the statistics pass past its register budget).
 // INDEP: PZT holds every observable's transposed samples (n x ldzt words
 // each, observable a at PZT + a n ldzt) and the parities are formed on the fly.
 template <int MODE, bool INDEP>
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(256, 2)
              const float *__restrict__ c, int64_t s, int64_t nparts, double2 *__restrict__ part,
              const double *__restrict__ alpha, const double *__restrict__ beta, const double *__restrict__ scale,
              unsigned long long *__restrict__ gfx, const int4 *__restrict__ sup, const uint64_t *__restrict__ G,
-             int64_t ldg, int64_t n) {
+             int64_t ldg, int64_t n, float *__restrict__ phi, int64_t ldphi) {
     const int lane = threadIdx.x & 31;
     const int64_t a = blockIdx.x;
     const int64_t r = (int64_t)blockIdx.y * (blockDim.x >> 5) + (threadIdx.x >> 5);  // 2048-sample range
@@ -276,7 +279,27 @@ __global__ void __launch_bounds__(256, 2)
     const ZSource zs{INDEP ? PZT + a * n * ldzt : PZT, ldzt, word, sup, G, ldg, n};
 
     uint64_t acc2[32];
-    phase_row<INDEP>(acc2, parow, ldp, zs, c, lane);
+    // The lane's 64 samples i0 .. i0 + 63 lie inside a row of phi (ldphi is a
+    // multiple of 64) whenever the lane's word is valid; they are kept in the
+    // accumulators' pair order (pair t: samples t and 32 + t), 256 bytes a lane.
+    if (MODE == 1 && !INDEP && phi != nullptr) {
+        const uint4 *prow = reinterpret_cast<const uint4 *>(phi + a * ldphi + (wvalid ? i0 : 0));
+#pragma unroll
+        for (int v = 0; v < 16; ++v) {
+            const uint4 q = wvalid ? prow[v] : make_uint4(0u, 0u, 0u, 0u);
+            acc2[2 * v] = (uint64_t)q.x | ((uint64_t)q.y << 32);
+            acc2[2 * v + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
+        }
+    } else {
+        phase_row<INDEP>(acc2, parow, ldp, zs, c, lane);
+        if (MODE == 0 && !INDEP && phi != nullptr && wvalid) {
+            uint4 *prow = reinterpret_cast<uint4 *>(phi + a * ldphi + i0);
+#pragma unroll
+            for (int v = 0; v < 16; ++v)
+                prow[v] = make_uint4((uint32_t)acc2[2 * v], (uint32_t)(acc2[2 * v] >> 32), (uint32_t)acc2[2 * v + 1],
+                                     (uint32_t)(acc2[2 * v + 1] >> 32));
+        }
+    }
     float acc[64];
 #pragma unroll
     for (int t = 0; t < 32; ++t) {
@@ -395,25 +418,27 @@ cudaError_t launch_fixed_scale(const double *alpha, const double *beta, int64_t 
 }
 
 // indep != nullptr: independent batches (PZT = every observable's ZT).
+// phi != nullptr: Phi is kept there (l x ldphi FP32, ldphi a multiple of 64).
 cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
                                 int64_t l, int64_t s, double2 *part, int64_t nparts, const SparseIndep *indep,
-                                cudaStream_t st) {
+                                float *phi, int64_t ldphi, cudaStream_t st) {
     int threads = 0;
     const dim3 grid = sparse_grid(l, nparts, &threads);
     LaunchScope ls(IQP_KERNEL_PHASE_SPARSE, st);
     if (indep)
         k_sparse<0, true><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, nullptr, nullptr,
-                                                    nullptr, nullptr, indep->sup, indep->G, indep->ldg, indep->n);
+                                                    nullptr, nullptr, indep->sup, indep->G, indep->ldg, indep->n,
+                                                    phi, ldphi);
     else
         k_sparse<0, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, nullptr, nullptr,
-                                                     nullptr, nullptr, nullptr, nullptr, 0, 0);
+                                                     nullptr, nullptr, nullptr, nullptr, 0, 0, phi, ldphi);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
                                int64_t l, int64_t s, int64_t m, int64_t nparts, const double *alpha,
                                const double *beta, double *scale, unsigned long long *gfx, double *grad,
-                               const SparseIndep *indep, cudaStream_t st) {
+                               const SparseIndep *indep, const float *phi, int64_t ldphi, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(gfx, 0, (size_t)m * sizeof(unsigned long long), st);
     if (e != cudaSuccess) return e;
     {
@@ -427,10 +452,12 @@ cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *
         LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
         if (indep)
             k_sparse<1, true><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, nullptr, alpha, beta, scale,
-                                                        gfx, indep->sup, indep->G, indep->ldg, indep->n);
+                                                        gfx, indep->sup, indep->G, indep->ldg, indep->n,
+                                                        const_cast<float *>(phi), ldphi);
         else
             k_sparse<1, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, nullptr, alpha, beta,
-                                                         scale, gfx, nullptr, nullptr, 0, 0);
+                                                         scale, gfx, nullptr, nullptr, 0, 0, const_cast<float *>(phi),
+                                                         ldphi);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     int blocks = (int)cdiv(m, 256);
