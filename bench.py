@@ -51,8 +51,9 @@ def parse():
     ap.add_argument("--s", type=int, default=None)
     ap.add_argument("--fp32-steps", type=int, default=2, help="timed steps of the plain FP32 form (0 = skip)")
     ap.add_argument("--step", default="fused", choices=["fused", "two-call"],
-                    help="fused: iqp_expval_value_and_grad (one phase pass); two-call: iqp_expval + iqp_expval_grad, "
-                         "as autograd runs them (Phi recomputed); the other form is timed too")
+                    help="fused: iqp_expval_value_and_grad (one phase pass); two-call: the estimates, then the "
+                         "gradient, as autograd runs them (Phi kept between the calls where the precision allows, "
+                         "else recomputed); the other form is timed too")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-rows", action="store_true", help="skip the bitflip and MMD per-call timings")
     ap.add_argument("--cpu-sample-l", type=int, default=512)
@@ -476,8 +477,25 @@ def main():
     P = ctypes.c_void_p
     st = P(stream.cuda_stream)
 
+    keep = prec in api.KEEP_PHI
+    phi = torch.empty((l, api.phi_ld(s)) if keep else (1, 64), dtype=torch.float32, device=dev)
+
     def two_call_step(precision, Gd=G, Ad=A, Zd=Z, th=theta, al=alpha, evd=ev, sed=se, gd=grad):
-        # what autograd runs: iqp_expval, then iqp_expval_grad (Phi recomputed)
+        # what autograd runs: the estimates, then the gradient from a second
+        # call; Phi kept between them where the precision supports it
+        # (iqp_expval_keep_phi + iqp_expval_grad_from_phi), else recomputed
+        # (iqp_expval + iqp_expval_grad)
+        if keep and precision in api.KEEP_PHI:
+            _lib.check(lib.iqp_expval_keep_phi(n, P(Gd.data_ptr()), m, Gd.shape[1], P(Ad.data_ptr()), l, Ad.shape[1],
+                                               P(Zd.data_ptr()), s, Zd.shape[1], P(th.data_ptr()), precision,
+                                               P(evd.data_ptr()), P(sed.data_ptr()), P(phi.data_ptr()), phi.shape[1],
+                                               P(ws.data_ptr()), ws.numel(), st), "iqp_expval_keep_phi")
+            _lib.check(lib.iqp_expval_grad_from_phi(n, P(Gd.data_ptr()), m, Gd.shape[1], P(Ad.data_ptr()), l,
+                                                    Ad.shape[1], P(Zd.data_ptr()), s, Zd.shape[1], P(th.data_ptr()),
+                                                    P(al.data_ptr()), None, precision, P(phi.data_ptr()),
+                                                    phi.shape[1], P(gd.data_ptr()), P(ws.data_ptr()), ws.numel(),
+                                                    st), "iqp_expval_grad_from_phi")
+            return
         _lib.check(lib.iqp_expval(n, P(Gd.data_ptr()), m, Gd.shape[1], P(Ad.data_ptr()), l, Ad.shape[1],
                                   P(Zd.data_ptr()), s, Zd.shape[1], P(th.data_ptr()), precision, P(evd.data_ptr()),
                                   P(sed.data_ptr()), P(ws.data_ptr()), ws.numel(), st), "iqp_expval")

@@ -170,7 +170,8 @@ iqp_status iqp_expval_noalloc(int64_t n, const uint64_t *G, int64_t m, int64_t l
  *   grad[j] = sum_a sum_i sin Phi(a,z_i) (alpha[a] + beta[a] cos Phi(a,z_i))
  *             * 2 [g_j.a odd] (1 - 2 [g_j.z_i odd]).
  * For L = sum_a w_a expval[a] pass alpha[a] = -w_a/s and beta = NULL.
- * Phi is recomputed tile by tile, never stored. alpha: float64[l] (device),
+ * Phi is recomputed tile by tile, never stored (iqp_expval_keep_phi and
+ * iqp_expval_grad_from_phi keep it instead). alpha: float64[l] (device),
  * beta: float64[l] or NULL. grad: float64[m], overwritten.
  * ws: iqp_workspace_bytes(IQP_OP_EXPVAL_GRAD, ...). */
 iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
@@ -179,6 +180,34 @@ iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                            const float *theta, const double *alpha, const double *beta,
                            iqp_precision prec, double *grad,
                            void *ws, size_t ws_bytes, void *stream);
+
+/* The forward/backward pair of autograd (Sec. 2.4) without a second phase
+ * pass. iqp_expval_keep_phi is iqp_expval that also writes Phi(a, z_i) into
+ * phi; iqp_expval_grad_from_phi is iqp_expval_grad that forms
+ * W = sin Phi (alpha + beta cos Phi) from that phi instead of recomputing
+ * Phi (the same W bit for bit, so the same gradient).
+ * phi: l x ldphi float32 on the device, caller-owned, 16-byte aligned,
+ * ldphi >= s and a multiple of 64; the order of the samples within a row is
+ * the precision's own, so phi is meaningful only to iqp_expval_grad_from_phi
+ * with the same n, G, A, Z, theta and prec (not re-checked). The gradient
+ * call only reads phi.
+ * prec: IQP_SPLIT_BF16, IQP_SPARSE_FP32 or IQP_LOWORDER_FP32
+ * (IQP_ERR_UNSUPPORTED for IQP_FP32). Errors: phi NULL, ldphi < s or not a
+ * multiple of 64 -> IQP_ERR_ARG; phi not 16-byte aligned -> IQP_ERR_ALIGN.
+ * ws: iqp_workspace_bytes(IQP_OP_EXPVAL, ...) for the first,
+ * iqp_workspace_bytes(IQP_OP_EXPVAL_GRAD, ...) for the second. */
+iqp_status iqp_expval_keep_phi(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                               const uint64_t *A, int64_t l, int64_t lda,
+                               const uint64_t *Z, int64_t s, int64_t ldz,
+                               const float *theta, iqp_precision prec,
+                               double *expval, double *std_err, float *phi, int64_t ldphi,
+                               void *ws, size_t ws_bytes, void *stream);
+iqp_status iqp_expval_grad_from_phi(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
+                                    const uint64_t *A, int64_t l, int64_t lda,
+                                    const uint64_t *Z, int64_t s, int64_t ldz,
+                                    const float *theta, const double *alpha, const double *beta,
+                                    iqp_precision prec, const float *phi, int64_t ldphi, double *grad,
+                                    void *ws, size_t ws_bytes, void *stream);
 
 /* Estimates and gradient in one call, for a loss whose gradient coefficients
  * alpha, beta (as in iqp_expval_grad) are known before the estimates, e.g.

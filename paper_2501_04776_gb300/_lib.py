@@ -33,6 +33,8 @@ SIGNATURES = {
     "iqp_bitflip_expval": (_int, [_i64] + _MAT * 2 + [_p, _p, _p, _sz, _p]),
     "iqp_bitflip_grad": (_int, [_i64] + _MAT * 2 + [_p, _p, _p, _p, _sz, _p]),
     "iqp_expval_value_and_grad": (_int, [_i64] + _MAT * 3 + [_p, _p, _p, _int, _p, _p, _p, _p, _sz, _p]),
+    "iqp_expval_keep_phi": (_int, [_i64] + _MAT * 3 + [_p, _int, _p, _p, _p, _i64, _p, _sz, _p]),
+    "iqp_expval_grad_from_phi": (_int, [_i64] + _MAT * 3 + [_p, _p, _p, _int, _p, _i64, _p, _p, _sz, _p]),
     "iqp_expval_indep": (_int, [_i64] + _MAT * 3 + [_p, _p, _p, _p, _sz, _p]),
     "iqp_expval_indep_grad": (_int, [_i64] + _MAT * 3 + [_p, _p, _p, _p, _p, _sz, _p]),
     "iqp_expand_params": (_int, [_p, _i64, _p, _p, _i64, _p]),

@@ -181,30 +181,93 @@ def expval_value_and_grad(n, theta, G, A, Z, alpha, beta=None, precision="split_
     return ev, se, grad
 
 
+# Precisions whose statistics pass can keep Phi for the gradient pass.
+KEEP_PHI = (SPLIT_BF16, SPARSE_FP32, LOWORDER_FP32)
+
+
+def phi_ld(s: int) -> int:
+    """Smallest row stride (float32 elements) of a kept Phi for s samples."""
+    return (s + 63) // 64 * 64
+
+
+def expval_keep_phi_raw(n, theta, G, A, Z, precision="split_bf16"):
+    """(expval, std_err, phi): iqp_expval that also keeps Phi (l x phi_ld(s)
+    float32, in the precision's own sample order) for expval_grad_from_phi.
+    No autograd."""
+    for t, nm in ((G, "G"), (A, "A"), (Z, "Z")):
+        _bits(t, nm)
+    th = _theta32(theta)
+    m, l, s = G.shape[0], A.shape[0], Z.shape[0]
+    prec = precision_code(precision)
+    lib = _lib.load()
+    ws = _WS.get(lib.iqp_workspace_bytes(OP_EXPVAL, n, m, l, s, 0, prec), G.device)
+    ev = torch.empty(l, dtype=torch.float64, device=G.device)
+    se = torch.empty(l, dtype=torch.float64, device=G.device)
+    ld = phi_ld(s)
+    phi = torch.empty((l, ld), dtype=torch.float32, device=G.device)
+    check(lib.iqp_expval_keep_phi(n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(Z), s, Z.shape[1], _ptr(th),
+                                  prec, _ptr(ev), _ptr(se), _ptr(phi), ld, _ptr(ws), ws.numel(),
+                                  ctypes.c_void_p(_stream(G.device))), "iqp_expval_keep_phi")
+    return ev, se, phi
+
+
+def expval_grad_from_phi(n, theta, G, A, Z, phi, alpha, beta=None, precision="split_bf16") -> torch.Tensor:
+    """expval_grad with W formed from a Phi that expval_keep_phi_raw kept for
+    the same inputs and precision (no second phase pass; same result)."""
+    for t, nm in ((G, "G"), (A, "A"), (Z, "Z")):
+        _bits(t, nm)
+    th = _theta32(theta)
+    m, l, s = G.shape[0], A.shape[0], Z.shape[0]
+    prec = precision_code(precision)
+    if not (phi.is_cuda and phi.dtype == torch.float32 and phi.dim() == 2 and phi.is_contiguous()
+            and phi.shape[0] == l):
+        raise ValueError("phi must be the contiguous l x ld float32 CUDA tensor expval_keep_phi_raw returned")
+    al = alpha.detach().to(device=G.device, dtype=torch.float64).contiguous()
+    be = None if beta is None else beta.detach().to(device=G.device, dtype=torch.float64).contiguous()
+    lib = _lib.load()
+    ws = _WS.get(lib.iqp_workspace_bytes(OP_EXPVAL_GRAD, n, m, l, s, 0, prec), G.device)
+    grad = torch.empty(m, dtype=torch.float64, device=G.device)
+    check(lib.iqp_expval_grad_from_phi(n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(Z), s, Z.shape[1],
+                                       _ptr(th), _ptr(al), _ptr(be), prec, _ptr(phi), phi.shape[1], _ptr(grad),
+                                       _ptr(ws), ws.numel(), ctypes.c_void_p(_stream(G.device))),
+          "iqp_expval_grad_from_phi")
+    return grad
+
+
 class _ExpvalFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, theta, G, A, Z, n, precision):
-        ev, se = expval_raw(n, theta, G, A, Z, precision)
-        ctx.save_for_backward(theta, G, A, Z)
+    def forward(ctx, theta, G, A, Z, n, precision, keep_phi):
+        phi = None
+        if keep_phi and ctx.needs_input_grad[0] and precision_code(precision) in KEEP_PHI:
+            ev, se, phi = expval_keep_phi_raw(n, theta, G, A, Z, precision)
+        else:
+            ev, se = expval_raw(n, theta, G, A, Z, precision)
+        ctx.save_for_backward(theta, G, A, Z, phi)
         ctx.n, ctx.precision = n, precision
         ctx.mark_non_differentiable(se)
         return ev, se
 
     @staticmethod
     def backward(ctx, g_ev, g_se):
-        theta, G, A, Z = ctx.saved_tensors
+        theta, G, A, Z, phi = ctx.saved_tensors
         if g_ev is None:
-            return (None,) * 6
+            return (None,) * 7
         s = Z.shape[0]
         alpha = -g_ev.to(torch.float64) / s
-        grad = expval_grad(ctx.n, theta, G, A, Z, alpha, None, ctx.precision)
-        return grad.to(theta.dtype), None, None, None, None, None
+        if phi is not None:
+            grad = expval_grad_from_phi(ctx.n, theta, G, A, Z, phi, alpha, None, ctx.precision)
+        else:
+            grad = expval_grad(ctx.n, theta, G, A, Z, alpha, None, ctx.precision)
+        return grad.to(theta.dtype), None, None, None, None, None, None
 
 
-def expval(theta, G, A, Z, n: int, precision="split_bf16"):
+def expval(theta, G, A, Z, n: int, precision="split_bf16", keep_phi=True):
     """Monte-Carlo <Z_a> estimates and standard errors (float64), differentiable
-    in theta (std_err is not)."""
-    return _ExpvalFn.apply(theta, G, A, Z, n, precision)
+    in theta (std_err is not). With keep_phi (split BF16, row-sparse and
+    low-order forms) the forward keeps Phi (4 l s bytes, held until the
+    backward) so the backward forms W from it instead of recomputing Phi;
+    keep_phi=False holds only the inputs and recomputes."""
+    return _ExpvalFn.apply(theta, G, A, Z, n, precision, keep_phi)
 
 
 def mmd_loss_raw(n, theta, G, A, Z, X, precision="split_bf16", unbiased=True, with_grad=False, sqrt_loss=False,
@@ -255,9 +318,10 @@ class _MmdFn(torch.autograd.Function):
 
 def mmd_loss(theta, G, A, Z, X, n: int, precision="split_bf16", unbiased=True, sqrt_loss=False, indep=False):
     """MMD^2 estimate (float64 scalar tensor), differentiable in theta: the loss
-    and its gradient come from one library call (the backward recomputes Phi
-    tile by tile inside it). sqrt_loss returns sqrt(max(MMD^2, 0)); indep uses
-    one sample batch per observable (Z with l * s rows)."""
+    and its gradient come from one library call (its statistics pass keeps Phi
+    for the gradient pass; the plain FP32 form and independent batches
+    recompute it). sqrt_loss returns sqrt(max(MMD^2, 0)); indep uses one
+    sample batch per observable (Z with l * s rows)."""
     return _MmdFn.apply(theta, G, A, Z, X, n, precision, unbiased, sqrt_loss, indep)
 
 

@@ -66,12 +66,13 @@ cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t l
                               cudaStream_t st);
 cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                             const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, double2 *part,
-                            int64_t nparts, float *phi_out, uint32_t *status, cudaStream_t st);
+                            int64_t nparts, float *phi, int64_t ldphi, uint32_t *status, cudaStream_t st);
 cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
                            const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
                            float *W, float *V, double *H, double *gsp, unsigned long long *Kfx, double *grad,
-                           __nv_bfloat16 *split, bool phi_ready, uint32_t *status, cudaStream_t st);
+                           __nv_bfloat16 *split, const float *phi, int64_t ldphi, uint32_t *status,
+                           cudaStream_t st);
 cudaError_t launch_bitflip_gates(const float *theta, int64_t m, int64_t mpad, double *c, double *t, cudaStream_t st);
 cudaError_t launch_bitflip_rows(const uint64_t *PA, int64_t ldp, int64_t l, const double *c, double *expval,
                                 cudaStream_t st);
@@ -146,7 +147,9 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     // beta come between). The low-order form keeps it in its W buffer.
     p.off_phi = (op == IQP_OP_MMD_LOSS_GRAD && (prec == IQP_SPLIT_BF16 || prec == IQP_SPARSE_FP32)) ? take(l * p.ldw * 4)
                                                                                                 : 0;
-    p.store_phi = false;
+    p.phi = nullptr;
+    p.ldphi = 0;
+    p.phi_out = p.phi_in = false;
     // Last, and optional: the split-tile scratch of the tensor-core phase (a
     // workspace that ends before it runs every phase tile whole).
     p.off_skp = 0;
@@ -334,13 +337,13 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
     } else if (p.prec == IQP_LOWORDER_FP32) {
         IQP_TRY(launch_lo_stats(p.A, p.lda, p.n, p.l, at<uint64_t>(ws, p.off_pzt), p.ldzt, at<float>(ws, p.off_lo_m),
                                 p.ldw, at<float>(ws, p.off_lo_c), p.ldc, p.s, part, p.nparts,
-                                p.store_phi ? at<float>(ws, p.off_w) : nullptr, at<uint32_t>(ws, p.off_status), st));
+                                p.phi_out ? p.phi : nullptr, p.ldphi, at<uint32_t>(ws, p.off_status), st));
     } else if (p.prec == IQP_SPARSE_FP32) {
         const SparseIndep ind{at<int4>(ws, p.off_sup), p.G, p.ldg, p.n};
         IQP_TRY(launch_sparse_stats(at<uint64_t>(ws, p.off_pa), p.ldp,
                                     at<uint64_t>(ws, p.indep ? p.off_zt : p.off_pzt), p.ldzt, at<float>(ws, p.off_c),
                                     p.l, p.s, part, p.nparts, p.indep ? &ind : nullptr,
-                                    p.store_phi ? at<float>(ws, p.off_phi) : nullptr, p.ldw, st));
+                                    p.phi_out ? p.phi : nullptr, p.ldphi, st));
     } else {
         IQP_TRY(launch_phase_simt(0, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pz), p.ldp,
                                   at<float>(ws, p.off_c), p.l, p.s, p.m, part, p.nparts, nullptr, nullptr, nullptr, 0,
@@ -360,7 +363,7 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
                                at<uint64_t>(ws, p.off_rt), p.ldlt, at<float>(ws, p.off_w), at<float>(ws, p.off_lo_v),
                                at<double>(ws, p.off_lo_h), at<double>(ws, p.off_lo_gs),
                                at<unsigned long long>(ws, p.off_gpart), grad, at<__nv_bfloat16>(ws, p.off_lo_a),
-                               p.store_phi, at<uint32_t>(ws, p.off_status), st));
+                               p.phi_in ? p.phi : nullptr, p.ldphi, at<uint32_t>(ws, p.off_status), st));
         return IQP_OK;
     }
     if (p.prec == IQP_SPARSE_FP32) {
@@ -369,13 +372,12 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
         IQP_TRY(launch_sparse_grad(at<uint64_t>(ws, p.off_pa), p.ldp,
                                    at<uint64_t>(ws, p.indep ? p.off_zt : p.off_pzt), p.ldzt, at<float>(ws, p.off_c),
                                    p.l, p.s, p.m, p.nparts, alpha, beta, reinterpret_cast<double *>(gfx + p.m), gfx,
-                                   grad, p.indep ? &ind : nullptr, p.store_phi ? at<float>(ws, p.off_phi) : nullptr,
-                                   p.ldw, st));
+                                   grad, p.indep ? &ind : nullptr, p.phi_in ? p.phi : nullptr, p.ldphi, st));
         return IQP_OK;
     }
     if (p.prec == IQP_SPLIT_BF16) {
         iqp_status why = IQP_OK;
-        if (p.store_phi) {
+        if (p.phi_in) {
             IQP_TRY(launch_w_from_phi(p, ws, alpha, beta, st));
         } else if (launch_phase_tc(1, p, ws, alpha, beta, st, &why) != cudaSuccess) {
             return why != IQP_OK ? why : IQP_ERR_CUDA;
@@ -418,7 +420,11 @@ iqp_status mmd_core(int op, int64_t n, const uint64_t *G, int64_t m, int64_t ldg
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
     double *S1 = at<double>(ws, p.off_s12), *S2 = S1 + l;
-    p.store_phi = g && (p.prec == IQP_LOWORDER_FP32 || p.off_phi != 0);
+    if (g && (p.prec == IQP_LOWORDER_FP32 || p.off_phi != 0)) {  // Phi kept for the gradient pass
+        p.phi = at<float>(ws, p.prec == IQP_LOWORDER_FP32 ? p.off_w : p.off_phi);
+        p.ldphi = p.ldw;
+        p.phi_out = p.phi_in = true;
+    }
     if ((rc = forward_stats(p, ws, nullptr, nullptr, S1, S2, st)) != IQP_OK) return rc;
     int64_t *T = at<int64_t>(ws, p.off_T);
     IQP_TRY(launch_parity_sum(n, A, l, lda, X, N, ldx, T, st));
@@ -529,6 +535,61 @@ iqp_status iqp_expval_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
     return backward(p, ws, alpha, beta, grad, st);
 }
 
+// Arguments of a caller-owned kept Phi: l x ldphi FP32, ldphi a multiple of
+// 64 and >= s, 16-byte aligned; precisions with a Phi-keeping statistics pass.
+static iqp_status check_phi(const float *phi, int64_t ldphi, int64_t s, iqp_precision prec) {
+    if (phi == nullptr || ldphi < s || ldphi % 64 != 0) return IQP_ERR_ARG;
+    if (!aligned(phi, 16)) return IQP_ERR_ALIGN;
+    if (prec != IQP_SPLIT_BF16 && prec != IQP_SPARSE_FP32 && prec != IQP_LOWORDER_FP32) return IQP_ERR_UNSUPPORTED;
+    return IQP_OK;
+}
+
+iqp_status iqp_expval_keep_phi(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                               int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                               iqp_precision prec, double *expval, double *std_err, float *phi, int64_t ldphi,
+                               void *ws, size_t ws_bytes, void *stream) {
+    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    if (rc != IQP_OK) return rc;
+    if ((rc = check_phi(phi, ldphi, s, prec)) != IQP_OK) return rc;
+    if ((expval && !aligned(expval, 8)) || (std_err && !aligned(std_err, 8))) return IQP_ERR_ALIGN;
+    Plan p = make_plan(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
+    p.G = G;
+    p.ldg = ldg;
+    p.A = A;
+    p.lda = lda;
+    if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
+    p.phi = phi;
+    p.ldphi = ldphi;
+    p.phi_out = true;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
+    return forward_stats(p, ws, expval, std_err, nullptr, nullptr, st);
+}
+
+iqp_status iqp_expval_grad_from_phi(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A,
+                                    int64_t l, int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz,
+                                    const float *theta, const double *alpha, const double *beta, iqp_precision prec,
+                                    const float *phi, int64_t ldphi, double *grad, void *ws, size_t ws_bytes,
+                                    void *stream) {
+    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    if (rc != IQP_OK) return rc;
+    if ((rc = check_phi(phi, ldphi, s, prec)) != IQP_OK) return rc;
+    if (alpha == nullptr || grad == nullptr) return IQP_ERR_ARG;
+    if (!aligned(alpha, 8) || !aligned(grad, 8) || (beta && !aligned(beta, 8))) return IQP_ERR_ALIGN;
+    Plan p = make_plan(IQP_OP_EXPVAL_GRAD, n, m, l, s, 0, prec);
+    p.G = G;
+    p.ldg = ldg;
+    p.A = A;
+    p.lda = lda;
+    if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
+    p.phi = const_cast<float *>(phi);  // read only: phi_in
+    p.ldphi = ldphi;
+    p.phi_in = true;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
+    return backward(p, ws, alpha, beta, grad, st);
+}
+
 iqp_status iqp_expval_value_and_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A,
                                      int64_t l, int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz,
                                      const float *theta, const double *alpha, const double *beta, iqp_precision prec,
@@ -549,7 +610,11 @@ iqp_status iqp_expval_value_and_grad(int64_t n, const uint64_t *G, int64_t m, in
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
     if (prec != IQP_SPLIT_BF16) {
-        p.store_phi = prec == IQP_LOWORDER_FP32;  // W from the kept Phi, no second phase pass
+        if (prec == IQP_LOWORDER_FP32) {  // W from the kept Phi (in the W buffer), no second phase pass
+            p.phi = at<float>(ws, p.off_w);
+            p.ldphi = p.ldw;
+            p.phi_out = p.phi_in = true;
+        }
         if ((rc = forward_stats(p, ws, expval, std_err, nullptr, nullptr, st)) != IQP_OK) return rc;
         return backward(p, ws, alpha, beta, grad, st);
     }

@@ -43,8 +43,13 @@ struct Plan {
     // low-order form: C (+ d), M = C S, V, H, single-gate partials; ldc floats per row of C and H
     size_t off_lo_c, off_lo_m, off_lo_v, off_lo_h, off_lo_gs, off_lo_a;
     size_t off_skp;  // split BF16: partial accumulators and counters of split phase tiles (0 if none)
-    size_t off_phi;  // split BF16 MMD gradient: Phi (l x ldw fp32) from the statistics pass (0 if none)
-    bool store_phi;  // the statistics pass keeps Phi for the gradient pass that follows in the same call
+    size_t off_phi;  // MMD gradient (split BF16, row-sparse): room for Phi, l x ldw fp32 (0 if none)
+    // Kept Phi (l x ldphi fp32, ldphi a multiple of 64 >= s; the layout is the
+    // precision's own): phi_out = the statistics pass writes it, phi_in = the
+    // gradient pass forms W from it instead of recomputing Phi.
+    float *phi;
+    int64_t ldphi;
+    bool phi_out, phi_in;
     int64_t ldc;
     bool indep;     // one sample batch per observable (Z has l * s rows)
     const uint64_t *G;  // generators (read by the independent-batch kernels)

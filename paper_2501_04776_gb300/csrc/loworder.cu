@@ -462,9 +462,9 @@ __device__ __forceinline__ float flip_if(float v, uint32_t y) {
 }
 
 // MODE 0: (sum cos, sum (cos - mean)^2) per (observable, 256 samples) into
-// part, and Phi itself into W (columns < lds) when W is not null (a gradient
-// pass follows). MODE 1: W[a][i] = sin Phi (alpha_a + beta_a cos Phi), zero
-// for i >= s.
+// part, and Phi itself into phi (row stride ldphi >= lds, columns < lds) when
+// phi is not null (a gradient pass follows). MODE 1: W[a][i] = sin Phi
+// (alpha_a + beta_a cos Phi), zero for i >= s.
 // The pair term visits only the pairs of Q_a that carry a generator (C_qr is
 // zero on the others). CTA (a, g) takes sample blocks kPGroup g ..
 // kPGroup g + kPGroup - 1. For |Q_a| <= kQ4 a thread owns four consecutive
@@ -480,7 +480,8 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
                                                    const float *__restrict__ d, const unsigned long long *__restrict__ E,
                                                    int64_t lde, int64_t s, int64_t nparts, double2 *__restrict__ part,
                                                    const double *__restrict__ alpha, const double *__restrict__ beta,
-                                                   float *__restrict__ W, uint32_t *__restrict__ status) {
+                                                   float *__restrict__ W, float *__restrict__ phi, int64_t ldphi,
+                                                   uint32_t *__restrict__ status) {
     [[maybe_unused]] uint32_t *status_dbg = status;
     __shared__ LoShared sh;
     __shared__ const float *mrow[kQ4];  // M + Q[t] lds (four-block form)
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
                 __syncthreads();
                 np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
             }
-            const float phi[4] = {p0 - 2.f * q0, p1 - 2.f * q1, p2 - 2.f * q2, p3 - 2.f * q3};
+            const float ph[4] = {p0 - 2.f * q0, p1 - 2.f * q1, p2 - 2.f * q2, p3 - 2.f * q3};
             bool valid[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k) valid[k] = i0 + k < s && blk < b1;
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
                 float cv[4], S1 = 0.f;
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
-                    cv[k] = valid[k] ? cosf(phi[k]) : 0.f;
+                    cv[k] = valid[k] ? cosf(ph[k]) : 0.f;
                     S1 += cv[k];
                 }
                 // Block b's sums: its two warps' shuffle sums, in warp order.
@@ -574,14 +575,14 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
                 __syncthreads();
                 if ((tid & 63) == 0 && blk < b1)
                     part[a * nparts + blk] = make_double2((double)S, (double)(sh.redf[w] + sh.redf[w + 1]));
-                if (W != nullptr && i0 < lds && blk < b1)
-                    *reinterpret_cast<float4 *>(W + a * lds + i0) = make_float4(phi[0], phi[1], phi[2], phi[3]);
+                if (phi != nullptr && i0 < lds && blk < b1)
+                    *reinterpret_cast<float4 *>(phi + a * ldphi + i0) = make_float4(ph[0], ph[1], ph[2], ph[3]);
             } else if (i0 < lds && blk < b1) {
                 float o[4];
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     float sn, cn;
-                    sincosf(phi[k], &sn, &cn);
+                    sincosf(ph[k], &sn, &cn);
                     o[k] = valid[k] ? sn * (al + be * cn) : 0.f;
                 }
                 *reinterpret_cast<float4 *>(W + a * lds + i0) = make_float4(o[0], o[1], o[2], o[3]);
@@ -594,12 +595,12 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
         const int64_t i = blk * kBlk + tid;
         const bool valid = i < s;
         const int64_t ic = valid ? i : s - 1;
-        float phi = 0.f;
+        float ph = 0.f;
         for (int t = 0; t < nq; ++t) {
             const int q = sh.Q[t];
             if (!LO_OK(q >= 0 && q < n && ic >= 0 && ic < lds, 7)) continue;
             const float v = d[q] + M[(int64_t)q * lds + ic];
-            phi += ((sh.bits[t][w] >> bit) & 1u) ? -v : v;
+            ph += ((sh.bits[t][w] >> bit) & 1u) ? -v : v;
         }
         float pairs = 0.f;
         if (!complete && blk != bstart) {
@@ -618,19 +619,19 @@ __global__ void __launch_bounds__(kBlk) k_lo_phase(const uint64_t *__restrict__ 
             __syncthreads();
             np = lo_fill_pairs(sh, nq, &c0, E, lde, C, ldc, n, status);
         }
-        phi -= 2.f * pairs;
+        ph -= 2.f * pairs;
         if (MODE == 0) {
-            const float cv = valid ? cosf(phi) : 0.f;
+            const float cv = valid ? cosf(ph) : 0.f;
             const float S = block_sum_f(cv, sh.redf);
             const int64_t nb = s - blk * kBlk < kBlk ? s - blk * kBlk : kBlk;
             const float mean = S / (float)nb;
             const float dv = cv - mean;
             const float M2 = block_sum_f(valid ? dv * dv : 0.f, sh.redf);
             if (tid == 0) part[a * nparts + blk] = make_double2((double)S, (double)M2);
-            if (W != nullptr && i < lds) W[a * lds + i] = phi;
+            if (phi != nullptr && i < lds) phi[a * ldphi + i] = ph;
         } else {
             float sn, cn;
-            sincosf(phi, &sn, &cn);
+            sincosf(ph, &sn, &cn);
             if (i < lds) W[a * lds + i] = valid ? sn * (al + be * cn) : 0.f;
         }
     }
@@ -729,19 +730,20 @@ __global__ void __launch_bounds__(kBlk) k_lo_v(const uint64_t *__restrict__ AT, 
     }
 }
 
-// W[a][i] = sin Phi (alpha_a + beta_a cos Phi) in place over the Phi the
-// statistics pass kept in W (zero for i >= s), four samples per thread: the
-// arithmetic of k_lo_phase<1>, without recomputing Phi.
-__global__ void __launch_bounds__(256) k_lo_w(float *__restrict__ W, int64_t lds, int64_t l, int64_t s,
-                                             const double *__restrict__ alpha, const double *__restrict__ beta) {
+// W[a][i] = sin Phi (alpha_a + beta_a cos Phi) (zero for i >= s) from the
+// Phi the statistics pass kept (l x ldphi; phi may be W itself: each
+// element is read before it is written, by the same thread), four samples
+// per thread: the arithmetic of k_lo_phase<1>, without recomputing Phi.
+__global__ void __launch_bounds__(256) k_lo_w(const float *phi, int64_t ldphi, float *W, int64_t lds, int64_t l,
+                                             int64_t s, const double *__restrict__ alpha,
+                                             const double *__restrict__ beta) {
     const int64_t per_row = lds / 4;
     const int64_t total = l * per_row;
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t a = g / per_row, i0 = (g - a * per_row) * 4;
         const float al = (float)alpha[a];
         const float be = beta ? (float)beta[a] : 0.f;
-        float4 *p = reinterpret_cast<float4 *>(W + a * lds + i0);
-        const float4 f = *p;
+        const float4 f = *reinterpret_cast<const float4 *>(phi + a * ldphi + i0);
         const float v[4] = {f.x, f.y, f.z, f.w};
         float o[4];
 #pragma unroll
@@ -750,7 +752,7 @@ __global__ void __launch_bounds__(256) k_lo_w(float *__restrict__ W, int64_t lds
             sincosf(v[k], &sn, &cn);
             o[k] = i0 + k < s ? sn * (al + be * cn) : 0.f;
         }
-        *p = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4 *>(W + a * lds + i0) = make_float4(o[0], o[1], o[2], o[3]);
     }
 }
 
@@ -984,13 +986,13 @@ cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t l
 
 cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                             const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, double2 *part,
-                            int64_t nparts, float *phi_out, uint32_t *status, cudaStream_t st) {
+                            int64_t nparts, float *phi, int64_t ldphi, uint32_t *status, cudaStream_t st) {
     LaunchScope ls(IQP_KERNEL_LOWORDER, st);
     const float *d = C + n * ldc;
     const unsigned long long *E = reinterpret_cast<const unsigned long long *>(d + ldc);
     k_lo_phase<0><<<dim3((unsigned)l, (unsigned)cdiv(nparts, kPGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d, E,
                                                                        lo_lde(n), s, nparts, part, nullptr, nullptr,
-                                                                       phi_out, status);
+                                                                       nullptr, phi, ldphi, status);
     return cudaGetLastError();
 }
 
@@ -1000,7 +1002,8 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
                            const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, int64_t m,
                            const int4 *sup, const double *alpha, const double *beta, uint64_t *AT, int64_t ldlt,
                            float *W, float *V, double *H, double *gsp, unsigned long long *Kfx, double *grad,
-                           __nv_bfloat16 *split, bool phi_ready, uint32_t *status, cudaStream_t st) {
+                           __nv_bfloat16 *split, const float *phi, int64_t ldphi, uint32_t *status,
+                           cudaStream_t st) {
     const int64_t nblk = cdiv(s, kBlk);
     double *scale = reinterpret_cast<double *>(Kfx + n * n);
     const float *d = C + n * ldc;
@@ -1010,14 +1013,14 @@ cudaError_t launch_lo_grad(const uint64_t *A, int64_t lda, int64_t n, int64_t l,
     if (e != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(Kfx, 0, (size_t)n * n * sizeof(unsigned long long), st)) != cudaSuccess) return e;
     if ((e = launch_fixed_scale(alpha, beta, l, s, scale, st)) != cudaSuccess) return e;
-    if (phi_ready) {  // W holds Phi from the statistics pass
+    if (phi != nullptr) {  // Phi kept by the statistics pass (possibly in W itself)
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_w<<<grid_1d(l * (lds / 4)), 256, 0, st>>>(W, lds, l, s, alpha, beta);
+        k_lo_w<<<grid_1d(l * (lds / 4)), 256, 0, st>>>(phi, ldphi, W, lds, l, s, alpha, beta);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
         k_lo_phase<1><<<dim3((unsigned)l, (unsigned)cdiv(nblk, kPGroup)), kBlk, 0, st>>>(A, lda, n, ZT, ldzt, M, lds, C, ldc, d,
-                                                                         E, lde, s, nblk, nullptr, alpha, beta, W,
+                                                                         E, lde, s, nblk, nullptr, alpha, beta, W, nullptr, 0,
                                                                          status);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }

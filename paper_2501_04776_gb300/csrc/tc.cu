@@ -254,11 +254,13 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     return lo | (hi << 16);
 }
 
-// W = sin Phi (alpha_a + beta_a cos Phi) as BF16 hi/lo from a Phi the
-// statistics pass kept (l x ldw FP32, columns < s), with the arithmetic of
-// the recompute epilogue, so W is the same bit for bit. Four samples per
-// thread; columns >= s get zeros (the gradient's tensor map ends at s).
-__global__ void __launch_bounds__(256) k_w_from_phi(const float *__restrict__ phi, int64_t ldw, int64_t l, int64_t s,
+// W = sin Phi (alpha_a + beta_a cos Phi) as BF16 hi/lo (l x ldw) from a Phi
+// the statistics pass kept (l x ldphi FP32, columns < s), with the
+// arithmetic of the recompute epilogue, so W is the same bit for bit. Four
+// samples per thread; columns >= s get zeros (the gradient's tensor map ends
+// at s).
+__global__ void __launch_bounds__(256) k_w_from_phi(const float *__restrict__ phi, int64_t ldphi, int64_t ldw,
+                                                    int64_t l, int64_t s,
                                                     const double *__restrict__ alpha,
                                                     const double *__restrict__ beta, __nv_bfloat16 *__restrict__ whi,
                                                     __nv_bfloat16 *__restrict__ wlo) {
@@ -269,7 +271,7 @@ __global__ void __launch_bounds__(256) k_w_from_phi(const float *__restrict__ ph
         if (i0 >= s) continue;
         const float al = (float)alpha[row];
         const float be = beta ? (float)beta[row] : 0.f;
-        const float4 f = *reinterpret_cast<const float4 *>(phi + row * ldw + i0);
+        const float4 f = *reinterpret_cast<const float4 *>(phi + row * ldphi + i0);
         const float v[4] = {f.x, f.y, f.z, f.w};
         uint32_t ph[2], pl[2];
 #pragma unroll
@@ -1099,8 +1101,8 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.ldp32 = 2 * p.ldp;
     a.gpart = nullptr;
     // MODE 0 keeps Phi (FP32, l x ldw) when a gradient pass follows.
-    a.out = (mode == 0 && p.store_phi && p.off_phi != 0) ? static_cast<void *>(at<float>(ws, p.off_phi)) : nullptr;
-    a.ldo = p.ldw;
+    a.out = (mode == 0 && p.phi_out) ? static_cast<void *>(p.phi) : nullptr;
+    a.ldo = p.ldphi;
     a.out_f64 = 0;
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
@@ -1184,7 +1186,7 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
 }
 
 cudaError_t launch_w_from_phi(const Plan &p, void *ws, const double *alpha, const double *beta, cudaStream_t st) {
-    if (p.off_phi == 0 || p.ldw % 4 != 0) return cudaErrorInvalidValue;
+    if (p.phi == nullptr || p.ldw % 4 != 0 || p.ldphi % 4 != 0) return cudaErrorInvalidValue;
     __nv_bfloat16 *whi = at<__nv_bfloat16>(ws, p.off_w);
     __nv_bfloat16 *wlo = whi + p.l * p.ldw;
     const int64_t total = p.l * (p.ldw / 4);
@@ -1193,7 +1195,7 @@ cudaError_t launch_w_from_phi(const Plan &p, void *ws, const double *alpha, cons
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
     LaunchScope ls(IQP_KERNEL_RECOMPUTE_TC, st);
-    k_w_from_phi<<<(unsigned)grid, 256, 0, st>>>(at<float>(ws, p.off_phi), p.ldw, p.l, p.s, alpha, beta, whi, wlo);
+    k_w_from_phi<<<(unsigned)grid, 256, 0, st>>>(p.phi, p.ldphi, p.ldw, p.l, p.s, alpha, beta, whi, wlo);
     return cudaGetLastError();
 }
 

@@ -144,6 +144,31 @@ def test_host_side_argument_errors_of_the_options(lib):
     assert lib.iqp_bitflip_grad(10, G, 4, 2, A, 3, 2, th, None, out, ws, 1 << 30, None) == _lib.ERR_ARG
 
 
+def test_host_side_argument_errors_of_the_kept_phase(lib):
+    """iqp_expval_keep_phi / iqp_expval_grad_from_phi check phi on the host
+    before any launch (no pointer below is dereferenced; the row-sparse form,
+    whose host checks need no GPU)."""
+    from paper_2501_04776_gb300 import _lib
+    G, A, Z, th, out, ws, al, phi = 0x10000, 0x20000, 0x30000, 0x40000, 0x50000, 0x100000, 0x60000, 0x200000
+    n, m, l, s = 10, 4, 3, 100
+
+    def keep(phi=phi, ldphi=128, prec=_lib.SPARSE_FP32):
+        return lib.iqp_expval_keep_phi(n, G, m, 2, A, l, 2, Z, s, 2, th, prec, out, out, phi, ldphi, ws, 1 << 30,
+                                       None)
+
+    def grad(phi=phi, ldphi=128, prec=_lib.SPARSE_FP32, alpha=al):
+        return lib.iqp_expval_grad_from_phi(n, G, m, 2, A, l, 2, Z, s, 2, th, alpha, None, prec, phi, ldphi, out,
+                                            ws, 1 << 30, None)
+
+    for call in (keep, grad):
+        assert call(phi=None) == _lib.ERR_ARG
+        assert call(ldphi=64) == _lib.ERR_ARG          # ldphi < s
+        assert call(ldphi=130) == _lib.ERR_ARG         # not a multiple of 64
+        assert call(phi=0x200008) == _lib.ERR_ALIGN    # not 16-byte aligned
+        assert call(prec=_lib.FP32) == _lib.ERR_UNSUPPORTED
+    assert grad(alpha=None) == _lib.ERR_ARG
+
+
 def test_workspace_sizes_of_the_options(lib):
     from paper_2501_04776_gb300 import _lib
     n, m, l, s = 1000, 100_000, 100, 1000
@@ -153,6 +178,11 @@ def test_workspace_sizes_of_the_options(lib):
     assert lib.iqp_workspace_bytes(_lib.OP_EXPVAL_INDEP_GRAD, n, m, l, s, 0, 0) >= ind + 8 * m
     mmd = lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD_INDEP, n, m, l, s, 50, 0)
     assert mmd > lib.iqp_workspace_bytes(_lib.OP_EXPVAL_INDEP_GRAD, n, m, l, s, 0, 0)
+    # The MMD gradient keeps Phi (l x s FP32) from its statistics pass: beside
+    # W (split BF16) or the fixed-point gradient (row-sparse).
+    for prec, extra in ((_lib.SPLIT_BF16, 8 * l * s), (_lib.SPARSE_FP32, 4 * l * s + 8 * m)):
+        assert lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD, n, m, l, s, 50, prec) - \
+            lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS, n, m, l, s, 50, prec) >= extra
     assert lib.iqp_workspace_bytes(10, n, m, l, s, 0, 0) == 0
 
 

@@ -201,6 +201,47 @@ def test_autograd_linear_loss(api, prec):
     assert not se.requires_grad
 
 
+@pytest.mark.parametrize("prec", ["split_bf16", "sparse_fp32", "loworder_fp32"])
+def test_kept_phase_gives_the_recomputed_results_bit_for_bit(api, prec):
+    """iqp_expval_keep_phi returns iqp_expval's estimates and
+    iqp_expval_grad_from_phi iqp_expval_grad's gradient, bit for bit (W is
+    formed from the kept Phi with the recompute's arithmetic), for a loss
+    with a beta term; autograd with and without keep_phi agrees the same way;
+    both match the oracle."""
+    import torch
+    if prec == "loworder_fp32":
+        rng = I.Rng(31)
+        n, l, s = 40, 70, 333
+        G = I.local_gates_packed(n)
+        th = (0.3 * rng.normal(G.shape[0], 1) / np.sqrt(n)).astype(np.float32)
+        A, Z = I.bernoulli_bits(rng, l, n, 0.2, 2), I.uniform_bits(rng, s, n, 3)
+    else:
+        p = ragged_problem(seed=13, l=140, s=333, m=700)
+        n, G, A, Z, th, l, s = p.n, p.G, p.A, p.Z, p.theta.astype(np.float32), p.l, p.s
+    Gd, Ad, Zd, thd = dev(api, G), dev(api, A), dev(api, Z), th_dev(th)
+    ev0, se0 = api.expval_raw(n, thd, Gd, Ad, Zd, prec)
+    ev1, se1, phi = api.expval_keep_phi_raw(n, thd, Gd, Ad, Zd, prec)
+    assert torch.equal(ev0, ev1) and torch.equal(se0, se1)
+    rng = I.Rng(6)
+    alpha = torch.from_numpy(rng.normal(l, 1) / s).cuda()
+    beta = torch.from_numpy(rng.normal(l, 2) / s).cuda()
+    g0 = api.expval_grad(n, thd, Gd, Ad, Zd, alpha, beta, prec)
+    g1 = api.expval_grad_from_phi(n, thd, Gd, Ad, Zd, phi, alpha, beta, prec)
+    assert torch.equal(g0, g1)
+    want = oracle.expval_grad(n, G, A, Z, th.astype(np.float64), alpha.cpu().numpy(), beta.cpu().numpy())
+    assert rel_l2(g1.cpu().numpy(), want) <= GRAD_RTOL
+    want_ev, _, _, _ = oracle.expval(n, G, A, Z, th.astype(np.float64))
+    assert np.max(np.abs(ev1.cpu().numpy() - want_ev)) <= TOL[prec]
+    w = torch.from_numpy(rng.normal(l, 3)).cuda()
+    grads = []
+    for keep in (True, False):
+        theta = th_dev(th).requires_grad_(True)
+        ev, _ = api.expval(theta, Gd, Ad, Zd, n, prec, keep_phi=keep)
+        ((ev * w).sum() + (ev * ev).sum()).backward()
+        grads.append(theta.grad)
+    assert torch.equal(grads[0], grads[1])
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_grad_central_differences_on_gpu(api, prec):
     """Directional derivative of the GPU estimator by central differences of

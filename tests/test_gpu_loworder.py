@@ -112,6 +112,38 @@ def test_mmd_loss_and_autograd(api):
     assert rel_l2(theta.grad.double().cpu().numpy(), want) <= GRAD_RTOL
 
 
+def test_heavy_observables_take_the_one_sample_form(api):
+    """Observables of 100 to 707 qubits in one launch: supports of at most
+    256 qubits run four samples per thread, larger ones one sample per thread,
+    and the heaviest carry more generator pairs than one pair list holds (the
+    list is rebuilt round by round). Weights 256 and 257 sit on the boundary.
+    Estimates, gradient, and the MMD loss and gradient (Phi kept from the
+    statistics pass) against the oracle; s = 701 leaves a ragged last word."""
+    rng = I.Rng(95)
+    n, m, s = 1200, 5000, 701
+    G = I.random_k_body(rng, m, n, [1, 2], 1)
+    A = np.concatenate([I.bernoulli_bits(rng, 2, n, pa, 2 + k) for k, pa in enumerate((0.1, 0.4, 0.35, 0.6))])
+    edge = np.zeros((2, n), np.uint8)
+    edge[0, :256] = 1
+    edge[1, 3:260] = 1
+    A = np.concatenate([A, I.pack_bits(edge)])
+    weights = I.unpack_bits(A, n).sum(axis=1)
+    assert weights.min() <= 256 < weights.max() and 256 in weights and 257 in weights
+    Z = I.uniform_bits(rng, s, n, 9)
+    X = I.uniform_bits(rng, 40, n, 10)
+    th = (0.05 * rng.normal(m, 3)).astype(np.float32)
+    w = rng.normal(A.shape[0], 4)
+    ev, se, g = run(api, n, G, A, Z, th, w)
+    want_ev, want_se, _, _ = oracle.expval(n, G, A, Z, th.astype(np.float64))
+    assert np.max(np.abs(ev - want_ev)) <= TOL and np.max(np.abs(se - want_se)) <= TOL
+    assert rel_l2(g, oracle.expval_grad(n, G, A, Z, th.astype(np.float64), -w / s)) <= GRAD_RTOL
+    loss, grad = api.mmd_loss_raw(n, th_dev(th), dev(api, G), dev(api, A), dev(api, Z), dev(api, X), LO, True,
+                                  with_grad=True)
+    wl, _, wg = oracle.mmd_loss_ex(n, G, A, Z, X, th.astype(np.float64), True, False, grad=True)
+    assert abs(float(loss) - wl) <= TOL
+    assert rel_l2(grad.cpu().numpy(), wg) <= GRAD_RTOL
+
+
 def test_gradient_is_reproducible(api):
     p = I.mmd_training(seed=12, n=60, l=100, s=800, N=10)
     args = (p.n, th_dev(p.theta * 10), dev(api, p.G), dev(api, p.A), dev(api, p.Z), t64(np.full(p.l, 0.01)), None,
