@@ -212,10 +212,10 @@ iqp_status iqp_expval_grad_from_phi(int64_t n, const uint64_t *G, int64_t m, int
 /* Estimates and gradient in one call, for a loss whose gradient coefficients
  * alpha, beta (as in iqp_expval_grad) are known before the estimates, e.g.
  * L = sum_a w_a <Z_a> with alpha_a = -w_a / s, beta = NULL. Outputs as
- * iqp_expval plus grad[m]. In IQP_SPLIT_BF16 the parities are formed once and
- * a single pass of the phase contraction yields both the statistics and W
- * (no recompute); the other forms run their forward and gradient passes on
- * parities formed once. ws: iqp_workspace_bytes(IQP_OP_EXPVAL_GRAD, ...). */
+ * iqp_expval plus grad[m]. The parities are formed once. In IQP_SPLIT_BF16
+ * and IQP_SPARSE_FP32 a single pass over Phi yields the statistics and W (no
+ * recompute); IQP_LOWORDER_FP32 keeps Phi from its statistics pass for W;
+ * IQP_FP32 recomputes it. ws: iqp_workspace_bytes(IQP_OP_EXPVAL_GRAD, ...). */
 iqp_status iqp_expval_value_and_grad(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                                      const uint64_t *A, int64_t l, int64_t lda,
                                      const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,

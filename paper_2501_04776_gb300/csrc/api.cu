@@ -45,6 +45,10 @@ cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *
                                int64_t l, int64_t s, int64_t m, int64_t nparts, const double *alpha,
                                const double *beta, double *scale, unsigned long long *gfx, double *grad,
                                const SparseIndep *indep, const float *phi, int64_t ldphi, cudaStream_t st);
+cudaError_t launch_sparse_value_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt,
+                                     const float *c, int64_t l, int64_t s, int64_t m, int64_t nparts, double2 *part,
+                                     const double *alpha, const double *beta, double *scale, unsigned long long *gfx,
+                                     double *grad, cudaStream_t st);
 cudaError_t launch_bit_transpose_batched(const uint64_t *in, int64_t batch, int64_t in_rows, int64_t in_cols,
                                          int64_t ld_in, uint64_t *out, int64_t ld_out, cudaStream_t st);
 cudaError_t launch_support_list(const uint64_t *G, int64_t m, int64_t ldg, int64_t n, int4 *sup, cudaStream_t st);
@@ -609,6 +613,15 @@ iqp_status iqp_expval_value_and_grad(int64_t n, const uint64_t *G, int64_t m, in
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if ((rc = prepare(p, ws, G, ldg, A, lda, Z, ldz, theta, st)) != IQP_OK) return rc;
+    if (prec == IQP_SPARSE_FP32) {  // one pass over Phi: statistics, W and the gradient contributions
+        unsigned long long *gfx = at<unsigned long long>(ws, p.off_gpart);
+        double2 *part = at<double2>(ws, p.off_part);
+        IQP_TRY(launch_sparse_value_grad(at<uint64_t>(ws, p.off_pa), p.ldp, at<uint64_t>(ws, p.off_pzt), p.ldzt,
+                                         at<float>(ws, p.off_c), p.l, p.s, p.m, p.nparts, part, alpha, beta,
+                                         reinterpret_cast<double *>(gfx + p.m), gfx, grad, st));
+        IQP_TRY(launch_finalize(part, p.nparts, p.pw, p.l, p.s, expval, std_err, nullptr, nullptr, st));
+        return IQP_OK;
+    }
     if (prec != IQP_SPLIT_BF16) {
         if (prec == IQP_LOWORDER_FP32) {  // W from the kept Phi (in the W buffer), no second phase pass
             p.phi = at<float>(ws, p.off_w);

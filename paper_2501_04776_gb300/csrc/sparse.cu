@@ -254,7 +254,8 @@ struct GradRun {
 // MODE 0: statistics partials, and Phi itself into phi (l x ldphi FP32) when
 // phi is not null (a gradient pass follows). MODE 1: W from Phi (read from
 // phi when not null, else recomputed), then the gradient contributions of
-// every gate of J_a. Independent batches always recompute (keeping Phi there
+// every gate of J_a. MODE 2: both from one Phi (gradient coefficients known
+// in advance), the statistics and W as MODE 0 and MODE 1 form them. Independent batches always recompute (keeping Phi there
 // would push the statistics pass past its register budget).
 // INDEP: PZT holds every observable's transposed samples (n x ldzt words
 // each, observable a at PZT + a n ldzt) and the parities are formed on the fly.
@@ -307,12 +308,13 @@ __global__ void __launch_bounds__(256, 2)
         acc[32 + t] = __uint_as_float((uint32_t)(acc2[t] >> 32));
     }
 
-    if (MODE == 0) {
+    if (MODE == 0 || MODE == 2) {
+        // MODE 2 keeps Phi in acc for W below and takes the cosines twice.
         float sum = 0.f;
 #pragma unroll
         for (int k = 0; k < 64; ++k) {
             const float cv = k < nvalid ? cosf(acc[k]) : 0.f;
-            acc[k] = cv;
+            if (MODE == 0) acc[k] = cv;
             sum += cv;
         }
         double ds = (double)sum;
@@ -323,14 +325,15 @@ __global__ void __launch_bounds__(256, 2)
         float m2 = 0.f;
 #pragma unroll
         for (int k = 0; k < 64; ++k) {
-            const float d = acc[k] - mean;
+            const float d = (MODE == 0 ? acc[k] : (k < nvalid ? cosf(acc[k]) : 0.f)) - mean;
             m2 += k < nvalid ? d * d : 0.f;
         }
         double dm = (double)m2;
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) dm += __shfl_xor_sync(kFull, dm, off);
         if (lane == 0) part[a * nparts + r] = make_double2(ds, dm);
-    } else {
+    }
+    if (MODE != 0) {
         const float al = (float)alpha[a];
         const float be = beta ? (float)beta[a] : 0.f;
 #pragma unroll
@@ -407,6 +410,34 @@ dim3 sparse_grid(int64_t l, int64_t nparts, int *threads) {
 }  // namespace
 
 int64_t sparse_part_samples() { return kWarpSamples; }
+
+// Statistics partials and the gradient from one pass over Phi (shared
+// batches; alpha, beta known before the estimates): k_sparse<2>.
+cudaError_t launch_sparse_value_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt,
+                                     const float *c, int64_t l, int64_t s, int64_t m, int64_t nparts, double2 *part,
+                                     const double *alpha, const double *beta, double *scale, unsigned long long *gfx,
+                                     double *grad, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(gfx, 0, (size_t)m * sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    {
+        LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
+        k_sparse_scale<<<1, 256, 0, st>>>(alpha, beta, l, s, scale);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    {
+        int threads = 0;
+        const dim3 grid = sparse_grid(l, nparts, &threads);
+        LaunchScope ls(IQP_KERNEL_PHASE_SPARSE, st);
+        k_sparse<2, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, alpha, beta, scale, gfx,
+                                                     nullptr, nullptr, 0, 0, nullptr, 0);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    int blocks = (int)cdiv(m, 256);
+    if (blocks > 8192) blocks = 8192;
+    LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
+    k_sparse_grad_out<<<blocks, 256, 0, st>>>(gfx, m, scale, grad);
+    return cudaGetLastError();
+}
 
 // scale (one double) = 2^k with sum_a 2 s (|alpha_a| + |beta_a|) 2^k < 2^61;
 // used by every fixed-point gradient accumulation.

@@ -639,9 +639,11 @@ def test_value_and_grad_matches_oracle(api, prec):
     want = oracle.expval_grad(p.n, p.G, p.A, p.Z, p.theta.astype(np.float64), -w / p.s,
                               beta.cpu().numpy())
     assert rel_l2(g.cpu().numpy(), want) <= GRAD_RTOL
-    # the same numbers as the two separate calls
+    # the same numbers as the two separate calls (W is formed with the same
+    # arithmetic from the same Phi, and every reduction has a fixed order)
     ev2, se2 = gpu_expval(api, p, prec)
     assert np.array_equal(ev.cpu().numpy(), ev2) and np.array_equal(se.cpu().numpy(), se2)
+    assert np.array_equal(g.cpu().numpy(), gpu_grad(api, p, -w / p.s, beta.cpu().numpy(), prec))
 
 
 def test_value_and_grad_full_size(api):
