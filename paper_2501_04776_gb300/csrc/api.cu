@@ -66,8 +66,8 @@ int64_t lo_part_samples();
 int64_t lo_split_elems(int64_t n, int64_t lds);
 cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *Z, int64_t s,
                               int64_t ldz, const float *c, int4 *sup, uint64_t *ZT, int64_t ldzt, float *C,
-                              int64_t ldc, float *M, int64_t lds, __nv_bfloat16 *split, uint32_t *status,
-                              cudaStream_t st);
+                              int64_t ldc, float *M, int64_t lds, __nv_bfloat16 *split, unsigned long long *fx,
+                              uint32_t *status, cudaStream_t st);
 cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,
                             const float *M, int64_t lds, const float *C, int64_t ldc, int64_t s, double2 *part,
                             int64_t nparts, float *phi, int64_t ldphi, uint32_t *status, cudaStream_t st);
@@ -139,7 +139,9 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_lo_gs = take(lo && grad ? n * cdiv(s, lo_part_samples()) * 8 : 0);
     p.off_lo_a = take(lo ? lo_split_elems(n, p.ldw) * 2 : 0);  // split-BF16 operand of the pair contractions
     // sparse: 64-bit fixed-point gradient accumulators and their scale
-    p.off_gpart = take(grad ? (sparse ? m * 8 + 8 : (lo ? n * n * 8 + 8 : p.natile * m * 8)) : 0);
+    // low-order: also the fixed-point sums that build C and d (n x n + n, and
+    // the largest |c_j|), before the gradient's pair corrections reuse it
+    p.off_gpart = take(lo ? n * n * 8 + n * 8 + 64 : (grad ? (sparse ? m * 8 + 8 : p.natile * m * 8) : 0));
     p.off_ab = take(mmd ? l * 16 : 0);
     p.off_s12 = take(mmd ? l * 16 : 0);
     p.off_T = take(mmd ? l * 8 : 0);
@@ -306,7 +308,7 @@ iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, cons
         IQP_TRY(launch_lo_prepare(p.n, G, p.m, ldg, Z, p.s, ldz, at<float>(ws, p.off_c), at<int4>(ws, p.off_sup),
                                   at<uint64_t>(ws, p.off_pzt), p.ldzt, at<float>(ws, p.off_lo_c), p.ldc,
                                   at<float>(ws, p.off_lo_m), p.ldw, at<__nv_bfloat16>(ws, p.off_lo_a),
-                                  at<uint32_t>(ws, p.off_status), st));
+                                  at<unsigned long long>(ws, p.off_gpart), at<uint32_t>(ws, p.off_status), st));
         return IQP_OK;
     }
     IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,

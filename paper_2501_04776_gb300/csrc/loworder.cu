@@ -16,8 +16,9 @@
 // The work is O(p s + l |Q_a|^2 s), p = number of qubit pairs carrying a
 // generator, instead of nnz(P_A) s, and nnz(P_A) is about l |Q_a| n for all
 // one- and two-body gates. FP32 arithmetic, FP64
-// reductions over samples, K accumulated in 64-bit fixed point (integer
-// atomics, so the gradient is bitwise reproducible).
+// reductions over samples; C, d and K accumulated in 64-bit fixed point
+// (integer atomics, so repeated supports and the gradient are bitwise
+// reproducible).
 //
 // Device-side errors: a generator of weight > 2 records IQP_ERR_ARG, an
 // observable of weight > 1024 records IQP_ERR_UNSUPPORTED (in the workspace
@@ -45,25 +46,81 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 #endif
 
 // d_q, C_qr and E (bits r of row q and q of row r set iff some generator
-// acts on {q, r}),
-// from the support list (q0 < q1 < ..., count).
+// acts on {q, r}) from the support list (q0 < q1 < ..., count). Repeated
+// supports add their coefficients; the sums are formed exactly in 64-bit
+// fixed point (integer atomics, so their order does not matter) and rounded
+// to FP32 once, which keeps every result bitwise reproducible.
+//
+// Scale 2^k of the fixed point, from the largest |c_j| (its float bits, taken
+// by an integer atomicMax) and m: m max|c_j| 2^k < 2^62, so no partial sum
+// overflows; k is clamped to [-60, 100].
+__device__ __forceinline__ int lo_fx_exp(unsigned cmax_bits, int64_t m) {
+    const float cm = __uint_as_float(cmax_bits);
+    if (!(cm > 0.f) || !(cm < INFINITY)) return 40;
+    int e = 0;
+    frexp((double)cm * (double)(m > 0 ? m : 1), &e);  // the bound is < 2^e
+    const int k = 62 - e;
+    return k < -60 ? -60 : (k > 100 ? 100 : k);
+}
+
+__global__ void k_lo_cmax(const int4 *__restrict__ sup, const float *__restrict__ c, int64_t m,
+                          unsigned *__restrict__ cmax) {
+    unsigned v = 0u;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int w = sup[j].w;
+        if (w == 1 || w == 2) {
+            const unsigned b = __float_as_uint(fabsf(c[j]));  // non-negative floats order like their bits
+            v = b > v ? b : v;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const unsigned o = __shfl_xor_sync(kFull, v, off);
+        v = o > v ? o : v;
+    }
+    if ((threadIdx.x & 31) == 0 && v != 0u) atomicMax(cmax, v);
+}
+
+// Cfx (n x n) and dfx (n): fixed-point sums of c_j; E bits.
 __global__ void k_lo_build(const int4 *__restrict__ sup, const float *__restrict__ c, int64_t m, int64_t n,
-                           float *__restrict__ C, int64_t ldc, float *__restrict__ d,
-                           unsigned long long *__restrict__ E, int64_t lde, uint32_t *__restrict__ status) {
+                           unsigned long long *__restrict__ Cfx, unsigned long long *__restrict__ dfx,
+                           const unsigned *__restrict__ cmax, unsigned long long *__restrict__ E, int64_t lde,
+                           uint32_t *__restrict__ status) {
     [[maybe_unused]] uint32_t *status_dbg = status;
-    (void)n;
+    const int k = lo_fx_exp(*cmax, m);
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const int4 sp = sup[j];
         if (!LO_OK(sp.w <= 0 || (sp.x >= 0 && sp.x < n && (sp.w < 2 || (sp.y > sp.x && sp.y < n))), 8)) continue;
-        if (sp.w == 1) {
-            atomicAdd(d + sp.x, c[j]);
-        } else if (sp.w == 2) {
-            atomicAdd(C + (int64_t)sp.x * ldc + sp.y, c[j]);
-            atomicAdd(C + (int64_t)sp.y * ldc + sp.x, c[j]);
-            atomicOr(E + (int64_t)sp.x * lde + (sp.y >> 6), 1ull << (sp.y & 63));
-            atomicOr(E + (int64_t)sp.y * lde + (sp.x >> 6), 1ull << (sp.x & 63));
+        if (sp.w == 1 || sp.w == 2) {
+            const unsigned long long v = (unsigned long long)llrint(ldexp((double)c[j], k));
+            if (sp.w == 1) {
+                atomicAdd(dfx + sp.x, v);
+            } else {
+                atomicAdd(Cfx + (int64_t)sp.x * n + sp.y, v);
+                atomicAdd(Cfx + (int64_t)sp.y * n + sp.x, v);
+                atomicOr(E + (int64_t)sp.x * lde + (sp.y >> 6), 1ull << (sp.y & 63));
+                atomicOr(E + (int64_t)sp.y * lde + (sp.x >> 6), 1ull << (sp.x & 63));
+            }
         } else if (sp.w > 2) {
             record_status(status, IQP_ERR_ARG);
+        }
+    }
+}
+
+// C (n x ldc, zero in columns >= n) and d (n) from their fixed-point sums,
+// each rounded to FP32 once.
+__global__ void k_lo_fx_float(const unsigned long long *__restrict__ Cfx, const unsigned long long *__restrict__ dfx,
+                              const unsigned *__restrict__ cmax, int64_t m, int64_t n, float *__restrict__ C,
+                              int64_t ldc, float *__restrict__ d) {
+    const float inv = ldexpf(1.0f, -lo_fx_exp(*cmax, m));
+    const int64_t total = n * ldc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total + n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < total) {
+            const int64_t q = i / ldc, r = i - q * ldc;
+            C[i] = r < n ? __ll2float_rn((long long)Cfx[q * n + r]) * inv : 0.f;
+        } else {
+            d[i - total] = __ll2float_rn((long long)dfx[i - total]) * inv;
         }
     }
 }
@@ -415,6 +472,11 @@ __device__ int lo_fill_pairs(LoShared &sh, int nq, int64_t *c0, const unsigned l
     return np;
 }
 
+// v with its sign flipped when bit 31 of y is set.
+__device__ __forceinline__ float flip_if(float v, uint32_t y) {
+    return __int_as_float(__float_as_int(v) ^ (int)(y & 0x80000000u));
+}
+
 // Sum of v over the CTA in FP32 (warp shuffles, then the warps' sums in
 // fixed order); every thread gets it. The partial sums of one 256-sample
 // block are kept in FP32 and combined across blocks in FP64, as in the
@@ -454,11 +516,6 @@ __device__ void lo_load_bits4(LoShared &sh, int nq, int64_t n, const uint64_t *_
     __syncthreads();
     lo_fill_bits4(sh, nq, n, ZT, ldzt, blk0, status_dbg);
     __syncthreads();
-}
-
-// v with its sign flipped when bit 31 of y is set.
-__device__ __forceinline__ float flip_if(float v, uint32_t y) {
-    return __int_as_float(__float_as_int(v) ^ (int)(y & 0x80000000u));
 }
 
 // MODE 0: (sum cos, sum (cos - mean)^2) per (observable, 256 samples) into
@@ -956,32 +1013,44 @@ int64_t lo_lde(int64_t n) { return cdiv(n, 64); }
 // transposed), sup: m int4.
 cudaError_t launch_lo_prepare(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *Z, int64_t s,
                               int64_t ldz, const float *c, int4 *sup, uint64_t *ZT, int64_t ldzt, float *C,
-                              int64_t ldc, float *M, int64_t lds, __nv_bfloat16 *split, uint32_t *status,
-                              cudaStream_t st) {
+                              int64_t ldc, float *M, int64_t lds, __nv_bfloat16 *split, unsigned long long *fx,
+                              uint32_t *status, cudaStream_t st) {
     cudaError_t e = launch_support_list(G, m, ldg, n, sup, st);
     if (e != cudaSuccess) return e;
     if ((e = launch_bit_transpose_batched(Z, 1, s, n, ldz, ZT, ldzt, st)) != cudaSuccess) return e;
     float *d = C + n * ldc;
     unsigned long long *E = reinterpret_cast<unsigned long long *>(d + ldc);
     const int64_t lde = lo_lde(n);
-    if ((e = cudaMemsetAsync(C, 0, (size_t)(n + 1) * ldc * sizeof(float) + (size_t)n * lde * 8, st)) != cudaSuccess)
-        return e;
+    // fx: Cfx (n x n), dfx (n), then the largest |c_j| (float bits).
+    unsigned long long *Cfx = fx, *dfx = fx + n * n;
+    unsigned *cmax = reinterpret_cast<unsigned *>(dfx + n);
+    if ((e = cudaMemsetAsync(E, 0, (size_t)n * lde * 8, st)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(fx, 0, (size_t)(n * n + n) * 8 + 16, st)) != cudaSuccess) return e;
     {
         LaunchScope ls(IQP_KERNEL_LOWORDER, st);
-        k_lo_build<<<grid_1d(m), 256, 0, st>>>(sup, c, m, n, C, ldc, d, E, lde, status);
+        k_lo_cmax<<<grid_1d(m), 256, 0, st>>>(sup, c, m, cmax);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_lo_build<<<grid_1d(m), 256, 0, st>>>(sup, c, m, n, Cfx, dfx, cmax, E, lde, status);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_lo_fx_float<<<grid_1d(n * ldc + n), 256, 0, st>>>(Cfx, dfx, cmax, m, n, C, ldc, d);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     // M = C S: rows q, columns the samples (Z's rows), K the qubits r.
     const int64_t kc = round_up(n, 64);
+    bool done = false;
     if (lo_tensor() && split != nullptr && ldz >= 4 && ldz % 2 == 0 && (reinterpret_cast<uintptr_t>(Z) & 15) == 0) {
         __nv_bfloat16 *hi = split, *lo = split + n * kc;
         if ((e = launch_split(C, ldc, n, n, nullptr, 0, kc, hi, lo, st)) != cudaSuccess) return e;
         e = launch_tc_dense(hi, lo, n, kc, n, Z, s, ldz, M, lds, false, status, st);
-        if (e != cudaErrorNotSupported) return e;
+        if (e != cudaSuccess && e != cudaErrorNotSupported) return e;
+        done = e == cudaSuccess;
     }
-    LaunchScope ls(IQP_KERNEL_LOWORDER_GEMM, st);
-    k_lo_cs<<<dim3((unsigned)n, (unsigned)cdiv(s, 2048)), 32, 0, st>>>(E, lde, C, ldc, ZT, ldzt, s, M, lds);
-    return cudaGetLastError();
+    if (!done) {
+        LaunchScope ls(IQP_KERNEL_LOWORDER_GEMM, st);
+        k_lo_cs<<<dim3((unsigned)n, (unsigned)cdiv(s, 2048)), 32, 0, st>>>(E, lde, C, ldc, ZT, ldzt, s, M, lds);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_lo_stats(const uint64_t *A, int64_t lda, int64_t n, int64_t l, const uint64_t *ZT, int64_t ldzt,

@@ -151,6 +151,25 @@ def test_gradient_is_reproducible(api):
     assert np.array_equal(api.expval_grad(*args).cpu().numpy(), api.expval_grad(*args).cpu().numpy())
 
 
+def test_repeated_supports_are_reproducible(api):
+    """Every support repeated 40 times (their coefficients add into one C or
+    d entry): estimates and gradient are the same bit for bit on every call,
+    and match the oracle."""
+    rng = I.Rng(13)
+    n, l, s = 64, 50, 700
+    base = I.random_k_body(rng, 120, n, [1, 2], 1)
+    G = np.concatenate([base] * 40)
+    th = (0.02 * rng.normal(G.shape[0], 2)).astype(np.float32)
+    A, Z = I.bernoulli_bits(rng, l, n, 0.2, 3), I.uniform_bits(rng, s, n, 4)
+    w = rng.normal(l, 5)
+    runs = [run(api, n, G, A, Z, th, w) for _ in range(3)]
+    for ev, se, g in runs[1:]:
+        assert np.array_equal(ev, runs[0][0]) and np.array_equal(se, runs[0][1]) and np.array_equal(g, runs[0][2])
+    want_ev, want_se, _, _ = oracle.expval(n, G, A, Z, th.astype(np.float64))
+    assert np.max(np.abs(runs[0][0] - want_ev)) <= TOL and np.max(np.abs(runs[0][1] - want_se)) <= TOL
+    assert rel_l2(runs[0][2], oracle.expval_grad(n, G, A, Z, th.astype(np.float64), -w / s)) <= GRAD_RTOL
+
+
 def _relevant_gates(n, G, A_sub):
     return np.nonzero(oracle.parity(n, A_sub, G).any(axis=0))[0]
 
