@@ -3,10 +3,11 @@
 
 Workload (default): m = 100000 random generators on k in {1,2,3} qubits,
 n = 1000 qubits, l = 10000 observables (Bernoulli(0.05) bits), s = 10000
-samples, theta ~ U(-0.05, 0.05). One step = iqp_expval (parities, phase
-contraction, cos / mean / standard error) followed by iqp_expval_grad for the
-linear loss sum_a w_a <Z_a> (parities, Phi recomputed tile by tile, gradient
-contraction), i.e. one autograd forward + backward.
+samples, theta ~ U(-0.05, 0.05). One step = one iqp_expval_value_and_grad
+call for the linear loss sum_a w_a <Z_a> (parities once; one phase pass that
+yields the cos / mean / standard-error partials and W; the gradient
+contraction). The autograd form of the same step (iqp_expval_keep_phi, then
+iqp_expval_grad_from_phi) is timed beside it (`other_step`).
 
 Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
 a bounded sample of the same workload instead.

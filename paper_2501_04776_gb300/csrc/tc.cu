@@ -9,10 +9,12 @@
 // (A_hi = hi_j [P_A], A_lo = lo_j [P_A], B = 1 - 2 P_Z, all exact in BF16);
 // one thread issues two tcgen05.mma per 16-gate step (hi and lo share B).
 // The epilogue runs in the producer warps straight from TMEM:
-//   mode 0: cos, per-observable (S, M2) partials over 64-sample groups;
+//   mode 0: cos, per-observable (S, M2) partials over 64-sample groups, and
+//           Phi itself (FP32) when a gradient pass follows that reads it back
+//           (the MMD loss, the autograd pair; k_w_from_phi forms W from it);
 //   mode 1: W = sin Phi (alpha + beta cos Phi), split into hi + lo BF16 rows;
 //   mode 2: both from one pass (the loss coefficients known in advance).
-// Phi itself is never written.
+// Otherwise Phi itself is never written.
 //
 // Dense form (mode 3, A by TMA): out = (A_hi + A_lo) (1 - 2 B_bits)^T for a
 // dense split-BF16 matrix A brought in by TMA and a +-1 operand expanded from
