@@ -371,14 +371,15 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
     # (m x ldlt words) once, a small fraction of HBM time; their work is one
     # FP64 multiply (product over a row's set bits, run by both calls) or add
     # (gradient sum over a column's set bits) per set bit: 3 nnz(P_A) FP64
-    # operations per call pair, against the FP64 pipe (1.25 TFLOP/s nominal
-    # with an FMA as 2: 2 FP64 operations per SM per clock).
+    # operations per call pair, against the FP64 pipe's sustained rate of one
+    # operation per SM per clock (the rate ncu's pipe_fp64 percentages imply
+    # for these DMULs).
     nbytes = 8.0 * (l * ldp + m * ldlt)
     nnz = nnz_parities(api, n, A, G)
     fp64_ops = 3.0 * nnz
     bf_ms = kt.get("bitflip", {}).get("total_ms", 0.0) / max(1, args.steps)
     mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
-    fp64_peak = 152 * 2 * mhz * 1e6 / 1e12  # TFLOP/s, one DMUL / DADD per slot
+    fp64_peak = 152 * 1 * mhz * 1e6 / 1e12  # TFLOP/s, one DMUL / DADD per SM per clock
     ach = fp64_ops / (bf_ms * 1e-3) / 1e12 if bf_ms else None
     out["bitflip_fwd_grad"] = {
         "workload": f"bitflip circuit, n={n} m={m} l={l} (the headline's G, A, theta), FP64",
@@ -388,7 +389,8 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
                      "frac": round(ach / fp64_peak, 4) if ach else None, "fp64_ops_per_call_pair": fp64_ops,
                      "nnz_PA": nnz, "bytes_per_call_pair": nbytes,
                      "hbm_frac": round(nbytes / (bf_ms * 1e-3) / 1e9 / hbm, 4) if bf_ms else None,
-                     "peak_source": "FP64: 152 SMs x 2 per clock x max SM clock (1.25 TFLOP/s nominal, FMA = 2)"}}
+                     "peak_source": "FP64 pipe: 152 SMs x 1 operation per clock x max SM clock (from ncu's "
+                                    "sm__inst_executed_pipe_fp64 percentage of peak for k_bitflip_rows)"}}
     del ws
 
     # MMD^2 loss and gradient, one training step's call (unbiased form), in
