@@ -47,9 +47,10 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 
 // d_q, C_qr and E (bits r of row q and q of row r set iff some generator
 // acts on {q, r}) from the support list (q0 < q1 < ..., count). Repeated
-// supports add their coefficients; the sums are formed exactly in 64-bit
-// fixed point (integer atomics, so their order does not matter) and rounded
-// to FP32 once, which keeps every result bitwise reproducible.
+// supports add their coefficients: each c_j is rounded to a multiple of
+// 2^-k, the sums are formed exactly in 64-bit fixed point (integer atomics,
+// so their order does not matter) and each is rounded to FP32 once, which
+// keeps every result bitwise reproducible.
 //
 // Scale 2^k of the fixed point, from the largest |c_j| (its float bits, taken
 // by an integer atomicMax) and m: m max|c_j| 2^k < 2^62, so no partial sum
