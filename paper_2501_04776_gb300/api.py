@@ -190,10 +190,10 @@ def phi_ld(s: int) -> int:
     return (s + 63) // 64 * 64
 
 
-def expval_keep_phi_raw(n, theta, G, A, Z, precision="split_bf16"):
-    """(expval, std_err, phi): iqp_expval that also keeps Phi (l x phi_ld(s)
-    float32, in the precision's own sample order) for expval_grad_from_phi.
-    No autograd."""
+def expval_keep_phi_raw(n, theta, G, A, Z, precision="split_bf16", ld=None):
+    """(expval, std_err, phi): iqp_expval that also keeps Phi (l x ld float32,
+    ld = phi_ld(s) by default, in the precision's own sample order) for
+    expval_grad_from_phi. No autograd."""
     for t, nm in ((G, "G"), (A, "A"), (Z, "Z")):
         _bits(t, nm)
     th = _theta32(theta)
@@ -203,7 +203,7 @@ def expval_keep_phi_raw(n, theta, G, A, Z, precision="split_bf16"):
     ws = _WS.get(lib.iqp_workspace_bytes(OP_EXPVAL, n, m, l, s, 0, prec), G.device)
     ev = torch.empty(l, dtype=torch.float64, device=G.device)
     se = torch.empty(l, dtype=torch.float64, device=G.device)
-    ld = phi_ld(s)
+    ld = phi_ld(s) if ld is None else int(ld)
     phi = torch.empty((l, ld), dtype=torch.float32, device=G.device)
     check(lib.iqp_expval_keep_phi(n, _ptr(G), m, G.shape[1], _ptr(A), l, A.shape[1], _ptr(Z), s, Z.shape[1], _ptr(th),
                                   prec, _ptr(ev), _ptr(se), _ptr(phi), ld, _ptr(ws), ws.numel(),

@@ -228,6 +228,10 @@ def test_kept_phase_gives_the_recomputed_results_bit_for_bit(api, prec):
     g0 = api.expval_grad(n, thd, Gd, Ad, Zd, alpha, beta, prec)
     g1 = api.expval_grad_from_phi(n, thd, Gd, Ad, Zd, phi, alpha, beta, prec)
     assert torch.equal(g0, g1)
+    # a wider row stride changes nothing
+    ev2, se2, phi2 = api.expval_keep_phi_raw(n, thd, Gd, Ad, Zd, prec, ld=api.phi_ld(s) + 128)
+    assert torch.equal(ev0, ev2) and torch.equal(se0, se2)
+    assert torch.equal(g0, api.expval_grad_from_phi(n, thd, Gd, Ad, Zd, phi2, alpha, beta, prec))
     want = oracle.expval_grad(n, G, A, Z, th.astype(np.float64), alpha.cpu().numpy(), beta.cpu().numpy())
     assert rel_l2(g1.cpu().numpy(), want) <= GRAD_RTOL
     want_ev, _, _, _ = oracle.expval(n, G, A, Z, th.astype(np.float64))
