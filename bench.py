@@ -408,11 +408,11 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
         ws = torch.empty(lib.iqp_workspace_bytes(_lib.OP_MMD_LOSS_GRAD, p.n, mm, lm, sm, Nm, prec),
                          dtype=torch.uint8, device=dev)
 
-        def mmd():
+        def mmd(sp=st):
             _lib.check(lib.iqp_mmd_loss_grad(p.n, P(Gm.data_ptr()), mm, Gm.shape[1], P(Am.data_ptr()), lm,
                                              Am.shape[1], P(Zm.data_ptr()), sm, Zm.shape[1], P(Xm.data_ptr()), Nm,
                                              Xm.shape[1], P(thm.data_ptr()), prec, 1, P(loss.data_ptr()),
-                                             P(gm.data_ptr()), P(ws.data_ptr()), ws.numel(), st),
+                                             P(gm.data_ptr()), P(ws.data_ptr()), ws.numel(), sp),
                        "iqp_mmd_loss_grad")
 
         lib.iqp_profile_reset()
@@ -444,6 +444,21 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
         out["mmd_loss_grad_" + tag] = {
             "workload": f"MMD^2 loss + grad, n={p.n} m={mm} (all 1- and 2-body) l={lm} s={sm} N={Nm}, {tag}",
             "ms_per_call": round(statistics.mean(ms), 3), "kernels": kt, "roofline": roof}
+        if prec == _lib.LOWORDER_FP32:
+            # The same call captured once in a CUDA graph and replayed (its
+            # ~26 short launches then cost no host-side launch overhead).
+            side = torch.cuda.Stream(dev)
+            side.wait_stream(torch.cuda.current_stream(dev))
+            with torch.cuda.stream(side):
+                for _ in range(2):
+                    mmd(P(side.cuda_stream))
+            torch.cuda.current_stream(dev).wait_stream(side)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                mmd(P(torch.cuda.current_stream(dev).cuda_stream))
+            ms_g, _ = timed(None, args.steps, args.warmup, profile=False, fn=graph.replay)
+            out["mmd_loss_grad_" + tag]["ms_per_call_cuda_graph"] = round(statistics.mean(ms_g), 3)
+            del graph
         del ws
     return out
 
