@@ -443,21 +443,29 @@ def words_per_row(n: int) -> int:
     return w + (w & 1)
 
 
-def uniform_bits(seed: int, stream: int, rows: int, n: int, device="cuda") -> torch.Tensor:
+def _bits_out(out, rows, ld, device):
+    if out is None:
+        return torch.empty(rows, ld, dtype=torch.int64, device=device)
+    if not (out.is_cuda and out.dtype == torch.int64 and out.shape == (rows, ld) and out.is_contiguous()):
+        raise ValueError(f"out must be a contiguous ({rows}, {ld}) int64 CUDA tensor")
+    return out
+
+
+def uniform_bits(seed: int, stream: int, rows: int, n: int, device="cuda", out=None) -> torch.Tensor:
     """Uniform bitstrings drawn on the device (same bits as
-    inputs.uniform_bits(Rng(seed), rows, n, stream))."""
+    inputs.uniform_bits(Rng(seed), rows, n, stream)), into `out` if given."""
     ld = words_per_row(n)
-    out = torch.empty(rows, ld, dtype=torch.int64, device=device)
+    out = _bits_out(out, rows, ld, device)
     check(_lib.load().iqp_uniform_bits(seed & (2 ** 64 - 1), stream & (2 ** 64 - 1), rows, n, _ptr(out), ld,
                                        ctypes.c_void_p(_stream(device))), "iqp_uniform_bits")
     return out
 
 
-def bernoulli_bits(seed: int, stream: int, rows: int, n: int, p: float, device="cuda") -> torch.Tensor:
+def bernoulli_bits(seed: int, stream: int, rows: int, n: int, p: float, device="cuda", out=None) -> torch.Tensor:
     """Bernoulli(p) bits drawn on the device (same bits as
-    inputs.bernoulli_bits(Rng(seed), rows, n, p, stream))."""
+    inputs.bernoulli_bits(Rng(seed), rows, n, p, stream)), into `out` if given."""
     ld = words_per_row(n)
-    out = torch.empty(rows, ld, dtype=torch.int64, device=device)
+    out = _bits_out(out, rows, ld, device)
     check(_lib.load().iqp_bernoulli_bits(seed & (2 ** 64 - 1), stream & (2 ** 64 - 1), rows, n, float(p),
                                          _ptr(out), ld, ctypes.c_void_p(_stream(device))), "iqp_bernoulli_bits")
     return out
