@@ -155,14 +155,21 @@ iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
  * the array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture. All calls share the one
  * array: calls that overlap on the GPU (other streams, other host threads)
- * race and corrupt each other's results, so serialise them. Device-side
- * status (a bounded wait that ran out) is recorded in the array and cleared
- * by the next call; it is not returned. */
+ * race and corrupt each other's results, so serialise them. Invalid
+ * arguments return the status iqp_expval would, before anything is queued.
+ * Device-side status (a bounded wait that ran out) is recorded in the array;
+ * read it with iqp_noalloc_read_status() before the next call, which
+ * clears it. */
 iqp_status iqp_expval_noalloc(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
                               const uint64_t *A, int64_t l, int64_t lda,
                               const uint64_t *Z, int64_t s, int64_t ldz,
                               const float *theta, iqp_precision prec,
                               double *expval, double *std_err, void *stream);
+
+/* Device-side status of the last iqp_expval_noalloc call on the current
+ * device (iqp_read_status for its array): waits for `stream`, returns the
+ * status word and clears it. Allocates nothing. */
+iqp_status iqp_noalloc_read_status(void *stream);
 
 /* Gradient of the estimator in theta (Sec. 2.4; the estimator is a
  * deterministic function of theta for fixed Z), for losses whose derivative

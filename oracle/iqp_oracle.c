@@ -15,8 +15,8 @@
  * Inputs use the bit format of the C ABI: a binary matrix is uint64 words,
  * row-major, `ld` words per row, LSB-first (bit b of word w is column 64w+b).
  *
- * Parity status of each function (what pins it) is listed in the design doc's
- * oracle table and in tests/test_oracle_pins.py.
+ * What pins each function against the paper and the mathematics is in
+ * tests/test_oracle_pins.py.
  */
 #include <math.h>
 #include <stdint.h>

@@ -27,6 +27,7 @@ SIGNATURES = {
     "iqp_parity_sum": (_int, [_i64] + _MAT + _MAT + [_p, _p]),
     "iqp_expval": (_int, [_i64] + _MAT * 3 + [_p, _int, _p, _p, _p, _sz, _p]),
     "iqp_expval_noalloc": (_int, [_i64] + _MAT * 3 + [_p, _int, _p, _p, _p]),
+    "iqp_noalloc_read_status": (_int, [_p]),
     "iqp_expval_grad": (_int, [_i64] + _MAT * 3 + [_p, _p, _p, _int, _p, _p, _sz, _p]),
     "iqp_mmd_loss": (_int, [_i64] + _MAT * 4 + [_p, _int, _int, _p, _p, _sz, _p]),
     "iqp_mmd_loss_grad": (_int, [_i64] + _MAT * 4 + [_p, _int, _int, _p, _p, _p, _sz, _p]),

@@ -192,9 +192,17 @@ static std::vector<PendingEvent> g_pending;
 static double g_prof_ms[IQP_KERNEL_COUNT];
 static uint64_t g_prof_n[IQP_KERNEL_COUNT];
 
+// A stream being captured into a CUDA graph gets no timing events: events
+// recorded into a capture exist only inside the graph, and waiting on them
+// from the host would fail or block.
+static bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone;
+}
+
 LaunchScope::LaunchScope(int k, cudaStream_t s) : kernel(k), st(s), ev0(nullptr), ev1(nullptr) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    if (g_profiling.load(std::memory_order_relaxed)) {
+    if (g_profiling.load(std::memory_order_relaxed) && !capturing(s)) {
         if (cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess) {
             cudaEventRecord(ev0, st);
         } else {
@@ -441,6 +449,20 @@ iqp_status mmd_core(int op, int64_t n, const uint64_t *G, int64_t m, int64_t ldg
     return IQP_OK;
 }
 
+}  // namespace
+
+// The host-side checks iqp_expval runs before it touches the workspace.
+iqp_status expval_arg_check(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                            int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                            iqp_precision prec, const double *expval, const double *std_err) {
+    const iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    if (rc != IQP_OK) return rc;
+    if ((expval && !aligned(expval, 8)) || (std_err && !aligned(std_err, 8))) return IQP_ERR_ALIGN;
+    return IQP_OK;
+}
+
+namespace {
+
 uint64_t spin_limit_ns() {
     const char *e = std::getenv("IQP_SPIN_LIMIT_MS");
     double ms = e ? std::atof(e) : 4000.0;
@@ -508,9 +530,8 @@ iqp_status iqp_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, 
 iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l, int64_t lda,
                       const uint64_t *Z, int64_t s, int64_t ldz, const float *theta, iqp_precision prec,
                       double *expval, double *std_err, void *ws, size_t ws_bytes, void *stream) {
-    iqp_status rc = check_common(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec);
+    iqp_status rc = expval_arg_check(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec, expval, std_err);
     if (rc != IQP_OK) return rc;
-    if ((expval && !aligned(expval, 8)) || (std_err && !aligned(std_err, 8))) return IQP_ERR_ALIGN;
     Plan p = make_plan(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
     p.G = G;
     p.ldg = ldg;

@@ -71,6 +71,12 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
 // scratch at the end of its plan); 0 for invalid arguments.
 size_t workspace_min_bytes(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, int prec);
 
+// Host-side argument checks of iqp_expval (sizes, pointers, alignment,
+// precision), without the workspace.
+iqp_status expval_arg_check(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const uint64_t *A, int64_t l,
+                            int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz, const float *theta,
+                            iqp_precision prec, const double *expval, const double *std_err);
+
 // Dense contraction on the tensor cores (split BF16, FP32 accumulation):
 //   out[r][c] = sum_{k < K} (a_hi[r][k] + a_lo[r][k]) (1 - 2 bit k of b row c)
 // for r < rows, c < nb. a_hi / a_lo: rows x kpad BF16 (row-major, kpad a
@@ -325,27 +331,6 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
         "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
             smem_u32(bar)),
         "h"((uint16_t)3)
-        : "memory");
-}
-
-// 2D TMA load multicast to the CTAs in `mask` (same shared offset in each),
-// completing on the barrier at `bar`'s offset in each of them.
-__device__ __forceinline__ void tma_load_2d_multicast(void *dst, const void *tmap, uint64_t *bar, int x, int y,
-                                                      uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(dst)),
-        "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar)), "h"(mask)
-        : "memory");
-}
-
-// Single-CTA MMA completion signalled to the barrier at `bar`'s offset in
-// every CTA of `mask`.
-__device__ __forceinline__ void umma_commit_multicast(uint64_t *bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
         : "memory");
 }
 

@@ -49,16 +49,27 @@ extern "C" iqp_status iqp_expval_noalloc(int64_t n, const uint64_t *G, int64_t m
                                          int64_t l, int64_t lda, const uint64_t *Z, int64_t s, int64_t ldz,
                                          const float *theta, iqp_precision prec, double *expval, double *std_err,
                                          void *stream) {
+    // The checks iqp_expval runs come first, so invalid arguments give the
+    // same status as there and nothing is queued for them.
+    iqp_status rc = iqp::expval_arg_check(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec, expval, std_err);
+    if (rc != IQP_OK) return rc;
     // The array must hold the op's workspace; the optional split-tile scratch
     // at its end is used only when it fits as well.
     const size_t need = iqp::workspace_min_bytes(IQP_OP_EXPVAL, n, m, l, s, 0, prec);
-    if (need == 0 || need > iqp::kNoAllocBytes) return IQP_ERR_WORKSPACE;
+    if (need == 0) return IQP_ERR_ARG;
+    if (need > iqp::kNoAllocBytes) return IQP_ERR_WORKSPACE;
     void *ws = nullptr;
-    const iqp_status rc = iqp::noalloc_scratch(&ws);
-    if (rc != IQP_OK) return rc;
+    if ((rc = iqp::noalloc_scratch(&ws)) != IQP_OK) return rc;
     // The array keeps the previous call's contents; the device status word at
     // its start must begin at zero. Every other region is fully rewritten.
     if (cudaMemsetAsync(ws, 0, 256, static_cast<cudaStream_t>(stream)) != cudaSuccess) return IQP_ERR_CUDA;
     return iqp_expval(n, G, m, ldg, A, l, lda, Z, s, ldz, theta, prec, expval, std_err, ws, iqp::kNoAllocBytes,
                       stream);
+}
+
+extern "C" iqp_status iqp_noalloc_read_status(void *stream) {
+    void *ws = nullptr;
+    const iqp_status rc = iqp::noalloc_scratch(&ws);
+    if (rc != IQP_OK) return rc;
+    return iqp_read_status(ws, iqp::kNoAllocBytes, stream);
 }

@@ -43,7 +43,7 @@
 // write 128 accumulator rows into each CTA's TMEM. Per SM this halves the B
 // operand's expansion work and the tensor core's B reads from shared memory.
 // Both CTAs' producer warps arrive on the even CTA's stage barrier; stage and
-// chunk completions are multicast to both CTAs.
+// chunk completions are signalled to both CTAs by one pair commit.
 //
 // Every wait is bounded (globaltimer); on expiry the CTA records
 // IQP_ERR_TIMEOUT, drains its in-flight copies and MMAs, frees TMEM and exits.
@@ -386,10 +386,7 @@ __device__ __noinline__ void split_sum(const float *src0, int64_t part_stride, i
 // the gradient's W; for MODE 3, a dense split-BF16 matrix); AT = false: the
 // producer warps expand it from P_A bits and the hi/lo split of 2 theta.
 // CG = 1: one CTA per tile of 128 rows; CG = 2: a CTA pair per tile of 256 rows.
-// MC = 2 (gradient with CG = 1): clusters of two CTAs on the same 128
-// observables and adjacent 256-gate columns; each loads half of every W tile
-// and multicasts it to both, halving W's L2-to-SM traffic.
-template <bool GRAD, int MODE, int CG, int MC, bool AT, bool SPL>
+template <bool GRAD, int MODE, int CG, bool AT, bool SPL>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
          const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
@@ -404,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t lim = args.limit_ns;
     uint32_t *status = args.status;
-    constexpr int CL = CG * MC;  // CTAs per cluster
+    constexpr int CL = CG;  // CTAs per cluster
     const uint32_t crank = CL == 2 ? cluster_ctarank() : 0u;  // CTA rank in the cluster
     const bool leader = CG == 1 || crank == 0;                 // issues this CTA's MMAs
     const int64_t group0 = blockIdx.x / CL, ngroups = gridDim.x / CL;
@@ -418,7 +415,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // Even CTA: its own producer warps, plus one forwarded arrival from
             // the odd CTA of a pair.
             mbar_init(&bar->op_full[i], CG == 2 ? NGEN + 1 : NGEN);
-            mbar_init(&bar->op_empty[i], MC);  // every MMA that reads the stage
+            mbar_init(&bar->op_empty[i], 1);  // the MMAs that read the stage
             mbar_init(&bar->w_full[i], 1);
             mbar_init(&bar->peer_full[i], NGEN);  // odd CTA: its producer warps
         }
@@ -447,9 +444,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = bar->tmem_slot;
 
-    // Tiles per cluster iteration: with MC = 2 a cluster takes two adjacent
-    // column tiles of one row block.
-    const int64_t tiles_nc = MC == 2 ? (args.tiles_n + 1) / 2 : args.tiles_n;
+    const int64_t tiles_nc = args.tiles_n;
     const int64_t nunits = args.nunits;
     const int nks = (int)args.nks;     // host guarantees nks < 2^31
     const int chunk = (int)args.chunk;
@@ -470,7 +465,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int64_t tm64, tc64;
                 tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm64, tc64);
                 const int tm = (int)tm64;
-                const int tn = (int)(MC == 2 ? 2 * tc64 + crank : tc64);
+                const int tn = (int)tc64;
                 const int prank = CG == 2 ? (int)crank : 0;        // rank within an MMA pair
                 const int a0 = tm * TM * CG + prank * TM;          // this CTA's first A row
                 const int b0 = tn * TN + prank * C::TNB;           // this CTA's first B row
@@ -506,22 +501,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                             }
                             uint8_t *op = smem + C::SM_OP + os * C::OP_BYTES;
                             mbar_arrive_expect_tx(&bar->w_full[os], 2 * TM * KS * 2);
-                            if (MC == 2) {
-                                // This CTA's half of the rows, written into both CTAs.
-                                const uint32_t h = crank * (TM / 2) * 128u;
-                                const int y = a0 + (int)crank * (TM / 2);
-                                tma_load_2d_multicast(op + C::OP_A_HI + h, &tmA, &bar->w_full[os], (int)(ks * KS), y,
-                                                      (uint16_t)3);
-                                tma_load_2d_multicast(op + C::OP_A_LO + h, &tmA2, &bar->w_full[os], (int)(ks * KS), y,
-                                                      (uint16_t)3);
-                            } else {
-                                tma_load_2d(op + C::OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), a0);
-                                tma_load_2d(op + C::OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), a0);
-                                // Warm L2 with the W tiles kWPrefetch stages ahead.
-                                if (ks + kWPrefetch < nks) {
-                                    tma_prefetch_2d(&tmA, (int)((ks + kWPrefetch) * KS), a0);
-                                    tma_prefetch_2d(&tmA2, (int)((ks + kWPrefetch) * KS), a0);
-                                }
+                            tma_load_2d(op + C::OP_A_HI, &tmA, &bar->w_full[os], (int)(ks * KS), a0);
+                            tma_load_2d(op + C::OP_A_LO, &tmA2, &bar->w_full[os], (int)(ks * KS), a0);
+                            // Warm L2 with the W tiles kWPrefetch stages ahead.
+                            if (ks + kWPrefetch < nks) {
+                                tma_prefetch_2d(&tmA, (int)((ks + kWPrefetch) * KS), a0);
+                                tma_prefetch_2d(&tmA2, (int)((ks + kWPrefetch) * KS), a0);
                             }
                             omask |= 1u << os;
                             opar = (opar & ~(1u << os)) | (((ito / NOP) & 1u) << os);
@@ -578,7 +563,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         }
                     }
                     if (CG == 2) umma_commit_pair(&bar->op_empty[os]);
-                    else if (MC == 2) umma_commit_multicast(&bar->op_empty[os], (uint16_t)3);
                     else umma_commit(&bar->op_empty[os]);
                     if (++kc == chunk || ks == ks1 - 1) {
                         if (CG == 2) umma_commit_pair(&bar->acc_full);
@@ -628,7 +612,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 unit_of<SPL>(u, args, nks, t, ks0, ks1, uv0);
                 tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm, tc);
             }
-            const int64_t tn = MC == 2 ? 2 * tc + crank : tc;
+            const int64_t tn = tc;
             const int64_t arow0 = tm * TM * CG + (CG == 2 ? (int64_t)crank * TM : 0);  // first observable here
             int kc = 0;              // stage index within the current chunk
             int nchunk = 0;          // chunks of this tile already folded into the running sum
@@ -900,7 +884,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     __syncthreads();
-    if (CL == 2) cluster_sync_all();  // no MMA or multicast copy still touches the peer
+    if (CL == 2) cluster_sync_all();  // no pair MMA still reads the peer's operands
     if (warp == 1) {
         __syncwarp();  // lane 0 ran the MMA loop alone; dealloc is warp-aligned
         tc_fence_after();
@@ -956,14 +940,14 @@ bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool GRAD, int MODE, int CG, int MC = 1, bool AT = GRAD, bool SPL = false>
+template <bool GRAD, int MODE, int CG, bool AT = GRAD, bool SPL = false>
 cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
                      cudaStream_t st) {
     using C = Cfg<CG, GRAD || AT>;
-    constexpr int CL = CG * MC;
+    constexpr int CL = CG;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, MC, AT, SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, AT, SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -977,7 +961,7 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
                                : IQP_KERNEL_PHASE_TC,
                    st);
     if (CL == 1) {
-        k_tc<GRAD, MODE, 1, 1, AT, SPL><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
+        k_tc<GRAD, MODE, 1, AT, SPL><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -992,19 +976,7 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, MC, AT, SPL>, a, a2, b, args);
-}
-
-// Gradient kernel form: single-CTA MMAs; with IQP_GRAD_MULTICAST=1, clusters
-// of two that share each W tile by TMA multicast (halves W's L2-to-SM
-// traffic; measured no faster on the benchmark workload, so off by default).
-bool grad_multicast() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = std::getenv("IQP_GRAD_MULTICAST");
-        v = (e != nullptr && e[0] == '1') ? 1 : 0;
-    }
-    return v == 1;
+    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, AT, SPL>, a, a2, b, args);
 }
 
 // Tensor-core group size: CTA pairs unless IQP_CTA_PAIRS=0.
@@ -1060,13 +1032,13 @@ template <bool SPL>
 cudaError_t launch_phase_k(int mode, int cg, const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a,
                            cudaStream_t st) {
     if (cg == 2) {
-        if (mode == 0) return launch_k<false, 0, 2, 1, false, SPL>(ma, ma, mb, a, st);
-        if (mode == 1) return launch_k<false, 1, 2, 1, false, SPL>(ma, ma, mb, a, st);
-        return launch_k<false, 2, 2, 1, false, SPL>(ma, ma, mb, a, st);
+        if (mode == 0) return launch_k<false, 0, 2, false, SPL>(ma, ma, mb, a, st);
+        if (mode == 1) return launch_k<false, 1, 2, false, SPL>(ma, ma, mb, a, st);
+        return launch_k<false, 2, 2, false, SPL>(ma, ma, mb, a, st);
     }
-    if (mode == 0) return launch_k<false, 0, 1, 1, false, SPL>(ma, ma, mb, a, st);
-    if (mode == 1) return launch_k<false, 1, 1, 1, false, SPL>(ma, ma, mb, a, st);
-    return launch_k<false, 2, 1, 1, false, SPL>(ma, ma, mb, a, st);
+    if (mode == 0) return launch_k<false, 0, 1, false, SPL>(ma, ma, mb, a, st);
+    if (mode == 1) return launch_k<false, 1, 1, false, SPL>(ma, ma, mb, a, st);
+    return launch_k<false, 2, 1, false, SPL>(ma, ma, mb, a, st);
 }
 }  // namespace
 
@@ -1144,12 +1116,11 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
 }
 
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why) {
-    const bool mc = grad_multicast();
     const int cg = 1;
     CUtensorMap mhi, mlo, mb;
     const __nv_bfloat16 *whi = at<__nv_bfloat16>(ws, p.off_w);
     const __nv_bfloat16 *wlo = whi + p.l * p.ldw;
-    const uint32_t wrows = mc ? TM / 2 : TM;  // each CTA of a multicast pair loads half the rows
+    const uint32_t wrows = TM;
     if (!make_map(&mhi, whi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, wrows,
                   CU_TENSOR_MAP_SWIZZLE_128B) ||
         !make_map(&mlo, wlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, wrows,
@@ -1180,10 +1151,9 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.out = nullptr;
     a.ldo = 0;
     a.out_f64 = 0;
-    whole_tiles(a, a.tiles_m * (mc ? (a.tiles_n + 1) / 2 : a.tiles_n));
+    whole_tiles(a, a.tiles_m * a.tiles_n);
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
-    if (mc) return launch_k<true, 0, 1, 2>(mhi, mlo, mb, a, st);
     return launch_k<true, 0, 1>(mhi, mlo, mb, a, st);
 }
 
@@ -1238,8 +1208,8 @@ cudaError_t launch_tc_dense(const __nv_bfloat16 *a_hi, const __nv_bfloat16 *a_lo
     whole_tiles(a, a.tiles_m * a.tiles_n);
     a.status = status;
     a.limit_ns = default_spin_limit_ns();
-    if (cg == 2) return launch_k<false, 3, 2, 1, true>(mhi, mlo, mb, a, st);
-    return launch_k<false, 3, 1, 1, true>(mhi, mlo, mb, a, st);
+    if (cg == 2) return launch_k<false, 3, 2, true>(mhi, mlo, mb, a, st);
+    return launch_k<false, 3, 1, true>(mhi, mlo, mb, a, st);
 }
 
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st) {
