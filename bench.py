@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-rows", action="store_true", help="skip the bitflip and MMD per-call timings")
     ap.add_argument("--cpu-sample-l", type=int, default=512)
     ap.add_argument("--cpu-sample-s", type=int, default=10_000)
+    ap.add_argument("--ref-sample-l", type=int, default=64,
+                    help="observables per timed step of the reference arm (the FP64 oracle)")
     return ap.parse_args()
 
 
@@ -130,24 +132,56 @@ def cpu_baseline(p, args, gpu_ev=None, gpu_se=None, gpu_grad_fn=None):
 
 
 def run_reference(args, rank, world):
+    """The FP64 oracle on the machine's host cores, on the same workload, metric and unit as the GPU arm. A full
+    step (10^4 observables x 10^4 samples x 10^5 gates) takes minutes of CPU time, so each timed step is a
+    bounded sample: --ref-sample-l observables with all samples and gates (expval, then the gradient of
+    sum_a w_a <Z_a>). The line's value is that sample extrapolated to all observables (the oracle's cost is
+    the sample parities, formed once per call, plus a part linear in the observables) and says so
+    ("extrapolated": true). The n=8 and n=300 configurations are also timed in full, once each."""
     if rank != 0:
         return
+    import oracle
+    oracle.build()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    oracle.set_threads(cores)
     p = workload(args)
-    steps = []
-    base = None
+    th = p.theta.astype(np.float64)
+    w = I.Rng(99).normal(p.l, 1)
+    ls = min(args.ref_sample_l, p.l)
+    A1 = p.A[:ls]
+    t0 = time.perf_counter()
+    oracle.parity(p.n, p.Z, p.G)  # the sample parities: the part of a call that does not scale with l
+    t_zpar = time.perf_counter() - t0
+    step_s = []
     for _ in range(args.warmup + args.steps):
-        base = cpu_baseline(p, args)
-        steps.append(base["value"])
-    timed = steps[args.warmup:]
-    ms = statistics.mean(timed)
-    base["value"] = ms
+        t0 = time.perf_counter()
+        oracle.expval(p.n, p.G, A1, p.Z, th)
+        oracle.expval_grad(p.n, p.G, A1, p.Z, th, -w[:ls] / p.s, None)
+        step_s.append(time.perf_counter() - t0)
+    t_sample = statistics.mean(step_s[args.warmup:])
+    per_obs = max(t_sample - 2 * t_zpar, 0.0) / ls
+    ms = (2 * t_zpar + per_obs * p.l) * 1e3
+    full = {}
+    for q in (I.tiny_local(), I.local300()):
+        wq = I.Rng(99).normal(q.l, 1)
+        t0 = time.perf_counter()
+        oracle.expval(q.n, q.G, q.A, q.Z, q.theta.astype(np.float64))
+        oracle.expval_grad(q.n, q.G, q.A, q.Z, q.theta.astype(np.float64), -wq / q.s, None)
+        full[q.name] = {"n": q.n, "m": q.m, "l": q.l, "s": q.s, "ms": round((time.perf_counter() - t0) * 1e3, 1),
+                        "extrapolated": False}
+    sample = (f"each step: oracle expval + expval_grad on {ls} of {p.l} observables x all {p.s} samples x all {p.m} "
+              f"gates, {t_sample:.2f} s mean over {args.steps} timed steps; value = 2 t_par + (t_step - 2 t_par) "
+              f"l / {ls} with t_par = {t_zpar:.2f} s (the sample parities, formed once per call)")
+    base = {"value": ms, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample, "extrapolated": True,
+            "sampled_fraction": round(ls / p.l, 5), "measured_step_s": round(t_sample, 3)}
     line = {
         "impl": "reference", "metric": METRIC, "value": ms, "unit": "ms", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded splitmix64)",
         "config": {"workload": workload_name(args, p), "n": p.n, "m": p.m, "l": p.l, "s": p.s,
                    "precision": "fp64 CPU oracle"},
-        "cpu_baseline": base,
+        "extrapolated": True, "sampled_fraction": round(ls / p.l, 5),
+        "cpu_baseline": base, "full_runs": full,
         "e2e": {"value": ms, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -155,21 +189,42 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ traffic
 
-def measured_traffic(kernel, sizes):
-    """DRAM bytes per contraction of `kernel` (summed over its launches) from the committed ncu capture
-    (profiles/dram_traffic.json), or None if the capture was of another
-    workload or the kernel sources changed since."""
+def tensor_source_sha():
+    """First 16 hex digits of sha256 over the tensor-core kernel sources (tc.cu, common.cuh): a committed ncu
+    record applies only while the sources still hash to the value it was captured with."""
     import hashlib
+    h = hashlib.sha256()
+    for f in ("tc.cu", "common.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2501_04776_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel, sizes):
+    """DRAM bytes per contraction of `kernel` (summed over its launches), from the committed ncu capture
+    (profiles/dram_traffic.json: a small case of the same kernel, scaled to the full launch by the tiles it
+    processes), or None if the kernel sources changed since the capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
-        h = hashlib.sha256()
-        for f in ("tc.cu", "common.cuh"):
-            h.update(open(os.path.join(ROOT, "paper_2501_04776_gb300", "csrc", f), "rb").read())
-        if h.hexdigest()[:16] != rec["source_sha"]:
+        if tensor_source_sha() != rec["source_sha"]:
             return None
-        if tuple(sizes) != (1000, 100_000, 10_000, 10_000):
+        if tuple(sizes) != tuple(rec["full_size"]):
             return None
-        return rec["kernels"][kernel]["traffic_bytes"]
+        return rec["kernels"][kernel]["traffic_bytes_full"]
+    except Exception:
+        return None
+
+
+def tensor_pipe_record(kernel):
+    """Tensor-pipe activity of `kernel` from the committed ncu capture (profiles/tensor_pipe.json: metric
+    sm__pipe_tensor_cycles_active, small case), with its source; None once the kernel sources changed."""
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "tensor_pipe.json")))
+        if tensor_source_sha() != rec["source_sha"]:
+            return None
+        k = rec["kernels"][kernel]
+        return {"pct_of_elapsed": k["pct_of_peak_sustained_elapsed"], "pct_of_active": k["pct_of_peak_sustained_active"],
+                "metric": rec["metric"], "case": rec["case"], "source": "profiles/tensor_pipe.json, "
+                + rec["summary"]}
     except Exception:
         return None
 
@@ -241,7 +296,34 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# ---------------------------------------------------- the other hot-path rows
+# ---------------------------------------------------- rooflines and the other hot-path rows
+
+def split_bf16_roofline(kt, dom, l, s, m, steps, peaks, step_ms=None, contractions=2):
+    """Roofline of the dominant tensor-core kernel on the method's work: the contraction of eq. Emat is
+    2 l s m flops (useful); the split-BF16 form runs two BF16 products (hi, lo) of it on the tensor pipe
+    (executed, 4 l s m), reported beside it. One contraction per launch group (the phase kernel's whole
+    tiles and split last round are timed together). The whole step's useful rate counts `contractions`
+    contractions (fused step: phase and gradient; two-call with recompute: three)."""
+    useful = 2.0 * l * s * m
+    peak = peaks.get("bf16_tflops_sustained") or 1700.0
+    per = kt[dom]["total_ms"] / max(1, steps)
+    ach = useful / (per * 1e-3) / 1e12
+    roof = {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
+            "frac": round(ach / peak, 4),
+            "work": "useful: 2 l s m flops per contraction (eq. Emat); the split's second BF16 product is not counted",
+            "flops_per_contraction": useful, "ms_per_contraction": round(per, 4),
+            "launches_per_contraction": round(kt[dom]["launches"] / max(1, steps), 2),
+            "executed": {"tflops": round(2 * ach, 1), "frac": round(2 * ach / peak, 4),
+                         "flops_per_contraction": 2 * useful,
+                         "note": "two BF16 products (hi and lo parts of 2 theta, or of W) per contraction on the "
+                                 "tensor pipe"},
+            "tensor_pipe": tensor_pipe_record(dom),
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
+            if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
+    if step_ms:
+        st = contractions * useful / (step_ms * 1e-3) / 1e12
+        roof["step_useful"] = {"tflops": round(st, 1), "frac": round(st / peak, 4), "contractions": contractions}
+    return roof
 
 def generator_pairs(n, G):
     """Number of distinct qubit pairs that carry a weight-2 generator
@@ -420,15 +502,7 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
         kt = _kernel_times(lib)
         if prec == _lib.SPLIT_BF16:
             dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
-            executed = 4.0 * lm * sm * mm  # one contraction per call (a split last round is a second launch)
-            peak = peaks.get("bf16_tflops_sustained") or 1700.0
-            per_call = kt[dom]["total_ms"] / max(1, args.steps)
-            ach = executed / (per_call * 1e-3) / 1e12
-            roof = {"bound": "tensor", "kernel": dom, "achieved": round(ach, 1), "peak": peak, "unit": "TFLOP/s",
-                    "frac": round(ach / peak, 4), "flops_per_contraction": executed,
-                    "ms_per_contraction": round(per_call, 4),
-                    "launches_per_contraction": round(kt[dom]["launches"] / max(1, args.steps), 2),
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"}
+            roof = split_bf16_roofline(kt, dom, lm, sm, mm, args.steps, peaks, statistics.mean(ms), 2)
         elif prec == _lib.LOWORDER_FP32:
             roof = loworder_roofline(kt, clocks, p.n, p.G, sm, peaks)
         else:
@@ -461,6 +535,194 @@ def other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l
             del graph
         del ws
     return out
+
+
+# ------------------------------------------------ the other workload shapes
+
+PREC_CODE = {"split_bf16": 1, "fp32": 0, "sparse_fp32": 2, "loworder_fp32": 3}
+
+
+def alu_peak(clocks, per_lane_per_clock=1):
+    """FP32 SIMT peak: 152 SMs x 128 lanes x max SM clock (x 2 for an FMA counted as two flops)."""
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    return 152 * 128 * per_lane_per_clock * mhz * 1e6 / 1e12
+
+
+def row_roofline(prec, kt, p, steps, peaks, clocks, api, dev_A, dev_G, step_ms, contractions, fused):
+    """Roofline of a row's dominant kernel, by form: split BF16 on the tensor pipe (useful 2 l s m per
+    contraction), FP32 on the FMA pipe (2 l s m per launch), row-sparse on FP32 adds (nnz(P_A) s per pass,
+    twice in the fused one-pass kernel), low-order on its pair contractions."""
+    l, s, m = p.A.shape[0], p.Z.shape[0], p.G.shape[0]
+    if prec == "split_bf16":
+        dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
+        return split_bf16_roofline(kt, dom, l, s, m, steps, peaks, step_ms, contractions)
+    if prec == "fp32":
+        dom = max(("phase_fp32", "recompute_fp32", "grad_fp32"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
+        ach = 2.0 * l * s * m / (kt[dom]["avg_ms"] * 1e-3) / 1e12
+        peak = alu_peak(clocks, 2)
+        return {"bound": "alu", "kernel": dom, "achieved": round(ach, 2), "peak": round(peak, 1), "unit": "TFLOP/s",
+                "frac": round(ach / peak, 4), "flops_per_launch": 2.0 * l * s * m,
+                "peak_source": "FP32 FMA: 152 SMs x 128 lanes x 2 x max SM clock"}
+    if prec == "sparse_fp32":
+        nnz = nnz_parities(api, p.n, dev_A, dev_G)
+        adds = (2 if fused else 1) * nnz * s
+        ach = adds / (kt["phase_sparse"]["avg_ms"] * 1e-3) / 1e12
+        peak = alu_peak(clocks)
+        return {"bound": "alu", "kernel": "phase_sparse", "achieved": round(ach, 2), "peak": round(peak, 1),
+                "unit": "Tadd/s", "frac": round(ach / peak, 4), "adds_per_launch": adds, "nnz_PA": nnz,
+                "density_PA": round(nnz / (l * m), 5), "peak_source": "FP32 add: 152 SMs x 128 lanes x max SM clock"}
+    return loworder_roofline(kt, clocks, p.n, p.G, s, peaks)
+
+
+def sampled_oracle_errors(p, idx, ev, se, grad_fn):
+    """Error of a GPU result against the FP64 oracle on the sampled observables idx, with the oracle
+    restricted to the gates that anticommute with at least one of them (every other gate adds exactly zero
+    to their phases and has an exactly zero gradient entry for a loss on them), on all samples."""
+    import oracle
+    A = p.A[idx]
+    J = np.nonzero(oracle.parity(p.n, A, p.G).any(axis=0))[0]
+    G, th = p.G[J], p.theta.astype(np.float64)[J]
+    S1, S2 = np.zeros(idx.size), np.zeros(idx.size)
+    for i0 in range(0, p.Z.shape[0], 4096):
+        _, _, s1, s2 = oracle.expval(p.n, G, A, p.Z[i0:i0 + 4096], th)
+        S1 += s1
+        S2 += s2
+    s = p.Z.shape[0]
+    want_ev = S1 / s
+    want_se = np.sqrt(np.maximum(S2 / s - want_ev ** 2, 0.0) / s)
+    alpha = np.zeros(p.A.shape[0])
+    alpha[idx] = I.Rng(7).normal(idx.size, 1) / s
+    want_g = np.zeros(p.G.shape[0])
+    for i0 in range(0, s, 4096):
+        want_g[J] += oracle.expval_grad(p.n, G, A, p.Z[i0:i0 + 4096], th, alpha[idx], None)
+    g = grad_fn(alpha)
+    return {"observables_checked": int(idx.size), "gates_relevant": int(J.size),
+            "max_abs_err_expval": float(np.max(np.abs(ev[idx] - want_ev))),
+            "max_abs_err_std_err": float(np.max(np.abs(se[idx] - want_se))),
+            "grad_rel_l2": float(np.linalg.norm(g - want_g) / np.linalg.norm(want_g))}
+
+
+def workload_rows(args, lib, dev, st, timed, peaks, clocks):
+    """The paper's other benchmark configurations (Sec. 4.1, 4.2), each timed through the C ABI on its own
+    synthetic workload: the n=300 one- and two-body circuit (estimates, then the gradient of sum_a w_a <Z_a>
+    as autograd runs them), the 1e5-gate random circuit at n=100 and n=5000 (one fused call), the
+    million-gate circuit in all three forms that apply (one fused call), and 50 Adam steps of the MMD
+    training workload. FP64 errors on sampled observables come from the CPU oracle (skipped with
+    --no-cpu-baseline)."""
+    import torch
+    from paper_2501_04776_gb300 import _lib, api, train
+    P = ctypes.c_void_p
+    specs = [
+        ("local300", lambda: I.local300(), [("split_bf16", 3, 2), ("fp32", 2, 1)], False, 8),
+        ("random_gates_n100", lambda: I.random_gates(n=100), [("split_bf16", 3, 2), ("fp32", 1, 1)], True, 8),
+        ("random_gates_n5000", lambda: I.random_gates(n=5000), [("split_bf16", 3, 2), ("fp32", 1, 1)], True, 8),
+        ("million_gates", lambda: I.million_gates(),
+         [("split_bf16", 2, 1), ("sparse_fp32", 2, 1), ("loworder_fp32", 5, 2)], True, 6),
+    ]
+    rows = {}
+    for name, make, forms, fused, nsample in specs:
+        try:
+            p = make()
+            n, m, l, s = p.n, p.G.shape[0], p.A.shape[0], p.Z.shape[0]
+            G, A, Z = (api.to_device_bits(x, dev) for x in (p.G, p.A, p.Z))
+            th = torch.from_numpy(p.theta).to(dev)
+            w = I.Rng(99).normal(l, 1)
+            al = torch.from_numpy(-w / s).to(dev)
+            ev = torch.empty(l, dtype=torch.float64, device=dev)
+            se = torch.empty_like(ev)
+            g = torch.empty(m, dtype=torch.float64, device=dev)
+            row = {"workload": p.name, "n": n, "m": m, "l": l, "s": s,
+                   "step": "one iqp_expval_value_and_grad call" if fused else
+                   "iqp_expval(_keep_phi), then iqp_expval_grad(_from_phi) (the autograd pair; Phi kept where the "
+                   "form allows)", "forms": {}}
+            for prec, steps, warm in forms:
+                code = PREC_CODE[prec]
+                nb = max(lib.iqp_workspace_bytes(_lib.OP_EXPVAL, n, m, l, s, 0, code),
+                         lib.iqp_workspace_bytes(_lib.OP_EXPVAL_GRAD, n, m, l, s, 0, code))
+                ws = torch.zeros(nb, dtype=torch.uint8, device=dev)
+                keep = code in api.KEEP_PHI and not fused
+                phi = torch.empty((l, api.phi_ld(s)) if keep else (1, 64), dtype=torch.float32, device=dev)
+                args_bits = (n, P(G.data_ptr()), m, G.shape[1], P(A.data_ptr()), l, A.shape[1], P(Z.data_ptr()), s,
+                             Z.shape[1], P(th.data_ptr()))
+
+                def call(args_bits=args_bits, code=code, ws=ws, phi=phi, keep=keep):
+                    if fused:
+                        _lib.check(lib.iqp_expval_value_and_grad(*args_bits, P(al.data_ptr()), None, code,
+                                                                 P(ev.data_ptr()), P(se.data_ptr()), P(g.data_ptr()),
+                                                                 P(ws.data_ptr()), ws.numel(), st), "value_and_grad")
+                    elif keep:
+                        _lib.check(lib.iqp_expval_keep_phi(*args_bits, code, P(ev.data_ptr()), P(se.data_ptr()),
+                                                           P(phi.data_ptr()), phi.shape[1], P(ws.data_ptr()),
+                                                           ws.numel(), st), "keep_phi")
+                        _lib.check(lib.iqp_expval_grad_from_phi(*args_bits, P(al.data_ptr()), None, code,
+                                                                P(phi.data_ptr()), phi.shape[1], P(g.data_ptr()),
+                                                                P(ws.data_ptr()), ws.numel(), st), "grad_from_phi")
+                    else:
+                        _lib.check(lib.iqp_expval(*args_bits, code, P(ev.data_ptr()), P(se.data_ptr()),
+                                                  P(ws.data_ptr()), ws.numel(), st), "expval")
+                        _lib.check(lib.iqp_expval_grad(*args_bits, P(al.data_ptr()), None, code, P(g.data_ptr()),
+                                                       P(ws.data_ptr()), ws.numel(), st), "expval_grad")
+
+                ms, launches = timed(None, steps, warm, profile=True, fn=call)
+                kt = _kernel_times(lib)
+                status = lib.iqp_read_status(P(ws.data_ptr()), ws.numel(), st)
+                mean_ms = statistics.mean(ms)
+                contractions = 2 if (fused or keep) else 3
+                f = {"ms_per_call": round(mean_ms, 3), "calls_timed": steps, "gpu_launches_per_call":
+                     round(launches / steps, 1), "device_status": int(status), "kernels": kt,
+                     "roofline": row_roofline(prec, kt, p, steps, peaks, clocks, api, A, G, mean_ms, contractions,
+                                              fused)}
+                if not args.no_cpu_baseline:
+                    call()
+                    torch.cuda.synchronize()
+                    evh, seh = ev.cpu().numpy(), se.cpu().numpy()
+
+                    def grad_fn(alpha_np, args_bits=args_bits, code=code, ws=ws):
+                        a2 = torch.from_numpy(alpha_np).to(dev)
+                        g2 = torch.empty(m, dtype=torch.float64, device=dev)
+                        _lib.check(lib.iqp_expval_grad(*args_bits, P(a2.data_ptr()), None, code, P(g2.data_ptr()),
+                                                       P(ws.data_ptr()), ws.numel(), st), "expval_grad")
+                        return g2.cpu().numpy()
+                    idx = np.unique(np.sort(I.Rng(77).integers(nsample, l, 1)))
+                    f["error_vs_fp64"] = sampled_oracle_errors(p, idx, evh, seh, grad_fn)
+                row["forms"][prec] = f
+                del ws, phi
+                torch.cuda.empty_cache()
+            rows[name] = row
+            del G, A, Z
+            torch.cuda.empty_cache()
+        except Exception as e:  # a failed row is reported, the headline line still prints
+            rows[name] = {"error": repr(e)[:400]}
+
+    # 50 Adam steps of the MMD^2 loss (training workload: fresh observables and samples drawn on the device
+    # every step), in the low-order form and in split BF16.
+    p = I.mmd_training()
+    adam = {"workload": p.name + ", 50 Adam steps, lr 1e-3, device-drawn observables and samples", "forms": {}}
+    for prec in ("loworder_fp32", "split_bf16"):
+        try:
+            train.adam_mmd(p, steps=2, lr=1e-3, precision=prec, device_rng=True)  # warm-up (and the build)
+            torch.cuda.synchronize()
+            lib.iqp_profile_reset()
+            lib.iqp_profile_enable(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, losses = train.adam_mmd(p, steps=50, lr=1e-3, precision=prec, device_rng=True)
+            e1.record()
+            torch.cuda.synchronize()
+            lib.iqp_profile_enable(0)
+            kt = _kernel_times(lib)
+            ms = e0.elapsed_time(e1) / 50
+            if prec == "split_bf16":
+                dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
+                roof = split_bf16_roofline(kt, dom, p.A.shape[0], p.Z.shape[0], p.G.shape[0], 50, peaks, ms, 2)
+            else:
+                roof = loworder_roofline(kt, clocks, p.n, p.G, p.Z.shape[0], peaks)
+            adam["forms"][prec] = {"ms_per_step": round(ms, 3), "loss_first": losses[0], "loss_last": losses[-1],
+                                   "kernels": kt, "roofline": roof}
+        except Exception as e:
+            adam["forms"][prec] = {"error": repr(e)[:400]}
+    rows["mmd_training_adam"] = adam
+    return rows
 
 
 # ---------------------------------------------------------------- GPU arm
@@ -598,21 +860,9 @@ def main():
         pass
     if prec == _lib.SPLIT_BF16:
         dom = max(("phase_tc", "recompute_tc", "grad_tc"), key=lambda k: kt.get(k, {}).get("total_ms", 0.0))
-        traffic = measured_traffic(dom, (n, m, l, s))
-        # two BF16 products (hi, lo) of 2*l*s*m flops per contraction; one
-        # contraction per step, in one launch or (a split last round of
-        # tiles) two, timed together
-        executed = 4.0 * l * s * m
-        peak = peaks.get("bf16_tflops_sustained") or 1700.0
-        per_step = kt[dom]["total_ms"] / max(1, args.steps)
-        achieved = executed / (per_step * 1e-3) / 1e12
-        roof = {"bound": "tensor", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "unit": "TFLOP/s", "frac": round(achieved / peak, 4), "traffic": traffic,
-                "flops_per_contraction": executed, "ms_per_contraction": round(per_step, 4),
-                "launches_per_contraction": round(kt[dom]["launches"] / max(1, args.steps), 2),
-                "useful_tflops": round(achieved / 2, 1),
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"
-                if "bf16_tflops_sustained" in peaks else "fallback 1.7 PFLOP/s sustained (of fallback)"}
+        roof = split_bf16_roofline(kt, dom, l, s, m, args.steps, peaks, ms,
+                                   contractions=2 if args.step == "fused" else 3)
+        roof["traffic"] = measured_traffic(dom, (n, m, l, s))
     elif prec == _lib.LOWORDER_FP32:
         roof = loworder_roofline(kt, clocks, n, p.G, s, peaks)
         roof["traffic"] = None
@@ -700,6 +950,7 @@ def main():
         line["fp32_form"] = fp32
     if not args.no_rows and prec == _lib.SPLIT_BF16:
         line["rows"] = other_rows(args, lib, dev, st, timed, peaks, clocks, G, A, theta, w, n, m, l)
+        line["rows"].update(workload_rows(args, lib, dev, st, timed, peaks, clocks))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         def gpu_grad_fn(alpha_np):
             al = torch.from_numpy(alpha_np).to(dev)

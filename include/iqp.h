@@ -26,7 +26,9 @@
  *    used from several host threads at once.
  *  - Errors: host-side argument checks run before any launch and return a
  *    status; nothing is launched then. Device-side failures (a bounded wait
- *    that ran out) set a status word inside `ws`, which iqp_read_status()
+ *    that ran out) set a status word inside `ws` (its first 4 bytes, which
+ *    must be zero when a workspace is first used: a zeroed allocation, or
+ *    after iqp_read_status, which clears it), which iqp_read_status()
  *    returns. Nothing aborts, exits or traps.
  *  - Outputs are float64. theta is float32 on the device.
  */

@@ -16,7 +16,7 @@ cudaError_t launch_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ld
                           int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt, cudaStream_t st);
 cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G,
                                  int64_t m, int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
-                                 uint64_t *RT, cudaStream_t st);
+                                 uint64_t *RT, cudaStream_t st, const int4 *sup = nullptr);
 cudaError_t launch_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,
                               int64_t ldx, int64_t *T, cudaStream_t st);
 cudaError_t launch_theta_prep(const float *theta, int64_t m, int64_t mpad, float *c32, __nv_bfloat16 *hi,
@@ -36,6 +36,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
                             cudaStream_t st, iqp_status *why);
 cudaError_t launch_w_from_phi(const Plan &p, void *ws, const double *alpha, const double *beta, cudaStream_t st);
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why);
+int64_t grad_tc_rows(const Plan &p);
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st);
 int64_t sparse_part_samples();
 cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
@@ -108,7 +109,7 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
                                        : kPartColsSimt;
     p.ldc = round_up(n, 4);
     p.nparts = cdiv(s, p.pw);
-    p.natile = cdiv(l, kATile);
+    p.natile = 2 * cdiv(l, kATile);  // enough for every gradient kernel form (at least 128 observables per tile)
     const bool grad = op == IQP_OP_EXPVAL_GRAD || op == IQP_OP_MMD_LOSS_GRAD || op == IQP_OP_EXPVAL_INDEP_GRAD ||
                       op == IQP_OP_MMD_LOSS_GRAD_INDEP;
     const bool mmd = op == IQP_OP_MMD_LOSS || op == IQP_OP_MMD_LOSS_GRAD || op == IQP_OP_MMD_LOSS_INDEP ||
@@ -147,7 +148,7 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_T = take(mmd ? l * 8 : 0);
     p.off_terms = take(mmd ? l * 8 : 0);
     p.off_zt = take(indep ? l * n * p.ldzt * 8 : 0);  // every batch transposed: n rows of bits over samples
-    p.off_sup = take(indep || lo ? m * 16 : 0);       // int4 support list per gate
+    p.off_sup = take(m * 16);  // int4 support list per gate (parity gathers, independent batches, low-order)
     // MMD gradient (split BF16, row-sparse; shared batches): Phi kept from
     // the statistics pass, so W needs no second phase pass (the loss's alpha,
     // beta come between). The low-order form keeps it in its W buffer.
@@ -319,18 +320,19 @@ iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, cons
                                   at<unsigned long long>(ws, p.off_gpart), at<uint32_t>(ws, p.off_status), st));
         return IQP_OK;
     }
+    const int4 *sup = at<int4>(ws, p.off_sup);
+    IQP_TRY(launch_support_list(G, p.m, ldg, p.n, at<int4>(ws, p.off_sup), st));
     IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
-                                 at<uint64_t>(ws, p.off_pat), p.ldlt, rt, st));
+                                 at<uint64_t>(ws, p.off_pat), p.ldlt, rt, st, sup));
     if (p.indep) {
         IQP_TRY(launch_bit_transpose_batched(Z, p.l, p.s, p.n, ldz, at<uint64_t>(ws, p.off_zt), p.ldzt, st));
-        IQP_TRY(launch_support_list(G, p.m, ldg, p.n, at<int4>(ws, p.off_sup), st));
         IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, at<float>(ws, p.off_c), nullptr, nullptr, st));
         return IQP_OK;
     }
     // The sparse form reads only P_Z^T (bits over samples).
     IQP_TRY(launch_parity_gather(p.n, Z, p.s, ldz, G, p.m, ldg,
                                  p.prec == IQP_SPARSE_FP32 ? nullptr : at<uint64_t>(ws, p.off_pz), p.ldp,
-                                 at<uint64_t>(ws, p.off_pzt), p.ldzt, rt, st));
+                                 at<uint64_t>(ws, p.off_pzt), p.ldzt, rt, st, sup));
     if (p.prec == IQP_SPLIT_BF16) {
         __nv_bfloat16 *hi = at<__nv_bfloat16>(ws, p.off_c);
         IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, nullptr, hi, hi + p.mpad, st));
@@ -404,7 +406,7 @@ iqp_status backward(const Plan &p, void *ws, const double *alpha, const double *
         IQP_TRY(launch_grad_simt(W, p.ldw, at<uint64_t>(ws, p.off_pz), at<uint64_t>(ws, p.off_pa), p.ldp, p.l, p.s,
                                  p.m, gpart, st));
     }
-    IQP_TRY(launch_grad_reduce(gpart, p.natile, p.m, grad, st));
+    IQP_TRY(launch_grad_reduce(gpart, p.prec == IQP_SPLIT_BF16 ? grad_tc_rows(p) : cdiv(p.l, kATile), p.m, grad, st));
     return IQP_OK;
 }
 
@@ -659,7 +661,7 @@ iqp_status iqp_expval_value_and_grad(int64_t n, const uint64_t *G, int64_t m, in
     IQP_TRY(launch_finalize(at<double2>(ws, p.off_part), p.nparts, p.pw, p.l, p.s, expval, std_err, nullptr, nullptr,
                             st));
     if (launch_grad_tc(p, ws, st, &why) != cudaSuccess) return why != IQP_OK ? why : IQP_ERR_CUDA;
-    IQP_TRY(launch_grad_reduce(at<double>(ws, p.off_gpart), p.natile, p.m, grad, st));
+    IQP_TRY(launch_grad_reduce(at<double>(ws, p.off_gpart), grad_tc_rows(p), p.m, grad, st));
     return IQP_OK;
 }
 
@@ -775,8 +777,10 @@ iqp_status bitflip_core(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, co
     Plan p = make_plan(IQP_OP_BITFLIP, n, m, l, 1, 0, IQP_FP32);
     if ((rc = check_ws(p, ws, ws_bytes)) != IQP_OK) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
+    IQP_TRY(launch_support_list(G, m, ldg, n, at<int4>(ws, p.off_sup), st));
     IQP_TRY(launch_parity_gather(n, A, l, lda, G, m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
-                                 at<uint64_t>(ws, p.off_pat), p.ldlt, at<uint64_t>(ws, p.off_rt), st));
+                                 at<uint64_t>(ws, p.off_pat), p.ldlt, at<uint64_t>(ws, p.off_rt), st,
+                                 at<int4>(ws, p.off_sup)));
     double *c = at<double>(ws, p.off_c), *t = c + p.mpad;
     IQP_TRY(launch_bitflip_gates(theta, m, p.mpad, c, t, st));
     double *ev = expval ? expval : at<double>(ws, p.off_part);

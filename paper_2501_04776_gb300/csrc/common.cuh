@@ -16,7 +16,8 @@ namespace iqp {
 
 constexpr int kPartColsSimt = 128;  // samples per (S, M2) partial, FP32 form
 constexpr int kPartColsTc = 64;     // samples per (S, M2) partial, tensor-core form
-constexpr int kATile = 128;      // observables per gradient partial row
+constexpr int kATile = 128;      // observables per gradient partial row (single-CTA gradient kernel)
+constexpr int kGradObs = 256;    // observables per tile of the CTA-pair gradient kernel (two partial rows each)
 // Split phase tiles: one 128 x 256 FP32 partial accumulator per (part, CTA),
 // for at most kMaxSplitCtas CTAs, then one int counter per (tile, CTA).
 constexpr int64_t kSplitSlotFloats = 128 * 256;
@@ -37,7 +38,7 @@ struct Plan {
     int64_t ldw;    // elements per row of W (multiple of 64)
     int64_t pw;     // samples per (S, M2) partial
     int64_t nparts; // (S, M2) partials per observable: ceil(s / pw)
-    int64_t natile; // ceil(l / 128)
+    int64_t natile; // room for gradient partial rows: 2 ceil(l / 128)
     size_t off_status, off_pa, off_pz, off_pzt, off_pat, off_rt, off_c, off_part, off_w, off_gpart;
     size_t off_ab, off_s12, off_T, off_terms, off_zt, off_sup, total;
     // low-order form: C (+ d), M = C S, V, H, single-gate partials; ldc floats per row of C and H
@@ -196,6 +197,18 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, uint64_
         : "memory");
 }
 
+// 2D tiled TMA load into this CTA's shared memory whose completion (tx
+// bytes) is signalled to an mbarrier of the CTA pair given by its
+// shared::cluster address `bar_cluster` (the leader's barrier, so that one
+// barrier tracks both CTAs' halves of a pair operand).
+__device__ __forceinline__ void tma_load_2d_pair(void *dst, const void *tmap, uint32_t bar_cluster, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(tmap), "r"(x), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+
 // Prefetch the 2D tile of `tmap` at {x, y} into L2 (no shared memory, no barrier).
 __device__ __forceinline__ void tma_prefetch_2d(const void *tmap, int x, int y) {
     asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(tmap), "r"(x), "r"(y)
@@ -324,6 +337,169 @@ __device__ __forceinline__ void umma_f16_pair(uint32_t d_tmem, uint64_t a_desc, 
         : "memory");
 }
 
+// Pair MMA with the A operand in tensor memory: rows 0..127 of A are TMEM
+// lanes 0..127 of this CTA at column address `a_tmem`, rows 128..255 the same
+// lanes and columns of the peer's TMEM; a 16-bit A element (row r, k) is half
+// k & 1 (0 = low) of the 32-bit cell (lane r, column a_tmem + k / 2).
+__device__ __forceinline__ void umma_f16_pair_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                                 uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Two MMAs of one K step, issued back to back: D (+)= A1 B1 (accumulating
+// iff `acc` != 0), then D += A2 B2. The split-BF16 hi and lo products share one
+// operand; each operand is a shared-memory descriptor or, where named
+// `*_tmem`, a TMEM address. Pair forms: cta_group::2, issued by the even CTA.
+__device__ __forceinline__ void umma2_pair_ss(uint32_t d, uint64_t a1, uint64_t a2, uint64_t b, uint32_t idesc,
+                                              uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "setp.eq.b32 q, %5, %5;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %3, %4, p;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %2, %3, %4, q;\n\t}\n"
+        ::"r"(d), "l"(a1), "l"(a2), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma2_pair_ts(uint32_t d, uint32_t a1_tmem, uint32_t a2_tmem, uint64_t b,
+                                              uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "setp.eq.b32 q, %5, %5;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %3, %4, p;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%2], %3, %4, q;\n\t}\n"
+        ::"r"(d), "r"(a1_tmem), "r"(a2_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma2_pair_ts_b(uint32_t d, uint32_t a_tmem, uint64_t b1, uint64_t b2,
+                                                uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "setp.eq.b32 q, %5, %5;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %4, p;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %3, %4, q;\n\t}\n"
+        ::"r"(d), "r"(a_tmem), "l"(b1), "l"(b2), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma2_ss(uint32_t d, uint64_t a1, uint64_t a2, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.b32 p, %5, 0;\n\t"
+        "setp.eq.b32 q, %5, %5;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %4, p;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %4, q;\n\t}\n"
+        ::"r"(d), "l"(a1), "l"(a2), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// One operand stage of MMAs from a single asm statement (descriptors and
+// TMEM addresses of the later K steps formed inside it), so that the issuing
+// thread spends as few instructions as possible per MMA. Every stage issues
+// the hi and lo products of each 16-wide K step back to back into D; the
+// first MMA accumulates iff `acc` != 0, every later one accumulates.
+// Shared-memory operand descriptors advance 32 bytes (2 in the start-address
+// field) per K step within a 128-byte swizzle atom.
+// Four K steps, all operands in shared memory (A hi, A lo, B).
+__device__ __forceinline__ void umma_stage4_pair_ss(uint32_t d, uint64_t ahi, uint64_t alo, uint64_t b, uint32_t idesc,
+                                             uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t.reg .b64 h, l, bb;\n\t"
+        "setp.ne.b32 p, %5, 0;\n\tsetp.eq.b32 q, %5, %5;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %3, %4, p;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], %2, %3, %4, q;\n\t"
+        "add.s64 h, %1, 2;\n\tadd.s64 l, %2, 2;\n\tadd.s64 bb, %3, 2;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], h, bb, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], l, bb, %4, q;\n\t"
+        "add.s64 h, %1, 4;\n\tadd.s64 l, %2, 4;\n\tadd.s64 bb, %3, 4;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], h, bb, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], l, bb, %4, q;\n\t"
+        "add.s64 h, %1, 6;\n\tadd.s64 l, %2, 6;\n\tadd.s64 bb, %3, 6;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], h, bb, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], l, bb, %4, q;\n}\n"
+        ::"r"(d), "l"(ahi), "l"(alo), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_stage4_ss(uint32_t d, uint64_t ahi, uint64_t alo, uint64_t b, uint32_t idesc,
+                                             uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t.reg .b64 h, l, bb;\n\t"
+        "setp.ne.b32 p, %5, 0;\n\tsetp.eq.b32 q, %5, %5;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %3, %4, p;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %2, %3, %4, q;\n\t"
+        "add.s64 h, %1, 2;\n\tadd.s64 l, %2, 2;\n\tadd.s64 bb, %3, 2;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], h, bb, %4, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], l, bb, %4, q;\n\t"
+        "add.s64 h, %1, 4;\n\tadd.s64 l, %2, 4;\n\tadd.s64 bb, %3, 4;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], h, bb, %4, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], l, bb, %4, q;\n\t"
+        "add.s64 h, %1, 6;\n\tadd.s64 l, %2, 6;\n\tadd.s64 bb, %3, 6;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], h, bb, %4, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], l, bb, %4, q;\n}\n"
+        ::"r"(d), "l"(ahi), "l"(alo), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Four K steps, A hi / A lo in TMEM (64 columns: hi at ta, lo at ta + 32), B in shared memory.
+__device__ __forceinline__ void umma_stage4_pair_ts(uint32_t d, uint32_t ta, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t.reg .b32 th, tl;\n\t.reg .b64 bb;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
+        "add.u32 tl, %1, 32;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [tl], %2, %3, q;\n\t"
+        "add.u32 th, %1, 8;\n\tadd.u32 tl, %1, 40;\n\tadd.s64 bb, %2, 2;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [th], bb, %3, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [tl], bb, %3, q;\n\t"
+        "add.u32 th, %1, 16;\n\tadd.u32 tl, %1, 48;\n\tadd.s64 bb, %2, 4;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [th], bb, %3, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [tl], bb, %3, q;\n\t"
+        "add.u32 th, %1, 24;\n\tadd.u32 tl, %1, 56;\n\tadd.s64 bb, %2, 6;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [th], bb, %3, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [tl], bb, %3, q;\n}\n"
+        ::"r"(d), "r"(ta), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+// Eight K steps (two 128-byte K atoms of B, `atom` bytes apart), A in TMEM at
+// ta + 8 k, B hi / B lo in shared memory.
+__device__ __forceinline__ void umma_stage8_pair_ts_b(uint32_t d, uint32_t ta, uint64_t bhi, uint64_t blo, uint32_t idesc,
+                                             uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t.reg .b32 t;\n\t.reg .b64 h, l;\n\t"
+        "setp.ne.b32 p, %5, 0;\n\tsetp.eq.b32 q, %5, %5;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %4, p;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %3, %4, q;\n\t"
+        "add.u32 t, %1, 8;\n\tadd.s64 h, %2, 2;\n\tadd.s64 l, %3, 2;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], h, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], l, %4, q;\n\t"
+        "add.u32 t, %1, 16;\n\tadd.s64 h, %2, 4;\n\tadd.s64 l, %3, 4;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], h, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], l, %4, q;\n\t"
+        "add.u32 t, %1, 24;\n\tadd.s64 h, %2, 6;\n\tadd.s64 l, %3, 6;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], h, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], l, %4, q;\n\t"
+        "add.u32 t, %1, 32;\n\tadd.s64 h, %2, 1024;\n\tadd.s64 l, %3, 1024;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], h, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], l, %4, q;\n\t"
+        "add.u32 t, %1, 40;\n\tadd.s64 h, %2, 1026;\n\tadd.s64 l, %3, 1026;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], h, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], l, %4, q;\n\t"
+        "add.u32 t, %1, 48;\n\tadd.s64 h, %2, 1028;\n\tadd.s64 l, %3, 1028;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], h, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], l, %4, q;\n\t"
+        "add.u32 t, %1, 56;\n\tadd.s64 h, %2, 1030;\n\tadd.s64 l, %3, 1030;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], h, %4, q;\n\t"
+        "tcgen05.mma.cta_group::2.kind::f16 [%0], [t], l, %4, q;\n}\n"
+        ::"r"(d), "r"(ta), "l"(bhi), "l"(blo), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 // Arrive once on the barrier at `bar`'s offset in both CTAs of the pair when
 // all previously issued pair MMAs of this thread complete.
 __device__ __forceinline__ void umma_commit_pair(uint64_t *bar) {
@@ -358,6 +534,25 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         : "r"(taddr)
         : "memory");
 }
+
+// Store 8 columns of 32-bit words to TMEM lane (lane_base + t), no wait
+// (tmem_wait_st completes every store of the thread).
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+        : "memory");
+}
+// Store 16 columns of 32-bit words to TMEM lane (lane_base + t), no wait.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // Store 32 columns of 32-bit words to TMEM lane (lane_base + t), then wait.
 __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {

@@ -194,6 +194,106 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
     }
 }
 
+// Support gather and transpose in one pass: for a tile of 512 gates x 512
+// rows, each P^T word is formed from the gates' supports (int4 list: first
+// three qubits and the count; gates with more than three qubits scan their
+// packed row) as the XOR of R^T rows, written to P^T, and the tile is
+// transposed in shared memory (as in k_bit_transpose) and written to P, so
+// P^T is never read back. R^T: n x ldrt32 words (bits over rows, zero past
+// `rows`); P^T: m x ldpt32 words; P: rows x ldp32 words (bits over gates,
+// zero past m).
+__global__ void __launch_bounds__(kTT) k_gather_transpose(const int4 *__restrict__ sup, const uint64_t *__restrict__ G,
+                                                           int64_t ldg, int64_t n, int64_t m, int64_t rows,
+                                                           const uint32_t *__restrict__ RT, int64_t ldrt32,
+                                                           uint32_t *__restrict__ PT, int64_t ldpt32,
+                                                           uint32_t *__restrict__ P, int64_t ldp32, int64_t gx) {
+    __shared__ uint32_t tin[kTT][kTW + 1];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t bid = blockIdx.x;
+    const int64_t r0 = (bid % gx) * kTT;   // gates (P^T rows) of this tile
+    const int64_t c0 = (bid / gx) * kTT;   // rows (P^T bit columns) of this tile
+    const int64_t w0 = c0 >> 5;
+#pragma unroll
+    for (int k = 0; k < kTW / 4; ++k) {
+        const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
+        const int64_t j = r0 + row;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (j < m && w0 + q < ldrt32) {
+            const int4 sp = sup[j];
+            if (sp.w <= 3) {
+                // ldrt32 is a multiple of 8 and w0 + q of 4: the 16-byte word is inside the row
+                if (sp.w > 0) {
+                    const uint4 a = *reinterpret_cast<const uint4 *>(RT + (int64_t)sp.x * ldrt32 + w0 + q);
+                    v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
+                }
+                if (sp.w > 1) {
+                    const uint4 a = *reinterpret_cast<const uint4 *>(RT + (int64_t)sp.y * ldrt32 + w0 + q);
+                    v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
+                }
+                if (sp.w > 2) {
+                    const uint4 a = *reinterpret_cast<const uint4 *>(RT + (int64_t)sp.z * ldrt32 + w0 + q);
+                    v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
+                }
+            } else {
+                // every qubit of the support, from the packed row
+                const int64_t nw = (n + 63) >> 6;
+                for (int64_t w = 0; w < nw; ++w) {
+                    uint64_t word = G[j * ldg + w];
+                    if (w == nw - 1 && (n & 63)) word &= (1ull << (n & 63)) - 1ull;
+                    while (word) {
+                        const int64_t qb = 64 * w + __ffsll((long long)word) - 1;
+                        word &= word - 1ull;
+                        const uint4 a = *reinterpret_cast<const uint4 *>(RT + qb * ldrt32 + w0 + q);
+                        v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
+                    }
+                }
+            }
+            *reinterpret_cast<uint4 *>(PT + j * ldpt32 + w0 + q) = v;
+        }
+        tin[row][q] = v.x;
+        tin[row][q + 1] = v.y;
+        tin[row][q + 2] = v.z;
+        tin[row][q + 3] = v.w;
+    }
+    __syncthreads();
+    for (int item = warp; item < kTW * (kTW + 1) / 2; item += kTT / 32) {
+        int rb = 0, rem = item;
+        while (rem >= kTW - rb) {
+            rem -= kTW - rb;
+            ++rb;
+        }
+        const int cb = rb + rem;
+        uint32_t x1 = tin[rb * 32 + lane][cb];
+        uint32_t x2 = tin[cb * 32 + lane][rb];
+#pragma unroll
+        for (int jj = 16; jj >= 1; jj >>= 1) {
+            const uint32_t lowm = jj == 16 ? 0x0000FFFFu
+                                  : jj == 8 ? 0x00FF00FFu
+                                  : jj == 4 ? 0x0F0F0F0Fu
+                                  : jj == 2 ? 0x33333333u
+                                            : 0x55555555u;
+            const uint32_t y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, jj);
+            const uint32_t y2 = __shfl_xor_sync(0xFFFFFFFFu, x2, jj);
+            x1 = (lane & jj) ? ((x1 & ~lowm) | ((y1 >> jj) & lowm)) : ((x1 & lowm) | ((y1 & lowm) << jj));
+            x2 = (lane & jj) ? ((x2 & ~lowm) | ((y2 >> jj) & lowm)) : ((x2 & lowm) | ((y2 & lowm) << jj));
+        }
+        tin[cb * 32 + lane][rb] = x1;
+        if (rb != cb) tin[rb * 32 + lane][cb] = x2;
+    }
+    __syncthreads();
+    const int64_t ow0 = r0 >> 5;
+#pragma unroll
+    for (int k = 0; k < kTW / 4; ++k) {
+        const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
+        const int64_t orow = c0 + row;
+        if (orow >= rows) continue;
+        // ldp32 is a multiple of 8 and ow0 + q of 4: whole 16-byte words
+        if (ow0 + q < ldp32)
+            *reinterpret_cast<uint4 *>(P + orow * ldp32 + ow0 + q) =
+                make_uint4(tin[row][q], tin[row][q + 1], tin[row][q + 2], tin[row][q + 3]);
+    }
+}
+
 // P^T[j][w] = XOR_{q in supp(g_j)} RT[q][w] for w < ldpt. One warp per
 // (gate, 256-word tile); the gate's support is scanned from its packed row.
 __global__ void __launch_bounds__(256) k_support_gather(const uint64_t *__restrict__ G, int64_t m, int64_t ldg,
@@ -339,12 +439,26 @@ cudaError_t launch_support_list(const uint64_t *G, int64_t m, int64_t ldg, int64
 
 // Support-gather parities: RT (n x ldpt words) is scratch; writes PT
 // (m x ldpt words: bits over rows, zero beyond `rows`) and, if P != nullptr,
-// P (rows x ldp words: bits over gates, zero beyond m).
+// P (rows x ldp words: bits over gates, zero beyond m). With the gates'
+// support list `sup` (and ldpt, ldp multiples of 4) P^T and P come from one
+// fused pass; without it P^T is gathered, then transposed into P.
 cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G,
                                  int64_t m, int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
-                                 uint64_t *RT, cudaStream_t st) {
+                                 uint64_t *RT, cudaStream_t st, const int4 *sup) {
     cudaError_t e = bit_transpose(R, rows, n, ldr, RT, ldpt, st);
     if (e != cudaSuccess) return e;
+    if (sup != nullptr && P != nullptr && ldpt % 4 == 0 && ldp % 4 == 0) {
+        // with the gates' support list (launch_support_list): P^T and P from one pass
+        const int64_t gx = cdiv(m, kTT);
+        const int64_t gy = cdiv(rows, kTT);
+        if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+        LaunchScope ls(IQP_KERNEL_PARITY, st);
+        k_gather_transpose<<<(unsigned)(gx * gy), kTT, 0, st>>>(sup, G, ldg, n, m, rows,
+                                                                  reinterpret_cast<const uint32_t *>(RT), 2 * ldpt,
+                                                                  reinterpret_cast<uint32_t *>(PT), 2 * ldpt,
+                                                                  reinterpret_cast<uint32_t *>(P), 2 * ldp, gx);
+        return cudaGetLastError();
+    }
     {
         dim3 grid((unsigned)cdiv(m, 8), (unsigned)cdiv(ldpt, 256));
         LaunchScope ls(IQP_KERNEL_PARITY, st);

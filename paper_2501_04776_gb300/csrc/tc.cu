@@ -1,14 +1,18 @@
 // Split-BF16 tensor-core (tcgen05 / TMEM) kernels for sm_103a.
 //
-// k_phase_tc: the phase contraction of eq. Emat, Phi = (2 theta . P_A) S_Z^T,
-// one 128 (observables) x 256 (samples) FP32 accumulator in TMEM per tile,
-// K = gates streamed in 64-wide stages. Operands never exist in HBM as
-// numbers: a TMA warp brings 256-gate slices of the parity bits (and of the
-// hi/lo BF16 split of 2 theta) into shared memory; sixteen producer warps
-// expand them into the 128-byte-swizzled K-major BF16 layout the MMA reads
-// (A_hi = hi_j [P_A], A_lo = lo_j [P_A], B = 1 - 2 P_Z, all exact in BF16);
-// one thread issues two tcgen05.mma per 16-gate step (hi and lo share B).
-// The epilogue runs in the producer warps straight from TMEM:
+// k_tc (phase modes): the phase contraction of eq. Emat,
+// Phi = (2 theta . P_A) S_Z^T, one 128 (observables) x 256 (samples) FP32
+// accumulator in TMEM per CTA and tile, K = gates streamed in 64-wide stages.
+// Operands never exist in HBM as numbers: a TMA warp brings 256-gate slices
+// of the parity bits (and of the hi/lo BF16 split of 2 theta) into shared
+// memory, and sixteen producer warps expand them: B = 1 - 2 P_Z into the
+// 128-byte-swizzled K-major BF16 layout in shared memory, and A_hi =
+// hi_j [P_A], A_lo = lo_j [P_A] (all exact in BF16) either straight into
+// TMEM with tcgen05.st (the default for CTA pairs: the MMA then reads A from
+// TMEM, and shared memory carries only B) or into shared memory like B
+// (IQP_PHASE_TMEM=0, and the one-CTA form). One thread issues two
+// tcgen05.mma per 16-gate step (hi and lo share B), a whole stage from one
+// asm statement. The epilogue runs in the producer warps straight from TMEM:
 //   mode 0: cos, per-observable (S, M2) partials over 64-sample groups, and
 //           Phi itself (FP32) when a gradient pass follows that reads it back
 //           (the MMD loss, the autograd pair; k_w_from_phi forms W from it);
@@ -21,29 +25,37 @@
 // bits as above, the FP32 accumulator stored as is (FP32 or FP64). The
 // low-order form's pair contractions M = C S and H = (s o V) S^T use it.
 //
-// k_grad_tc: the gradient contraction Q[a][j] = sum_i W[a][i] S_Z[i][j]
-// (Sec. 2.4, backward of eq. Emat), 128 observables x 256 gates per tile,
-// K = samples. W_hi / W_lo tiles arrive by TMA in the swizzled layout (three
-// operand stages, each W tile also prefetched into L2 eight stages ahead); the
-// +-1 operand is expanded from the transposed sample parities P_Z^T. The
-// epilogue masks by 2 P_A[a][j], reduces over the tile's observables with a
-// warp reduce-scatter and writes one FP64 partial per (observable tile, gate).
+// Gradient contraction (Sec. 2.4, backward of eq. Emat), two kernels:
+//  - k_grad_pair (default): CTA pairs in the transposed orientation,
+//    D[j][a] = sum_i S_Z[i][j] W[a][i] over 256 gates x 256 observables per
+//    tile, K = samples in 128-wide stages, the +-1 operand written into TMEM
+//    from P_Z^T bits, W_hi / W_lo by TMA; the epilogue masks by 2 P_A[a][j]
+//    (bits of P_A^T) and sums over the tile's observables per gate row
+//    (description at the kernel);
+//  - k_tc<GRAD> (IQP_GRAD_PAIR=0): one CTA per 128 observables x 256 gates,
+//    W tiles by TMA as A, the +-1 operand expanded into shared memory from
+//    P_Z^T, reduced over observables with a warp reduce-scatter.
+// Both write FP64 partials per (observable tile, gate) that k_grad_reduce
+// sums in a fixed order.
 //
 // Accumulation: the tensor core's FP32 accumulation rounds toward zero, so a
 // single accumulator over ~10^4 K-steps shrinks |Phi| by ~1e-4 relative. Each
 // tile therefore accumulates in chunks of `chunk` K-stages: a chunk starts a
 // fresh accumulator (TMEM columns 0..255) and, when it completes, the
-// producer warps add it into an FP32 running sum (columns 256..511) with
-// round-to-nearest adds. The epilogue reads accumulator + running sum.
+// producer warps add it into an FP32 running sum with round-to-nearest adds
+// (TMEM columns 256..511, or shared memory when A occupies those columns).
+// The epilogue reads accumulator + running sum. The pair gradient reduces
+// every chunk into its FP64 per-gate partials instead.
 //
 // CTA pairs: with CG = 2 the kernels run as clusters of two CTAs on two SMs.
-// A tile is 256 observables x 256 columns; each CTA holds 128 observables'
-// A rows and half (128 rows) of the B operand, and the even CTA issues
-// M256 x N256 pair MMAs (cta_group::2) that read both CTAs' shared memory and
-// write 128 accumulator rows into each CTA's TMEM. Per SM this halves the B
-// operand's expansion work and the tensor core's B reads from shared memory.
-// Both CTAs' producer warps arrive on the even CTA's stage barrier; stage and
-// chunk completions are signalled to both CTAs by one pair commit.
+// A phase tile is 256 observables x 256 samples; each CTA holds 128
+// observables' A rows and half (128 rows) of the B operand, and the even CTA
+// issues M256 x N256 pair MMAs (cta_group::2) that read both CTAs' operands
+// and write 128 accumulator rows into each CTA's TMEM. Per SM this halves the
+// B operand's expansion work and the tensor core's B reads. Both CTAs'
+// producer warps arrive on the even CTA's stage barrier (the odd CTA's through
+// one forwarding thread); stage and chunk completions are signalled to both
+// CTAs by one pair commit.
 //
 // Every wait is bounded (globaltimer); on expiry the CTA records
 // IQP_ERR_TIMEOUT, drains its in-flight copies and MMAs, frees TMEM and exits.
@@ -71,17 +83,25 @@ constexpr int kGroupCols = TN / (NGEN / 4);   // accumulator columns per epilogu
 constexpr int kGroupLoads = kGroupCols / 32;
 constexpr uint32_t kTmemCols = 512;   // accumulator (0..255) + running sum (256..511)
 constexpr uint32_t kSumCol = 256;
+// A-in-TMEM form: columns 256..511 hold the A operand of the four operand
+// stages instead of the running sum: stage os at 256 + 64 os, A_hi in its
+// first 32 columns (64 BF16 per lane), A_lo in the next 32.
+constexpr uint32_t kAColBase = 256;
+constexpr uint32_t kAColStage = 64;
 constexpr int kMaxOp = 4;
 constexpr int kWPrefetch = 8;  // gradient: W tiles prefetched into L2 this many stages ahead
 
-// Shared-memory layout for a CTA group of CG CTAs (CG = 1 or 2).
-template <int CG, bool ATMA>
+// Shared-memory layout for a CTA group of CG CTAs (CG = 1 or 2). ATM: the A
+// operand (hi / lo) lives in TMEM, so an operand stage in shared memory holds
+// only B, and the running sum of the accumulation chunks moves from TMEM to
+// shared memory (TM x TN FP32, as float4 groups of 4 columns, row-minor).
+template <int CG, bool ATMA, bool ATM = false>
 struct Cfg {
     static constexpr int TNB = TN / CG;      // B rows this CTA holds
-    static constexpr int NOP = CG == 2 ? 4 : (ATMA ? 3 : 2);  // operand stages
-    // Operand stage: A_hi (128 x 128 B), A_lo, B (TNB x 128 B).
-    static constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = 32768;
-    static constexpr uint32_t OP_BYTES = 32768 + TNB * 128;
+    static constexpr int NOP = (CG == 2 || ATM) ? 4 : (ATMA ? 3 : 2);  // operand stages
+    // Operand stage: A_hi (128 x 128 B), A_lo, B (TNB x 128 B); ATM: B only.
+    static constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = ATM ? 0 : 32768;
+    static constexpr uint32_t OP_BYTES = ATM ? TNB * 128 : 32768 + TNB * 128;
     // Bits stage: A bits (128 rows x 32 B), B bits (TNB rows x 32 B), c_hi, c_lo.
     static constexpr uint32_t BT_A = 0, BT_B = 4096;
     static constexpr uint32_t BT_CHI = BT_B + TNB * 32, BT_CLO = BT_CHI + 512;
@@ -90,10 +110,11 @@ struct Cfg {
     static constexpr uint32_t SM_BITS = SM_OP + NOP * OP_BYTES;
     static constexpr uint32_t SM_BAR = SM_BITS + NBITS * BT_BYTES;
     static constexpr uint32_t SM_RED = SM_BAR + 256;   // 4 x 256 floats (grad epilogue)
-    static constexpr uint32_t SM_END = SM_RED + 4 * 256 * 4;
+    static constexpr uint32_t SM_SUM = SM_RED + 4 * 256 * 4;  // ATM: running sum
+    static constexpr uint32_t SM_END = SM_SUM + (ATM ? TM * TN * 4 : 0);
     static constexpr uint32_t SMEM = SM_END + 1024;     // + alignment slack
     static constexpr uint32_t IDESC = idesc_bf16(TM * CG, TN);
-    static_assert(OP_BYTES % 1024 == 0 && BT_BYTES % 1024 == 0, "stage alignment");
+    static_assert(OP_BYTES % 1024 == 0 && BT_BYTES % 1024 == 0 && SM_SUM % 16 == 0, "stage alignment");
     static_assert(SMEM <= 232448, "shared memory");
 };
 
@@ -238,16 +259,59 @@ __device__ __forceinline__ bool wait_warp(uint64_t *b, uint32_t parity, volatile
     return __all_sync(0xFFFFFFFFu, got);
 }
 
+// wait_warp with cluster-scope acquire (the barrier completes from the peer CTA too).
+__device__ __forceinline__ bool wait_warp_cluster(uint64_t *b, uint32_t parity, volatile int *abort_flag,
+                                                  uint32_t *status, uint64_t lim) {
+    const bool got = mbar_wait_cluster(b, parity, abort_flag, status, lim);
+    return __all_sync(0xFFFFFFFFu, got);
+}
+
 // 32 columns of the tile at TMEM address `t`: the current accumulator plus,
-// when the tile was accumulated in more than one chunk, the running sum.
-__device__ __forceinline__ void load_sum32(uint32_t t, bool chunked, uint32_t (&r)[32]) {
+// when the tile was accumulated in more than one chunk, the running sum (in
+// TMEM at t + kSumCol, or, when `ss` is given, in shared memory: the 8 float4
+// groups of these columns for this thread's row at ss[0], ss[TM], ...).
+__device__ __forceinline__ void load_sum32(uint32_t t, bool chunked, uint32_t (&r)[32], const float4 *ss = nullptr) {
     tmem_ld32(t, r);
     if (chunked) {
+        if (ss != nullptr) {
+#pragma unroll
+            for (int e4 = 0; e4 < 8; ++e4) {
+                const float4 v = ss[e4 * TM];
+                r[4 * e4] = __float_as_uint(__uint_as_float(r[4 * e4]) + v.x);
+                r[4 * e4 + 1] = __float_as_uint(__uint_as_float(r[4 * e4 + 1]) + v.y);
+                r[4 * e4 + 2] = __float_as_uint(__uint_as_float(r[4 * e4 + 2]) + v.z);
+                r[4 * e4 + 3] = __float_as_uint(__uint_as_float(r[4 * e4 + 3]) + v.w);
+            }
+            return;
+        }
         uint32_t acc[32];
         tmem_ld32(t + kSumCol, acc);
 #pragma unroll
         for (int e = 0; e < 32; ++e) r[e] = __float_as_uint(__uint_as_float(r[e]) + __uint_as_float(acc[e]));
     }
+}
+
+// A-in-TMEM form: this warp's share of one 64-gate operand stage of A, the 16
+// gates [16 g, 16 g + 16) for the row of TMEM lane (32 quarter + lane): hi_j
+// (A_hi) and lo_j (A_lo) where bit j of `b16` (the row's parities of these
+// gates) is set, 0 elsewhere, two BF16 per 32-bit column (the lower gate in
+// the low half). chi / clo: the bits stage's hi / lo split of 2 theta; q: the
+// operand stage within the bits stage. `t` is the TMEM address of the warp's
+// first A_hi column; A_lo starts 32 columns further.
+__device__ __forceinline__ void expand_a_tmem(uint32_t b16, const uint8_t *chi, const uint8_t *clo, int q, int g,
+                                              uint32_t t) {
+    const uint32_t off = (uint32_t)q * 128u + (uint32_t)g * 32u;
+    const uint4 h0 = *reinterpret_cast<const uint4 *>(chi + off);
+    const uint4 h1 = *reinterpret_cast<const uint4 *>(chi + off + 16);
+    const uint4 l0 = *reinterpret_cast<const uint4 *>(clo + off);
+    const uint4 l1 = *reinterpret_cast<const uint4 *>(clo + off + 16);
+    const uint4 m0 = expand_mask(b16 & 0xFFu), m1 = expand_mask((b16 >> 8) & 0xFFu);
+    const uint32_t hv[8] = {h0.x & m0.x, h0.y & m0.y, h0.z & m0.z, h0.w & m0.w,
+                            h1.x & m1.x, h1.y & m1.y, h1.z & m1.z, h1.w & m1.w};
+    const uint32_t lv[8] = {l0.x & m0.x, l0.y & m0.y, l0.z & m0.z, l0.w & m0.w,
+                            l1.x & m1.x, l1.y & m1.y, l1.z & m1.z, l1.w & m1.w};
+    tmem_st8(t, hv);
+    tmem_st8(t + 32u, lv);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -346,11 +410,11 @@ __device__ __forceinline__ void store_out32(const TcArgs &args, int64_t row, int
 // on the stage loop). split_store: this warp's 32 rows x 64 columns of the
 // accumulator (+ running sum) into its part's slot. split_sum: the sum of
 // the tile's nsplit parts, in part order, into the accumulator columns.
-__device__ __noinline__ void split_store(float *dst, uint32_t tbase, bool chunked) {
+__device__ __noinline__ void split_store(float *dst, uint32_t tbase, bool chunked, const float4 *ss0) {
     uint32_t r[32];
 #pragma unroll 1
     for (int c = 0; c < kGroupLoads; ++c) {
-        load_sum32(tbase + c * 32, chunked, r);
+        load_sum32(tbase + c * 32, chunked, r, ss0 != nullptr ? ss0 + c * 8 * TM : nullptr);
 #pragma unroll
         for (int e = 0; e < 32; e += 4)
             *reinterpret_cast<float4 *>(dst + c * 32 + e) = make_float4(
@@ -386,17 +450,20 @@ __device__ __noinline__ void split_sum(const float *src0, int64_t part_stride, i
 // the gradient's W; for MODE 3, a dense split-BF16 matrix); AT = false: the
 // producer warps expand it from P_A bits and the hi/lo split of 2 theta.
 // CG = 1: one CTA per tile of 128 rows; CG = 2: a CTA pair per tile of 256 rows.
-template <bool GRAD, int MODE, int CG, bool AT, bool SPL>
+template <bool GRAD, int MODE, int CG, bool AT, bool SPL, bool TA>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
          const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
     constexpr bool ATMA = GRAD || AT;  // A operand by TMA
-    using C = Cfg<CG, ATMA>;
+    // A operand in TMEM, written by the producer warps (phase modes, CTA pairs)
+    constexpr bool ATM = TA && !GRAD && !AT && CG == 2;
+    using C = Cfg<CG, ATMA, ATM>;
     constexpr int NOP = C::NOP;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = aligned_smem(smem_raw);
     Bars *bar = reinterpret_cast<Bars *>(smem + C::SM_BAR);
     float *red = reinterpret_cast<float *>(smem + C::SM_RED);
+    float4 *sum4 = reinterpret_cast<float4 *>(smem + C::SM_SUM);  // ATM: running sum
     volatile int *abort_flag = &bar->abort_flag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint64_t lim = args.limit_ns;
@@ -430,7 +497,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_proxy_async_smem();
     }
     if (warp == 1) {
-        if (CG == 2) {
+        if constexpr (CG == 2) {
             tmem_alloc_pair(&bar->tmem_slot, kTmemCols);
             tmem_relinquish_pair();
         } else {
@@ -528,6 +595,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0 && leader) {
             uint32_t ito = 0;
             bool ok = true;
+            // operand descriptors of stage 0 (K step 0)
+            const uint32_t sb = smem_u32(smem + C::SM_OP);
+            const uint64_t d_b0 = sdesc_k128(sb + C::OP_B);
+            const uint64_t d_hi0 = sdesc_k128(sb + C::OP_A_HI), d_lo0 = sdesc_k128(sb + C::OP_A_LO);
             for (int64_t u = group0; u < nunits && ok; u += ngroups) {
                 int64_t t, uv;
                 int ks0, ks1;
@@ -547,25 +618,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t base = smem_u32(smem + C::SM_OP + os * C::OP_BYTES);
-                    const bool fresh = kc == 0;  // first stage of a chunk: overwrite the accumulator
-#pragma unroll
-                    for (int k = 0; k < KS / 16; ++k) {
-                        const uint64_t bdesc = sdesc_k128(base + C::OP_B + k * 32);
-                        const uint64_t ahi = sdesc_k128(base + C::OP_A_HI + k * 32);
-                        const uint64_t alo = sdesc_k128(base + C::OP_A_LO + k * 32);
-                        if (CG == 2) {
-                            umma_f16_pair(tmem, ahi, bdesc, C::IDESC, (fresh && k == 0) ? 0u : 1u);
-                            umma_f16_pair(tmem, alo, bdesc, C::IDESC, 1u);
-                        } else {
-                            umma_f16(tmem, ahi, bdesc, C::IDESC, (fresh && k == 0) ? 0u : 1u);
-                            umma_f16(tmem, alo, bdesc, C::IDESC, 1u);
-                        }
-                    }
-                    if (CG == 2) umma_commit_pair(&bar->op_empty[os]);
+                    // first stage of a chunk: overwrite the accumulator
+                    const uint32_t acc = kc == 0 ? 0u : 1u;
+                    // Descriptors of the stage's first K step (stage os is
+                    // os * OP_BYTES / 16 further in the start-address field).
+                    const uint64_t so = (uint64_t)(os * (C::OP_BYTES >> 4));
+                    // (one function may not mix cta_group::1 and ::2 forms)
+                    if constexpr (ATM)
+                        umma_stage4_pair_ts(tmem, tmem + kAColBase + os * kAColStage, d_b0 + so, C::IDESC, acc);
+                    else if constexpr (CG == 2)
+                        umma_stage4_pair_ss(tmem, d_hi0 + so, d_lo0 + so, d_b0 + so, C::IDESC, acc);
+                    else
+                        umma_stage4_ss(tmem, d_hi0 + so, d_lo0 + so, d_b0 + so, C::IDESC, acc);
+                    if constexpr (CG == 2) umma_commit_pair(&bar->op_empty[os]);
                     else umma_commit(&bar->op_empty[os]);
                     if (++kc == chunk || ks == ks1 - 1) {
-                        if (CG == 2) umma_commit_pair(&bar->acc_full);
+                        if constexpr (CG == 2) umma_commit_pair(&bar->acc_full);
                         else umma_commit(&bar->acc_full);
                         kc = 0;
                     }
@@ -573,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // Drain: all issued MMAs complete before TMEM is freed (and, for a
             // pair, before the peer may leave: the cluster barrier below).
-            if (CG == 2) umma_commit_pair(&bar->drain);
+            if constexpr (CG == 2) umma_commit_pair(&bar->drain);
             else umma_commit(&bar->drain);
             mbar_drain(&bar->drain, 0u, status, lim);
         } else if (CG == 2 && lane == 0) {
@@ -603,6 +671,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int quarter = warp & 3;      // TMEM lane quarter this warp may access
         const int group = (warp - 2) >> 2; // accumulator column group of the epilogue
         uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
+        const int rl = quarter * 32 + lane;  // accumulator row (TMEM lane) of this thread
+        // ATM: this thread's A parity bits of the current bits stage, 16 per
+        // operand stage (see expand_a_tmem), packed two stages per word
+        uint32_t abits01 = 0, abits23 = 0;
         bool ok = true;
         for (int64_t u = group0; u < nunits && ok; u += ngroups, ++tcount) {
             int ks0, ks1;
@@ -624,17 +696,43 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = false;
                     break;
                 }
+                const uint8_t *bits = smem + C::SM_BITS + bs * C::BT_BYTES;
+                if (ATM && q == 0) {
+                    // Row rl's 256 parity bits of this bits stage (8 words);
+                    // operand stage j needs bits [64 j + 16 group, +16), in
+                    // word 2 j + (group >> 1) at bit 16 (group & 1).
+                    const uint4 x0 = *reinterpret_cast<const uint4 *>(bits + C::BT_A + rl * 32);
+                    const uint4 x1 = *reinterpret_cast<const uint4 *>(bits + C::BT_A + rl * 32 + 16);
+                    const bool odd = (group >> 1) & 1;
+                    const uint32_t sh = (uint32_t)(group & 1) * 16u;
+                    const uint32_t w0 = odd ? x0.y : x0.x, w1 = odd ? x0.w : x0.z;
+                    const uint32_t w2 = odd ? x1.y : x1.x, w3 = odd ? x1.w : x1.z;
+                    abits01 = ((w0 >> sh) & 0xFFFFu) | ((w1 >> sh) << 16);
+                    abits23 = ((w2 >> sh) & 0xFFFFu) | ((w3 >> sh) << 16);
+                }
                 const uint32_t os = ito % NOP;
                 if (!wait_warp(&bar->op_empty[os], ((ito / NOP) & 1u) ^ 1u, abort_flag, status, lim)) {
                     ok = false;
                     break;
                 }
-                const uint8_t *bits = smem + C::SM_BITS + bs * C::BT_BYTES;
                 uint8_t *op = smem + C::SM_OP + os * C::OP_BYTES;
+                if (ATM) {
+                    // The MMAs that read this stage's A columns have completed
+                    // (op_empty); order the TMEM stores after them.
+                    tc_fence_after();
+                    const uint32_t b16 = ((q < 2 ? abits01 : abits23) >> ((q & 1) * 16)) & 0xFFFFu;
+                    const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + kAColBase + os * kAColStage +
+                                        (uint32_t)group * 8u;
+                    expand_a_tmem(b16, bits + C::BT_CHI, bits + C::BT_CLO, q, group, ta);
+                }
                 expand_b<C::TNB>(bits + C::BT_B, op + C::OP_B, q, gt);
-                if (!ATMA)
+                if (!ATMA && !ATM)
                     expand_a(bits + C::BT_A, bits + C::BT_CHI, bits + C::BT_CLO, op + C::OP_A_HI, op + C::OP_A_LO, q,
                              gt);
+                if (ATM) {
+                    tmem_wait_st();
+                    tc_fence_before();
+                }
                 fence_proxy_async_smem();
                 __syncwarp();
                 if (ATMA && CG == 2 && !wait_warp(&bar->w_full[os], (ito / NOP) & 1u, abort_flag, status, lim)) {
@@ -659,6 +757,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int c = 0; c < kGroupLoads; ++c) {
                         uint32_t r[32], acc[32];
                         tmem_ld32(tb + c * 32, r);
+                        if (ATM) {
+                            // running sum in shared memory (this thread's row only)
+                            float4 *sp = sum4 + ((group * kGroupCols + c * 32) >> 2) * TM + rl;
+#pragma unroll
+                            for (int e4 = 0; e4 < 8; ++e4) {
+                                float4 v = make_float4(__uint_as_float(r[4 * e4]), __uint_as_float(r[4 * e4 + 1]),
+                                                       __uint_as_float(r[4 * e4 + 2]), __uint_as_float(r[4 * e4 + 3]));
+                                if (nchunk > 0) {
+                                    const float4 o = sp[e4 * TM];
+                                    v.x += o.x;
+                                    v.y += o.y;
+                                    v.z += o.z;
+                                    v.w += o.w;
+                                }
+                                sp[e4 * TM] = v;
+                            }
+                            continue;
+                        }
                         if (nchunk > 0) {
                             tmem_ld32(tb + kSumCol + c * 32, acc);
 #pragma unroll
@@ -699,14 +815,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t row = arow0 + quarter * 32 + lane;  // observable a
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(group * kGroupCols);
             bool chunked = nchunk > 0;
+            // ATM: where the running sum of this thread's row keeps the
+            // group's 32 columns c * 32.. (shared memory); else in TMEM
+            auto ssum = [&](int c) -> const float4 * {
+                return ATM ? sum4 + ((group * kGroupCols + c * 32) >> 2) * TM + rl : nullptr;
+            };
             if (!GRAD && MODE != 3 && SPL) {
                 const int64_t uv = u;  // this part's slot
                 // A part of a split tile: store this part's accumulator; the
                 // CTA that finishes the tile's last part sums every part's,
                 // in part order, back into TMEM and runs the epilogue.
                 const int64_t half = CG == 2 ? (int64_t)crank : 0;
-                const int rl = quarter * 32 + lane;  // accumulator row in this CTA
-                split_store(args.skp + ((uv * CG + half) * TM + rl) * TN + group * kGroupCols, tbase, chunked);
+                split_store(args.skp + ((uv * CG + half) * TM + rl) * TN + group * kGroupCols, tbase, chunked,
+                            ATM ? sum4 + ((group * kGroupCols) >> 2) * TM + rl : nullptr);
                 __threadfence();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar->part_done);
@@ -746,7 +867,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r);
+                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
@@ -754,7 +875,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
 #pragma unroll 1
                 for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r);
+                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (c * 32 + e < nvalid) {
@@ -767,7 +888,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (args.out != nullptr) {  // uniform: every lane takes the TMEM loads
 #pragma unroll 1
                     for (int c = 0; c * 32 < nvalid; ++c) {
-                        load_sum32(tbase + c * 32, chunked, r);
+                        load_sum32(tbase + c * 32, chunked, r, ssum(c));
                         if (row < args.l) store_out32(args, row, c0 + c * 32, r);
                     }
                 }
@@ -786,7 +907,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r);
+                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
 #pragma unroll
                     for (int e = 0; e < 32; ++e)
                         if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
@@ -794,7 +915,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
 #pragma unroll 1
                 for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r);
+                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
                     const int64_t i0 = c0 + c * 32;
                     uint32_t ph[16], pl[16];
 #pragma unroll
@@ -820,7 +941,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r);
+                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
                     if (row < args.l && c0 + c * 32 < args.s) store_out32(args, row, c0 + c * 32, r);
                 }
             } else if (!GRAD) {
@@ -831,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r);
+                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
                     const int64_t i0 = c0 + c * 32;
                     uint32_t ph[16], pl[16];
 #pragma unroll
@@ -853,7 +974,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 uint32_t r[32];
 #pragma unroll 1
                 for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r);
+                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
                     const int64_t j0 = tn * TN + group * kGroupCols + c * 32;
                     const uint32_t mask = (rv && j0 < args.m) ? args.pa32[row * args.ldp32 + (j0 >> 5)] : 0u;
                     float v[32];
@@ -888,8 +1009,411 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 1) {
         __syncwarp();  // lane 0 ran the MMA loop alone; dealloc is warp-aligned
         tc_fence_after();
-        if (CG == 2) tmem_dealloc_pair(tmem, kTmemCols);
+        if constexpr (CG == 2) tmem_dealloc_pair(tmem, kTmemCols);
         else tmem_dealloc(tmem, kTmemCols);
+    }
+}
+
+// ------------------------------------------------------------------ gradient, CTA pairs
+// k_grad_pair: the gradient contraction in the transposed orientation,
+//   D[j][a] = sum_i S_Z[i][j] W[a][i],   grad partial g_j += sum_a 2 P_A[a][j] D[j][a],
+// as CTA pairs (cta_group::2): a tile is 256 gates (M, 128 per CTA) x 256
+// observables (N), K = samples in 128-sample operand stages, GNS stages in
+// flight.
+//  - W (B operand: hi and lo BF16 tiles, 128 observables per CTA, two
+//    128-byte K atoms each) arrives by TMA; both CTAs' loads complete on the
+//    even CTA's w_full barrier.
+//  - S_Z^T (A operand, +-1) is expanded from the transposed sample parities
+//    P_Z^T straight into TMEM by eight producer warps (tcgen05.st). The even
+//    CTA's producers also wait for the stage's W (w_full, both CTAs' halves)
+//    before they arrive, and the odd CTA's readiness is forwarded by one
+//    thread, so the MMA thread waits on a single barrier per stage.
+//  - The accumulator (256 TMEM columns) is reduced every 4096 samples by
+//    eight epilogue warps: mask by 2 P_A[a][j] (bits of P_A^T), sum over the
+//    warp's 128 observables in FP32, add into an FP64 per-gate partial. Each
+//    epilogue warp writes one FP64 partial per (tile, gate): row
+//    2 * (observable tile) + (its column half).
+// One MMA-issuing thread is the critical path here: its per-stage work is
+// one barrier wait and 16 MMAs with precomputed descriptors, and the stage is
+// twice as long as the phase kernel's to halve the per-stage overheads.
+// Warps: 0 = W loads, 1 = MMA issuer (even CTA) / forwarder (odd CTA),
+// 2 = P_Z^T bit loads, 3..10 = producers, 11..18 = epilogue.
+// TMEM: accumulator at columns 0..255, A stage os at 256 + 64 os.
+constexpr int GN = kGradObs;     // observables per tile (accumulator columns)
+constexpr int GNB = GN / 2;      // W rows (observables) per CTA
+constexpr int GKS = 128;         // samples per operand stage
+constexpr int GNS = 3;           // operand stages in flight
+constexpr int GSPB = 256 / GKS;  // operand stages per bits stage
+constexpr int GACOLS = GKS / 2;  // TMEM columns per A stage
+constexpr int GPROD = 8;         // producer warps
+constexpr int GEPI = 8;          // epilogue warps
+constexpr int GW0 = 3;           // first producer warp
+constexpr int GE0 = GW0 + GPROD; // first epilogue warp
+constexpr int kGThreads = (GE0 + GEPI) * 32;
+constexpr int kGChunk = 4096 / GKS;  // operand stages per accumulation chunk
+constexpr uint32_t kGAcol = GN;      // first A column
+
+struct GCfg {
+    static constexpr uint32_t ATOM = GNB * 128;           // one 128-byte K atom of a W tile
+    static constexpr uint32_t OP_HI = 0, OP_LO = 2 * ATOM;
+    static constexpr uint32_t OP_BYTES = 4 * ATOM;        // W_hi + W_lo, two atoms each
+    static constexpr uint32_t SM_BITS = GNS * OP_BYTES;
+    static constexpr uint32_t BT_BYTES = TM * 32;         // P_Z^T: 128 gates x 256 samples
+    static constexpr uint32_t SM_BAR = SM_BITS + NBITS * BT_BYTES;
+    static constexpr uint32_t SM_END = SM_BAR + 256;
+    static constexpr uint32_t SMEM = SM_END + 1024;
+    static constexpr uint32_t IDESC = idesc_bf16(2 * TM, GN);
+    static_assert(OP_BYTES % 1024 == 0 && BT_BYTES % 1024 == 0, "stage alignment");
+    static_assert(ATOM == 16384, "umma_stage8_pair_ts_b steps 16384 bytes between K atoms");
+    static_assert(kGAcol + GNS * GACOLS <= kTmemCols, "TMEM columns");
+    static_assert(SMEM <= 232448, "shared memory");
+};
+
+struct GBars {
+    uint64_t bits_full[NBITS], bits_empty[NBITS], a_full[GNS], a_peer[GNS], w_full[GNS], empty[GNS], acc_full,
+        acc_empty, drain;
+    uint32_t tmem_slot;
+    int abort_flag;
+};
+
+struct GradArgs {
+    int64_t l, s, m;
+    int64_t nks;                  // operand stages per tile: ceil(s / GKS)
+    int64_t tiles_g, tiles_o;     // gate blocks (256), observable blocks (GN)
+    int64_t group_o;              // observable blocks per tile group (L2 rasterisation)
+    const uint32_t *pat32;        // P_A^T: m rows of ldlt32 32-bit words (bits over observables)
+    int64_t ldlt32;
+    double *gpart;                // 2 * tiles_o rows of m FP64 partials
+    uint32_t *status;
+    uint64_t limit_ns;
+};
+
+__global__ void __launch_bounds__(kGThreads, 1)
+    k_grad_pair(const __grid_constant__ CUtensorMap tmWhi, const __grid_constant__ CUtensorMap tmWlo,
+                const __grid_constant__ CUtensorMap tmZt, const GradArgs args) {
+    using C = GCfg;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = aligned_smem(smem_raw);
+    GBars *bar = reinterpret_cast<GBars *>(smem + C::SM_BAR);
+    volatile int *abort_flag = &bar->abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t lim = args.limit_ns;
+    uint32_t *status = args.status;
+    const uint32_t crank = cluster_ctarank();
+    const bool leader = crank == 0;
+    const int64_t group0 = blockIdx.x / 2, ngroups = gridDim.x / 2;
+    const int64_t ntiles = args.tiles_g * args.tiles_o;
+    const int nks = (int)args.nks;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NBITS; ++i) {
+            mbar_init(&bar->bits_full[i], 1);
+            mbar_init(&bar->bits_empty[i], GPROD);
+        }
+        for (int i = 0; i < GNS; ++i) {
+            mbar_init(&bar->a_full[i], GPROD + 1);  // even CTA: its producers + the odd CTA's forwarded arrival
+            mbar_init(&bar->a_peer[i], GPROD);     // odd CTA: its producers
+            mbar_init(&bar->w_full[i], 1);         // even CTA: its arrive.expect_tx; both CTAs' bytes
+            mbar_init(&bar->empty[i], 1);          // the pair commit of the stage's MMAs
+        }
+        mbar_init(&bar->acc_full, 1);
+        mbar_init(&bar->acc_empty, 2 * GEPI);  // even CTA: both CTAs' epilogue warps
+        mbar_init(&bar->drain, 1);
+        bar->abort_flag = 0;
+        fence_barrier_init();
+        fence_proxy_async_smem();
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(&bar->tmem_slot, kTmemCols);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();
+    tc_fence_after();
+    const uint32_t tmem = bar->tmem_slot;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------ W loads
+        if (lane == 0) {
+            prefetch_tmap(&tmWhi);
+            prefetch_tmap(&tmWlo);
+            const uint32_t w_full_leader = mapa_shared(smem_u32(&bar->w_full[0]), 0u);
+            uint32_t os = 0, ph = 0, omask = 0, opar = 0;  // stage ring position and its phase parity
+            bool ok = true;
+            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+                int64_t to, tg;
+                tile_coords(t, args.tiles_o, args.tiles_g, args.group_o, to, tg);
+                const int a0 = (int)(to * GN) + (int)crank * GNB;  // this CTA's first W row
+                int a0n = -1;                                      // the next tile's (for L2 prefetch)
+                if (t + ngroups < ntiles) {
+                    int64_t ton, tgn;
+                    tile_coords(t + ngroups, args.tiles_o, args.tiles_g, args.group_o, ton, tgn);
+                    a0n = (int)(ton * GN) + (int)crank * GNB;
+                }
+                for (int ks = 0; ks < nks; ++ks) {
+                    if (!mbar_wait(&bar->empty[os], ph ^ 1u, abort_flag, status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *op = smem + os * C::OP_BYTES;
+                    if (leader) mbar_arrive_expect_tx(&bar->w_full[os], 2 * C::OP_BYTES);
+#pragma unroll
+                    for (int at = 0; at < 2; ++at) {
+                        const int x = ks * GKS + at * 64;
+                        if (leader) {
+                            tma_load_2d(op + C::OP_HI + at * C::ATOM, &tmWhi, &bar->w_full[os], x, a0);
+                            tma_load_2d(op + C::OP_LO + at * C::ATOM, &tmWlo, &bar->w_full[os], x, a0);
+                        } else {
+                            tma_load_2d_pair(op + C::OP_HI + at * C::ATOM, &tmWhi, w_full_leader + os * 8u, x, a0);
+                            tma_load_2d_pair(op + C::OP_LO + at * C::ATOM, &tmWlo, w_full_leader + os * 8u, x, a0);
+                        }
+                    }
+                    // warm L2 with the tiles 512 samples beyond this load (the next tile's near the end)
+                    int xp = ks * GKS + 512, ap = a0;
+                    if (xp >= nks * GKS) {
+                        xp -= nks * GKS;
+                        ap = a0n;
+                    }
+                    if (ap >= 0) {
+                        tma_prefetch_2d(&tmWhi, xp, ap);
+                        tma_prefetch_2d(&tmWhi, xp + 64, ap);
+                        tma_prefetch_2d(&tmWlo, xp, ap);
+                        tma_prefetch_2d(&tmWlo, xp + 64, ap);
+                    }
+                    omask |= 1u << os;
+                    opar = (opar & ~(1u << os)) | (ph << os);
+                    if (++os == GNS) {
+                        os = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            // Drain: every W load has landed before exit (the odd CTA's land on
+            // the even CTA's barriers, part of the bytes it expects).
+            if (leader) {
+#pragma unroll
+                for (int i = 0; i < GNS; ++i)
+                    if ((omask >> i) & 1u) mbar_drain(&bar->w_full[i], (opar >> i) & 1u, status, lim);
+            }
+        }
+    } else if (warp == 2) {
+        // ------------------------------------------------------ P_Z^T bit loads
+        if (lane == 0) {
+            prefetch_tmap(&tmZt);
+            uint32_t itb = 0, bmask = 0, bpar = 0;
+            bool ok = true;
+            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+                int64_t to, tg;
+                tile_coords(t, args.tiles_o, args.tiles_g, args.group_o, to, tg);
+                const int j0 = (int)(tg * 2 * TM) + (int)crank * TM;  // this CTA's first gate
+                for (int kb = 0; kb < (nks + GSPB - 1) / GSPB; ++kb, ++itb) {
+                    const uint32_t bs = itb % NBITS;
+                    if (!mbar_wait(&bar->bits_empty[bs], ((itb / NBITS) & 1u) ^ 1u, abort_flag, status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    uint8_t *bits = smem + C::SM_BITS + bs * C::BT_BYTES;
+                    mbar_arrive_expect_tx(&bar->bits_full[bs], C::BT_BYTES);
+                    tma_load_2d(bits, &tmZt, &bar->bits_full[bs], kb * 4, j0);  // 256 samples = 4 words
+                    bmask |= 1u << bs;
+                    bpar = (bpar & ~(1u << bs)) | (((itb / NBITS) & 1u) << bs);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < NBITS; ++i)
+                if ((bmask >> i) & 1u) mbar_drain(&bar->bits_full[i], (bpar >> i) & 1u, status, lim);
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            // ------------------------------------------------------------ MMA issuer
+            uint32_t os = 0, ph = 0, nchk = 0;
+            bool ok = true;
+            const uint64_t d_w0 = sdesc_k128(smem_u32(smem) + C::OP_HI);  // W_hi of stage 0, K step 0
+            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+                int kc = 0;
+                for (int ks = 0; ks < nks; ++ks) {
+                    if (kc == 0 &&
+                        !mbar_wait_cluster(&bar->acc_empty, (nchk & 1u) ^ 1u, abort_flag, status, lim)) {
+                        // the epilogue warps of both CTAs have read the previous chunk
+                        ok = false;
+                        break;
+                    }
+                    if (!mbar_wait_cluster(&bar->a_full[os], ph, abort_flag, status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t dhi = d_w0 + (uint64_t)(os * (C::OP_BYTES >> 4));
+                    umma_stage8_pair_ts_b(tmem, tmem + kGAcol + os * GACOLS, dhi, dhi + (C::OP_LO >> 4), C::IDESC,
+                                          kc == 0 ? 0u : 1u);
+                    umma_commit_pair(&bar->empty[os]);
+                    if (++kc == kGChunk || ks == nks - 1) {
+                        umma_commit_pair(&bar->acc_full);
+                        ++nchk;
+                        kc = 0;
+                    }
+                    if (++os == GNS) {
+                        os = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+            umma_commit_pair(&bar->drain);
+            mbar_drain(&bar->drain, 0u, status, lim);
+        } else if (lane == 0) {
+            // Odd CTA: forward "my A half of stage os is in TMEM" to the even CTA.
+            const uint32_t a_full_remote = mapa_shared(smem_u32(&bar->a_full[0]), 0u);
+            uint32_t os = 0, ph = 0;
+            bool ok = true;
+            for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+                for (int ks = 0; ks < nks; ++ks) {
+                    if (!mbar_wait(&bar->a_peer[os], ph, abort_flag, status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_remote(a_full_remote + os * 8u);
+                    if (++os == GNS) {
+                        os = 0;
+                        ph ^= 1u;
+                    }
+                }
+            }
+        }
+    } else if (warp < GE0) {
+        // --------------------------------------- producers: S_Z^T (+-1) into TMEM
+        const int quarter = warp & 3;        // TMEM lane quarter
+        const int h = (warp - GW0) >> 2;     // 64-sample half of each operand stage
+        const int rl = quarter * 32 + lane;  // gate row of this CTA
+        uint32_t itb = 0, os = 0, ph = 0, zb[4] = {0u, 0u, 0u, 0u};
+        bool ok = true;
+        for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+            for (int ks = 0; ks < nks; ++ks) {
+                const int q = ks % GSPB;
+                const uint32_t bs = itb % NBITS;
+                if (q == 0) {
+                    if (!wait_warp(&bar->bits_full[bs], (itb / NBITS) & 1u, abort_flag, status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    // this row's bits for its halves of the bits stage's two operand stages
+                    const uint8_t *bits = smem + C::SM_BITS + bs * C::BT_BYTES;
+                    const uint4 x0 = *reinterpret_cast<const uint4 *>(bits + rl * 32);
+                    const uint4 x1 = *reinterpret_cast<const uint4 *>(bits + rl * 32 + 16);
+                    zb[0] = h ? x0.z : x0.x;  // operand stage 0: words 2 h, 2 h + 1
+                    zb[1] = h ? x0.w : x0.y;
+                    zb[2] = h ? x1.z : x1.x;  // operand stage 1: words 4 + 2 h, 5 + 2 h
+                    zb[3] = h ? x1.w : x1.y;
+                }
+                if (!wait_warp(&bar->empty[os], ph ^ 1u, abort_flag, status, lim)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + kGAcol + os * GACOLS + (uint32_t)h * 32u;
+#pragma unroll
+                for (int wd = 0; wd < 2; ++wd) {
+                    const uint32_t b = q == 0 ? zb[wd] : zb[2 + wd];
+                    uint32_t v[16];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint4 e = expand_pm1((b >> (8 * i)) & 0xFFu);
+                        v[4 * i] = e.x;
+                        v[4 * i + 1] = e.y;
+                        v[4 * i + 2] = e.z;
+                        v[4 * i + 3] = e.w;
+                    }
+                    tmem_st16(ta + (uint32_t)wd * 16u, v);
+                }
+                tmem_wait_st();
+                tc_fence_before();
+                // The even CTA's producers vouch for the stage's W as well
+                // (both CTAs' halves complete on its w_full).
+                if (leader && !wait_warp_cluster(&bar->w_full[os], ph, abort_flag, status, lim)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    if (leader) mbar_arrive(&bar->a_full[os]);
+                    else mbar_arrive(&bar->a_peer[os]);
+                }
+                if (++os == GNS) {
+                    os = 0;
+                    ph ^= 1u;
+                }
+                if (q == GSPB - 1 || ks == nks - 1) {
+                    if (lane == 0) mbar_arrive(&bar->bits_empty[bs]);
+                    ++itb;
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------- epilogue: masked reduction
+        const int quarter = warp & 3;
+        const int e = (warp - GE0) >> 2;  // column half: observables [GNB e, GNB e + GNB) of the tile
+        const int rl = quarter * 32 + lane;
+        const uint32_t acc_empty_remote = mapa_shared(smem_u32(&bar->acc_empty), 0u);
+        constexpr int NW = GNB / 32;
+        uint32_t nchk = 0;
+        bool ok = true;
+        const int nch = (nks + kGChunk - 1) / kGChunk;
+        for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
+            int64_t to, tg;
+            tile_coords(t, args.tiles_o, args.tiles_g, args.group_o, to, tg);
+            const int64_t j = tg * 2 * TM + (int64_t)crank * TM + rl;  // gate of this thread
+            const int64_t a0 = to * GN + (int64_t)e * GNB;             // first observable of this warp
+            // 2 P_A[a][j] for the warp's GNB observables: GNB / 32 words of P_A^T
+            // row j (a0 is a multiple of 32); bits of observables >= l are dropped.
+            uint32_t mk[NW];
+#pragma unroll
+            for (int w = 0; w < NW; ++w) mk[w] = 0u;
+            if (j < args.m) {
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    const int64_t wi = a0 / 32 + w;
+                    if (wi < args.ldlt32) mk[w] = __ldg(args.pat32 + j * args.ldlt32 + wi);
+                    const int64_t rem = args.l - (a0 + 32 * w);  // valid observables in this word
+                    if (rem < 32) mk[w] &= rem <= 0 ? 0u : ((1u << rem) - 1u);
+                }
+            }
+            double gsum = 0.0;
+            for (int c = 0; c < nch; ++c, ++nchk) {
+                if (!wait_warp(&bar->acc_full, nchk & 1u, abort_flag, status, lim)) {
+                    ok = false;
+                    break;
+                }
+                __syncwarp();
+                tc_fence_after();
+                float part = 0.f;
+                const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)e * GNB;
+#pragma unroll
+                for (int w = 0; w < NW; ++w) {
+                    uint32_t r[32];
+                    tmem_ld32(tb + w * 32, r);
+#pragma unroll
+                    for (int x = 0; x < 32; ++x)
+                        if ((mk[w] >> x) & 1u) part += __uint_as_float(r[x]);
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    if (leader) mbar_arrive(&bar->acc_empty);
+                    else mbar_arrive_remote(acc_empty_remote);
+                }
+                gsum += 2.0 * (double)part;
+            }
+            if (!ok) break;
+            if (j < args.m) args.gpart[(2 * to + e) * args.m + j] = gsum;
+        }
+    }
+
+    __syncthreads();
+    cluster_sync_all();  // no pair MMA or pair-barrier copy still touches the peer
+    if (warp == 1) {
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc_pair(tmem, kTmemCols);
     }
 }
 
@@ -940,14 +1464,14 @@ bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool GRAD, int MODE, int CG, bool AT = GRAD, bool SPL = false>
+template <bool GRAD, int MODE, int CG, bool AT = GRAD, bool SPL = false, bool TA = false>
 cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
                      cudaStream_t st) {
-    using C = Cfg<CG, GRAD || AT>;
+    using C = Cfg<CG, GRAD || AT, TA && !GRAD && !AT && CG == 2>;
     constexpr int CL = CG;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, AT, SPL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_tc<GRAD, MODE, CG, AT, SPL, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)C::SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -961,7 +1485,7 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
                                : IQP_KERNEL_PHASE_TC,
                    st);
     if (CL == 1) {
-        k_tc<GRAD, MODE, 1, AT, SPL><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
+        k_tc<GRAD, MODE, 1, AT, SPL, TA><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
         return cudaGetLastError();
     }
     cudaLaunchConfig_t cfg = {};
@@ -976,7 +1500,7 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, AT, SPL>, a, a2, b, args);
+    return cudaLaunchKernelEx(&cfg, k_tc<GRAD, MODE, CG, AT, SPL, TA>, a, a2, b, args);
 }
 
 // Tensor-core group size: CTA pairs unless IQP_CTA_PAIRS=0.
@@ -998,6 +1522,28 @@ bool split_tail() {
     static int v = -1;
     if (v < 0) {
         const char *e = std::getenv("IQP_SPLIT_TAIL");
+        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+// Phase kernels of CTA pairs with the A operand in TMEM (default) or in
+// shared memory (IQP_PHASE_TMEM=0).
+bool phase_tmem() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("IQP_PHASE_TMEM");
+        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
+// Gradient contraction as CTA pairs in the transposed orientation
+// (k_grad_pair, default) or single CTAs (IQP_GRAD_PAIR=0, or IQP_CTA_PAIRS=0).
+bool grad_pair() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("IQP_GRAD_PAIR");
         v = (e != nullptr && e[0] == '0') ? 0 : 1;
     }
     return v == 1;
@@ -1031,6 +1577,11 @@ namespace {
 template <bool SPL>
 cudaError_t launch_phase_k(int mode, int cg, const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a,
                            cudaStream_t st) {
+    if (cg == 2 && phase_tmem()) {
+        if (mode == 0) return launch_k<false, 0, 2, false, SPL, true>(ma, ma, mb, a, st);
+        if (mode == 1) return launch_k<false, 1, 2, false, SPL, true>(ma, ma, mb, a, st);
+        return launch_k<false, 2, 2, false, SPL, true>(ma, ma, mb, a, st);
+    }
     if (cg == 2) {
         if (mode == 0) return launch_k<false, 0, 2, false, SPL>(ma, ma, mb, a, st);
         if (mode == 1) return launch_k<false, 1, 2, false, SPL>(ma, ma, mb, a, st);
@@ -1115,7 +1666,70 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     return launch_phase_k<true>(mode, cg, ma, mb, a, st);
 }
 
+
+namespace {
+cudaError_t launch_grad_pair(const Plan &p, void *ws, cudaStream_t st, iqp_status *why) {
+    using C = GCfg;
+    CUtensorMap mhi, mlo, mz;
+    const __nv_bfloat16 *whi = at<__nv_bfloat16>(ws, p.off_w);
+    const __nv_bfloat16 *wlo = whi + p.l * p.ldw;
+    if (!make_map(&mhi, whi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, GNB,
+                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mlo, wlo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, p.s, p.l, p.ldw * 2, KS, GNB,
+                  CU_TENSOR_MAP_SWIZZLE_128B) ||
+        !make_map(&mz, at<uint64_t>(ws, p.off_pzt), CU_TENSOR_MAP_DATA_TYPE_UINT64, p.ldzt, p.m, p.ldzt * 8, 4, TM,
+                  CU_TENSOR_MAP_SWIZZLE_NONE)) {
+        *why = IQP_ERR_UNSUPPORTED;
+        return cudaErrorNotSupported;
+    }
+    GradArgs a;
+    a.l = p.l;
+    a.s = p.s;
+    a.m = p.m;
+    a.nks = cdiv(p.s, GKS);
+    a.tiles_g = cdiv(p.m, 2 * TM);
+    a.tiles_o = cdiv(p.l, GN);
+    a.group_o = tile_group();
+    a.pat32 = at<uint32_t>(ws, p.off_pat);
+    a.ldlt32 = 2 * p.ldlt;
+    a.gpart = at<double>(ws, p.off_gpart);
+    a.status = at<uint32_t>(ws, p.off_status);
+    a.limit_ns = default_spin_limit_ns();
+    static bool attr_set = false;
+    if (!attr_set) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_grad_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int sms = num_sms();
+    if (sms < 2) sms = 2;
+    const int64_t ntiles = a.tiles_g * a.tiles_o;
+    const int64_t groups = ntiles < sms / 2 ? ntiles : sms / 2;
+    LaunchScope ls(IQP_KERNEL_GRAD_TC, st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(groups * 2), 1, 1);
+    cfg.blockDim = dim3(kGThreads, 1, 1);
+    cfg.dynamicSmemBytes = C::SMEM;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_grad_pair, mhi, mlo, mz, a);
+}
+}  // namespace
+
+// Rows of FP64 gradient partials the gradient contraction writes: two per
+// 256-observable tile for the CTA-pair kernel, one per 128-observable tile
+// for the single-CTA kernel (IQP_GRAD_PAIR=0 or IQP_CTA_PAIRS=0).
+int64_t grad_tc_rows(const Plan &p) { return cta_group() == 2 && grad_pair() ? 2 * cdiv(p.l, GN) : cdiv(p.l, TM); }
+
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why) {
+    if (cta_group() == 2 && grad_pair()) return launch_grad_pair(p, ws, st, why);
     const int cg = 1;
     CUtensorMap mhi, mlo, mb;
     const __nv_bfloat16 *whi = at<__nv_bfloat16>(ws, p.off_w);

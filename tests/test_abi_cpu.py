@@ -44,9 +44,10 @@ def test_workspace_bytes(lib):
     fwd = lib.iqp_workspace_bytes(_lib.OP_EXPVAL, n, m, l, s, 0, _lib.SPLIT_BF16)
     grad = lib.iqp_workspace_bytes(_lib.OP_EXPVAL_GRAD, n, m, l, s, 0, _lib.SPLIT_BF16)
     assert fwd > 0 and grad > fwd
-    # Bit-packed parities: (l + s) rows of ceil(m/64) words dominate the forward.
+    # Bit-packed parities: (l + s) rows of ceil(m/64) words dominate the forward
+    # (beside them: the (S, M2) partials and a 16-byte support entry per gate).
     assert fwd >= (l + s) * ((m + 63) // 64) * 8
-    assert fwd < 2 * (l + s) * ((m + 255) // 256) * 32 + 64 * l * ((s + 127) // 128) + (1 << 22)
+    assert fwd < 2 * (l + s) * ((m + 255) // 256) * 32 + 64 * l * ((s + 127) // 128) + 16 * m + (1 << 22)
     # W (hi + lo BF16, l x s) dominates the gradient's extra scratch.
     assert grad - fwd >= 4 * l * s
     assert lib.iqp_workspace_bytes(_lib.OP_EXPVAL, 0, m, l, s, 0, _lib.FP32) == 0

@@ -518,13 +518,16 @@ def test_adam_on_mmd_loss_converges(api):
     assert np.mean(losses[-5:]) < 0.3 * np.mean(losses[:5])
 
 
-@pytest.mark.parametrize("pairs,split", [("0", "1"), ("2", "0"), ("0", "0")])
-def test_other_tensor_kernel_forms_match_oracle(pairs, split):
-    """The tensor-core kernel forms the defaults do not use: one-CTA phase
-    kernels (IQP_CTA_PAIRS=0), and whole phase tiles without the split last
-    round (IQP_SPLIT_TAIL=0; this small problem is all last round, so with
-    the default every tile is split along the gates), on the ragged problem,
-    in a fresh process."""
+@pytest.mark.parametrize("pairs,split,tmem,gpair", [("0", "1", "1", "1"), ("2", "0", "1", "1"), ("0", "0", "1", "1"),
+                                                   ("2", "1", "0", "1"), ("2", "1", "1", "0"), ("2", "0", "0", "0")])
+def test_other_tensor_kernel_forms_match_oracle(pairs, split, tmem, gpair):
+    """The tensor-core kernel forms the defaults do not use: one-CTA kernels
+    (IQP_CTA_PAIRS=0), whole phase tiles without the split last round
+    (IQP_SPLIT_TAIL=0; this small problem is all last round, so with the
+    default every tile is split along the gates), the pair phase kernel with
+    its A operand in shared memory instead of TMEM (IQP_PHASE_TMEM=0), and
+    the single-CTA gradient contraction in place of the CTA-pair one
+    (IQP_GRAD_PAIR=0), on the ragged problem, in a fresh process."""
     import json
     import os
     import subprocess
@@ -546,7 +549,8 @@ print(json.dumps({"ev": float(np.max(np.abs(ev.cpu().numpy() - wev))), "se": flo
                   "g": float(np.linalg.norm(g.cpu().numpy() - wg) / np.linalg.norm(wg)), "status": api.read_status()}))
 '''
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, IQP_CTA_PAIRS=pairs, IQP_SPLIT_TAIL=split, PYTHONPATH=root)
+    env = dict(os.environ, IQP_CTA_PAIRS=pairs, IQP_SPLIT_TAIL=split, IQP_PHASE_TMEM=tmem, IQP_GRAD_PAIR=gpair,
+               PYTHONPATH=root)
     out = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     r = json.loads(out.stdout.strip().splitlines()[-1])

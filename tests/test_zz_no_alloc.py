@@ -59,7 +59,7 @@ def _run(env, prob, prec, noalloc):
         status = lib.iqp_noalloc_read_status(st)
     else:
         nbytes = lib.iqp_workspace_bytes(_lib.OP_EXPVAL, n, m, l, s, 0, prec)
-        ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        ws = torch.zeros(nbytes, dtype=torch.uint8, device="cuda")  # status word starts at zero
         rc = lib.iqp_expval(*args, P(ws), nbytes, st)
         assert rc == _lib.OK, _lib.status_string(rc)
         status = lib.iqp_read_status(P(ws), nbytes, st)
