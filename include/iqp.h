@@ -358,6 +358,19 @@ iqp_status iqp_read_status(void *ws, size_t ws_bytes, void *stream);
  * IQP_ERR_TIMEOUT in ws and returns. Read it with iqp_read_status(). */
 iqp_status iqp_selftest_timeout(void *ws, size_t ws_bytes, double limit_seconds, void *stream);
 
+/* Device-side self-checks. A library built with -DIQP_CHECKS compares every
+ * global index its kernels derive from the caller's shapes with the extent of
+ * the buffer before the access; an index outside is skipped and recorded.
+ * iqp_check_status() synchronises the device and returns 0 if no index left
+ * its buffer since the last call, else 200 + the site of the first that did
+ * (the low-order kernels record 100 + site in the workspace status word
+ * instead, read by iqp_read_status); it clears what it reports. In the
+ * default build the checks are compiled out: iqp_checks_enabled() returns 0
+ * and iqp_check_status() returns 0. Not a counterpart of anything in the
+ * paper: it stands in for a memory checker. */
+uint32_t iqp_check_status(void);
+int iqp_checks_enabled(void);
+
 /* Kernels of this library, for iqp_profile_query(). */
 typedef enum {
     IQP_KERNEL_PARITY = 0,         /* GF(2) products (P_A, P_Z, P_Z^T)          */

@@ -10,6 +10,11 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libiqp_gb300.so")
+# The self-checked build (build.build(checks=True)) sits beside it; setting
+# IQP_CHECKED_LIB=1 loads that one instead.
+CHECKED_LIB_PATH = os.path.join(HERE, "libiqp_gb300_checked.so")
+if os.environ.get("IQP_CHECKED_LIB") == "1":
+    LIB_PATH = CHECKED_LIB_PATH
 
 OK, ERR_ARG, ERR_ALIGN, ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(7)
 FP32, SPLIT_BF16, SPARSE_FP32, LOWORDER_FP32 = 0, 1, 2, 3
@@ -48,6 +53,8 @@ SIGNATURES = {
     "iqp_status_string": (ctypes.c_char_p, [_int]),
     "iqp_launch_count": (ctypes.c_uint64, []),
     "iqp_tensor_path_available": (_int, []),
+    "iqp_check_status": (ctypes.c_uint32, []),
+    "iqp_checks_enabled": (_int, []),
     "iqp_profile_enable": (None, [_int]),
     "iqp_profile_reset": (None, []),
     "iqp_profile_query": (_int, [_int, _p, _p]),

@@ -20,6 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build", "iqp")
 LIB = os.path.join(HERE, "libiqp_gb300.so")
+CHECKED_LIB = os.path.join(HERE, "libiqp_gb300_checked.so")
 SOURCES = ["parity.cu", "simt.cu", "tc.cu", "bitflip.cu", "sparse.cu", "variants.cu", "loworder.cu", "api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O2", "-I" + INCLUDE, "-I" + CSRC]
@@ -39,15 +40,21 @@ def _stale(obj: str, src: str) -> bool:
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, extra: list[str] | None = None, checks: bool = False) -> str:
+    """Compile (what changed) and link the library. checks=True builds the
+    self-checked variant (-DIQP_CHECKS: every kernel index derived from the
+    caller's shapes is compared with its buffer's extent) into
+    libiqp_gb300_checked.so beside the default library, from its own objects."""
+    build_dir = BUILD + ("_checked" if checks else "")
+    lib = CHECKED_LIB if checks else LIB
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DIQP_CHECKS"] if checks else [])
 
     def compile_one(name: str) -> str:
         src = os.path.join(CSRC, name)
-        obj = os.path.join(BUILD, name + ".o")
-        if force or extra or _stale(obj, src):
+        obj = os.path.join(build_dir, name + ".o")
+        if force or (extra and not checks) or _stale(obj, src):
             cmd = [cc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
             r = subprocess.run(cmd, capture_output=True, text=True)
             if r.returncode != 0:
@@ -58,14 +65,15 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
 
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    if force or extra or not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs):
-        tmp = LIB + ".tmp"
+    if force or (extra and not checks) or not os.path.exists(lib) or any(
+            os.path.getmtime(o) > os.path.getmtime(lib) for o in objs):
+        tmp = lib + ".tmp"
         cmd = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-cudart", "static"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":  # pragma: no cover

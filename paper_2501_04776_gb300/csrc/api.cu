@@ -37,11 +37,18 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
 cudaError_t launch_w_from_phi(const Plan &p, void *ws, const double *alpha, const double *beta, cudaStream_t st);
 cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status *why);
 int64_t grad_tc_rows(const Plan &p);
+// per-translation-unit self-check words (builds with -DIQP_CHECKS; 0 otherwise)
+uint32_t check_word_parity();
+uint32_t check_word_simt();
+uint32_t check_word_tc();
+uint32_t check_word_sparse();
+uint32_t check_word_bitflip();
+uint32_t check_word_variants();
 cudaError_t launch_timeout_selftest(uint32_t *status, uint64_t limit_ns, cudaStream_t st);
 int64_t sparse_part_samples();
 cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
-                                int64_t l, int64_t s, double2 *part, int64_t nparts, const SparseIndep *indep,
-                                float *phi, int64_t ldphi, cudaStream_t st);
+                                int64_t l, int64_t s, int64_t m, double2 *part, int64_t nparts,
+                                const SparseIndep *indep, float *phi, int64_t ldphi, cudaStream_t st);
 cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
                                int64_t l, int64_t s, int64_t m, int64_t nparts, const double *alpha,
                                const double *beta, double *scale, unsigned long long *gfx, double *grad,
@@ -358,7 +365,7 @@ iqp_status forward_stats(const Plan &p, void *ws, double *expval, double *std_er
         const SparseIndep ind{at<int4>(ws, p.off_sup), p.G, p.ldg, p.n};
         IQP_TRY(launch_sparse_stats(at<uint64_t>(ws, p.off_pa), p.ldp,
                                     at<uint64_t>(ws, p.indep ? p.off_zt : p.off_pzt), p.ldzt, at<float>(ws, p.off_c),
-                                    p.l, p.s, part, p.nparts, p.indep ? &ind : nullptr,
+                                    p.l, p.s, p.m, part, p.nparts, p.indep ? &ind : nullptr,
                                     p.phi_out ? p.phi : nullptr, p.ldphi, st));
     } else {
         IQP_TRY(launch_phase_simt(0, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pz), p.ldp,
@@ -859,6 +866,24 @@ iqp_status iqp_profile_query(iqp_kernel kernel, double *total_ms, uint64_t *laun
     if (total_ms) *total_ms = g_prof_ms[kernel];
     if (launches) *launches = g_prof_n[kernel];
     return IQP_OK;
+}
+
+uint32_t iqp_check_status(void) {
+    // the first recorded failure of any translation unit (each reads and clears its own word)
+    uint32_t first = 0;
+    const uint32_t words[] = {check_word_parity(), check_word_simt(), check_word_tc(), check_word_sparse(),
+                              check_word_bitflip(), check_word_variants()};
+    for (uint32_t w : words)
+        if (first == 0 && w != 0) first = w;
+    return first;
+}
+
+int iqp_checks_enabled(void) {
+#ifdef IQP_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int iqp_tensor_path_available(void) {

@@ -12,6 +12,8 @@
 
 namespace iqp {
 
+uint32_t check_word_bitflip() { return take_check_word(); }
+
 namespace {
 
 // c_j = cos(2 theta_j), t_j = -2 tan(2 theta_j), zero beyond m.
@@ -44,7 +46,7 @@ __global__ void __launch_bounds__(256) k_bitflip_rows(const uint64_t *__restrict
         while (bits) {
             const int b = __ffsll((long long)bits) - 1;
             bits &= bits - 1ull;
-            prod *= c[w * 64 + b];
+            if (IQP_IN(w * 64 + b, ldp * 64, 90)) prod *= c[w * 64 + b];
         }
     }
 #pragma unroll
@@ -61,8 +63,8 @@ __global__ void k_bitflip_weights(const double *__restrict__ w, const double *__
 
 // grad[j] = t_j * sum of v[a] over the set bits a of P_A^T row j. One warp per gate.
 __global__ void __launch_bounds__(256) k_bitflip_grad(const uint64_t *__restrict__ PAT, int64_t ldlt, int64_t m,
-                                                       const double *__restrict__ v, const double *__restrict__ t,
-                                                       double *__restrict__ grad) {
+                                                       [[maybe_unused]] int64_t l, const double *__restrict__ v,
+                                                       const double *__restrict__ t, double *__restrict__ grad) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (j >= m) return;
@@ -73,7 +75,7 @@ __global__ void __launch_bounds__(256) k_bitflip_grad(const uint64_t *__restrict
         while (bits) {
             const int b = __ffsll((long long)bits) - 1;
             bits &= bits - 1ull;
-            acc += v[w * 64 + b];
+            if (IQP_IN(w * 64 + b, l, 91)) acc += v[w * 64 + b];  // bits past the last observable are zero
         }
     }
 #pragma unroll
@@ -107,7 +109,7 @@ cudaError_t launch_bitflip_grad(const uint64_t *PAT, int64_t ldlt, int64_t m, in
         if (e != cudaSuccess) return e;
     }
     LaunchScope ls(IQP_KERNEL_BITFLIP, st);
-    k_bitflip_grad<<<(unsigned)cdiv(m, 8), 256, 0, st>>>(PAT, ldlt, m, v, t, grad);
+    k_bitflip_grad<<<(unsigned)cdiv(m, 8), 256, 0, st>>>(PAT, ldlt, m, l, v, t, grad);
     return cudaGetLastError();
 }
 

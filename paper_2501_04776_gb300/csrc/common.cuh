@@ -97,6 +97,32 @@ __device__ inline void record_status(uint32_t *status, uint32_t code) {
     if (status) atomicCAS(status, 0u, code);
 }
 
+// Optional self-checks (build with -DIQP_CHECKS): every global index a
+// kernel derives from the caller's shapes is compared with the extent of its
+// buffer before the access; an index outside records 200 + site in this
+// translation unit's check word (the first failure wins) and the access is
+// skipped. iqp_check_status() reads and clears the words of all units. In
+// the default build the checks compile to nothing. Nothing traps.
+#ifdef IQP_CHECKS
+static __device__ uint32_t g_check_word;
+__device__ __forceinline__ bool check_in(int64_t idx, int64_t extent, uint32_t site) {
+    if (idx >= 0 && idx < extent) return true;
+    atomicCAS(&g_check_word, 0u, 200u + site);
+    return false;
+}
+#define IQP_IN(idx, extent, site) ::iqp::check_in((int64_t)(idx), (int64_t)(extent), (uint32_t)(site))
+// This unit's check word, cleared (host; synchronises the device).
+static inline uint32_t take_check_word() {
+    uint32_t v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_check_word, sizeof(v)) != cudaSuccess) return 0xFFFFFFFFu;
+    if (cudaMemcpyToSymbol(g_check_word, &z, sizeof(z)) != cudaSuccess) return 0xFFFFFFFFu;
+    return v;
+}
+#else
+#define IQP_IN(idx, extent, site) true
+static inline uint32_t take_check_word() { return 0u; }
+#endif
+
 // Host-side launch accounting (iqp_launch_count) and optional per-kernel
 // event timing (iqp_profile_*). Construct one right before each launch.
 struct LaunchScope {

@@ -37,8 +37,12 @@ constexpr int kBlk = 256;    // samples per CTA in the per-observable kernels
 constexpr int kQ4 = 256;     // supports up to this size take four sample blocks per pass in k_lo_phase
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-// Optional self-checks (-DIQP_LO_CHECKS): an index out of its buffer records
-// status 100 + site and the access is skipped.
+// Optional self-checks (-DIQP_LO_CHECKS, or the library-wide -DIQP_CHECKS):
+// an index out of its buffer records status 100 + site in the workspace status
+// word and the access is skipped.
+#if defined(IQP_CHECKS) && !defined(IQP_LO_CHECKS)
+#define IQP_LO_CHECKS
+#endif
 #ifdef IQP_LO_CHECKS
 #define LO_OK(cond, site) ((cond) ? true : (record_status(status_dbg, 100u + (site)), false))
 #else

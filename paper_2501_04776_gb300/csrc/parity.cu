@@ -7,6 +7,8 @@
 
 namespace iqp {
 
+uint32_t check_word_parity() { return take_check_word(); }
+
 namespace {
 
 constexpr int kRows = 32;    // rows of R per block
@@ -36,7 +38,7 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
         {
             const int row = tid >> 3, q = tid & 7;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (r0 + row < rows && w0 + 4 * q < nw4)
+            if (r0 + row < rows && w0 + 4 * q < nw4 && IQP_IN((r0 + row) * ldr32 + w0 + 4 * q + 3, rows * ldr32, 0))
                 v = *reinterpret_cast<const uint4 *>(R + (r0 + row) * ldr32 + w0 + 4 * q);
             *reinterpret_cast<uint4 *>(&Rs[row][4 * q]) = v;
         }
@@ -45,7 +47,7 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
         for (int k = 0; k < 8; ++k) {
             const int idx = tid + 256 * k, row = idx >> 3, q = idx & 7;
             uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (g0 + row < m && w0 + 4 * q < nw4)
+            if (g0 + row < m && w0 + 4 * q < nw4 && IQP_IN((g0 + row) * ldg32 + w0 + 4 * q + 3, m * ldg32, 1))
                 v = *reinterpret_cast<const uint4 *>(G + (g0 + row) * ldg32 + w0 + 4 * q);
             *reinterpret_cast<uint4 *>(&Gs[row][4 * q]) = v;
         }
@@ -73,8 +75,9 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
             col |= bit << r;
         }
         const int64_t row = r0 + lane;
-        if (row < rows && (g0 >> 5) + warp < ldp32) P[row * ldp32 + (g0 >> 5) + warp] = mine;
-        if (PT != nullptr && gen < m) PT[gen * ldpt32 + (r0 >> 5)] = col;
+        if (row < rows && (g0 >> 5) + warp < ldp32 && IQP_IN(row * ldp32 + (g0 >> 5) + warp, rows * ldp32, 2))
+            P[row * ldp32 + (g0 >> 5) + warp] = mine;
+        if (PT != nullptr && gen < m && IQP_IN((r0 >> 5), ldpt32, 3)) PT[gen * ldpt32 + (r0 >> 5)] = col;
     } else {
         // Sum over the valid generators (data rows) of this warp: +1 even, -1 odd.
         int64_t valid = m - (g0 + warp * 32);
@@ -82,7 +85,7 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
 #pragma unroll
         for (int r = 0; r < kRows; ++r) {
             const uint32_t bal = __ballot_sync(0xFFFFFFFFu, __popc(acc[r]) & 1u);
-            if (lane == r && r0 + r < rows && valid > 0) {
+            if (lane == r && r0 + r < rows && valid > 0 && IQP_IN(r0 + r, rows, 4)) {
                 const long long v = (long long)valid - 2LL * (long long)__popc(bal);
                 atomicAdd(reinterpret_cast<unsigned long long *>(T + r0 + r), (unsigned long long)v);
             }
@@ -129,7 +132,9 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
         for (int k = 0; k < kTW / 4; ++k) {
             const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
             const int64_t r = r0 + row;
-            if (vin && r < in_rows && w0 + q + 3 < ld_in32) {
+            if (r < in_rows && !IQP_IN(r * ld_in32 + (w0 + q < ld_in32 ? w0 + q : 0), in_rows * ld_in32, 5)) {
+                v[k] = make_uint4(0u, 0u, 0u, 0u);
+            } else if (vin && r < in_rows && w0 + q + 3 < ld_in32) {
                 v[k] = *reinterpret_cast<const uint4 *>(in + r * ld_in32 + w0 + q);
             } else {
                 v[k].x = (r < in_rows && w0 + q < ld_in32) ? in[r * ld_in32 + w0 + q] : 0u;
@@ -184,6 +189,7 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
         const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
         const int64_t orow = c0 + row;
         if (orow >= in_cols) continue;
+        if (!IQP_IN(orow * ld_out32 + (ow0 + q < ld_out32 ? ow0 + q : 0), in_cols * ld_out32, 6)) continue;
         if (vout && ow0 + q + 3 < ld_out32) {
             *reinterpret_cast<uint4 *>(out + orow * ld_out32 + ow0 + q) =
                 make_uint4(tin[row][q], tin[row][q + 1], tin[row][q + 2], tin[row][q + 3]);
@@ -218,9 +224,10 @@ __global__ void __launch_bounds__(kTT) k_gather_transpose(const int4 *__restrict
         const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
         const int64_t j = r0 + row;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (j < m && w0 + q < ldrt32) {
+        if (j < m && w0 + q < ldrt32 && IQP_IN(j * ldpt32 + w0 + q + 3, m * ldpt32, 7)) {
             const int4 sp = sup[j];
-            if (sp.w <= 3) {
+            if (sp.w <= 3 && IQP_IN(sp.w > 0 ? sp.x : 0, n, 8) && IQP_IN(sp.w > 1 ? sp.y : 0, n, 8) &&
+                IQP_IN(sp.w > 2 ? sp.z : 0, n, 8)) {
                 // ldrt32 is a multiple of 8 and w0 + q of 4: the 16-byte word is inside the row
                 if (sp.w > 0) {
                     const uint4 a = *reinterpret_cast<const uint4 *>(RT + (int64_t)sp.x * ldrt32 + w0 + q);
@@ -234,7 +241,7 @@ __global__ void __launch_bounds__(kTT) k_gather_transpose(const int4 *__restrict
                     const uint4 a = *reinterpret_cast<const uint4 *>(RT + (int64_t)sp.z * ldrt32 + w0 + q);
                     v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
                 }
-            } else {
+            } else if (sp.w > 3) {
                 // every qubit of the support, from the packed row
                 const int64_t nw = (n + 63) >> 6;
                 for (int64_t w = 0; w < nw; ++w) {
@@ -288,7 +295,7 @@ __global__ void __launch_bounds__(kTT) k_gather_transpose(const int4 *__restrict
         const int64_t orow = c0 + row;
         if (orow >= rows) continue;
         // ldp32 is a multiple of 8 and ow0 + q of 4: whole 16-byte words
-        if (ow0 + q < ldp32)
+        if (ow0 + q < ldp32 && IQP_IN(orow * ldp32 + ow0 + q + 3, rows * ldp32, 9))
             *reinterpret_cast<uint4 *>(P + orow * ldp32 + ow0 + q) =
                 make_uint4(tin[row][q], tin[row][q + 1], tin[row][q + 2], tin[row][q + 3]);
     }
@@ -319,6 +326,7 @@ __global__ void __launch_bounds__(256) k_support_gather(const uint64_t *__restri
                 wv &= wv - 1ull;
                 const int64_t q = (int64_t)64 * (wb + src) + b;
                 if (q >= n) break;  // padding bits must be zero; never read past R^T
+                if (!IQP_IN(q * ldrt + wt, n * ldrt, 10)) continue;
                 const uint64_t *rt = RT + q * ldrt + wt;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
@@ -331,7 +339,7 @@ __global__ void __launch_bounds__(256) k_support_gather(const uint64_t *__restri
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
         const int64_t w = wt + lane + 32 * k;
-        if (w < ldpt) PT[j * ldpt + w] = acc[k];
+        if (w < ldpt && IQP_IN(j * ldpt + w, m * ldpt, 11)) PT[j * ldpt + w] = acc[k];
     }
 }
 
@@ -375,7 +383,7 @@ __global__ void __launch_bounds__(256) k_support_list(const uint64_t *__restrict
             }
         }
     }
-    if (lane == 0) sup[j] = make_int4(q0, q1, q2, cnt);
+    if (lane == 0 && IQP_IN(j, m, 12)) sup[j] = make_int4(q0, q1, q2, cnt);
 }
 
 // The same list with one thread per generator, for rows of at most 16 words
@@ -398,7 +406,7 @@ __global__ void __launch_bounds__(256) k_support_list_short(const uint64_t *__re
                 ++cnt;
             }
         }
-        sup[j] = make_int4(q0, q1, q2, cnt);
+        if (IQP_IN(j, m, 13)) sup[j] = make_int4(q0, q1, q2, cnt);
     }
 }
 

@@ -11,6 +11,8 @@
 
 namespace iqp {
 
+uint32_t check_word_simt() { return take_check_word(); }
+
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32, PADF = 4;
@@ -23,6 +25,7 @@ __global__ void k_theta_prep(const float *__restrict__ theta, int64_t m, int64_t
                              __nv_bfloat16 *__restrict__ hi, __nv_bfloat16 *__restrict__ lo) {
     for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < mpad; j += (int64_t)gridDim.x * blockDim.x) {
         const float c = j < m ? 2.0f * theta[j] : 0.0f;
+        if (!IQP_IN(j, mpad, 20)) continue;
         if (c32) c32[j] = c;
         if (hi) {
             const __nv_bfloat16 h = __float2bfloat16_rn(c);
@@ -63,7 +66,8 @@ __global__ void __launch_bounds__(256) k_phase_simt(const uint32_t *__restrict__
 #pragma unroll
         for (int q = 0; q < 8; ++q) acc[r][q] = 0.f;
 
-    uint32_t bits = rvalid ? src[0] : 0u;
+    const int64_t srows = isA ? l : s;  // rows of the matrix this thread reads
+    uint32_t bits = rvalid && IQP_IN((src - (isA ? PA : PZ)) + 0, srows * ldp32, 21) ? src[0] : 0u;
     float cnext = tid < BK ? c[tid] : 0.f;
     for (int64_t kw = 0; kw < kwords; ++kw) {
         const int buf = (int)(kw & 1);
@@ -78,8 +82,8 @@ __global__ void __launch_bounds__(256) k_phase_simt(const uint32_t *__restrict__
         }
         __syncthreads();
         if (kw + 1 < kwords) {
-            bits = rvalid ? src[kw + 1] : 0u;
-            cnext = tid < BK ? c[(kw + 1) * BK + tid] : 0.f;
+            bits = rvalid && IQP_IN((src - (isA ? PA : PZ)) + kw + 1, srows * ldp32, 22) ? src[kw + 1] : 0u;
+            cnext = tid < BK && IQP_IN((kw + 1) * BK + tid, kwords * BK, 23) ? c[(kw + 1) * BK + tid] : 0.f;
         }
 #pragma unroll 8
         for (int k = 0; k < BK; ++k) {
@@ -121,7 +125,8 @@ __global__ void __launch_bounds__(256) k_phase_simt(const uint32_t *__restrict__
             }
 #pragma unroll
             for (int off = 8; off >= 1; off >>= 1) m2 += __shfl_xor_sync(0xFFFFFFFFu, m2, off);
-            if (tx == 0 && a < l) part[a * nparts + blockIdx.x] = make_double2((double)sum, (double)m2);
+            if (tx == 0 && a < l && IQP_IN(a * nparts + blockIdx.x, l * nparts, 24))
+                part[a * nparts + blockIdx.x] = make_double2((double)sum, (double)m2);
         } else {
             if (a < l) {
                 const float al = (float)alpha[a];
@@ -129,7 +134,7 @@ __global__ void __launch_bounds__(256) k_phase_simt(const uint32_t *__restrict__
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int64_t i = i0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + (q - 4));
-                    if (i < s) {
+                    if (i < s && IQP_IN(a * ldw + i, l * ldw, 25)) {
                         float sn, cn;
                         sincosf(acc[r][q], &sn, &cn);
                         W[a * ldw + i] = sn * (al + be * cn);
@@ -172,7 +177,7 @@ __global__ void __launch_bounds__(256) k_grad_simt(const float *__restrict__ W, 
         for (int q = 0; q < 4; ++q) {
             const int64_t i = ib + wc + 4 * q;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (wrow < l) {
+            if (wrow < l && IQP_IN(wrow * ldw + (i + 3 < s ? i + 3 : (i < s ? i : 0)), l * ldw, 26)) {
                 if (i + 3 < s) {
                     v = *reinterpret_cast<const float4 *>(W + wrow * ldw + i);
                 } else {
@@ -190,7 +195,8 @@ __global__ void __launch_bounds__(256) k_grad_simt(const float *__restrict__ W, 
         {
             const int64_t i = ib + bk;
             uint32_t b = 0u;
-            if (i < s) b = (PZ[i * ldp32 + ((j0 + bg * 16) >> 5)] >> ((bg & 1) * 16)) & 0xFFFFu;
+            if (i < s && IQP_IN(i * ldp32 + ((j0 + bg * 16) >> 5), s * ldp32, 27))
+                b = (PZ[i * ldp32 + ((j0 + bg * 16) >> 5)] >> ((bg & 1) * 16)) & 0xFFFFu;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 float4 v;
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(256) k_grad_simt(const float *__restrict__ W, 
 #pragma unroll
     for (int r = 0; r < 8; ++r) {
         const int64_t a = a0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
-        if (a < l) {
+        if (a < l && IQP_IN(a * ldp32 + ((j0 + 64 + tx * 4) >> 5), l * ldp32, 28)) {
             const uint32_t w_lo = PA[a * ldp32 + ((j0 + tx * 4) >> 5)];
             const uint32_t w_hi = PA[a * ldp32 + ((j0 + 64 + tx * 4) >> 5)];
 #pragma unroll
@@ -244,7 +250,7 @@ __global__ void __launch_bounds__(256) k_grad_simt(const float *__restrict__ W, 
 #pragma unroll
         for (int y = 0; y < 16; ++y) t += (double)red[y][tid];
         const int64_t j = j0 + tid;
-        if (j < m) gpart[(int64_t)blockIdx.y * m + j] = t;
+        if (j < m && IQP_IN((int64_t)blockIdx.y * m + j, (int64_t)gridDim.y * m, 29)) gpart[(int64_t)blockIdx.y * m + j] = t;
     }
 }
 
@@ -257,6 +263,7 @@ __global__ void k_finalize(const double2 *__restrict__ part, int64_t nparts, int
                            double *__restrict__ S2) {
     const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (a >= l) return;
+    if (!IQP_IN(a * nparts + nparts - 1, l * nparts, 30)) return;
     const double2 *p = part + a * nparts;
     double S = 0.0;
     for (int64_t k = 0; k < nparts; ++k) S += p[k].x;

@@ -115,12 +115,17 @@ struct ZSource {
     const uint64_t *G;
     int64_t ldg;
     int64_t n;
+    int64_t m;            // gates
 
     template <bool INDEP>
     __device__ __forceinline__ uint64_t get(int64_t j) const {
+        if (!IQP_IN(j, m, 70)) return 0ull;  // a set parity bit past the last gate
         if (!INDEP) return __ldg(PZT + j * ldzt + word);
         const int4 sp = __ldg(sup + j);
         if (sp.w <= 3) {
+            if (!IQP_IN(sp.w > 0 ? sp.x : 0, n, 71) || !IQP_IN(sp.w > 1 ? sp.y : 0, n, 71) ||
+                !IQP_IN(sp.w > 2 ? sp.z : 0, n, 71))
+                return 0ull;
             uint64_t z = 0ull;
             if (sp.w > 0) z = __ldg(PZT + (int64_t)sp.x * ldzt + word);
             if (sp.w > 1) z ^= __ldg(PZT + (int64_t)sp.y * ldzt + word);
@@ -229,7 +234,7 @@ struct GradRun {
         float d = signed_dot(w, z);
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) d += __shfl_xor_sync(kFull, d, off);
-        if (lane == 0) {
+        if (lane == 0 && IQP_IN(j, zs.m, 72)) {
             const float x = sc * d;
             const float hi = truncf(x * 0x1.0p-31f);
             const float lo = fmaf(-hi, 0x1.0p31f, x);
@@ -262,7 +267,7 @@ struct GradRun {
 template <int MODE, bool INDEP>
 __global__ void __launch_bounds__(256, 2)
     k_sparse(const uint64_t *__restrict__ PA, int64_t ldp, const uint64_t *__restrict__ PZT, int64_t ldzt,
-             const float *__restrict__ c, int64_t s, int64_t nparts, double2 *__restrict__ part,
+             int64_t m, const float *__restrict__ c, int64_t s, int64_t nparts, double2 *__restrict__ part,
              const double *__restrict__ alpha, const double *__restrict__ beta, const double *__restrict__ scale,
              unsigned long long *__restrict__ gfx, const int4 *__restrict__ sup, const uint64_t *__restrict__ G,
              int64_t ldg, int64_t n, float *__restrict__ phi, int64_t ldphi) {
@@ -277,23 +282,25 @@ __global__ void __launch_bounds__(256, 2)
     const int64_t i0 = word_raw * 64;
     const int nvalid = !wvalid ? 0 : (s - i0 >= 64 ? 64 : (int)(s - i0));
     const uint64_t *parow = PA + a * ldp;
-    const ZSource zs{INDEP ? PZT + a * n * ldzt : PZT, ldzt, word, sup, G, ldg, n};
+    const ZSource zs{INDEP ? PZT + a * n * ldzt : PZT, ldzt, word, sup, G, ldg, n, m};
+    [[maybe_unused]] const int64_t l = gridDim.x;  // one observable per CTA column
 
     uint64_t acc2[32];
     // The lane's 64 samples i0 .. i0 + 63 lie inside a row of phi (ldphi is a
     // multiple of 64) whenever the lane's word is valid; they are kept in the
     // accumulators' pair order (pair t: samples t and 32 + t), 256 bytes a lane.
     if (MODE == 1 && !INDEP && phi != nullptr) {
-        const uint4 *prow = reinterpret_cast<const uint4 *>(phi + a * ldphi + (wvalid ? i0 : 0));
+        const bool pin = IQP_IN(a * ldphi + (wvalid ? i0 + 63 : 0), l * ldphi, 73);
+        const uint4 *prow = reinterpret_cast<const uint4 *>(phi + a * ldphi + (wvalid && pin ? i0 : 0));
 #pragma unroll
         for (int v = 0; v < 16; ++v) {
-            const uint4 q = wvalid ? prow[v] : make_uint4(0u, 0u, 0u, 0u);
+            const uint4 q = wvalid && pin ? prow[v] : make_uint4(0u, 0u, 0u, 0u);
             acc2[2 * v] = (uint64_t)q.x | ((uint64_t)q.y << 32);
             acc2[2 * v + 1] = (uint64_t)q.z | ((uint64_t)q.w << 32);
         }
     } else {
         phase_row<INDEP>(acc2, parow, ldp, zs, c, lane);
-        if (MODE == 0 && !INDEP && phi != nullptr && wvalid) {
+        if (MODE == 0 && !INDEP && phi != nullptr && wvalid && IQP_IN(a * ldphi + i0 + 63, l * ldphi, 74)) {
             uint4 *prow = reinterpret_cast<uint4 *>(phi + a * ldphi + i0);
 #pragma unroll
             for (int v = 0; v < 16; ++v)
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(256, 2)
         double dm = (double)m2;
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) dm += __shfl_xor_sync(kFull, dm, off);
-        if (lane == 0) part[a * nparts + r] = make_double2(ds, dm);
+        if (lane == 0 && IQP_IN(a * nparts + r, l * nparts, 75)) part[a * nparts + r] = make_double2(ds, dm);
     }
     if (MODE != 0) {
         const float al = (float)alpha[a];
@@ -410,6 +417,7 @@ dim3 sparse_grid(int64_t l, int64_t nparts, int *threads) {
 }  // namespace
 
 int64_t sparse_part_samples() { return kWarpSamples; }
+uint32_t check_word_sparse() { return take_check_word(); }
 
 // Statistics partials and the gradient from one pass over Phi (shared
 // batches; alpha, beta known before the estimates): k_sparse<2>.
@@ -428,7 +436,7 @@ cudaError_t launch_sparse_value_grad(const uint64_t *PA, int64_t ldp, const uint
         int threads = 0;
         const dim3 grid = sparse_grid(l, nparts, &threads);
         LaunchScope ls(IQP_KERNEL_PHASE_SPARSE, st);
-        k_sparse<2, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, alpha, beta, scale, gfx,
+        k_sparse<2, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, m, c, s, nparts, part, alpha, beta, scale, gfx,
                                                      nullptr, nullptr, 0, 0, nullptr, 0);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -451,17 +459,17 @@ cudaError_t launch_fixed_scale(const double *alpha, const double *beta, int64_t 
 // indep != nullptr: independent batches (PZT = every observable's ZT).
 // phi != nullptr: Phi is kept there (l x ldphi FP32, ldphi a multiple of 64).
 cudaError_t launch_sparse_stats(const uint64_t *PA, int64_t ldp, const uint64_t *PZT, int64_t ldzt, const float *c,
-                                int64_t l, int64_t s, double2 *part, int64_t nparts, const SparseIndep *indep,
-                                float *phi, int64_t ldphi, cudaStream_t st) {
+                                int64_t l, int64_t s, int64_t m, double2 *part, int64_t nparts,
+                                const SparseIndep *indep, float *phi, int64_t ldphi, cudaStream_t st) {
     int threads = 0;
     const dim3 grid = sparse_grid(l, nparts, &threads);
     LaunchScope ls(IQP_KERNEL_PHASE_SPARSE, st);
     if (indep)
-        k_sparse<0, true><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, nullptr, nullptr,
+        k_sparse<0, true><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, m, c, s, nparts, part, nullptr, nullptr,
                                                     nullptr, nullptr, indep->sup, indep->G, indep->ldg, indep->n,
                                                     phi, ldphi);
     else
-        k_sparse<0, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, part, nullptr, nullptr,
+        k_sparse<0, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, m, c, s, nparts, part, nullptr, nullptr,
                                                      nullptr, nullptr, nullptr, nullptr, 0, 0, phi, ldphi);
     return cudaGetLastError();
 }
@@ -482,11 +490,11 @@ cudaError_t launch_sparse_grad(const uint64_t *PA, int64_t ldp, const uint64_t *
         const dim3 grid = sparse_grid(l, nparts, &threads);
         LaunchScope ls(IQP_KERNEL_GRAD_SPARSE, st);
         if (indep)
-            k_sparse<1, true><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, nullptr, alpha, beta, scale,
+            k_sparse<1, true><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, m, c, s, nparts, nullptr, alpha, beta, scale,
                                                         gfx, indep->sup, indep->G, indep->ldg, indep->n,
                                                         const_cast<float *>(phi), ldphi);
         else
-            k_sparse<1, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, c, s, nparts, nullptr, alpha, beta,
+            k_sparse<1, false><<<grid, threads, 0, st>>>(PA, ldp, PZT, ldzt, m, c, s, nparts, nullptr, alpha, beta,
                                                          scale, gfx, nullptr, nullptr, 0, 0, const_cast<float *>(phi),
                                                          ldphi);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

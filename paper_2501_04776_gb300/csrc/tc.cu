@@ -68,6 +68,7 @@
 namespace iqp {
 
 uint64_t default_spin_limit_ns();
+uint32_t check_word_tc() { return take_check_word(); }
 
 namespace {
 
@@ -140,6 +141,7 @@ struct TcArgs {
     int64_t tiles_m, tiles_n;
     int64_t group_m;      // row blocks per tile group (L2 rasterisation)
     const __nv_bfloat16 *chi, *clo;
+    int64_t mpad;          // length of chi / clo
     double2 *part;
     int64_t nparts;
     const double *alpha, *beta;
@@ -335,6 +337,8 @@ __global__ void __launch_bounds__(256) k_w_from_phi(const float *__restrict__ ph
     for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < total; g += (int64_t)gridDim.x * blockDim.x) {
         const int64_t row = g / per_row, i0 = (g - row * per_row) * 4;
         if (i0 >= s) continue;
+        if (!IQP_IN(row, l, 40) || !IQP_IN(row * ldphi + i0 + 3, l * ldphi, 41) || !IQP_IN(row * ldw + i0 + 3, l * ldw, 42))
+            continue;
         const float al = (float)alpha[row];
         const float be = beta ? (float)beta[row] : 0.f;
         const float4 f = *reinterpret_cast<const float4 *>(phi + row * ldphi + i0);
@@ -361,6 +365,9 @@ __global__ void __launch_bounds__(256) k_w_from_phi(const float *__restrict__ ph
 // W hi/lo (BF16 pairs) of 32 consecutive samples i0.. of observable row.
 __device__ __forceinline__ void store_w32(const TcArgs &args, int64_t row, int64_t i0, const uint32_t (&ph)[16],
                                           const uint32_t (&pl)[16]) {
+    if (!IQP_IN(row * args.ldw + i0, args.l * args.ldw, 43) ||
+        !IQP_IN(row * args.ldw + (i0 + 32 <= args.s ? i0 + 31 : args.s - 1), args.l * args.ldw, 44))
+        return;
     __nv_bfloat16 *dh = args.whi + row * args.ldw + i0;
     __nv_bfloat16 *dl = args.wlo + row * args.ldw + i0;
     if (i0 + 32 <= args.s) {
@@ -383,6 +390,9 @@ __device__ __forceinline__ void store_w32(const TcArgs &args, int64_t row, int64
 // args.out (row-major, args.ldo elements per row, columns < args.s): FP32, or
 // FP64 when args.out_f64. Rows start 16-byte aligned (ldo a multiple of 4).
 __device__ __forceinline__ void store_out32(const TcArgs &args, int64_t row, int64_t col0, const uint32_t (&r)[32]) {
+    if (!IQP_IN(row * args.ldo + col0, args.l * args.ldo, 45) ||
+        !IQP_IN(row * args.ldo + (col0 + 32 <= args.s ? col0 + 31 : args.s - 1), args.l * args.ldo, 46))
+        return;
     if (args.out_f64) {
         double *d = static_cast<double *>(args.out) + row * args.ldo + col0;
         if (col0 + 32 <= args.s) {
@@ -551,8 +561,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         mbar_arrive_expect_tx(&bar->bits_full[bs], TM * 32 + C::TNB * 32 + 1024);
                         tma_load_2d(bits + C::BT_A, &tmA, &bar->bits_full[bs], x, a0);
                         tma_load_2d(bits + C::BT_B, &tmB, &bar->bits_full[bs], x, b0);
-                        bulk_load(bits + C::BT_CHI, args.chi + kb * KB, 512, &bar->bits_full[bs]);
-                        bulk_load(bits + C::BT_CLO, args.clo + kb * KB, 512, &bar->bits_full[bs]);
+                        // the split of 2 theta is mpad long (bits stages never pass it)
+                        const bool cin = IQP_IN((int64_t)kb * KB + KB - 1, args.mpad, 54);
+                        bulk_load(bits + C::BT_CHI, args.chi + (cin ? kb * KB : 0), 512, &bar->bits_full[bs]);
+                        bulk_load(bits + C::BT_CLO, args.clo + (cin ? kb * KB : 0), 512, &bar->bits_full[bs]);
                     }
                     bmask |= 1u << bs;
                     bpar = (bpar & ~(1u << bs)) | (((itb / NBITS) & 1u) << bs);
@@ -826,8 +838,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // CTA that finishes the tile's last part sums every part's,
                 // in part order, back into TMEM and runs the epilogue.
                 const int64_t half = CG == 2 ? (int64_t)crank : 0;
-                split_store(args.skp + ((uv * CG + half) * TM + rl) * TN + group * kGroupCols, tbase, chunked,
-                            ATM ? sum4 + ((group * kGroupCols) >> 2) * TM + rl : nullptr);
+                [[maybe_unused]] constexpr int64_t kSkp = (int64_t)kMaxSplitCtas * kSplitSlotFloats;  // slot floats
+                const int64_t so = ((uv * CG + half) * TM + rl) * TN + group * kGroupCols;
+                if (IQP_IN(so + kGroupCols - 1, kSkp, 47))
+                    split_store(args.skp + so, tbase, chunked, ATM ? sum4 + ((group * kGroupCols) >> 2) * TM + rl : nullptr);
                 __threadfence();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar->part_done);
@@ -835,11 +849,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t nsu = tcount;          // split parts this CTA finished before
                 if (warp == 2 && lane == 0) {
                     if (mbar_wait(&bar->part_done, nsu & 1u, abort_flag, status, lim)) {
-                        int *cnt = args.skc + tt * CG + half;
-                        const int last = atomicAdd(cnt, 1) == args.nsplit - 1;
-                        if (last) {
-                            atomicExch(cnt, 0);  // ready for the next launch
-                            __threadfence();
+                        int last = 0;
+                        if (IQP_IN(tt * CG + half, kMaxSplitCtas, 48)) {
+                            int *cnt = args.skc + tt * CG + half;
+                            last = atomicAdd(cnt, 1) == args.nsplit - 1;
+                            if (last) {
+                                atomicExch(cnt, 0);  // ready for the next launch
+                                __threadfence();
+                            }
                         }
                         bar->last_flag = last;
                     }
@@ -854,8 +871,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     continue;  // another CTA finishes this tile
                 }
                 __threadfence();
-                split_sum(args.skp + ((tt * args.nsplit * CG + half) * TM + rl) * TN + group * kGroupCols,
-                          (int64_t)CG * TM * TN, args.nsplit, tbase);
+                const int64_t s0 = ((tt * args.nsplit * CG + half) * TM + rl) * TN + group * kGroupCols;
+                if (IQP_IN(s0 + (int64_t)(args.nsplit - 1) * CG * TM * TN + kGroupCols - 1, kSkp, 49))
+                    split_sum(args.skp + s0, (int64_t)CG * TM * TN, args.nsplit, tbase);
                 chunked = false;  // the sum of the parts is in the accumulator columns
             }
             // Phi (or Q) for 32 columns: last chunk's accumulator + running sum.
@@ -892,7 +910,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         if (row < args.l) store_out32(args, row, c0 + c * 32, r);
                     }
                 }
-                if (row < args.l && nvalid > 0)
+                if (row < args.l && nvalid > 0 && IQP_IN(row * args.nparts + c0 / kGroupCols, args.l * args.nparts, 50))
                     args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
             } else if (!GRAD && MODE == 2) {
                 // Both: the statistics of MODE 0 and W of MODE 1 from one
@@ -901,7 +919,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int64_t nvalid = args.s - c0;
                 nvalid = nvalid < 0 ? 0 : (nvalid > kGroupCols ? kGroupCols : nvalid);
                 const bool rv = row < args.l;
-                const float al = rv ? (float)args.alpha[row] : 0.f;
+                const float al = rv && IQP_IN(row, args.l, 55) ? (float)args.alpha[row] : 0.f;
                 const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
                 float S = 0.f, M2 = 0.f;
                 uint32_t r[32];
@@ -934,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (rv && i0 < args.s) store_w32(args, row, i0, ph, pl);
                 }
-                if (rv && nvalid > 0)
+                if (rv && nvalid > 0 && IQP_IN(row * args.nparts + c0 / kGroupCols, args.l * args.nparts, 51))
                     args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
             } else if (!GRAD && MODE == 3) {
                 const int64_t c0 = tn * TN + group * kGroupCols;
@@ -947,7 +965,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             } else if (!GRAD) {
                 const int64_t c0 = tn * TN + group * kGroupCols;
                 const bool rv = row < args.l;
-                const float al = rv ? (float)args.alpha[row] : 0.f;
+                const float al = rv && IQP_IN(row, args.l, 55) ? (float)args.alpha[row] : 0.f;
                 const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
                 uint32_t r[32];
 #pragma unroll 1
@@ -976,7 +994,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 for (int c = 0; c < kGroupLoads; ++c) {
                     load_sum32(tbase + c * 32, chunked, r, ssum(c));
                     const int64_t j0 = tn * TN + group * kGroupCols + c * 32;
-                    const uint32_t mask = (rv && j0 < args.m) ? args.pa32[row * args.ldp32 + (j0 >> 5)] : 0u;
+                    const uint32_t mask = (rv && j0 < args.m &&
+                                           IQP_IN(row * args.ldp32 + (j0 >> 5), args.l * args.ldp32, 52))
+                                              ? args.pa32[row * args.ldp32 + (j0 >> 5)]
+                                              : 0u;
                     float v[32];
 #pragma unroll
                     for (int e = 0; e < 32; ++e) v[e] = ((mask >> e) & 1u) ? 2.f * __uint_as_float(r[e]) : 0.f;
@@ -997,7 +1018,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (gt < TN && j < args.m && arow0 < args.l) {
                     const double sum = (double)red[gt] + (double)red[256 + gt] + (double)red[512 + gt] +
                                        (double)red[768 + gt];
-                    args.gpart[(arow0 / TM) * args.m + j] = sum;
+                    if (IQP_IN((arow0 / TM) * args.m + j, args.tiles_m * args.m, 53))
+                        args.gpart[(arow0 / TM) * args.m + j] = sum;
                 }
             }
             tc_fence_before();
@@ -1372,7 +1394,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
 #pragma unroll
                 for (int w = 0; w < NW; ++w) {
                     const int64_t wi = a0 / 32 + w;
-                    if (wi < args.ldlt32) mk[w] = __ldg(args.pat32 + j * args.ldlt32 + wi);
+                    if (wi < args.ldlt32 && IQP_IN(j * args.ldlt32 + wi, args.m * args.ldlt32, 56))
+                        mk[w] = __ldg(args.pat32 + j * args.ldlt32 + wi);
                     const int64_t rem = args.l - (a0 + 32 * w);  // valid observables in this word
                     if (rem < 32) mk[w] &= rem <= 0 ? 0u : ((1u << rem) - 1u);
                 }
@@ -1404,7 +1427,8 @@ __global__ void __launch_bounds__(kGThreads, 1)
                 gsum += 2.0 * (double)part;
             }
             if (!ok) break;
-            if (j < args.m) args.gpart[(2 * to + e) * args.m + j] = gsum;
+            if (j < args.m && IQP_IN((2 * to + e) * args.m + j, 2 * args.tiles_o * args.m, 57))
+                args.gpart[(2 * to + e) * args.m + j] = gsum;
         }
     }
 
@@ -1614,6 +1638,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.tiles_n = cdiv(p.s, TN);
     a.group_m = tile_group();
     a.chi = at<__nv_bfloat16>(ws, p.off_c);
+    a.mpad = p.mpad;
     a.clo = a.chi + p.mpad;
     a.part = at<double2>(ws, p.off_part);
     a.nparts = p.nparts;
@@ -1754,6 +1779,7 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
     a.tiles_n = cdiv(p.m, TN);
     a.group_m = tile_group();
     a.chi = a.clo = nullptr;
+    a.mpad = 0;
     a.part = nullptr;
     a.nparts = 0;
     a.alpha = a.beta = nullptr;
@@ -1808,6 +1834,7 @@ cudaError_t launch_tc_dense(const __nv_bfloat16 *a_hi, const __nv_bfloat16 *a_lo
     a.tiles_n = cdiv(nb, TN);
     a.group_m = tile_group();
     a.chi = a.clo = nullptr;
+    a.mpad = 0;
     a.part = nullptr;
     a.nparts = 0;
     a.alpha = a.beta = nullptr;

@@ -34,7 +34,8 @@ __global__ void k_expand_params(const float *__restrict__ theta_p, int64_t np, c
         j0 = j0 < 0 ? 0 : j0;
         j1 = j1 > m ? m : j1;
         const float t = theta_p[p];
-        for (int64_t j = j0; j < j1; ++j) theta_gen[j] = t;
+        for (int64_t j = j0; j < j1; ++j)
+            if (IQP_IN(j, m, 102)) theta_gen[j] = t;
     }
 }
 
@@ -46,7 +47,8 @@ __global__ void k_reduce_params(const double *__restrict__ grad_gen, int64_t m, 
         j0 = j0 < 0 ? 0 : j0;
         j1 = j1 > m ? m : j1;
         double acc = 0.0;
-        for (int64_t j = j0; j < j1; ++j) acc += grad_gen[j];
+        for (int64_t j = j0; j < j1; ++j)
+            if (IQP_IN(j, m, 103)) acc += grad_gen[j];
         grad_p[p] = acc;
     }
 }
@@ -63,6 +65,7 @@ __global__ void k_embed_bits(const uint64_t *__restrict__ src, int64_t rows, int
         for (int64_t k = 0; k < nw; ++k) {
             const int64_t q = wires[k];
             if (q < 0 || q >= n) continue;
+            if (!IQP_IN(k >> 6, ld_src, 100) || !IQP_IN(q >> 6, ld_dst, 101)) continue;
             if ((s[k >> 6] >> (k & 63)) & 1ull) d[q >> 6] |= 1ull << (q & 63);
         }
     }
@@ -107,6 +110,12 @@ __global__ void k_bernoulli_bits(uint64_t seed, uint64_t stream, int64_t rows, i
         out[e] = v;
     }
 }
+
+}  // namespace
+
+uint32_t check_word_variants() { return take_check_word(); }
+
+namespace {
 
 int grid_for(int64_t work) {
     int64_t b = cdiv(work, 256);
