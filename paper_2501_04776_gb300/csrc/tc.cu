@@ -1050,7 +1050,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 //    CTA's producers also wait for the stage's W (w_full, both CTAs' halves)
 //    before they arrive, and the odd CTA's readiness is forwarded by one
 //    thread, so the MMA thread waits on a single barrier per stage.
-//  - The accumulator (256 TMEM columns) is reduced every 4096 samples by
+//  - The accumulator (256 TMEM columns) is reduced after every chunk of at
+//    most 5120 samples (see kGChunkMax) by
 //    eight epilogue warps: mask by 2 P_A[a][j] (bits of P_A^T), sum over the
 //    warp's 128 observables in FP32, add into an FP64 per-gate partial. Each
 //    epilogue warp writes one FP64 partial per (tile, gate): row
@@ -1072,7 +1073,12 @@ constexpr int GEPI = 8;          // epilogue warps
 constexpr int GW0 = 3;           // first producer warp
 constexpr int GE0 = GW0 + GPROD; // first epilogue warp
 constexpr int kGThreads = (GE0 + GEPI) * 32;
-constexpr int kGChunk = 4096 / GKS;  // operand stages per accumulation chunk
+// Accumulation chunks: a tile's K loop is cut into the fewest chunks of at
+// most kGChunkMax stages (5120 samples), of equal length up to one stage. Each
+// chunk boundary stalls the MMAs while the epilogue reads the accumulator, so
+// fewer, longer chunks are faster; 5120 samples keep the tensor core's
+// truncating FP32 accumulation well inside the gradient tolerance.
+constexpr int kGChunkMax = 5120 / GKS;
 constexpr uint32_t kGAcol = GN;      // first A column
 
 struct GCfg {
@@ -1101,6 +1107,7 @@ struct GBars {
 struct GradArgs {
     int64_t l, s, m;
     int64_t nks;                  // operand stages per tile: ceil(s / GKS)
+    int64_t chunk;                // operand stages per accumulation chunk
     int64_t tiles_g, tiles_o;     // gate blocks (256), observable blocks (GN)
     int64_t group_o;              // observable blocks per tile group (L2 rasterisation)
     const uint32_t *pat32;        // P_A^T: m rows of ldlt32 32-bit words (bits over observables)
@@ -1126,6 +1133,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
     const int64_t group0 = blockIdx.x / 2, ngroups = gridDim.x / 2;
     const int64_t ntiles = args.tiles_g * args.tiles_o;
     const int nks = (int)args.nks;
+    const int chunk = (int)args.chunk;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < NBITS; ++i) {
@@ -1270,7 +1278,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
                     umma_stage8_pair_ts_b(tmem, tmem + kGAcol + os * GACOLS, dhi, dhi + (C::OP_LO >> 4), C::IDESC,
                                           kc == 0 ? 0u : 1u);
                     umma_commit_pair(&bar->empty[os]);
-                    if (++kc == kGChunk || ks == nks - 1) {
+                    if (++kc == chunk || ks == nks - 1) {
                         umma_commit_pair(&bar->acc_full);
                         ++nchk;
                         kc = 0;
@@ -1379,7 +1387,7 @@ __global__ void __launch_bounds__(kGThreads, 1)
         constexpr int NW = GNB / 32;
         uint32_t nchk = 0;
         bool ok = true;
-        const int nch = (nks + kGChunk - 1) / kGChunk;
+        const int nch = (nks + chunk - 1) / chunk;
         for (int64_t t = group0; t < ntiles && ok; t += ngroups) {
             int64_t to, tg;
             tile_coords(t, args.tiles_o, args.tiles_g, args.group_o, to, tg);
@@ -1712,6 +1720,7 @@ cudaError_t launch_grad_pair(const Plan &p, void *ws, cudaStream_t st, iqp_statu
     a.s = p.s;
     a.m = p.m;
     a.nks = cdiv(p.s, GKS);
+    a.chunk = cdiv(a.nks, cdiv(a.nks, kGChunkMax));  // fewest chunks, balanced
     a.tiles_g = cdiv(p.m, 2 * TM);
     a.tiles_o = cdiv(p.l, GN);
     a.group_o = tile_group();
