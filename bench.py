@@ -200,9 +200,9 @@ def tensor_source_sha():
 
 
 def measured_traffic(kernel, sizes):
-    """DRAM bytes per contraction of `kernel` (summed over its launches), from the committed ncu capture
-    (profiles/dram_traffic.json: a small case of the same kernel, scaled to the full launch by the tiles it
-    processes), or None if the kernel sources changed since the capture."""
+    """DRAM bytes per contraction of `kernel` (summed over its launches), from the committed one-pass ncu
+    capture of the same workload (profiles/dram_traffic.json), or None if the kernel sources changed since the
+    capture or the workload differs."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "dram_traffic.json")))
         if tensor_source_sha() != rec["source_sha"]:
@@ -325,6 +325,17 @@ def split_bf16_roofline(kt, dom, l, s, m, steps, peaks, step_ms=None, contractio
         roof["step_useful"] = {"tflops": round(st, 1), "frac": round(st / peak, 4), "contractions": contractions}
     return roof
 
+def tensor_algorithmic_bytes(kernel, l, s, m):
+    """Bytes a tensor-core contraction must move at least once, each operand read once and each result
+    written once. Phase pass of the fused step: P_A and P_Z bits (rows of ceil(m / 256) * 4 words), W hi and
+    lo written (BF16, l x s each), the (sum cos, M2) partials (16 bytes per 64 samples). Gradient: W hi and lo
+    read, P_Z^T and P_A^T bits, the FP64 partial rows (two per 256 observables)."""
+    ldp = -(-m // 256) * 4
+    if kernel == "grad_tc":
+        return 4.0 * l * s + 32.0 * m * (-(-s // 256) + -(-l // 256)) + 16.0 * -(-l // 256) * m
+    return 8.0 * ldp * (l + s) + 4.0 * l * s + 16.0 * l * -(-s // 64)
+
+
 def generator_pairs(n, G):
     """Number of distinct qubit pairs that carry a weight-2 generator
     (host-side count from the packed rows)."""
@@ -375,7 +386,7 @@ def parity_roofline(kt, peaks, n, m, l, s, steps, calls=2, loworder=False):
     ms = kt["parity"]["total_ms"] / max(1, steps)
     hbm = peaks.get("hbm_gbs") or 6800.0
     gbs = nbytes / (ms * 1e-3) / 1e9
-    names = "k_support_list + k_bit_transpose" if loworder else "k_bit_transpose + k_support_gather"
+    names = "k_support_list + k_bit_transpose" if loworder else "k_bit_transpose + k_gather_transpose"
     return {"bound": "hbm", "kernels": names, "bytes_per_step": nbytes,
             "ms_per_step": round(ms, 4), "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(gbs / hbm, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
@@ -863,6 +874,9 @@ def main():
         roof = split_bf16_roofline(kt, dom, l, s, m, args.steps, peaks, ms,
                                    contractions=2 if args.step == "fused" else 3)
         roof["traffic"] = measured_traffic(dom, (n, m, l, s))
+        alg = tensor_algorithmic_bytes(dom, l, s, m)
+        roof["algorithmic_bytes"] = alg
+        roof["traffic_ratio"] = None if roof["traffic"] is None else round(roof["traffic"] / alg, 3)
     elif prec == _lib.LOWORDER_FP32:
         roof = loworder_roofline(kt, clocks, n, p.G, s, peaks)
         roof["traffic"] = None

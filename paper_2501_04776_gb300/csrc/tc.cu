@@ -1050,10 +1050,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 //    CTA's producers also wait for the stage's W (w_full, both CTAs' halves)
 //    before they arrive, and the odd CTA's readiness is forwarded by one
 //    thread, so the MMA thread waits on a single barrier per stage.
-//  - The accumulator (256 TMEM columns) is reduced after every chunk of at
-//    most 5120 samples (see kGChunkMax) by
-//    eight epilogue warps: mask by 2 P_A[a][j] (bits of P_A^T), sum over the
-//    warp's 128 observables in FP32, add into an FP64 per-gate partial. Each
+//  - The accumulator (256 TMEM columns) is reduced after every accumulation
+//    chunk (see below) by eight epilogue warps: mask by 2 P_A[a][j] (bits of
+//    P_A^T), sum over the warp's 128 observables in FP32, add into an FP64
+//    per-gate partial. Each
 //    epilogue warp writes one FP64 partial per (tile, gate): row
 //    2 * (observable tile) + (its column half).
 // One MMA-issuing thread is the critical path here: its per-stage work is
@@ -1074,11 +1074,10 @@ constexpr int GW0 = 3;           // first producer warp
 constexpr int GE0 = GW0 + GPROD; // first epilogue warp
 constexpr int kGThreads = (GE0 + GEPI) * 32;
 // Accumulation chunks: a tile's K loop is cut into the fewest chunks of at
-// most kGChunkMax stages (5120 samples), of equal length up to one stage. Each
-// chunk boundary stalls the MMAs while the epilogue reads the accumulator, so
-// fewer, longer chunks are faster; 5120 samples keep the tensor core's
-// truncating FP32 accumulation well inside the gradient tolerance.
-constexpr int kGChunkMax = 5120 / GKS;
+// most grad_chunk_samples() samples (default 10240), of equal length up to
+// one stage. Each chunk boundary stalls the MMAs while the epilogue reads the
+// accumulator, so fewer, longer chunks are faster; the chunk bounds the
+// error of the tensor core's truncating FP32 accumulation.
 constexpr uint32_t kGAcol = GN;      // first A column
 
 struct GCfg {
@@ -1559,6 +1558,46 @@ bool split_tail() {
     return v == 1;
 }
 
+// Observable blocks per tile group of the pair gradient (IQP_GRAD_GROUP,
+// 1..64; default 4). Each block's W panel (256 observables x s samples, hi
+// and lo) is read by every gate block of its group; the group's panels must
+// stay in L2 while the group sweeps the gate blocks, or W is read from DRAM
+// once per round of tiles.
+int64_t grad_group() {
+    static int64_t g = -1;
+    if (g < 0) {
+        const char *e = std::getenv("IQP_GRAD_GROUP");
+        const long v = e ? std::atol(e) : 4;
+        g = (v >= 1 && v <= 64) ? v : 4;
+    }
+    return g;
+}
+
+// Accumulation chunk lengths: gates per chunk of the phase kernels
+// (IQP_PHASE_CHUNK, a multiple of 256 from 256 to 65536; default 8192) and
+// the longest chunk of the pair gradient in samples (IQP_GRAD_CHUNK, a
+// multiple of 128 from 128 to 65536; default 10240). A chunk boundary stalls
+// the MMAs while the accumulator is read; a longer chunk lets the tensor
+// core's truncating FP32 accumulation drift further. On 10^4 x 10^4 x 10^5
+// with theta ~ U(-0.05, 0.05) the gradient's relative error is 1.9e-5 at 4096
+// gates, 2.7e-5 at 8192 and 5.3e-5 at 16384; the gradient chunk moves it by
+// less than 4e-6 between 2560 and 10240 samples.
+int64_t env_multiple(const char *name, int64_t unit, int64_t dflt) {
+    const char *e = std::getenv(name);
+    const long v = e ? std::atol(e) : dflt;
+    return (v >= unit && v <= 65536 && v % unit == 0) ? v : dflt;
+}
+int64_t phase_chunk_gates() {
+    static int64_t g = -1;
+    if (g < 0) g = env_multiple("IQP_PHASE_CHUNK", 256, 8192);
+    return g;
+}
+int64_t grad_chunk_samples() {
+    static int64_t g = -1;
+    if (g < 0) g = env_multiple("IQP_GRAD_CHUNK", 128, 10240);
+    return g;
+}
+
 // Phase kernels of CTA pairs with the A operand in TMEM (default) or in
 // shared memory (IQP_PHASE_TMEM=0).
 bool phase_tmem() {
@@ -1641,7 +1680,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.s = p.s;
     a.m = p.m;
     a.nks = cdiv(p.m, KS);
-    a.chunk = 64;  // 4096 gates per accumulation chunk
+    a.chunk = phase_chunk_gates() / KS;  // operand stages per accumulation chunk
     a.tiles_m = cdiv(p.l, TM * cg);
     a.tiles_n = cdiv(p.s, TN);
     a.group_m = tile_group();
@@ -1720,10 +1759,11 @@ cudaError_t launch_grad_pair(const Plan &p, void *ws, cudaStream_t st, iqp_statu
     a.s = p.s;
     a.m = p.m;
     a.nks = cdiv(p.s, GKS);
-    a.chunk = cdiv(a.nks, cdiv(a.nks, kGChunkMax));  // fewest chunks, balanced
+    const int64_t cmax = grad_chunk_samples() / GKS;
+    a.chunk = cdiv(a.nks, cdiv(a.nks, cmax));  // fewest chunks, balanced
     a.tiles_g = cdiv(p.m, 2 * TM);
     a.tiles_o = cdiv(p.l, GN);
-    a.group_o = tile_group();
+    a.group_o = grad_group();
     a.pat32 = at<uint32_t>(ws, p.off_pat);
     a.ldlt32 = 2 * p.ldlt;
     a.gpart = at<double>(ws, p.off_gpart);
