@@ -258,22 +258,41 @@ __global__ void __launch_bounds__(256) k_grad_simt(const float *__restrict__ W, 
 
 // Merge the (S, M2) partials of each observable in fixed order (Chan et al.):
 // mean = S/s, M2 = sum_k [M2_k + n_k (S_k/n_k - mean)^2].
-__global__ void k_finalize(const double2 *__restrict__ part, int64_t nparts, int64_t pw, int64_t l, int64_t s,
-                           double *__restrict__ expval, double *__restrict__ std_err, double *__restrict__ S1,
-                           double *__restrict__ S2) {
-    const int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (a >= l) return;
+// Per observable a: the mean of cos Phi over the s samples and its standard
+// error from the (sum, M2) partials of pw samples each (Chan's combination),
+// plus the sums S1 = sum cos, S2 = sum cos^2 for the MMD loss. One warp per
+// observable: lane q takes partials q, q + 32, ... (coalesced 16-byte loads)
+// and a fixed xor-shuffle tree combines the lanes, so the result does not
+// depend on the launch.
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, w);
+    return v;
+}
+
+__global__ void __launch_bounds__(256) k_finalize(const double2 *__restrict__ part, int64_t nparts, int64_t pw,
+                                                  int64_t l, int64_t s, double *__restrict__ expval,
+                                                  double *__restrict__ std_err, double *__restrict__ S1,
+                                                  double *__restrict__ S2) {
+    const int lane = threadIdx.x & 31;
+    const int64_t a = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (a >= l) return;  // whole warps
     if (!IQP_IN(a * nparts + nparts - 1, l * nparts, 30)) return;
     const double2 *p = part + a * nparts;
     double S = 0.0;
-    for (int64_t k = 0; k < nparts; ++k) S += p[k].x;
+    for (int64_t k = lane; k < nparts; k += 32) S += p[k].x;
+    S = warp_sum_f64(S);
     const double mean = S / (double)s;
+    const double inv_pw = 1.0 / (double)pw;
     double M2 = 0.0;
-    for (int64_t k = 0; k < nparts; ++k) {
+    for (int64_t k = lane; k < nparts; k += 32) {
         const int64_t nk = (s - k * pw) < pw ? (s - k * pw) : pw;
-        const double d = p[k].x / (double)nk - mean;
-        M2 += p[k].y + (double)nk * d * d;
+        const double2 v = p[k];
+        const double d = (nk == pw ? v.x * inv_pw : v.x / (double)nk) - mean;
+        M2 += v.y + (double)nk * d * d;
     }
+    M2 = warp_sum_f64(M2);
+    if (lane != 0) return;
     if (expval) expval[a] = mean;
     if (std_err) std_err[a] = sqrt(M2 / (double)s) / sqrt((double)s);
     if (S1) S1[a] = S;
@@ -398,7 +417,7 @@ cudaError_t launch_grad_simt(const float *W, int64_t ldw, const uint64_t *PZ, co
 cudaError_t launch_finalize(const double2 *part, int64_t nparts, int64_t pw, int64_t l, int64_t s, double *expval,
                             double *std_err, double *S1, double *S2, cudaStream_t st) {
     LaunchScope ls(IQP_KERNEL_FINALIZE, st);
-    k_finalize<<<(unsigned)cdiv(l, 256), 256, 0, st>>>(part, nparts, pw, l, s, expval, std_err, S1, S2);
+    k_finalize<<<(unsigned)cdiv(l, 8), 256, 0, st>>>(part, nparts, pw, l, s, expval, std_err, S1, S2);
     return cudaGetLastError();
 }
 
