@@ -110,6 +110,67 @@ __global__ void __launch_bounds__(256) k_parity(int nw32, const uint32_t *__rest
 // Batched over blockIdx.y: matrix b starts at in + b in_bs32 / out + b out_bs32.
 constexpr int kTT = 512;            // tile edge in bits
 constexpr int kTW = kTT / 32;       // 32-bit words per tile row
+constexpr int kTPairs = kTW * (kTW + 1) / 2;  // 32 x 32 block pairs (rb <= cb) of a tile
+
+// Block pairs of a tile in the order rb = 0, 1, ..., cb = rb .. kTW - 1.
+struct TilePairs {
+    uint8_t rb[kTPairs], cb[kTPairs];
+};
+constexpr TilePairs make_tile_pairs() {
+    TilePairs t{};
+    int k = 0;
+    for (int r = 0; r < kTW; ++r)
+        for (int c = r; c < kTW; ++c) {
+            t.rb[k] = (uint8_t)r;
+            t.cb[k] = (uint8_t)c;
+            ++k;
+        }
+    return t;
+}
+__constant__ TilePairs kTilePairs = make_tile_pairs();
+
+// Transpose, in place, the 512 x 512-bit tile tin (row r = 16 words, bit b of
+// word w = column 32 w + b) as 32 x 32 blocks (row block rb, word column cb):
+// each warp takes pairs (rb, cb), (cb, rb) with rb <= cb, transposes both in
+// registers and swaps them, so afterwards tin[32 cb + lane][rb] holds row
+// 32 cb + lane of the transpose, word rb. A lane stores only to the two words
+// it loaded. The 32 x 32 transpose (one row word per lane) takes five
+// butterfly rounds j = 16, 8, 4, 2, 1: lane L pairs with lane L ^ j and,
+// within every 2j-bit group of its word, keeps its own half (the low half if
+// bit j of L is clear: mask m_j; else the high half) and takes the other half
+// from the partner's word moved by j bits toward it. The move is a rotation
+// by j (lane bit clear: left; set: right), since the bits it wraps around land
+// in the half that is kept, so a round is one shuffle, one funnel shift and
+// one bitwise select.
+__device__ __forceinline__ void transpose_tile_smem(uint32_t (*tin)[kTW + 1], int warp, int lane) {
+    uint32_t keep[5], rot[5];
+#pragma unroll
+    for (int r = 0; r < 5; ++r) {
+        const int j = 16 >> r;
+        const uint32_t m = r == 0 ? 0x0000FFFFu : r == 1 ? 0x00FF00FFu : r == 2 ? 0x0F0F0F0Fu
+                                                  : r == 3 ? 0x33333333u : 0x55555555u;
+        const bool hi = (lane & j) != 0;
+        keep[r] = hi ? ~m : m;
+        rot[r] = hi ? (uint32_t)(32 - j) : (uint32_t)j;
+    }
+    for (int item = warp; item < kTPairs; item += kTT / 32) {
+        const int rb = kTilePairs.rb[item], cb = kTilePairs.cb[item];
+        uint32_t x1 = tin[rb * 32 + lane][cb];
+        uint32_t x2 = tin[cb * 32 + lane][rb];
+#pragma unroll
+        for (int r = 0; r < 5; ++r) {
+            const int j = 16 >> r;
+            const uint32_t y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, j);
+            const uint32_t y2 = __shfl_xor_sync(0xFFFFFFFFu, x2, j);
+            const uint32_t t1 = __funnelshift_l(y1, y1, rot[r]);
+            const uint32_t t2 = __funnelshift_l(y2, y2, rot[r]);
+            x1 = (x1 & keep[r]) | (t1 & ~keep[r]);
+            x2 = (x2 & keep[r]) | (t2 & ~keep[r]);
+        }
+        tin[cb * 32 + lane][rb] = x1;
+        if (rb != cb) tin[rb * 32 + lane][cb] = x2;
+    }
+}
 
 __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restrict__ in, int64_t in_rows,
                                                         int64_t in_cols, int64_t ld_in32,
@@ -153,34 +214,7 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
         }
     }
     __syncthreads();
-    // 32 x 32 blocks (row block rb, word column cb): each warp takes a pair
-    // (rb, cb), (cb, rb) with rb <= cb, transposes both and swaps them, so
-    // afterwards tin[32 cb + lane][rb] is output row c0 + 32 cb + lane, word
-    // r0/32 + rb. A lane stores only to the two words it loaded.
-    for (int item = warp; item < kTW * (kTW + 1) / 2; item += kTT / 32) {
-        int rb = 0, rem = item;
-        while (rem >= kTW - rb) {
-            rem -= kTW - rb;
-            ++rb;
-        }
-        const int cb = rb + rem;
-        uint32_t x1 = tin[rb * 32 + lane][cb];
-        uint32_t x2 = tin[cb * 32 + lane][rb];
-#pragma unroll
-        for (int j = 16; j >= 1; j >>= 1) {
-            const uint32_t lowm = j == 16 ? 0x0000FFFFu
-                                  : j == 8 ? 0x00FF00FFu
-                                  : j == 4 ? 0x0F0F0F0Fu
-                                  : j == 2 ? 0x33333333u
-                                           : 0x55555555u;
-            const uint32_t y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, j);
-            const uint32_t y2 = __shfl_xor_sync(0xFFFFFFFFu, x2, j);
-            x1 = (lane & j) ? ((x1 & ~lowm) | ((y1 >> j) & lowm)) : ((x1 & lowm) | ((y1 & lowm) << j));
-            x2 = (lane & j) ? ((x2 & ~lowm) | ((y2 >> j) & lowm)) : ((x2 & lowm) | ((y2 & lowm) << j));
-        }
-        tin[cb * 32 + lane][rb] = x1;
-        if (rb != cb) tin[rb * 32 + lane][cb] = x2;
-    }
+    transpose_tile_smem(tin, warp, lane);
     __syncthreads();
     const int64_t ow0 = r0 >> 5;
     const bool vout = ((ld_out32 & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & 15) == 0);
@@ -263,30 +297,7 @@ __global__ void __launch_bounds__(kTT) k_gather_transpose(const int4 *__restrict
         tin[row][q + 3] = v.w;
     }
     __syncthreads();
-    for (int item = warp; item < kTW * (kTW + 1) / 2; item += kTT / 32) {
-        int rb = 0, rem = item;
-        while (rem >= kTW - rb) {
-            rem -= kTW - rb;
-            ++rb;
-        }
-        const int cb = rb + rem;
-        uint32_t x1 = tin[rb * 32 + lane][cb];
-        uint32_t x2 = tin[cb * 32 + lane][rb];
-#pragma unroll
-        for (int jj = 16; jj >= 1; jj >>= 1) {
-            const uint32_t lowm = jj == 16 ? 0x0000FFFFu
-                                  : jj == 8 ? 0x00FF00FFu
-                                  : jj == 4 ? 0x0F0F0F0Fu
-                                  : jj == 2 ? 0x33333333u
-                                            : 0x55555555u;
-            const uint32_t y1 = __shfl_xor_sync(0xFFFFFFFFu, x1, jj);
-            const uint32_t y2 = __shfl_xor_sync(0xFFFFFFFFu, x2, jj);
-            x1 = (lane & jj) ? ((x1 & ~lowm) | ((y1 >> jj) & lowm)) : ((x1 & lowm) | ((y1 & lowm) << jj));
-            x2 = (lane & jj) ? ((x2 & ~lowm) | ((y2 >> jj) & lowm)) : ((x2 & lowm) | ((y2 & lowm) << jj));
-        }
-        tin[cb * 32 + lane][rb] = x1;
-        if (rb != cb) tin[rb * 32 + lane][cb] = x2;
-    }
+    transpose_tile_smem(tin, warp, lane);
     __syncthreads();
     const int64_t ow0 = r0 >> 5;
 #pragma unroll
