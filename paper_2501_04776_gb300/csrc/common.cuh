@@ -472,21 +472,22 @@ __device__ __forceinline__ void umma_stage4_ss(uint32_t d, uint64_t ahi, uint64_
         ::"r"(d), "l"(ahi), "l"(alo), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
-// Four K steps, A hi / A lo in TMEM (64 columns: hi at ta, lo at ta + 32), B in shared memory.
+// Four K steps, A hi / A lo in TMEM (64 columns; K step k: hi at ta + 16 k,
+// lo at ta + 16 k + 8), B in shared memory.
 __device__ __forceinline__ void umma_stage4_pair_ts(uint32_t d, uint32_t ta, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t.reg .b32 th, tl;\n\t.reg .b64 bb;\n\t"
         "setp.ne.b32 p, %4, 0;\n\tsetp.eq.b32 q, %4, %4;\n\t"
-        "add.u32 tl, %1, 32;\n\t"
+        "add.u32 tl, %1, 8;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], [tl], %2, %3, q;\n\t"
-        "add.u32 th, %1, 8;\n\tadd.u32 tl, %1, 40;\n\tadd.s64 bb, %2, 2;\n\t"
+        "add.u32 th, %1, 16;\n\tadd.u32 tl, %1, 24;\n\tadd.s64 bb, %2, 2;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], [th], bb, %3, q;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], [tl], bb, %3, q;\n\t"
-        "add.u32 th, %1, 16;\n\tadd.u32 tl, %1, 48;\n\tadd.s64 bb, %2, 4;\n\t"
+        "add.u32 th, %1, 32;\n\tadd.u32 tl, %1, 40;\n\tadd.s64 bb, %2, 4;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], [th], bb, %3, q;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], [tl], bb, %3, q;\n\t"
-        "add.u32 th, %1, 24;\n\tadd.u32 tl, %1, 56;\n\tadd.s64 bb, %2, 6;\n\t"
+        "add.u32 th, %1, 48;\n\tadd.u32 tl, %1, 56;\n\tadd.s64 bb, %2, 6;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], [th], bb, %3, q;\n\t"
         "tcgen05.mma.cta_group::2.kind::f16 [%0], [tl], bb, %3, q;\n}\n"
         ::"r"(d), "r"(ta), "l"(b), "r"(idesc), "r"(acc)

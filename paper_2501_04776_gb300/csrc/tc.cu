@@ -85,8 +85,9 @@ constexpr int kGroupLoads = kGroupCols / 32;
 constexpr uint32_t kTmemCols = 512;   // accumulator (0..255) + running sum (256..511)
 constexpr uint32_t kSumCol = 256;
 // A-in-TMEM form: columns 256..511 hold the A operand of the four operand
-// stages instead of the running sum: stage os at 256 + 64 os, A_hi in its
-// first 32 columns (64 BF16 per lane), A_lo in the next 32.
+// stages instead of the running sum: stage os at 256 + 64 os; its 16-gate
+// K step k (0..3) has A_hi at + 16 k and A_lo at + 16 k + 8 (8 columns of
+// two BF16 each), so one warp's share is 16 contiguous columns.
 constexpr uint32_t kAColBase = 256;
 constexpr uint32_t kAColStage = 64;
 constexpr int kMaxOp = 4;
@@ -162,6 +163,7 @@ struct TcArgs {
     int *skc;              // per (split tile, CTA of the pair): parts finished so far
     uint32_t *status;
     uint64_t limit_ns;
+    int serp;              // phase, whole tiles: every other round of tiles walks the gates backwards
 };
 
 struct Bars {
@@ -294,12 +296,13 @@ __device__ __forceinline__ void load_sum32(uint32_t t, bool chunked, uint32_t (&
 }
 
 // A-in-TMEM form: this warp's share of one 64-gate operand stage of A, the 16
-// gates [16 g, 16 g + 16) for the row of TMEM lane (32 quarter + lane): hi_j
-// (A_hi) and lo_j (A_lo) where bit j of `b16` (the row's parities of these
-// gates) is set, 0 elsewhere, two BF16 per 32-bit column (the lower gate in
-// the low half). chi / clo: the bits stage's hi / lo split of 2 theta; q: the
-// operand stage within the bits stage. `t` is the TMEM address of the warp's
-// first A_hi column; A_lo starts 32 columns further.
+// gates [16 g, 16 g + 16) (K step g) for the row of TMEM lane
+// (32 quarter + lane): hi_j (A_hi) and lo_j (A_lo) where bit j of `b16` (the
+// row's parities of these gates) is set, 0 elsewhere, two BF16 per 32-bit
+// column (the lower gate in the low half). chi / clo: the bits stage's hi /
+// lo split of 2 theta; q: the operand stage within the bits stage. `t` is the
+// TMEM address of the warp's 16 columns: A_hi in the first 8, A_lo in the
+// next 8, stored at once.
 __device__ __forceinline__ void expand_a_tmem(uint32_t b16, const uint8_t *chi, const uint8_t *clo, int q, int g,
                                               uint32_t t) {
     const uint32_t off = (uint32_t)q * 128u + (uint32_t)g * 32u;
@@ -308,12 +311,11 @@ __device__ __forceinline__ void expand_a_tmem(uint32_t b16, const uint8_t *chi, 
     const uint4 l0 = *reinterpret_cast<const uint4 *>(clo + off);
     const uint4 l1 = *reinterpret_cast<const uint4 *>(clo + off + 16);
     const uint4 m0 = expand_mask(b16 & 0xFFu), m1 = expand_mask((b16 >> 8) & 0xFFu);
-    const uint32_t hv[8] = {h0.x & m0.x, h0.y & m0.y, h0.z & m0.z, h0.w & m0.w,
-                            h1.x & m1.x, h1.y & m1.y, h1.z & m1.z, h1.w & m1.w};
-    const uint32_t lv[8] = {l0.x & m0.x, l0.y & m0.y, l0.z & m0.z, l0.w & m0.w,
+    const uint32_t v[16] = {h0.x & m0.x, h0.y & m0.y, h0.z & m0.z, h0.w & m0.w,
+                            h1.x & m1.x, h1.y & m1.y, h1.z & m1.z, h1.w & m1.w,
+                            l0.x & m0.x, l0.y & m0.y, l0.z & m0.z, l0.w & m0.w,
                             l1.x & m1.x, l1.y & m1.y, l1.z & m1.z, l1.w & m1.w};
-    tmem_st8(t, hv);
-    tmem_st8(t + 32u, lv);
+    tmem_st16(t, v);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
@@ -469,6 +471,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr bool ATM = TA && !GRAD && !AT && CG == 2;
     using C = Cfg<CG, ATMA, ATM>;
     constexpr int NOP = C::NOP;
+    // Serpentine gate order (phase kernels, whole tiles): the CTA groups' odd
+    // rounds of tiles walk their bits stages from the last to the first, so a
+    // round starts on the operand rows the round before it read last, which
+    // are still in L2. The sum is the same up to the order of its terms.
+    constexpr bool SERP = !GRAD && !ATMA && !SPL;
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = aligned_smem(smem_raw);
     Bars *bar = reinterpret_cast<Bars *>(smem + C::SM_BAR);
@@ -546,7 +553,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int prank = CG == 2 ? (int)crank : 0;        // rank within an MMA pair
                 const int a0 = tm * TM * CG + prank * TM;          // this CTA's first A row
                 const int b0 = tn * TN + prank * C::TNB;           // this CTA's first B row
-                for (int kb = ks0 / (KB / KS); kb < (ks1 + KB / KS - 1) / (KB / KS) && ok; ++kb, ++itb) {
+                const bool rev = SERP && args.serp != 0 && ((((u - group0) / ngroups) & 1) != 0);
+                const int kbA = ks0 / (KB / KS), kbN = (ks1 + KB / KS - 1) / (KB / KS) - kbA;
+                for (int i = 0; i < kbN && ok; ++i, ++itb) {
+                    const int kb = rev ? kbA + kbN - 1 - i : kbA + i;
                     const uint32_t bs = itb % NBITS;
                     if (!mbar_wait(&bar->bits_empty[bs], ((itb / NBITS) & 1u) ^ 1u, abort_flag, status, lim)) {
                         ok = false;
@@ -701,8 +711,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             int kc = 0;              // stage index within the current chunk
             int nchunk = 0;          // chunks of this tile already folded into the running sum
             bool fold_due = false;   // a finished chunk must be folded before the next release
+            // Stage order: bits stages forwards, or (serpentine rounds) from the
+            // last one (c0 operand stages, ks1 - 4 kbTop) down to the first;
+            // within a bits stage always q = 0, 1, ...
+            const bool rev = SERP && args.serp != 0 && ((((u - group0) / ngroups) & 1) != 0);
+            const int kbTop = (ks1 - 1) >> 2;
+            const int c0 = ks1 - 4 * kbTop;
             for (int ks = ks0; ks < ks1; ++ks) {
-                const int q = ks & 3;
+                const int idx = ks - ks0;  // position in the tile's stage sequence
+                int q;
+                bool qlast;  // the bits stage's last operand stage
+                if (!rev) {
+                    q = ks & 3;
+                    qlast = q == 3 || ks == ks1 - 1;
+                } else if (idx < c0) {
+                    q = idx;
+                    qlast = idx == c0 - 1;
+                } else {
+                    q = (idx - c0) & 3;
+                    qlast = q == 3;
+                }
                 const uint32_t bs = itb % NBITS;
                 if (q == 0 && !wait_warp(&bar->bits_full[bs], (itb / NBITS) & 1u, abort_flag, status, lim)) {
                     ok = false;
@@ -734,7 +762,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t b16 = ((q < 2 ? abits01 : abits23) >> ((q & 1) * 16)) & 0xFFFFu;
                     const uint32_t ta = tmem + ((uint32_t)(quarter * 32) << 16) + kAColBase + os * kAColStage +
-                                        (uint32_t)group * 8u;
+                                        (uint32_t)group * 16u;
                     expand_a_tmem(b16, bits + C::BT_CHI, bits + C::BT_CLO, q, group, ta);
                 }
                 expand_b<C::TNB>(bits + C::BT_B, op + C::OP_B, q, gt);
@@ -806,7 +834,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     else mbar_arrive(&bar->op_full[os]);
                 }
                 ++ito;
-                if (q == 3 || ks == ks1 - 1) {
+                if (qlast) {
                     if (lane == 0) mbar_arrive(&bar->bits_empty[bs]);
                     ++itb;
                 }
@@ -1598,6 +1626,17 @@ int64_t grad_chunk_samples() {
     return g;
 }
 
+// Serpentine gate order for the phase kernels' whole tiles (IQP_PHASE_SERP;
+// default 1; 0 = every tile walks the gates forwards).
+bool phase_serp() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("IQP_PHASE_SERP");
+        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 // Phase kernels of CTA pairs with the A operand in TMEM (default) or in
 // shared memory (IQP_PHASE_TMEM=0).
 bool phase_tmem() {
@@ -1675,7 +1714,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
         *why = IQP_ERR_UNSUPPORTED;
         return cudaErrorNotSupported;
     }
-    TcArgs a;
+    TcArgs a{};  // every field zero unless set below
     a.l = p.l;
     a.s = p.s;
     a.m = p.m;
@@ -1703,6 +1742,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.out_f64 = 0;
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
+    a.serp = phase_serp() ? 1 : 0;
     // A last round of tiles that would leave CTA groups idle is split along
     // the gates across them: the whole tiles run first (full rounds), then a
     // second launch runs the remaining tiles' parts, each a range of whole
@@ -1818,7 +1858,7 @@ cudaError_t launch_grad_tc(const Plan &p, void *ws, cudaStream_t st, iqp_status 
         *why = IQP_ERR_UNSUPPORTED;
         return cudaErrorNotSupported;
     }
-    TcArgs a;
+    TcArgs a{};  // every field zero unless set below
     a.l = p.l;
     a.s = p.s;
     a.m = p.m;
@@ -1873,7 +1913,7 @@ cudaError_t launch_tc_dense(const __nv_bfloat16 *a_hi, const __nv_bfloat16 *a_lo
         !make_map(&mb, b_bits, CU_TENSOR_MAP_DATA_TYPE_UINT64, ldb, nb, ldb * 8, 4, (uint32_t)(TN / cg),
                   CU_TENSOR_MAP_SWIZZLE_NONE))
         return cudaErrorNotSupported;
-    TcArgs a;
+    TcArgs a{};  // every field zero unless set below
     a.l = rows;
     a.s = nb;
     a.m = k;
