@@ -94,10 +94,13 @@ typedef enum {
 
 /* Bytes of device scratch `ws` needed by `op` for these sizes (N is ignored
  * except for the MMD ops). Returns 0 for invalid sizes. Host only.
- * With IQP_SPLIT_BF16 the last 20.5 MB of it (160 x 128 KiB plus 640 bytes)
- * are optional: they let a last round of phase tiles that would leave SMs
- * idle be split along the gates across them. A `ws_bytes` short of the full
- * size by at most that much runs every phase tile whole instead. */
+ * With IQP_SPLIT_BF16 its end is optional, in two parts. The last 40 MiB
+ * (160 x 256 KiB) hold the running sums of the phase kernels that take two
+ * sample tiles per tile; a `ws_bytes` short of the full size by at most that
+ * much runs one sample tile per tile instead. The 20.5 MB before them
+ * (160 x 128 KiB plus 640 bytes) let a last round of phase tiles that would
+ * leave SMs idle be split along the gates across them; a `ws_bytes` short
+ * of the full size by both parts runs every phase tile whole. */
 size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N,
                            iqp_precision prec);
 

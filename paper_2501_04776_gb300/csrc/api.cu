@@ -165,16 +165,20 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.ldphi = 0;
     p.phi_out = p.phi_in = false;
     // Last, and optional: the split-tile scratch of the tensor-core phase (a
-    // workspace that ends before it runs every phase tile whole).
-    p.off_skp = 0;
-    if (prec == IQP_SPLIT_BF16 && !bitflip && !indep)
+    // workspace that ends before it runs every phase tile whole), then the
+    // running sums of the two-sample-tile phase kernels (a workspace that
+    // ends before them runs one sample tile per tile).
+    p.off_skp = p.off_gsum = 0;
+    if (prec == IQP_SPLIT_BF16 && !bitflip && !indep) {
         p.off_skp = take((int64_t)kMaxSplitCtas * kSplitSlotFloats * 4 + (int64_t)kMaxSplitCtas * 4);
+        p.off_gsum = take((int64_t)kMaxSplitCtas * kDtSumFloats * 4);
+    }
     p.total = off;
     return p;
 }
 
-// Bytes of the workspace below which `p` cannot run (the optional split-tile
-// scratch at its end left out).
+// Bytes of the workspace below which `p` cannot run (the optional regions at
+// its end left out).
 size_t plan_min_bytes(const Plan &p) { return p.off_skp != 0 ? p.off_skp : p.total; }
 
 // The smallest workspace `op` runs with (iqp_workspace_bytes less the
@@ -296,7 +300,12 @@ iqp_status check_ws(Plan &p, void *ws, size_t ws_bytes) {
     if (ws == nullptr || !aligned(ws, 256)) return IQP_ERR_WORKSPACE;
     if (ws_bytes < p.total) {
         if (ws_bytes < plan_min_bytes(p)) return IQP_ERR_WORKSPACE;
-        p.off_skp = 0;  // no room for the split-tile scratch: phase tiles run whole
+        // no room for the two-tile running sums: one sample tile per tile
+        p.off_gsum = 0;
+        // no room for the split-tile scratch either: phase tiles run whole
+        if (p.off_skp != 0 && ws_bytes < p.off_skp + (size_t)round_up((int64_t)kMaxSplitCtas * kSplitSlotFloats * 4 +
+                                                                       (int64_t)kMaxSplitCtas * 4, 256))
+            p.off_skp = 0;
     }
     return IQP_OK;
 }

@@ -20,6 +20,15 @@
 //   mode 2: both from one pass (the loss coefficients known in advance).
 // Otherwise Phi itself is never written.
 //
+// Two sample tiles per tile (TA = 3; the full rounds of tiles of CTA
+// pairs): a pair computes 256 observables x 512 samples against each A stage,
+// in two M256 x N256 accumulators that fill TMEM (columns 0..255, 256..511).
+// A_hi / A_lo then live in shared memory beside the two B operands, a stage
+// takes sixteen MMAs, and the A expansion per flop halves. The running sums
+// of the accumulation chunks go to a per-CTA buffer in global memory (it
+// stays in L2). The double tiles of a last, partial round run as single
+// tiles (TcArgs::dtmap), split along the gates as below.
+//
 // Dense form (mode 3, A by TMA): out = (A_hi + A_lo) (1 - 2 B_bits)^T for a
 // dense split-BF16 matrix A brought in by TMA and a +-1 operand expanded from
 // bits as above, the FP32 accumulator stored as is (FP32 or FP64). The
@@ -43,7 +52,8 @@
 // tile therefore accumulates in chunks of `chunk` K-stages: a chunk starts a
 // fresh accumulator (TMEM columns 0..255) and, when it completes, the
 // producer warps add it into an FP32 running sum with round-to-nearest adds
-// (TMEM columns 256..511, or shared memory when A occupies those columns).
+// (TMEM columns 256..511, or shared memory when A occupies those columns, or
+// global memory in the two-sample-tile form).
 // The epilogue reads accumulator + running sum. The pair gradient reduces
 // every chunk into its FP64 per-gate partials instead.
 //
@@ -97,16 +107,22 @@ constexpr int kWPrefetch = 8;  // gradient: W tiles prefetched into L2 this many
 // operand (hi / lo) lives in TMEM, so an operand stage in shared memory holds
 // only B, and the running sum of the accumulation chunks moves from TMEM to
 // shared memory (TM x TN FP32, as float4 groups of 4 columns, row-minor).
-template <int CG, bool ATMA, bool ATM = false>
+// DT (two sample tiles per tile): an operand stage holds A_hi, A_lo and the
+// B operands of both sample tiles, the two accumulators fill TMEM, and the
+// running sums live in global memory.
+template <int CG, bool ATMA, bool ATM = false, bool DT = false>
 struct Cfg {
-    static constexpr int TNB = TN / CG;      // B rows this CTA holds
-    static constexpr int NOP = (CG == 2 || ATM) ? 4 : (ATMA ? 3 : 2);  // operand stages
-    // Operand stage: A_hi (128 x 128 B), A_lo, B (TNB x 128 B); ATM: B only.
+    static constexpr int TNB = TN / CG;      // B rows this CTA holds (per sample tile)
+    static constexpr int NOP = DT ? 3 : (CG == 2 || ATM) ? 4 : (ATMA ? 3 : 2);  // operand stages
+    // Operand stage: A_hi (128 x 128 B), A_lo, B (TNB x 128 B) [DT: then the
+    // second sample tile's B]; ATM: B only.
     static constexpr uint32_t OP_A_HI = 0, OP_A_LO = 16384, OP_B = ATM ? 0 : 32768;
-    static constexpr uint32_t OP_BYTES = ATM ? TNB * 128 : 32768 + TNB * 128;
-    // Bits stage: A bits (128 rows x 32 B), B bits (TNB rows x 32 B), c_hi, c_lo.
-    static constexpr uint32_t BT_A = 0, BT_B = 4096;
-    static constexpr uint32_t BT_CHI = BT_B + TNB * 32, BT_CLO = BT_CHI + 512;
+    static constexpr uint32_t OP_B1 = OP_B + TNB * 128;
+    static constexpr uint32_t OP_BYTES = ATM ? TNB * 128 : 32768 + (DT ? 2 : 1) * TNB * 128;
+    // Bits stage: A bits (128 rows x 32 B), B bits (TNB rows x 32 B) [DT: then
+    // the second sample tile's], c_hi, c_lo.
+    static constexpr uint32_t BT_A = 0, BT_B = 4096, BT_B1 = BT_B + TNB * 32;
+    static constexpr uint32_t BT_CHI = BT_B + (DT ? 2 : 1) * TNB * 32, BT_CLO = BT_CHI + 512;
     static constexpr uint32_t BT_BYTES = BT_CLO + 512;
     static constexpr uint32_t SM_OP = 0;
     static constexpr uint32_t SM_BITS = SM_OP + NOP * OP_BYTES;
@@ -134,6 +150,9 @@ __device__ __forceinline__ void tile_coords(int64_t t, int64_t tiles_m, int64_t 
     tm = g * gm + r % rows;
     tc = r / rows;
 }
+
+struct TcArgs;
+__device__ __forceinline__ void tile_rc(int64_t t, const TcArgs &a, int64_t &tm, int64_t &tc);
 
 struct TcArgs {
     int64_t l, s, m;
@@ -164,7 +183,25 @@ struct TcArgs {
     uint32_t *status;
     uint64_t limit_ns;
     int serp;              // phase, whole tiles: every other round of tiles walks the gates backwards
+    // Two-sample-tile phase kernels: per CTA, the running sums of both
+    // accumulators (2 x TM x TN FP32 as float4 groups of 4 columns, row-minor).
+    float4 *gsum;
+    // Single tiles taken from double tiles (the last round of a two-tile
+    // phase): tile t is half t % 2 of double tile dbase + t / 2 of a
+    // tiles_m x tiles_n2 walk.
+    int dtmap;
+    int64_t dbase, tiles_n2;
 };
+
+__device__ __forceinline__ void tile_rc(int64_t t, const TcArgs &a, int64_t &tm, int64_t &tc) {
+    if (a.dtmap) {
+        int64_t tc2;
+        tile_coords(a.dbase + t / 2, a.tiles_m, a.tiles_n2, a.group_m, tm, tc2);
+        tc = 2 * tc2 + (t & 1);
+        return;
+    }
+    tile_coords(t, a.tiles_m, a.tiles_n, a.group_m, tm, tc);
+}
 
 struct Bars {
     uint64_t bits_full[NBITS], bits_empty[NBITS], op_full[kMaxOp], op_empty[kMaxOp], w_full[kMaxOp],
@@ -462,14 +499,19 @@ __device__ __noinline__ void split_sum(const float *src0, int64_t part_stride, i
 // the gradient's W; for MODE 3, a dense split-BF16 matrix); AT = false: the
 // producer warps expand it from P_A bits and the hi/lo split of 2 theta.
 // CG = 1: one CTA per tile of 128 rows; CG = 2: a CTA pair per tile of 256 rows.
-template <bool GRAD, int MODE, int CG, bool AT, bool SPL, bool TA>
+// TA (phase modes of CTA pairs): 0 = A in shared memory; 1 = A in TMEM; 3 =
+// two sample tiles (2 x 256 samples) per tile against each A stage.
+template <bool GRAD, int MODE, int CG, bool AT, bool SPL, int TA>
 __global__ void __launch_bounds__(kThreads, 1)
     k_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmA2,
          const __grid_constant__ CUtensorMap tmB, const TcArgs args) {
     constexpr bool ATMA = GRAD || AT;  // A operand by TMA
     // A operand in TMEM, written by the producer warps (phase modes, CTA pairs)
-    constexpr bool ATM = TA && !GRAD && !AT && CG == 2;
-    using C = Cfg<CG, ATMA, ATM>;
+    constexpr bool ATM = TA == 1 && !GRAD && !AT && CG == 2;
+    // Two sample tiles per tile (phase modes, CTA pairs, whole tiles): A in
+    // shared memory, two accumulators, running sums in global memory
+    constexpr bool DT = TA == 3 && !GRAD && !AT && CG == 2 && !SPL;
+    using C = Cfg<CG, ATMA, ATM, DT>;
     constexpr int NOP = C::NOP;
     // Serpentine gate order (phase kernels, whole tiles): the CTA groups' odd
     // rounds of tiles walk their bits stages from the last to the first, so a
@@ -528,7 +570,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = bar->tmem_slot;
 
-    const int64_t tiles_nc = args.tiles_n;
     const int64_t nunits = args.nunits;
     const int nks = (int)args.nks;     // host guarantees nks < 2^31
     const int chunk = (int)args.chunk;
@@ -547,12 +588,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int ks0, ks1;
                 unit_of<SPL>(u, args, nks, t, ks0, ks1, uv);
                 int64_t tm64, tc64;
-                tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm64, tc64);
+                tile_rc(t, args, tm64, tc64);
                 const int tm = (int)tm64;
                 const int tn = (int)tc64;
                 const int prank = CG == 2 ? (int)crank : 0;        // rank within an MMA pair
                 const int a0 = tm * TM * CG + prank * TM;          // this CTA's first A row
-                const int b0 = tn * TN + prank * C::TNB;           // this CTA's first B row
+                const int b0 = tn * TN * (DT ? 2 : 1) + prank * C::TNB;  // this CTA's first B row
                 const bool rev = SERP && args.serp != 0 && ((((u - group0) / ngroups) & 1) != 0);
                 const int kbA = ks0 / (KB / KS), kbN = (ks1 + KB / KS - 1) / (KB / KS) - kbA;
                 for (int i = 0; i < kbN && ok; ++i, ++itb) {
@@ -567,6 +608,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (ATMA) {
                         mbar_arrive_expect_tx(&bar->bits_full[bs], C::TNB * 32);
                         tma_load_2d(bits + C::BT_B, &tmB, &bar->bits_full[bs], x, b0);
+                    } else if (DT) {
+                        mbar_arrive_expect_tx(&bar->bits_full[bs], TM * 32 + 2 * C::TNB * 32 + 1024);
+                        tma_load_2d(bits + C::BT_A, &tmA, &bar->bits_full[bs], x, a0);
+                        tma_load_2d(bits + C::BT_B, &tmB, &bar->bits_full[bs], x, b0);
+                        tma_load_2d(bits + C::BT_B1, &tmB, &bar->bits_full[bs], x, b0 + TN);
+                        const bool cin = IQP_IN((int64_t)kb * KB + KB - 1, args.mpad, 54);
+                        bulk_load(bits + C::BT_CHI, args.chi + (cin ? kb * KB : 0), 512, &bar->bits_full[bs]);
+                        bulk_load(bits + C::BT_CLO, args.clo + (cin ? kb * KB : 0), 512, &bar->bits_full[bs]);
                     } else {
                         mbar_arrive_expect_tx(&bar->bits_full[bs], TM * 32 + C::TNB * 32 + 1024);
                         tma_load_2d(bits + C::BT_A, &tmA, &bar->bits_full[bs], x, a0);
@@ -620,6 +669,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // operand descriptors of stage 0 (K step 0)
             const uint32_t sb = smem_u32(smem + C::SM_OP);
             const uint64_t d_b0 = sdesc_k128(sb + C::OP_B);
+            [[maybe_unused]] const uint64_t d_b1 = sdesc_k128(sb + C::OP_B1);
             const uint64_t d_hi0 = sdesc_k128(sb + C::OP_A_HI), d_lo0 = sdesc_k128(sb + C::OP_A_LO);
             for (int64_t u = group0; u < nunits && ok; u += ngroups) {
                 int64_t t, uv;
@@ -648,7 +698,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // (one function may not mix cta_group::1 and ::2 forms)
                     if constexpr (ATM)
                         umma_stage4_pair_ts(tmem, tmem + kAColBase + os * kAColStage, d_b0 + so, C::IDESC, acc);
-                    else if constexpr (CG == 2)
+                    else if constexpr (DT) {
+                        umma_stage4_pair_ss(tmem, d_hi0 + so, d_lo0 + so, d_b0 + so, C::IDESC, acc);
+                        umma_stage4_pair_ss(tmem + (uint32_t)TN, d_hi0 + so, d_lo0 + so, d_b1 + so, C::IDESC, acc);
+                    } else if constexpr (CG == 2)
                         umma_stage4_pair_ss(tmem, d_hi0 + so, d_lo0 + so, d_b0 + so, C::IDESC, acc);
                     else
                         umma_stage4_ss(tmem, d_hi0 + so, d_lo0 + so, d_b0 + so, C::IDESC, acc);
@@ -694,6 +747,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int group = (warp - 2) >> 2; // accumulator column group of the epilogue
         uint32_t itb = 0, ito = 0, tcount = 0, nacc = 0;
         const int rl = quarter * 32 + lane;  // accumulator row (TMEM lane) of this thread
+        // DT: this CTA's running sums (both accumulators) in global memory
+        // (the host launches at most kMaxSplitCtas CTAs of this form)
+        [[maybe_unused]] float4 *gsum_cta =
+            DT && IQP_IN(blockIdx.x, kMaxSplitCtas, 59) ? args.gsum + (int64_t)blockIdx.x * (kDtSumFloats / 4) : nullptr;
         // ATM: this thread's A parity bits of the current bits stage, 16 per
         // operand stage (see expand_a_tmem), packed two stages per word
         uint32_t abits01 = 0, abits23 = 0;
@@ -704,7 +761,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             {
                 int64_t t, uv0;
                 unit_of<SPL>(u, args, nks, t, ks0, ks1, uv0);
-                tile_coords(t, args.tiles_m, tiles_nc, args.group_m, tm, tc);
+                tile_rc(t, args, tm, tc);
             }
             const int64_t tn = tc;
             const int64_t arow0 = tm * TM * CG + (CG == 2 ? (int64_t)crank * TM : 0);  // first observable here
@@ -766,6 +823,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     expand_a_tmem(b16, bits + C::BT_CHI, bits + C::BT_CLO, q, group, ta);
                 }
                 expand_b<C::TNB>(bits + C::BT_B, op + C::OP_B, q, gt);
+                if constexpr (DT) expand_b<C::TNB>(bits + C::BT_B1, op + C::OP_B1, q, gt);
                 if (!ATMA && !ATM)
                     expand_a(bits + C::BT_A, bits + C::BT_CHI, bits + C::BT_CLO, op + C::OP_A_HI, op + C::OP_A_LO, q,
                              gt);
@@ -794,12 +852,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tc_fence_after();
                     const uint32_t tb = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(group * kGroupCols);
 #pragma unroll 1
-                    for (int c = 0; c < kGroupLoads; ++c) {
+                    for (int c = 0; c < (DT ? 2 : 1) * kGroupLoads; ++c) {
                         uint32_t r[32], acc[32];
-                        tmem_ld32(tb + c * 32, r);
-                        if (ATM) {
-                            // running sum in shared memory (this thread's row only)
-                            float4 *sp = sum4 + ((group * kGroupCols + c * 32) >> 2) * TM + rl;
+                        const int hb = DT && c >= kGroupLoads ? 1 : 0;  // DT: accumulator of the second sample tile
+                        const int cc = c - hb * kGroupLoads;
+                        tmem_ld32(tb + (uint32_t)(hb * TN + cc * 32), r);
+                        if (ATM || DT) {
+                            // running sum in shared memory (ATM) or global memory
+                            // (DT), this thread's row only
+                            float4 *sp = ATM ? sum4 + ((group * kGroupCols + cc * 32) >> 2) * TM + rl
+                                             : gsum_cta + ((hb * TN + group * kGroupCols + cc * 32) >> 2) * TM + rl;
 #pragma unroll
                             for (int e4 = 0; e4 < 8; ++e4) {
                                 float4 v = make_float4(__uint_as_float(r[4 * e4]), __uint_as_float(r[4 * e4 + 1]),
@@ -855,11 +917,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int64_t row = arow0 + quarter * 32 + lane;  // observable a
             const uint32_t tbase = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(group * kGroupCols);
             bool chunked = nchunk > 0;
-            // ATM: where the running sum of this thread's row keeps the
-            // group's 32 columns c * 32.. (shared memory); else in TMEM
-            auto ssum = [&](int c) -> const float4 * {
-                return ATM ? sum4 + ((group * kGroupCols + c * 32) >> 2) * TM + rl : nullptr;
-            };
+
             if (!GRAD && MODE != 3 && SPL) {
                 const int64_t uv = u;  // this part's slot
                 // A part of a split tile: store this part's accumulator; the
@@ -905,151 +963,165 @@ __global__ void __launch_bounds__(kThreads, 1)
                 chunked = false;  // the sum of the parts is in the accumulator columns
             }
             // Phi (or Q) for 32 columns: last chunk's accumulator + running sum.
-            if (!GRAD && MODE == 0) {
-                const int64_t c0 = tn * TN + group * kGroupCols;  // first sample of this group
-                int64_t nvalid = args.s - c0;
-                nvalid = nvalid < 0 ? 0 : (nvalid > kGroupCols ? kGroupCols : nvalid);
-                float S = 0.f, M2 = 0.f;
-                uint32_t r[32];
+            // DT: the two sample tiles' accumulators in turn.
+            for (int hb = 0; hb < (DT ? 2 : 1) && ok; ++hb) {
+                const int64_t tn_h = DT ? 2 * tn + hb : tn;
+                const uint32_t tb_h = tbase + (uint32_t)(hb * TN);
+                // where the running sum of this thread's row keeps the group's
+                // 32 columns c * 32..: shared memory (ATM), global memory (DT),
+                // else TMEM
+                auto ssum = [&](int c) -> const float4 * {
+                    return ATM  ? sum4 + ((group * kGroupCols + c * 32) >> 2) * TM + rl
+                           : DT ? gsum_cta + ((hb * TN + group * kGroupCols + c * 32) >> 2) * TM + rl
+                                : nullptr;
+                };
+                if (!GRAD && MODE == 0) {
+                    const int64_t c0 = tn_h * TN + group * kGroupCols;  // first sample of this group
+                    int64_t nvalid = args.s - c0;
+                    nvalid = nvalid < 0 ? 0 : (nvalid > kGroupCols ? kGroupCols : nvalid);
+                    float S = 0.f, M2 = 0.f;
+                    uint32_t r[32];
 #pragma unroll 1
-                for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
+                    for (int c = 0; c < kGroupLoads; ++c) {
+                        load_sum32(tb_h + c * 32, chunked, r, ssum(c));
 #pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
-                }
-                const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
+                        for (int e = 0; e < 32; ++e)
+                            if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
+                    }
+                    const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
 #pragma unroll 1
-                for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
+                    for (int c = 0; c < kGroupLoads; ++c) {
+                        load_sum32(tb_h + c * 32, chunked, r, ssum(c));
 #pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        if (c * 32 + e < nvalid) {
-                            const float d = cosf(__uint_as_float(r[e])) - mean;
-                            M2 = fmaf(d, d, M2);
+                        for (int e = 0; e < 32; ++e)
+                            if (c * 32 + e < nvalid) {
+                                const float d = cosf(__uint_as_float(r[e])) - mean;
+                                M2 = fmaf(d, d, M2);
+                            }
+                    }
+                    // Phi itself, when a gradient pass follows (W from it instead
+                    // of a second contraction).
+                    if (args.out != nullptr) {  // uniform: every lane takes the TMEM loads
+#pragma unroll 1
+                        for (int c = 0; c * 32 < nvalid; ++c) {
+                            load_sum32(tb_h + c * 32, chunked, r, ssum(c));
+                            if (row < args.l) store_out32(args, row, c0 + c * 32, r);
                         }
-                }
-                // Phi itself, when a gradient pass follows (W from it instead
-                // of a second contraction).
-                if (args.out != nullptr) {  // uniform: every lane takes the TMEM loads
-#pragma unroll 1
-                    for (int c = 0; c * 32 < nvalid; ++c) {
-                        load_sum32(tbase + c * 32, chunked, r, ssum(c));
-                        if (row < args.l) store_out32(args, row, c0 + c * 32, r);
                     }
-                }
-                if (row < args.l && nvalid > 0 && IQP_IN(row * args.nparts + c0 / kGroupCols, args.l * args.nparts, 50))
-                    args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
-            } else if (!GRAD && MODE == 2) {
-                // Both: the statistics of MODE 0 and W of MODE 1 from one
-                // pass over Phi (the loss's alpha, beta known in advance).
-                const int64_t c0 = tn * TN + group * kGroupCols;
-                int64_t nvalid = args.s - c0;
-                nvalid = nvalid < 0 ? 0 : (nvalid > kGroupCols ? kGroupCols : nvalid);
-                const bool rv = row < args.l;
-                const float al = rv && IQP_IN(row, args.l, 55) ? (float)args.alpha[row] : 0.f;
-                const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
-                float S = 0.f, M2 = 0.f;
-                uint32_t r[32];
+                    if (row < args.l && nvalid > 0 && IQP_IN(row * args.nparts + c0 / kGroupCols, args.l * args.nparts, 50))
+                        args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
+                } else if (!GRAD && MODE == 2) {
+                    // Both: the statistics of MODE 0 and W of MODE 1 from one
+                    // pass over Phi (the loss's alpha, beta known in advance).
+                    const int64_t c0 = tn_h * TN + group * kGroupCols;
+                    int64_t nvalid = args.s - c0;
+                    nvalid = nvalid < 0 ? 0 : (nvalid > kGroupCols ? kGroupCols : nvalid);
+                    const bool rv = row < args.l;
+                    const float al = rv && IQP_IN(row, args.l, 55) ? (float)args.alpha[row] : 0.f;
+                    const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
+                    float S = 0.f, M2 = 0.f;
+                    uint32_t r[32];
 #pragma unroll 1
-                for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
+                    for (int c = 0; c < kGroupLoads; ++c) {
+                        load_sum32(tb_h + c * 32, chunked, r, ssum(c));
 #pragma unroll
-                    for (int e = 0; e < 32; ++e)
-                        if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
-                }
-                const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
-#pragma unroll 1
-                for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
-                    const int64_t i0 = c0 + c * 32;
-                    uint32_t ph[16], pl[16];
-#pragma unroll
-                    for (int e = 0; e < 32; e += 2) {
-                        float s0, k0, s1, k1;
-                        sincosf(__uint_as_float(r[e]), &s0, &k0);
-                        sincosf(__uint_as_float(r[e + 1]), &s1, &k1);
-                        const float d0 = k0 - mean, d1 = k1 - mean;
-                        if (c * 32 + e < nvalid) M2 = fmaf(d0, d0, M2);
-                        if (c * 32 + e + 1 < nvalid) M2 = fmaf(d1, d1, M2);
-                        const float w0 = s0 * (al + be * k0), w1 = s1 * (al + be * k1);
-                        const float h0 = __bfloat162float(__float2bfloat16_rn(w0));
-                        const float h1 = __bfloat162float(__float2bfloat16_rn(w1));
-                        ph[e / 2] = pack_bf16x2(h0, h1);
-                        pl[e / 2] = pack_bf16x2(w0 - h0, w1 - h1);
+                        for (int e = 0; e < 32; ++e)
+                            if (c * 32 + e < nvalid) S += cosf(__uint_as_float(r[e]));
                     }
-                    if (rv && i0 < args.s) store_w32(args, row, i0, ph, pl);
-                }
-                if (rv && nvalid > 0 && IQP_IN(row * args.nparts + c0 / kGroupCols, args.l * args.nparts, 51))
-                    args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
-            } else if (!GRAD && MODE == 3) {
-                const int64_t c0 = tn * TN + group * kGroupCols;
-                uint32_t r[32];
+                    const float mean = nvalid > 0 ? S / (float)nvalid : 0.f;
 #pragma unroll 1
-                for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
-                    if (row < args.l && c0 + c * 32 < args.s) store_out32(args, row, c0 + c * 32, r);
-                }
-            } else if (!GRAD) {
-                const int64_t c0 = tn * TN + group * kGroupCols;
-                const bool rv = row < args.l;
-                const float al = rv && IQP_IN(row, args.l, 55) ? (float)args.alpha[row] : 0.f;
-                const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
-                uint32_t r[32];
-#pragma unroll 1
-                for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
-                    const int64_t i0 = c0 + c * 32;
-                    uint32_t ph[16], pl[16];
+                    for (int c = 0; c < kGroupLoads; ++c) {
+                        load_sum32(tb_h + c * 32, chunked, r, ssum(c));
+                        const int64_t i0 = c0 + c * 32;
+                        uint32_t ph[16], pl[16];
 #pragma unroll
-                    for (int e = 0; e < 32; e += 2) {
-                        float s0, k0, s1, k1;
-                        sincosf(__uint_as_float(r[e]), &s0, &k0);
-                        sincosf(__uint_as_float(r[e + 1]), &s1, &k1);
-                        const float w0 = s0 * (al + be * k0), w1 = s1 * (al + be * k1);
-                        const float h0 = __bfloat162float(__float2bfloat16_rn(w0));
-                        const float h1 = __bfloat162float(__float2bfloat16_rn(w1));
-                        ph[e / 2] = pack_bf16x2(h0, h1);
-                        pl[e / 2] = pack_bf16x2(w0 - h0, w1 - h1);
+                        for (int e = 0; e < 32; e += 2) {
+                            float s0, k0, s1, k1;
+                            sincosf(__uint_as_float(r[e]), &s0, &k0);
+                            sincosf(__uint_as_float(r[e + 1]), &s1, &k1);
+                            const float d0 = k0 - mean, d1 = k1 - mean;
+                            if (c * 32 + e < nvalid) M2 = fmaf(d0, d0, M2);
+                            if (c * 32 + e + 1 < nvalid) M2 = fmaf(d1, d1, M2);
+                            const float w0 = s0 * (al + be * k0), w1 = s1 * (al + be * k1);
+                            const float h0 = __bfloat162float(__float2bfloat16_rn(w0));
+                            const float h1 = __bfloat162float(__float2bfloat16_rn(w1));
+                            ph[e / 2] = pack_bf16x2(h0, h1);
+                            pl[e / 2] = pack_bf16x2(w0 - h0, w1 - h1);
+                        }
+                        if (rv && i0 < args.s) store_w32(args, row, i0, ph, pl);
                     }
-                    if (rv && i0 < args.s) store_w32(args, row, i0, ph, pl);
-                }
-            } else {
-                // Gradient epilogue: mask by 2 P_A[a][j], reduce over observables.
-                const bool rv = row < args.l;
-                uint32_t r[32];
+                    if (rv && nvalid > 0 && IQP_IN(row * args.nparts + c0 / kGroupCols, args.l * args.nparts, 51))
+                        args.part[row * args.nparts + (c0 / kGroupCols)] = make_double2((double)S, (double)M2);
+                } else if (!GRAD && MODE == 3) {
+                    const int64_t c0 = tn_h * TN + group * kGroupCols;
+                    uint32_t r[32];
 #pragma unroll 1
-                for (int c = 0; c < kGroupLoads; ++c) {
-                    load_sum32(tbase + c * 32, chunked, r, ssum(c));
-                    const int64_t j0 = tn * TN + group * kGroupCols + c * 32;
-                    const uint32_t mask = (rv && j0 < args.m &&
-                                           IQP_IN(row * args.ldp32 + (j0 >> 5), args.l * args.ldp32, 52))
-                                              ? args.pa32[row * args.ldp32 + (j0 >> 5)]
-                                              : 0u;
-                    float v[32];
+                    for (int c = 0; c < kGroupLoads; ++c) {
+                        load_sum32(tb_h + c * 32, chunked, r, ssum(c));
+                        if (row < args.l && c0 + c * 32 < args.s) store_out32(args, row, c0 + c * 32, r);
+                    }
+                } else if (!GRAD) {
+                    const int64_t c0 = tn_h * TN + group * kGroupCols;
+                    const bool rv = row < args.l;
+                    const float al = rv && IQP_IN(row, args.l, 55) ? (float)args.alpha[row] : 0.f;
+                    const float be = (rv && args.beta) ? (float)args.beta[row] : 0.f;
+                    uint32_t r[32];
+#pragma unroll 1
+                    for (int c = 0; c < kGroupLoads; ++c) {
+                        load_sum32(tb_h + c * 32, chunked, r, ssum(c));
+                        const int64_t i0 = c0 + c * 32;
+                        uint32_t ph[16], pl[16];
 #pragma unroll
-                    for (int e = 0; e < 32; ++e) v[e] = ((mask >> e) & 1u) ? 2.f * __uint_as_float(r[e]) : 0.f;
-                    red[quarter * 256 + group * kGroupCols + c * 32 + lane] = reduce_scatter32(v, lane);
-                }
-                // All producer warps' column sums are in `red`; combine the four
-                // lane quarters in fixed order. (The next tile's writes to
-                // `red` follow a full K loop that needs every warp, so a
-                // second barrier is not needed.)
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&bar->red_full);
-                if (!wait_warp(&bar->red_full, tcount & 1u, abort_flag, status, lim)) {
-                    ok = false;
-                    break;
-                }
-                __syncwarp();
-                const int64_t j = tn * TN + gt;
-                if (gt < TN && j < args.m && arow0 < args.l) {
-                    const double sum = (double)red[gt] + (double)red[256 + gt] + (double)red[512 + gt] +
-                                       (double)red[768 + gt];
-                    if (IQP_IN((arow0 / TM) * args.m + j, args.tiles_m * args.m, 53))
-                        args.gpart[(arow0 / TM) * args.m + j] = sum;
+                        for (int e = 0; e < 32; e += 2) {
+                            float s0, k0, s1, k1;
+                            sincosf(__uint_as_float(r[e]), &s0, &k0);
+                            sincosf(__uint_as_float(r[e + 1]), &s1, &k1);
+                            const float w0 = s0 * (al + be * k0), w1 = s1 * (al + be * k1);
+                            const float h0 = __bfloat162float(__float2bfloat16_rn(w0));
+                            const float h1 = __bfloat162float(__float2bfloat16_rn(w1));
+                            ph[e / 2] = pack_bf16x2(h0, h1);
+                            pl[e / 2] = pack_bf16x2(w0 - h0, w1 - h1);
+                        }
+                        if (rv && i0 < args.s) store_w32(args, row, i0, ph, pl);
+                    }
+                } else {
+                    // Gradient epilogue: mask by 2 P_A[a][j], reduce over observables.
+                    const bool rv = row < args.l;
+                    uint32_t r[32];
+#pragma unroll 1
+                    for (int c = 0; c < kGroupLoads; ++c) {
+                        load_sum32(tb_h + c * 32, chunked, r, ssum(c));
+                        const int64_t j0 = tn_h * TN + group * kGroupCols + c * 32;
+                        const uint32_t mask = (rv && j0 < args.m &&
+                                               IQP_IN(row * args.ldp32 + (j0 >> 5), args.l * args.ldp32, 52))
+                                                  ? args.pa32[row * args.ldp32 + (j0 >> 5)]
+                                                  : 0u;
+                        float v[32];
+#pragma unroll
+                        for (int e = 0; e < 32; ++e) v[e] = ((mask >> e) & 1u) ? 2.f * __uint_as_float(r[e]) : 0.f;
+                        red[quarter * 256 + group * kGroupCols + c * 32 + lane] = reduce_scatter32(v, lane);
+                    }
+                    // All producer warps' column sums are in `red`; combine the four
+                    // lane quarters in fixed order. (The next tile's writes to
+                    // `red` follow a full K loop that needs every warp, so a
+                    // second barrier is not needed.)
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&bar->red_full);
+                    if (!wait_warp(&bar->red_full, tcount & 1u, abort_flag, status, lim)) {
+                        ok = false;
+                        break;
+                    }
+                    __syncwarp();
+                    const int64_t j = tn_h * TN + gt;
+                    if (gt < TN && j < args.m && arow0 < args.l) {
+                        const double sum = (double)red[gt] + (double)red[256 + gt] + (double)red[512 + gt] +
+                                           (double)red[768 + gt];
+                        if (IQP_IN((arow0 / TM) * args.m + j, args.tiles_m * args.m, 53))
+                            args.gpart[(arow0 / TM) * args.m + j] = sum;
+                    }
                 }
             }
+            if (!ok) break;
             tc_fence_before();
         }
     }
@@ -1523,10 +1595,10 @@ bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <bool GRAD, int MODE, int CG, bool AT = GRAD, bool SPL = false, bool TA = false>
+template <bool GRAD, int MODE, int CG, bool AT = GRAD, bool SPL = false, int TA = 0>
 cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
                      cudaStream_t st) {
-    using C = Cfg<CG, GRAD || AT, TA && !GRAD && !AT && CG == 2>;
+    using C = Cfg<CG, GRAD || AT, TA == 1 && !GRAD && !AT && CG == 2, TA == 3 && !GRAD && !AT && CG == 2 && !SPL>;
     constexpr int CL = CG;
     static bool attr_set = false;
     if (!attr_set) {
@@ -1543,7 +1615,7 @@ cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensor
                    : MODE == 3 ? IQP_KERNEL_LOWORDER_GEMM
                                : IQP_KERNEL_PHASE_TC,
                    st);
-    if (CL == 1) {
+    if constexpr (CL == 1) {
         k_tc<GRAD, MODE, 1, AT, SPL, TA><<<(unsigned)groups, kThreads, C::SMEM, st>>>(a, a2, b, args);
         return cudaGetLastError();
     }
@@ -1637,6 +1709,18 @@ bool phase_serp() {
     return v == 1;
 }
 
+// Phase kernels of CTA pairs: full rounds of tiles of two sample tiles
+// (256 observables x 512 samples) against each A stage, the rest as single
+// tiles (IQP_PHASE_DT; default 1; 0 = single tiles only).
+bool phase_dt() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("IQP_PHASE_DT");
+        v = (e != nullptr && e[0] == '0') ? 0 : 1;
+    }
+    return v == 1;
+}
+
 // Phase kernels of CTA pairs with the A operand in TMEM (default) or in
 // shared memory (IQP_PHASE_TMEM=0).
 bool phase_tmem() {
@@ -1684,13 +1768,21 @@ T *at(void *ws, size_t off) {
 }  // namespace
 
 namespace {
+// Two sample tiles per tile (CTA pairs, whole tiles).
+cudaError_t launch_phase_dt_k(int mode, const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a,
+                              cudaStream_t st) {
+    if (mode == 0) return launch_k<false, 0, 2, false, false, 3>(ma, ma, mb, a, st);
+    if (mode == 1) return launch_k<false, 1, 2, false, false, 3>(ma, ma, mb, a, st);
+    return launch_k<false, 2, 2, false, false, 3>(ma, ma, mb, a, st);
+}
+
 template <bool SPL>
 cudaError_t launch_phase_k(int mode, int cg, const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a,
                            cudaStream_t st) {
     if (cg == 2 && phase_tmem()) {
-        if (mode == 0) return launch_k<false, 0, 2, false, SPL, true>(ma, ma, mb, a, st);
-        if (mode == 1) return launch_k<false, 1, 2, false, SPL, true>(ma, ma, mb, a, st);
-        return launch_k<false, 2, 2, false, SPL, true>(ma, ma, mb, a, st);
+        if (mode == 0) return launch_k<false, 0, 2, false, SPL, 1>(ma, ma, mb, a, st);
+        if (mode == 1) return launch_k<false, 1, 2, false, SPL, 1>(ma, ma, mb, a, st);
+        return launch_k<false, 2, 2, false, SPL, 1>(ma, ma, mb, a, st);
     }
     if (cg == 2) {
         if (mode == 0) return launch_k<false, 0, 2, false, SPL>(ma, ma, mb, a, st);
@@ -1743,12 +1835,36 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.status = at<uint32_t>(ws, p.off_status);
     a.limit_ns = default_spin_limit_ns();
     a.serp = phase_serp() ? 1 : 0;
+    // Two sample tiles per tile: the full rounds of double tiles (256 x 512)
+    // run in one launch; the double tiles of the last, partial round continue
+    // below as single tiles (tile t = half t % 2 of double tile dbase + t / 2).
+    int64_t T = a.tiles_m * a.tiles_n;
+    {
+        int sms = num_sms();
+        if (sms > kMaxSplitCtas) sms = kMaxSplitCtas;
+        const int64_t P = sms / 2;  // CTA pairs
+        const int64_t tiles_n2 = cdiv(p.s, 2 * TN);
+        const int64_t T2 = a.tiles_m * tiles_n2;
+        if (cg == 2 && phase_dt() && p.off_gsum != 0 && num_sms() <= kMaxSplitCtas && P >= 1 && T2 >= P) {
+            const int64_t full = (T2 / P) * P;
+            TcArgs d = a;
+            d.tiles_n = tiles_n2;
+            whole_tiles(d, full);
+            d.gsum = at<float4>(ws, p.off_gsum);
+            const cudaError_t e = launch_phase_dt_k(mode, ma, mb, d, st);
+            if (e != cudaSuccess) return e;
+            if (full == T2) return cudaSuccess;
+            a.dtmap = 1;
+            a.dbase = full;
+            a.tiles_n2 = tiles_n2;
+            T = 2 * (T2 - full);
+        }
+    }
     // A last round of tiles that would leave CTA groups idle is split along
     // the gates across them: the whole tiles run first (full rounds), then a
     // second launch runs the remaining tiles' parts, each a range of whole
     // bits stages, and the last part of a tile to finish sums the parts (in
     // part order) and runs the epilogue.
-    const int64_t T = a.tiles_m * a.tiles_n;
     whole_tiles(a, T);
     int64_t R = 0, ns = 1;
     if (split_tail() && p.off_skp != 0) {

@@ -390,10 +390,11 @@ def test_workspace_too_small_is_rejected_and_the_split_scratch_is_optional(api):
     ws = torch.zeros(need, dtype=torch.uint8, device="cuda")
     out = torch.zeros(p.l, dtype=torch.float64, device="cuda")
     P = ctypes.c_void_p
-    # The split-tile scratch at the end of the split-BF16 workspace (160
-    # partial accumulators of 128 x 256 FP32 and 160 counters, rounded to
-    # 256 bytes) is optional; anything shorter than the rest is rejected.
-    optional = -(-(160 * 128 * 256 * 4 + 160 * 4) // 256) * 256
+    # The end of the split-BF16 workspace is optional: the split-tile scratch
+    # (160 partial accumulators of 128 x 256 FP32 and 160 counters, rounded
+    # to 256 bytes), then the running sums of the two-sample-tile phase (160
+    # CTAs x 2 x 128 x 256 FP32). Anything shorter than the rest is rejected.
+    optional = -(-(160 * 128 * 256 * 4 + 160 * 4) // 256) * 256 + 160 * 2 * 128 * 256 * 4
 
     def call(nbytes, res):
         return lib.iqp_expval(p.n, P(G.data_ptr()), p.m, G.shape[1], P(A.data_ptr()), p.l, A.shape[1],
@@ -556,6 +557,75 @@ print(json.dumps({"ev": float(np.max(np.abs(ev.cpu().numpy() - wev))), "se": flo
     r = json.loads(out.stdout.strip().splitlines()[-1])
     assert r["status"] == 0
     assert r["ev"] <= TOL["split_bf16"] and r["se"] <= TOL["split_bf16"] and r["g"] <= GRAD_RTOL
+
+
+def test_two_sample_tile_phase_matches_single_tiles_and_oracle():
+    """The split-BF16 phase of CTA pairs runs its full rounds as tiles of two
+    256-sample tiles against each A stage (running sums in global memory) and
+    the last round's double tiles as single tiles, split along the gates.
+    On a shape with 88 double tiles for 76 CTA pairs and three accumulation
+    chunks per tile, the fused statistics + gradient call agrees with the
+    single-tile form (IQP_PHASE_DT=0) to FP32 rounding and, on sampled
+    observables, with the oracle."""
+    import os
+    import subprocess
+    import sys
+    import tempfile
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = {}
+    for dt in ("1", "0"):
+        with tempfile.TemporaryDirectory() as tmp:
+            path = os.path.join(tmp, "r.npz")
+            env = dict(os.environ, IQP_PHASE_DT=dt, PYTHONPATH=root)
+            r = subprocess.run([sys.executable, "-c", _TWO_TILE_CODE, path], env=env, cwd=root, capture_output=True,
+                               text=True, timeout=600)
+            assert r.returncode == 0, r.stderr[-2000:]
+            z = np.load(path)
+            out[dt] = {k: z[k] for k in ("ev", "se", "g", "status")}
+    for dt in ("1", "0"):
+        assert int(out[dt]["status"]) == 0
+    # The two forms sum the gates in different orders (serpentine rounds
+    # differ), so they agree to FP32 rounding of Phi and of the per-64-sample
+    # cos statistics: 1e-6 of the estimates and of the standard errors. Each
+    # gradient is about 2e-5 (relative) from the FP64 one, so two of them may
+    # differ by that much; half the gradient tolerance bounds the difference.
+    assert np.max(np.abs(out["1"]["ev"] - out["0"]["ev"])) <= 1e-6
+    assert np.max(np.abs(out["1"]["se"] - out["0"]["se"])) <= 1e-7
+    assert rel_l2(out["1"]["g"], out["0"]["g"]) <= GRAD_RTOL / 2
+    n, G, A, Z, th, idx, al = _two_tile_problem()
+    wev, wse, _, _ = oracle.expval(n, G, A[idx], Z, th.astype(np.float64))
+    assert np.max(np.abs(out["1"]["ev"][idx] - wev)) <= TOL["split_bf16"]
+    assert np.max(np.abs(out["1"]["se"][idx] - wse)) <= TOL["split_bf16"]
+    wg = oracle.expval_grad(n, G, A[idx], Z, th.astype(np.float64), al[idx], None)
+    assert rel_l2(out["1"]["g"], wg) <= GRAD_RTOL
+
+
+def _two_tile_problem():
+    """n=130, m=20000, l=2600 (11 observable blocks), s=3600 (8 double sample
+    blocks); sampled observables on both sides of block edges."""
+    rng = I.Rng(29)
+    n, m, l, s = 130, 20000, 2600, 3600
+    G = I.random_k_body(rng, m, n, [1, 2, 3], 1)
+    th = (0.05 * rng.normal(m, 2)).astype(np.float32)
+    A = I.bernoulli_bits(rng, l, n, 0.05, 3)
+    Z = I.uniform_bits(rng, s, n, 4)
+    idx = np.array([0, 1, 255, 256, 511, 1300, 2047, 2048, 2303, 2304, 2599])
+    al = np.zeros(l)
+    al[idx] = I.Rng(9).normal(idx.size, 1) / s
+    return n, G, A, Z, th, idx, al
+
+
+_TWO_TILE_CODE = """
+import sys, numpy as np, torch
+sys.path.insert(0, "tests")
+from test_gpu import _two_tile_problem
+from paper_2501_04776_gb300 import api
+n, G, A, Z, th, idx, al = _two_tile_problem()
+d = api.to_device_bits
+ev, se, g = api.expval_value_and_grad(n, torch.from_numpy(th).cuda(), d(G), d(A), d(Z), torch.from_numpy(al).cuda(),
+                                      None, "split_bf16")
+np.savez(sys.argv[1], ev=ev.cpu().numpy(), se=se.cpu().numpy(), g=g.cpu().numpy(), status=api.read_status())
+"""
 
 
 # --------------------------------------------------------- bitflip circuits
