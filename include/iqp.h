@@ -156,7 +156,10 @@ iqp_status iqp_expval(int64_t n, const uint64_t *G, int64_t m, int64_t ldg,
  * process exits; this call allocates nothing. Sizes whose
  * iqp_workspace_bytes(IQP_OP_EXPVAL, ...), less its optional part (see
  * there), exceeds 64 MiB are rejected with IQP_ERR_WORKSPACE before any
- * launch. The first call on a device looks up
+ * launch. Where the array holds less than the full workspace, the
+ * split-BF16 phase runs the forms whose optional regions fit, so its results
+ * may differ in the last bits from iqp_expval's with a full workspace (the
+ * same tolerance holds). The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) with that device current;
  * make that first call before any stream capture. All calls share the one
  * array: calls that overlap on the GPU (other streams, other host threads)
