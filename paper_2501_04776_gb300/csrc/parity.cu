@@ -242,49 +242,59 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
 // P^T is never read back. R^T: n x ldrt32 words (bits over rows, zero past
 // `rows`); P^T: m x ldpt32 words; P: rows x ldp32 words (bits over gates,
 // zero past m).
+// IT: the index type. int32_t when the host has checked that every element
+// index of the launch fits (the common case: fewer instructions per access),
+// else int64_t.
+template <typename IT>
 __global__ void __launch_bounds__(kTT) k_gather_transpose(const int4 *__restrict__ sup, const uint64_t *__restrict__ G,
-                                                           int64_t ldg, int64_t n, int64_t m, int64_t rows,
-                                                           const uint32_t *__restrict__ RT, int64_t ldrt32,
-                                                           uint32_t *__restrict__ PT, int64_t ldpt32,
-                                                           uint32_t *__restrict__ P, int64_t ldp32, int64_t gx) {
+                                                           int64_t ldg_, int64_t n_, int64_t m_, int64_t rows_,
+                                                           const uint32_t *__restrict__ RT, int64_t ldrt32_,
+                                                           uint32_t *__restrict__ PT, int64_t ldpt32_,
+                                                           uint32_t *__restrict__ P, int64_t ldp32_, int64_t gx) {
     __shared__ uint32_t tin[kTT][kTW + 1];
+    const IT ldg = (IT)ldg_, n = (IT)n_, m = (IT)m_, rows = (IT)rows_;
+    const IT ldrt32 = (IT)ldrt32_, ldpt32 = (IT)ldpt32_, ldp32 = (IT)ldp32_;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t bid = blockIdx.x;
-    const int64_t r0 = (bid % gx) * kTT;   // gates (P^T rows) of this tile
-    const int64_t c0 = (bid / gx) * kTT;   // rows (P^T bit columns) of this tile
-    const int64_t w0 = c0 >> 5;
+    const IT r0 = (IT)((bid % gx) * kTT);  // gates (P^T rows) of this tile
+    const IT c0 = (IT)((bid / gx) * kTT);  // rows (P^T bit columns) of this tile
+    const IT w0 = c0 >> 5;
+    // this thread's rows of the tile are row0 + kTT / 4 * k, its words q .. q + 3
+    const int row0 = tid / 4, q = (tid % 4) * 4;
+    const bool colok = w0 + q < ldrt32;
+    const uint32_t *rtq = RT + w0 + q;  // + qubit * ldrt32
 #pragma unroll
     for (int k = 0; k < kTW / 4; ++k) {
-        const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
-        const int64_t j = r0 + row;
+        const int row = row0 + (kTT / 4) * k;
+        const IT j = r0 + row;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (j < m && w0 + q < ldrt32 && IQP_IN(j * ldpt32 + w0 + q + 3, m * ldpt32, 7)) {
+        if (j < m && colok && IQP_IN((int64_t)j * ldpt32 + w0 + q + 3, (int64_t)m * ldpt32, 7)) {
             const int4 sp = sup[j];
             if (sp.w <= 3 && IQP_IN(sp.w > 0 ? sp.x : 0, n, 8) && IQP_IN(sp.w > 1 ? sp.y : 0, n, 8) &&
                 IQP_IN(sp.w > 2 ? sp.z : 0, n, 8)) {
                 // ldrt32 is a multiple of 8 and w0 + q of 4: the 16-byte word is inside the row
                 if (sp.w > 0) {
-                    const uint4 a = *reinterpret_cast<const uint4 *>(RT + (int64_t)sp.x * ldrt32 + w0 + q);
+                    const uint4 a = *reinterpret_cast<const uint4 *>(rtq + (IT)sp.x * ldrt32);
                     v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
                 }
                 if (sp.w > 1) {
-                    const uint4 a = *reinterpret_cast<const uint4 *>(RT + (int64_t)sp.y * ldrt32 + w0 + q);
+                    const uint4 a = *reinterpret_cast<const uint4 *>(rtq + (IT)sp.y * ldrt32);
                     v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
                 }
                 if (sp.w > 2) {
-                    const uint4 a = *reinterpret_cast<const uint4 *>(RT + (int64_t)sp.z * ldrt32 + w0 + q);
+                    const uint4 a = *reinterpret_cast<const uint4 *>(rtq + (IT)sp.z * ldrt32);
                     v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
                 }
             } else if (sp.w > 3) {
                 // every qubit of the support, from the packed row
-                const int64_t nw = (n + 63) >> 6;
-                for (int64_t w = 0; w < nw; ++w) {
+                const IT nw = (n + 63) >> 6;
+                for (IT w = 0; w < nw; ++w) {
                     uint64_t word = G[j * ldg + w];
                     if (w == nw - 1 && (n & 63)) word &= (1ull << (n & 63)) - 1ull;
                     while (word) {
-                        const int64_t qb = 64 * w + __ffsll((long long)word) - 1;
+                        const IT qb = 64 * w + (IT)__ffsll((long long)word) - 1;
                         word &= word - 1ull;
-                        const uint4 a = *reinterpret_cast<const uint4 *>(RT + qb * ldrt32 + w0 + q);
+                        const uint4 a = *reinterpret_cast<const uint4 *>(rtq + qb * ldrt32);
                         v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
                     }
                 }
@@ -299,14 +309,15 @@ __global__ void __launch_bounds__(kTT) k_gather_transpose(const int4 *__restrict
     __syncthreads();
     transpose_tile_smem(tin, warp, lane);
     __syncthreads();
-    const int64_t ow0 = r0 >> 5;
+    const IT ow0 = r0 >> 5;
+    // ldp32 is a multiple of 8 and ow0 + q of 4: whole 16-byte words
+    if (ow0 + q >= ldp32) return;
 #pragma unroll
     for (int k = 0; k < kTW / 4; ++k) {
-        const int idx = tid + kTT * k, row = idx / 4, q = (idx % 4) * 4;
-        const int64_t orow = c0 + row;
+        const int row = row0 + (kTT / 4) * k;
+        const IT orow = c0 + row;
         if (orow >= rows) continue;
-        // ldp32 is a multiple of 8 and ow0 + q of 4: whole 16-byte words
-        if (ow0 + q < ldp32 && IQP_IN(orow * ldp32 + ow0 + q + 3, rows * ldp32, 9))
+        if (IQP_IN((int64_t)orow * ldp32 + ow0 + q + 3, (int64_t)rows * ldp32, 9))
             *reinterpret_cast<uint4 *>(P + orow * ldp32 + ow0 + q) =
                 make_uint4(tin[row][q], tin[row][q + 1], tin[row][q + 2], tin[row][q + 3]);
     }
@@ -471,11 +482,19 @@ cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int
         const int64_t gx = cdiv(m, kTT);
         const int64_t gy = cdiv(rows, kTT);
         if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+        // 32-bit element indices where every one of this launch fits
+        const int64_t lim = (int64_t)1 << 31;
+        const bool i32 = m * 2 * ldpt < lim && rows * 2 * ldp < lim && n * 2 * ldpt < lim && m * ldg < lim &&
+                         gx * kTT < lim && gy * kTT < lim;
         LaunchScope ls(IQP_KERNEL_PARITY, st);
-        k_gather_transpose<<<(unsigned)(gx * gy), kTT, 0, st>>>(sup, G, ldg, n, m, rows,
-                                                                  reinterpret_cast<const uint32_t *>(RT), 2 * ldpt,
-                                                                  reinterpret_cast<uint32_t *>(PT), 2 * ldpt,
-                                                                  reinterpret_cast<uint32_t *>(P), 2 * ldp, gx);
+        if (i32)
+            k_gather_transpose<int32_t><<<(unsigned)(gx * gy), kTT, 0, st>>>(
+                sup, G, ldg, n, m, rows, reinterpret_cast<const uint32_t *>(RT), 2 * ldpt,
+                reinterpret_cast<uint32_t *>(PT), 2 * ldpt, reinterpret_cast<uint32_t *>(P), 2 * ldp, gx);
+        else
+            k_gather_transpose<int64_t><<<(unsigned)(gx * gy), kTT, 0, st>>>(
+                sup, G, ldg, n, m, rows, reinterpret_cast<const uint32_t *>(RT), 2 * ldpt,
+                reinterpret_cast<uint32_t *>(PT), 2 * ldpt, reinterpret_cast<uint32_t *>(P), 2 * ldp, gx);
         return cudaGetLastError();
     }
     {

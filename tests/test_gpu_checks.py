@@ -61,6 +61,18 @@ for prec in ("fp32", "split_bf16", "sparse_fp32", "loworder_fp32"):
             out["errors"][tag]["g3"] = rel(g3.cpu().numpy(), wg)
             record(tag + "-kept")
 
+# A shape whose split-BF16 phase runs full rounds of two-sample tiles and the
+# last round as single tiles and split parts (88 double tiles for 76 pairs):
+# sampled observables against the oracle
+n, G, A, Z, theta = problem(17, 130, 20000, 2600, 3600, (1, 2, 3))
+theta = (theta / 6).astype(np.float32)
+idx = np.array([0, 255, 256, 1300, 2303, 2304, 2599])
+ev, se = api.expval_raw(n, th(theta), d(G), d(A), d(Z), "split_bf16")
+wev, wse, _, _ = oracle.expval(n, G, A[idx], Z, theta.astype(np.float64))
+out["errors"]["two-tile"] = {"ev": float(np.max(np.abs(ev.cpu().numpy()[idx] - wev))),
+                             "se": float(np.max(np.abs(se.cpu().numpy()[idx] - wse))), "tol": TOL["split_bf16"]}
+record("two-tile")
+
 # MMD loss and gradient (shared and independent batches), bitflip, parities, variants
 rng = I.Rng(3)
 n, G, A, Z, theta = problem(21, 60, 400, 120, 300, (1, 2, 3))
