@@ -94,13 +94,15 @@ typedef enum {
 
 /* Bytes of device scratch `ws` needed by `op` for these sizes (N is ignored
  * except for the MMD ops). Returns 0 for invalid sizes. Host only.
- * With IQP_SPLIT_BF16 its end is optional, in two parts. The last 40 MiB
- * (160 x 256 KiB) hold the running sums of the phase kernels that take two
- * sample tiles per tile; a `ws_bytes` short of the full size by at most that
- * much runs one sample tile per tile instead. The 20.5 MB before them
- * (160 x 128 KiB plus 640 bytes) let a last round of phase tiles that would
- * leave SMs idle be split along the gates across them; a `ws_bytes` short
- * of the full size by both parts runs every phase tile whole. */
+ * With IQP_SPLIT_BF16 its end is optional, in three parts, each used only
+ * when `ws_bytes` reaches its end:
+ *  - 20.5 MB (160 x 128 KiB plus 640 bytes): a last round of phase tiles that
+ *    would leave SMs idle is split along the gates across them (else every
+ *    phase tile runs whole);
+ *  - 40 MiB (160 x 256 KiB): the running sums of the phase kernels that take
+ *    two sample tiles per tile (else one sample tile per tile);
+ *  - 80 MiB (640 x 128 KiB plus 640 bytes): the last round of those kernels
+ *    is split evenly across the SMs (else it runs as single tiles). */
 size_t iqp_workspace_bytes(iqp_op op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N,
                            iqp_precision prec);
 

@@ -165,13 +165,16 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.ldphi = 0;
     p.phi_out = p.phi_in = false;
     // Last, and optional: the split-tile scratch of the tensor-core phase (a
-    // workspace that ends before it runs every phase tile whole), then the
-    // running sums of the two-sample-tile phase kernels (a workspace that
-    // ends before them runs one sample tile per tile).
-    p.off_skp = p.off_gsum = 0;
+    // workspace that ends before it runs every phase tile whole), the running
+    // sums of the two-sample-tile phase kernels (a workspace that ends before
+    // them runs one sample tile per tile), and the scratch of their balanced
+    // last round (a workspace that ends before it runs that round as single
+    // tiles).
+    p.off_skp = p.off_gsum = p.off_skx = 0;
     if (prec == IQP_SPLIT_BF16 && !bitflip && !indep) {
         p.off_skp = take((int64_t)kMaxSplitCtas * kSplitSlotFloats * 4 + (int64_t)kMaxSplitCtas * 4);
         p.off_gsum = take((int64_t)kMaxSplitCtas * kDtSumFloats * 4);
+        p.off_skx = take((int64_t)kSplitSlots * kSplitSlotFloats * 4 + (int64_t)kMaxSplitCtas * 4);
     }
     p.total = off;
     return p;
@@ -300,12 +303,14 @@ iqp_status check_ws(Plan &p, void *ws, size_t ws_bytes) {
     if (ws == nullptr || !aligned(ws, 256)) return IQP_ERR_WORKSPACE;
     if (ws_bytes < p.total) {
         if (ws_bytes < plan_min_bytes(p)) return IQP_ERR_WORKSPACE;
-        // no room for the two-tile running sums: one sample tile per tile
-        p.off_gsum = 0;
-        // no room for the split-tile scratch either: phase tiles run whole
+        // The optional regions at the end, in order: each is used only where
+        // the workspace reaches its end.
+        p.off_skx = 0;  // the two-tile last round runs as single tiles
+        if (p.off_gsum != 0 && ws_bytes < p.off_gsum + (size_t)kMaxSplitCtas * kDtSumFloats * 4)
+            p.off_gsum = 0;  // one sample tile per tile
         if (p.off_skp != 0 && ws_bytes < p.off_skp + (size_t)round_up((int64_t)kMaxSplitCtas * kSplitSlotFloats * 4 +
                                                                        (int64_t)kMaxSplitCtas * 4, 256))
-            p.off_skp = 0;
+            p.off_skp = 0;  // phase tiles run whole
     }
     return IQP_OK;
 }

@@ -22,6 +22,9 @@ constexpr int kGradObs = 256;    // observables per tile of the CTA-pair gradien
 // for at most kMaxSplitCtas CTAs, then one int counter per (tile, CTA).
 constexpr int64_t kSplitSlotFloats = 128 * 256;
 constexpr int kMaxSplitCtas = 160;
+// Balanced split of the two-sample-tile phase's last round: kSplitSlots slots
+// (one per piece, CTA and accumulator), then kMaxSplitCtas counters.
+constexpr int kSplitSlots = 640;
 // Two-sample-tile phase kernels: the running sums of both accumulators, per
 // CTA (at most kMaxSplitCtas CTAs).
 constexpr int64_t kDtSumFloats = 2 * 128 * 256;
@@ -48,6 +51,7 @@ struct Plan {
     size_t off_lo_c, off_lo_m, off_lo_v, off_lo_h, off_lo_gs, off_lo_a;
     size_t off_skp;  // split BF16: partial accumulators and counters of split phase tiles (0 if none)
     size_t off_gsum; // split BF16: per-CTA running sums of the two-sample-tile phase kernels (0 if none)
+    size_t off_skx;  // split BF16: pieces and counters of the two-tile phase's balanced last round (0 if none)
     size_t off_phi;  // MMD gradient (split BF16, row-sparse): room for Phi, l x ldw fp32 (0 if none)
     // Kept Phi (l x ldphi fp32, ldphi a multiple of 64 >= s; the layout is the
     // precision's own): phi_out = the statistics pass writes it, phi_in = the

@@ -26,8 +26,11 @@
 // A_hi / A_lo then live in shared memory beside the two B operands, a stage
 // takes sixteen MMAs, and the A expansion per flop halves. The running sums
 // of the accumulation chunks go to a per-CTA buffer in global memory (it
-// stays in L2). The double tiles of a last, partial round run as single
-// tiles (TcArgs::dtmap), split along the gates as below.
+// stays in L2). The double tiles of a last, partial round run as a balanced
+// split (TcArgs::sk): their bits stages, end to end, in one equal range per
+// CTA pair, each range's piece of a tile a split part; or, without room for
+// its scratch, as single tiles (TcArgs::dtmap), split along the gates as
+// below.
 //
 // Dense form (mode 3, A by TMA): out = (A_hi + A_lo) (1 - 2 B_bits)^T for a
 // dense split-BF16 matrix A brought in by TMA and a +-1 operand expanded from
@@ -191,6 +194,15 @@ struct TcArgs {
     // tiles_m x tiles_n2 walk.
     int dtmap;
     int64_t dbase, tiles_n2;
+    // Balanced split of a last round (sk = 1; split units only): the skW
+    // bits stages of the tiles from `whole` on, laid end to end, are cut into
+    // skP equal contiguous ranges, one per CTA group; unit u is piece u / skP
+    // of range u % skP (the part of the range inside one tile; empty when the
+    // range has fewer pieces). The pieces of tile whole + t take the slots
+    // t * skKP + j, j = 0, 1, ... in range order.
+    int sk;
+    int64_t skW, skP, skKP;
+    int64_t skcap;  // floats of split-part scratch at skp
 };
 
 __device__ __forceinline__ void tile_rc(int64_t t, const TcArgs &a, int64_t &tm, int64_t &tc) {
@@ -226,13 +238,50 @@ __device__ __forceinline__ void unit_of(int64_t u, const TcArgs &a, int nks, int
         v = -1;
         return;
     }
+    const int64_t nkb = (nks + KB / KS - 1) / (KB / KS);
+    if (a.sk) {
+        const int64_t g = u % a.skP, k = u / a.skP;
+        const int64_t A = g * a.skW / a.skP, B = (g + 1) * a.skW / a.skP;
+        const int64_t start = k == 0 ? A : (A / nkb + k) * nkb;
+        tile = a.whole;
+        ks0 = ks1 = 0;
+        v = -1;
+        if (start >= B) return;  // this range has no piece k
+        const int64_t t = start / nkb;
+        const int64_t end = B < (t + 1) * nkb ? B : (t + 1) * nkb;
+        tile = a.whole + t;
+        ks0 = (KB / KS) * (int)(start - t * nkb);
+        const int64_t e = (KB / KS) * (end - t * nkb);
+        ks1 = e < nks ? (int)e : nks;
+        // the range holding the tile's first bits stage: the largest g0 with g0 W / P <= t nkb
+        const int64_t g0 = ((t * nkb + 1) * a.skP - 1) / a.skW;
+        v = t * a.skKP + (g - g0);
+        return;
+    }
     v = u;
     tile = a.whole + v / a.nsplit;
     const int64_t part = v % a.nsplit;
-    const int64_t nkb = (nks + KB / KS - 1) / (KB / KS);
     ks0 = (KB / KS) * (int)(part * nkb / a.nsplit);
     const int e = (KB / KS) * (int)((part + 1) * nkb / a.nsplit);
     ks1 = e < nks ? e : nks;
+}
+
+// A split unit's slot v -> its tile's index tt among the split tiles, the
+// number of parts of that tile and the slot of its first part.
+__device__ __forceinline__ void part_info(int64_t v, const TcArgs &a, int nks, int64_t &tt, int64_t &np,
+                                          int64_t &base) {
+    if (a.sk) {
+        const int64_t nkb = (nks + KB / KS - 1) / (KB / KS);
+        tt = v / a.skKP;
+        const int64_t g0 = ((tt * nkb + 1) * a.skP - 1) / a.skW;
+        const int64_t g1 = ((tt + 1) * nkb * a.skP - 1) / a.skW;
+        np = g1 - g0 + 1;
+        base = tt * a.skKP;
+        return;
+    }
+    tt = v / a.nsplit;
+    np = a.nsplit;
+    base = tt * a.nsplit;
 }
 
 __device__ __forceinline__ uint8_t *aligned_smem(uint8_t *raw) {
@@ -510,7 +559,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr bool ATM = TA == 1 && !GRAD && !AT && CG == 2;
     // Two sample tiles per tile (phase modes, CTA pairs, whole tiles): A in
     // shared memory, two accumulators, running sums in global memory
-    constexpr bool DT = TA == 3 && !GRAD && !AT && CG == 2 && !SPL;
+    constexpr bool DT = TA == 3 && !GRAD && !AT && CG == 2;
     using C = Cfg<CG, ATMA, ATM, DT>;
     constexpr int NOP = C::NOP;
     // Serpentine gate order (phase kernels, whole tiles): the CTA groups' odd
@@ -755,14 +804,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         // operand stage (see expand_a_tmem), packed two stages per word
         uint32_t abits01 = 0, abits23 = 0;
         bool ok = true;
-        for (int64_t u = group0; u < nunits && ok; u += ngroups, ++tcount) {
+        for (int64_t u = group0; u < nunits && ok; u += ngroups) {
             int ks0, ks1;
-            int64_t tm, tc;
+            int64_t tm, tc, slot;
             {
-                int64_t t, uv0;
-                unit_of<SPL>(u, args, nks, t, ks0, ks1, uv0);
+                int64_t t;
+                unit_of<SPL>(u, args, nks, t, ks0, ks1, slot);
                 tile_rc(t, args, tm, tc);
             }
+            if (ks0 >= ks1) continue;      // an empty piece of a balanced split: no work
+            const uint32_t tix = tcount++;  // units this CTA ran before this one
             const int64_t tn = tc;
             const int64_t arow0 = tm * TM * CG + (CG == 2 ? (int64_t)crank * TM : 0);  // first observable here
             int kc = 0;              // stage index within the current chunk
@@ -919,26 +970,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool chunked = nchunk > 0;
 
             if (!GRAD && MODE != 3 && SPL) {
-                const int64_t uv = u;  // this part's slot
-                // A part of a split tile: store this part's accumulator; the
-                // CTA that finishes the tile's last part sums every part's,
-                // in part order, back into TMEM and runs the epilogue.
+                // A part of a split tile: store this part's accumulator(s);
+                // the CTA that finishes the tile's last part sums every
+                // part's, in part order, back into TMEM and runs the
+                // epilogue. Slot layout: ((slot * CG + CTA) * NH + h) per
+                // TM x TN accumulator h (DT: two).
+                constexpr int NH = DT ? 2 : 1;
                 const int64_t half = CG == 2 ? (int64_t)crank : 0;
-                [[maybe_unused]] constexpr int64_t kSkp = (int64_t)kMaxSplitCtas * kSplitSlotFloats;  // slot floats
-                const int64_t so = ((uv * CG + half) * TM + rl) * TN + group * kGroupCols;
-                if (IQP_IN(so + kGroupCols - 1, kSkp, 47))
-                    split_store(args.skp + so, tbase, chunked, ATM ? sum4 + ((group * kGroupCols) >> 2) * TM + rl : nullptr);
+                [[maybe_unused]] const int64_t kSkp = args.skcap;  // floats of part scratch
+                int64_t tt, np, pbase;  // index among the split tiles, its parts, its first part's slot
+                part_info(slot, args, nks, tt, np, pbase);
+#pragma unroll 1
+                for (int h = 0; h < NH; ++h) {
+                    const int64_t so = (((slot * CG + half) * NH + h) * TM + rl) * TN + group * kGroupCols;
+                    const float4 *ss0 = ATM  ? sum4 + ((group * kGroupCols) >> 2) * TM + rl
+                                        : DT ? gsum_cta + ((h * TN + group * kGroupCols) >> 2) * TM + rl
+                                             : nullptr;
+                    if (IQP_IN(so + kGroupCols - 1, kSkp, 47))
+                        split_store(args.skp + so, tbase + (uint32_t)(h * TN), chunked, ss0);
+                }
                 __threadfence();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bar->part_done);
-                const int64_t tt = uv / args.nsplit;  // index among the split tiles
-                const uint32_t nsu = tcount;          // split parts this CTA finished before
+                const uint32_t nsu = tix;  // split parts this CTA finished before
                 if (warp == 2 && lane == 0) {
                     if (mbar_wait(&bar->part_done, nsu & 1u, abort_flag, status, lim)) {
                         int last = 0;
                         if (IQP_IN(tt * CG + half, kMaxSplitCtas, 48)) {
                             int *cnt = args.skc + tt * CG + half;
-                            last = atomicAdd(cnt, 1) == args.nsplit - 1;
+                            last = atomicAdd(cnt, 1) == np - 1;
                             if (last) {
                                 atomicExch(cnt, 0);  // ready for the next launch
                                 __threadfence();
@@ -957,9 +1017,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                     continue;  // another CTA finishes this tile
                 }
                 __threadfence();
-                const int64_t s0 = ((tt * args.nsplit * CG + half) * TM + rl) * TN + group * kGroupCols;
-                if (IQP_IN(s0 + (int64_t)(args.nsplit - 1) * CG * TM * TN + kGroupCols - 1, kSkp, 49))
-                    split_sum(args.skp + s0, (int64_t)CG * TM * TN, args.nsplit, tbase);
+#pragma unroll 1
+                for (int h = 0; h < NH; ++h) {
+                    const int64_t s0 = (((pbase * CG + half) * NH + h) * TM + rl) * TN + group * kGroupCols;
+                    const int64_t pstride = (int64_t)CG * NH * TM * TN;
+                    if (IQP_IN(s0 + (np - 1) * pstride + kGroupCols - 1, kSkp, 49))
+                        split_sum(args.skp + s0, pstride, (int)np, tbase + (uint32_t)(h * TN));
+                }
                 chunked = false;  // the sum of the parts is in the accumulator columns
             }
             // Phi (or Q) for 32 columns: last chunk's accumulator + running sum.
@@ -1107,7 +1171,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // second barrier is not needed.)
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&bar->red_full);
-                    if (!wait_warp(&bar->red_full, tcount & 1u, abort_flag, status, lim)) {
+                    if (!wait_warp(&bar->red_full, tix & 1u, abort_flag, status, lim)) {
                         ok = false;
                         break;
                     }
@@ -1598,7 +1662,7 @@ bool make_map(CUtensorMap *map, const void *base, CUtensorMapDataType dt, int64_
 template <bool GRAD, int MODE, int CG, bool AT = GRAD, bool SPL = false, int TA = 0>
 cudaError_t launch_k(const CUtensorMap &a, const CUtensorMap &a2, const CUtensorMap &b, const TcArgs &args,
                      cudaStream_t st) {
-    using C = Cfg<CG, GRAD || AT, TA == 1 && !GRAD && !AT && CG == 2, TA == 3 && !GRAD && !AT && CG == 2 && !SPL>;
+    using C = Cfg<CG, GRAD || AT, TA == 1 && !GRAD && !AT && CG == 2, TA == 3 && !GRAD && !AT && CG == 2>;
     constexpr int CL = CG;
     static bool attr_set = false;
     if (!attr_set) {
@@ -1768,12 +1832,14 @@ T *at(void *ws, size_t off) {
 }  // namespace
 
 namespace {
-// Two sample tiles per tile (CTA pairs, whole tiles).
+// Two sample tiles per tile (CTA pairs): whole tiles, or (SPL) the pieces of
+// a balanced split of the last round.
+template <bool SPL>
 cudaError_t launch_phase_dt_k(int mode, const CUtensorMap &ma, const CUtensorMap &mb, const TcArgs &a,
                               cudaStream_t st) {
-    if (mode == 0) return launch_k<false, 0, 2, false, false, 3>(ma, ma, mb, a, st);
-    if (mode == 1) return launch_k<false, 1, 2, false, false, 3>(ma, ma, mb, a, st);
-    return launch_k<false, 2, 2, false, false, 3>(ma, ma, mb, a, st);
+    if (mode == 0) return launch_k<false, 0, 2, false, SPL, 3>(ma, ma, mb, a, st);
+    if (mode == 1) return launch_k<false, 1, 2, false, SPL, 3>(ma, ma, mb, a, st);
+    return launch_k<false, 2, 2, false, SPL, 3>(ma, ma, mb, a, st);
 }
 
 template <bool SPL>
@@ -1851,9 +1917,38 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
             d.tiles_n = tiles_n2;
             whole_tiles(d, full);
             d.gsum = at<float4>(ws, p.off_gsum);
-            const cudaError_t e = launch_phase_dt_k(mode, ma, mb, d, st);
+            const cudaError_t e = launch_phase_dt_k<false>(mode, ma, mb, d, st);
             if (e != cudaSuccess) return e;
             if (full == T2) return cudaSuccess;
+            // The last round, balanced: its double tiles' bits stages, end to
+            // end, in P equal ranges, one per CTA pair (pieces of at most two
+            // or three tiles each; see unit_of).
+            const int64_t left = T2 - full;
+            const int64_t nkb = cdiv(a.nks, KB / KS);
+            const int64_t W = left * nkb;
+            if (split_tail() && p.off_skx != 0 && W >= P && left * 2 <= kMaxSplitCtas) {
+                int64_t KP = 1;
+                for (int64_t t = 0; t < left; ++t) {
+                    const int64_t g0 = ((t * nkb + 1) * P - 1) / W, g1 = ((t + 1) * nkb * P - 1) / W;
+                    if (g1 - g0 + 1 > KP) KP = g1 - g0 + 1;
+                }
+                if (left * KP * 2 * 2 <= kSplitSlots) {
+                    TcArgs e2 = d;
+                    e2.whole = full;
+                    e2.nsplit = 1;
+                    e2.nunits = P * (cdiv(W / P + 1, nkb) + 2);
+                    e2.sk = 1;
+                    e2.skW = W;
+                    e2.skP = P;
+                    e2.skKP = KP;
+                    e2.skp = at<float>(ws, p.off_skx);
+                    e2.skc = reinterpret_cast<int *>(e2.skp + (int64_t)kSplitSlots * kSplitSlotFloats);
+                    e2.skcap = (int64_t)kSplitSlots * kSplitSlotFloats;
+                    const cudaError_t e3 = cudaMemsetAsync(e2.skc, 0, (size_t)(left * 2) * sizeof(int), st);
+                    if (e3 != cudaSuccess) return e3;
+                    return launch_phase_dt_k<true>(mode, ma, mb, e2, st);
+                }
+            }
             a.dtmap = 1;
             a.dbase = full;
             a.tiles_n2 = tiles_n2;
@@ -1889,6 +1984,7 @@ cudaError_t launch_phase_tc(int mode, const Plan &p, void *ws, const double *alp
     a.nunits = R * ns;
     a.skp = at<float>(ws, p.off_skp);
     a.skc = reinterpret_cast<int *>(a.skp + (int64_t)kMaxSplitCtas * kSplitSlotFloats);
+    a.skcap = (int64_t)kMaxSplitCtas * kSplitSlotFloats;
     const cudaError_t e = cudaMemsetAsync(a.skc, 0, (size_t)(R * cg) * sizeof(int), st);
     if (e != cudaSuccess) return e;
     return launch_phase_k<true>(mode, cg, ma, mb, a, st);

@@ -47,9 +47,10 @@ def test_workspace_bytes(lib):
     # Bit-packed parities: (l + s) rows of ceil(m/64) words dominate the forward
     # (beside them: the (S, M2) partials and a 16-byte support entry per gate).
     assert fwd >= (l + s) * ((m + 63) // 64) * 8
-    # Beside them, at the end: the split-tile scratch and the running sums of
-    # the two-sample-tile phase (both optional, about 21 MB and 42 MB).
-    opt = 160 * 128 * 256 * 4 + 160 * 2 * 128 * 256 * 4
+    # Beside them, at the end (all optional): the split-tile scratch, the
+    # running sums of the two-sample-tile phase and the scratch of its
+    # balanced last round (about 21, 42 and 84 MB).
+    opt = 160 * 128 * 256 * 4 + 160 * 2 * 128 * 256 * 4 + 640 * 128 * 256 * 4 + 4096
     assert fwd < 2 * (l + s) * ((m + 255) // 256) * 32 + 64 * l * ((s + 127) // 128) + 16 * m + opt + (1 << 22)
     # W (hi + lo BF16, l x s) dominates the gradient's extra scratch.
     assert grad - fwd >= 4 * l * s

@@ -392,9 +392,12 @@ def test_workspace_too_small_is_rejected_and_the_split_scratch_is_optional(api):
     P = ctypes.c_void_p
     # The end of the split-BF16 workspace is optional: the split-tile scratch
     # (160 partial accumulators of 128 x 256 FP32 and 160 counters, rounded
-    # to 256 bytes), then the running sums of the two-sample-tile phase (160
-    # CTAs x 2 x 128 x 256 FP32). Anything shorter than the rest is rejected.
-    optional = -(-(160 * 128 * 256 * 4 + 160 * 4) // 256) * 256 + 160 * 2 * 128 * 256 * 4
+    # to 256 bytes), the running sums of the two-sample-tile phase (160 CTAs
+    # x 2 x 128 x 256 FP32) and the scratch of its balanced last round (640
+    # such accumulators and 160 counters). Anything shorter than the rest is
+    # rejected.
+    rnd = lambda b: -(-b // 256) * 256
+    optional = rnd(160 * 128 * 256 * 4 + 160 * 4) + 160 * 2 * 128 * 256 * 4 + rnd(640 * 128 * 256 * 4 + 160 * 4)
 
     def call(nbytes, res):
         return lib.iqp_expval(p.n, P(G.data_ptr()), p.m, G.shape[1], P(A.data_ptr()), p.l, A.shape[1],
