@@ -122,8 +122,11 @@ iqp_status iqp_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr,
  * of supp(g_j); a gate of weight k costs O(k) per 64 rows instead of a fold
  * over all n qubits. Writes PT (m x ldpt words; bit r of row j is
  * (R_r . g_j) mod 2, zero for r >= rows) and, if P != NULL, P exactly as
- * iqp_parity does. ldpt >= ceil(rows/64), even. scratch: device memory of
- * n*ldpt*8 bytes, 16-byte aligned, overwritten. Bit-exact. */
+ * iqp_parity does. With P, the gates' support list is formed first and P^T
+ * and P come from one pass (the estimators' own parity step). ldpt >=
+ * ceil(rows/64), even. scratch: device memory of n*ldpt*8 bytes, plus 16*m
+ * bytes when P != NULL (the support list, after R^T), 16-byte aligned,
+ * overwritten. Bit-exact. */
 iqp_status iqp_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr,
                              const uint64_t *G, int64_t m, int64_t ldg,
                              uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,

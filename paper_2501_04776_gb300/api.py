@@ -101,7 +101,7 @@ def parity_gather(n: int, R: torch.Tensor, G: torch.Tensor):
     ldpt += ldpt & 1
     P = torch.empty((rows, ldp), dtype=torch.int64, device=R.device)
     PT = torch.empty((m, ldpt), dtype=torch.int64, device=R.device)
-    scratch = torch.empty((n, ldpt), dtype=torch.int64, device=R.device)
+    scratch = torch.empty((n * ldpt + 2 * m,), dtype=torch.int64, device=R.device)  # R^T, then the support list
     check(_lib.load().iqp_parity_gather(n, _ptr(R), rows, R.shape[1], _ptr(G), m, G.shape[1], _ptr(P), ldp, _ptr(PT),
                                         ldpt, _ptr(scratch), ctypes.c_void_p(_stream(R.device))), "iqp_parity_gather")
     return P, PT

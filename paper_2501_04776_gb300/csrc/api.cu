@@ -535,8 +535,13 @@ iqp_status iqp_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t
     if (ldpt < cdiv(rows, 64) || (ldpt & 1)) return IQP_ERR_ARG;
     if (P != nullptr && (ldp < cdiv(m, 64) || (ldp & 1))) return IQP_ERR_ARG;
     if (!aligned(PT, 16) || !aligned(scratch, 16) || (P && !aligned(P, 16))) return IQP_ERR_ALIGN;
-    return cuda_status(launch_parity_gather(n, R, rows, ldr, G, m, ldg, P, ldp, PT, ldpt, scratch,
-                                            static_cast<cudaStream_t>(stream)));
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (P == nullptr) return cuda_status(launch_parity_gather(n, R, rows, ldr, G, m, ldg, P, ldp, PT, ldpt, scratch, st));
+    // the support list after R^T (n * ldpt words, an even count: 16-byte aligned), then the fused pass
+    int4 *sup = reinterpret_cast<int4 *>(scratch + n * ldpt);
+    cudaError_t e = launch_support_list(G, m, ldg, n, sup, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(launch_parity_gather(n, R, rows, ldr, G, m, ldg, P, ldp, PT, ldpt, scratch, st, sup));
 }
 
 iqp_status iqp_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,

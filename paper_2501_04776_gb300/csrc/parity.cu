@@ -3,6 +3,8 @@
 // rows. A lane owns one generator and folds (r AND g) over 32-bit words with
 // one LOP3 per word per row into a per-row XOR accumulator; popc(acc) & 1 is
 // the parity. Bit-exact.
+#include <cstdlib>
+
 #include "common.cuh"
 
 namespace iqp {
@@ -234,92 +236,203 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
     }
 }
 
-// Support gather and transpose in one pass: for a tile of 512 gates x 512
-// rows, each P^T word is formed from the gates' supports (int4 list: first
-// three qubits and the count; gates with more than three qubits scan their
-// packed row) as the XOR of R^T rows, written to P^T, and the tile is
-// transposed in shared memory (as in k_bit_transpose) and written to P, so
-// P^T is never read back. R^T: n x ldrt32 words (bits over rows, zero past
-// `rows`); P^T: m x ldpt32 words; P: rows x ldp32 words (bits over gates,
-// zero past m).
+// Support gather and transpose in one pass, one thread per 32 x 32-bit block.
+// A CTA of V warps takes 32 V gates x 1024 rows: warp v owns the gates
+// g0 + 32 v .. + 31, lane L the row word w = w0 + L (rows 32 w .. 32 w + 31).
+// For each of its 32 gates a lane XORs the R^T words at the gate's support
+// (the int4 list: first three qubits and the count; a gate with more qubits
+// scans its packed row) and stores that P^T word; across the warp these are
+// consecutive words of one R^T row and of one P^T row. The lane then
+// transposes its 32 words in registers, after which word b holds the 32
+// gates' bits of row 32 w + b, one word of P. The words are staged in shared
+// memory and the CTA writes P as row segments of V words (the tile's gates),
+// so P^T is never read back.
+// R^T: n x ldrt32 words (bits over rows, zero past `rows`); P^T: m x ldrt32
+// words, all written; P: rows x ldp32 words (bits over gates, zero past m;
+// ldp32 a multiple of 4, P 16-byte aligned).
 // IT: the index type. int32_t when the host has checked that every element
 // index of the launch fits (the common case: fewer instructions per access),
 // else int64_t.
-template <typename IT>
-__global__ void __launch_bounds__(kTT) k_gather_transpose(const int4 *__restrict__ sup, const uint64_t *__restrict__ G,
-                                                           int64_t ldg_, int64_t n_, int64_t m_, int64_t rows_,
-                                                           const uint32_t *__restrict__ RT, int64_t ldrt32_,
-                                                           uint32_t *__restrict__ PT, int64_t ldpt32_,
-                                                           uint32_t *__restrict__ P, int64_t ldp32_, int64_t gx) {
-    __shared__ uint32_t tin[kTT][kTW + 1];
-    const IT ldg = (IT)ldg_, n = (IT)n_, m = (IT)m_, rows = (IT)rows_;
-    const IT ldrt32 = (IT)ldrt32_, ldpt32 = (IT)ldpt32_, ldp32 = (IT)ldp32_;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t bid = blockIdx.x;
-    const IT r0 = (IT)((bid % gx) * kTT);  // gates (P^T rows) of this tile
-    const IT c0 = (IT)((bid / gx) * kTT);  // rows (P^T bit columns) of this tile
-    const IT w0 = c0 >> 5;
-    // this thread's rows of the tile are row0 + kTT / 4 * k, its words q .. q + 3
-    const int row0 = tid / 4, q = (tid % 4) * 4;
-    const bool colok = w0 + q < ldrt32;
-    const uint32_t *rtq = RT + w0 + q;  // + qubit * ldrt32
+constexpr int kGtWords = 32;            // row words per CTA (lanes)
+constexpr int kGtRows = 32 * kGtWords;  // 1024 rows per CTA
+// Staged P: warp v's 32 lanes x 32 words at gt_region(v) + 33 L + b. The pad
+// word per lane puts the 32 lanes of one store (fixed v and b) in 32 distinct
+// banks; the offset 32 / (V / 4) per four warps does the same for the loads
+// of the output pass, which take four consecutive warps' words of a row.
+__host__ __device__ constexpr int gt_region(int V, int v) { return v * 33 * 32 + (32 / (V / 4)) * (v >> 2); }
+__host__ __device__ constexpr int gt_staged_words(int V) { return V * 33 * 32 + 32; }
+// staged P + support list of a CTA of V warps: 37.9 KB for 8 warps
+__host__ __device__ constexpr int gt_smem_bytes(int V) { return gt_staged_words(V) * 4 + 32 * V * 16; }
+
+// Rounds of the in-register 32 x 32 transpose: in every word pair (i, i + J)
+// with bit J of i clear, the high J-bit half of each 2J-bit group of x[i]
+// trades places with the low half of the same group of x[i + J].
+template <int J>
+__device__ __forceinline__ void swap_halves(uint32_t (&x)[32], uint32_t lo) {
 #pragma unroll
-    for (int k = 0; k < kTW / 4; ++k) {
-        const int row = row0 + (kTT / 4) * k;
-        const IT j = r0 + row;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (j < m && colok && IQP_IN((int64_t)j * ldpt32 + w0 + q + 3, (int64_t)m * ldpt32, 7)) {
-            const int4 sp = sup[j];
-            if (sp.w <= 3 && IQP_IN(sp.w > 0 ? sp.x : 0, n, 8) && IQP_IN(sp.w > 1 ? sp.y : 0, n, 8) &&
-                IQP_IN(sp.w > 2 ? sp.z : 0, n, 8)) {
-                // ldrt32 is a multiple of 8 and w0 + q of 4: the 16-byte word is inside the row
-                if (sp.w > 0) {
-                    const uint4 a = *reinterpret_cast<const uint4 *>(rtq + (IT)sp.x * ldrt32);
-                    v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
-                }
-                if (sp.w > 1) {
-                    const uint4 a = *reinterpret_cast<const uint4 *>(rtq + (IT)sp.y * ldrt32);
-                    v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
-                }
-                if (sp.w > 2) {
-                    const uint4 a = *reinterpret_cast<const uint4 *>(rtq + (IT)sp.z * ldrt32);
-                    v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
-                }
-            } else if (sp.w > 3) {
-                // every qubit of the support, from the packed row
-                const IT nw = (n + 63) >> 6;
-                for (IT w = 0; w < nw; ++w) {
-                    uint64_t word = G[j * ldg + w];
-                    if (w == nw - 1 && (n & 63)) word &= (1ull << (n & 63)) - 1ull;
-                    while (word) {
-                        const IT qb = 64 * w + (IT)__ffsll((long long)word) - 1;
-                        word &= word - 1ull;
-                        const uint4 a = *reinterpret_cast<const uint4 *>(rtq + qb * ldrt32);
-                        v.x ^= a.x; v.y ^= a.y; v.z ^= a.z; v.w ^= a.w;
-                    }
-                }
-            }
-            *reinterpret_cast<uint4 *>(PT + j * ldpt32 + w0 + q) = v;
+    for (int i = 0; i < 32; ++i)
+        if ((i & J) == 0) {
+            const uint32_t t = x[i], u = x[i + J];
+            // the shifts as multiplies (low and high word), so that they can run beside the selects
+            x[i] = (t & lo) | ((u * (1u << J)) & ~lo);
+            x[i + J] = (__umulhi(t, 1u << (32 - J)) & lo) | (u & ~lo);
         }
-        tin[row][q] = v.x;
-        tin[row][q + 1] = v.y;
-        tin[row][q + 2] = v.z;
-        tin[row][q + 3] = v.w;
+}
+
+// Transpose a 32 x 32-bit block held as 32 words (bit b of x[i] is element
+// (i, b)) in place: afterwards bit i of x[b] is the former bit b of x[i].
+// In the 16- and 8-bit rounds the halves are whole bytes, and each new word
+// is one byte permute of the pair.
+__device__ __forceinline__ void transpose32(uint32_t (&x)[32]) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        const uint32_t t = x[i], u = x[i + 16];
+        x[i] = __byte_perm(t, u, 0x5410);       // low halves of t and u
+        x[i + 16] = __byte_perm(t, u, 0x7632);  // high halves
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+        if ((i & 8) == 0) {
+            const uint32_t t = x[i], u = x[i + 8];
+            x[i] = __byte_perm(t, u, 0x6240);      // bytes 0 and 2 of t, of u
+            x[i + 8] = __byte_perm(t, u, 0x7351);  // bytes 1 and 3
+        }
+    swap_halves<4>(x, 0x0F0F0F0Fu);
+    swap_halves<2>(x, 0x33333333u);
+    swap_halves<1>(x, 0x55555555u);
+}
+
+// The P^T word of a gate with more than three qubits: the XOR of the R^T
+// words (at rtw, pitch ldrt32) of every qubit of its packed row g.
+template <typename IT>
+__device__ __noinline__ uint32_t gather_wide(const uint64_t *__restrict__ g, IT n, const uint32_t *__restrict__ rtw,
+                                             IT ldrt32, int64_t rt_extent) {
+    uint32_t v = 0u;
+    const IT nw = (n + 63) >> 6;
+    for (IT k = 0; k < nw; ++k) {
+        uint64_t word = g[k];
+        if (k == nw - 1 && (n & 63)) word &= (1ull << (n & 63)) - 1ull;  // never a qubit >= n
+        while (word) {
+            const IT qb = 64 * k + (IT)__ffsll((long long)word) - 1;
+            word &= word - 1ull;
+            if (IQP_IN((int64_t)qb * ldrt32, rt_extent, 8)) v ^= rtw[qb * ldrt32];
+        }
+    }
+    return v;
+}
+
+// The fast pass over a warp's 32 gates (entries e[0..31]): x[i] = the P^T
+// word of gate j0 + i, stored at ptw + i ldrt32 where the lane's word is in
+// the row (wok) and, if CHECK, the gate is below jlim = m - j0. It has no
+// branch, so the loads of later gates can be issued before earlier words are
+// done.
+template <typename IT, bool CHECK>
+__device__ __forceinline__ void gather_fast(uint32_t (&x)[32], const int4 *__restrict__ e,
+                                            const uint32_t *__restrict__ rtw, uint32_t *__restrict__ ptw, IT ldrt32,
+                                            bool wok, IT jlim, int64_t rt_extent, int64_t pt_at, int64_t pt_extent) {
+    constexpr bool kOff = sizeof(IT) == 4;  // entries hold word offsets q ldrt32, else qubits
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int4 ei = e[i];  // the same entry for the whole warp
+        const IT o0 = kOff ? (IT)ei.x : (IT)ei.x * ldrt32, o1 = kOff ? (IT)ei.y : (IT)ei.y * ldrt32,
+                 o2 = kOff ? (IT)ei.z : (IT)ei.z * ldrt32;
+        const uint32_t a0 = IQP_IN((int64_t)o0, rt_extent, 8) ? rtw[o0] : 0u;
+        const uint32_t a1 = IQP_IN((int64_t)o1, rt_extent, 8) ? rtw[o1] : 0u;
+        const uint32_t a2 = IQP_IN((int64_t)o2, rt_extent, 8) ? rtw[o2] : 0u;
+        const uint32_t v = a0 ^ a1 ^ (a2 & (uint32_t)ei.w);
+        if (wok && (!CHECK || (IT)i < jlim) && IQP_IN(pt_at + (int64_t)i * ldrt32, pt_extent, 7))
+            ptw[(IT)i * ldrt32] = v;
+        x[i] = v;
+    }
+}
+
+template <typename IT, int V>
+__global__ void __launch_bounds__(V * 32, 32 / V)
+    k_gather_transpose(const int4 *__restrict__ sup, const uint64_t *__restrict__ G, int64_t ldg_, int64_t n_,
+                       int64_t m_, int64_t rows_, const uint32_t *__restrict__ RT, int64_t ldrt32_,
+                       uint32_t *__restrict__ PT, uint32_t *__restrict__ P, int64_t ldp32_, int64_t gx) {
+    static_assert(V == 8 || V == 16, "a CTA row is V words: 2 or 4 16-byte words");
+    constexpr int NG = V / 4;  // 16-byte words per staged row
+    extern __shared__ __align__(16) uint32_t gt_smem[];
+    uint32_t *sP = gt_smem;
+    int4 *sS = reinterpret_cast<int4 *>(gt_smem + gt_staged_words(V));  // the tile's support entries
+    const IT ldg = (IT)ldg_, n = (IT)n_, m = (IT)m_, rows = (IT)rows_;
+    const IT ldrt32 = (IT)ldrt32_, ldp32 = (IT)ldp32_;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t rt_extent = (int64_t)n * ldrt32;
+    const int64_t bid = blockIdx.x;
+    const IT g0 = (IT)((bid % gx) * 32 * V);    // first gate of this tile
+    const IT w0 = (IT)((bid / gx) * kGtWords);  // first row word of this tile
+    constexpr bool kOff = sizeof(IT) == 4;      // 32-bit word offsets in the entries
+    {
+        // Each gate's entry for the fast pass: three R^T rows and a mask, XORed as
+        // row0 ^ row1 ^ (row2 & mask). One qubit: (q0, q0, q0, ~0); two: (q0, q1, q1, 0); three: (q0, q1, q2,
+        // ~0). A gate with no qubit or more than three is marked by mask 1 and redone from its packed row
+        // after the fast pass; gates past m get zero words. Rows are given as word offsets (q ldrt32) where
+        // those fit in 32 bits, else as qubits.
+        const IT j = g0 + tid;
+        const IT pitch = kOff ? ldrt32 : (IT)1;
+        int4 e = make_int4(0, 0, 0, 0);
+        if (j < m && IQP_IN(j, m, 14)) {
+            const int4 sp = sup[j];
+            const int o0 = (int)((IT)sp.x * pitch), o1 = (int)((IT)sp.y * pitch), o2 = (int)((IT)sp.z * pitch);
+            e = sp.w == 1   ? make_int4(o0, o0, o0, -1)
+                : sp.w == 2 ? make_int4(o0, o1, o1, 0)
+                : sp.w == 3 ? make_int4(o0, o1, o2, -1)
+                            : make_int4(0, 0, 0, 1);
+        }
+        sS[tid] = e;
     }
     __syncthreads();
-    transpose_tile_smem(tin, warp, lane);
-    __syncthreads();
-    const IT ow0 = r0 >> 5;
-    // ldp32 is a multiple of 8 and ow0 + q of 4: whole 16-byte words
-    if (ow0 + q >= ldp32) return;
+    // Lanes past the row read in bounds; their words are never stored: the P rows they would form lie past
+    // `rows` (32 ldrt32 >= rows).
+    const IT w = w0 + lane;
+    const bool wok = w < ldrt32;
+    const uint32_t *rtw = RT + (wok ? w : 0);
+    uint32_t x[32];
+    {
+        const IT j0 = g0 + 32 * warp;
+        uint32_t *ptw = PT + (wok && j0 < m ? j0 * ldrt32 + w : 0);  // dereferenced only for gates below m
+        const int64_t pt_at = (int64_t)j0 * ldrt32 + w, pt_extent = (int64_t)m * ldrt32;
+        if (j0 + 32 <= m)  // every gate of the warp is below m
+            gather_fast<IT, false>(x, sS + 32 * warp, rtw, ptw, ldrt32, wok, m - j0, rt_extent, pt_at, pt_extent);
+        else
+            gather_fast<IT, true>(x, sS + 32 * warp, rtw, ptw, ldrt32, wok, m - j0, rt_extent, pt_at, pt_extent);
+    }
+    const uint32_t wide = __ballot_sync(0xFFFFFFFFu, sS[32 * warp + lane].w == 1);
+    if (wide != 0u) {
 #pragma unroll
-    for (int k = 0; k < kTW / 4; ++k) {
-        const int row = row0 + (kTT / 4) * k;
-        const IT orow = c0 + row;
-        if (orow >= rows) continue;
-        if (IQP_IN((int64_t)orow * ldp32 + ow0 + q + 3, (int64_t)rows * ldp32, 9))
-            *reinterpret_cast<uint4 *>(P + orow * ldp32 + ow0 + q) =
-                make_uint4(tin[row][q], tin[row][q + 1], tin[row][q + 2], tin[row][q + 3]);
+        for (int i = 0; i < 32; ++i)
+            if ((wide >> i) & 1u) {
+                const IT j = g0 + 32 * warp + i;  // < m: entries past m are never marked
+                const uint32_t v = IQP_IN((int64_t)j * ldg, (int64_t)m * ldg, 15)
+                                       ? gather_wide<IT>(G + j * ldg, n, rtw, ldrt32, rt_extent)
+                                       : 0u;
+                if (wok && IQP_IN((int64_t)j * ldrt32 + w, (int64_t)m * ldrt32, 7)) PT[j * ldrt32 + w] = v;
+                x[i] = v;
+            }
+    }
+    transpose32(x);
+    {
+        uint32_t *col = sP + gt_region(V, warp) + 33 * lane;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) col[b] = x[b];
+    }
+    __syncthreads();
+    // Thread t writes 16-byte word t % NG of the tile's row t / NG + 128 k.
+    const int grp = tid % NG;
+    const IT c = (g0 >> 5) + 4 * grp;
+    if (c >= ldp32) return;  // ldp32 and c are multiples of 4: whole 16-byte words
+    const uint32_t *src = sP + gt_region(V, 4 * grp);  // warps 4 grp .. + 3 share the offset of gt_region
+#pragma unroll
+    for (int k = 0; k < kGtRows / 128; ++k) {
+        const int r = tid / NG + 128 * k;  // row of the tile: lane r / 32, word r % 32
+        const IT row = 32 * w0 + r;
+        if (row >= rows) break;
+        const int pos = r + (r >> 5);
+        const uint4 o = make_uint4(src[pos], src[33 * 32 + pos], src[2 * 33 * 32 + pos], src[3 * 33 * 32 + pos]);
+        if (IQP_IN((int64_t)row * ldp32 + c + 3, (int64_t)rows * ldp32, 9))
+            *reinterpret_cast<uint4 *>(P + row * ldp32 + c) = o;
     }
 }
 
@@ -467,35 +580,71 @@ cudaError_t launch_support_list(const uint64_t *G, int64_t m, int64_t ldg, int64
     return cudaGetLastError();
 }
 
+// Warps per CTA of the fused gather (IQP_GATHER_WARPS, 8 or 16; default 8:
+// four CTAs per SM, whose phases interleave better than two CTAs of 16).
+int gather_warps() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = std::getenv("IQP_GATHER_WARPS");
+        v = (e != nullptr && std::atoi(e) == 16) ? 16 : 8;
+    }
+    return v;
+}
+
+template <int V>
+cudaError_t launch_gather_transpose(bool i32, int64_t gx, int64_t gy, const int4 *sup, const uint64_t *G,
+                                    int64_t ldg, int64_t n, int64_t m, int64_t rows, const uint32_t *rt32,
+                                    int64_t ldrt32, uint32_t *pt32, uint32_t *p32, int64_t ldp32, cudaStream_t st) {
+    constexpr int smem = gt_smem_bytes(V);
+    static bool attr_set[2] = {false, false};
+    if (!attr_set[i32]) {
+        const cudaError_t e =
+            i32 ? cudaFuncSetAttribute(k_gather_transpose<int32_t, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem)
+                : cudaFuncSetAttribute(k_gather_transpose<int64_t, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem);
+        if (e != cudaSuccess) return e;
+        attr_set[i32] = true;
+    }
+    LaunchScope ls(IQP_KERNEL_PARITY, st);
+    if (i32)
+        k_gather_transpose<int32_t, V><<<(unsigned)(gx * gy), V * 32, smem, st>>>(sup, G, ldg, n, m, rows, rt32,
+                                                                                 ldrt32, pt32, p32, ldp32, gx);
+    else
+        k_gather_transpose<int64_t, V><<<(unsigned)(gx * gy), V * 32, smem, st>>>(sup, G, ldg, n, m, rows, rt32,
+                                                                                 ldrt32, pt32, p32, ldp32, gx);
+    return cudaGetLastError();
+}
+
 // Support-gather parities: RT (n x ldpt words) is scratch; writes PT
 // (m x ldpt words: bits over rows, zero beyond `rows`) and, if P != nullptr,
 // P (rows x ldp words: bits over gates, zero beyond m). With the gates'
-// support list `sup` (and ldpt, ldp multiples of 4) P^T and P come from one
-// fused pass; without it P^T is gathered, then transposed into P.
+// support list `sup` (and ldp even) P^T and P come from one fused pass;
+// without it P^T is gathered, then transposed into P.
 cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G,
                                  int64_t m, int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
                                  uint64_t *RT, cudaStream_t st, const int4 *sup) {
     cudaError_t e = bit_transpose(R, rows, n, ldr, RT, ldpt, st);
     if (e != cudaSuccess) return e;
-    if (sup != nullptr && P != nullptr && ldpt % 4 == 0 && ldp % 4 == 0) {
-        // with the gates' support list (launch_support_list): P^T and P from one pass
-        const int64_t gx = cdiv(m, kTT);
-        const int64_t gy = cdiv(rows, kTT);
+    if (sup != nullptr && P != nullptr && ldp % 2 == 0) {
+        // with the gates' support list (launch_support_list): P^T and P from one pass. The tiles cover
+        // every word of P (gates past m give zero words) and of P^T.
+        const int64_t tg = 32 * gather_warps();  // gates per tile
+        int64_t gx = cdiv(m, tg);
+        if (gx < cdiv(2 * ldp, tg / 32)) gx = cdiv(2 * ldp, tg / 32);
+        const int64_t gy = cdiv(2 * ldpt, kGtWords);
         if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
         // 32-bit element indices where every one of this launch fits
         const int64_t lim = (int64_t)1 << 31;
         const bool i32 = m * 2 * ldpt < lim && rows * 2 * ldp < lim && n * 2 * ldpt < lim && m * ldg < lim &&
-                         gx * kTT < lim && gy * kTT < lim;
-        LaunchScope ls(IQP_KERNEL_PARITY, st);
-        if (i32)
-            k_gather_transpose<int32_t><<<(unsigned)(gx * gy), kTT, 0, st>>>(
-                sup, G, ldg, n, m, rows, reinterpret_cast<const uint32_t *>(RT), 2 * ldpt,
-                reinterpret_cast<uint32_t *>(PT), 2 * ldpt, reinterpret_cast<uint32_t *>(P), 2 * ldp, gx);
-        else
-            k_gather_transpose<int64_t><<<(unsigned)(gx * gy), kTT, 0, st>>>(
-                sup, G, ldg, n, m, rows, reinterpret_cast<const uint32_t *>(RT), 2 * ldpt,
-                reinterpret_cast<uint32_t *>(PT), 2 * ldpt, reinterpret_cast<uint32_t *>(P), 2 * ldp, gx);
-        return cudaGetLastError();
+                         gx * tg < lim && gy * kGtRows < lim;
+        const uint32_t *rt32 = reinterpret_cast<const uint32_t *>(RT);
+        uint32_t *pt32 = reinterpret_cast<uint32_t *>(PT), *p32 = reinterpret_cast<uint32_t *>(P);
+        if (gather_warps() == 8)
+            return launch_gather_transpose<8>(i32, gx, gy, sup, G, ldg, n, m, rows, rt32, 2 * ldpt, pt32, p32,
+                                              2 * ldp, st);
+        return launch_gather_transpose<16>(i32, gx, gy, sup, G, ldg, n, m, rows, rt32, 2 * ldpt, pt32, p32, 2 * ldp,
+                                           st);
     }
     {
         dim3 grid((unsigned)cdiv(m, 8), (unsigned)cdiv(ldpt, 256));

@@ -84,7 +84,8 @@ def test_parity_bit_exact(api, n, m, rows):
 
 
 @pytest.mark.parametrize("n,m,rows,dense", [(1, 1, 1, False), (63, 65, 33, False), (130, 300, 257, False),
-                                            (300, 1000, 700, False), (5000, 513, 40, False), (777, 300, 129, True)])
+                                            (300, 1000, 700, False), (5000, 513, 40, False), (777, 300, 129, True),
+                                            (200, 1100, 2100, False), (1000, 1537, 1025, False)])
 def test_parity_gather_bit_exact(api, n, m, rows, dense):
     rng = I.Rng(300 + n)
     R = I.bernoulli_bits(rng, rows, n, 0.5, 1)
