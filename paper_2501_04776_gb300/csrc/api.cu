@@ -17,6 +17,8 @@ cudaError_t launch_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ld
 cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G,
                                  int64_t m, int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
                                  uint64_t *RT, cudaStream_t st, const int4 *sup = nullptr);
+cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const int4 *sup,
+                                       int64_t ldp, const ParitySide *side, int nside, cudaStream_t st);
 cudaError_t launch_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,
                               int64_t ldx, int64_t *T, cudaStream_t st);
 cudaError_t launch_theta_prep(const float *theta, int64_t m, int64_t mpad, float *c32, __nv_bfloat16 *hi,
@@ -136,7 +138,7 @@ Plan make_plan(int op, int64_t n, int64_t m, int64_t l, int64_t s, int64_t N, in
     p.off_pz = take(bitflip || sparse || lo ? 0 : s * p.ldp * 8);
     p.off_pzt = take(bitflip || indep ? 0 : (lo ? n : m) * p.ldzt * 8);  // low-order: the samples transposed
     p.off_pat = take(lo ? 0 : m * p.ldlt * 8);
-    p.off_rt = take(n * (p.ldzt > p.ldlt ? p.ldzt : p.ldlt) * 8);
+    p.off_rt = take(n * (p.ldzt + p.ldlt) * 8);  // R^T of A, then of Z (one fused parity launch for both)
     p.off_c = take(bitflip ? p.mpad * 16 : p.mpad * 4);  // bitflip: cos(2 theta), -2 tan(2 theta) in FP64
     p.off_part = take(bitflip ? l * 16 : l * p.nparts * 16);  // bitflip: expval, w * expval
     p.off_w = take(grad && !sparse ? l * p.ldw * 4 : 0);
@@ -343,6 +345,20 @@ iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, cons
     }
     const int4 *sup = at<int4>(ws, p.off_sup);
     IQP_TRY(launch_support_list(G, p.m, ldg, p.n, at<int4>(ws, p.off_sup), st));
+    if (!p.indep && p.prec != IQP_SPARSE_FP32) {
+        // P_A, P_A^T, P_Z, P_Z^T: both transposes in one launch, both gathers in one launch
+        const ParitySide sides[2] = {
+            {A, p.l, lda, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pat), p.ldlt, rt},
+            {Z, p.s, ldz, at<uint64_t>(ws, p.off_pz), at<uint64_t>(ws, p.off_pzt), p.ldzt, rt + p.n * p.ldlt}};
+        IQP_TRY(launch_parity_gather_fused(p.n, G, p.m, ldg, sup, p.ldp, sides, 2, st));
+        if (p.prec == IQP_SPLIT_BF16) {
+            __nv_bfloat16 *hi = at<__nv_bfloat16>(ws, p.off_c);
+            IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, nullptr, hi, hi + p.mpad, st));
+        } else {
+            IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, at<float>(ws, p.off_c), nullptr, nullptr, st));
+        }
+        return IQP_OK;
+    }
     IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
                                  at<uint64_t>(ws, p.off_pat), p.ldlt, rt, st, sup));
     if (p.indep) {

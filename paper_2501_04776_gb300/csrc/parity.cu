@@ -174,15 +174,12 @@ __device__ __forceinline__ void transpose_tile_smem(uint32_t (*tin)[kTW + 1], in
     }
 }
 
-__global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restrict__ in, int64_t in_rows,
-                                                        int64_t in_cols, int64_t ld_in32,
-                                                        uint32_t *__restrict__ out, int64_t ld_out32, int64_t gx,
-                                                        int64_t in_bs32, int64_t out_bs32) {
-    in += (int64_t)blockIdx.y * in_bs32;
-    out += (int64_t)blockIdx.y * out_bs32;
-    __shared__ uint32_t tin[kTT][kTW + 1];  // transposed in place
+// One 512 x 512-bit tile (number bid) of the bit transpose, staged in tin.
+__device__ __forceinline__ void bit_transpose_tile(uint32_t (*tin)[kTW + 1], const uint32_t *__restrict__ in,
+                                                   int64_t in_rows, int64_t in_cols, int64_t ld_in32,
+                                                   uint32_t *__restrict__ out, int64_t ld_out32, int64_t gx,
+                                                   int64_t bid) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t bid = blockIdx.x;
     const int64_t r0 = (bid % gx) * kTT;   // input rows = output bit columns
     const int64_t c0 = (bid / gx) * kTT;   // input bit columns = output rows
     const int64_t w0 = c0 >> 5;
@@ -234,6 +231,31 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
                 if (ow0 + q + e < ld_out32) out[orow * ld_out32 + ow0 + q + e] = tin[row][q + e];
         }
     }
+}
+
+__global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restrict__ in, int64_t in_rows,
+                                                        int64_t in_cols, int64_t ld_in32,
+                                                        uint32_t *__restrict__ out, int64_t ld_out32, int64_t gx,
+                                                        int64_t in_bs32, int64_t out_bs32) {
+    __shared__ uint32_t tin[kTT][kTW + 1];  // transposed in place
+    bit_transpose_tile(tin, in + (int64_t)blockIdx.y * in_bs32, in_rows, in_cols, ld_in32,
+                       out + (int64_t)blockIdx.y * out_bs32, ld_out32, gx, blockIdx.x);
+}
+
+// Two bit transposes of different shapes in one launch: blocks [0, tiles0)
+// take the first, the rest the second.
+struct BitTransposeJob {
+    const uint32_t *in;
+    int64_t in_rows, in_cols, ld_in32;
+    uint32_t *out;
+    int64_t ld_out32, gx, tiles;
+};
+__global__ void __launch_bounds__(kTT) k_bit_transpose_two(BitTransposeJob a, BitTransposeJob b) {
+    __shared__ uint32_t tin[kTT][kTW + 1];  // transposed in place
+    const bool second = (int64_t)blockIdx.x >= a.tiles;
+    bit_transpose_tile(tin, second ? b.in : a.in, second ? b.in_rows : a.in_rows, second ? b.in_cols : a.in_cols,
+                       second ? b.ld_in32 : a.ld_in32, second ? b.out : a.out, second ? b.ld_out32 : a.ld_out32,
+                       second ? b.gx : a.gx, (int64_t)blockIdx.x - (second ? a.tiles : 0));
 }
 
 // Support gather and transpose in one pass, one thread per 32 x 32-bit block.
@@ -346,11 +368,25 @@ __device__ __forceinline__ void gather_fast(uint32_t (&x)[32], const int4 *__res
     }
 }
 
+// One row matrix of the fused gather: its R^T (n x ldrt32 words), P^T and P,
+// and the number of tiles (gx x gy) it takes.
+struct GatherSide {
+    const uint32_t *RT;
+    uint32_t *PT, *P;
+    int64_t rows, ldrt32, tiles;
+};
+
+// Blocks [0, s0.tiles) take side s0, the rest side s1 (the observables' and
+// the samples' parities of one call share the gates and their support list).
 template <typename IT, int V>
 __global__ void __launch_bounds__(V * 32, 32 / V)
     k_gather_transpose(const int4 *__restrict__ sup, const uint64_t *__restrict__ G, int64_t ldg_, int64_t n_,
-                       int64_t m_, int64_t rows_, const uint32_t *__restrict__ RT, int64_t ldrt32_,
-                       uint32_t *__restrict__ PT, uint32_t *__restrict__ P, int64_t ldp32_, int64_t gx) {
+                       int64_t m_, GatherSide s0, GatherSide s1, int64_t ldp32_, int64_t gx) {
+    const bool second = (int64_t)blockIdx.x >= s0.tiles;
+    const uint32_t *__restrict__ RT = second ? s1.RT : s0.RT;
+    uint32_t *__restrict__ PT = second ? s1.PT : s0.PT;
+    uint32_t *__restrict__ P = second ? s1.P : s0.P;
+    const int64_t rows_ = second ? s1.rows : s0.rows, ldrt32_ = second ? s1.ldrt32 : s0.ldrt32;
     static_assert(V == 8 || V == 16, "a CTA row is V words: 2 or 4 16-byte words");
     constexpr int NG = V / 4;  // 16-byte words per staged row
     extern __shared__ __align__(16) uint32_t gt_smem[];
@@ -360,7 +396,7 @@ __global__ void __launch_bounds__(V * 32, 32 / V)
     const IT ldrt32 = (IT)ldrt32_, ldp32 = (IT)ldp32_;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t rt_extent = (int64_t)n * ldrt32;
-    const int64_t bid = blockIdx.x;
+    const int64_t bid = (int64_t)blockIdx.x - (second ? s0.tiles : 0);
     const IT g0 = (IT)((bid % gx) * 32 * V);    // first gate of this tile
     const IT w0 = (IT)((bid / gx) * kGtWords);  // first row word of this tile
     constexpr bool kOff = sizeof(IT) == 4;      // 32-bit word offsets in the entries
@@ -592,9 +628,9 @@ int gather_warps() {
 }
 
 template <int V>
-cudaError_t launch_gather_transpose(bool i32, int64_t gx, int64_t gy, const int4 *sup, const uint64_t *G,
-                                    int64_t ldg, int64_t n, int64_t m, int64_t rows, const uint32_t *rt32,
-                                    int64_t ldrt32, uint32_t *pt32, uint32_t *p32, int64_t ldp32, cudaStream_t st) {
+cudaError_t launch_gather_transpose(bool i32, int64_t gx, const int4 *sup, const uint64_t *G, int64_t ldg, int64_t n,
+                                    int64_t m, const GatherSide &s0, const GatherSide &s1, int64_t ldp32,
+                                    cudaStream_t st) {
     constexpr int smem = gt_smem_bytes(V);
     static bool attr_set[2] = {false, false};
     if (!attr_set[i32]) {
@@ -606,14 +642,52 @@ cudaError_t launch_gather_transpose(bool i32, int64_t gx, int64_t gy, const int4
         if (e != cudaSuccess) return e;
         attr_set[i32] = true;
     }
+    const int64_t blocks = s0.tiles + s1.tiles;
+    if (blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
     LaunchScope ls(IQP_KERNEL_PARITY, st);
     if (i32)
-        k_gather_transpose<int32_t, V><<<(unsigned)(gx * gy), V * 32, smem, st>>>(sup, G, ldg, n, m, rows, rt32,
-                                                                                 ldrt32, pt32, p32, ldp32, gx);
+        k_gather_transpose<int32_t, V><<<(unsigned)blocks, V * 32, smem, st>>>(sup, G, ldg, n, m, s0, s1, ldp32, gx);
     else
-        k_gather_transpose<int64_t, V><<<(unsigned)(gx * gy), V * 32, smem, st>>>(sup, G, ldg, n, m, rows, rt32,
-                                                                                 ldrt32, pt32, p32, ldp32, gx);
+        k_gather_transpose<int64_t, V><<<(unsigned)blocks, V * 32, smem, st>>>(sup, G, ldg, n, m, s0, s1, ldp32, gx);
     return cudaGetLastError();
+}
+
+// Fused support-gather parities of one or two row matrices sharing the gates
+// G and their support list `sup` (ldp even; ldpt of each side even): both
+// R^T in one launch, then P^T and P of both in one launch.
+cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const int4 *sup,
+                                       int64_t ldp, const ParitySide *side, int nside, cudaStream_t st) {
+    if (nside < 1 || nside > 2 || ldp % 2 != 0) return cudaErrorInvalidValue;
+    BitTransposeJob bt[2] = {};
+    for (int k = 0; k < nside; ++k) {
+        const ParitySide &d = side[k];
+        bt[k] = BitTransposeJob{reinterpret_cast<const uint32_t *>(d.R), d.rows, n, 2 * d.ldr,
+                                reinterpret_cast<uint32_t *>(d.RT), 2 * d.ldpt, cdiv(d.ldpt * 64, kTT), 0};
+        bt[k].tiles = bt[k].gx * cdiv(n, kTT);
+    }
+    if (bt[0].tiles + bt[1].tiles > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+    {
+        LaunchScope ls(IQP_KERNEL_PARITY, st);
+        k_bit_transpose_two<<<(unsigned)(bt[0].tiles + bt[1].tiles), kTT, 0, st>>>(bt[0], bt[1]);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // The tiles cover every word of P (gates past m give zero words) and of P^T.
+    const int V = gather_warps(), tg = 32 * V;  // gates per tile
+    int64_t gx = cdiv(m, tg);
+    if (gx < cdiv(2 * ldp, tg / 32)) gx = cdiv(2 * ldp, tg / 32);
+    GatherSide gs[2] = {};
+    const int64_t lim = (int64_t)1 << 31;
+    bool i32 = m * ldg < lim && gx * tg < lim;  // 32-bit element indices where every one of the launch fits
+    for (int k = 0; k < nside; ++k) {
+        const ParitySide &d = side[k];
+        const int64_t gy = cdiv(2 * d.ldpt, kGtWords);
+        gs[k] = GatherSide{reinterpret_cast<const uint32_t *>(d.RT), reinterpret_cast<uint32_t *>(d.PT),
+                           reinterpret_cast<uint32_t *>(d.P), d.rows, 2 * d.ldpt, gx * gy};
+        i32 = i32 && m * 2 * d.ldpt < lim && d.rows * 2 * ldp < lim && n * 2 * d.ldpt < lim && gy * kGtRows < lim;
+    }
+    if (V == 16) return launch_gather_transpose<16>(i32, gx, sup, G, ldg, n, m, gs[0], gs[1], 2 * ldp, st);
+    return launch_gather_transpose<8>(i32, gx, sup, G, ldg, n, m, gs[0], gs[1], 2 * ldp, st);
 }
 
 // Support-gather parities: RT (n x ldpt words) is scratch; writes PT
@@ -624,28 +698,13 @@ cudaError_t launch_gather_transpose(bool i32, int64_t gx, int64_t gy, const int4
 cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G,
                                  int64_t m, int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
                                  uint64_t *RT, cudaStream_t st, const int4 *sup) {
+    if (sup != nullptr && P != nullptr && ldp % 2 == 0) {
+        // with the gates' support list (launch_support_list): P^T and P from one pass
+        const ParitySide side{R, rows, ldr, P, PT, ldpt, RT};
+        return launch_parity_gather_fused(n, G, m, ldg, sup, ldp, &side, 1, st);
+    }
     cudaError_t e = bit_transpose(R, rows, n, ldr, RT, ldpt, st);
     if (e != cudaSuccess) return e;
-    if (sup != nullptr && P != nullptr && ldp % 2 == 0) {
-        // with the gates' support list (launch_support_list): P^T and P from one pass. The tiles cover
-        // every word of P (gates past m give zero words) and of P^T.
-        const int64_t tg = 32 * gather_warps();  // gates per tile
-        int64_t gx = cdiv(m, tg);
-        if (gx < cdiv(2 * ldp, tg / 32)) gx = cdiv(2 * ldp, tg / 32);
-        const int64_t gy = cdiv(2 * ldpt, kGtWords);
-        if (gx * gy > 0x7FFFFFFFll) return cudaErrorInvalidValue;
-        // 32-bit element indices where every one of this launch fits
-        const int64_t lim = (int64_t)1 << 31;
-        const bool i32 = m * 2 * ldpt < lim && rows * 2 * ldp < lim && n * 2 * ldpt < lim && m * ldg < lim &&
-                         gx * tg < lim && gy * kGtRows < lim;
-        const uint32_t *rt32 = reinterpret_cast<const uint32_t *>(RT);
-        uint32_t *pt32 = reinterpret_cast<uint32_t *>(PT), *p32 = reinterpret_cast<uint32_t *>(P);
-        if (gather_warps() == 8)
-            return launch_gather_transpose<8>(i32, gx, gy, sup, G, ldg, n, m, rows, rt32, 2 * ldpt, pt32, p32,
-                                              2 * ldp, st);
-        return launch_gather_transpose<16>(i32, gx, gy, sup, G, ldg, n, m, rows, rt32, 2 * ldpt, pt32, p32, 2 * ldp,
-                                           st);
-    }
     {
         dim3 grid((unsigned)cdiv(m, 8), (unsigned)cdiv(ldpt, 256));
         LaunchScope ls(IQP_KERNEL_PARITY, st);
