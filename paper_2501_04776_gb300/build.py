@@ -36,7 +36,7 @@ def nvcc() -> str:
 def _stale(obj: str, src: str) -> bool:
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "common.cuh"), os.path.join(INCLUDE, "iqp.h")]
+    deps = [src, os.path.join(INCLUDE, "iqp.h")] + [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "parity.cuh"
 
 namespace iqp {
 
@@ -17,8 +18,6 @@ cudaError_t launch_parity(int64_t n, const uint64_t *R, int64_t rows, int64_t ld
 cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int64_t ldr, const uint64_t *G,
                                  int64_t m, int64_t ldg, uint64_t *P, int64_t ldp, uint64_t *PT, int64_t ldpt,
                                  uint64_t *RT, cudaStream_t st, const int4 *sup = nullptr);
-cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const int4 *sup,
-                                       int64_t ldp, const ParitySide *side, int nside, cudaStream_t st);
 cudaError_t launch_parity_sum(int64_t n, const uint64_t *A, int64_t l, int64_t lda, const uint64_t *X, int64_t N,
                               int64_t ldx, int64_t *T, cudaStream_t st);
 cudaError_t launch_theta_prep(const float *theta, int64_t m, int64_t mpad, float *c32, __nv_bfloat16 *hi,

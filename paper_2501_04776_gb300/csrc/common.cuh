@@ -131,17 +131,6 @@ static inline uint32_t take_check_word() {
 static inline uint32_t take_check_word() { return 0u; }
 #endif
 
-// One row matrix R (rows x ldr words) of a fused parity call
-// (launch_parity_gather_fused): its R^T scratch (n x ldpt words), P^T
-// (m x ldpt) and P (rows x ldp).
-struct ParitySide {
-    const uint64_t *R;
-    int64_t rows, ldr;
-    uint64_t *P, *PT;
-    int64_t ldpt;
-    uint64_t *RT;
-};
-
 // Host-side launch accounting (iqp_launch_count) and optional per-kernel
 // event timing (iqp_profile_*). Construct one right before each launch.
 struct LaunchScope {

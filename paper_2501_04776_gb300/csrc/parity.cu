@@ -6,6 +6,7 @@
 #include <cstdlib>
 
 #include "common.cuh"
+#include "parity.cuh"
 
 namespace iqp {
 
@@ -652,9 +653,6 @@ cudaError_t launch_gather_transpose(bool i32, int64_t gx, const int4 *sup, const
     return cudaGetLastError();
 }
 
-// Fused support-gather parities of one or two row matrices sharing the gates
-// G and their support list `sup` (ldp even; ldpt of each side even): both
-// R^T in one launch, then P^T and P of both in one launch.
 cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const int4 *sup,
                                        int64_t ldp, const ParitySide *side, int nside, cudaStream_t st) {
     if (nside < 1 || nside > 2 || ldp % 2 != 0) return cudaErrorInvalidValue;
