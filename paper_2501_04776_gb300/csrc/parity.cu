@@ -347,22 +347,39 @@ __device__ __noinline__ uint32_t gather_wide(const uint64_t *__restrict__ g, IT 
 // The fast pass over a warp's 32 gates (entries e[0..31]): x[i] = the P^T
 // word of gate j0 + i, stored at ptw + i ldrt32 where the lane's word is in
 // the row (wok) and, if CHECK, the gate is below jlim = m - j0. It has no
-// branch, so the loads of later gates can be issued before earlier words are
-// done.
+// branch, and the three loads of gate i + kGtDepth are issued before gate i
+// is combined, so kGtDepth gates' loads are in flight behind the latency of
+// the L2.
+#ifndef IQP_GT_DEPTH
+#define IQP_GT_DEPTH 4  // 2: the same time; 8 (96 registers, half the CTAs per SM): 12% slower
+#endif
+#ifndef IQP_GT_WARPS_PER_SM
+#define IQP_GT_WARPS_PER_SM 32  // the register file's limit at 64 registers per thread
+#endif
+constexpr int kGtDepth = IQP_GT_DEPTH;
+__host__ __device__ constexpr int kGtMinBlocks(int V) { return IQP_GT_WARPS_PER_SM / V; }
 template <typename IT, bool CHECK>
 __device__ __forceinline__ void gather_fast(uint32_t (&x)[32], const int4 *__restrict__ e,
                                             const uint32_t *__restrict__ rtw, uint32_t *__restrict__ ptw, IT ldrt32,
                                             bool wok, IT jlim, int64_t rt_extent, int64_t pt_at, int64_t pt_extent) {
     constexpr bool kOff = sizeof(IT) == 4;  // entries hold word offsets q ldrt32, else qubits
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
+    uint32_t r0[kGtDepth], r1[kGtDepth], r2[kGtDepth], mk[kGtDepth];
+    auto issue = [&](int i, int slot) {
         const int4 ei = e[i];  // the same entry for the whole warp
         const IT o0 = kOff ? (IT)ei.x : (IT)ei.x * ldrt32, o1 = kOff ? (IT)ei.y : (IT)ei.y * ldrt32,
                  o2 = kOff ? (IT)ei.z : (IT)ei.z * ldrt32;
-        const uint32_t a0 = IQP_IN((int64_t)o0, rt_extent, 8) ? rtw[o0] : 0u;
-        const uint32_t a1 = IQP_IN((int64_t)o1, rt_extent, 8) ? rtw[o1] : 0u;
-        const uint32_t a2 = IQP_IN((int64_t)o2, rt_extent, 8) ? rtw[o2] : 0u;
-        const uint32_t v = a0 ^ a1 ^ (a2 & (uint32_t)ei.w);
+        r0[slot] = IQP_IN((int64_t)o0, rt_extent, 8) ? rtw[o0] : 0u;
+        r1[slot] = IQP_IN((int64_t)o1, rt_extent, 8) ? rtw[o1] : 0u;
+        r2[slot] = IQP_IN((int64_t)o2, rt_extent, 8) ? rtw[o2] : 0u;
+        mk[slot] = (uint32_t)ei.w;
+    };
+#pragma unroll
+    for (int d = 0; d < kGtDepth; ++d) issue(d, d);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const int slot = i % kGtDepth;
+        const uint32_t v = r0[slot] ^ r1[slot] ^ (r2[slot] & mk[slot]);
+        if (i + kGtDepth < 32) issue(i + kGtDepth, slot);
         if (wok && (!CHECK || (IT)i < jlim) && IQP_IN(pt_at + (int64_t)i * ldrt32, pt_extent, 7))
             ptw[(IT)i * ldrt32] = v;
         x[i] = v;
@@ -380,7 +397,7 @@ struct GatherSide {
 // Blocks [0, s0.tiles) take side s0, the rest side s1 (the observables' and
 // the samples' parities of one call share the gates and their support list).
 template <typename IT, int V>
-__global__ void __launch_bounds__(V * 32, 32 / V)
+__global__ void __launch_bounds__(V * 32, kGtMinBlocks(V))
     k_gather_transpose(const int4 *__restrict__ sup, const uint64_t *__restrict__ G, int64_t ldg_, int64_t n_,
                        int64_t m_, GatherSide s0, GatherSide s1, int64_t ldp32_, int64_t gx) {
     const bool second = (int64_t)blockIdx.x >= s0.tiles;
