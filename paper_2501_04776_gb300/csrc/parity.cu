@@ -347,9 +347,9 @@ __device__ __noinline__ uint32_t gather_wide(const uint64_t *__restrict__ g, IT 
 // The fast pass over a warp's 32 gates (entries e[0..31]): x[i] = the P^T
 // word of gate j0 + i, stored at ptw + i ldrt32 where the lane's word is in
 // the row (wok) and, if CHECK, the gate is below jlim = m - j0. It has no
-// branch, and the three loads of gate i + kGtDepth are issued before gate i
-// is combined, so kGtDepth gates' loads are in flight behind the latency of
-// the L2.
+// branch: a gate's three loads are predicated on its weight. The loads of
+// gate i + kGtDepth are issued before gate i is combined, so kGtDepth gates'
+// loads are in flight behind the latency of the L2.
 #ifndef IQP_GT_DEPTH
 #define IQP_GT_DEPTH 4  // 2: the same time; 8 (96 registers, half the CTAs per SM): 12% slower
 #endif
@@ -363,22 +363,22 @@ __device__ __forceinline__ void gather_fast(uint32_t (&x)[32], const int4 *__res
                                             const uint32_t *__restrict__ rtw, uint32_t *__restrict__ ptw, IT ldrt32,
                                             bool wok, IT jlim, int64_t rt_extent, int64_t pt_at, int64_t pt_extent) {
     constexpr bool kOff = sizeof(IT) == 4;  // entries hold word offsets q ldrt32, else qubits
-    uint32_t r0[kGtDepth], r1[kGtDepth], r2[kGtDepth], mk[kGtDepth];
+    uint32_t r0[kGtDepth], r1[kGtDepth], r2[kGtDepth];
     auto issue = [&](int i, int slot) {
         const int4 ei = e[i];  // the same entry for the whole warp
         const IT o0 = kOff ? (IT)ei.x : (IT)ei.x * ldrt32, o1 = kOff ? (IT)ei.y : (IT)ei.y * ldrt32,
                  o2 = kOff ? (IT)ei.z : (IT)ei.z * ldrt32;
-        r0[slot] = IQP_IN((int64_t)o0, rt_extent, 8) ? rtw[o0] : 0u;
-        r1[slot] = IQP_IN((int64_t)o1, rt_extent, 8) ? rtw[o1] : 0u;
-        r2[slot] = IQP_IN((int64_t)o2, rt_extent, 8) ? rtw[o2] : 0u;
-        mk[slot] = (uint32_t)ei.w;
+        const int c = ei.w & 3;  // the loads past the gate's weight are predicated off: no L1 work
+        r0[slot] = c >= 1 && IQP_IN((int64_t)o0, rt_extent, 8) ? rtw[o0] : 0u;
+        r1[slot] = c >= 2 && IQP_IN((int64_t)o1, rt_extent, 8) ? rtw[o1] : 0u;
+        r2[slot] = c >= 3 && IQP_IN((int64_t)o2, rt_extent, 8) ? rtw[o2] : 0u;
     };
 #pragma unroll
     for (int d = 0; d < kGtDepth; ++d) issue(d, d);
 #pragma unroll
     for (int i = 0; i < 32; ++i) {
         const int slot = i % kGtDepth;
-        const uint32_t v = r0[slot] ^ r1[slot] ^ (r2[slot] & mk[slot]);
+        const uint32_t v = r0[slot] ^ r1[slot] ^ r2[slot];
         if (i + kGtDepth < 32) issue(i + kGtDepth, slot);
         if (wok && (!CHECK || (IT)i < jlim) && IQP_IN(pt_at + (int64_t)i * ldrt32, pt_extent, 7))
             ptw[(IT)i * ldrt32] = v;
@@ -419,21 +419,17 @@ __global__ void __launch_bounds__(V * 32, kGtMinBlocks(V))
     const IT w0 = (IT)((bid / gx) * kGtWords);  // first row word of this tile
     constexpr bool kOff = sizeof(IT) == 4;      // 32-bit word offsets in the entries
     {
-        // Each gate's entry for the fast pass: three R^T rows and a mask, XORed as
-        // row0 ^ row1 ^ (row2 & mask). One qubit: (q0, q0, q0, ~0); two: (q0, q1, q1, 0); three: (q0, q1, q2,
-        // ~0). A gate with no qubit or more than three is marked by mask 1 and redone from its packed row
-        // after the fast pass; gates past m get zero words. Rows are given as word offsets (q ldrt32) where
-        // those fit in 32 bits, else as qubits.
+        // Each gate's entry for the fast pass: its first three R^T rows and its weight c (1..3); the pass
+        // XORs rows 0 .. c - 1. A gate with no qubit or more than three is marked by 4 and redone from its
+        // packed row after the fast pass; gates past m get zero words (weight 0). Rows are given as word
+        // offsets (q ldrt32) where those fit in 32 bits, else as qubits.
         const IT j = g0 + tid;
         const IT pitch = kOff ? ldrt32 : (IT)1;
         int4 e = make_int4(0, 0, 0, 0);
         if (j < m && IQP_IN(j, m, 14)) {
             const int4 sp = sup[j];
             const int o0 = (int)((IT)sp.x * pitch), o1 = (int)((IT)sp.y * pitch), o2 = (int)((IT)sp.z * pitch);
-            e = sp.w == 1   ? make_int4(o0, o0, o0, -1)
-                : sp.w == 2 ? make_int4(o0, o1, o1, 0)
-                : sp.w == 3 ? make_int4(o0, o1, o2, -1)
-                            : make_int4(0, 0, 0, 1);
+            e = sp.w >= 1 && sp.w <= 3 ? make_int4(o0, o1, o2, sp.w) : make_int4(0, 0, 0, 4);
         }
         sS[tid] = e;
     }
@@ -453,7 +449,7 @@ __global__ void __launch_bounds__(V * 32, kGtMinBlocks(V))
         else
             gather_fast<IT, true>(x, sS + 32 * warp, rtw, ptw, ldrt32, wok, m - j0, rt_extent, pt_at, pt_extent);
     }
-    const uint32_t wide = __ballot_sync(0xFFFFFFFFu, sS[32 * warp + lane].w == 1);
+    const uint32_t wide = __ballot_sync(0xFFFFFFFFu, sS[32 * warp + lane].w == 4);
     if (wide != 0u) {
 #pragma unroll
         for (int i = 0; i < 32; ++i)
