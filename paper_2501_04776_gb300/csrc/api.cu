@@ -343,13 +343,12 @@ iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, cons
         return IQP_OK;
     }
     const int4 *sup = at<int4>(ws, p.off_sup);
-    IQP_TRY(launch_support_list(G, p.m, ldg, p.n, at<int4>(ws, p.off_sup), st));
     if (!p.indep && p.prec != IQP_SPARSE_FP32) {
-        // P_A, P_A^T, P_Z, P_Z^T: both transposes in one launch, both gathers in one launch
+        // P_A, P_A^T, P_Z, P_Z^T: the support list with both transposes in one launch, both gathers in one
         const ParitySide sides[2] = {
             {A, p.l, lda, at<uint64_t>(ws, p.off_pa), at<uint64_t>(ws, p.off_pat), p.ldlt, rt},
             {Z, p.s, ldz, at<uint64_t>(ws, p.off_pz), at<uint64_t>(ws, p.off_pzt), p.ldzt, rt + p.n * p.ldlt}};
-        IQP_TRY(launch_parity_gather_fused(p.n, G, p.m, ldg, sup, p.ldp, sides, 2, st));
+        IQP_TRY(launch_parity_gather_fused(p.n, G, p.m, ldg, at<int4>(ws, p.off_sup), true, p.ldp, sides, 2, st));
         if (p.prec == IQP_SPLIT_BF16) {
             __nv_bfloat16 *hi = at<__nv_bfloat16>(ws, p.off_c);
             IQP_TRY(launch_theta_prep(theta, p.m, p.mpad, nullptr, hi, hi + p.mpad, st));
@@ -358,6 +357,7 @@ iqp_status prepare(const Plan &p, void *ws, const uint64_t *G, int64_t ldg, cons
         }
         return IQP_OK;
     }
+    IQP_TRY(launch_support_list(G, p.m, ldg, p.n, at<int4>(ws, p.off_sup), st));
     IQP_TRY(launch_parity_gather(p.n, A, p.l, lda, G, p.m, ldg, at<uint64_t>(ws, p.off_pa), p.ldp,
                                  at<uint64_t>(ws, p.off_pat), p.ldlt, rt, st, sup));
     if (p.indep) {

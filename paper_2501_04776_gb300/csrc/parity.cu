@@ -243,20 +243,52 @@ __global__ void __launch_bounds__(kTT) k_bit_transpose(const uint32_t *__restric
                        out + (int64_t)blockIdx.y * out_bs32, ld_out32, gx, blockIdx.x);
 }
 
-// Two bit transposes of different shapes in one launch: blocks [0, tiles0)
-// take the first, the rest the second.
+// Gate j's support entry (q0, q1, q2, |supp g_j|) from its packed row, one thread.
+__device__ __forceinline__ int4 support_entry(const uint64_t *__restrict__ row, int64_t n) {
+    const int64_t nw = (n + 63) >> 6;
+    int cnt = 0, q0 = 0, q1 = 0, q2 = 0;
+    for (int64_t w = 0; w < nw; ++w) {
+        uint64_t word = row[w];
+        if (w == nw - 1 && (n & 63)) word &= (1ull << (n & 63)) - 1ull;  // never a qubit >= n
+        while (word) {
+            const int q = (int)(64 * w) + __ffsll((long long)word) - 1;
+            word &= word - 1ull;
+            if (cnt == 0) q0 = q;
+            else if (cnt == 1) q1 = q;
+            else if (cnt == 2) q2 = q;
+            ++cnt;
+        }
+    }
+    return make_int4(q0, q1, q2, cnt);
+}
+
+// The parity step's preparation in one launch: two bit transposes of
+// different shapes (blocks [0, a.tiles) take the first, the next b.tiles the
+// second) and, in the blocks after them, the gates' support list (one gate per
+// thread; rows of at most 16 words).
 struct BitTransposeJob {
     const uint32_t *in;
     int64_t in_rows, in_cols, ld_in32;
     uint32_t *out;
     int64_t ld_out32, gx, tiles;
 };
-__global__ void __launch_bounds__(kTT) k_bit_transpose_two(BitTransposeJob a, BitTransposeJob b) {
+struct SupportJob {
+    const uint64_t *G;
+    int64_t m, ldg, n;
+    int4 *sup;
+};
+__global__ void __launch_bounds__(kTT) k_parity_prep(BitTransposeJob a, BitTransposeJob b, SupportJob g) {
     __shared__ uint32_t tin[kTT][kTW + 1];  // transposed in place
-    const bool second = (int64_t)blockIdx.x >= a.tiles;
+    const int64_t bid = blockIdx.x;
+    if (bid >= a.tiles + b.tiles) {
+        const int64_t j = (bid - a.tiles - b.tiles) * kTT + threadIdx.x;
+        if (j < g.m && IQP_IN(j, g.m, 13)) g.sup[j] = support_entry(g.G + j * g.ldg, g.n);
+        return;
+    }
+    const bool second = bid >= a.tiles;
     bit_transpose_tile(tin, second ? b.in : a.in, second ? b.in_rows : a.in_rows, second ? b.in_cols : a.in_cols,
                        second ? b.ld_in32 : a.ld_in32, second ? b.out : a.out, second ? b.ld_out32 : a.ld_out32,
-                       second ? b.gx : a.gx, (int64_t)blockIdx.x - (second ? a.tiles : 0));
+                       second ? b.gx : a.gx, bid - (second ? a.tiles : 0));
 }
 
 // Support gather and transpose in one pass, one thread per 32 x 32-bit block.
@@ -575,24 +607,8 @@ __global__ void __launch_bounds__(256) k_support_list(const uint64_t *__restrict
 // (n <= 1024): a warp per generator would leave most lanes idle there.
 __global__ void __launch_bounds__(256) k_support_list_short(const uint64_t *__restrict__ G, int64_t m, int64_t ldg,
                                                              int64_t n, int4 *__restrict__ sup) {
-    const int64_t nw = (n + 63) >> 6;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t *row = G + j * ldg;
-        int cnt = 0, q0 = 0, q1 = 0, q2 = 0;
-        for (int64_t w = 0; w < nw; ++w) {
-            uint64_t word = row[w];
-            if (w == nw - 1 && (n & 63)) word &= (1ull << (n & 63)) - 1ull;  // never a qubit >= n
-            while (word) {
-                const int q = (int)(64 * w) + __ffsll((long long)word) - 1;
-                word &= word - 1ull;
-                if (cnt == 0) q0 = q;
-                else if (cnt == 1) q1 = q;
-                else if (cnt == 2) q2 = q;
-                ++cnt;
-            }
-        }
-        if (IQP_IN(j, m, 13)) sup[j] = make_int4(q0, q1, q2, cnt);
-    }
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        if (IQP_IN(j, m, 13)) sup[j] = support_entry(G + j * ldg, n);
 }
 
 }  // namespace
@@ -666,9 +682,16 @@ cudaError_t launch_gather_transpose(bool i32, int64_t gx, const int4 *sup, const
     return cudaGetLastError();
 }
 
-cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const int4 *sup,
-                                       int64_t ldp, const ParitySide *side, int nside, cudaStream_t st) {
+cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, int4 *sup,
+                                       bool form_sup, int64_t ldp, const ParitySide *side, int nside,
+                                       cudaStream_t st) {
     if (nside < 1 || nside > 2 || ldp % 2 != 0) return cudaErrorInvalidValue;
+    // the support list in the preparation launch where its rows are short, else on its own first
+    const bool sup_in_prep = form_sup && cdiv(n, 64) <= 16;
+    if (form_sup && !sup_in_prep) {
+        const cudaError_t e = launch_support_list(G, m, ldg, n, sup, st);
+        if (e != cudaSuccess) return e;
+    }
     BitTransposeJob bt[2] = {};
     for (int k = 0; k < nside; ++k) {
         const ParitySide &d = side[k];
@@ -676,10 +699,12 @@ cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, 
                                 reinterpret_cast<uint32_t *>(d.RT), 2 * d.ldpt, cdiv(d.ldpt * 64, kTT), 0};
         bt[k].tiles = bt[k].gx * cdiv(n, kTT);
     }
-    if (bt[0].tiles + bt[1].tiles > 0x7FFFFFFFll) return cudaErrorInvalidValue;
+    const int64_t sl_blocks = sup_in_prep ? cdiv(m, kTT) : 0;
+    if (bt[0].tiles + bt[1].tiles + sl_blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
     {
         LaunchScope ls(IQP_KERNEL_PARITY, st);
-        k_bit_transpose_two<<<(unsigned)(bt[0].tiles + bt[1].tiles), kTT, 0, st>>>(bt[0], bt[1]);
+        k_parity_prep<<<(unsigned)(bt[0].tiles + bt[1].tiles + sl_blocks), kTT, 0, st>>>(
+            bt[0], bt[1], SupportJob{G, m, ldg, n, sup});
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -712,7 +737,7 @@ cudaError_t launch_parity_gather(int64_t n, const uint64_t *R, int64_t rows, int
     if (sup != nullptr && P != nullptr && ldp % 2 == 0) {
         // with the gates' support list (launch_support_list): P^T and P from one pass
         const ParitySide side{R, rows, ldr, P, PT, ldpt, RT};
-        return launch_parity_gather_fused(n, G, m, ldg, sup, ldp, &side, 1, st);
+        return launch_parity_gather_fused(n, G, m, ldg, const_cast<int4 *>(sup), false, ldp, &side, 1, st);
     }
     cudaError_t e = bit_transpose(R, rows, n, ldr, RT, ldpt, st);
     if (e != cudaSuccess) return e;

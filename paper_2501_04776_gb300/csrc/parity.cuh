@@ -17,9 +17,12 @@ struct ParitySide {
 };
 
 // Fused support-gather parities of one or two row matrices sharing the gates
-// G (m x ldg words over n qubits) and their support list `sup`: both R^T in
-// one launch, then P^T and P of both in one launch. ldp even, each ldpt even.
-cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, const int4 *sup,
-                                       int64_t ldp, const ParitySide *side, int nside, cudaStream_t st);
+// G (m x ldg words over n qubits) and their support list `sup` (formed here
+// first if form_sup, in the same launch as both R^T where rows are short):
+// both R^T in one launch, then P^T and P of both in one launch. ldp even,
+// each ldpt even.
+cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, int64_t ldg, int4 *sup,
+                                       bool form_sup, int64_t ldp, const ParitySide *side, int nside,
+                                       cudaStream_t st);
 
 }  // namespace iqp
