@@ -386,7 +386,7 @@ def parity_roofline(kt, peaks, n, m, l, s, steps, calls=2, loworder=False):
     ms = kt["parity"]["total_ms"] / max(1, steps)
     hbm = peaks.get("hbm_gbs") or 6800.0
     gbs = nbytes / (ms * 1e-3) / 1e9
-    names = "k_support_list + k_bit_transpose" if loworder else "k_support_list + k_bit_transpose_two + k_gather_transpose"
+    names = "k_support_list + k_bit_transpose" if loworder else "k_parity_prep + k_gather_transpose"
     return {"bound": "hbm", "kernels": names, "bytes_per_step": nbytes,
             "ms_per_step": round(ms, 4), "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
             "frac": round(gbs / hbm, 4), "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
