@@ -563,6 +563,47 @@ print(json.dumps({"ev": float(np.max(np.abs(ev.cpu().numpy() - wev))), "se": flo
     assert r["ev"] <= TOL["split_bf16"] and r["se"] <= TOL["split_bf16"] and r["g"] <= GRAD_RTOL
 
 
+def test_sixteen_warp_parity_gather_is_bit_exact():
+    """The fused parity gather in CTAs of 16 warps (IQP_GATHER_WARPS=16: 512
+    gates x 1024 rows per CTA) instead of 8: P and P^T bit-exact against the
+    oracle on multi-tile ragged shapes, and the estimator that reads them,
+    in a fresh process."""
+    import json
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import json, numpy as np, torch, oracle
+from paper_2501_04776_gb300 import api, inputs as I
+d = api.to_device_bits
+ok = True
+for n, m, rows in [(200, 1100, 2100), (130, 1537, 1025), (777, 300, 129)]:
+    rng = I.Rng(500 + n)
+    R = I.bernoulli_bits(rng, rows, n, 0.5, 1)
+    G = I.random_k_body(rng, m, n, [1, 2, 3], 2) if n != 777 else I.bernoulli_bits(rng, m, n, 0.5, 2)
+    P, PT = api.parity_gather(n, d(R), d(G))
+    want = oracle.parity(n, R, G)
+    gP = I.unpack_bits(P.cpu().numpy().view(np.uint64), P.shape[1] * 64)
+    gT = I.unpack_bits(PT.cpu().numpy().view(np.uint64), PT.shape[1] * 64)
+    ok = ok and np.array_equal(gP[:, :m], want) and not gP[:, m:].any()
+    ok = ok and np.array_equal(gT[:, :rows], want.T) and not gT[:, rows:].any()
+rng = I.Rng(8)
+n, m, l, s = 130, 1000, 260, 520
+G = I.random_k_body(rng, m, n, [1, 2, 3], 1); th = (0.3 * rng.normal(m, 2)).astype(np.float32)
+A = I.bernoulli_bits(rng, l, n, 0.1, 3); Z = I.uniform_bits(rng, s, n, 4)
+ev, se = api.expval_raw(n, torch.from_numpy(th).cuda(), d(G), d(A), d(Z), "split_bf16")
+wev, wse, _, _ = oracle.expval(n, G, A, Z, th.astype(np.float64))
+print(json.dumps({"bits": bool(ok), "ev": float(np.max(np.abs(ev.cpu().numpy() - wev))),
+                  "se": float(np.max(np.abs(se.cpu().numpy() - wse))), "status": api.read_status()}))
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, IQP_GATHER_WARPS="16", PYTHONPATH=root)
+    out = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    assert r["bits"] and r["status"] == 0
+    assert r["ev"] <= TOL["split_bf16"] and r["se"] <= TOL["split_bf16"]
+
 def test_two_sample_tile_phase_matches_single_tiles_and_oracle():
     """The split-BF16 phase of CTA pairs runs its full rounds as tiles of two
     256-sample tiles against each A stage (running sums in global memory) and
