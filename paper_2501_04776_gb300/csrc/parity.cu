@@ -277,12 +277,33 @@ struct SupportJob {
     int64_t m, ldg, n;
     int4 *sup;
 };
+constexpr int kSlGates = 256;  // gates per support-list block of k_parity_prep
 __global__ void __launch_bounds__(kTT) k_parity_prep(BitTransposeJob a, BitTransposeJob b, SupportJob g) {
-    __shared__ uint32_t tin[kTT][kTW + 1];  // transposed in place
+    __shared__ __align__(16) uint32_t tin[kTT][kTW + 1];  // transposed in place
     const int64_t bid = blockIdx.x;
     if (bid >= a.tiles + b.tiles) {
-        const int64_t j = (bid - a.tiles - b.tiles) * kTT + threadIdx.x;
-        if (j < g.m && IQP_IN(j, g.m, 13)) g.sup[j] = support_entry(g.G + j * g.ldg, g.n);
+        // 256 gates: their rows (at most 16 words) staged in tin with coalesced loads, all in flight
+        // together (row r at 17 r), then one thread scans each row there
+        uint64_t *rows = reinterpret_cast<uint64_t *>(&tin[0][0]);
+        static_assert(kSlGates * 17 * 8 <= sizeof(tin), "staged rows");
+        const int nw = (int)((g.n + 63) >> 6);
+        const int64_t j0 = (bid - a.tiles - b.tiles) * kSlGates;
+        uint64_t v[kSlGates * 16 / kTT];
+#pragma unroll
+        for (int k = 0; k < kSlGates * 16 / kTT; ++k) {
+            const int idx = threadIdx.x + kTT * k, r = idx >> 4, w = idx & 15;
+            const int64_t j = j0 + r;
+            v[k] = (w < nw && j < g.m && IQP_IN(j * g.ldg + w, g.m * g.ldg, 16)) ? g.G[j * g.ldg + w] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < kSlGates * 16 / kTT; ++k) {
+            const int idx = threadIdx.x + kTT * k;
+            rows[17 * (idx >> 4) + (idx & 15)] = v[k];
+        }
+        __syncthreads();
+        const int64_t j = j0 + threadIdx.x;
+        if (threadIdx.x < kSlGates && j < g.m && IQP_IN(j, g.m, 13))
+            g.sup[j] = support_entry(rows + 17 * threadIdx.x, g.n);
         return;
     }
     const bool second = bid >= a.tiles;
@@ -699,7 +720,7 @@ cudaError_t launch_parity_gather_fused(int64_t n, const uint64_t *G, int64_t m, 
                                 reinterpret_cast<uint32_t *>(d.RT), 2 * d.ldpt, cdiv(d.ldpt * 64, kTT), 0};
         bt[k].tiles = bt[k].gx * cdiv(n, kTT);
     }
-    const int64_t sl_blocks = sup_in_prep ? cdiv(m, kTT) : 0;
+    const int64_t sl_blocks = sup_in_prep ? cdiv(m, kSlGates) : 0;
     if (bt[0].tiles + bt[1].tiles + sl_blocks > 0x7FFFFFFFll) return cudaErrorInvalidValue;
     {
         LaunchScope ls(IQP_KERNEL_PARITY, st);
